@@ -1,0 +1,19 @@
+"""CPU FP64 oracle of the Metropolis sweep (test infrastructure only).
+
+Only the tests, `__graft_entry__.smoke()` and the benchmark's CPU-baseline leg import
+this package. The CUDA library never does, and shares no code with it.
+"""
+
+from .oracle import (  # noqa: F401
+    build,
+    delta_e,
+    energy,
+    greedy_colour,
+    init_spins,
+    magnetisation,
+    philox4x32_10,
+    renormalise,
+    run,
+    sphere,
+    uniform,
+)

@@ -1,0 +1,231 @@
+"""ctypes binding of the C oracle (vegas_oracle.c), built with gcc on first use.
+
+Test infrastructure only: see the header of vegas_oracle.c for what is computed and which
+passage of the paper each part follows.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vegas_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "libvegas_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ERR_NAN = 1
+ERR_SPHERE = 2
+
+
+class _Sample(C.Structure):
+    _fields_ = [
+        ("n", C.c_int32),
+        ("pad_", C.c_int32),
+        ("row_ptr", C.c_void_p),
+        ("col", C.c_void_p),
+        ("J", C.c_void_p),
+        ("spin_norm", C.c_void_p),
+        ("field_axis", C.c_void_p),
+        ("k_uni", C.c_void_p),
+        ("e_uni", C.c_void_p),
+        ("k_cub", C.c_void_p),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with FMA contraction off; returns the path of the .so."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared",
+               _SRC, "-o", tmp, "-lm", "-lpthread"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def _configure(lib):
+    P = C.c_void_p
+    lib.vo_philox4x32_10.argtypes = [P, P, P]
+    lib.vo_sphere.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, P]
+    lib.vo_sphere.restype = C.c_int
+    lib.vo_uniform.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]
+    lib.vo_uniform.restype = C.c_double
+    lib.vo_greedy_colour.argtypes = [C.c_int32, P, P, P]
+    lib.vo_greedy_colour.restype = C.c_int32
+    lib.vo_energy.argtypes = [P, P, C.c_double]
+    lib.vo_energy.restype = C.c_double
+    lib.vo_magnetisation.argtypes = [C.c_int32, P, P]
+    lib.vo_delta_e.argtypes = [P, P, C.c_int32, P, C.c_double]
+    lib.vo_delta_e.restype = C.c_double
+    lib.vo_renormalise.argtypes = [P, P]
+    lib.vo_init_spins.argtypes = [P, C.c_uint64, C.c_int32, P]
+    lib.vo_init_spins.restype = C.c_int
+    lib.vo_run.argtypes = [P, P, C.c_uint64, C.c_int32, C.c_int32, P, P, C.c_int32, C.c_int32,
+                           C.c_uint32, P, C.c_int32, P, P, C.c_int32, C.c_int32, C.c_int32]
+    lib.vo_run.restype = C.c_int
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _configure(C.CDLL(build()))
+    return _lib
+
+
+class use_library:
+    """Context manager that points every oracle call at another build of vegas_oracle.c
+    (the mutation tests compile deliberately broken copies and check that pins fail)."""
+
+    def __init__(self, path: str):
+        self.lib = _configure(C.CDLL(path))
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self.saved = _lib
+        _lib = self.lib
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def compile_source(text: str, out_path: str) -> str:
+    """Compile C source text with the oracle's flags into out_path (a shared library)."""
+    src = out_path + ".c"
+    with open(src, "w") as f:
+        f.write(text)
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared", src,
+                    "-o", out_path, "-lm", "-lpthread"], check=True)
+    return out_path
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class _Bound:
+    """Holds the contiguous arrays a _Sample points into, for the call's lifetime."""
+
+    def __init__(self, s):
+        def f64(a, shape=None):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            return a if shape is None else a.reshape(shape)
+
+        n = s.n_sites
+        self.row_ptr = np.ascontiguousarray(s.row_ptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(s.col, dtype=np.int32)
+        self.J = f64(s.J)
+        self.spin_norm = f64(s.spin_norm)
+        self.field_axis = f64(s.field_axis, (n, 3))
+        self.k_uni = f64(s.k_uni)
+        self.e_uni = f64(s.e_uni, (n, 3))
+        self.k_cub = f64(s.k_cub)
+        self.c = _Sample(n, 0, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.J), _ptr(self.spin_norm),
+                         _ptr(self.field_axis), _ptr(self.k_uni), _ptr(self.e_uni), _ptr(self.k_cub))
+
+    @property
+    def ref(self):
+        return C.byref(self.c)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    _load().vo_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
+    return o
+
+
+def sphere(seed: int, c0: int, c1: int, c2: int, purpose: int):
+    """Returns (unit vector, candidates used)."""
+    o = np.zeros(3)
+    k = _load().vo_sphere(seed, c0, c1, c2, purpose, _ptr(o))
+    return o, k
+
+
+def uniform(seed: int, c0: int, c1: int, c2: int, c3: int) -> float:
+    return _load().vo_uniform(seed, c0, c1, c2, c3)
+
+
+def greedy_colour(sample):
+    n = sample.n_sites
+    rp = np.ascontiguousarray(sample.row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(sample.col, dtype=np.int32)
+    out = np.zeros(max(n, 1), dtype=np.int32)
+    nc = _load().vo_greedy_colour(n, _ptr(rp), _ptr(cl), _ptr(out))
+    return out[:n], int(nc)
+
+
+def energy(sample, S, B: float) -> float:
+    b = _Bound(sample)
+    S = np.ascontiguousarray(S, dtype=np.float64).reshape(sample.n_sites, 3)
+    return _load().vo_energy(b.ref, _ptr(S), float(B))
+
+
+def magnetisation(S) -> np.ndarray:
+    S = np.ascontiguousarray(S, dtype=np.float64).reshape(-1, 3)
+    o = np.zeros(3)
+    _load().vo_magnetisation(S.shape[0], _ptr(S), _ptr(o))
+    return o
+
+
+def delta_e(sample, S, i: int, trial, B: float) -> float:
+    b = _Bound(sample)
+    S = np.ascontiguousarray(S, dtype=np.float64).reshape(sample.n_sites, 3)
+    t = np.ascontiguousarray(trial, dtype=np.float64)
+    return _load().vo_delta_e(b.ref, _ptr(S), int(i), _ptr(t), float(B))
+
+
+def renormalise(sample, S) -> np.ndarray:
+    b = _Bound(sample)
+    S = np.array(S, dtype=np.float64).reshape(sample.n_sites, 3)
+    _load().vo_renormalise(b.ref, _ptr(S))
+    return S
+
+
+def init_spins(sample, seed: int, inst: int) -> np.ndarray:
+    b = _Bound(sample)
+    S = np.zeros((sample.n_sites, 3))
+    err = _load().vo_init_spins(b.ref, seed, inst, _ptr(S))
+    if err:
+        raise RuntimeError(f"oracle init error {err}")
+    return S
+
+
+def run(sample, T, B, mcs: int, seed: int = 1, spins=None, inst_base: int = 0, t0: int = 0,
+        colour=None, log_mcs: int = 0, mode: int = 0, n_threads: int = 1):
+    """Run the chain for every instance in T's first axis.
+
+    T, B: [n_inst, n_steps]. spins: None (Philox initial state) or [n_inst, n, 3].
+    Returns dict(spins=[n_inst,n,3], history=[n_inst, n_steps*mcs, 4], accept_log=
+    [n_inst, log_mcs, n] uint8 or None, err=int).
+    """
+    T = np.ascontiguousarray(np.atleast_2d(T), dtype=np.float64)
+    B = np.ascontiguousarray(np.broadcast_to(np.atleast_2d(B), T.shape), dtype=np.float64)
+    n_inst, n_steps = T.shape
+    n = sample.n_sites
+    b = _Bound(sample)
+    init = 1 if spins is None else 0
+    S = np.zeros((n_inst, n, 3)) if spins is None else np.array(spins, dtype=np.float64).reshape(n_inst, n, 3)
+    hist = np.zeros((n_inst, n_steps * mcs, 4))
+    log = np.zeros((n_inst, log_mcs, n), dtype=np.uint8) if log_mcs > 0 else None
+    cl = None if colour is None else np.ascontiguousarray(colour, dtype=np.int32)
+    err = _load().vo_run(b.ref, _ptr(cl), seed, n_inst, inst_base, _ptr(T), _ptr(B), n_steps, mcs, t0, _ptr(S),
+                         init, _ptr(hist), _ptr(log), log_mcs, mode, n_threads)
+    if err < 0:
+        raise ValueError("oracle rejected its arguments")
+    return {"spins": S, "history": hist, "accept_log": log, "err": err}

@@ -1,0 +1,430 @@
+/*
+ * CPU FP64 oracle of the Metropolis sweep of the classical Heisenberg model.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the library's product path links, loads or calls
+ * this file; only the tests, the smoke check and the benchmark's CPU-baseline leg do.
+ * It shares no code with the CUDA library: its Philox generator, sphere sampler, greedy
+ * colouring and energy are written here again, from their published definitions.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no -ffast-math). FMA contraction must
+ * stay off: the FP64 GPU path is compared with this code bit for bit.
+ *
+ * What it computes, with the paper's notation (Sec. III.A-B):
+ *   Energy (Eq. 1-3), S_i = s_i * unit vector, each undirected bond counted once:
+ *     E = -1/2 sum_i sum_{j in N(i)} J_ij S_i.S_j - B sum_i S_i.n_i
+ *         - sum_i k_i (S_i.e_i)^2 - sum_i kc_i (Sx^2 Sy^2 + Sy^2 Sz^2 + Sx^2 Sz^2)_i
+ *     The anisotropy enters Eq. 1 with a minus sign, so k > 0 is an easy axis.
+ *   Metropolis step (Eq. 4): trial S' uniform on the sphere of radius s_i ("random"
+ *     update policy); accept when dE <= 0, else when u < exp(-dE / T), k_B = 1.
+ *   One MCS = one attempt per spin. Mode 0 sweeps the colour classes of a proper
+ *     colouring in colour order (sites of one class are not linked, so any order inside a
+ *     class gives the same result; increasing site id is used). Mode 1 is the paper's
+ *     literal form: N attempts on uniformly drawn sites.
+ *   History: after every MCS, E from the definition above and M = sum_i S_i (Sec. II).
+ *   After the last MCS of each temperature/field step every spin is rescaled to its norm
+ *     s_i (periodic renormalisation of |S|).
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = (seed low 32
+ * bits, seed high 32 bits), counter = (site, MCS t, instance, purpose | k):
+ *   purpose 0x00000|k  trial candidate k of the sphere sampler
+ *   purpose 0x10000    acceptance uniform
+ *   purpose 0x20000|k  initial spin candidate k (with t = 0xFFFFFFFF)
+ *   purposes 0x50000 (site pick), 0x60000|k (trial), 0x70000 (acceptance) in mode 1,
+ *     where the first counter word is the attempt index instead of the site.
+ * Sphere sampler: Marsaglia, Ann. Math. Stat. 43 (1972) 645: a, b uniform in [0,1) from
+ *   53-bit words, u1 = 2a-1, u2 = 2b-1, s = u1^2+u2^2, reject s >= 1, then
+ *   (2 u1 sqrt(1-s), 2 u2 sqrt(1-s), 1-2s). Uses only correctly rounded operations.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t n;
+    int32_t pad_;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const double *J;
+    const double *spin_norm;  /* NULL: all 1 */
+    const double *field_axis; /* NULL: all +z */
+    const double *k_uni;      /* NULL: all 0 */
+    const double *e_uni;      /* NULL: all +z */
+    const double *k_cub;      /* NULL: all 0 */
+} vo_sample;
+
+enum { VO_ERR_NAN = 1, VO_ERR_SPHERE = 2 };
+
+/* ---------------------------------------------------------------- Philox4x32-10 */
+
+static void philox_round(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k0;
+    const uint32_t n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+void vo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        philox_round(c, k0, k1);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    memcpy(out, c, sizeof c);
+}
+
+static void philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t w[4]) {
+    const uint32_t ctr[4] = {c0, c1, c2, c3};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    vo_philox4x32_10(ctr, key, w);
+}
+
+/* 53-bit uniform in [0, 1) from two words: (hi * 2^21 + lo >> 11) * 2^-53. */
+static double u53(uint32_t hi, uint32_t lo) {
+    const uint64_t m = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
+    return (double)m * 0x1p-53;
+}
+
+/* Marsaglia (1972) point on the unit sphere; returns candidates used, or -1 past 64. */
+int vo_sphere(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t purpose, double out[3]) {
+    for (uint32_t k = 0; k < 64; ++k) {
+        uint32_t w[4];
+        philox(seed, c0, c1, c2, purpose | k, w);
+        const double a = u53(w[0], w[1]);
+        const double b = u53(w[2], w[3]);
+        const double u1 = 2.0 * a - 1.0;
+        const double u2 = 2.0 * b - 1.0;
+        const double s = u1 * u1 + u2 * u2;
+        if (s >= 1.0) continue;
+        const double q = sqrt(1.0 - s);
+        out[0] = (2.0 * u1) * q;
+        out[1] = (2.0 * u2) * q;
+        out[2] = 1.0 - 2.0 * s;
+        return (int)k + 1;
+    }
+    out[0] = 0.0;
+    out[1] = 0.0;
+    out[2] = 1.0;
+    return -1;
+}
+
+double vo_uniform(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
+    uint32_t w[4];
+    philox(seed, c0, c1, c2, c3, w);
+    return u53(w[0], w[1]);
+}
+
+/* ---------------------------------------------------------------- colouring */
+
+/* Greedy colouring: visit sites in index order, give each the smallest colour not used by
+ * an already coloured neighbour. Returns the number of colours. */
+int32_t vo_greedy_colour(int32_t n, const int64_t *row_ptr, const int32_t *col, int32_t *colour) {
+    int32_t nc = 0;
+    int32_t cap = 64;
+    int32_t *mark = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    for (int32_t c = 0; c < cap; ++c) mark[c] = -1;
+    for (int32_t i = 0; i < n; ++i) colour[i] = -1;
+    for (int32_t i = 0; i < n; ++i) {
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int32_t j = col[e];
+            const int32_t cj = colour[j];
+            if (cj >= 0) mark[cj] = i; /* every assigned colour is < cap */
+        }
+        int32_t c = 0;
+        while (c < cap && mark[c] == i) ++c;
+        if (c == cap) {
+            int32_t ncap = cap * 2;
+            mark = (int32_t *)realloc(mark, sizeof(int32_t) * (size_t)ncap);
+            for (int32_t q = cap; q < ncap; ++q) mark[q] = -1;
+            cap = ncap;
+        }
+        colour[i] = c;
+        if (c + 1 > nc) nc = c + 1;
+    }
+    free(mark);
+    return nc;
+}
+
+/* ---------------------------------------------------------------- energy */
+
+static double norm_of(const vo_sample *s, int32_t i) { return s->spin_norm ? s->spin_norm[i] : 1.0; }
+
+static void axis_of(const double *a, int32_t i, double v[3]) {
+    if (a) {
+        v[0] = a[3 * (int64_t)i];
+        v[1] = a[3 * (int64_t)i + 1];
+        v[2] = a[3 * (int64_t)i + 2];
+    } else {
+        v[0] = 0.0;
+        v[1] = 0.0;
+        v[2] = 1.0;
+    }
+}
+
+static double cubic_form(const double v[3]) {
+    const double xx = v[0] * v[0], yy = v[1] * v[1], zz = v[2] * v[2];
+    return (xx * yy + yy * zz) + xx * zz;
+}
+
+/* Energy of site i's own terms plus half of its bonds (Eq. 1-3). */
+static double site_energy(const vo_sample *s, const double *S, int32_t i, double B) {
+    const double *Si = S + 3 * (int64_t)i;
+    double ex = 0.0;
+    for (int64_t e = s->row_ptr[i]; e < s->row_ptr[i + 1]; ++e) {
+        const double *Sj = S + 3 * (int64_t)s->col[e];
+        ex += s->J[e] * ((Si[0] * Sj[0] + Si[1] * Sj[1]) + Si[2] * Sj[2]);
+    }
+    double n[3], ea[3];
+    axis_of(s->field_axis, i, n);
+    axis_of(s->e_uni, i, ea);
+    const double k = s->k_uni ? s->k_uni[i] : 0.0;
+    const double kc = s->k_cub ? s->k_cub[i] : 0.0;
+    const double zee = (Si[0] * n[0] + Si[1] * n[1]) + Si[2] * n[2];
+    const double pe = (Si[0] * ea[0] + Si[1] * ea[1]) + Si[2] * ea[2];
+    return -0.5 * ex - B * zee - k * (pe * pe) - kc * cubic_form(Si);
+}
+
+double vo_energy(const vo_sample *s, const double *S, double B) {
+    double E = 0.0;
+    for (int32_t i = 0; i < s->n; ++i) E += site_energy(s, S, i, B);
+    return E;
+}
+
+void vo_magnetisation(int32_t n, const double *S, double M[3]) {
+    M[0] = M[1] = M[2] = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        M[0] += S[3 * (int64_t)i];
+        M[1] += S[3 * (int64_t)i + 1];
+        M[2] += S[3 * (int64_t)i + 2];
+    }
+}
+
+/* Energy change of replacing S_i by Sp (Eq. 1-3), evaluated in a fixed order:
+ * h = sum_j J_ij S_j (row order) + B n_i; d = Sp - S_i;
+ * dE = (-(d.h) - k((Sp.e)^2 - (S.e)^2)) - kc(cub(Sp) - cub(S)). */
+double vo_delta_e(const vo_sample *s, const double *S, int32_t i, const double Sp[3], double B) {
+    double hx = 0.0, hy = 0.0, hz = 0.0;
+    for (int64_t e = s->row_ptr[i]; e < s->row_ptr[i + 1]; ++e) {
+        const double *Sj = S + 3 * (int64_t)s->col[e];
+        const double J = s->J[e];
+        hx = hx + J * Sj[0];
+        hy = hy + J * Sj[1];
+        hz = hz + J * Sj[2];
+    }
+    double n[3], ea[3];
+    axis_of(s->field_axis, i, n);
+    axis_of(s->e_uni, i, ea);
+    hx = hx + B * n[0];
+    hy = hy + B * n[1];
+    hz = hz + B * n[2];
+    const double *Si = S + 3 * (int64_t)i;
+    const double dx = Sp[0] - Si[0], dy = Sp[1] - Si[1], dz = Sp[2] - Si[2];
+    const double dEex = -((dx * hx + dy * hy) + dz * hz);
+    const double k = s->k_uni ? s->k_uni[i] : 0.0;
+    const double kc = s->k_cub ? s->k_cub[i] : 0.0;
+    const double pn = (Sp[0] * ea[0] + Sp[1] * ea[1]) + Sp[2] * ea[2];
+    const double po = (Si[0] * ea[0] + Si[1] * ea[1]) + Si[2] * ea[2];
+    const double dEan = -(k * (pn * pn - po * po));
+    const double dEcub = -(kc * (cubic_form(Sp) - cubic_form(Si)));
+    return (dEex + dEan) + dEcub;
+}
+
+/* S_i <- s_i * S_i / |S_i|, with f = s_i / sqrt((x^2 + y^2) + z^2). */
+void vo_renormalise(const vo_sample *s, double *S) {
+    for (int32_t i = 0; i < s->n; ++i) {
+        double *v = S + 3 * (int64_t)i;
+        const double n2 = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
+        const double f = norm_of(s, i) / sqrt(n2);
+        v[0] = v[0] * f;
+        v[1] = v[1] * f;
+        v[2] = v[2] * f;
+    }
+}
+
+/* Initial state: S_i = s_i * sphere(counter = (i, 0xFFFFFFFF, inst, 0x20000 | k)). */
+int vo_init_spins(const vo_sample *s, uint64_t seed, int32_t inst, double *S) {
+    int err = 0;
+    for (int32_t i = 0; i < s->n; ++i) {
+        double u[3];
+        if (vo_sphere(seed, (uint32_t)i, 0xFFFFFFFFu, (uint32_t)inst, 0x20000u, u) < 0) err |= VO_ERR_SPHERE;
+        const double sn = norm_of(s, i);
+        S[3 * (int64_t)i] = sn * u[0];
+        S[3 * (int64_t)i + 1] = sn * u[1];
+        S[3 * (int64_t)i + 2] = sn * u[2];
+    }
+    return err;
+}
+
+/* ---------------------------------------------------------------- the Markov chain */
+
+typedef struct {
+    const vo_sample *s;
+    const int32_t *order;   /* sites in sweep order: colour 0 by id, colour 1 by id, ... */
+    uint64_t seed;
+    int32_t inst;
+    const double *T, *B;    /* this instance's schedule, n_steps entries */
+    int32_t n_steps, mcs;
+    uint32_t t0;
+    double *S;              /* n*3 */
+    double *hist;           /* n_steps*mcs*4 */
+    uint8_t *accept_log;    /* log_mcs*n or NULL */
+    int32_t log_mcs;
+    int32_t mode;
+    int err;
+} vo_job;
+
+/* One Metropolis attempt on site i (Eq. 4). Trial and acceptance counters are
+ * (c0, t, inst, purpose). Returns 1 when accepted. */
+static int attempt(vo_job *jb, int32_t i, uint32_t c0, uint32_t t, double beta, double B, uint32_t p_trial,
+                   uint32_t p_accept) {
+    const vo_sample *s = jb->s;
+    double u[3];
+    if (vo_sphere(jb->seed, c0, t, (uint32_t)jb->inst, p_trial, u) < 0) jb->err |= VO_ERR_SPHERE;
+    const double sn = norm_of(s, i);
+    const double Sp[3] = {sn * u[0], sn * u[1], sn * u[2]};
+    const double dE = vo_delta_e(s, jb->S, i, Sp, B);
+    int acc;
+    if (dE <= 0.0) {
+        acc = 1;
+    } else {
+        const double r = vo_uniform(jb->seed, c0, t, (uint32_t)jb->inst, p_accept);
+        acc = r < exp(-(beta * dE));
+    }
+    if (isnan(dE)) {
+        jb->err |= VO_ERR_NAN;
+        acc = 0;
+    }
+    if (acc) {
+        double *Si = jb->S + 3 * (int64_t)i;
+        Si[0] = Sp[0];
+        Si[1] = Sp[1];
+        Si[2] = Sp[2];
+    }
+    return acc;
+}
+
+static void *run_job(void *arg) {
+    vo_job *jb = (vo_job *)arg;
+    const vo_sample *s = jb->s;
+    const int32_t n = s->n;
+    uint32_t t = jb->t0;
+    int64_t rec = 0;
+    for (int32_t st = 0; st < jb->n_steps; ++st) {
+        const double beta = 1.0 / jb->T[st];
+        const double B = jb->B[st];
+        for (int32_t m = 0; m < jb->mcs; ++m) {
+            const int64_t mrun = (int64_t)st * jb->mcs + m;
+            uint8_t *log = (jb->accept_log && mrun < jb->log_mcs) ? jb->accept_log + mrun * n : NULL;
+            if (jb->mode == 0) {
+                for (int32_t q = 0; q < n; ++q) {
+                    const int32_t i = jb->order[q];
+                    const int a = attempt(jb, i, (uint32_t)i, t, beta, B, 0x00000u, 0x10000u);
+                    if (log) log[i] = (uint8_t)a;
+                }
+            } else {
+                for (int32_t a = 0; a < n; ++a) {
+                    const double r = vo_uniform(jb->seed, (uint32_t)a, t, (uint32_t)jb->inst, 0x50000u);
+                    int32_t i = (int32_t)(r * (double)n);
+                    if (i >= n) i = n - 1;
+                    attempt(jb, i, (uint32_t)a, t, beta, B, 0x60000u, 0x70000u);
+                }
+            }
+            double M[3];
+            vo_magnetisation(n, jb->S, M);
+            double *h = jb->hist + rec * 4;
+            h[0] = vo_energy(s, jb->S, B);
+            h[1] = M[0];
+            h[2] = M[1];
+            h[3] = M[2];
+            ++rec;
+            ++t;
+        }
+        vo_renormalise(s, jb->S);
+    }
+    return NULL;
+}
+
+/*
+ * Run n_inst instances of one sample (replicas inst_base .. inst_base+n_inst-1) through
+ * n_steps temperature/field steps of mcs MCS each, starting at global MCS counter t0.
+ *   colour    NULL: greedy colouring; else a colouring (not checked for properness here)
+ *   T, B      [n_inst][n_steps]
+ *   spins     [n_inst][n][3], in/out; when init != 0 it is first filled by vo_init_spins
+ *   history   [n_inst][n_steps*mcs][4] = (E, Mx, My, Mz) after every MCS
+ *   accept_log NULL or [n_inst][log_mcs][n] bytes, 1 where the attempt at that site in
+ *             that MCS was accepted (mode 0 only)
+ * Returns the OR of VO_ERR_* over instances, or -1 on invalid arguments.
+ */
+int vo_run(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t n_inst, int32_t inst_base,
+           const double *T, const double *B, int32_t n_steps, int32_t mcs, uint32_t t0, double *spins, int32_t init,
+           double *history, uint8_t *accept_log, int32_t log_mcs, int32_t mode, int32_t n_threads) {
+    if (!s || s->n < 0 || n_inst < 1 || n_steps < 0 || mcs < 0 || !T || !B || !spins || !history) return -1;
+    const int32_t n = s->n;
+    int32_t *col_own = NULL;
+    const int32_t *cl = colour;
+    int32_t nc = 0;
+    if (!cl) {
+        col_own = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        nc = vo_greedy_colour(n, s->row_ptr, s->col, col_own);
+        cl = col_own;
+    } else {
+        for (int32_t i = 0; i < n; ++i)
+            if (cl[i] + 1 > nc) nc = cl[i] + 1;
+    }
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t q = 0;
+    for (int32_t c = 0; c < nc; ++c)
+        for (int32_t i = 0; i < n; ++i)
+            if (cl[i] == c) order[q++] = i;
+
+    vo_job *jobs = (vo_job *)calloc((size_t)n_inst, sizeof(vo_job));
+    int err = 0;
+    for (int32_t r = 0; r < n_inst; ++r) {
+        vo_job *jb = &jobs[r];
+        jb->s = s;
+        jb->order = order;
+        jb->seed = seed;
+        jb->inst = inst_base + r;
+        jb->T = T + (int64_t)r * n_steps;
+        jb->B = B + (int64_t)r * n_steps;
+        jb->n_steps = n_steps;
+        jb->mcs = mcs;
+        jb->t0 = t0;
+        jb->S = spins + (int64_t)r * n * 3;
+        jb->hist = history + (int64_t)r * n_steps * mcs * 4;
+        jb->accept_log = accept_log ? accept_log + (int64_t)r * log_mcs * n : NULL;
+        jb->log_mcs = log_mcs;
+        jb->mode = mode;
+        if (init) err |= vo_init_spins(s, seed, jb->inst, jb->S);
+    }
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_inst) n_threads = n_inst;
+    /* instances r, r + n_threads, ... run on thread r */
+    for (int32_t base = 0; base < n_inst; base += n_threads) {
+        pthread_t th[256];
+        int32_t cnt = 0;
+        for (int32_t r = base; r < n_inst && cnt < n_threads && cnt < 256; ++r, ++cnt) {
+            if (n_threads == 1) {
+                run_job(&jobs[r]);
+            } else {
+                pthread_create(&th[cnt], NULL, run_job, &jobs[r]);
+            }
+        }
+        if (n_threads > 1)
+            for (int32_t k = 0; k < cnt; ++k) pthread_join(th[k], NULL);
+    }
+    for (int32_t r = 0; r < n_inst; ++r) err |= jobs[r].err;
+    free(jobs);
+    free(order);
+    free(col_own);
+    return err;
+}
