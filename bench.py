@@ -1,0 +1,326 @@
+"""Throughput of the GB300 Metropolis sweep on the large batched spin-glass workload.
+
+Workload (one "step" = one vegas_run over the whole schedule of the workload): 32
+temperature replicas (T geometric 0.1 -> 2.0) of a 256^3 periodic simple-cubic +-J spin
+glass, uniform-on-sphere trial moves, 200 MCS, FP32 spins with FP64 per-MCS E/M history.
+Metric: Metropolis spin-update attempts per second (one attempt per site per MCS).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mcs M]
+
+With N > 1 (launched by torchrun) every rank sweeps its own 32 replicas (instances
+32*rank ...): weak scaling with no collective on the data path; value is the sum over
+ranks divided by the slowest rank's time. `--impl reference` times the CPU FP64 oracle on
+this host's cores on a bounded sample of the same workload (one MCS of one replica per
+core per step).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Metropolis spin-update attempts/s on 1 GB300; batched vs plain; % HBM roofline"
+UNIT = "attempts/s"
+L_SIDE, REPLICAS, MCS, SEED = 256, 32, 200, 1
+# algorithmic bytes per attempt: 16 B read + 16 B write of the FP32 spin (float4), plus one
+# row of six (int32 col, f32 J) links = 48 B shared by the 32 replicas that sweep it together
+BYTES_PER_ATTEMPT = 16 + 16 + 48.0 / REPLICAS
+PASS_KERNEL = "pass32_kernel"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pass32_sg256x32.txt")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1803_07030_gb300", "csrc", "vegas_kernels.cu")
+
+
+def workload_desc(mcs):
+    return {
+        "workload": f"sg256x32: 32 temperature replicas (T 0.1->2.0 geometric) of a {L_SIDE}^3 periodic sc +-J "
+                    f"spin glass, random moves, {mcs} MCS per step, FP32 spins / FP64 history",
+        "sites_per_replica": L_SIDE ** 3,
+        "replicas_per_gpu": REPLICAS,
+        "mcs_per_step": mcs,
+        "l2": "inputs larger than L2 (8.6 GB of spins + 0.8 GB of links per GPU)",
+        "seed": SEED,
+    }
+
+
+def temperatures():
+    return 0.1 * 20.0 ** (np.arange(REPLICAS) / (REPLICAS - 1.0))
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    with open(KERNEL_SOURCE, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it still describes
+    the current kernel source (else None)."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    vals = {}
+    with open(PROFILE_SUMMARY) as f:
+        for line in f:
+            if ":" in line and line.split(":", 1)[0].strip() in ("kernel_source_sha256_16", "dram_bytes_per_launch"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != kernel_hash() or "dram_bytes_per_launch" not in vals:
+        return None
+    return float(vals["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"vegas_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+            self.f.close()
+        return False
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.remove(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline_run(sample, n_threads, mcs=1):
+    """Oracle (CPU FP64, as it stands) on n_threads replicas of the full lattice, one per thread."""
+    import oracle
+
+    T = temperatures()[:n_threads, None]
+    t0 = time.perf_counter()
+    oracle.run(sample, T, np.zeros_like(T), mcs, seed=SEED, n_threads=n_threads)
+    dt = time.perf_counter() - t0
+    return n_threads * sample.n_sites * mcs / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from lattices import sc_periodic
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    n_threads = min(REPLICAS, cores)
+    s = sc_periodic(L_SIDE, bimodal_seed=SEED)
+    for _ in range(args.warmup):
+        cpu_baseline_run(s, n_threads)
+    total, vals = 0.0, []
+    for _ in range(args.steps):
+        v, dt = cpu_baseline_run(s, n_threads)
+        total += dt
+        vals.append(v)
+    value = args.steps * n_threads * s.n_sites / total
+    sample = f"1 MCS of {n_threads} replicas (one per host thread) of the {L_SIDE}^3 lattice per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_desc(args.mcs),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    import paper_1803_07030_gb300 as vg
+    from lattices import sc_periodic
+
+    vg.build()
+    mcs = args.mcs
+    s = sc_periodic(L_SIDE, bimodal_seed=SEED)
+    T = temperatures()[:, None]
+    B = np.zeros_like(T)
+    stream = torch.cuda.current_stream()
+    inst_base = rank * REPLICAS
+    t0 = time.perf_counter()
+    ctx = vg.Context([s], precision=32, replicas=REPLICAS, seed=SEED, inst_base=inst_base, device=dev,
+                     stream=int(stream.cuda_stream), timing=True)
+    create_s = time.perf_counter() - t0
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ctx.run(T, B, mcs)
+    barrier()
+    st0 = ctx.stats()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.run(T, B, mcs)
+        ev1.record(stream)
+        barrier()
+    st1 = ctx.stats()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    attempts_rank = REPLICAS * s.n_sites * mcs * args.steps
+    value = attempts_rank * world / (ms / 1000.0)
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
+    sweeps = st1["sweep_launches"] - st0["sweep_launches"]
+    sweep_ms = (st1["sweep_ms"] - st0["sweep_ms"]) / max(sweeps, 1)
+    attempts_per_launch = REPLICAS * s.n_sites // 2  # one colour class of the checkerboard
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_ATTEMPT * attempts_per_launch / (sweep_ms / 1000.0) / 1e9
+    traffic = profiled_traffic()
+
+    # end to end through the public API with host buffers: schedule in, history out
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.run(T, B, mcs)
+        h = ctx.history()
+    e2e_s = time.perf_counter() - te
+    e2e_value = attempts_rank * world / e2e_s
+    h2d = T.size * 2 * 8 + 40
+    d2h = REPLICAS * mcs * 4 * 8 + 4
+
+    # plain single-instance path on the same lattice: one replica per context, R = 1
+    ctx.close()
+    torch.cuda.synchronize()
+    plain_reps = (0, REPLICAS - 1)
+    plain_ms = 0.0
+    for p in plain_reps:
+        with vg.Context([s], precision=32, replicas=1, seed=SEED, inst_base=inst_base + p, device=dev,
+                        stream=int(stream.cuda_stream)) as q:
+            q.run(T[p:p + 1], B[p:p + 1], 2)  # warm-up
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            q.run(T[p:p + 1], B[p:p + 1], mcs)
+            b.record(stream)
+            torch.cuda.synchronize()
+            plain_ms += a.elapsed_time(b)
+    plain_value = len(plain_reps) * s.n_sites * mcs / (plain_ms / 1000.0)
+
+    line = None
+    if rank == 0:
+        cores = min(REPLICAS, os.cpu_count() or 1)
+        cpu_v, cpu_dt = cpu_baseline_run(s, cores)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_desc(mcs),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                         else "fallback 6.8 TB/s",
+                         "kernel": PASS_KERNEL, "bytes_per_attempt": BYTES_PER_ATTEMPT,
+                         "attempts_per_launch": attempts_per_launch, "avg_launch_ms": sweep_ms},
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"1 MCS of {cores} replicas (one per host thread) of the {L_SIDE}^3 lattice, "
+                                       f"{cpu_dt:.1f} s"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "api": "vegas_run(host T, B) + vegas_history(host buffer)"},
+            "plain": {"value": plain_value, "unit": UNIT, "replicas_timed": len(plain_reps),
+                      "note": "same lattice, one replica per context (R = 1), one launch per colour class"},
+            "batched_over_plain": value / world / plain_value,
+            "gpu_launches": launches,
+            "create_s": create_s,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--mcs", type=int, default=MCS)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

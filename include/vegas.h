@@ -1,0 +1,185 @@
+/*
+ * vegas.h - C-ABI of the GB300 Metropolis sweep of the classical Heisenberg model.
+ *
+ * The library runs the Monte Carlo Metropolis method of Sec. III.B (Eq. 4) on the spin
+ * Hamiltonian of Sec. III.A (Eq. 1-3) for many independent instances on one GPU, and
+ * records energy and magnetization after every Monte Carlo step (MCS) of every
+ * temperature/field step (Sec. II, first feature). Every entry point is plain C: host
+ * pointers and sizes in, status codes out. Nothing here throws, aborts, exits or traps.
+ *
+ * Model (Eq. 1-3), with each undirected bond counted once:
+ *   E = -1/2 sum_i sum_{j in N(i)} J_ij S_i.S_j - B sum_i S_i.n_i
+ *       - sum_i k_i (S_i.e_i)^2 - sum_i kc_i (Sx^2 Sy^2 + Sy^2 Sz^2 + Sx^2 Sz^2)_i
+ *   S_i = s_i * (unit vector); B is a scalar field intensity and n_i the per-site field
+ *   axis (Sec. III.C material file); k > 0 is an easy axis. k_B = 1.
+ * Update policy: "random" (trial uniform on the sphere of radius s_i, Sec. III.B).
+ * Sweep order: one MCS visits every site once, colour class by colour class of a proper
+ *   colouring (greedy in site order unless the caller gives one). Sites of one class
+ *   share no link, so they are updated in parallel with exactly the result of any
+ *   sequential order.
+ *
+ * Instances: n_samples samples, each run as `replicas` independent replicas; instance
+ *   id = inst_base + sample * replicas + replica. Random numbers are Philox4x32-10 keyed
+ *   by the seed, with counter (site id in the caller's numbering, global MCS index,
+ *   instance id, purpose), so a result does not depend on how instances are batched.
+ *
+ * Ownership: every pointer passed in stays owned by the caller and is only read during
+ *   the call. The library owns all device memory and frees it in vegas_destroy.
+ * Errors: a call that fails returns a non-zero vegas_status and stores a message
+ *   readable with vegas_last_error(ctx) (vegas_last_error(NULL) for vegas_create).
+ *   After VEGAS_ECUDA or VEGAS_EDEVICE the context is poisoned: later calls return
+ *   VEGAS_ESTATE, except vegas_last_error, vegas_stats and vegas_destroy.
+ * Threads: one context must not be used from two threads at once.
+ */
+#ifndef VEGAS_H
+#define VEGAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vegas_ctx vegas_ctx;
+
+typedef enum {
+    VEGAS_OK = 0,
+    VEGAS_EINVAL = 1,   /* invalid argument or sample (message says which) */
+    VEGAS_ENOMEM = 2,   /* host or device allocation failed */
+    VEGAS_ECUDA = 3,    /* a CUDA runtime call failed (no device, launch error, ...) */
+    VEGAS_ETIMEOUT = 4, /* a bounded device wait ran out */
+    VEGAS_EDEVICE = 5,  /* a kernel flagged an error: NaN energy change, sampler cap */
+    VEGAS_ESTATE = 6    /* context poisoned by an earlier ECUDA/EDEVICE */
+} vegas_status;
+
+/*
+ * One sample: the material file of Sec. III.C (sites, spin norms, field axes, types and
+ * exchange links) plus the anisotropy file, as arrays. Links are a directed CSR in which
+ * every link appears in both directions with equal J (J[i->j] == J[j->i]); no self-links,
+ * no duplicate links, col in [0, n_sites). Optional arrays may be NULL (default noted).
+ * The order of a row is kept: the local field sums neighbours in that order.
+ */
+typedef struct {
+    int32_t n_sites;           /* >= 1 and < 2^31 */
+    int32_t pad_;
+    int64_t n_edges;           /* == row_ptr[n_sites] */
+    const int64_t *row_ptr;    /* [n_sites + 1], row_ptr[0] == 0, non-decreasing */
+    const int32_t *col;        /* [n_edges] neighbour site */
+    const double *J;           /* [n_edges] exchange J_ij (Eq. 1) */
+    const int32_t *type;       /* [n_sites] or NULL (all 0); kept for per-type output */
+    const double *spin_norm;   /* [n_sites] s_i > 0, or NULL (all 1) */
+    const double *field_axis;  /* [n_sites][3] n_i, or NULL (all +z) */
+    const double *k_uni;       /* [n_sites] uniaxial constant k_i (Eq. 2), or NULL (0) */
+    const double *e_uni;       /* [n_sites][3] uniaxial axis e_i, or NULL (all +z) */
+    const double *k_cub;       /* [n_sites] cubic constant (Eq. 3), or NULL (0) */
+    const int32_t *color;      /* [n_sites] proper colouring, or NULL (greedy) */
+    const double *init_spins;  /* [n_sites][3] initial state for every replica, or NULL:
+                                  S_i = s_i * uniform-on-sphere from Philox */
+} vegas_sample;
+
+typedef struct {
+    int32_t precision;      /* 64: FP64 spins and arithmetic; 32: FP32 spins and energy
+                               changes with FP64 history sums. Default 32. */
+    int32_t replicas;       /* replicas per sample: 1, 2, 4, 8, 16 or 32. Default 1. */
+    uint64_t seed;          /* Philox key. Default 1. */
+    int32_t inst_base;      /* id of the first instance. Default 0. */
+    int32_t device;         /* CUDA device ordinal, -1 = current. Default -1. */
+    void *cuda_stream;      /* cudaStream_t to run on, NULL = a stream of the library */
+    int32_t variant;        /* -1 automatic, 0 one launch per colour class ("stream"),
+                               1 one persistent launch per step ("resident"). Default -1. */
+    int32_t accept_log_mcs; /* > 0: keep the accept/reject bit of every attempt of the
+                               first accept_log_mcs MCS (debugging and parity). Default 0. */
+    int32_t timing;         /* 1: time every sweep launch with CUDA events. Default 0. */
+    int32_t graphs;         /* 1: replay the per-MCS launches as a CUDA graph. Default 1. */
+} vegas_options;
+
+typedef struct {
+    int32_t n_samples, n_instances, replicas, precision;
+    int32_t max_colours;        /* largest colour count over samples */
+    int32_t variant;            /* variant used by the last run */
+    int64_t n_sites;            /* sites over all samples (one replica) */
+    int64_t n_edges;            /* directed links over all samples */
+    int64_t records;            /* history records per instance so far */
+    uint32_t mcs_done;          /* global MCS counter t */
+    uint32_t device_error;      /* error bits set by kernels (1 NaN dE, 2 sampler cap) */
+    int64_t kernel_launches;    /* kernels launched by the library so far */
+    int64_t sweep_launches;     /* colour-pass (or resident) sweep launches so far */
+    double sweep_ms;            /* summed event time of sweep launches (timing = 1) */
+    double last_run_ms;         /* event time of the last vegas_run on the device */
+    int64_t device_bytes;       /* device memory held by the context */
+} vegas_stats_t;
+
+/* Fills *opt with the defaults listed above. */
+void vegas_default_options(vegas_options *opt);
+
+/*
+ * Build a context: validate every sample, colour it (greedy in site order when no
+ * colouring is given), renumber sites colour-major (colour 0 first) while keeping the
+ * caller's ids for random-number keys and the caller's neighbour order inside each row,
+ * upload topology and parameters, and set the initial spins (Sec. III.C material file;
+ * Sec. III.B "an initial state is chosen"). opt may be NULL (defaults).
+ * Returns VEGAS_EINVAL for: n_samples < 1; a NULL required array; row_ptr not starting
+ * at 0, decreasing, or not ending at n_edges; col out of range; a self-link; a duplicate
+ * link; J not symmetric; a non-finite parameter; spin_norm <= 0; a zero axis; a colouring
+ * that is not proper; bad options. On failure *out is NULL.
+ */
+vegas_status vegas_create(const vegas_sample *samples, int32_t n_samples, const vegas_options *opt,
+                          vegas_ctx **out);
+
+/*
+ * Continue the Markov chain of every instance through n_steps temperature/field steps
+ * of mcs_per_step MCS each (Sec. III.C parameters; Sec. II history). T and B are
+ * [n_instances][n_steps] host arrays (row-major), T > 0 and finite, B finite. The state
+ * carries over between steps and between calls; one call with n_steps = a + b gives the
+ * same spins and history as a call with the first a steps followed by a call with the
+ * remaining b. After every MCS one history record (E, Mx, My, Mz) per instance is kept;
+ * after the last MCS of every step each spin is rescaled to its norm s_i in FP64.
+ * Blocking: returns when the device work is done.
+ */
+vegas_status vegas_run(vegas_ctx *ctx, const double *T, const double *B, int32_t n_steps, int32_t mcs_per_step);
+
+/*
+ * Copy the history into out as [n_instances][records][4] doubles (E, Mx, My, Mz; totals
+ * over the instance's sites, FP64), records in run order. With out == NULL only
+ * *n_written is set (to the number of doubles). Returns VEGAS_EINVAL if capacity_doubles
+ * is too small.
+ */
+vegas_status vegas_history(const vegas_ctx *ctx, double *out, size_t capacity_doubles, size_t *n_written);
+
+/* Spins of one instance as [n_sites][3] doubles in the caller's site order. */
+vegas_status vegas_get_spins(const vegas_ctx *ctx, int32_t instance, double *out);
+
+/* Replace the spins of one instance ([n_sites][3] doubles, caller's site order; each
+ * vector is used as given, FP32 contexts round it). For checkpoint/resume. */
+vegas_status vegas_set_spins(vegas_ctx *ctx, int32_t instance, const double *in);
+
+/*
+ * Accept/reject bits of the first accept_log_mcs MCS (option), as
+ * [mcs][n_instances][n_sites] bytes (1 = accepted) in the caller's site order.
+ * out == NULL: size query.
+ */
+vegas_status vegas_accept_log(const vegas_ctx *ctx, uint8_t *out, size_t capacity, size_t *n_written);
+
+/* Counters and sizes of the context (valid also on a poisoned context). */
+vegas_status vegas_stats(const vegas_ctx *ctx, vegas_stats_t *out);
+
+/*
+ * Greedy colouring used by vegas_create when a sample has no colouring: sites in index
+ * order, each takes the smallest colour not used by an already coloured neighbour.
+ * Host only (no device needed). Returns the number of colours, or -1 on invalid input.
+ */
+int32_t vegas_greedy_colour(int32_t n_sites, const int64_t *row_ptr, const int32_t *col, int32_t *color_out);
+
+/* Message of the last failed call on ctx (ctx == NULL: last failed vegas_create of this
+ * thread). Valid until the next call on ctx. Never NULL. */
+const char *vegas_last_error(const vegas_ctx *ctx);
+
+/* Free the context and its device memory. NULL is accepted. */
+void vegas_destroy(vegas_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VEGAS_H */

@@ -1,0 +1,23 @@
+"""GB300 (sm_103a) Metropolis sweep of the classical Heisenberg model behind a C-ABI.
+
+The compute path is the CUDA library built from csrc/ (libvegas.so); vegas.py is its ctypes
+binding. Importing the package does not build anything; call build.build() first.
+"""
+
+from .build import LIB, build  # noqa: F401
+from .vegas import (  # noqa: F401
+    Context,
+    VegasError,
+    load_library,
+    vegas_accept_log,
+    vegas_create,
+    vegas_default_options,
+    vegas_destroy,
+    vegas_get_spins,
+    vegas_greedy_colour,
+    vegas_history,
+    vegas_last_error,
+    vegas_run,
+    vegas_set_spins,
+    vegas_stats,
+)

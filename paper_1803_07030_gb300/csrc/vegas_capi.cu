@@ -1,0 +1,761 @@
+// C-ABI of the Metropolis sweep: context creation (packing samples into device memory),
+// the schedule driver (one CUDA graph per MCS, replayed), history and spin I/O.
+// See include/vegas.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vegas_internal.h"
+
+using namespace vegas;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct SampleInfo {
+    int32_t n = 0, n_colours = 0, uniform_degree = 0;
+    int32_t site_off = 0;      // first global site
+    int64_t edge_off = 0;      // first global edge
+    std::vector<int32_t> cstart, lower_mode, orig;
+    bool uniform_params = false, has_anisotropy = false;
+    SiteParams64 u{};
+    int64_t slot_base = 0;     // first partial slot (blocks)
+    int32_t slot_count = 0;
+};
+
+struct PassLaunch {
+    PassArgs args;
+    int grid;
+};
+
+}  // namespace
+
+struct vegas_ctx {
+    vegas_options opt{};
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    bool own_stream = false;
+    int precision = 32, R = 1, log2R = 0, n_samples = 0, n_inst = 0, max_colours = 0;
+    int64_t n_sites = 0, n_edges = 0;
+    std::vector<SampleInfo> samples;
+    std::vector<PassLaunch> passes;
+    // device buffers
+    void *d_spins = nullptr, *d_edges = nullptr, *d_p0 = nullptr, *d_p1 = nullptr, *d_pk = nullptr;
+    int64_t *d_rowptr = nullptr, *d_slot_base = nullptr;
+    int32_t *d_orig = nullptr, *d_slot_count = nullptr;
+    double *d_norm = nullptr, *d_partial = nullptr, *d_sched = nullptr, *d_hist = nullptr;
+    size_t sched_cap = 0, hist_cap = 0;
+    RunState *d_run = nullptr;
+    uint32_t *d_err = nullptr;
+    uint8_t *d_alog = nullptr;
+    int64_t alog_bytes = 0;
+    int64_t device_bytes = 0;
+    // graph of one MCS
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    // host state
+    std::vector<std::vector<double>> hist;  // per instance: records * 4
+    int64_t records = 0;
+    uint32_t t = 0;
+    uint32_t device_error = 0;
+    int64_t kernel_launches = 0, sweep_launches = 0;
+    double sweep_ms = 0.0, last_run_ms = 0.0;
+    int variant = 0;
+    bool poisoned = false;
+    std::string err;
+};
+
+namespace {
+
+vegas_status fail(vegas_ctx *c, vegas_status st, const std::string &msg) {
+    if (c) {
+        c->err = msg;
+        if (st == VEGAS_ECUDA || st == VEGAS_EDEVICE || st == VEGAS_ETIMEOUT) c->poisoned = true;
+    } else {
+        g_create_error = msg;
+    }
+    return st;
+}
+
+#define CK(ctx, call)                                                                                     \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? VEGAS_ENOMEM : VEGAS_ECUDA,              \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(vegas_ctx *c, T **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess) c->device_bytes += (int64_t)bytes;
+    return e;
+}
+
+void free_all(vegas_ctx *c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    void *bufs[] = {c->d_spins, c->d_edges, c->d_p0, c->d_p1, c->d_pk, c->d_rowptr, c->d_slot_base, c->d_orig,
+                    c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+int32_t float_bits(float f) {
+    int32_t i;
+    std::memcpy(&i, &f, sizeof i);
+    return i;
+}
+
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+// Launch one MCS: every colour class of every sample, then the reduction.
+void enqueue_mcs(vegas_ctx *c, cudaStream_t st, std::vector<cudaEvent_t> *ev) {
+    int k = 0;
+    for (const PassLaunch &p : c->passes) {
+        if (ev) cudaEventRecord((*ev)[2 * k], st);
+        if (c->precision == 64)
+            launch_pass64(p.args, p.grid, st);
+        else
+            launch_pass32(p.args, p.grid, st);
+        if (ev) cudaEventRecord((*ev)[2 * k + 1], st);
+        ++k;
+    }
+    ReduceArgs ra{c->d_partial, c->d_slot_base, c->d_slot_count, c->d_run, c->R, c->n_inst};
+    launch_reduce(ra, st);
+}
+
+vegas_status build_graph(vegas_ctx *c) {
+    if (c->graph_exec) return VEGAS_OK;
+    CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_mcs(c, c->cap_stream, nullptr);
+    CK(c, cudaStreamEndCapture(c->cap_stream, &c->graph));
+    CK(c, cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
+    return VEGAS_OK;
+}
+
+vegas_status check_usable(vegas_ctx *c) {
+    if (!c) return VEGAS_EINVAL;
+    if (c->poisoned) {
+        if (c->err.rfind("context poisoned", 0) != 0) c->err = "context poisoned by an earlier error: " + c->err;
+        return VEGAS_ESTATE;
+    }
+    return VEGAS_OK;
+}
+
+vegas_status set_device(vegas_ctx *c) {
+    CK(c, cudaSetDevice(c->device));
+    return VEGAS_OK;
+}
+
+}  // namespace
+
+extern "C" void vegas_default_options(vegas_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = 32;
+    o->replicas = 1;
+    o->seed = 1;
+    o->inst_base = 0;
+    o->device = -1;
+    o->cuda_stream = nullptr;
+    o->variant = -1;
+    o->accept_log_mcs = 0;
+    o->timing = 0;
+    o->graphs = 1;
+}
+
+extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samples, const vegas_options *opt,
+                                     vegas_ctx **out) {
+    if (!out) return fail(nullptr, VEGAS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!samples || n_samples < 1) return fail(nullptr, VEGAS_EINVAL, "need at least one sample");
+    vegas_options o;
+    vegas_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != 32 && o.precision != 64) return fail(nullptr, VEGAS_EINVAL, "precision must be 32 or 64");
+    if (o.replicas < 1 || o.replicas > 32 || (o.replicas & (o.replicas - 1)))
+        return fail(nullptr, VEGAS_EINVAL, "replicas must be 1, 2, 4, 8, 16 or 32");
+    if (o.accept_log_mcs < 0 || o.inst_base < 0) return fail(nullptr, VEGAS_EINVAL, "negative option");
+    if (o.variant < -1 || o.variant > 1) return fail(nullptr, VEGAS_EINVAL, "variant must be -1, 0 or 1");
+    if ((int64_t)o.inst_base + (int64_t)n_samples * o.replicas > (int64_t)UINT32_MAX)
+        return fail(nullptr, VEGAS_EINVAL, "instance ids exceed 32 bits");
+
+    // validate and renumber every sample before touching the device
+    std::vector<LoadedSample> L((size_t)n_samples);
+    int64_t n_sites = 0, n_edges = 0;
+    for (int32_t s = 0; s < n_samples; ++s) {
+        std::string e;
+        if (!load_sample(samples[s], L[(size_t)s], e))
+            return fail(nullptr, VEGAS_EINVAL, "sample " + std::to_string(s) + ": " + e);
+        n_sites += L[(size_t)s].n;
+        n_edges += L[(size_t)s].n_edges + (L[(size_t)s].n_edges & 1);  // keep every sample 16-byte aligned
+    }
+    if (n_sites * o.replicas > ((int64_t)1 << 40) || n_sites >= INT32_MAX || n_edges >= INT32_MAX)
+        return fail(nullptr, VEGAS_EINVAL, "too many sites or links for one context");
+
+    vegas_ctx *c = new (std::nothrow) vegas_ctx();
+    if (!c) return fail(nullptr, VEGAS_ENOMEM, "host allocation failed");
+    c->opt = o;
+    c->precision = o.precision;
+    c->R = o.replicas;
+    c->log2R = ilog2(o.replicas);
+    c->n_samples = n_samples;
+    c->n_inst = n_samples * o.replicas;
+    c->n_sites = n_sites;
+    c->n_edges = n_edges;
+    c->variant = 0;
+
+    auto bail = [&](vegas_status st) {
+        g_create_error = c->err;
+        free_all(c);
+        delete c;
+        return st;
+    };
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess || ndev == 0) {
+        c->err = std::string("no CUDA device: ") + cudaGetErrorString(ce);
+        return bail(VEGAS_ECUDA);
+    }
+    if (o.device >= 0) {
+        c->device = o.device;
+    } else if (cudaGetDevice(&c->device) != cudaSuccess) {
+        c->err = "cudaGetDevice failed";
+        return bail(VEGAS_ECUDA);
+    }
+    vegas_status st;
+#define TRY(x)                         \
+    do {                               \
+        if ((st = (x)) != VEGAS_OK) return bail(st); \
+    } while (0)
+    TRY(set_device(c));
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) {
+        c->err = "cudaGetDeviceProperties failed";
+        return bail(VEGAS_ECUDA);
+    }
+    c->sm_count = prop.multiProcessorCount;
+    if (o.cuda_stream) {
+        c->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            c->err = "cudaStreamCreate failed";
+            return bail(VEGAS_ECUDA);
+        }
+        c->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        c->err = "cudaStreamCreate failed";
+        return bail(VEGAS_ECUDA);
+    }
+
+    // ---- pack samples (host staging)
+    const int R = c->R;
+    const bool p64 = c->precision == 64;
+    bool any_site_params = false;
+    for (auto &l : L) any_site_params |= !l.uniform_params;
+    std::vector<int32_t> h_orig((size_t)n_sites);
+    std::vector<int64_t> h_rowptr((size_t)n_sites + 1);
+    std::vector<double> h_norm((size_t)n_sites);
+    std::vector<int2> h_e32;
+    std::vector<Edge64> h_e64;
+    if (p64)
+        h_e64.resize((size_t)n_edges, Edge64{0.0, 0, 0});
+    else
+        h_e32.resize((size_t)n_edges, make_int2(0, 0));
+    std::vector<float4> h_p0f, h_p1f;
+    std::vector<float> h_pkf;
+    std::vector<double4_32a> h_p0d, h_p1d;
+    std::vector<double> h_pkd;
+    if (any_site_params) {
+        if (p64) {
+            h_p0d.resize((size_t)n_sites);
+            h_p1d.resize((size_t)n_sites);
+            h_pkd.resize((size_t)n_sites);
+        } else {
+            h_p0f.resize((size_t)n_sites);
+            h_p1f.resize((size_t)n_sites);
+            h_pkf.resize((size_t)n_sites);
+        }
+    }
+    c->samples.resize((size_t)n_samples);
+    int64_t site_off = 0, edge_off = 0;
+    for (int32_t s = 0; s < n_samples; ++s) {
+        LoadedSample &l = L[(size_t)s];
+        SampleInfo &si = c->samples[(size_t)s];
+        si.n = l.n;
+        si.n_colours = l.n_colours;
+        si.uniform_degree = l.uniform_degree;
+        si.site_off = (int32_t)site_off;
+        si.edge_off = edge_off;
+        si.cstart = l.cstart;
+        si.lower_mode = l.lower_mode;
+        si.orig = l.orig;
+        si.uniform_params = l.uniform_params;
+        si.has_anisotropy = l.has_anisotropy;
+        si.u = SiteParams64{l.field_axis[0], l.field_axis[1], l.field_axis[2], l.spin_norm[0],
+                            l.e_uni[0],      l.e_uni[1],      l.e_uni[2],      l.k_uni[0], l.k_cub[0]};
+        c->max_colours = std::max(c->max_colours, l.n_colours);
+        for (int32_t g = 0; g < l.n; ++g) {
+            const size_t G = (size_t)(site_off + g);
+            h_orig[G] = l.orig[(size_t)g];
+            h_rowptr[G] = edge_off + l.row_ptr[(size_t)g];
+            h_norm[G] = l.spin_norm[(size_t)g];
+            if (any_site_params) {
+                const double *fa = &l.field_axis[3 * (size_t)g], *ea = &l.e_uni[3 * (size_t)g];
+                if (p64) {
+                    h_p0d[G] = make_double4_32a(fa[0], fa[1], fa[2], l.spin_norm[(size_t)g]);
+                    h_p1d[G] = make_double4_32a(ea[0], ea[1], ea[2], l.k_uni[(size_t)g]);
+                    h_pkd[G] = l.k_cub[(size_t)g];
+                } else {
+                    h_p0f[G] = make_float4((float)fa[0], (float)fa[1], (float)fa[2], (float)l.spin_norm[(size_t)g]);
+                    h_p1f[G] = make_float4((float)ea[0], (float)ea[1], (float)ea[2], (float)l.k_uni[(size_t)g]);
+                    h_pkf[G] = (float)l.k_cub[(size_t)g];
+                }
+            }
+        }
+        for (int64_t e = 0; e < l.n_edges; ++e) {
+            const int32_t colg = (int32_t)(site_off + l.col[(size_t)e]);
+            if (p64)
+                h_e64[(size_t)(edge_off + e)] = Edge64{l.J[(size_t)e], colg, 0};
+            else
+                h_e32[(size_t)(edge_off + e)] = make_int2(colg, float_bits((float)l.J[(size_t)e]));
+        }
+        site_off += l.n;
+        edge_off += l.n_edges + (l.n_edges & 1);
+    }
+    h_rowptr[(size_t)n_sites] = edge_off;
+
+    // ---- device buffers
+    const size_t vbytes = p64 ? sizeof(double4_32a) : sizeof(float4);
+#define DALLOC(ptr, bytes)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = dalloc(c, &(ptr), (bytes));                                    \
+        if (e_ != cudaSuccess) {                                                        \
+            c->err = std::string("cudaMalloc ") + #ptr + ": " + cudaGetErrorString(e_); \
+            return bail(e_ == cudaErrorMemoryAllocation ? VEGAS_ENOMEM : VEGAS_ECUDA);  \
+        }                                                                               \
+    } while (0)
+#define H2D(dst, src, bytes)                                                                  \
+    do {                                                                                      \
+        cudaError_t e_ = cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyHostToDevice, c->stream); \
+        if (e_ != cudaSuccess) {                                                              \
+            c->err = std::string("upload: ") + cudaGetErrorString(e_);                        \
+            return bail(VEGAS_ECUDA);                                                         \
+        }                                                                                     \
+    } while (0)
+    DALLOC(c->d_spins, (size_t)n_sites * R * vbytes);
+    DALLOC(c->d_orig, sizeof(int32_t) * (size_t)n_sites);
+    DALLOC(c->d_rowptr, sizeof(int64_t) * ((size_t)n_sites + 1));
+    DALLOC(c->d_norm, sizeof(double) * (size_t)n_sites);
+    DALLOC(c->d_edges, (p64 ? sizeof(Edge64) : sizeof(int2)) * (size_t)std::max<int64_t>(n_edges, 1));
+    DALLOC(c->d_run, sizeof(RunState));
+    DALLOC(c->d_err, sizeof(uint32_t));
+    H2D(c->d_orig, h_orig.data(), sizeof(int32_t) * (size_t)n_sites);
+    H2D(c->d_rowptr, h_rowptr.data(), sizeof(int64_t) * ((size_t)n_sites + 1));
+    H2D(c->d_norm, h_norm.data(), sizeof(double) * (size_t)n_sites);
+    if (n_edges > 0) {
+        if (p64)
+            H2D(c->d_edges, h_e64.data(), sizeof(Edge64) * (size_t)n_edges);
+        else
+            H2D(c->d_edges, h_e32.data(), sizeof(int2) * (size_t)n_edges);
+    }
+    if (any_site_params) {
+        const size_t pv = p64 ? sizeof(double4_32a) : sizeof(float4), ps = p64 ? sizeof(double) : sizeof(float);
+        DALLOC(c->d_p0, pv * (size_t)n_sites);
+        DALLOC(c->d_p1, pv * (size_t)n_sites);
+        DALLOC(c->d_pk, ps * (size_t)n_sites);
+        H2D(c->d_p0, p64 ? (const void *)h_p0d.data() : (const void *)h_p0f.data(), pv * (size_t)n_sites);
+        H2D(c->d_p1, p64 ? (const void *)h_p1d.data() : (const void *)h_p1f.data(), pv * (size_t)n_sites);
+        H2D(c->d_pk, p64 ? (const void *)h_pkd.data() : (const void *)h_pkf.data(), ps * (size_t)n_sites);
+    }
+    if (cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), c->stream) != cudaSuccess) {
+        c->err = "memset failed";
+        return bail(VEGAS_ECUDA);
+    }
+    if (o.accept_log_mcs > 0) {
+        c->alog_bytes = (int64_t)o.accept_log_mcs * n_sites * R;
+        DALLOC(c->d_alog, (size_t)c->alog_bytes);
+        if (cudaMemsetAsync(c->d_alog, 0, (size_t)c->alog_bytes, c->stream) != cudaSuccess) {
+            c->err = "memset failed";
+            return bail(VEGAS_ECUDA);
+        }
+    }
+
+    // ---- sweep launches, one per non-empty colour class of each sample
+    int64_t slots = 0;
+    int64_t alog_base = 0;
+    for (int32_t s = 0; s < n_samples; ++s) {
+        SampleInfo &si = c->samples[(size_t)s];
+        si.slot_base = slots;
+        for (int32_t col = 0; col < si.n_colours; ++col) {
+            const int32_t nc = si.cstart[(size_t)col + 1] - si.cstart[(size_t)col];
+            if (nc == 0) continue;
+            PassLaunch pl;
+            PassArgs &a = pl.args;
+            std::memset(&a, 0, sizeof a);
+            a.spins = c->d_spins;
+            a.edges = c->d_edges;
+            a.row_ptr = c->d_rowptr;
+            a.orig = c->d_orig;
+            a.p0 = si.uniform_params ? nullptr : c->d_p0;
+            a.p1 = si.uniform_params ? nullptr : c->d_p1;
+            a.pk = si.uniform_params ? nullptr : c->d_pk;
+            a.run = c->d_run;
+            a.err = c->d_err;
+            a.alog = c->d_alog;
+            a.seed = o.seed;
+            a.edge_base = si.edge_off;
+            a.site_off = si.site_off;
+            a.g_begin = si.site_off + si.cstart[(size_t)col];
+            a.g_end = si.site_off + si.cstart[(size_t)col + 1];
+            a.lower_end = a.g_begin;
+            a.log2R = c->log2R;
+            a.inst0 = o.inst_base + s * R;
+            a.inst_local0 = s * R;
+            a.n_inst = c->n_inst;
+            a.n_sample_sites = si.n;
+            a.alog_stride = (int64_t)n_sites * R;
+            a.alog_base = alog_base;
+            a.alog_mcs = (uint32_t)o.accept_log_mcs;
+            a.deg = si.uniform_degree;
+            a.lower_mode = si.lower_mode[(size_t)col];
+            a.params_mode = si.uniform_params ? (si.has_anisotropy ? 1 : 0) : 2;
+            a.u64 = si.u;
+            a.u32 = SiteParams32{(float)si.u.nx, (float)si.u.ny, (float)si.u.nz, (float)si.u.s, (float)si.u.ex,
+                                 (float)si.u.ey, (float)si.u.ez, (float)si.u.k,  (float)si.u.kc};
+            const int64_t work = (int64_t)nc * R;
+            const int64_t need = (work + kThreads - 1) / kThreads;
+            const int64_t cap = (int64_t)c->sm_count * pass_blocks_per_sm(c->precision, a);
+            pl.grid = (int)std::max<int64_t>(1, std::min(need, cap));
+            a.partial = nullptr;  // set below, once the slot buffer exists
+            si.slot_count += pl.grid;
+            slots += pl.grid;
+            c->passes.push_back(pl);
+        }
+        alog_base += (int64_t)si.n * R;
+    }
+    DALLOC(c->d_partial, sizeof(double) * 4 * (size_t)slots * R);
+    {
+        int64_t off = 0;
+        for (PassLaunch &pl : c->passes) {
+            pl.args.partial = c->d_partial + off * R * 4;
+            off += pl.grid;
+        }
+    }
+    std::vector<int64_t> h_sb((size_t)n_samples);
+    std::vector<int32_t> h_sc((size_t)n_samples);
+    for (int32_t s = 0; s < n_samples; ++s) {
+        h_sb[(size_t)s] = c->samples[(size_t)s].slot_base;
+        h_sc[(size_t)s] = c->samples[(size_t)s].slot_count;
+    }
+    DALLOC(c->d_slot_base, sizeof(int64_t) * (size_t)n_samples);
+    DALLOC(c->d_slot_count, sizeof(int32_t) * (size_t)n_samples);
+    H2D(c->d_slot_base, h_sb.data(), sizeof(int64_t) * (size_t)n_samples);
+    H2D(c->d_slot_count, h_sc.data(), sizeof(int32_t) * (size_t)n_samples);
+    RunState rs0{};
+    rs0.mcs = 1;
+    H2D(c->d_run, &rs0, sizeof rs0);
+
+    // ---- initial state
+    for (int32_t s = 0; s < n_samples; ++s) {
+        const SampleInfo &si = c->samples[(size_t)s];
+        double *d_given = nullptr;
+        const LoadedSample &l = L[(size_t)s];
+        if (!l.init_spins.empty()) {
+            if (cudaMalloc(&d_given, sizeof(double) * l.init_spins.size()) != cudaSuccess) {
+                c->err = "cudaMalloc for initial spins failed";
+                return bail(VEGAS_ENOMEM);
+            }
+            H2D(d_given, l.init_spins.data(), sizeof(double) * l.init_spins.size());
+        }
+        InitArgs ia{c->d_spins, c->d_orig, c->d_norm, d_given, c->d_err, o.seed, si.site_off, si.site_off + si.n,
+                    o.inst_base + s * R, c->log2R};
+        const int64_t work = (int64_t)si.n * R;
+        const int grid = (int)std::min<int64_t>((work + 255) / 256, (int64_t)c->sm_count * 8);
+        if (p64)
+            launch_init64(ia, grid, c->stream);
+        else
+            launch_init32(ia, grid, c->stream);
+        c->kernel_launches++;
+        if (d_given) {
+            cudaError_t e = cudaStreamSynchronize(c->stream);
+            cudaFree(d_given);
+            if (e != cudaSuccess) {
+                c->err = std::string("initial state: ") + cudaGetErrorString(e);
+                return bail(VEGAS_ECUDA);
+            }
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->err = std::string("create: ") + cudaGetErrorString(e);
+        return bail(VEGAS_ECUDA);
+    }
+    c->hist.assign((size_t)c->n_inst, std::vector<double>());
+#undef TRY
+#undef DALLOC
+#undef H2D
+    *out = c;
+    return VEGAS_OK;
+}
+
+extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B, int32_t n_steps, int32_t mcs) {
+    vegas_status st = check_usable(c);
+    if (st != VEGAS_OK) return st;
+    if (n_steps < 0 || mcs < 0) return fail(c, VEGAS_EINVAL, "n_steps and mcs_per_step must be >= 0");
+    if (n_steps == 0 || mcs == 0) return VEGAS_OK;
+    if (!T || !B) return fail(c, VEGAS_EINVAL, "T or B is NULL");
+    const int64_t NI = c->n_inst;
+    if ((int64_t)c->t + (int64_t)n_steps * mcs >= (int64_t)UINT32_MAX)
+        return fail(c, VEGAS_EINVAL, "global MCS counter would exceed 32 bits");
+    std::vector<double> sched((size_t)n_steps * NI * 2);
+    for (int64_t i = 0; i < NI; ++i)
+        for (int32_t s = 0; s < n_steps; ++s) {
+            const double Ti = T[i * n_steps + s], Bi = B[i * n_steps + s];
+            if (!(Ti > 0.0) || !std::isfinite(Ti)) return fail(c, VEGAS_EINVAL, "T must be finite and > 0");
+            if (!std::isfinite(Bi)) return fail(c, VEGAS_EINVAL, "B must be finite");
+            sched[((size_t)s * NI + i) * 2] = 1.0 / Ti;
+            sched[((size_t)s * NI + i) * 2 + 1] = Bi;
+        }
+    if ((st = set_device(c)) != VEGAS_OK) return st;
+    const int64_t nrec = (int64_t)n_steps * mcs;
+    if (sched.size() > c->sched_cap) {
+        if (c->d_sched) {
+            cudaFree(c->d_sched);
+            c->device_bytes -= (int64_t)(c->sched_cap * sizeof(double));
+        }
+        c->sched_cap = 0;
+        CK(c, dalloc(c, &c->d_sched, sizeof(double) * sched.size()));
+        c->sched_cap = sched.size();
+    }
+    const size_t hneed = (size_t)nrec * NI * 4;
+    if (hneed > c->hist_cap) {
+        if (c->d_hist) {
+            cudaFree(c->d_hist);
+            c->device_bytes -= (int64_t)(c->hist_cap * sizeof(double));
+        }
+        c->hist_cap = 0;
+        CK(c, dalloc(c, &c->d_hist, sizeof(double) * hneed));
+        c->hist_cap = hneed;
+    }
+    CK(c, cudaMemcpyAsync(c->d_sched, sched.data(), sizeof(double) * sched.size(), cudaMemcpyHostToDevice, c->stream));
+    RunState rs{};
+    rs.t = c->t;
+    rs.rec = 0;
+    rs.ticket = 0;
+    rs.mcs = (uint32_t)mcs;
+    rs.sched = c->d_sched;
+    rs.hist = c->d_hist;
+    CK(c, cudaMemcpyAsync(c->d_run, &rs, sizeof rs, cudaMemcpyHostToDevice, c->stream));
+
+    const bool use_graph = c->opt.graphs && !c->opt.timing;
+    if (use_graph && (st = build_graph(c)) != VEGAS_OK) return st;
+    std::vector<cudaEvent_t> ev;
+    std::vector<float> ev_ms;
+    if (c->opt.timing) {
+        ev.resize(2 * c->passes.size() * (size_t)mcs);
+        for (auto &x : ev) CK(c, cudaEventCreate(&x));
+    }
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    CK(c, cudaEventRecord(e0, c->stream));
+    RenormArgs ra{c->d_spins, c->d_norm, c->n_sites * c->R, c->log2R};
+    const int rgrid = (int)std::min<int64_t>((ra.n_work + 255) / 256, (int64_t)c->sm_count * 8);
+    double sweep_ms = 0.0;
+    for (int32_t s = 0; s < n_steps; ++s) {
+        for (int32_t m = 0; m < mcs; ++m) {
+            if (use_graph) {
+                CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
+            } else if (c->opt.timing) {
+                std::vector<cudaEvent_t> sub(ev.begin() + (size_t)m * 2 * c->passes.size(),
+                                             ev.begin() + (size_t)(m + 1) * 2 * c->passes.size());
+                enqueue_mcs(c, c->stream, &sub);
+            } else {
+                enqueue_mcs(c, c->stream, nullptr);
+            }
+            c->kernel_launches += (int64_t)c->passes.size() + 1;
+            c->sweep_launches += (int64_t)c->passes.size();
+        }
+        if (c->precision == 64)
+            launch_renorm64(ra, rgrid, c->stream);
+        else
+            launch_renorm32(ra, rgrid, c->stream);
+        c->kernel_launches++;
+        if (c->opt.timing) {  // read this step's pass timings before the events are reused
+            CK(c, cudaStreamSynchronize(c->stream));
+            for (size_t k = 0; k + 1 < ev.size(); k += 2) {
+                float ms = 0.f;
+                CK(c, cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+                sweep_ms += ms;
+            }
+        }
+    }
+    CK(c, cudaEventRecord(e1, c->stream));
+    CK(c, cudaGetLastError());
+    CK(c, cudaStreamSynchronize(c->stream));
+    float run_ms = 0.f;
+    CK(c, cudaEventElapsedTime(&run_ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (auto &x : ev) cudaEventDestroy(x);
+    c->last_run_ms = run_ms;
+    c->sweep_ms += sweep_ms;
+    uint32_t derr = 0;
+    CK(c, cudaMemcpy(&derr, c->d_err, sizeof derr, cudaMemcpyDeviceToHost));
+    // history: device [rec][inst][4] -> host per instance, appended
+    std::vector<double> h(hneed);
+    CK(c, cudaMemcpy(h.data(), c->d_hist, sizeof(double) * hneed, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < NI; ++i) {
+        auto &v = c->hist[(size_t)i];
+        const size_t old = v.size();
+        v.resize(old + (size_t)nrec * 4);
+        for (int64_t r = 0; r < nrec; ++r)
+            std::memcpy(&v[old + (size_t)r * 4], &h[((size_t)r * NI + i) * 4], 4 * sizeof(double));
+    }
+    c->records += nrec;
+    c->t += (uint32_t)nrec;
+    c->device_error |= derr;
+    if (derr) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "device error flags 0x%x (1: NaN energy change, 2: sphere sampler cap)", derr);
+        return fail(c, VEGAS_EDEVICE, msg);
+    }
+    return VEGAS_OK;
+}
+
+extern "C" vegas_status vegas_history(const vegas_ctx *cc, double *out, size_t capacity, size_t *n_written) {
+    vegas_ctx *c = const_cast<vegas_ctx *>(cc);
+    vegas_status st = check_usable(c);
+    if (st != VEGAS_OK) return st;
+    const size_t need = (size_t)c->n_inst * (size_t)c->records * 4;
+    if (n_written) *n_written = need;
+    if (!out) return VEGAS_OK;
+    if (capacity < need) return fail(c, VEGAS_EINVAL, "history buffer too small");
+    for (int i = 0; i < c->n_inst; ++i)
+        std::memcpy(out + (size_t)i * c->records * 4, c->hist[(size_t)i].data(), sizeof(double) * c->records * 4);
+    return VEGAS_OK;
+}
+
+namespace {
+
+vegas_status spins_io(vegas_ctx *c, int32_t inst, double *out, const double *in) {
+    vegas_status st = check_usable(c);
+    if (st != VEGAS_OK) return st;
+    if (inst < 0 || inst >= c->n_inst) return fail(c, VEGAS_EINVAL, "instance out of range");
+    if (!out && !in) return fail(c, VEGAS_EINVAL, "buffer is NULL");
+    if ((st = set_device(c)) != VEGAS_OK) return st;
+    const SampleInfo &si = c->samples[(size_t)(inst / c->R)];
+    const int32_t r = inst % c->R;
+    const size_t n = (size_t)si.n;
+    double *d = nullptr;
+    CK(c, cudaMalloc(&d, sizeof(double) * 3 * n));
+    std::vector<double> h(3 * n);
+    const int grid = (int)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)c->sm_count * 8);
+    cudaError_t e = cudaSuccess;
+    if (out) {
+        launch_gather(c->d_spins, c->precision, si.site_off, (int64_t)n, c->log2R, r, d, grid, c->stream);
+        e = cudaMemcpyAsync(h.data(), d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess)
+            for (size_t g = 0; g < n; ++g)
+                for (int q = 0; q < 3; ++q) out[3 * (size_t)si.orig[g] + q] = h[3 * g + q];
+    } else {
+        for (size_t g = 0; g < n; ++g)
+            for (int q = 0; q < 3; ++q) {
+                const double v = in[3 * (size_t)si.orig[g] + q];
+                if (!std::isfinite(v)) {
+                    cudaFree(d);
+                    return fail(c, VEGAS_EINVAL, "non-finite spin component");
+                }
+                h[3 * g + q] = v;
+            }
+        e = cudaMemcpyAsync(d, h.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) launch_scatter(c->d_spins, c->precision, si.site_off, (int64_t)n, c->log2R, r, d, grid, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    c->kernel_launches++;
+    cudaFree(d);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    CK(c, e);
+    return VEGAS_OK;
+}
+
+}  // namespace
+
+extern "C" vegas_status vegas_get_spins(const vegas_ctx *c, int32_t inst, double *out) {
+    if (!out) return fail(const_cast<vegas_ctx *>(c), VEGAS_EINVAL, "out is NULL");
+    return spins_io(const_cast<vegas_ctx *>(c), inst, out, nullptr);
+}
+
+extern "C" vegas_status vegas_set_spins(vegas_ctx *c, int32_t inst, const double *in) {
+    if (!in) return fail(c, VEGAS_EINVAL, "in is NULL");
+    return spins_io(c, inst, nullptr, in);
+}
+
+extern "C" vegas_status vegas_accept_log(const vegas_ctx *cc, uint8_t *out, size_t capacity, size_t *n_written) {
+    vegas_ctx *c = const_cast<vegas_ctx *>(cc);
+    vegas_status st = check_usable(c);
+    if (st != VEGAS_OK) return st;
+    if (n_written) *n_written = (size_t)c->alog_bytes;
+    if (!out || c->alog_bytes == 0) return VEGAS_OK;
+    if (capacity < (size_t)c->alog_bytes) return fail(c, VEGAS_EINVAL, "accept log buffer too small");
+    if ((st = set_device(c)) != VEGAS_OK) return st;
+    CK(c, cudaMemcpy(out, c->d_alog, (size_t)c->alog_bytes, cudaMemcpyDeviceToHost));
+    return VEGAS_OK;
+}
+
+extern "C" vegas_status vegas_stats(const vegas_ctx *c, vegas_stats_t *o) {
+    if (!c || !o) return VEGAS_EINVAL;
+    std::memset(o, 0, sizeof *o);
+    o->n_samples = c->n_samples;
+    o->n_instances = c->n_inst;
+    o->replicas = c->R;
+    o->precision = c->precision;
+    o->max_colours = c->max_colours;
+    o->variant = c->variant;
+    o->n_sites = c->n_sites;
+    o->n_edges = c->n_edges;
+    o->records = c->records;
+    o->mcs_done = c->t;
+    o->device_error = c->device_error;
+    o->kernel_launches = c->kernel_launches;
+    o->sweep_launches = c->sweep_launches;
+    o->sweep_ms = c->sweep_ms;
+    o->last_run_ms = c->last_run_ms;
+    o->device_bytes = c->device_bytes;
+    return VEGAS_OK;
+}
+
+extern "C" const char *vegas_last_error(const vegas_ctx *c) {
+    if (!c) return g_create_error.c_str();
+    return c->err.c_str();
+}
+
+extern "C" void vegas_destroy(vegas_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}

@@ -1,0 +1,164 @@
+// Internal declarations shared by the loader, the kernels and the C-ABI driver.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/vegas.h"
+
+namespace vegas {
+
+constexpr int kMaxColours = 64;
+constexpr int kThreads = 256;  // threads per block of the sweep kernels
+
+// Random-number purposes (fourth Philox counter word; low 16 bits hold a candidate index).
+constexpr uint32_t kPurposeTrial64 = 0x00000u;   // FP64 sphere candidates
+constexpr uint32_t kPurposeAccept64 = 0x10000u;  // FP64 acceptance uniform
+constexpr uint32_t kPurposeInit = 0x20000u;      // initial spins (t = 0xFFFFFFFF)
+constexpr uint32_t kPurposeTrial32 = 0x40000u;   // FP32 trial (z, azimuth) + acceptance
+constexpr uint32_t kInitT = 0xFFFFFFFFu;
+
+// Error bits set by kernels in the device error word.
+constexpr uint32_t kErrNaN = 1u;
+constexpr uint32_t kErrSphere = 2u;
+
+// ------------------------------------------------------------------ host-side sample
+
+// A validated sample renumbered colour-major: sites of colour 0 first, then colour 1, ...;
+// inside a colour class, increasing caller id. Neighbour order inside a row is the caller's.
+struct LoadedSample {
+    int32_t n = 0;
+    int32_t n_colours = 0;
+    int64_t n_edges = 0;
+    int32_t uniform_degree = 0;  // > 0 when every row has this many links
+    std::vector<int32_t> orig;   // new index -> caller id
+    std::vector<int32_t> inv;    // caller id -> new index
+    std::vector<int32_t> cstart; // [n_colours + 1] class boundaries (new numbering)
+    std::vector<int64_t> row_ptr;  // new numbering
+    std::vector<int32_t> col;      // new numbering, sample-local
+    std::vector<double> J;
+    // per-site parameters in new numbering (always filled; defaults where NULL)
+    std::vector<double> spin_norm, field_axis, k_uni, e_uni, k_cub;
+    std::vector<double> init_spins;  // empty: Philox initial state
+    bool uniform_params = false;     // every site has the same (s, n, k, e, kc)
+    bool has_anisotropy = false;     // some k or kc is non-zero
+    // per colour class: 0 = no neighbour of a lower colour, 1 = every neighbour lower,
+    // 2 = mixed (tested per link)
+    std::vector<int32_t> lower_mode;
+};
+
+// Validates and renumbers; on failure returns false and sets err.
+bool load_sample(const vegas_sample &s, LoadedSample &out, std::string &err);
+
+// ------------------------------------------------------------------ device-side layouts
+
+struct SiteParams32 {  // uniform parameters of a sample, FP32 kernels
+    float nx, ny, nz, s;
+    float ex, ey, ez, k;
+    float kc;
+};
+
+struct SiteParams64 {
+    double nx, ny, nz, s;
+    double ex, ey, ez, k;
+    double kc;
+};
+
+struct Edge64 {  // one directed link, FP64 path
+    double J;
+    int32_t col;  // global (packed) site index
+    int32_t pad;
+};
+
+// Mutable run state kept in device memory so that captured launches need no new
+// arguments between MCS or between calls.
+struct RunState {
+    uint32_t t;       // global MCS counter (Philox counter word 1)
+    uint32_t rec;     // records written in the current run
+    uint32_t ticket;  // last-block-done counter of the reduction
+    uint32_t mcs;     // MCS per temperature/field step of the current run
+    const double *sched;  // [n_steps][n_inst][2] = (beta, B)
+    double *hist;         // [records][n_inst][4]
+};
+
+// One colour class of one sample: everything a sweep launch needs.
+struct PassArgs {
+    void *spins;               // float4 or double4_32a, [global site][replica]
+    const void *edges;         // int2 (col, J float bits) or Edge64, global edge index
+    const int64_t *row_ptr;    // [global site + 1] global edge offsets
+    const int32_t *orig;       // [global site] caller id
+    const void *p0;            // per-site (n, s): float4/double4_32a, or NULL when uniform
+    const void *p1;            // per-site (e, k)
+    const void *pk;            // per-site kc (float/double)
+    RunState *run;
+    double *partial;           // [block][replica][4] of this pass
+    uint32_t *err;
+    uint8_t *alog;             // accept log or NULL
+    uint64_t seed;
+    int64_t edge_base;         // first edge of the sample (uniform degree indexing)
+    int32_t site_off;          // first global site of the sample
+    int32_t g_begin, g_end;    // global site range of the class
+    int32_t lower_end;         // sites with global index < lower_end have a lower colour
+    int32_t log2R;
+    int32_t inst0;             // instance id of the sample's replica 0 (Philox)
+    int32_t inst_local0;       // ctx-local index of replica 0 (schedule column)
+    int32_t n_inst;            // ctx-local instances (schedule row length)
+    int32_t n_sample_sites;    // sites of the sample (accept log indexing)
+    int64_t alog_stride;       // bytes per MCS of the accept log
+    int64_t alog_base;         // offset of replica 0 of this sample inside one MCS
+    uint32_t alog_mcs;
+    int32_t deg;               // uniform degree or 0
+    int32_t lower_mode;        // 0: no link to a lower colour, 1: every link, 2: test each
+    int32_t params_mode;       // 0: uniform, no anisotropy; 1: uniform; 2: per site
+    SiteParams32 u32;
+    SiteParams64 u64;
+};
+
+struct ReduceArgs {
+    const double *partial;     // all passes
+    const int64_t *slot_base;  // [n_samples] first block slot of the sample
+    const int32_t *slot_count; // [n_samples] block slots of the sample (all colours)
+    RunState *run;
+    int32_t R, n_inst;
+};
+
+struct RenormArgs {
+    void *spins;
+    const double *norm;      // [global site] spin norm s_i
+    int64_t n_work;          // global sites * R
+    int32_t log2R;
+};
+
+struct InitArgs {
+    void *spins;
+    const int32_t *orig;
+    const double *norm;      // [global site] spin norm s_i
+    const double *given;     // [sample site][3] caller initial state (new numbering) or NULL
+    uint32_t *err;
+    uint64_t seed;
+    int32_t g_begin, g_end;  // global sites of the sample
+    int32_t inst0;           // instance id of replica 0
+    int32_t log2R;
+};
+
+// ------------------------------------------------------------------ launchers
+
+// Sweep launch of one colour class; lower_mode, params_mode and deg pick the compiled variant.
+void launch_pass32(const PassArgs &a, int grid, void *stream);
+void launch_pass64(const PassArgs &a, int grid, void *stream);
+void launch_reduce(const ReduceArgs &a, void *stream);
+void launch_renorm32(const RenormArgs &a, int grid, void *stream);
+void launch_renorm64(const RenormArgs &a, int grid, void *stream);
+void launch_init32(const InitArgs &a, int grid, void *stream);
+void launch_init64(const InitArgs &a, int grid, void *stream);
+void launch_gather(void *spins, int precision, int64_t site_off, int64_t n, int32_t log2R, int32_t r, double *out3,
+                   int grid, void *stream);
+void launch_scatter(void *spins, int precision, int64_t site_off, int64_t n, int32_t log2R, int32_t r,
+                    const double *in3, int grid, void *stream);
+
+// Blocks per SM the pass kernels reach at kThreads threads (occupancy query).
+int pass_blocks_per_sm(int precision, const PassArgs &a);
+
+}  // namespace vegas

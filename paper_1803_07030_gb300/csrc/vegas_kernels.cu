@@ -1,0 +1,525 @@
+// Device kernels of the Metropolis sweep (Sec. III.B, Eq. 4) on the Heisenberg
+// Hamiltonian (Sec. III.A, Eq. 1-3), for sm_103a.
+//
+// Layout in HBM: spins are [global site][replica] (float4 or double4_32a; w unused), so the R
+// replicas of one site sit next to each other; sites are numbered colour-major per sample,
+// samples packed one after the other. A warp of 32 threads covers 32/R sites x R
+// replicas: with R = 32 one warp is one site, its neighbour rows are contiguous 512-byte
+// lines and each link (col, J) is one broadcast load shared by the replicas.
+//
+// One launch sweeps one colour class: no site of the class links to another, so every
+// thread updates its site from neighbours that this launch never writes. While it
+// gathers the local field, a thread also sums the links to lower colours; those
+// neighbours are already final for this MCS, so -S_i.h_i(lower) - B S_i.n_i - anisotropy
+// summed over all sites is the exact energy after the MCS (each bond is counted once, at
+// its higher-coloured end) without a second pass over the links.
+//
+// The FP64 kernel evaluates every step exactly as the CPU oracle does (no FMA, the same
+// operation order, Marsaglia sampler, correctly rounded sqrt and divide), so its spins and
+// accept decisions match the oracle bit for bit. The FP32 kernels draw one Philox block per
+// attempt (uniform z and azimuth, the acceptance uniform) and use FMA.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "vegas_internal.h"
+
+namespace vegas {
+namespace {
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11:
+// ten rounds of two 32x32->64 multiplies (M0 = 0xD2511F53, M1 = 0xCD9E8D57) with the key
+// bumped by the Weyl constants (0x9E3779B9, 0xBB67AE85) between rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// ------------------------------------------------------------------ FP64 helpers
+// Explicit round-to-nearest operations: the compiler may not fuse them, which keeps the
+// FP64 path identical to the CPU oracle built without contraction.
+__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
+
+// Uniform in [0, 1) with 53 bits: (hi * 2^21 + (lo >> 11)) * 2^-53 (exact).
+__device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
+    const unsigned long long m = ((unsigned long long)hi << 21) | (unsigned long long)(lo >> 11);
+    return __dmul_rn(__ull2double_rn(m), 0x1p-53);
+}
+
+// Point on the unit sphere by Marsaglia's method (Ann. Math. Stat. 43, 1972): draw
+// (u1, u2) uniform in the square [-1, 1)^2 until s = u1^2 + u2^2 < 1, then
+// (2 u1 sqrt(1-s), 2 u2 sqrt(1-s), 1 - 2 s). Candidate k uses counter word 3 = purpose|k.
+__device__ double3 sphere64(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t purpose, uint32_t k0, uint32_t k1,
+                            uint32_t *err) {
+    for (uint32_t k = 0; k < 64; ++k) {
+        const uint4 w = philox10(make_uint4(c0, c1, c2, purpose | k), k0, k1);
+        const double u1 = ds(dm(2.0, u53(w.x, w.y)), 1.0);
+        const double u2 = ds(dm(2.0, u53(w.z, w.w)), 1.0);
+        const double s = da(dm(u1, u1), dm(u2, u2));
+        if (s >= 1.0) continue;
+        const double q = __dsqrt_rn(ds(1.0, s));
+        return make_double3(dm(dm(2.0, u1), q), dm(dm(2.0, u2), q), ds(1.0, dm(2.0, s)));
+    }
+    atomicOr(err, kErrSphere);
+    return make_double3(0.0, 0.0, 1.0);
+}
+
+__device__ __forceinline__ double cub64(double x, double y, double z) {
+    const double xx = dm(x, x), yy = dm(y, y), zz = dm(z, z);
+    return da(da(dm(xx, yy), dm(yy, zz)), dm(xx, zz));
+}
+
+__device__ __forceinline__ float cub32(float x, float y, float z) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    return fmaf(xx, yy, fmaf(yy, zz, xx * zz));
+}
+
+// ------------------------------------------------------------------ block partials
+// Per-block sums of (E, Mx, My, Mz) for each replica. Lanes whose index agrees modulo R
+// hold the same replica; a fixed butterfly and a fixed warp order make the result
+// deterministic. out points at this block's [R][4] slot.
+__device__ __forceinline__ void block_partials(double v[4], int R, double *out) {
+    __shared__ double sm[kThreads / 32][32][4];
+    for (int off = 16; off >= R; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < R) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sm[warp][lane][q] = v[q];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < R) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += sm[w][threadIdx.x][q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[threadIdx.x * 4 + q] = acc[q];
+    }
+}
+
+// ------------------------------------------------------------------ FP64 colour pass
+
+__global__ void __launch_bounds__(kThreads) pass64_kernel(const PassArgs a) {
+    const RunState *rs = a.run;
+    const uint32_t t = rs->t;
+    const uint32_t step = rs->rec / rs->mcs;
+    const double *sched = rs->sched;
+    const int R = 1 << a.log2R;
+    const int64_t n_work = (int64_t)(a.g_end - a.g_begin) << a.log2R;
+    double4_32a *S = (double4_32a *)a.spins;
+    const Edge64 *E = (const Edge64 *)a.edges;
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    double acc4[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += stride) {
+        const int g = a.g_begin + (int)(w >> a.log2R);
+        const int r = (int)(w & (R - 1));
+        const uint32_t inst = (uint32_t)(a.inst0 + r);
+        const double *sc = sched + ((int64_t)step * a.n_inst + a.inst_local0 + r) * 2;
+        const double beta = sc[0], B = sc[1];
+        const uint32_t orig = (uint32_t)a.orig[g];
+        double nx, ny, nz, sn, ex, ey, ez, k, kc;
+        if (a.params_mode == 2) {
+            const double4_32a p0 = ((const double4_32a *)a.p0)[g], p1 = ((const double4_32a *)a.p1)[g];
+            nx = p0.x; ny = p0.y; nz = p0.z; sn = p0.w;
+            ex = p1.x; ey = p1.y; ez = p1.z; k = p1.w;
+            kc = ((const double *)a.pk)[g];
+        } else {
+            nx = a.u64.nx; ny = a.u64.ny; nz = a.u64.nz; sn = a.u64.s;
+            ex = a.u64.ex; ey = a.u64.ey; ez = a.u64.ez; k = a.u64.k; kc = a.u64.kc;
+        }
+        const int64_t si = (int64_t)g * R + r;
+        const double4_32a Si = S[si];
+        // local field in the caller's row order, plus the links to lower colours
+        double hx = 0.0, hy = 0.0, hz = 0.0, lx = 0.0, ly = 0.0, lz = 0.0;
+        for (int64_t e = a.row_ptr[g]; e < a.row_ptr[g + 1]; ++e) {
+            const Edge64 ed = E[e];
+            const double4_32a Sj = S[(int64_t)ed.col * R + r];
+            hx = da(hx, dm(ed.J, Sj.x));
+            hy = da(hy, dm(ed.J, Sj.y));
+            hz = da(hz, dm(ed.J, Sj.z));
+            if (a.lower_mode == 1 || (a.lower_mode == 2 && ed.col < a.lower_end)) {
+                lx = da(lx, dm(ed.J, Sj.x));
+                ly = da(ly, dm(ed.J, Sj.y));
+                lz = da(lz, dm(ed.J, Sj.z));
+            }
+        }
+        hx = da(hx, dm(B, nx));
+        hy = da(hy, dm(B, ny));
+        hz = da(hz, dm(B, nz));
+        // trial: uniform on the sphere of radius s_i
+        const double3 u = sphere64(orig, t, inst, kPurposeTrial64, k0, k1, a.err);
+        const double px = dm(sn, u.x), py = dm(sn, u.y), pz = dm(sn, u.z);
+        // energy change (Eq. 1-3) in a fixed order
+        const double dx = ds(px, Si.x), dy = ds(py, Si.y), dz = ds(pz, Si.z);
+        const double dEex = -da(da(dm(dx, hx), dm(dy, hy)), dm(dz, hz));
+        double dE = dEex;
+        if (a.params_mode != 0) {
+            const double pn = da(da(dm(px, ex), dm(py, ey)), dm(pz, ez));
+            const double po = da(da(dm(Si.x, ex), dm(Si.y, ey)), dm(Si.z, ez));
+            const double dEan = -dm(k, ds(dm(pn, pn), dm(po, po)));
+            const double dEcub = -dm(kc, ds(cub64(px, py, pz), cub64(Si.x, Si.y, Si.z)));
+            dE = da(da(dEex, dEan), dEcub);
+        }
+        // Metropolis acceptance (Eq. 4), k_B = 1
+        bool acc;
+        if (dE <= 0.0) {
+            acc = true;
+        } else {
+            const uint4 wa = philox10(make_uint4(orig, t, inst, kPurposeAccept64), k0, k1);
+            acc = u53(wa.x, wa.y) < exp(-dm(beta, dE));
+        }
+        if (isnan(dE)) {
+            atomicOr(a.err, kErrNaN);
+            acc = false;
+        }
+        if (acc) S[si] = make_double4_32a(px, py, pz, 0.0);
+        if (a.alog && t < a.alog_mcs)
+            a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = acc ? 1 : 0;
+        // this site's share of E and M after the MCS
+        const double qx = acc ? px : Si.x, qy = acc ? py : Si.y, qz = acc ? pz : Si.z;
+        double e_i = -(qx * lx + qy * ly + qz * lz) - B * (qx * nx + qy * ny + qz * nz);
+        if (a.params_mode != 0) {
+            const double pe = qx * ex + qy * ey + qz * ez;
+            e_i -= k * pe * pe + kc * cub64(qx, qy, qz);
+        }
+        acc4[0] += e_i;
+        acc4[1] += qx;
+        acc4[2] += qy;
+        acc4[3] += qz;
+    }
+    block_partials(acc4, R, a.partial + (int64_t)blockIdx.x * R * 4);
+}
+
+// ------------------------------------------------------------------ FP32 colour pass
+// DEG: 6 = every row has six links (loaded as three 16-byte words), 0 = read row_ptr.
+// PM: params_mode (0 uniform without anisotropy, 1 uniform, 2 per site).
+// LM: lower_mode (0 no lower links, 1 all links lower, 2 test each link).
+
+template <int DEG, int PM, int LM>
+__global__ void __launch_bounds__(kThreads) pass32_kernel(const PassArgs a) {
+    const RunState *rs = a.run;
+    const uint32_t t = rs->t;
+    const uint32_t step = rs->rec / rs->mcs;
+    const double *sched = rs->sched;
+    const int R = 1 << a.log2R;
+    const int64_t n_work = (int64_t)(a.g_end - a.g_begin) << a.log2R;
+    float4 *S = (float4 *)a.spins;
+    const int2 *E = (const int2 *)a.edges;
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t w0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // a thread always serves the same replica (the stride is a multiple of 32 >= R)
+    const int r = (int)(w0 & (R - 1));
+    const uint32_t inst = (uint32_t)(a.inst0 + r);
+    const double *sc = sched + ((int64_t)step * a.n_inst + a.inst_local0 + r) * 2;
+    const float beta = (float)sc[0], B = (float)sc[1];
+    float nx = a.u32.nx, ny = a.u32.ny, nz = a.u32.nz, sn = a.u32.s;
+    float ex = a.u32.ex, ey = a.u32.ey, ez = a.u32.ez, k = a.u32.k, kc = a.u32.kc;
+    double acc4[4] = {0.0, 0.0, 0.0, 0.0};
+    float f4[4] = {0.f, 0.f, 0.f, 0.f};
+    int cnt = 0;
+    for (int64_t w = w0; w < n_work; w += stride) {
+        const int g = a.g_begin + (int)(w >> a.log2R);
+        const uint32_t orig = (uint32_t)__ldg(a.orig + g);
+        if (PM == 2) {
+            const float4 p0 = __ldg((const float4 *)a.p0 + g), p1 = __ldg((const float4 *)a.p1 + g);
+            nx = p0.x; ny = p0.y; nz = p0.z; sn = p0.w;
+            ex = p1.x; ey = p1.y; ez = p1.z; k = p1.w;
+            kc = __ldg((const float *)a.pk + g);
+        }
+        const int64_t si = (int64_t)g * R + r;
+        const float4 Si = S[si];
+        float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+        auto link = [&](int2 ed) {
+            const float J = __int_as_float(ed.y);
+            const float4 Sj = __ldg(S + (int64_t)ed.x * R + r);
+            hx = fmaf(J, Sj.x, hx);
+            hy = fmaf(J, Sj.y, hy);
+            hz = fmaf(J, Sj.z, hz);
+            if (LM == 2 && ed.x < a.lower_end) {
+                lx = fmaf(J, Sj.x, lx);
+                ly = fmaf(J, Sj.y, ly);
+                lz = fmaf(J, Sj.z, lz);
+            }
+        };
+        if (DEG == 6) {
+            const int4 *row = (const int4 *)(E + a.edge_base + (int64_t)(g - a.site_off) * 6);
+            const int4 q0 = __ldg(row), q1 = __ldg(row + 1), q2 = __ldg(row + 2);
+            link(make_int2(q0.x, q0.y));
+            link(make_int2(q0.z, q0.w));
+            link(make_int2(q1.x, q1.y));
+            link(make_int2(q1.z, q1.w));
+            link(make_int2(q2.x, q2.y));
+            link(make_int2(q2.z, q2.w));
+        } else {
+            const int64_t e0 = __ldg(a.row_ptr + g), e1 = __ldg(a.row_ptr + g + 1);
+            for (int64_t e = e0; e < e1; ++e) link(__ldg(E + e));
+        }
+        if (LM == 1) {
+            lx = hx;
+            ly = hy;
+            lz = hz;
+        }
+        const float Hx = fmaf(B, nx, hx), Hy = fmaf(B, ny, hy), Hz = fmaf(B, nz, hz);
+        // trial: z uniform in (-1, 1), azimuth uniform in (-pi, pi) (Archimedes' theorem
+        // makes the point uniform on the sphere); third word: acceptance uniform
+        const uint4 rw = philox10(make_uint4(orig, t, inst, kPurposeTrial32), k0, k1);
+        const float z = fmaf((float)(rw.x >> 8), 0x1p-23f, -1.0f + 0x1p-24f);
+        const float phi = fmaf((float)(rw.y >> 8), 0x1p-23f, -1.0f + 0x1p-24f) * 3.14159265358979f;
+        float sphi, cphi;
+        __sincosf(phi, &sphi, &cphi);
+        const float rho2 = fmaf(-z, z, 1.0f);
+        const float rho = rho2 * rsqrtf(rho2);
+        const float px = sn * (rho * cphi), py = sn * (rho * sphi), pz = sn * z;
+        const float dx = px - Si.x, dy = py - Si.y, dz = pz - Si.z;
+        float dE = -fmaf(dx, Hx, fmaf(dy, Hy, dz * Hz));
+        if (PM != 0) {
+            const float pn = fmaf(px, ex, fmaf(py, ey, pz * ez));
+            const float po = fmaf(Si.x, ex, fmaf(Si.y, ey, Si.z * ez));
+            dE = fmaf(-k, (pn - po) * (pn + po), dE);
+            dE = fmaf(-kc, cub32(px, py, pz) - cub32(Si.x, Si.y, Si.z), dE);
+        }
+        const float uacc = (float)(rw.z >> 8) * 0x1p-24f;
+        bool acc = (dE <= 0.f) || (uacc < __expf(-beta * dE));
+        if (dE != dE) {
+            atomicOr(a.err, kErrNaN);
+            acc = false;
+        }
+        if (acc) S[si] = make_float4(px, py, pz, 0.f);
+        if (a.alog && t < a.alog_mcs)
+            a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = acc ? 1 : 0;
+        const float qx = acc ? px : Si.x, qy = acc ? py : Si.y, qz = acc ? pz : Si.z;
+        float e_i = -B * fmaf(qx, nx, fmaf(qy, ny, qz * nz));
+        if (LM != 0) e_i -= fmaf(qx, lx, fmaf(qy, ly, qz * lz));
+        if (PM != 0) {
+            const float pe = fmaf(qx, ex, fmaf(qy, ey, qz * ez));
+            e_i -= fmaf(k * pe, pe, kc * cub32(qx, qy, qz));
+        }
+        f4[0] += e_i;
+        f4[1] += qx;
+        f4[2] += qy;
+        f4[3] += qz;
+        if (++cnt == 16) {  // short FP32 runs, FP64 beyond
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc4[q] += (double)f4[q];
+                f4[q] = 0.f;
+            }
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc4[q] += (double)f4[q];
+    block_partials(acc4, R, a.partial + (int64_t)blockIdx.x * R * 4);
+}
+
+// ------------------------------------------------------------------ per-MCS reduction
+// One warp per instance sums its sample's block partials over every colour class in a
+// fixed order and appends the record; the last block to finish advances the MCS
+// counter and the record index (no waiting: a ticket counter, not a barrier).
+__global__ void __launch_bounds__(256) reduce_kernel(const ReduceArgs a) {
+    RunState *rs = a.run;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int il = blockIdx.x * 8 + warp;
+    const uint32_t rec = rs->rec;
+    if (il < a.n_inst) {
+        const int s = il / a.R, r = il % a.R;
+        const int64_t base = a.slot_base[s];
+        const int32_t cnt = a.slot_count[s];
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int32_t j = lane; j < cnt; j += 32) {
+            const double *p = a.partial + ((base + j) * a.R + r) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] += p[q];
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+        }
+        if (lane == 0) {
+            double *h = rs->hist + ((int64_t)rec * a.n_inst + il) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) h[q] = v[q];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t done = atomicAdd(&rs->ticket, 1u);
+        if (done == gridDim.x - 1) {
+            rs->ticket = 0;
+            rs->t = rs->t + 1;
+            rs->rec = rec + 1;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ renormalisation
+// S_i <- s_i S_i / |S_i| with FP64 arithmetic (the FP64 form matches the oracle's
+// f = s / sqrt((x^2 + y^2) + z^2), then x f, y f, z f).
+__global__ void renorm64_kernel(const RenormArgs a) {
+    double4_32a *S = (double4_32a *)a.spins;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < a.n_work; w += (int64_t)gridDim.x * blockDim.x) {
+        const double4_32a v = S[w];
+        const double n2 = da(da(dm(v.x, v.x), dm(v.y, v.y)), dm(v.z, v.z));
+        const double f = __ddiv_rn(a.norm[w >> a.log2R], __dsqrt_rn(n2));
+        S[w] = make_double4_32a(dm(v.x, f), dm(v.y, f), dm(v.z, f), 0.0);
+    }
+}
+
+__global__ void renorm32_kernel(const RenormArgs a) {
+    float4 *S = (float4 *)a.spins;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < a.n_work; w += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = S[w];
+        const double x = v.x, y = v.y, z = v.z;
+        const double f = a.norm[w >> a.log2R] / sqrt(x * x + y * y + z * z);
+        S[w] = make_float4((float)(x * f), (float)(y * f), (float)(z * f), 0.f);
+    }
+}
+
+// ------------------------------------------------------------------ initial state
+// S_i = s_i * sphere(counter = (caller id, 0xFFFFFFFF, instance, 0x20000|k)), in FP64 for
+// both precisions (FP32 contexts round it), or the caller's state.
+template <typename V>
+__global__ void init_kernel(const InitArgs a) {
+    V *S = (V *)a.spins;
+    const int R = 1 << a.log2R;
+    const int64_t n_work = (int64_t)(a.g_end - a.g_begin) << a.log2R;
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += (int64_t)gridDim.x * blockDim.x) {
+        const int g = a.g_begin + (int)(w >> a.log2R);
+        const int r = (int)(w & (R - 1));
+        double x, y, z;
+        if (a.given) {
+            const double *p = a.given + (int64_t)(g - a.g_begin) * 3;
+            x = p[0];
+            y = p[1];
+            z = p[2];
+        } else {
+            const double s = a.norm[g];
+            const double3 u = sphere64((uint32_t)a.orig[g], kInitT, (uint32_t)(a.inst0 + r), kPurposeInit, k0, k1, a.err);
+            x = dm(s, u.x);
+            y = dm(s, u.y);
+            z = dm(s, u.z);
+        }
+        V v;
+        v.x = x;
+        v.y = y;
+        v.z = z;
+        v.w = 0;
+        S[(int64_t)g * R + r] = v;
+    }
+}
+
+// ------------------------------------------------------------------ gather / scatter
+__global__ void gather_kernel(const void *spins, int precision, int64_t site_off, int64_t n, int32_t log2R, int32_t r,
+                              double *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t w = ((site_off + i) << log2R) + r;
+        if (precision == 64) {
+            const double4_32a v = ((const double4_32a *)spins)[w];
+            out[3 * i] = v.x;
+            out[3 * i + 1] = v.y;
+            out[3 * i + 2] = v.z;
+        } else {
+            const float4 v = ((const float4 *)spins)[w];
+            out[3 * i] = v.x;
+            out[3 * i + 1] = v.y;
+            out[3 * i + 2] = v.z;
+        }
+    }
+}
+
+__global__ void scatter_kernel(void *spins, int precision, int64_t site_off, int64_t n, int32_t log2R, int32_t r,
+                               const double *in) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t w = ((site_off + i) << log2R) + r;
+        if (precision == 64)
+            ((double4_32a *)spins)[w] = make_double4_32a(in[3 * i], in[3 * i + 1], in[3 * i + 2], 0.0);
+        else
+            ((float4 *)spins)[w] = make_float4((float)in[3 * i], (float)in[3 * i + 1], (float)in[3 * i + 2], 0.f);
+    }
+}
+
+// ------------------------------------------------------------------ variant table
+using PassFn = void (*)(PassArgs);
+
+template <int DEG>
+PassFn pick32(int pm, int lm) {
+    static const PassFn tab[3][3] = {
+        {pass32_kernel<DEG, 0, 0>, pass32_kernel<DEG, 0, 1>, pass32_kernel<DEG, 0, 2>},
+        {pass32_kernel<DEG, 1, 0>, pass32_kernel<DEG, 1, 1>, pass32_kernel<DEG, 1, 2>},
+        {pass32_kernel<DEG, 2, 0>, pass32_kernel<DEG, 2, 1>, pass32_kernel<DEG, 2, 2>},
+    };
+    return tab[pm][lm];
+}
+
+PassFn select32(const PassArgs &a) { return a.deg == 6 ? pick32<6>(a.params_mode, a.lower_mode) : pick32<0>(a.params_mode, a.lower_mode); }
+
+}  // namespace
+
+void launch_pass32(const PassArgs &a, int grid, void *stream) {
+    select32(a)<<<grid, kThreads, 0, (cudaStream_t)stream>>>(a);
+}
+
+void launch_pass64(const PassArgs &a, int grid, void *stream) {
+    pass64_kernel<<<grid, kThreads, 0, (cudaStream_t)stream>>>(a);
+}
+
+void launch_reduce(const ReduceArgs &a, void *stream) {
+    const int grid = (a.n_inst + 7) / 8;
+    reduce_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+}
+
+void launch_renorm32(const RenormArgs &a, int grid, void *stream) {
+    renorm32_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+}
+
+void launch_renorm64(const RenormArgs &a, int grid, void *stream) {
+    renorm64_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+}
+
+void launch_init32(const InitArgs &a, int grid, void *stream) {
+    init_kernel<float4><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+}
+
+void launch_init64(const InitArgs &a, int grid, void *stream) {
+    init_kernel<double4_32a><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+}
+
+void launch_gather(void *spins, int precision, int64_t site_off, int64_t n, int32_t log2R, int32_t r, double *out3,
+                   int grid, void *stream) {
+    gather_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(spins, precision, site_off, n, log2R, r, out3);
+}
+
+void launch_scatter(void *spins, int precision, int64_t site_off, int64_t n, int32_t log2R, int32_t r,
+                    const double *in3, int grid, void *stream) {
+    scatter_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(spins, precision, site_off, n, log2R, r, in3);
+}
+
+int pass_blocks_per_sm(int precision, const PassArgs &a) {
+    int nb = 0;
+    if (precision == 64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass64_kernel, kThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select32(a), kThreads, 0);
+    return nb > 0 ? nb : 1;
+}
+
+}  // namespace vegas

@@ -1,0 +1,233 @@
+// Sample loader (host): validation, greedy colouring and colour-major renumbering.
+//
+// The sample is the paper's material file (Sec. III.C: per-site spin norm, field axis and
+// type; links with exchange J_ij) plus its anisotropy file, given as arrays. The loader
+// rejects anything the sweep cannot treat exactly: asymmetric or duplicate links,
+// self-links, out-of-range neighbours, non-finite parameters, an improper colouring.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+
+#include "vegas_internal.h"
+
+namespace vegas {
+
+namespace {
+
+bool finite_all(const double *p, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+std::string at(const char *what, int64_t i) { return std::string(what) + " at index " + std::to_string(i); }
+
+
+}  // namespace
+
+}  // namespace vegas
+
+extern "C" int32_t vegas_greedy_colour(int32_t n, const int64_t *row_ptr, const int32_t *col, int32_t *color) {
+    if (n < 0 || (n > 0 && (!row_ptr || !color))) return -1;
+    std::vector<int32_t> seen;  // seen[c] == i  <=>  colour c is used by a coloured neighbour of i
+    int32_t nc = 0;
+    for (int32_t i = 0; i < n; ++i) color[i] = -1;
+    for (int32_t i = 0; i < n; ++i) {
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int32_t j = col[e];
+            if (j < 0 || j >= n) return -1;
+            const int32_t cj = color[j];
+            if (cj >= 0) {
+                if ((size_t)cj >= seen.size()) seen.resize((size_t)cj + 1, -1);
+                seen[(size_t)cj] = i;
+            }
+        }
+        int32_t c = 0;
+        while ((size_t)c < seen.size() && seen[(size_t)c] == i) ++c;
+        color[i] = c;
+        nc = std::max(nc, c + 1);
+    }
+    return nc;
+}
+
+namespace vegas {
+
+bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err) {
+    const int32_t n = s.n_sites;
+    if (n < 1) { err = "n_sites must be >= 1"; return false; }
+    if (!s.row_ptr) { err = "row_ptr is NULL"; return false; }
+    if (s.n_edges < 0) { err = "n_edges < 0"; return false; }
+    if (s.n_edges > 0 && (!s.col || !s.J)) { err = "col or J is NULL"; return false; }
+    if (s.row_ptr[0] != 0) { err = "row_ptr[0] != 0"; return false; }
+    for (int32_t i = 0; i < n; ++i)
+        if (s.row_ptr[i + 1] < s.row_ptr[i]) { err = at("row_ptr decreases", i); return false; }
+    if (s.row_ptr[n] != s.n_edges) { err = "row_ptr[n_sites] != n_edges"; return false; }
+    if (s.n_edges > (int64_t)INT32_MAX) { err = "more than 2^31-1 links in one sample"; return false; }
+    const int64_t E = s.n_edges;
+    for (int64_t e = 0; e < E; ++e)
+        if (s.col[e] < 0 || s.col[e] >= n) { err = at("col out of range", e); return false; }
+    if (!finite_all(s.J, E)) { err = "non-finite J"; return false; }
+
+    // self-links, duplicates and symmetry: short rows are scanned, long rows use a sorted copy
+    constexpr int64_t kScan = 32;
+    // sorted (col, J) copies of the rows too long to scan
+    std::unordered_map<int32_t, std::vector<std::pair<int32_t, double>>> sorted;
+    for (int32_t i = 0; i < n; ++i) {
+        const int64_t b = s.row_ptr[i], d = s.row_ptr[i + 1] - b;
+        if (d > kScan) {
+            auto &v = sorted[i];
+            v.reserve((size_t)d);
+            for (int64_t e = b; e < b + d; ++e) v.emplace_back(s.col[e], s.J[e]);
+            std::sort(v.begin(), v.end());
+        }
+    }
+    auto find_in_row = [&](int32_t j, int32_t i, double *Jout) -> int {
+        const int64_t b = s.row_ptr[j], d = s.row_ptr[j + 1] - b;
+        if (d > kScan) {
+            const auto &v = sorted.at(j);
+            auto it = std::lower_bound(v.begin(), v.end(), std::make_pair(i, -(double)INFINITY));
+            if (it == v.end() || it->first != i) return 0;
+            *Jout = it->second;
+            return 1;
+        }
+        for (int64_t e = b; e < b + d; ++e)
+            if (s.col[e] == i) { *Jout = s.J[e]; return 1; }
+        return 0;
+    };
+    for (int32_t i = 0; i < n; ++i) {
+        const int64_t b = s.row_ptr[i], d = s.row_ptr[i + 1] - b;
+        if (d > kScan) {
+            const auto &v = sorted.at(i);
+            for (size_t q = 0; q < v.size(); ++q) {
+                if (v[q].first == i) { err = at("self-link at site", i); return false; }
+                if (q > 0 && v[q].first == v[q - 1].first) { err = at("duplicate link at site", i); return false; }
+            }
+        } else {
+            for (int64_t e = b; e < b + d; ++e) {
+                if (s.col[e] == i) { err = at("self-link at site", i); return false; }
+                for (int64_t f = b; f < e; ++f)
+                    if (s.col[f] == s.col[e]) { err = at("duplicate link at site", i); return false; }
+            }
+        }
+        for (int64_t e = b; e < b + d; ++e) {
+            double Jr = 0.0;
+            if (!find_in_row(s.col[e], i, &Jr)) { err = at("link without its reverse, edge", e); return false; }
+            if (Jr != s.J[e]) { err = at("J not symmetric, edge", e); return false; }
+        }
+    }
+    sorted.clear();
+
+    // parameters (defaults: s = 1, n = +z, k = 0, e = +z, kc = 0)
+    const double *prm[5] = {s.spin_norm, s.field_axis, s.k_uni, s.e_uni, s.k_cub};
+    const int64_t len[5] = {n, 3 * (int64_t)n, n, 3 * (int64_t)n, n};
+    const char *name[5] = {"spin_norm", "field_axis", "k_uni", "e_uni", "k_cub"};
+    for (int q = 0; q < 5; ++q)
+        if (prm[q] && !finite_all(prm[q], len[q])) { err = std::string("non-finite ") + name[q]; return false; }
+    if (s.spin_norm)
+        for (int32_t i = 0; i < n; ++i)
+            if (!(s.spin_norm[i] > 0.0)) { err = at("spin_norm <= 0", i); return false; }
+    if (s.init_spins && !finite_all(s.init_spins, 3 * (int64_t)n)) { err = "non-finite init_spins"; return false; }
+
+    // colouring
+    std::vector<int32_t> colour((size_t)n);
+    int32_t nc = 0;
+    if (s.color) {
+        for (int32_t i = 0; i < n; ++i) {
+            if (s.color[i] < 0 || s.color[i] >= kMaxColours) { err = at("colour outside [0, 64)", i); return false; }
+            colour[(size_t)i] = s.color[i];
+            nc = std::max(nc, s.color[i] + 1);
+        }
+        for (int32_t i = 0; i < n; ++i)
+            for (int64_t e = s.row_ptr[i]; e < s.row_ptr[i + 1]; ++e)
+                if (colour[(size_t)s.col[e]] == colour[(size_t)i]) { err = at("colouring not proper at site", i); return false; }
+    } else {
+        nc = vegas_greedy_colour(n, s.row_ptr, s.col, colour.data());
+        if (nc > kMaxColours) { err = "greedy colouring needs more than 64 colours"; return false; }
+    }
+
+    // colour-major renumbering, increasing caller id inside a class
+    L.n = n;
+    L.n_colours = nc;
+    L.n_edges = E;
+    L.cstart.assign((size_t)nc + 1, 0);
+    for (int32_t i = 0; i < n; ++i) L.cstart[(size_t)colour[(size_t)i] + 1]++;
+    for (int32_t c = 0; c < nc; ++c) L.cstart[(size_t)c + 1] += L.cstart[(size_t)c];
+    std::vector<int32_t> fill(L.cstart.begin(), L.cstart.end() - 1);
+    L.orig.resize((size_t)n);
+    L.inv.resize((size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t g = fill[(size_t)colour[(size_t)i]]++;
+        L.orig[(size_t)g] = i;
+        L.inv[(size_t)i] = g;
+    }
+    L.row_ptr.resize((size_t)n + 1);
+    L.col.resize((size_t)E);
+    L.J.resize((size_t)E);
+    L.row_ptr[0] = 0;
+    int32_t deg0 = (int32_t)(s.row_ptr[1] - s.row_ptr[0]);
+    bool uni_deg = true;
+    for (int32_t g = 0; g < n; ++g) {
+        const int32_t i = L.orig[(size_t)g];
+        const int64_t b = s.row_ptr[i], d = s.row_ptr[i + 1] - b;
+        if (d != deg0) uni_deg = false;
+        const int64_t o = L.row_ptr[(size_t)g];
+        for (int64_t k = 0; k < d; ++k) {
+            L.col[(size_t)(o + k)] = L.inv[(size_t)s.col[b + k]];
+            L.J[(size_t)(o + k)] = s.J[b + k];
+        }
+        L.row_ptr[(size_t)g + 1] = o + d;
+    }
+    L.uniform_degree = (uni_deg && deg0 > 0) ? deg0 : 0;
+
+    // which classes see lower colours
+    L.lower_mode.assign((size_t)nc, 0);
+    for (int32_t c = 0; c < nc; ++c) {
+        int64_t lo = 0, all = 0;
+        for (int32_t g = L.cstart[(size_t)c]; g < L.cstart[(size_t)c + 1]; ++g)
+            for (int64_t e = L.row_ptr[(size_t)g]; e < L.row_ptr[(size_t)g + 1]; ++e) {
+                ++all;
+                if (L.col[(size_t)e] < L.cstart[(size_t)c]) ++lo;
+            }
+        L.lower_mode[(size_t)c] = (lo == 0) ? 0 : (lo == all ? 1 : 2);
+    }
+
+    // parameters in the new numbering
+    L.spin_norm.resize((size_t)n);
+    L.field_axis.resize(3 * (size_t)n);
+    L.k_uni.resize((size_t)n);
+    L.e_uni.resize(3 * (size_t)n);
+    L.k_cub.resize((size_t)n);
+    for (int32_t g = 0; g < n; ++g) {
+        const int64_t i = L.orig[(size_t)g];
+        L.spin_norm[(size_t)g] = s.spin_norm ? s.spin_norm[i] : 1.0;
+        for (int q = 0; q < 3; ++q) {
+            L.field_axis[3 * (size_t)g + q] = s.field_axis ? s.field_axis[3 * i + q] : (q == 2 ? 1.0 : 0.0);
+            L.e_uni[3 * (size_t)g + q] = s.e_uni ? s.e_uni[3 * i + q] : (q == 2 ? 1.0 : 0.0);
+        }
+        L.k_uni[(size_t)g] = s.k_uni ? s.k_uni[i] : 0.0;
+        L.k_cub[(size_t)g] = s.k_cub ? s.k_cub[i] : 0.0;
+    }
+    bool uni = true, ani = false;
+    for (int32_t g = 0; g < n && (uni || !ani); ++g) {
+        if (L.k_uni[(size_t)g] != 0.0 || L.k_cub[(size_t)g] != 0.0) ani = true;
+        if (L.spin_norm[(size_t)g] != L.spin_norm[0] || L.k_uni[(size_t)g] != L.k_uni[0] ||
+            L.k_cub[(size_t)g] != L.k_cub[0])
+            uni = false;
+        for (int q = 0; q < 3; ++q)
+            if (L.field_axis[3 * (size_t)g + q] != L.field_axis[(size_t)q] ||
+                L.e_uni[3 * (size_t)g + q] != L.e_uni[(size_t)q])
+                uni = false;
+    }
+    L.uniform_params = uni;
+    L.has_anisotropy = ani;
+    if (s.init_spins) {
+        L.init_spins.resize(3 * (size_t)n);
+        for (int32_t g = 0; g < n; ++g)
+            for (int q = 0; q < 3; ++q) L.init_spins[3 * (size_t)g + q] = s.init_spins[3 * (int64_t)L.orig[(size_t)g] + q];
+    }
+    return true;
+}
+
+}  // namespace vegas

@@ -1,0 +1,326 @@
+"""Thin ctypes binding of the C-ABI in include/vegas.h (argument marshalling only).
+
+Every step of the sweep runs in the CUDA library; this module only converts numpy arrays
+to the C structs and back. The library must have been built (paper_1803_07030_gb300.build);
+if it is missing, loading raises instead of falling back to anything else.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .build import LIB
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEVICE, ESTATE = range(7)
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EDEVICE", 6: "ESTATE"}
+
+P = C.c_void_p
+
+
+class vegas_sample(C.Structure):
+    _fields_ = [
+        ("n_sites", C.c_int32),
+        ("pad_", C.c_int32),
+        ("n_edges", C.c_int64),
+        ("row_ptr", P),
+        ("col", P),
+        ("J", P),
+        ("type", P),
+        ("spin_norm", P),
+        ("field_axis", P),
+        ("k_uni", P),
+        ("e_uni", P),
+        ("k_cub", P),
+        ("color", P),
+        ("init_spins", P),
+    ]
+
+
+class vegas_options(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32),
+        ("replicas", C.c_int32),
+        ("seed", C.c_uint64),
+        ("inst_base", C.c_int32),
+        ("device", C.c_int32),
+        ("cuda_stream", P),
+        ("variant", C.c_int32),
+        ("accept_log_mcs", C.c_int32),
+        ("timing", C.c_int32),
+        ("graphs", C.c_int32),
+    ]
+
+
+class vegas_stats_t(C.Structure):
+    _fields_ = [
+        ("n_samples", C.c_int32),
+        ("n_instances", C.c_int32),
+        ("replicas", C.c_int32),
+        ("precision", C.c_int32),
+        ("max_colours", C.c_int32),
+        ("variant", C.c_int32),
+        ("n_sites", C.c_int64),
+        ("n_edges", C.c_int64),
+        ("records", C.c_int64),
+        ("mcs_done", C.c_uint32),
+        ("device_error", C.c_uint32),
+        ("kernel_launches", C.c_int64),
+        ("sweep_launches", C.c_int64),
+        ("sweep_ms", C.c_double),
+        ("last_run_ms", C.c_double),
+        ("device_bytes", C.c_int64),
+    ]
+
+
+# every function declared in include/vegas.h, with its ctypes signature
+SIGNATURES = {
+    "vegas_default_options": (None, [P]),
+    "vegas_create": (C.c_int, [P, C.c_int32, P, P]),
+    "vegas_run": (C.c_int, [P, P, P, C.c_int32, C.c_int32]),
+    "vegas_history": (C.c_int, [P, P, C.c_size_t, P]),
+    "vegas_get_spins": (C.c_int, [P, C.c_int32, P]),
+    "vegas_set_spins": (C.c_int, [P, C.c_int32, P]),
+    "vegas_accept_log": (C.c_int, [P, P, C.c_size_t, P]),
+    "vegas_stats": (C.c_int, [P, P]),
+    "vegas_greedy_colour": (C.c_int32, [C.c_int32, P, P, P]),
+    "vegas_last_error": (C.c_char_p, [P]),
+    "vegas_destroy": (None, [P]),
+}
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None) -> C.CDLL:
+    """Load libvegas.so (built in-tree); raises OSError if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB
+    if not os.path.exists(p):
+        raise OSError(f"CUDA library not built: {p} (run paper_1803_07030_gb300.build.build())")
+    lib = C.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class VegasError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st: int, ctx_ptr) -> None:
+    if st != OK:
+        msg = load_library().vegas_last_error(ctx_ptr)
+        raise VegasError(st, msg.decode() if msg else "")
+
+
+def _arr(a, dtype, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a if shape is None else a.reshape(shape)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def vegas_greedy_colour(row_ptr, col) -> tuple:
+    """Host-only greedy colouring of the library (sites in index order)."""
+    rp = _arr(row_ptr, np.int64)
+    cl = _arr(col, np.int32)
+    n = rp.shape[0] - 1
+    out = np.zeros(max(n, 1), dtype=np.int32)
+    nc = load_library().vegas_greedy_colour(n, _ptr(rp), _ptr(cl), _ptr(out))
+    if nc < 0:
+        raise ValueError("invalid CSR")
+    return out[:n], int(nc)
+
+
+def vegas_default_options() -> vegas_options:
+    o = vegas_options()
+    load_library().vegas_default_options(C.byref(o))
+    return o
+
+
+class _SampleArrays:
+    """Keeps the numpy arrays a vegas_sample points into alive."""
+
+    def __init__(self, s):
+        n = int(np.asarray(s.row_ptr).shape[0] - 1)
+        self.row_ptr = _arr(s.row_ptr, np.int64)
+        self.col = _arr(s.col, np.int32)
+        self.J = _arr(s.J, np.float64)
+        g = lambda k: getattr(s, k, None)  # noqa: E731
+        self.type = _arr(g("type"), np.int32)
+        self.spin_norm = _arr(g("spin_norm"), np.float64)
+        self.field_axis = _arr(g("field_axis"), np.float64, (n, 3) if g("field_axis") is not None else None)
+        self.k_uni = _arr(g("k_uni"), np.float64)
+        self.e_uni = _arr(g("e_uni"), np.float64, (n, 3) if g("e_uni") is not None else None)
+        self.k_cub = _arr(g("k_cub"), np.float64)
+        self.color = _arr(g("colour"), np.int32)
+        self.init_spins = _arr(g("init_spins"), np.float64)
+        self.c = vegas_sample(n, 0, int(self.col.shape[0]), _ptr(self.row_ptr), _ptr(self.col), _ptr(self.J),
+                              _ptr(self.type), _ptr(self.spin_norm), _ptr(self.field_axis), _ptr(self.k_uni),
+                              _ptr(self.e_uni), _ptr(self.k_cub), _ptr(self.color), _ptr(self.init_spins))
+
+
+def vegas_create(samples: Sequence, options: vegas_options):
+    """Returns an opaque context pointer (int). Raises VegasError on failure."""
+    keep = [_SampleArrays(s) for s in samples]
+    arr = (vegas_sample * len(keep))(*[k.c for k in keep])
+    ctx = P()
+    st = load_library().vegas_create(arr, len(keep), C.byref(options), C.byref(ctx))
+    _check(st, None)
+    return ctx.value
+
+
+def vegas_run(ctx, T, B, n_steps: int, mcs: int) -> None:
+    T = _arr(T, np.float64)
+    B = _arr(B, np.float64)
+    _check(load_library().vegas_run(ctx, _ptr(T), _ptr(B), n_steps, mcs), ctx)
+
+
+def vegas_history(ctx) -> np.ndarray:
+    lib = load_library()
+    n = C.c_size_t()
+    _check(lib.vegas_history(ctx, None, 0, C.byref(n)), ctx)
+    out = np.zeros(n.value, dtype=np.float64)
+    _check(lib.vegas_history(ctx, _ptr(out), n.value, C.byref(n)), ctx)
+    return out
+
+
+def vegas_get_spins(ctx, inst: int, n_sites: int) -> np.ndarray:
+    out = np.zeros((n_sites, 3), dtype=np.float64)
+    _check(load_library().vegas_get_spins(ctx, inst, _ptr(out)), ctx)
+    return out
+
+
+def vegas_set_spins(ctx, inst: int, spins) -> None:
+    s = _arr(spins, np.float64)
+    _check(load_library().vegas_set_spins(ctx, inst, _ptr(s)), ctx)
+
+
+def vegas_accept_log(ctx) -> np.ndarray:
+    lib = load_library()
+    n = C.c_size_t()
+    _check(lib.vegas_accept_log(ctx, None, 0, C.byref(n)), ctx)
+    out = np.zeros(n.value, dtype=np.uint8)
+    if n.value:
+        _check(lib.vegas_accept_log(ctx, _ptr(out), n.value, C.byref(n)), ctx)
+    return out
+
+
+def vegas_stats(ctx) -> dict:
+    s = vegas_stats_t()
+    _check(load_library().vegas_stats(ctx, C.byref(s)), ctx)
+    return {k: getattr(s, k) for k, _ in vegas_stats_t._fields_}
+
+
+def vegas_last_error(ctx=None) -> str:
+    m = load_library().vegas_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def vegas_destroy(ctx) -> None:
+    if ctx:
+        load_library().vegas_destroy(ctx)
+
+
+def _current_stream() -> Optional[int]:
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # torch missing or no device: the library makes its own stream
+        return None
+    return None
+
+
+class Context:
+    """One vegas context: samples x replicas instances on one GPU.
+
+    samples: objects with numpy attributes row_ptr, col, J and optionally type, spin_norm,
+    field_axis, k_uni, e_uni, k_cub, colour, init_spins (the vegas_sample fields).
+    stream: a cudaStream_t as int, 'torch' for torch's current stream, or None (own stream).
+    """
+
+    def __init__(self, samples: Sequence, precision: int = 32, replicas: int = 1, seed: int = 1,
+                 inst_base: int = 0, device: int = -1, stream="torch", variant: int = -1,
+                 accept_log_mcs: int = 0, timing: bool = False, graphs: bool = True):
+        self.samples = list(samples)
+        self.n_sites = [int(np.asarray(s.row_ptr).shape[0] - 1) for s in self.samples]
+        o = vegas_default_options()
+        o.precision = precision
+        o.replicas = replicas
+        o.seed = seed
+        o.inst_base = inst_base
+        o.device = device
+        o.variant = variant
+        o.accept_log_mcs = accept_log_mcs
+        o.timing = 1 if timing else 0
+        o.graphs = 1 if graphs else 0
+        o.cuda_stream = _current_stream() if stream == "torch" else stream
+        self.replicas = replicas
+        self.ptr = None
+        self.ptr = vegas_create(self.samples, o)
+
+    @property
+    def n_instances(self) -> int:
+        return len(self.samples) * self.replicas
+
+    def run(self, T, B, mcs: int) -> None:
+        """T, B: scalars, per-step 1-D arrays, or [n_instances, n_steps] arrays."""
+        T = np.asarray(T, dtype=np.float64)
+        T = T.reshape(1, 1) if T.ndim == 0 else (T[None, :] if T.ndim == 1 else T)
+        n_steps = T.shape[1]
+        B = np.asarray(B, dtype=np.float64)
+        B = np.full((1, n_steps), float(B)) if B.ndim == 0 else (B[None, :] if B.ndim == 1 else B)
+        shape = (self.n_instances, n_steps)
+        vegas_run(self.ptr, np.broadcast_to(T, shape), np.broadcast_to(B, shape), n_steps, mcs)
+
+    def history(self) -> np.ndarray:
+        """[n_instances, records, 4] = (E, Mx, My, Mz) after every MCS."""
+        h = vegas_history(self.ptr)
+        return h.reshape(self.n_instances, -1, 4)
+
+    def spins(self, inst: int) -> np.ndarray:
+        return vegas_get_spins(self.ptr, inst, self.n_sites[inst // self.replicas])
+
+    def set_spins(self, inst: int, spins) -> None:
+        vegas_set_spins(self.ptr, inst, spins)
+
+    def accept_log(self) -> np.ndarray:
+        return vegas_accept_log(self.ptr)
+
+    def stats(self) -> dict:
+        return vegas_stats(self.ptr)
+
+    def close(self) -> None:
+        if self.ptr:
+            vegas_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,125 @@
+"""C-ABI library on the host (no GPU): it builds, loads, exports what include/vegas.h
+declares, colours like the oracle, and rejects invalid samples and options before it
+touches a device."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+import oracle
+import paper_1803_07030_gb300 as vg
+from paper_1803_07030_gb300 import vegas as vb
+from lattices import fcc_sphere, random_graph, sc_periodic, triangles
+
+
+@pytest.fixture(scope="module")
+def lib():
+    vg.build()
+    return vg.load_library()
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "vegas.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vegas_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_function(lib):
+    names = _declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(vb.SIGNATURES)
+
+
+def test_struct_sizes_match_header(lib):
+    import ctypes as C
+
+    # vegas_sample: 2 int32 + int64 + 11 pointers; options and stats as laid out in the header
+    assert C.sizeof(vb.vegas_sample) == 16 + 11 * 8
+    o = vg.vegas_default_options()
+    assert (o.precision, o.replicas, o.seed, o.device, o.variant, o.graphs) == (32, 1, 1, -1, -1, 1)
+
+
+@pytest.mark.parametrize("make", [lambda: sc_periodic(6), lambda: sc_periodic((5, 4, 3)), lambda: triangles(7),
+                                  lambda: fcc_sphere(3.7), lambda: random_graph(150, 0.04, 9)])
+def test_greedy_colouring_matches_oracle(lib, make):
+    s = make()
+    c, nc = vg.vegas_greedy_colour(s.row_ptr, s.col)
+    c2, nc2 = oracle.greedy_colour(s)
+    assert nc == nc2 and np.array_equal(c, c2)
+
+
+def _create_status(samples, **kw):
+    o = vg.vegas_default_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    try:
+        ctx = vb.vegas_create(samples, o)
+    except vb.VegasError as e:
+        return e.status, str(e)
+    vb.vegas_destroy(ctx)
+    return vb.OK, ""
+
+
+def _bad(mut):
+    s = sc_periodic(4)
+    s.J = s.J.copy()
+    s.col = s.col.copy()
+    s.row_ptr = s.row_ptr.copy()
+    mut(s)
+    return s
+
+
+@pytest.mark.parametrize(
+    "name,mut,needle",
+    [
+        ("asymmetric J", lambda s: s.J.__setitem__(0, 0.5), "not symmetric"),
+        ("self link", lambda s: s.col.__setitem__(0, 0), "self-link"),
+        ("duplicate", lambda s: s.col.__setitem__(1, s.col[0]), "duplicate"),
+        ("out of range", lambda s: s.col.__setitem__(2, 64), "out of range"),
+        ("row_ptr start", lambda s: s.row_ptr.__setitem__(0, 1), "row_ptr[0]"),
+        ("nan J", lambda s: s.J.__setitem__(5, np.nan), "non-finite J"),
+        ("bad norm", lambda s: setattr(s, "spin_norm", np.zeros(64)), "spin_norm"),
+        ("nan axis", lambda s: setattr(s, "field_axis", np.full((64, 3), np.nan)), "field_axis"),
+        ("improper colouring", lambda s: setattr(s, "colour", np.zeros(64, dtype=np.int32)), "not proper"),
+    ],
+)
+def test_invalid_samples_rejected(lib, name, mut, needle):
+    st, msg = _create_status([_bad(mut)])
+    assert st == vb.EINVAL, (name, st, msg)
+    assert needle in msg
+
+
+@pytest.mark.parametrize("opt", [{"precision": 16}, {"replicas": 3}, {"replicas": 64}, {"variant": 7},
+                                 {"accept_log_mcs": -1}])
+def test_invalid_options_rejected(lib, opt):
+    st, msg = _create_status([sc_periodic(4)], **opt)
+    assert st == vb.EINVAL, (opt, msg)
+
+
+def test_null_safety(lib):
+    import ctypes as C
+
+    lib.vegas_destroy(None)
+    assert isinstance(lib.vegas_last_error(None), bytes)
+    assert lib.vegas_stats(None, None) == vb.EINVAL
+    assert lib.vegas_run(None, None, None, 1, 1) == vb.EINVAL
+    out = C.c_void_p()
+    assert lib.vegas_create(None, 0, None, C.byref(out)) == vb.EINVAL and not out.value
+
+
+def test_no_device_is_an_error_not_a_fallback(lib):
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    st, msg = _create_status([sc_periodic(4)])
+    assert st == vb.ECUDA and "no CUDA device" in msg

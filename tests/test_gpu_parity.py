@@ -1,0 +1,335 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+FP64: spins, accept/reject decisions and history must match the oracle bit for bit
+(history energy and magnetization to 1e-12 relative: the GPU sums per colour class in a
+different order). FP32: bitwise independence of batching and of run splitting, the
+history's E/N against the oracle's energy of the same spins (|d(E/N)| < 1e-3), and the
+observables against the oracle and closed forms within 4 standard errors.
+"""
+
+import numpy as np
+import pytest
+
+from conftest import binned
+
+import oracle
+import paper_1803_07030_gb300 as vg
+from paper_1803_07030_gb300 import vegas as vb
+from lattices import (chain_open, core_shell_particle, dimers, fcc_sphere, free_spins, nanoparticle_batch,
+                      random_graph, sc_periodic, triangles)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    vg.build()
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def ctx(samples, **kw):
+    kw.setdefault("stream", None)
+    return vg.Context(samples, **kw)
+
+
+def first_divergence(a, b):
+    d = np.argwhere(a != b)
+    return None if d.size == 0 else tuple(int(x) for x in d[0])
+
+
+def assert_history_close(h, hr, n_sites, rel=1e-12):
+    scale = np.maximum(np.abs(hr[..., 0]), 1.0)
+    assert np.all(np.abs(h[..., 0] - hr[..., 0]) <= rel * scale), np.max(np.abs(h[..., 0] - hr[..., 0]) / scale)
+    assert np.all(np.abs(h[..., 1:] - hr[..., 1:]) <= rel * n_sites)
+
+
+# --------------------------------------------------------------------------- FP64 bit identity
+
+def test_fp64_sc8_first_100_mcs_bitwise():
+    s = sc_periodic(8)
+    with ctx([s], precision=64, seed=1, accept_log_mcs=100) as c:
+        c.run([[3.0]], [[0.0]], 100)
+        ref = oracle.run(s, [[3.0]], [[0.0]], 100, seed=1, log_mcs=100)
+        alog = c.accept_log().reshape(100, 512)
+        assert first_divergence(alog, ref["accept_log"][0]) is None, first_divergence(alog, ref["accept_log"][0])
+        assert np.array_equal(c.spins(0), ref["spins"][0])
+        assert_history_close(c.history()[0], ref["history"][0], 512)
+        assert 0.3 < alog.mean() < 0.9
+
+
+def test_fp64_sc8_full_schedule_bitwise():
+    """The 8^3 ferromagnet, 30 temperatures 3.0 -> 0.1, 1000 MCS each."""
+    s = sc_periodic(8)
+    T = np.linspace(3.0, 0.1, 30)[None, :]
+    with ctx([s], precision=64, seed=1) as c:
+        c.run(T, np.zeros_like(T), 1000)
+        ref = oracle.run(s, T, np.zeros_like(T), 1000, seed=1)
+        S = c.spins(0)
+        d = first_divergence(S, ref["spins"][0])
+        assert d is None, f"first spin divergence at {d}"
+        h = c.history()[0]
+        assert_history_close(h, ref["history"][0], 512)
+        assert abs(h[-1, 0] - ref["history"][0, -1, 0]) <= 1e-12 * abs(ref["history"][0, -1, 0])
+
+
+def _packed_samples():
+    cs = core_shell_particle(seed=3, radius=5.0, core_radius=3.5)
+    rg = random_graph(60, 0.1, 4)
+    iso = free_spins(5, k_cub=0.7, spin_norm=1.3)
+    return [sc_periodic((10, 9, 11)), fcc_sphere(4.3), cs, rg, chain_open(37), iso, free_spins(1)]
+
+
+def test_fp64_packed_ragged_replicas_bitwise():
+    samples = _packed_samples()
+    R, base, mcs = 4, 5, 12
+    Tl = np.array([2.0, 1.0, 0.4])
+    Bl = np.array([0.3, -0.5, 1.0])
+    n_inst = len(samples) * R
+    T = np.stack([Tl * (1 + 0.1 * i) for i in range(n_inst)])
+    B = np.stack([Bl * (1 - 0.05 * i) for i in range(n_inst)])
+    with ctx(samples, precision=64, replicas=R, inst_base=base, seed=77) as c:
+        c.run(T, B, mcs)
+        H = c.history()
+        for si, s in enumerate(samples):
+            rows = slice(si * R, (si + 1) * R)
+            ref = oracle.run(s, T[rows], B[rows], mcs, seed=77, inst_base=base + si * R)
+            assert ref["err"] == 0
+            for r in range(R):
+                S = c.spins(si * R + r)
+                assert first_divergence(S, ref["spins"][r]) is None, (s.name, r, first_divergence(S, ref["spins"][r]))
+                assert_history_close(H[si * R + r], ref["history"][r], s.n_sites)
+
+
+def test_fp64_given_initial_state_and_set_spins():
+    s = random_graph(40, 0.15, 8)
+    rng = np.random.Generator(np.random.PCG64(2))
+    S0 = rng.normal(size=(40, 3))
+    s.init_spins = S0
+    with ctx([s], precision=64, seed=9) as c:
+        assert np.array_equal(c.spins(0), S0)
+        c.run([[1.1]], [[0.2]], 7)
+        ref = oracle.run(s, [[1.1]], [[0.2]], 7, seed=9, spins=S0[None])
+        assert np.array_equal(c.spins(0), ref["spins"][0])
+        c.set_spins(0, S0)
+        assert np.array_equal(c.spins(0), S0)
+
+
+# --------------------------------------------------------------------------- chain continuation
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_run_splitting_is_bitwise_invisible(precision):
+    s = fcc_sphere(3.9)
+    T = np.array([[2.5, 1.5, 0.7, 0.3]])
+    B = np.array([[0.1, 0.4, -0.2, 0.0]])
+    with ctx([s], precision=precision, seed=5) as a, ctx([s], precision=precision, seed=5) as b:
+        a.run(T, B, 9)
+        b.run(T[:, :1], B[:, :1], 9)
+        b.run(T[:, 1:3], B[:, 1:3], 9)
+        b.run(T[:, 3:], B[:, 3:], 9)
+        assert np.array_equal(a.spins(0), b.spins(0))
+        assert np.array_equal(a.history(), b.history())
+
+
+def test_graph_and_direct_launches_agree():
+    s = sc_periodic(6, k_uni=0.1)
+    with ctx([s], seed=3, graphs=True) as a, ctx([s], seed=3, graphs=False) as b, ctx([s], seed=3, timing=True) as t:
+        for c in (a, b, t):
+            c.run([[1.0, 0.5]], [[0.2, 0.3]], 11)
+        assert np.array_equal(a.spins(0), b.spins(0)) and np.array_equal(a.spins(0), t.spins(0))
+        assert np.array_equal(a.history(), b.history())
+        assert t.stats()["sweep_ms"] > 0.0
+
+
+# --------------------------------------------------------------------------- FP32 batching
+
+def test_fp32_replica_batch_equals_plain_runs():
+    s = sc_periodic(12, bimodal_seed=3)
+    R = 32
+    T = (0.1 * 20.0 ** (np.arange(R) / (R - 1.0)))[:, None]
+    with ctx([s], precision=32, replicas=R, seed=11) as c:
+        c.run(T, np.zeros_like(T), 30)
+        H = c.history()
+        for p in (0, 7, 31):
+            with ctx([s], precision=32, replicas=1, inst_base=p, seed=11) as q:
+                q.run(T[p:p + 1], np.zeros((1, 1)), 30)
+                assert np.array_equal(c.spins(p), q.spins(0)), p
+                np.testing.assert_allclose(H[p], q.history()[0], rtol=1e-12, atol=1e-9)
+
+
+def test_fp32_sample_batch_equals_single_sample_runs():
+    samples = nanoparticle_batch(6, seed=4, r_max=6.0)
+    T = np.linspace(0.3, 2.0, 6)[:, None]
+    with ctx(samples, precision=32, seed=2) as c:
+        c.run(T, np.full_like(T, 0.1), 25)
+        H = c.history()
+        for p in (0, 3, 5):
+            with ctx([samples[p]], precision=32, inst_base=p, seed=2) as q:
+                q.run(T[p:p + 1], np.full((1, 1), 0.1), 25)
+                assert np.array_equal(c.spins(p), q.spins(0))
+                np.testing.assert_allclose(H[p], q.history()[0], rtol=1e-12, atol=1e-9)
+
+
+# --------------------------------------------------------------------------- FP32 precision statement
+
+def _precision_case(samples, T, B, mcs, R=1):
+    worst = 0.0
+    with ctx(samples, precision=32, replicas=R, seed=21) as c:
+        for step in range(T.shape[1]):
+            c.run(T[:, step:step + 1], B[:, step:step + 1], mcs)
+            H = c.history()
+            for i in range(c.n_instances):
+                s = samples[i // R]
+                S = c.spins(i)
+                e_ref = oracle.energy(s, S, B[i, step]) / s.n_sites
+                worst = max(worst, abs(H[i, -1, 0] / s.n_sites - e_ref))
+                np.testing.assert_allclose(H[i, -1, 1:], S.sum(axis=0), rtol=0, atol=1e-5 * s.n_sites)
+                norms = np.linalg.norm(S, axis=1)
+                sn = s.param("spin_norm")
+                assert np.all(np.abs(norms - sn) < 1e-5 * sn)
+    return worst
+
+
+def test_fp32_history_energy_matches_oracle_energy_of_same_spins():
+    cases = [
+        ([sc_periodic(16, k_uni=0.05)], np.full((1, 3), 0.5), np.array([[2.0, 0.0, -2.0]]), 20, 1),
+        ([core_shell_particle(seed=1, radius=6.0, core_radius=4.5)], np.array([[3.0, 1.0, 0.1]]),
+         np.full((1, 3), 0.5), 20, 1),
+        (nanoparticle_batch(5, seed=7, r_max=7.0), np.full((5, 2), 0.8), np.zeros((5, 2)), 15, 1),
+        ([sc_periodic(10, bimodal_seed=5)], np.tile([[0.2, 1.0]], (8, 1)), np.zeros((8, 2)), 15, 8),
+        ([random_graph(300, 0.02, 3)], np.array([[1.5, 0.5]]), np.array([[0.7, -0.4]]), 15, 1),
+    ]
+    for samples, T, B, mcs, R in cases:
+        worst = _precision_case(samples, T, B, mcs, R)
+        assert worst < 1e-3, (samples[0].name, worst)
+        assert worst < 1e-5, (samples[0].name, worst)  # what FP32 spins with FP64 sums deliver
+
+
+# --------------------------------------------------------------------------- FP32 statistics
+
+def _series_stats(e, m, N, T):
+    """Binned means of e = E/N and m = |M|/N, jackknife C_v and chi over 20 bins."""
+    cut = e.shape[-1] // 5
+    e, m = e[..., cut:], m[..., cut:]
+    out = {}
+    for name, x in (("e", e), ("m", m)):
+        means = [binned(xi, cut=0.0) for xi in x]
+        out[name] = (np.mean([a for a, _ in means]), np.sqrt(np.sum([b ** 2 for _, b in means])) / len(means))
+    for name, x, pref in (("cv", e, N / T ** 2), ("chi", m, N / T)):
+        vals, errs = [], []
+        for xi in x:
+            k = (len(xi) // 20) * 20
+            bins = xi[len(xi) - k:].reshape(20, -1)
+            jk = []
+            for j in range(20):
+                rest = np.delete(bins, j, axis=0).reshape(-1)
+                jk.append(pref * (np.mean(rest ** 2) - np.mean(rest) ** 2))
+            jk = np.array(jk)
+            vals.append(pref * (np.mean(xi ** 2) - np.mean(xi) ** 2))
+            errs.append(np.sqrt(19.0 / 20.0 * np.sum((jk - jk.mean()) ** 2)))
+        out[name] = (np.mean(vals), np.sqrt(np.sum(np.square(errs))) / len(vals))
+    return out
+
+
+@pytest.mark.parametrize("T,B", [(0.9, 0.0), (1.4, 0.0), (2.5, 0.3)])
+def test_fp32_observables_match_oracle(T, B):
+    s = sc_periodic(8)
+    N, R, mcs = s.n_sites, 4, 4000
+    with ctx([s], precision=32, replicas=R, seed=31) as c:
+        c.run(np.full((R, 1), T), np.full((R, 1), B), mcs)
+        H = c.history()
+    ref = oracle.run(s, np.full((R, 1), T), np.full((R, 1), B), mcs, seed=32, n_threads=R)
+    Hr = ref["history"]
+    g = _series_stats(H[:, :, 0] / N, np.linalg.norm(H[:, :, 1:], axis=2) / N, N, T)
+    o = _series_stats(Hr[:, :, 0] / N, np.linalg.norm(Hr[:, :, 1:], axis=2) / N, N, T)
+    for k in ("e", "m", "cv", "chi"):
+        (a, sa), (b, sb) = g[k], o[k]
+        assert abs(a - b) < 4 * np.hypot(sa, sb), (k, a, sa, b, sb)
+    assert abs(g["e"][0] - o["e"][0]) < 1e-3 or abs(g["e"][0] - o["e"][0]) < 4 * np.hypot(g["e"][1], o["e"][1])
+
+
+def test_fp32_closed_forms():
+    """FP32 GPU path against the exact results used to pin the oracle."""
+    n = 4000
+    # Langevin with a tilted field axis, three fields at once (one instance each)
+    axis = np.array([1.0, 2.0, 2.0]) / 3.0
+    Bs = np.array([0.5, 2.0, 8.0])
+    with ctx([free_spins(n, field_axis=axis)], precision=32, replicas=4, seed=41) as c:
+        c.run(np.ones((4, 1)), np.append(Bs, 1.0)[:, None], 400)
+        H = c.history()
+    for k, B in enumerate(Bs):
+        m, se = binned(H[k, :, 1:] @ axis / n)
+        L = 1 / np.tanh(B) - 1 / B
+        assert abs(m - L) < 4 * se + 2e-5, (B, m, se, L)
+    # open chain, antiferromagnetic
+    N, R, beta = 64, 16, 2.0
+    with ctx([chain_open(N, J=-1.0)], precision=32, replicas=R, seed=42) as c:
+        c.run(np.full((R, 1), 1 / beta), np.zeros((R, 1)), 1500)
+        H = c.history()
+    u = 1 / np.tanh(-beta) + 1 / beta
+    U = (N - 1) * u
+    means = [binned(h) for h in H[:, :, 0]]
+    m = np.mean([a for a, _ in means])
+    se = np.sqrt(np.sum([b ** 2 for _, b in means])) / R
+    assert abs(m - U) < 4 * se, (m, se, U)
+    # frustrated three-spin ring (three colour classes)
+    P, T = 2000, 0.7
+    with ctx([triangles(P, J=-1.0)], precision=32, seed=43) as c:
+        c.run([[T]], [[0.0]], 500)
+        H = c.history()
+    ref = oracle.run(triangles(P, J=-1.0), [[T]], [[0.0]], 500, seed=44)
+    a, sa = binned(H[0, :, 0] / P)
+    b, sb = binned(ref["history"][0, :, 0] / P)
+    assert abs(a - b) < 4 * np.hypot(sa, sb)
+
+
+def test_fp32_dimer_detailed_balance():
+    P, J, T = 20000, 1.0, 0.5
+    with ctx([dimers(P, J=J)], precision=32, seed=45) as c:
+        c.run([[T]], [[0.0]], 200)
+        S = c.spins(0)
+    from scipy import stats
+
+    cth = np.einsum("ij,ij->i", S[0::2], S[1::2])
+    K = J / T
+    edges = np.linspace(-1, 1, 21)
+    obs, _ = np.histogram(np.clip(cth, -1, 1), bins=edges)
+    p = (np.exp(K * edges[1:]) - np.exp(K * edges[:-1])) / (np.exp(K) - np.exp(-K))
+    chi2 = float(((obs - P * p) ** 2 / (P * p)).sum())
+    assert chi2 < stats.chi2.ppf(1 - 1e-4, 19), chi2
+
+
+# --------------------------------------------------------------------------- errors and edge cases
+
+def test_errors_leave_context_usable():
+    s = sc_periodic(4)
+    with ctx([s], seed=1) as c:
+        for T in (0.0, -1.0, np.nan, np.inf):
+            with pytest.raises(vb.VegasError) as e:
+                c.run([[T]], [[0.0]], 1)
+            assert e.value.status == vb.EINVAL
+        with pytest.raises(vb.VegasError):
+            c.run([[1.0]], [[np.nan]], 1)
+        with pytest.raises(vb.VegasError):
+            vb.vegas_get_spins(c.ptr, 5, 64)
+        with pytest.raises(vb.VegasError):
+            c.set_spins(0, np.full((64, 3), np.nan))
+        c.run([[1.0]], [[0.0]], 0)
+        assert c.history().shape == (1, 0, 4)
+        c.run([[1.0]], [[0.0]], 3)
+        assert c.history().shape == (1, 3, 4)
+        st = c.stats()
+        assert st["mcs_done"] == 3 and st["device_error"] == 0 and st["records"] == 3
+
+
+def test_extreme_temperatures():
+    s = sc_periodic(6)
+    with ctx([s], precision=32, replicas=2, seed=3) as c:
+        up = np.tile([0, 0, 1.0], (s.n_sites, 1))
+        c.set_spins(0, up)
+        c.set_spins(1, up)
+        c.run(np.array([[1e-6], [1e6]]), np.zeros((2, 1)), 20)
+        H = c.history()
+    assert np.all(H[0, :, 0] / s.n_sites < -2.9999)  # only downhill moves at T -> 0
+    assert abs(H[1, -5:, 0].mean() / s.n_sites) < 0.5  # near-random at T -> infinity
