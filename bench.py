@@ -43,7 +43,7 @@ KERNEL_SOURCE = os.path.join(ROOT, "paper_1803_07030_gb300", "csrc", "vegas_kern
 
 def workload_desc(mcs):
     return {
-        "workload": f"sg256x32: 32 temperature replicas (T 0.1->2.0 geometric) of a {L_SIDE}^3 periodic sc +-J "
+        "workload": f"sg{L_SIDE}x32: 32 temperature replicas (T 0.1->2.0 geometric) of a {L_SIDE}^3 periodic sc +-J "
                     f"spin glass, random moves, {mcs} MCS per step, FP32 spins / FP64 history",
         "sites_per_replica": L_SIDE ** 3,
         "replicas_per_gpu": REPLICAS,
@@ -248,6 +248,14 @@ def run_ours(args):
     achieved = BYTES_PER_ATTEMPT * attempts_per_launch / (sweep_ms / 1000.0) / 1e9
     traffic = profiled_traffic()
 
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms / args.steps,
+                              "config": workload_desc(mcs), "quick": True, "avg_launch_ms": sweep_ms,
+                              "achieved_gbs": achieved, "gpu_launches": launches}), flush=True)
+        ctx.close()
+        return 0
+
     # end to end through the public API with host buffers: schedule in, history out
     torch.cuda.synchronize()
     te = time.perf_counter()
@@ -310,13 +318,18 @@ def run_ours(args):
 
 
 def main():
+    global L_SIDE
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--mcs", type=int, default=MCS)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=L_SIDE, help="lattice side (smaller cases for ncu captures)")
+    ap.add_argument("--quick", action="store_true",
+                    help="time the sweep only (no e2e, plain-path or CPU-baseline legs); for profiling runs")
     args = ap.parse_args()
+    L_SIDE = args.side
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -92,6 +92,8 @@ typedef struct {
                                first accept_log_mcs MCS (debugging and parity). Default 0. */
     int32_t timing;         /* 1: time every sweep launch with CUDA events. Default 0. */
     int32_t graphs;         /* 1: replay the per-MCS launches as a CUDA graph. Default 1. */
+    int32_t max_blocks;     /* > 0: at most this many thread blocks per sweep launch (tests,
+                               tuning); 0 = as many as fit on the device. Default 0. */
 } vegas_options;
 
 typedef struct {
@@ -102,7 +104,8 @@ typedef struct {
     int64_t n_edges;            /* directed links over all samples */
     int64_t records;            /* history records per instance so far */
     uint32_t mcs_done;          /* global MCS counter t */
-    uint32_t device_error;      /* error bits set by kernels (1 NaN dE, 2 sampler cap) */
+    uint32_t device_error;      /* error bits set by kernels (1 NaN dE, 2 sampler cap,
+                                   4 index check failed in a debug build) */
     int64_t kernel_launches;    /* kernels launched by the library so far */
     int64_t sweep_launches;     /* colour-pass (or resident) sweep launches so far */
     double sweep_ms;            /* summed event time of sweep launches (timing = 1) */
@@ -121,7 +124,7 @@ void vegas_default_options(vegas_options *opt);
  * Sec. III.B "an initial state is chosen"). opt may be NULL (defaults).
  * Returns VEGAS_EINVAL for: n_samples < 1; a NULL required array; row_ptr not starting
  * at 0, decreasing, or not ending at n_edges; col out of range; a self-link; a duplicate
- * link; J not symmetric; a non-finite parameter; spin_norm <= 0; a zero axis; a colouring
+ * link; J not symmetric; a non-finite parameter; spin_norm <= 0; a colouring
  * that is not proper; bad options. On failure *out is NULL.
  */
 vegas_status vegas_create(const vegas_sample *samples, int32_t n_samples, const vegas_options *opt,

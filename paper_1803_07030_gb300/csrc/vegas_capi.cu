@@ -180,6 +180,7 @@ extern "C" void vegas_default_options(vegas_options *o) {
     o->accept_log_mcs = 0;
     o->timing = 0;
     o->graphs = 1;
+    o->max_blocks = 0;
 }
 
 extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samples, const vegas_options *opt,
@@ -193,7 +194,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     if (o.precision != 32 && o.precision != 64) return fail(nullptr, VEGAS_EINVAL, "precision must be 32 or 64");
     if (o.replicas < 1 || o.replicas > 32 || (o.replicas & (o.replicas - 1)))
         return fail(nullptr, VEGAS_EINVAL, "replicas must be 1, 2, 4, 8, 16 or 32");
-    if (o.accept_log_mcs < 0 || o.inst_base < 0) return fail(nullptr, VEGAS_EINVAL, "negative option");
+    if (o.accept_log_mcs < 0 || o.inst_base < 0 || o.max_blocks < 0) return fail(nullptr, VEGAS_EINVAL, "negative option");
     if (o.variant < -1 || o.variant > 1) return fail(nullptr, VEGAS_EINVAL, "variant must be -1, 0 or 1");
     if ((int64_t)o.inst_base + (int64_t)n_samples * o.replicas > (int64_t)UINT32_MAX)
         return fail(nullptr, VEGAS_EINVAL, "instance ids exceed 32 bits");
@@ -208,7 +209,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         n_sites += L[(size_t)s].n;
         n_edges += L[(size_t)s].n_edges + (L[(size_t)s].n_edges & 1);  // keep every sample 16-byte aligned
     }
-    if (n_sites * o.replicas > ((int64_t)1 << 40) || n_sites >= INT32_MAX || n_edges >= INT32_MAX)
+    if (n_sites * o.replicas > ((int64_t)1 << 40) || n_sites > INT32_MAX - (1 << 24) || n_edges >= INT32_MAX)
         return fail(nullptr, VEGAS_EINVAL, "too many sites or links for one context");
 
     vegas_ctx *c = new (std::nothrow) vegas_ctx();
@@ -368,7 +369,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     DALLOC(c->d_norm, sizeof(double) * (size_t)n_sites);
     DALLOC(c->d_edges, (p64 ? sizeof(Edge64) : sizeof(int2)) * (size_t)std::max<int64_t>(n_edges, 1));
     DALLOC(c->d_run, sizeof(RunState));
-    DALLOC(c->d_err, sizeof(uint32_t));
+    DALLOC(c->d_err, 4 * sizeof(uint32_t));
     H2D(c->d_orig, h_orig.data(), sizeof(int32_t) * (size_t)n_sites);
     H2D(c->d_rowptr, h_rowptr.data(), sizeof(int64_t) * ((size_t)n_sites + 1));
     H2D(c->d_norm, h_norm.data(), sizeof(double) * (size_t)n_sites);
@@ -387,7 +388,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         H2D(c->d_p1, p64 ? (const void *)h_p1d.data() : (const void *)h_p1f.data(), pv * (size_t)n_sites);
         H2D(c->d_pk, p64 ? (const void *)h_pkd.data() : (const void *)h_pkf.data(), ps * (size_t)n_sites);
     }
-    if (cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), c->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(c->d_err, 0, 4 * sizeof(uint32_t), c->stream) != cudaSuccess) {
         c->err = "memset failed";
         return bail(VEGAS_ECUDA);
     }
@@ -437,6 +438,8 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
             a.alog_base = alog_base;
             a.alog_mcs = (uint32_t)o.accept_log_mcs;
             a.deg = si.uniform_degree;
+            a.n_sites_total = (int32_t)n_sites;
+            a.n_edges_total = n_edges;
             a.lower_mode = si.lower_mode[(size_t)col];
             a.params_mode = si.uniform_params ? (si.has_anisotropy ? 1 : 0) : 2;
             a.u64 = si.u;
@@ -444,7 +447,8 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
                                  (float)si.u.ey, (float)si.u.ez, (float)si.u.k,  (float)si.u.kc};
             const int64_t work = (int64_t)nc * R;
             const int64_t need = (work + kThreads - 1) / kThreads;
-            const int64_t cap = (int64_t)c->sm_count * pass_blocks_per_sm(c->precision, a);
+            int64_t cap = (int64_t)c->sm_count * pass_blocks_per_sm(c->precision, a);
+            if (o.max_blocks > 0) cap = std::min<int64_t>(cap, o.max_blocks);
             pl.grid = (int)std::max<int64_t>(1, std::min(need, cap));
             a.partial = nullptr;  // set below, once the slot buffer exists
             si.slot_count += pl.grid;
@@ -621,8 +625,9 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
     for (auto &x : ev) cudaEventDestroy(x);
     c->last_run_ms = run_ms;
     c->sweep_ms += sweep_ms;
-    uint32_t derr = 0;
-    CK(c, cudaMemcpy(&derr, c->d_err, sizeof derr, cudaMemcpyDeviceToHost));
+    uint32_t derr4[4] = {0, 0, 0, 0};
+    CK(c, cudaMemcpy(derr4, c->d_err, sizeof derr4, cudaMemcpyDeviceToHost));
+    const uint32_t derr = derr4[0];
     // history: device [rec][inst][4] -> host per instance, appended
     std::vector<double> h(hneed);
     CK(c, cudaMemcpy(h.data(), c->d_hist, sizeof(double) * hneed, cudaMemcpyDeviceToHost));
@@ -637,8 +642,11 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
     c->t += (uint32_t)nrec;
     c->device_error |= derr;
     if (derr) {
-        char msg[160];
-        std::snprintf(msg, sizeof msg, "device error flags 0x%x (1: NaN energy change, 2: sphere sampler cap)", derr);
+        char msg[200];
+        std::snprintf(msg, sizeof msg,
+                      "device error flags 0x%x (1: NaN energy change, 2: sphere sampler cap, 4: index check; "
+                      "check code %u, value %u)",
+                      derr, derr4[1], derr4[2]);
         return fail(c, VEGAS_EDEVICE, msg);
     }
     return VEGAS_OK;

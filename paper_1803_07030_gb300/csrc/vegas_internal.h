@@ -23,6 +23,7 @@ constexpr uint32_t kInitT = 0xFFFFFFFFu;
 // Error bits set by kernels in the device error word.
 constexpr uint32_t kErrNaN = 1u;
 constexpr uint32_t kErrSphere = 2u;
+constexpr uint32_t kErrIndex = 4u;  // debug builds: an index or alignment check failed
 
 // ------------------------------------------------------------------ host-side sample
 
@@ -110,6 +111,8 @@ struct PassArgs {
     int64_t alog_base;         // offset of replica 0 of this sample inside one MCS
     uint32_t alog_mcs;
     int32_t deg;               // uniform degree or 0
+    int32_t n_sites_total;     // sites over all samples (debug index checks)
+    int64_t n_edges_total;
     int32_t lower_mode;        // 0: no link to a lower colour, 1: every link, 2: test each
     int32_t params_mode;       // 0: uniform, no anisotropy; 1: uniform; 2: per site
     SiteParams32 u32;

@@ -205,17 +205,108 @@ __global__ void __launch_bounds__(kThreads) pass64_kernel(const PassArgs a) {
     block_partials(acc4, R, a.partial + (int64_t)blockIdx.x * R * 4);
 }
 
-// ------------------------------------------------------------------ FP32 colour pass
-// DEG: 6 = every row has six links (loaded as three 16-byte words), 0 = read row_ptr.
+// ------------------------------------------------------------------ FP32 attempt
+// One Metropolis attempt in FP32, written with explicit roundings (fmaf where a fused
+// multiply-add is meant, __fmul_rn / __fadd_rn elsewhere) so that every kernel that calls
+// it computes bit-identical results for the same inputs, whatever the surrounding code.
+// h is the exchange field sum_j J_ij S_j (row order), l its part over lower colours.
+struct Site32 {
+    float nx, ny, nz, sn, ex, ey, ez, k, kc;
+};
+
+template <int PM, int LM>
+__device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, float hz, float lx, float ly, float lz,
+                                          const Site32 &p, float beta, float B, uint4 rw, float4 &Sn, bool &acc,
+                                          float &e_i, bool &nan_seen) {
+    const float Hx = fmaf(B, p.nx, hx), Hy = fmaf(B, p.ny, hy), Hz = fmaf(B, p.nz, hz);
+    // trial: z uniform in (-1, 1), azimuth uniform in (-pi, pi): by Archimedes' theorem the
+    // point (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z) is uniform on the sphere
+    const float z = fmaf((float)(rw.x >> 8), 0x1p-23f, -1.0f + 0x1p-24f);
+    const float phi = __fmul_rn(fmaf((float)(rw.y >> 8), 0x1p-23f, -1.0f + 0x1p-24f), 3.14159265358979f);
+    float sphi, cphi;
+    __sincosf(phi, &sphi, &cphi);
+    const float rho2 = fmaf(-z, z, 1.0f);
+    const float rho = __fmul_rn(rho2, rsqrtf(rho2));
+    const float px = __fmul_rn(p.sn, __fmul_rn(rho, cphi));
+    const float py = __fmul_rn(p.sn, __fmul_rn(rho, sphi));
+    const float pz = __fmul_rn(p.sn, z);
+    const float dx = __fsub_rn(px, Si.x), dy = __fsub_rn(py, Si.y), dz = __fsub_rn(pz, Si.z);
+    float dE = -fmaf(dx, Hx, fmaf(dy, Hy, __fmul_rn(dz, Hz)));
+    if (PM != 0) {
+        const float pn = fmaf(px, p.ex, fmaf(py, p.ey, __fmul_rn(pz, p.ez)));
+        const float po = fmaf(Si.x, p.ex, fmaf(Si.y, p.ey, __fmul_rn(Si.z, p.ez)));
+        dE = fmaf(-p.k, __fmul_rn(__fsub_rn(pn, po), __fadd_rn(pn, po)), dE);
+        dE = fmaf(-p.kc, __fsub_rn(cub32(px, py, pz), cub32(Si.x, Si.y, Si.z)), dE);
+    }
+    // Metropolis acceptance (Eq. 4) with the third word as the uniform; NaN rejects
+    const float u = __fmul_rn((float)(rw.z >> 8), 0x1p-24f);
+    acc = (dE <= 0.f) || (u < __expf(__fmul_rn(-beta, dE)));
+    nan_seen = (dE != dE);
+    if (nan_seen) acc = false;
+    const float qx = acc ? px : Si.x, qy = acc ? py : Si.y, qz = acc ? pz : Si.z;
+    Sn = make_float4(qx, qy, qz, 0.f);
+    // this site's share of the energy after the MCS: -S.l - B S.n - k (S.e)^2 - kc cub(S)
+    float e = __fmul_rn(-B, fmaf(qx, p.nx, fmaf(qy, p.ny, __fmul_rn(qz, p.nz))));
+    if (LM != 0) e = __fsub_rn(e, fmaf(qx, lx, fmaf(qy, ly, __fmul_rn(qz, lz))));
+    if (PM != 0) {
+        const float pe = fmaf(qx, p.ex, fmaf(qy, p.ey, __fmul_rn(qz, p.ez)));
+        e = __fsub_rn(e, fmaf(__fmul_rn(p.k, pe), pe, __fmul_rn(p.kc, cub32(qx, qy, qz))));
+    }
+    e_i = e;
+}
+
+// Short FP32 runs of the per-thread sums, then FP64.
+struct Acc32 {
+    double d[4] = {0.0, 0.0, 0.0, 0.0};
+    float f[4] = {0.f, 0.f, 0.f, 0.f};
+    int n = 0;
+    __device__ __forceinline__ void add(float e, float4 q) {
+        f[0] = __fadd_rn(f[0], e);
+        f[1] = __fadd_rn(f[1], q.x);
+        f[2] = __fadd_rn(f[2], q.y);
+        f[3] = __fadd_rn(f[3], q.z);
+        if (++n == 16) flush();
+    }
+    __device__ __forceinline__ void flush() {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            d[q] += (double)f[q];
+            f[q] = 0.f;
+        }
+        n = 0;
+    }
+};
+
+__device__ __forceinline__ void link32(const float4 Sj, float J, bool lower, float &hx, float &hy, float &hz,
+                                       float &lx, float &ly, float &lz) {
+    hx = fmaf(J, Sj.x, hx);
+    hy = fmaf(J, Sj.y, hy);
+    hz = fmaf(J, Sj.z, hz);
+    if (lower) {
+        lx = fmaf(J, Sj.x, lx);
+        ly = fmaf(J, Sj.y, ly);
+        lz = fmaf(J, Sj.z, lz);
+    }
+}
+
+__device__ __forceinline__ Site32 site_params32(const PassArgs &a, int PMv, int g) {
+    Site32 p{a.u32.nx, a.u32.ny, a.u32.nz, a.u32.s, a.u32.ex, a.u32.ey, a.u32.ez, a.u32.k, a.u32.kc};
+    if (PMv == 2) {
+        const float4 p0 = __ldg((const float4 *)a.p0 + g), p1 = __ldg((const float4 *)a.p1 + g);
+        p = Site32{p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, __ldg((const float *)a.pk + g)};
+    }
+    return p;
+}
+
+// ------------------------------------------------------------------ FP32 colour pass (direct)
+// Any row length: reads row_ptr and gathers neighbours with plain loads.
 // PM: params_mode (0 uniform without anisotropy, 1 uniform, 2 per site).
 // LM: lower_mode (0 no lower links, 1 all links lower, 2 test each link).
-
-template <int DEG, int PM, int LM>
+template <int PM, int LM>
 __global__ void __launch_bounds__(kThreads) pass32_kernel(const PassArgs a) {
     const RunState *rs = a.run;
     const uint32_t t = rs->t;
     const uint32_t step = rs->rec / rs->mcs;
-    const double *sched = rs->sched;
     const int R = 1 << a.log2R;
     const int64_t n_work = (int64_t)(a.g_end - a.g_begin) << a.log2R;
     float4 *S = (float4 *)a.spins;
@@ -226,106 +317,209 @@ __global__ void __launch_bounds__(kThreads) pass32_kernel(const PassArgs a) {
     // a thread always serves the same replica (the stride is a multiple of 32 >= R)
     const int r = (int)(w0 & (R - 1));
     const uint32_t inst = (uint32_t)(a.inst0 + r);
-    const double *sc = sched + ((int64_t)step * a.n_inst + a.inst_local0 + r) * 2;
+    const double *sc = rs->sched + ((int64_t)step * a.n_inst + a.inst_local0 + r) * 2;
     const float beta = (float)sc[0], B = (float)sc[1];
-    float nx = a.u32.nx, ny = a.u32.ny, nz = a.u32.nz, sn = a.u32.s;
-    float ex = a.u32.ex, ey = a.u32.ey, ez = a.u32.ez, k = a.u32.k, kc = a.u32.kc;
-    double acc4[4] = {0.0, 0.0, 0.0, 0.0};
-    float f4[4] = {0.f, 0.f, 0.f, 0.f};
-    int cnt = 0;
+    Acc32 acc;
     for (int64_t w = w0; w < n_work; w += stride) {
         const int g = a.g_begin + (int)(w >> a.log2R);
         const uint32_t orig = (uint32_t)__ldg(a.orig + g);
-        if (PM == 2) {
-            const float4 p0 = __ldg((const float4 *)a.p0 + g), p1 = __ldg((const float4 *)a.p1 + g);
-            nx = p0.x; ny = p0.y; nz = p0.z; sn = p0.w;
-            ex = p1.x; ey = p1.y; ez = p1.z; k = p1.w;
-            kc = __ldg((const float *)a.pk + g);
-        }
+        const Site32 p = site_params32(a, PM, g);
         const int64_t si = (int64_t)g * R + r;
         const float4 Si = S[si];
         float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-        auto link = [&](int2 ed) {
-            const float J = __int_as_float(ed.y);
-            const float4 Sj = __ldg(S + (int64_t)ed.x * R + r);
-            hx = fmaf(J, Sj.x, hx);
-            hy = fmaf(J, Sj.y, hy);
-            hz = fmaf(J, Sj.z, hz);
-            if (LM == 2 && ed.x < a.lower_end) {
-                lx = fmaf(J, Sj.x, lx);
-                ly = fmaf(J, Sj.y, ly);
-                lz = fmaf(J, Sj.z, lz);
-            }
-        };
-        if (DEG == 6) {
-            const int4 *row = (const int4 *)(E + a.edge_base + (int64_t)(g - a.site_off) * 6);
-            const int4 q0 = __ldg(row), q1 = __ldg(row + 1), q2 = __ldg(row + 2);
-            link(make_int2(q0.x, q0.y));
-            link(make_int2(q0.z, q0.w));
-            link(make_int2(q1.x, q1.y));
-            link(make_int2(q1.z, q1.w));
-            link(make_int2(q2.x, q2.y));
-            link(make_int2(q2.z, q2.w));
-        } else {
-            const int64_t e0 = __ldg(a.row_ptr + g), e1 = __ldg(a.row_ptr + g + 1);
-            for (int64_t e = e0; e < e1; ++e) link(__ldg(E + e));
+        const int64_t e0 = __ldg(a.row_ptr + g), e1 = __ldg(a.row_ptr + g + 1);
+        for (int64_t e = e0; e < e1; ++e) {
+            const int2 ed = __ldg(E + e);
+            link32(__ldg(S + (int64_t)ed.x * R + r), __int_as_float(ed.y), LM == 2 && ed.x < a.lower_end, hx, hy,
+                   hz, lx, ly, lz);
         }
         if (LM == 1) {
             lx = hx;
             ly = hy;
             lz = hz;
         }
-        const float Hx = fmaf(B, nx, hx), Hy = fmaf(B, ny, hy), Hz = fmaf(B, nz, hz);
-        // trial: z uniform in (-1, 1), azimuth uniform in (-pi, pi) (Archimedes' theorem
-        // makes the point uniform on the sphere); third word: acceptance uniform
         const uint4 rw = philox10(make_uint4(orig, t, inst, kPurposeTrial32), k0, k1);
-        const float z = fmaf((float)(rw.x >> 8), 0x1p-23f, -1.0f + 0x1p-24f);
-        const float phi = fmaf((float)(rw.y >> 8), 0x1p-23f, -1.0f + 0x1p-24f) * 3.14159265358979f;
-        float sphi, cphi;
-        __sincosf(phi, &sphi, &cphi);
-        const float rho2 = fmaf(-z, z, 1.0f);
-        const float rho = rho2 * rsqrtf(rho2);
-        const float px = sn * (rho * cphi), py = sn * (rho * sphi), pz = sn * z;
-        const float dx = px - Si.x, dy = py - Si.y, dz = pz - Si.z;
-        float dE = -fmaf(dx, Hx, fmaf(dy, Hy, dz * Hz));
-        if (PM != 0) {
-            const float pn = fmaf(px, ex, fmaf(py, ey, pz * ez));
-            const float po = fmaf(Si.x, ex, fmaf(Si.y, ey, Si.z * ez));
-            dE = fmaf(-k, (pn - po) * (pn + po), dE);
-            dE = fmaf(-kc, cub32(px, py, pz) - cub32(Si.x, Si.y, Si.z), dE);
-        }
-        const float uacc = (float)(rw.z >> 8) * 0x1p-24f;
-        bool acc = (dE <= 0.f) || (uacc < __expf(-beta * dE));
-        if (dE != dE) {
-            atomicOr(a.err, kErrNaN);
-            acc = false;
-        }
-        if (acc) S[si] = make_float4(px, py, pz, 0.f);
+        float4 Sn;
+        bool ok, bad;
+        float e_i;
+        attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, rw, Sn, ok, e_i, bad);
+        if (bad) atomicOr(a.err, kErrNaN);
+        if (ok) S[si] = Sn;
         if (a.alog && t < a.alog_mcs)
-            a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = acc ? 1 : 0;
-        const float qx = acc ? px : Si.x, qy = acc ? py : Si.y, qz = acc ? pz : Si.z;
-        float e_i = -B * fmaf(qx, nx, fmaf(qy, ny, qz * nz));
-        if (LM != 0) e_i -= fmaf(qx, lx, fmaf(qy, ly, qz * lz));
-        if (PM != 0) {
-            const float pe = fmaf(qx, ex, fmaf(qy, ey, qz * ez));
-            e_i -= fmaf(k * pe, pe, kc * cub32(qx, qy, qz));
-        }
-        f4[0] += e_i;
-        f4[1] += qx;
-        f4[2] += qy;
-        f4[3] += qz;
-        if (++cnt == 16) {  // short FP32 runs, FP64 beyond
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                acc4[q] += (double)f4[q];
-                f4[q] = 0.f;
-            }
-            cnt = 0;
-        }
+            a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
+        acc.add(e_i, Sn);
     }
+    acc.flush();
+    block_partials(acc.d, R, a.partial + (int64_t)blockIdx.x * R * 4);
+}
+
+// ------------------------------------------------------------------ FP32 colour pass (staged)
+// Rows of exactly DEG links. Each warp walks its share of the class in "groups" of 32
+// work items (32/R sites x R replicas) and keeps a software pipeline in shared memory:
+// the links and caller ids of group k+2D and the neighbour and own spin rows of group k+D
+// are copied with cp.async while group k is computed, so DRAM latency overlaps compute
+// instead of stalling the warp. Group k's rows are complete once all but the last D-1
+// committed copy groups have landed (cp.async.wait_group D-1).
+__device__ __forceinline__ void cp16(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp4(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Bytes of shared memory per warp for the staged kernel.
+__host__ __device__ constexpr int staged_rows_bytes(int deg, int D) { return D * (deg + 1) * 32 * 16; }
+__host__ __device__ inline int staged_slot_bytes(int deg, int spg) {
+    return ((spg * deg * 8 + 15) / 16) * 16 + ((spg * 4 + 15) / 16) * 16;
+}
+__host__ __device__ inline int staged_warp_bytes(int deg, int D, int spg) {
+    return staged_rows_bytes(deg, D) + 2 * D * staged_slot_bytes(deg, spg);
+}
+
+// Debug builds (VEGAS_DEBUG_CHECKS) check every staged copy: a failed check sets
+// kErrIndex, records a code and a value, and skips the access.
+#ifdef VEGAS_DEBUG_CHECKS
+#define VEGAS_CHECK(cond, code, val)                   \
+    if (!(cond)) {                                     \
+        atomicOr(a.err, kErrIndex);                    \
+        atomicCAS(a.err + 1, 0u, (uint32_t)(code));    \
+        a.err[2] = (uint32_t)(val);                    \
+        return;                                        \
+    }
+#else
+#define VEGAS_CHECK(cond, code, val)
+#endif
+
+template <int DEG, int PM, int LM, int D>
+__global__ void __launch_bounds__(kThreads) pass32_staged(const PassArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const RunState *rs_ = a.run;
+    const uint32_t t = rs_->t;
+    const uint32_t step_idx = rs_->rec / rs_->mcs;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int log2R = a.log2R, R = 1 << log2R, spg = 32 >> log2R;
+    const int r = lane & (R - 1), my = lane >> log2R;  // replica, site within the group
+    const int slot_bytes = staged_slot_bytes(DEG, spg);
+    const int edge_pad = ((spg * DEG * 8 + 15) / 16) * 16;
+    unsigned char *wbase = smem + (size_t)warp * staged_warp_bytes(DEG, D, spg);
+    float4 *rows = (float4 *)wbase;                            // [D][DEG+1][32]
+    unsigned char *slots = wbase + staged_rows_bytes(DEG, D);  // [2D][links | caller ids]
+    float4 *S = (float4 *)a.spins;
+    const float4 *Sr = S + r;
+    const int2 *E = (const int2 *)a.edges;
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    const uint32_t inst = (uint32_t)(a.inst0 + r);
+    const double *sc = rs_->sched + ((int64_t)step_idx * a.n_inst + a.inst_local0 + r) * 2;
+    const float beta = (float)sc[0], B = (float)sc[1];
+    const int g_end = a.g_end;
+    const int W = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int step = gridDim.x * (blockDim.x >> 5) * spg;  // sites between this warp's groups
+
+    auto issue_links = [&](int sbase, int slot) {  // links and caller ids of the group at sbase
+        if (sbase >= g_end) return;
+        const int ns = min(spg, g_end - sbase);
+        unsigned char *dst = slots + slot * slot_bytes;
+        const unsigned char *src = (const unsigned char *)(E + a.edge_base + (int64_t)(sbase - a.site_off) * DEG);
+        const int nch = ns * (DEG * 8 / 16);
+        VEGAS_CHECK(sbase >= a.g_begin && slot >= 0 && slot < 2 * D, 1, sbase);
+        VEGAS_CHECK(a.edge_base + (int64_t)(sbase - a.site_off) * DEG + (int64_t)ns * DEG <= a.n_edges_total, 2, sbase);
+        VEGAS_CHECK(((uintptr_t)src & 15) == 0 && ((uintptr_t)dst & 15) == 0, 3, sbase);
+        VEGAS_CHECK(sbase + ns <= a.n_sites_total, 4, sbase);
+        for (int c = lane; c < nch; c += 32) cp16(dst + 16 * c, src + 16 * c);
+        if (lane < ns) cp4(dst + edge_pad + 4 * lane, a.orig + sbase + lane);
+    };
+    auto issue_rows = [&](int sbase, int lslot, int rslot) {  // rows of the group at sbase
+        const int g = sbase + my;
+        if (g >= g_end) return;
+        const int4 *lk = (const int4 *)(slots + lslot * slot_bytes) + my * (DEG / 2);
+        float4 *dst = rows + rslot * (DEG + 1) * 32 + lane;
+        VEGAS_CHECK(lslot >= 0 && lslot < 2 * D && rslot >= 0 && rslot < D, 5, lslot * 16 + rslot);
+        VEGAS_CHECK(g < a.n_sites_total, 6, g);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc4[q] += (double)f4[q];
-    block_partials(acc4, R, a.partial + (int64_t)blockIdx.x * R * 4);
+        for (int j = 0; j < DEG / 2; ++j) {
+            const int4 q = lk[j];
+            VEGAS_CHECK(q.x >= 0 && q.x < a.n_sites_total && q.z >= 0 && q.z < a.n_sites_total, 7, q.x);
+            cp16(dst + (2 * j) * 32, Sr + ((int64_t)q.x << log2R));
+            cp16(dst + (2 * j + 1) * 32, Sr + ((int64_t)q.z << log2R));
+        }
+        cp16(dst + DEG * 32, Sr + ((int64_t)g << log2R));
+    };
+
+    int s0 = a.g_begin + W * spg;  // first site of the current group
+    for (int k = 0; k < 2 * D; ++k) issue_links(s0 + k * step, k);
+    cp_commit();
+    cp_wait<0>();
+    __syncwarp();
+    for (int k = 0; k < D; ++k) {
+        issue_rows(s0 + k * step, k, k);
+        cp_commit();
+    }
+    int ls = 0, la = D, rsl = 0;  // links slot of this group, of the group D ahead; rows slot
+    Acc32 acc;
+    for (; s0 < g_end; s0 += step) {
+        cp_wait<D - 1>();
+        __syncwarp();
+        const int g = s0 + my;
+        if (g < g_end) {
+            const unsigned char *slot = slots + ls * slot_bytes;
+            const int4 *lk = (const int4 *)slot + my * (DEG / 2);
+            const float4 *row = rows + rsl * (DEG + 1) * 32 + lane;
+            const uint32_t orig = ((const uint32_t *)(slot + edge_pad))[my];
+            bool skip = false;
+#ifdef VEGAS_DEBUG_CHECKS
+            if (orig >= (uint32_t)a.n_sample_sites || g >= a.n_sites_total) {
+                atomicOr(a.err, kErrIndex);
+                atomicCAS(a.err + 1, 0u, 8u);
+                a.err[2] = orig;
+                skip = true;
+            }
+#endif
+            if (!skip) {
+            const Site32 p = site_params32(a, PM, g);
+            float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+#pragma unroll
+            for (int j = 0; j < DEG / 2; ++j) {
+                const int4 q = lk[j];
+                link32(row[(2 * j) * 32], __int_as_float(q.y), LM == 2 && q.x < a.lower_end, hx, hy, hz, lx, ly, lz);
+                link32(row[(2 * j + 1) * 32], __int_as_float(q.w), LM == 2 && q.z < a.lower_end, hx, hy, hz, lx, ly,
+                       lz);
+            }
+            if (LM == 1) {
+                lx = hx;
+                ly = hy;
+                lz = hz;
+            }
+            const float4 Si = row[DEG * 32];
+            const uint4 rw = philox10(make_uint4(orig, t, inst, kPurposeTrial32), k0, k1);
+            float4 Sn;
+            bool ok, bad;
+            float e_i;
+            attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, rw, Sn, ok, e_i, bad);
+            if (bad) atomicOr(a.err, kErrNaN);
+            if (ok) S[((int64_t)g << log2R) + r] = Sn;
+            if (a.alog && t < a.alog_mcs)
+                a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
+            acc.add(e_i, Sn);
+            }
+        }
+        __syncwarp();
+        issue_links(s0 + 2 * D * step, ls);
+        issue_rows(s0 + D * step, la, rsl);
+        cp_commit();
+        ls = (ls + 1 == 2 * D) ? 0 : ls + 1;
+        la = (la + 1 == 2 * D) ? 0 : la + 1;
+        rsl = (rsl + 1 == D) ? 0 : rsl + 1;
+    }
+    cp_wait<0>();
+    acc.flush();
+    block_partials(acc.d, R, a.partial + (int64_t)blockIdx.x * R * 4);
 }
 
 // ------------------------------------------------------------------ per-MCS reduction
@@ -460,22 +654,42 @@ __global__ void scatter_kernel(void *spins, int precision, int64_t site_off, int
 // ------------------------------------------------------------------ variant table
 using PassFn = void (*)(PassArgs);
 
-template <int DEG>
-PassFn pick32(int pm, int lm) {
+constexpr int kStages = 3;  // cp.async pipeline depth of the staged kernel
+
+PassFn select_direct(int pm, int lm) {
     static const PassFn tab[3][3] = {
-        {pass32_kernel<DEG, 0, 0>, pass32_kernel<DEG, 0, 1>, pass32_kernel<DEG, 0, 2>},
-        {pass32_kernel<DEG, 1, 0>, pass32_kernel<DEG, 1, 1>, pass32_kernel<DEG, 1, 2>},
-        {pass32_kernel<DEG, 2, 0>, pass32_kernel<DEG, 2, 1>, pass32_kernel<DEG, 2, 2>},
+        {pass32_kernel<0, 0>, pass32_kernel<0, 1>, pass32_kernel<0, 2>},
+        {pass32_kernel<1, 0>, pass32_kernel<1, 1>, pass32_kernel<1, 2>},
+        {pass32_kernel<2, 0>, pass32_kernel<2, 1>, pass32_kernel<2, 2>},
     };
     return tab[pm][lm];
 }
 
-PassFn select32(const PassArgs &a) { return a.deg == 6 ? pick32<6>(a.params_mode, a.lower_mode) : pick32<0>(a.params_mode, a.lower_mode); }
+PassFn select_staged6(int pm, int lm) {
+    static const PassFn tab[3][3] = {
+        {pass32_staged<6, 0, 0, kStages>, pass32_staged<6, 0, 1, kStages>, pass32_staged<6, 0, 2, kStages>},
+        {pass32_staged<6, 1, 0, kStages>, pass32_staged<6, 1, 1, kStages>, pass32_staged<6, 1, 2, kStages>},
+        {pass32_staged<6, 2, 0, kStages>, pass32_staged<6, 2, 1, kStages>, pass32_staged<6, 2, 2, kStages>},
+    };
+    return tab[pm][lm];
+}
+
+bool use_staged(const PassArgs &a) { return a.deg == 6; }
+
+int staged_smem(const PassArgs &a) {
+    return (kThreads / 32) * staged_warp_bytes(6, kStages, 32 >> a.log2R);
+}
+
+PassFn select32(const PassArgs &a) {
+    return use_staged(a) ? select_staged6(a.params_mode, a.lower_mode) : select_direct(a.params_mode, a.lower_mode);
+}
+
+int smem32(const PassArgs &a) { return use_staged(a) ? staged_smem(a) : 0; }
 
 }  // namespace
 
 void launch_pass32(const PassArgs &a, int grid, void *stream) {
-    select32(a)<<<grid, kThreads, 0, (cudaStream_t)stream>>>(a);
+    select32(a)<<<grid, kThreads, smem32(a), (cudaStream_t)stream>>>(a);
 }
 
 void launch_pass64(const PassArgs &a, int grid, void *stream) {
@@ -517,8 +731,11 @@ int pass_blocks_per_sm(int precision, const PassArgs &a) {
     int nb = 0;
     if (precision == 64)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass64_kernel, kThreads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select32(a), kThreads, 0);
+    else {
+        const int sm = smem32(a);
+        if (sm > 0) cudaFuncSetAttribute(select32(a), cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select32(a), kThreads, sm);
+    }
     return nb > 0 ? nb : 1;
 }
 

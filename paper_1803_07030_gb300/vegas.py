@@ -52,6 +52,7 @@ class vegas_options(C.Structure):
         ("accept_log_mcs", C.c_int32),
         ("timing", C.c_int32),
         ("graphs", C.c_int32),
+        ("max_blocks", C.c_int32),
     ]
 
 
@@ -258,9 +259,13 @@ class Context:
 
     def __init__(self, samples: Sequence, precision: int = 32, replicas: int = 1, seed: int = 1,
                  inst_base: int = 0, device: int = -1, stream="torch", variant: int = -1,
-                 accept_log_mcs: int = 0, timing: bool = False, graphs: bool = True):
+                 accept_log_mcs: int = 0, timing: bool = False, graphs: bool = True, max_blocks: int = 0,
+                 library: Optional[str] = None):
         self.samples = list(samples)
         self.n_sites = [int(np.asarray(s.row_ptr).shape[0] - 1) for s in self.samples]
+        if library is not None:
+            global _lib
+            _lib = load_library(library)
         o = vegas_default_options()
         o.precision = precision
         o.replicas = replicas
@@ -271,6 +276,7 @@ class Context:
         o.accept_log_mcs = accept_log_mcs
         o.timing = 1 if timing else 0
         o.graphs = 1 if graphs else 0
+        o.max_blocks = max_blocks
         o.cuda_stream = _current_stream() if stream == "torch" else stream
         self.replicas = replicas
         self.ptr = None
