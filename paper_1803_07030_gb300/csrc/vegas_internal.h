@@ -115,6 +115,7 @@ struct PassArgs {
     int64_t n_edges_total;
     int32_t lower_mode;        // 0: no link to a lower colour, 1: every link, 2: test each
     int32_t params_mode;       // 0: uniform, no anisotropy; 1: uniform; 2: per site
+    int32_t depth;             // staged FP32 kernel: cp.async pipeline depth (2..4); 0 = direct kernel
     SiteParams32 u32;
     SiteParams64 u64;
 };

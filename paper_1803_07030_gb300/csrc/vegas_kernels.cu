@@ -374,13 +374,24 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Bytes of shared memory per warp for the staged kernel.
-__host__ __device__ constexpr int staged_rows_bytes(int deg, int D) { return D * (deg + 1) * 32 * 16; }
-__host__ __device__ inline int staged_slot_bytes(int deg, int spg) {
-    return ((spg * deg * 8 + 15) / 16) * 16 + ((spg * 4 + 15) / 16) * 16;
-}
-__host__ __device__ inline int staged_warp_bytes(int deg, int D, int spg) {
-    return staged_rows_bytes(deg, D) + 2 * D * staged_slot_bytes(deg, spg);
+// Geometry of the staged kernel. A group is 32 work items (spg = 32/R sites x R replicas);
+// a block is NB consecutive groups (BS = NB * spg >= 8 consecutive sites) whose links and
+// caller ids are staged together. NLS block slots cover the 2D-group lookahead of links.
+struct StagedGeom {
+    int spg, BS, NB, NLS, link_bytes, slot_bytes, rows_bytes, warp_bytes;
+};
+
+__host__ __device__ inline StagedGeom staged_geom(int deg, int D, int log2R) {
+    StagedGeom g;
+    g.spg = 32 >> log2R;
+    g.BS = g.spg > 8 ? g.spg : 8;
+    g.NB = g.BS / g.spg;
+    g.NLS = (2 * D + g.NB - 1) / g.NB + 1;
+    g.link_bytes = ((g.BS * deg * 8 + 15) / 16) * 16;
+    g.slot_bytes = g.link_bytes + ((g.BS * 4 + 15) / 16) * 16;
+    g.rows_bytes = D * (deg + 1) * 32 * 16;
+    g.warp_bytes = g.rows_bytes + g.NLS * g.slot_bytes;
+    return g;
 }
 
 // Debug builds (VEGAS_DEBUG_CHECKS) check every staged copy: a failed check sets
@@ -397,6 +408,21 @@ __host__ __device__ inline int staged_warp_bytes(int deg, int D, int spg) {
 #define VEGAS_CHECK(cond, code, val)
 #endif
 
+// Position of one group in the warp's sequence: first site, index inside its block, and
+// the slot holding its block's links. Groups are visited in increasing site order.
+struct GroupPos {
+    int sbase, j, lslot;
+    __device__ __forceinline__ void next(const StagedGeom &G, int bstride) {
+        if (++j == G.NB) {
+            j = 0;
+            sbase += bstride - (G.NB - 1) * G.spg;
+            lslot = (lslot + 1 == G.NLS) ? 0 : lslot + 1;
+        } else {
+            sbase += G.spg;
+        }
+    }
+};
+
 template <int DEG, int PM, int LM, int D>
 __global__ void __launch_bounds__(kThreads) pass32_staged(const PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -404,43 +430,53 @@ __global__ void __launch_bounds__(kThreads) pass32_staged(const PassArgs a) {
     const uint32_t t = rs_->t;
     const uint32_t step_idx = rs_->rec / rs_->mcs;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int log2R = a.log2R, R = 1 << log2R, spg = 32 >> log2R;
+    const int log2R = a.log2R, R = 1 << log2R;
+    const StagedGeom G = staged_geom(DEG, D, log2R);
     const int r = lane & (R - 1), my = lane >> log2R;  // replica, site within the group
-    const int slot_bytes = staged_slot_bytes(DEG, spg);
-    const int edge_pad = ((spg * DEG * 8 + 15) / 16) * 16;
-    unsigned char *wbase = smem + (size_t)warp * staged_warp_bytes(DEG, D, spg);
-    float4 *rows = (float4 *)wbase;                            // [D][DEG+1][32]
-    unsigned char *slots = wbase + staged_rows_bytes(DEG, D);  // [2D][links | caller ids]
+    unsigned char *wbase = smem + (size_t)warp * G.warp_bytes;
+    float4 *rows = (float4 *)wbase;                     // [D][DEG+1][32]
+    unsigned char *lslots = wbase + G.rows_bytes;       // [NLS][links | caller ids]
     float4 *S = (float4 *)a.spins;
     const float4 *Sr = S + r;
     const int2 *E = (const int2 *)a.edges;
-    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     const uint32_t inst = (uint32_t)(a.inst0 + r);
     const double *sc = rs_->sched + ((int64_t)step_idx * a.n_inst + a.inst_local0 + r) * 2;
     const float beta = (float)sc[0], B = (float)sc[1];
     const int g_end = a.g_end;
-    const int W = blockIdx.x * (blockDim.x >> 5) + warp;
-    const int step = gridDim.x * (blockDim.x >> 5) * spg;  // sites between this warp's groups
+    const int nwarps = blockDim.x >> 5;
+    const int W = blockIdx.x * nwarps + warp;
+    const int bstride = gridDim.x * nwarps * G.BS;  // sites between this warp's blocks
+    uint32_t rk0[10], rk1[10];                      // Philox round keys, kept in registers
+    {
+        uint32_t x = (uint32_t)a.seed, y = (uint32_t)(a.seed >> 32);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            rk0[q] = x;
+            rk1[q] = y;
+            x += 0x9E3779B9u;
+            y += 0xBB67AE85u;
+        }
+    }
 
-    auto issue_links = [&](int sbase, int slot) {  // links and caller ids of the group at sbase
-        if (sbase >= g_end) return;
-        const int ns = min(spg, g_end - sbase);
-        unsigned char *dst = slots + slot * slot_bytes;
-        const unsigned char *src = (const unsigned char *)(E + a.edge_base + (int64_t)(sbase - a.site_off) * DEG);
-        const int nch = ns * (DEG * 8 / 16);
-        VEGAS_CHECK(sbase >= a.g_begin && slot >= 0 && slot < 2 * D, 1, sbase);
-        VEGAS_CHECK(a.edge_base + (int64_t)(sbase - a.site_off) * DEG + (int64_t)ns * DEG <= a.n_edges_total, 2, sbase);
-        VEGAS_CHECK(((uintptr_t)src & 15) == 0 && ((uintptr_t)dst & 15) == 0, 3, sbase);
-        VEGAS_CHECK(sbase + ns <= a.n_sites_total, 4, sbase);
+    auto issue_links = [&](int sb, int slot) {  // links and caller ids of the block at sb
+        if (sb >= g_end) return;
+        const int ns = min(G.BS, g_end - sb);
+        unsigned char *dst = lslots + slot * G.slot_bytes;
+        const unsigned char *src = (const unsigned char *)(E + a.edge_base + (int64_t)(sb - a.site_off) * DEG);
+        const int nch = ns * (DEG / 2);
+        VEGAS_CHECK(sb >= a.g_begin && slot >= 0 && slot < G.NLS, 1, sb);
+        VEGAS_CHECK(a.edge_base + (int64_t)(sb - a.site_off) * DEG + (int64_t)ns * DEG <= a.n_edges_total, 2, sb);
+        VEGAS_CHECK(((uintptr_t)src & 15) == 0 && ((uintptr_t)dst & 15) == 0, 3, sb);
+        VEGAS_CHECK(sb + ns <= a.n_sites_total, 4, sb);
         for (int c = lane; c < nch; c += 32) cp16(dst + 16 * c, src + 16 * c);
-        if (lane < ns) cp4(dst + edge_pad + 4 * lane, a.orig + sbase + lane);
+        if (lane < ns) cp4(dst + G.link_bytes + 4 * lane, a.orig + sb + lane);
     };
-    auto issue_rows = [&](int sbase, int lslot, int rslot) {  // rows of the group at sbase
-        const int g = sbase + my;
+    auto issue_rows = [&](const GroupPos &p, int rslot) {  // rows of a group (its links have landed)
+        const int g = p.sbase + my;
         if (g >= g_end) return;
-        const int4 *lk = (const int4 *)(slots + lslot * slot_bytes) + my * (DEG / 2);
+        const int4 *lk = (const int4 *)(lslots + p.lslot * G.slot_bytes) + (p.j * G.spg + my) * (DEG / 2);
         float4 *dst = rows + rslot * (DEG + 1) * 32 + lane;
-        VEGAS_CHECK(lslot >= 0 && lslot < 2 * D && rslot >= 0 && rslot < D, 5, lslot * 16 + rslot);
+        VEGAS_CHECK(p.lslot >= 0 && p.lslot < G.NLS && rslot >= 0 && rslot < D, 5, p.lslot * 16 + rslot);
         VEGAS_CHECK(g < a.n_sites_total, 6, g);
 #pragma unroll
         for (int j = 0; j < DEG / 2; ++j) {
@@ -452,26 +488,35 @@ __global__ void __launch_bounds__(kThreads) pass32_staged(const PassArgs a) {
         cp16(dst + DEG * 32, Sr + ((int64_t)g << log2R));
     };
 
-    int s0 = a.g_begin + W * spg;  // first site of the current group
-    for (int k = 0; k < 2 * D; ++k) issue_links(s0 + k * step, k);
+    // prologue: links of every block whose first group is among the first 2D, then the
+    // rows of the first D groups
+    const int g0 = a.g_begin + W * G.BS;
+    const int nb_pro = (2 * D + G.NB - 1) / G.NB;
+    for (int b = 0; b < nb_pro; ++b) issue_links(g0 + b * bstride, b);
     cp_commit();
     cp_wait<0>();
     __syncwarp();
-    for (int k = 0; k < D; ++k) {
-        issue_rows(s0 + k * step, k, k);
+    GroupPos pk{g0, 0, 0};  // group k (computed now)
+    GroupPos pd = pk;       // group k + D (rows issued at the end of this iteration)
+    for (int q = 0; q < D; ++q) {
+        issue_rows(pd, q);
         cp_commit();
+        pd.next(G, bstride);
     }
-    int ls = 0, la = D, rsl = 0;  // links slot of this group, of the group D ahead; rows slot
+    int k_issue = nb_pro * G.NB - 2 * D;  // iteration whose end issues the next block's links
+    int sb_next = g0 + nb_pro * bstride, ls_next = nb_pro;
+    int rsl = 0;
     Acc32 acc;
-    for (; s0 < g_end; s0 += step) {
+    for (int k = 0; pk.sbase < g_end; ++k) {
         cp_wait<D - 1>();
         __syncwarp();
-        const int g = s0 + my;
+        const int g = pk.sbase + my;
         if (g < g_end) {
-            const unsigned char *slot = slots + ls * slot_bytes;
-            const int4 *lk = (const int4 *)slot + my * (DEG / 2);
+            const unsigned char *slot = lslots + pk.lslot * G.slot_bytes;
+            const int li = pk.j * G.spg + my;
+            const int4 *lk = (const int4 *)slot + li * (DEG / 2);
             const float4 *row = rows + rsl * (DEG + 1) * 32 + lane;
-            const uint32_t orig = ((const uint32_t *)(slot + edge_pad))[my];
+            const uint32_t orig = ((const uint32_t *)(slot + G.link_bytes))[li];
             bool skip = false;
 #ifdef VEGAS_DEBUG_CHECKS
             if (orig >= (uint32_t)a.n_sample_sites || g >= a.n_sites_total) {
@@ -482,39 +527,51 @@ __global__ void __launch_bounds__(kThreads) pass32_staged(const PassArgs a) {
             }
 #endif
             if (!skip) {
-            const Site32 p = site_params32(a, PM, g);
-            float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+                const Site32 p = site_params32(a, PM, g);
+                float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
 #pragma unroll
-            for (int j = 0; j < DEG / 2; ++j) {
-                const int4 q = lk[j];
-                link32(row[(2 * j) * 32], __int_as_float(q.y), LM == 2 && q.x < a.lower_end, hx, hy, hz, lx, ly, lz);
-                link32(row[(2 * j + 1) * 32], __int_as_float(q.w), LM == 2 && q.z < a.lower_end, hx, hy, hz, lx, ly,
-                       lz);
-            }
-            if (LM == 1) {
-                lx = hx;
-                ly = hy;
-                lz = hz;
-            }
-            const float4 Si = row[DEG * 32];
-            const uint4 rw = philox10(make_uint4(orig, t, inst, kPurposeTrial32), k0, k1);
-            float4 Sn;
-            bool ok, bad;
-            float e_i;
-            attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, rw, Sn, ok, e_i, bad);
-            if (bad) atomicOr(a.err, kErrNaN);
-            if (ok) S[((int64_t)g << log2R) + r] = Sn;
-            if (a.alog && t < a.alog_mcs)
-                a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
-            acc.add(e_i, Sn);
+                for (int j = 0; j < DEG / 2; ++j) {
+                    const int4 q = lk[j];
+                    link32(row[(2 * j) * 32], __int_as_float(q.y), LM == 2 && q.x < a.lower_end, hx, hy, hz, lx, ly,
+                           lz);
+                    link32(row[(2 * j + 1) * 32], __int_as_float(q.w), LM == 2 && q.z < a.lower_end, hx, hy, hz, lx,
+                           ly, lz);
+                }
+                if (LM == 1) {
+                    lx = hx;
+                    ly = hy;
+                    lz = hz;
+                }
+                const float4 Si = row[DEG * 32];
+                uint4 c = make_uint4(orig, t, inst, kPurposeTrial32);
+#pragma unroll
+                for (int q = 0; q < 10; ++q) {  // Philox4x32-10 with the round keys above
+                    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+                    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+                    c = make_uint4(hi1 ^ c.y ^ rk0[q], lo1, hi0 ^ c.w ^ rk1[q], lo0);
+                }
+                float4 Sn;
+                bool ok, bad;
+                float e_i;
+                attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, c, Sn, ok, e_i, bad);
+                if (bad) atomicOr(a.err, kErrNaN);
+                if (ok) S[((int64_t)g << log2R) + r] = Sn;
+                if (a.alog && t < a.alog_mcs)
+                    a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
+                acc.add(e_i, Sn);
             }
         }
         __syncwarp();
-        issue_links(s0 + 2 * D * step, ls);
-        issue_rows(s0 + D * step, la, rsl);
+        if (k == k_issue) {
+            issue_links(sb_next, ls_next);
+            k_issue += G.NB;
+            sb_next += bstride;
+            ls_next = (ls_next + 1 == G.NLS) ? 0 : ls_next + 1;
+        }
+        issue_rows(pd, rsl);
         cp_commit();
-        ls = (ls + 1 == 2 * D) ? 0 : ls + 1;
-        la = (la + 1 == 2 * D) ? 0 : la + 1;
+        pk.next(G, bstride);
+        pd.next(G, bstride);
         rsl = (rsl + 1 == D) ? 0 : rsl + 1;
     }
     cp_wait<0>();
@@ -654,8 +711,6 @@ __global__ void scatter_kernel(void *spins, int precision, int64_t site_off, int
 // ------------------------------------------------------------------ variant table
 using PassFn = void (*)(PassArgs);
 
-constexpr int kStages = 3;  // cp.async pipeline depth of the staged kernel
-
 PassFn select_direct(int pm, int lm) {
     static const PassFn tab[3][3] = {
         {pass32_kernel<0, 0>, pass32_kernel<0, 1>, pass32_kernel<0, 2>},
@@ -665,23 +720,30 @@ PassFn select_direct(int pm, int lm) {
     return tab[pm][lm];
 }
 
+template <int D>
 PassFn select_staged6(int pm, int lm) {
     static const PassFn tab[3][3] = {
-        {pass32_staged<6, 0, 0, kStages>, pass32_staged<6, 0, 1, kStages>, pass32_staged<6, 0, 2, kStages>},
-        {pass32_staged<6, 1, 0, kStages>, pass32_staged<6, 1, 1, kStages>, pass32_staged<6, 1, 2, kStages>},
-        {pass32_staged<6, 2, 0, kStages>, pass32_staged<6, 2, 1, kStages>, pass32_staged<6, 2, 2, kStages>},
+        {pass32_staged<6, 0, 0, D>, pass32_staged<6, 0, 1, D>, pass32_staged<6, 0, 2, D>},
+        {pass32_staged<6, 1, 0, D>, pass32_staged<6, 1, 1, D>, pass32_staged<6, 1, 2, D>},
+        {pass32_staged<6, 2, 0, D>, pass32_staged<6, 2, 1, D>, pass32_staged<6, 2, 2, D>},
     };
     return tab[pm][lm];
 }
 
-bool use_staged(const PassArgs &a) { return a.deg == 6; }
+bool use_staged(const PassArgs &a) { return a.deg == 6 && a.depth >= 2; }
 
-int staged_smem(const PassArgs &a) {
-    return (kThreads / 32) * staged_warp_bytes(6, kStages, 32 >> a.log2R);
+int staged_smem(const PassArgs &a) { return (kThreads / 32) * staged_geom(6, a.depth, a.log2R).warp_bytes; }
+
+PassFn select_staged(const PassArgs &a) {
+    switch (a.depth) {
+        case 2: return select_staged6<2>(a.params_mode, a.lower_mode);
+        case 4: return select_staged6<4>(a.params_mode, a.lower_mode);
+        default: return select_staged6<3>(a.params_mode, a.lower_mode);
+    }
 }
 
 PassFn select32(const PassArgs &a) {
-    return use_staged(a) ? select_staged6(a.params_mode, a.lower_mode) : select_direct(a.params_mode, a.lower_mode);
+    return use_staged(a) ? select_staged(a) : select_direct(a.params_mode, a.lower_mode);
 }
 
 int smem32(const PassArgs &a) { return use_staged(a) ? staged_smem(a) : 0; }

@@ -53,6 +53,7 @@ class vegas_options(C.Structure):
         ("timing", C.c_int32),
         ("graphs", C.c_int32),
         ("max_blocks", C.c_int32),
+        ("pipeline_depth", C.c_int32),
     ]
 
 
@@ -260,7 +261,7 @@ class Context:
     def __init__(self, samples: Sequence, precision: int = 32, replicas: int = 1, seed: int = 1,
                  inst_base: int = 0, device: int = -1, stream="torch", variant: int = -1,
                  accept_log_mcs: int = 0, timing: bool = False, graphs: bool = True, max_blocks: int = 0,
-                 library: Optional[str] = None):
+                 pipeline_depth: int = 0, library: Optional[str] = None):
         self.samples = list(samples)
         self.n_sites = [int(np.asarray(s.row_ptr).shape[0] - 1) for s in self.samples]
         if library is not None:
@@ -277,6 +278,7 @@ class Context:
         o.timing = 1 if timing else 0
         o.graphs = 1 if graphs else 0
         o.max_blocks = max_blocks
+        o.pipeline_depth = pipeline_depth
         o.cuda_stream = _current_stream() if stream == "torch" else stream
         self.replicas = replicas
         self.ptr = None
