@@ -177,6 +177,51 @@ vegas_status vegas_stats(const vegas_ctx *ctx, vegas_stats_t *out);
  */
 int32_t vegas_greedy_colour(int32_t n_sites, const int64_t *row_ptr, const int32_t *col, int32_t *color_out);
 
+/*
+ * One MCS on device memory the caller owns; the library allocates nothing.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot let a
+ * library call cudaMalloc (programs that manage every device byte in their own pool or
+ * arena, loops that cannot afford the implicit device synchronisation of an allocation,
+ * plug-in hosts that hand out fixed buffers). They cannot create a context, so the data
+ * comes as device pointers, and the sweep keeps its scratch (partial sums of E and M for
+ * at most 1024 thread blocks x 32 replicas, the run state, the error word: about 1 MB) in
+ * a static device array of the library that every GPU loading the library holds until
+ * the process exits.
+ *
+ * Layout (the library's own): sites numbered colour-major, colour class c being sites
+ * [colour_start[c], colour_start[c+1]); no link joins two sites of one class.
+ *   spins     device, [n_sites][replicas] x (x, y, z, unused) float32, 16-byte aligned;
+ *             updated in place
+ *   links     device, [n_edges] x (neighbour index as int32, J as float32 bits), every
+ *             link present in both directions with equal J
+ *   row_ptr   device, [n_sites + 1] int64 link offsets
+ *   site_id   device, [n_sites] int32 ids used as Philox keys (the caller's numbering)
+ *   colour_start  host, [n_colours + 1], from 0 to n_sites, n_colours <= 64
+ *   replicas  1, 2, 4, ..., 32 (larger values are rejected: the scratch holds 32)
+ *   beta, field   host, [replicas]: 1/T > 0 and B of each replica
+ *   site_params   host, 9 doubles (nx, ny, nz, s, ex, ey, ez, k, kc) shared by all
+ *             sites, or NULL (field axis +z, s = 1, no anisotropy)
+ *   seed, inst0, t  Philox key, instance id of replica 0, global MCS index
+ *   out       device, [replicas][4] doubles: (E, Mx, My, Mz) after the MCS
+ *   stream    cudaStream_t or NULL (legacy default stream)
+ * Computes what vegas_run computes for one MCS of an FP32 context with these replicas
+ * (same random numbers for the same seed, ids, instances and t); no renormalisation.
+ * Blocking: returns after the sweep finished on the stream. The first call on a device
+ * looks up the device address of the static scratch (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture. Every call uses the
+ * same scratch and rewrites it; calls whose GPU work overlaps (other threads, other
+ * streams) race on it. Errors: VEGAS_EINVAL for bad sizes or pointers (message from
+ * vegas_noalloc_last_error), VEGAS_ECUDA, VEGAS_EDEVICE (NaN energy change).
+ */
+vegas_status vegas_sweep_noalloc(void *spins, const void *links, const int64_t *row_ptr, const int32_t *site_id,
+                                 int32_t n_sites, const int32_t *colour_start, int32_t n_colours, int32_t replicas,
+                                 const double *beta, const double *field, const double *site_params, uint64_t seed,
+                                 int32_t inst0, uint32_t t, double *out, void *stream);
+
+/* Message of the last failed vegas_sweep_noalloc call of this thread. Never NULL. */
+const char *vegas_noalloc_last_error(void);
+
 /* Message of the last failed call on ctx (ctx == NULL: last failed vegas_create of this
  * thread). Valid until the next call on ctx. Never NULL. */
 const char *vegas_last_error(const vegas_ctx *ctx);

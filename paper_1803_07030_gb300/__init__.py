@@ -19,5 +19,6 @@ from .vegas import (  # noqa: F401
     vegas_last_error,
     vegas_run,
     vegas_set_spins,
+    vegas_sweep_noalloc,
     vegas_stats,
 )

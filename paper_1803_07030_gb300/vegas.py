@@ -91,6 +91,9 @@ SIGNATURES = {
     "vegas_greedy_colour": (C.c_int32, [C.c_int32, P, P, P]),
     "vegas_last_error": (C.c_char_p, [P]),
     "vegas_destroy": (None, [P]),
+    "vegas_sweep_noalloc": (C.c_int, [P, P, P, P, C.c_int32, P, C.c_int32, C.c_int32, P, P, P, C.c_uint64,
+                                      C.c_int32, C.c_uint32, P, P]),
+    "vegas_noalloc_last_error": (C.c_char_p, []),
 }
 
 _lib = None
@@ -227,6 +230,22 @@ def vegas_stats(ctx) -> dict:
     s = vegas_stats_t()
     _check(load_library().vegas_stats(ctx, C.byref(s)), ctx)
     return {k: getattr(s, k) for k, _ in vegas_stats_t._fields_}
+
+
+def vegas_sweep_noalloc(spins_ptr: int, links_ptr: int, row_ptr_ptr: int, site_id_ptr: int, n_sites: int,
+                        colour_start, replicas: int, beta, field, site_params=None, seed: int = 1, inst0: int = 0,
+                        t: int = 0, out_ptr: int = 0, stream: Optional[int] = None) -> None:
+    """One MCS on caller-owned device buffers (device pointers as ints); allocates nothing."""
+    cs = _arr(colour_start, np.int32)
+    b = _arr(beta, np.float64)
+    f = _arr(field, np.float64)
+    sp = _arr(site_params, np.float64)
+    lib = load_library()
+    st = lib.vegas_sweep_noalloc(spins_ptr, links_ptr, row_ptr_ptr, site_id_ptr, n_sites, _ptr(cs), len(cs) - 1,
+                                 replicas, _ptr(b), _ptr(f), _ptr(sp), seed, inst0, t, out_ptr, stream)
+    if st != OK:
+        m = lib.vegas_noalloc_last_error()
+        raise VegasError(st, m.decode() if m else "")
 
 
 def vegas_last_error(ctx=None) -> str:
