@@ -76,6 +76,10 @@ typedef struct {
     const int32_t *color;      /* [n_sites] proper colouring, or NULL (greedy) */
     const double *init_spins;  /* [n_sites][3] initial state for every replica, or NULL:
                                   S_i = s_i * uniform-on-sphere from Philox */
+    const double *positions;   /* [n_sites][3] site coordinates, or NULL. Used only to order
+                                  sites in device memory (a Morton curve inside each colour
+                                  class) so that a sweep's neighbour reads stay in L2; results
+                                  do not depend on it. */
 } vegas_sample;
 
 typedef struct {

@@ -135,6 +135,7 @@ def sc_periodic(
     col = nbr.reshape(-1).astype(np.int32)
     Jf = Jtab.reshape(-1)
     s = Sample(name=f"sc{Lx}x{Ly}x{Lz}", row_ptr=row_ptr, col=col, J=Jf)
+    s.positions = np.stack([x, y, z], axis=1).astype(np.float64)
     if k_uni != 0.0:
         e = np.asarray(e_axis, dtype=np.float64)
         e = e / np.linalg.norm(e)

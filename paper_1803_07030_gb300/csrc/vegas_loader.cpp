@@ -24,6 +24,40 @@ bool finite_all(const double *p, int64_t n) {
 
 std::string at(const char *what, int64_t i) { return std::string(what) + " at index " + std::to_string(i); }
 
+// Spread the low 21 bits of v so that bit b lands on bit 3b (Morton interleave helper).
+uint64_t spread3(uint64_t v) {
+    v &= 0x1FFFFFull;
+    v = (v | (v << 32)) & 0x1F00000000FFFFull;
+    v = (v | (v << 16)) & 0x1F0000FF0000FFull;
+    v = (v | (v << 8)) & 0x100F00F00F00F00Full;
+    v = (v | (v << 4)) & 0x10C30C30C30C30C3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+// Morton (Z-order) keys of the site positions on a 2^21 grid spanning their bounding box.
+std::vector<uint64_t> morton_keys(const double *pos, int32_t n) {
+    double lo[3] = {pos[0], pos[1], pos[2]}, hi[3] = {pos[0], pos[1], pos[2]};
+    for (int32_t i = 0; i < n; ++i)
+        for (int q = 0; q < 3; ++q) {
+            lo[q] = std::min(lo[q], pos[3 * (int64_t)i + q]);
+            hi[q] = std::max(hi[q], pos[3 * (int64_t)i + q]);
+        }
+    const double ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]});
+    const double scale = ext > 0.0 ? 2097151.0 / ext : 0.0;
+    std::vector<uint64_t> key((size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        uint64_t k = 0;
+        for (int q = 0; q < 3; ++q) {
+            double c = (pos[3 * (int64_t)i + q] - lo[q]) * scale;
+            c = std::min(std::max(c, 0.0), 2097151.0);
+            k |= spread3((uint64_t)c) << q;
+        }
+        key[(size_t)i] = k;
+    }
+    return key;
+}
+
 
 }  // namespace
 
@@ -129,6 +163,7 @@ bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err) {
         for (int32_t i = 0; i < n; ++i)
             if (!(s.spin_norm[i] > 0.0)) { err = at("spin_norm <= 0", i); return false; }
     if (s.init_spins && !finite_all(s.init_spins, 3 * (int64_t)n)) { err = "non-finite init_spins"; return false; }
+    if (s.positions && !finite_all(s.positions, 3 * (int64_t)n)) { err = "non-finite positions"; return false; }
 
     // colouring
     std::vector<int32_t> colour((size_t)n);
@@ -157,11 +192,14 @@ bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err) {
     std::vector<int32_t> fill(L.cstart.begin(), L.cstart.end() - 1);
     L.orig.resize((size_t)n);
     L.inv.resize((size_t)n);
-    for (int32_t i = 0; i < n; ++i) {
-        const int32_t g = fill[(size_t)colour[(size_t)i]]++;
-        L.orig[(size_t)g] = i;
-        L.inv[(size_t)i] = g;
+    for (int32_t i = 0; i < n; ++i) L.orig[(size_t)fill[(size_t)colour[(size_t)i]]++] = i;
+    if (s.positions) {  // memory order inside each class: Morton curve of the positions
+        const std::vector<uint64_t> key = morton_keys(s.positions, n);
+        for (int32_t c = 0; c < nc; ++c)
+            std::stable_sort(L.orig.begin() + L.cstart[(size_t)c], L.orig.begin() + L.cstart[(size_t)c + 1],
+                             [&](int32_t x, int32_t y) { return key[(size_t)x] < key[(size_t)y]; });
     }
+    for (int32_t g = 0; g < n; ++g) L.inv[(size_t)L.orig[(size_t)g]] = g;
     L.row_ptr.resize((size_t)n + 1);
     L.col.resize((size_t)E);
     L.J.resize((size_t)E);

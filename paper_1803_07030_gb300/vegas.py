@@ -37,6 +37,7 @@ class vegas_sample(C.Structure):
         ("k_cub", P),
         ("color", P),
         ("init_spins", P),
+        ("positions", P),
     ]
 
 
@@ -175,9 +176,11 @@ class _SampleArrays:
         self.k_cub = _arr(g("k_cub"), np.float64)
         self.color = _arr(g("colour"), np.int32)
         self.init_spins = _arr(g("init_spins"), np.float64)
+        self.positions = _arr(g("positions"), np.float64, (n, 3) if g("positions") is not None else None)
         self.c = vegas_sample(n, 0, int(self.col.shape[0]), _ptr(self.row_ptr), _ptr(self.col), _ptr(self.J),
                               _ptr(self.type), _ptr(self.spin_norm), _ptr(self.field_axis), _ptr(self.k_uni),
-                              _ptr(self.e_uni), _ptr(self.k_cub), _ptr(self.color), _ptr(self.init_spins))
+                              _ptr(self.e_uni), _ptr(self.k_cub), _ptr(self.color), _ptr(self.init_spins),
+                              _ptr(self.positions))
 
 
 def vegas_create(samples: Sequence, options: vegas_options):

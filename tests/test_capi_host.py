@@ -39,8 +39,12 @@ def test_exports_every_declared_function(lib):
 def test_struct_sizes_match_header(lib):
     import ctypes as C
 
-    # vegas_sample: 2 int32 + int64 + 11 pointers; options and stats as laid out in the header
-    assert C.sizeof(vb.vegas_sample) == 16 + 11 * 8
+    # vegas_sample: 2 int32 + int64 + one pointer per array field of the header's struct
+    text = open(os.path.join(ROOT, "include", "vegas.h")).read()
+    body = text[text.index("typedef struct {\n    int32_t n_sites;"):text.index("} vegas_sample;")]
+    n_ptr = len(re.findall(r"^\s*const [a-z0-9_]+ \*[A-Za-z_]+;", body, flags=re.M))
+    assert n_ptr == len(vb.vegas_sample._fields_) - 3
+    assert C.sizeof(vb.vegas_sample) == 16 + n_ptr * 8
     o = vg.vegas_default_options()
     assert (o.precision, o.replicas, o.seed, o.device, o.variant, o.graphs) == (32, 1, 1, -1, -1, 1)
 

@@ -168,6 +168,23 @@ def test_fp32_staged_many_groups_per_warp(R, max_blocks):
             assert abs(Ha[i, -1, 0] - oracle.energy(s, S, 0.0)) < 1e-5 * s.n_sites
 
 
+@pytest.mark.parametrize("precision,R", [(32, 32), (32, 1), (64, 2)])
+def test_memory_order_from_positions_does_not_change_spins(precision, R):
+    import copy
+
+    s = sc_periodic(10, bimodal_seed=2)
+    u = copy.copy(s)
+    u.positions = None
+    assert s.positions is not None
+    T = np.linspace(0.3, 2.0, R)[:, None]
+    with ctx([s], precision=precision, replicas=R, seed=9) as a, ctx([u], precision=precision, replicas=R, seed=9) as b:
+        a.run(T, np.full_like(T, 0.1), 6)
+        b.run(T, np.full_like(T, 0.1), 6)
+        for i in sorted({0, R - 1}):
+            assert np.array_equal(a.spins(i), b.spins(i))
+        assert_fp32_history_close(a.history(), b.history(), s.n_sites)
+
+
 def test_fp32_direct_kernel_many_items_per_thread():
     s = fcc_sphere(7.0)
     T = np.array([[0.5], [1.0], [1.5], [3.0]])
