@@ -99,7 +99,7 @@ typedef struct {
     int32_t max_blocks;     /* > 0: at most this many thread blocks per sweep launch (tests,
                                tuning); 0 = as many as fit on the device. Default 0. */
     int32_t pipeline_depth; /* FP32 sweeps of rows with six links: groups of rows kept in
-                               flight per warp, 2..4; 1 = no staging (direct kernel);
+                               flight per warp, 2 or 3; 1 = no staging (direct kernel);
                                0 = automatic. Default 0. */
 } vegas_options;
 

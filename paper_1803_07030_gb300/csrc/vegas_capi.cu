@@ -197,7 +197,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         return fail(nullptr, VEGAS_EINVAL, "replicas must be 1, 2, 4, 8, 16 or 32");
     if (o.accept_log_mcs < 0 || o.inst_base < 0 || o.max_blocks < 0) return fail(nullptr, VEGAS_EINVAL, "negative option");
     if (o.variant < -1 || o.variant > 1) return fail(nullptr, VEGAS_EINVAL, "variant must be -1, 0 or 1");
-    if (o.pipeline_depth < 0 || o.pipeline_depth > 4) return fail(nullptr, VEGAS_EINVAL, "pipeline_depth must be 0..4");
+    if (o.pipeline_depth < 0 || o.pipeline_depth > 3) return fail(nullptr, VEGAS_EINVAL, "pipeline_depth must be 0..3");
     if ((int64_t)o.inst_base + (int64_t)n_samples * o.replicas > (int64_t)UINT32_MAX)
         return fail(nullptr, VEGAS_EINVAL, "instance ids exceed 32 bits");
 
@@ -445,8 +445,8 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
             a.lower_mode = si.lower_mode[(size_t)col];
             a.params_mode = si.uniform_params ? (si.has_anisotropy ? 1 : 0) : 2;
             // measured on the 32 x 256^3 spin glass: depth 2 keeps 3 blocks per SM for R >= 16
-            // (2.93 ms per class vs 3.07 ms at depth 3, 4.32 ms at depth 4); fewer replicas
-            // per site spread each row over more lanes and prefer the deeper pipeline
+            // (2.93 ms per class vs 3.07 ms at depth 3 and 4.32 ms at depth 4, which fits only
+            // one block per SM); with fewer replicas the deeper pipeline was marginally faster
             a.depth = (o.pipeline_depth == 0) ? (c->R >= 16 ? 2 : 3) : (o.pipeline_depth == 1 ? 0 : o.pipeline_depth);
             a.u64 = si.u;
             a.u32 = SiteParams32{(float)si.u.nx, (float)si.u.ny, (float)si.u.nz, (float)si.u.s, (float)si.u.ex,

@@ -220,9 +220,13 @@ __device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, f
                                           float &e_i, bool &nan_seen) {
     const float Hx = fmaf(B, p.nx, hx), Hy = fmaf(B, p.ny, hy), Hz = fmaf(B, p.nz, hz);
     // trial: z uniform in (-1, 1), azimuth uniform in (-pi, pi): by Archimedes' theorem the
-    // point (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z) is uniform on the sphere
-    const float z = fmaf((float)(rw.x >> 8), 0x1p-23f, -1.0f + 0x1p-24f);
-    const float phi = __fmul_rn(fmaf((float)(rw.y >> 8), 0x1p-23f, -1.0f + 0x1p-24f), 3.14159265358979f);
+    // point (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z) is uniform on the sphere. Each
+    // uniform takes 23 random bits as the mantissa of a float in [1, 2): f = 1 + k 2^-23,
+    // so z = 2 (f - 1.5) + 2^-23 = (2k + 1) 2^-23 - 1 exactly (midpoints of 2^23 cells).
+    const float fz = __uint_as_float(0x3F800000u | (rw.x >> 9));
+    const float fp = __uint_as_float(0x3F800000u | (rw.y >> 9));
+    const float z = fmaf(__fsub_rn(fz, 1.5f), 2.0f, 0x1p-23f);
+    const float phi = fmaf(__fsub_rn(fp, 1.5f), 6.28318530717959f, 3.14159265358979f * 0x1p-23f);
     float sphi, cphi;
     __sincosf(phi, &sphi, &cphi);
     const float rho2 = fmaf(-z, z, 1.0f);
@@ -239,7 +243,7 @@ __device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, f
         dE = fmaf(-p.kc, __fsub_rn(cub32(px, py, pz), cub32(Si.x, Si.y, Si.z)), dE);
     }
     // Metropolis acceptance (Eq. 4) with the third word as the uniform; NaN rejects
-    const float u = __fmul_rn((float)(rw.z >> 8), 0x1p-24f);
+    const float u = __fsub_rn(__uint_as_float(0x3F800000u | (rw.z >> 9)), 1.0f);  // k 2^-23 in [0, 1)
     acc = (dE <= 0.f) || (u < __expf(__fmul_rn(-beta, dE)));
     nan_seen = (dE != dE);
     if (nan_seen) acc = false;
@@ -255,7 +259,8 @@ __device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, f
     e_i = e;
 }
 
-// Short FP32 runs of the per-thread sums, then FP64.
+// Per-thread sums of E and M: runs of at most 64 attempts in FP32, then FP64 (a run's
+// rounding error is below 64 * 2^-24 of its absolute sum, < 1e-5 of E/N).
 struct Acc32 {
     double d[4] = {0.0, 0.0, 0.0, 0.0};
     float f[4] = {0.f, 0.f, 0.f, 0.f};
@@ -265,8 +270,9 @@ struct Acc32 {
         f[1] = __fadd_rn(f[1], q.x);
         f[2] = __fadd_rn(f[2], q.y);
         f[3] = __fadd_rn(f[3], q.z);
-        if (++n == 16) flush();
+        if (++n == 64) flush();
     }
+
     __device__ __forceinline__ void flush() {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -374,6 +380,45 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// One staged attempt: links lk (int4 pairs), rows row[j*32] (neighbour j) and row[DEG*32]
+// (own) already in shared memory.
+template <int DEG, int PM, int LM>
+__device__ __forceinline__ void staged_attempt(const PassArgs &a, const int4 *lk, const float4 *row, uint32_t orig,
+                                               int g, int r, int R, uint32_t t, uint32_t inst, const uint32_t *rk0,
+                                               const uint32_t *rk1, float beta, float B, float4 *S, Acc32 &acc,
+                                               bool &nan_seen, bool log_accepts) {
+    const Site32 p = site_params32(a, PM, g);
+    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+#pragma unroll
+    for (int j = 0; j < DEG / 2; ++j) {
+        const int4 q = lk[j];
+        link32(row[(2 * j) * 32], __int_as_float(q.y), LM == 2 && q.x < a.lower_end, hx, hy, hz, lx, ly, lz);
+        link32(row[(2 * j + 1) * 32], __int_as_float(q.w), LM == 2 && q.z < a.lower_end, hx, hy, hz, lx, ly, lz);
+    }
+    if (LM == 1) {
+        lx = hx;
+        ly = hy;
+        lz = hz;
+    }
+    const float4 Si = row[DEG * 32];
+    uint4 c = make_uint4(orig, t, inst, kPurposeTrial32);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {  // Philox4x32-10 with precomputed round keys
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk0[q], lo1, hi0 ^ c.w ^ rk1[q], lo0);
+    }
+    float4 Sn;
+    bool ok, bad;
+    float e_i;
+    attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, c, Sn, ok, e_i, bad);
+    nan_seen |= bad;
+    if (ok) S[(int64_t)g * R + r] = Sn;
+    if (log_accepts)
+        a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
+    acc.add(e_i, Sn);
+}
+
 // Geometry of the staged kernel. A group is 32 work items (spg = 32/R sites x R replicas);
 // a block is NB consecutive groups (BS = NB * spg >= 8 consecutive sites) whose links and
 // caller ids are staged together. NLS block slots cover the 2D-group lookahead of links.
@@ -423,14 +468,17 @@ struct GroupPos {
     }
 };
 
-template <int DEG, int PM, int LM, int D>
-__global__ void __launch_bounds__(kThreads) pass32_staged(const PassArgs a) {
+// LOG2R >= 0 fixes the replica count at compile time (the batched case R = 32); -1 reads it
+// from the arguments.
+// Depth 2 fits three blocks per SM in shared memory; the register cap keeps them resident.
+template <int DEG, int PM, int LM, int D, int LOG2R>
+__global__ void __launch_bounds__(kThreads, D == 2 ? 3 : 2) pass32_staged(const PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const RunState *rs_ = a.run;
     const uint32_t t = rs_->t;
     const uint32_t step_idx = rs_->rec / rs_->mcs;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int log2R = a.log2R, R = 1 << log2R;
+    const int log2R = LOG2R >= 0 ? LOG2R : a.log2R, R = 1 << log2R;
     const StagedGeom G = staged_geom(DEG, D, log2R);
     const int r = lane & (R - 1), my = lane >> log2R;  // replica, site within the group
     unsigned char *wbase = smem + (size_t)warp * G.warp_bytes;
@@ -482,10 +530,10 @@ __global__ void __launch_bounds__(kThreads) pass32_staged(const PassArgs a) {
         for (int j = 0; j < DEG / 2; ++j) {
             const int4 q = lk[j];
             VEGAS_CHECK(q.x >= 0 && q.x < a.n_sites_total && q.z >= 0 && q.z < a.n_sites_total, 7, q.x);
-            cp16(dst + (2 * j) * 32, Sr + ((int64_t)q.x << log2R));
-            cp16(dst + (2 * j + 1) * 32, Sr + ((int64_t)q.z << log2R));
+            cp16(dst + (2 * j) * 32, Sr + (int64_t)q.x * R);
+            cp16(dst + (2 * j + 1) * 32, Sr + (int64_t)q.z * R);
         }
-        cp16(dst + DEG * 32, Sr + ((int64_t)g << log2R));
+        cp16(dst + DEG * 32, Sr + (int64_t)g * R);
     };
 
     // prologue: links of every block whose first group is among the first 2D, then the
@@ -507,6 +555,8 @@ __global__ void __launch_bounds__(kThreads) pass32_staged(const PassArgs a) {
     int sb_next = g0 + nb_pro * bstride, ls_next = nb_pro;
     int rsl = 0;
     Acc32 acc;
+    bool nan_seen = false;
+    const bool log_accepts = a.alog && t < a.alog_mcs;
     for (int k = 0; pk.sbase < g_end; ++k) {
         cp_wait<D - 1>();
         __syncwarp();
@@ -526,40 +576,8 @@ __global__ void __launch_bounds__(kThreads) pass32_staged(const PassArgs a) {
                 skip = true;
             }
 #endif
-            if (!skip) {
-                const Site32 p = site_params32(a, PM, g);
-                float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-#pragma unroll
-                for (int j = 0; j < DEG / 2; ++j) {
-                    const int4 q = lk[j];
-                    link32(row[(2 * j) * 32], __int_as_float(q.y), LM == 2 && q.x < a.lower_end, hx, hy, hz, lx, ly,
-                           lz);
-                    link32(row[(2 * j + 1) * 32], __int_as_float(q.w), LM == 2 && q.z < a.lower_end, hx, hy, hz, lx,
-                           ly, lz);
-                }
-                if (LM == 1) {
-                    lx = hx;
-                    ly = hy;
-                    lz = hz;
-                }
-                const float4 Si = row[DEG * 32];
-                uint4 c = make_uint4(orig, t, inst, kPurposeTrial32);
-#pragma unroll
-                for (int q = 0; q < 10; ++q) {  // Philox4x32-10 with the round keys above
-                    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-                    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-                    c = make_uint4(hi1 ^ c.y ^ rk0[q], lo1, hi0 ^ c.w ^ rk1[q], lo0);
-                }
-                float4 Sn;
-                bool ok, bad;
-                float e_i;
-                attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, c, Sn, ok, e_i, bad);
-                if (bad) atomicOr(a.err, kErrNaN);
-                if (ok) S[((int64_t)g << log2R) + r] = Sn;
-                if (a.alog && t < a.alog_mcs)
-                    a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
-                acc.add(e_i, Sn);
-            }
+            if (!skip) staged_attempt<DEG, PM, LM>(a, lk, row, orig, g, r, R, t, inst, rk0, rk1, beta, B, S, acc, nan_seen,
+                                              log_accepts);
         }
         __syncwarp();
         if (k == k_issue) {
@@ -575,6 +593,115 @@ __global__ void __launch_bounds__(kThreads) pass32_staged(const PassArgs a) {
         rsl = (rsl + 1 == D) ? 0 : rsl + 1;
     }
     cp_wait<0>();
+    if (nan_seen) atomicOr(a.err, kErrNaN);
+    acc.flush();
+    block_partials(acc.d, R, a.partial + (int64_t)blockIdx.x * R * 4);
+}
+
+// Replica-batched sweep (R = 32): one warp = one site x 32 replicas, depth-2 pipeline. A
+// warp owns blocks of eight consecutive sites (block b starts at g0 + b * bstride); the
+// eight groups of a block are unrolled, so every ring slot and offset is a constant:
+// group j of block b computes from row slot j & 1 and link slot b & 1; at j = 4 the links of
+// the next block are copied; rows of group j + 2 (the next block's first two at j = 6, 7)
+// are copied at the end of group j.
+template <int PM, int LM>
+__global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
+    constexpr int DEG = 6, D = 2, BS = 8, R = 32;
+    constexpr int ROWS = D * (DEG + 1) * 32 * 16;
+    constexpr int LINK_BYTES = BS * DEG * 8;
+    constexpr int SLOT = LINK_BYTES + BS * 4;
+    constexpr int WARP_BYTES = ROWS + 2 * SLOT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const RunState *rs_ = a.run;
+    const uint32_t t = rs_->t;
+    const uint32_t step_idx = rs_->rec / rs_->mcs;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = lane;
+    unsigned char *wbase = smem + warp * WARP_BYTES;
+    float4 *rows = (float4 *)wbase;
+    unsigned char *lslots = wbase + ROWS;
+    float4 *S = (float4 *)a.spins;
+    const float4 *Sr = S + r;
+    const int2 *E = (const int2 *)a.edges;
+    const uint32_t inst = (uint32_t)(a.inst0 + r);
+    const double *sc = rs_->sched + ((int64_t)step_idx * a.n_inst + a.inst_local0 + r) * 2;
+    const float beta = (float)sc[0], B = (float)sc[1];
+    const int g_end = a.g_end;
+    const int nwarps = blockDim.x >> 5;
+    const int bstride = gridDim.x * nwarps * BS;
+    const int g0 = a.g_begin + (blockIdx.x * nwarps + warp) * BS;
+    uint32_t rk0[10], rk1[10];
+    {
+        uint32_t x = (uint32_t)a.seed, y = (uint32_t)(a.seed >> 32);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            rk0[q] = x;
+            rk1[q] = y;
+            x += 0x9E3779B9u;
+            y += 0xBB67AE85u;
+        }
+    }
+    auto issue_links = [&](int sb, int slot) {
+        if (sb >= g_end) return;
+        const int ns = min(BS, g_end - sb);
+        unsigned char *dst = lslots + slot * SLOT;
+        const unsigned char *src = (const unsigned char *)(E + a.edge_base + (int64_t)(sb - a.site_off) * DEG);
+        VEGAS_CHECK(sb >= a.g_begin && sb + ns <= a.n_sites_total, 11, sb);
+        VEGAS_CHECK(a.edge_base + (int64_t)(sb - a.site_off + ns) * DEG <= a.n_edges_total, 12, sb);
+        VEGAS_CHECK(((uintptr_t)src & 15) == 0, 13, sb);
+        if (lane < ns * (DEG / 2)) cp16(dst + 16 * lane, src + 16 * lane);
+        if (lane < ns) cp4(dst + LINK_BYTES + 4 * lane, a.orig + sb + lane);
+    };
+    auto issue_rows = [&](int g, int lslot, int j, int rslot) {
+        if (g >= g_end) return;
+        const int4 *lk = (const int4 *)(lslots + lslot * SLOT) + j * (DEG / 2);
+        float4 *dst = rows + rslot * (DEG + 1) * 32 + lane;
+        VEGAS_CHECK(g < a.n_sites_total, 14, g);
+#pragma unroll
+        for (int q = 0; q < DEG / 2; ++q) {
+            const int4 l = lk[q];
+            VEGAS_CHECK(l.x >= 0 && l.x < a.n_sites_total && l.z >= 0 && l.z < a.n_sites_total, 15, l.x);
+            cp16(dst + (2 * q) * 32, Sr + (int64_t)l.x * R);
+            cp16(dst + (2 * q + 1) * 32, Sr + (int64_t)l.z * R);
+        }
+        cp16(dst + DEG * 32, Sr + (int64_t)g * R);
+    };
+
+    issue_links(g0, 0);
+    cp_commit();
+    cp_wait<0>();
+    __syncwarp();
+    issue_rows(g0, 0, 0, 0);
+    cp_commit();
+    issue_rows(g0 + 1, 0, 1, 1);
+    cp_commit();
+    Acc32 acc;
+    bool nan_seen = false;
+    const bool log_accepts = a.alog && t < a.alog_mcs;
+    int ls = 0;
+    for (int sb = g0; sb < g_end; sb += bstride, ls ^= 1) {
+#pragma unroll
+        for (int j = 0; j < BS; ++j) {
+            cp_wait<D - 1>();
+            __syncwarp();
+            const int g = sb + j;
+            if (g < g_end) {
+                const unsigned char *slot = lslots + ls * SLOT;
+                const uint32_t orig = ((const uint32_t *)(slot + LINK_BYTES))[j];
+                staged_attempt<DEG, PM, LM>(a, (const int4 *)slot + j * (DEG / 2), rows + (j & 1) * (DEG + 1) * 32 + lane,
+                                            orig, g, r, R, t, inst, rk0, rk1, beta, B, S, acc, nan_seen, log_accepts);
+            }
+            __syncwarp();
+            if (j == 4) issue_links(sb + bstride, ls ^ 1);
+            if (j + 2 < BS)
+                issue_rows(sb + j + 2, ls, j + 2, j & 1);
+            else
+                issue_rows(sb + bstride + j + 2 - BS, ls ^ 1, j + 2 - BS, j & 1);
+            cp_commit();
+        }
+    }
+    cp_wait<0>();
+    if (nan_seen) atomicOr(a.err, kErrNaN);
     acc.flush();
     block_partials(acc.d, R, a.partial + (int64_t)blockIdx.x * R * 4);
 }
@@ -723,23 +850,33 @@ PassFn select_direct(int pm, int lm) {
 template <int D>
 PassFn select_staged6(int pm, int lm) {
     static const PassFn tab[3][3] = {
-        {pass32_staged<6, 0, 0, D>, pass32_staged<6, 0, 1, D>, pass32_staged<6, 0, 2, D>},
-        {pass32_staged<6, 1, 0, D>, pass32_staged<6, 1, 1, D>, pass32_staged<6, 1, 2, D>},
-        {pass32_staged<6, 2, 0, D>, pass32_staged<6, 2, 1, D>, pass32_staged<6, 2, 2, D>},
+        {pass32_staged<6, 0, 0, D, -1>, pass32_staged<6, 0, 1, D, -1>, pass32_staged<6, 0, 2, D, -1>},
+        {pass32_staged<6, 1, 0, D, -1>, pass32_staged<6, 1, 1, D, -1>, pass32_staged<6, 1, 2, D, -1>},
+        {pass32_staged<6, 2, 0, D, -1>, pass32_staged<6, 2, 1, D, -1>, pass32_staged<6, 2, 2, D, -1>},
+    };
+    return tab[pm][lm];
+}
+
+PassFn select_r32(int pm, int lm) {
+    static const PassFn tab[3][3] = {
+        {pass32_r32<0, 0>, pass32_r32<0, 1>, pass32_r32<0, 2>},
+        {pass32_r32<1, 0>, pass32_r32<1, 1>, pass32_r32<1, 2>},
+        {pass32_r32<2, 0>, pass32_r32<2, 1>, pass32_r32<2, 2>},
     };
     return tab[pm][lm];
 }
 
 bool use_staged(const PassArgs &a) { return a.deg == 6 && a.depth >= 2; }
+bool use_r32(const PassArgs &a) { return use_staged(a) && a.log2R == 5 && a.depth == 2; }
 
-int staged_smem(const PassArgs &a) { return (kThreads / 32) * staged_geom(6, a.depth, a.log2R).warp_bytes; }
+int staged_smem(const PassArgs &a) {
+    if (use_r32(a)) return (kThreads / 32) * (2 * 7 * 32 * 16 + 2 * (8 * 6 * 8 + 8 * 4));
+    return (kThreads / 32) * staged_geom(6, a.depth, a.log2R).warp_bytes;
+}
 
 PassFn select_staged(const PassArgs &a) {
-    switch (a.depth) {
-        case 2: return select_staged6<2>(a.params_mode, a.lower_mode);
-        case 4: return select_staged6<4>(a.params_mode, a.lower_mode);
-        default: return select_staged6<3>(a.params_mode, a.lower_mode);
-    }
+    if (use_r32(a)) return select_r32(a.params_mode, a.lower_mode);
+    return a.depth == 2 ? select_staged6<2>(a.params_mode, a.lower_mode) : select_staged6<3>(a.params_mode, a.lower_mode);
 }
 
 PassFn select32(const PassArgs &a) {
