@@ -36,8 +36,8 @@ L_SIDE, REPLICAS, MCS, SEED = 256, 32, 200, 1
 # algorithmic bytes per attempt: 16 B read + 16 B write of the FP32 spin (float4), plus one
 # row of six (int32 col, f32 J) links = 48 B shared by the 32 replicas that sweep it together
 BYTES_PER_ATTEMPT = 16 + 16 + 48.0 / REPLICAS
-PASS_KERNEL = "pass32_kernel"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pass32_sg256x32.txt")
+PASS_KERNEL = "pass32_r32"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pass32_r32_sg256x32.txt")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1803_07030_gb300", "csrc", "vegas_kernels.cu")
 
 
