@@ -59,6 +59,15 @@ struct vegas_ctx {
     uint8_t *d_alog = nullptr;
     int64_t alog_bytes = 0;
     int64_t device_bytes = 0;
+    // resident (persistent) sweep
+    ResidentInst *d_insts = nullptr;
+    int32_t *d_cstart = nullptr;
+    uint32_t *d_queue = nullptr;
+    ResidentArgs res{};
+    int res_threads = 256, res_grid = 1;
+    bool res_eligible = false, tuned = false;
+    int32_t max_instance_sites = 0;
+    double tune_ms[2] = {0.0, 0.0};  // per-MCS time of the stream and resident sweeps when tuned
     // graph of one MCS
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -107,7 +116,8 @@ void free_all(vegas_ctx *c) {
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
     void *bufs[] = {c->d_spins, c->d_edges, c->d_p0, c->d_p1, c->d_pk, c->d_rowptr, c->d_slot_base, c->d_orig,
-                    c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog};
+                    c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog,
+                    c->d_insts, c->d_cstart, c->d_queue};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -198,6 +208,8 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     if (o.accept_log_mcs < 0 || o.inst_base < 0 || o.max_blocks < 0) return fail(nullptr, VEGAS_EINVAL, "negative option");
     if (o.variant < -1 || o.variant > 1) return fail(nullptr, VEGAS_EINVAL, "variant must be -1, 0 or 1");
     if (o.pipeline_depth < 0 || o.pipeline_depth > 3) return fail(nullptr, VEGAS_EINVAL, "pipeline_depth must be 0..3");
+    if (o.variant == 1 && o.precision != 32)
+        return fail(nullptr, VEGAS_EINVAL, "the resident sweep (variant 1) is FP32 only");
     if ((int64_t)o.inst_base + (int64_t)n_samples * o.replicas > (int64_t)UINT32_MAX)
         return fail(nullptr, VEGAS_EINVAL, "instance ids exceed 32 bits");
 
@@ -485,6 +497,84 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     rs0.mcs = 1;
     H2D(c->d_run, &rs0, sizeof rs0);
 
+    // ---- resident sweep: one entry per instance, largest first
+    if (!p64) {
+        std::vector<ResidentInst> insts;
+        std::vector<int32_t> h_cs;
+        int64_t alog_off = 0;
+        for (int32_t s = 0; s < n_samples; ++s) {
+            const SampleInfo &si = c->samples[(size_t)s];
+            const int32_t cls_off = (int32_t)h_cs.size();
+            for (int32_t q = 0; q <= si.n_colours; ++q) h_cs.push_back(si.site_off + si.cstart[(size_t)q]);
+            c->max_instance_sites = std::max(c->max_instance_sites, si.n);
+            for (int32_t r = 0; r < R; ++r) {
+                ResidentInst I;
+                std::memset(&I, 0, sizeof I);
+                I.g_begin = si.site_off;
+                I.g_end = si.site_off + si.n;
+                I.cls_off = cls_off;
+                I.n_colours = si.n_colours;
+                I.inst_id = o.inst_base + s * R + r;
+                I.inst_local = s * R + r;
+                I.r = r;
+                I.params_mode = si.uniform_params ? (si.has_anisotropy ? 1 : 0) : 2;
+                I.n_sample_sites = si.n;
+                I.alog_base = alog_off;
+                I.u = SiteParams32{(float)si.u.nx, (float)si.u.ny, (float)si.u.nz, (float)si.u.s, (float)si.u.ex,
+                                   (float)si.u.ey, (float)si.u.ez, (float)si.u.k,  (float)si.u.kc};
+                insts.push_back(I);
+            }
+            alog_off += (int64_t)si.n * R;
+        }
+        std::stable_sort(insts.begin(), insts.end(), [](const ResidentInst &x, const ResidentInst &y) {
+            return (x.g_end - x.g_begin) > (y.g_end - y.g_begin);
+        });
+        DALLOC(c->d_insts, sizeof(ResidentInst) * insts.size());
+        DALLOC(c->d_cstart, sizeof(int32_t) * h_cs.size());
+        DALLOC(c->d_queue, sizeof(uint32_t));
+        H2D(c->d_insts, insts.data(), sizeof(ResidentInst) * insts.size());
+        H2D(c->d_cstart, h_cs.data(), sizeof(int32_t) * h_cs.size());
+        c->res_threads = c->max_instance_sites >= 4096 ? 512 : 256;
+        c->res_grid = (int)std::min<int64_t>((int64_t)insts.size(), (int64_t)c->sm_count *
+                                                                       resident_blocks_per_sm(c->res_threads));
+        ResidentArgs &ra = c->res;
+        std::memset(&ra, 0, sizeof ra);
+        ra.spins = c->d_spins;
+        ra.edges = c->d_edges;
+        ra.row_ptr = c->d_rowptr;
+        ra.orig = c->d_orig;
+        ra.p0 = c->d_p0;
+        ra.p1 = c->d_p1;
+        ra.pk = c->d_pk;
+        ra.insts = c->d_insts;
+        ra.cstart = c->d_cstart;
+        ra.queue = c->d_queue;
+        ra.err = c->d_err;
+        ra.alog = c->d_alog;
+        ra.seed = o.seed;
+        ra.alog_stride = (int64_t)n_sites * R;
+        ra.alog_mcs = (uint32_t)o.accept_log_mcs;
+        ra.n_items = (int32_t)insts.size();
+        ra.n_inst = c->n_inst;
+        ra.log2R = c->log2R;
+        // one block per instance only pays while instances are small
+        c->res_eligible = c->max_instance_sites <= (1 << 18);
+    }
+    if (o.variant == 1) {
+        if (!c->res_eligible) {
+            c->err = "variant 1 (resident) needs FP32 and samples of at most 262144 sites";
+            return bail(VEGAS_EINVAL);
+        }
+        c->variant = 1;
+        c->tuned = true;
+    } else if (o.variant == 0 || !c->res_eligible) {
+        c->variant = 0;
+        c->tuned = true;
+    } else {
+        // automatic: timed on the first run; until then, the shape suggests one
+        c->variant = (c->n_inst >= 2 && c->max_instance_sites <= 16384) ? 1 : 0;
+    }
+
     // ---- initial state
     for (int32_t s = 0; s < n_samples; ++s) {
         const SampleInfo &si = c->samples[(size_t)s];
@@ -581,9 +671,8 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
     const bool use_graph = c->opt.graphs && !c->opt.timing;
     if (use_graph && (st = build_graph(c)) != VEGAS_OK) return st;
     std::vector<cudaEvent_t> ev;
-    std::vector<float> ev_ms;
     if (c->opt.timing) {
-        ev.resize(2 * c->passes.size() * (size_t)mcs);
+        ev.resize(2 * c->passes.size() * (size_t)mcs + 2);
         for (auto &x : ev) CK(c, cudaEventCreate(&x));
     }
     cudaEvent_t e0, e1;
@@ -593,8 +682,18 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
     RenormArgs ra{c->d_spins, c->d_norm, c->n_sites * c->R, c->log2R};
     const int rgrid = (int)std::min<int64_t>((ra.n_work + 255) / 256, (int64_t)c->sm_count * 8);
     double sweep_ms = 0.0;
-    for (int32_t s = 0; s < n_steps; ++s) {
-        for (int32_t m = 0; m < mcs; ++m) {
+    const uint32_t t_run = c->t;
+    // device run state for the per-class sweep (the resident sweep takes its own arguments)
+    auto set_state = [&](uint32_t t, uint32_t rec) -> vegas_status {
+        RunState r2 = rs;
+        r2.t = t;
+        r2.rec = rec;
+        CK(c, cudaMemcpyAsync(c->d_run, &r2, sizeof r2, cudaMemcpyHostToDevice, c->stream));
+        return VEGAS_OK;
+    };
+    // MCS m0 .. m0+n-1 of the current step with one launch per colour class
+    auto stream_mcs = [&](int32_t m0, int32_t n) -> vegas_status {
+        for (int32_t m = m0; m < m0 + n; ++m) {
             if (use_graph) {
                 CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
             } else if (c->opt.timing) {
@@ -607,17 +706,85 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             c->kernel_launches += (int64_t)c->passes.size() + 1;
             c->sweep_launches += (int64_t)c->passes.size();
         }
+        return VEGAS_OK;
+    };
+    // MCS m0 .. m0+n-1 of step s in one persistent launch
+    auto resident = [&](int32_t s, int32_t m0, int32_t n) -> vegas_status {
+        if (n <= 0) return VEGAS_OK;
+        CK(c, cudaMemsetAsync(c->d_queue, 0, sizeof(uint32_t), c->stream));
+        ResidentArgs a = c->res;
+        a.sched = c->d_sched;
+        a.hist = c->d_hist;
+        a.t0 = t_run + (uint32_t)s * (uint32_t)mcs + (uint32_t)m0;
+        a.mcs = n;
+        a.rec0 = s * mcs + m0;
+        a.step = s;
+        if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 2], c->stream));
+        launch_resident(a, c->res_grid, c->res_threads, c->stream);
+        if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 1], c->stream));
+        c->kernel_launches++;
+        c->sweep_launches++;
+        return VEGAS_OK;
+    };
+    for (int32_t s = 0; s < n_steps; ++s) {
+        int32_t m0 = 0;
+        if (!c->tuned && mcs >= 2) {
+            // autotune: time a few MCS of each sweep on the real chain (both give the same
+            // spins) and keep the faster for this context
+            const int32_t probe = std::max(1, std::min(4, mcs / 4));
+            cudaEvent_t a0, a1, b0, b1;
+            CK(c, cudaEventCreate(&a0));
+            CK(c, cudaEventCreate(&a1));
+            CK(c, cudaEventCreate(&b0));
+            CK(c, cudaEventCreate(&b1));
+            CK(c, cudaEventRecord(a0, c->stream));
+            if ((st = resident(s, 0, probe)) != VEGAS_OK) return st;
+            CK(c, cudaEventRecord(a1, c->stream));
+            if ((st = set_state(t_run + (uint32_t)s * (uint32_t)mcs + (uint32_t)probe, (uint32_t)(s * mcs + probe))) !=
+                VEGAS_OK)
+                return st;
+            CK(c, cudaEventRecord(b0, c->stream));
+            if ((st = stream_mcs(probe, probe)) != VEGAS_OK) return st;
+            CK(c, cudaEventRecord(b1, c->stream));
+            CK(c, cudaStreamSynchronize(c->stream));
+            float tr = 0.f, ts = 0.f;
+            CK(c, cudaEventElapsedTime(&tr, a0, a1));
+            CK(c, cudaEventElapsedTime(&ts, b0, b1));
+            cudaEventDestroy(a0);
+            cudaEventDestroy(a1);
+            cudaEventDestroy(b0);
+            cudaEventDestroy(b1);
+            c->tune_ms[0] = ts / probe;
+            c->tune_ms[1] = tr / probe;
+            c->variant = (tr < ts) ? 1 : 0;
+            c->tuned = true;
+            sweep_ms += tr + ts;
+            m0 = 2 * probe;
+        }
+        if (c->variant == 1) {
+            if ((st = resident(s, m0, mcs - m0)) != VEGAS_OK) return st;
+        } else {
+            if ((st = set_state(t_run + (uint32_t)s * (uint32_t)mcs + (uint32_t)m0, (uint32_t)(s * mcs + m0))) != VEGAS_OK)
+                return st;
+            if ((st = stream_mcs(m0, mcs - m0)) != VEGAS_OK) return st;
+        }
         if (c->precision == 64)
             launch_renorm64(ra, rgrid, c->stream);
         else
             launch_renorm32(ra, rgrid, c->stream);
         c->kernel_launches++;
-        if (c->opt.timing) {  // read this step's pass timings before the events are reused
+        if (c->opt.timing) {  // read this step's sweep timings before the events are reused
             CK(c, cudaStreamSynchronize(c->stream));
-            for (size_t k = 0; k + 1 < ev.size(); k += 2) {
+            if (c->variant == 1) {
                 float ms = 0.f;
-                CK(c, cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+                CK(c, cudaEventElapsedTime(&ms, ev[ev.size() - 2], ev[ev.size() - 1]));
                 sweep_ms += ms;
+            } else {
+                for (size_t k = (size_t)m0 * 2 * c->passes.size(); k + 1 < ev.size() - 2; k += 2) {
+                    float ms = 0.f;
+                    CK(c, cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+                    sweep_ms += ms;
+                }
             }
         }
     }

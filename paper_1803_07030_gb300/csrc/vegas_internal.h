@@ -147,6 +147,46 @@ struct InitArgs {
     int32_t log2R;
 };
 
+// One instance of the resident sweep: a sample's sites and one of its replicas.
+struct ResidentInst {
+    int32_t g_begin, g_end;    // the sample's global sites
+    int32_t cls_off;           // first entry of the sample's class starts in ResidentArgs::cstart
+    int32_t n_colours;
+    int32_t inst_id;           // Philox instance id
+    int32_t inst_local;        // schedule and history column
+    int32_t r;                 // replica within the sample
+    int32_t params_mode;       // 0, 1, 2 as for PassArgs
+    int32_t n_sample_sites;
+    int32_t pad_;
+    int64_t alog_base;         // accept-log offset of replica 0 of the sample
+    SiteParams32 u;
+};
+
+// Persistent sweep: every block takes instances from a queue (largest first) and runs all
+// MCS of one temperature/field step on each, colour class after colour class.
+struct ResidentArgs {
+    void *spins;
+    const void *edges;         // int2 (col, J float bits)
+    const int64_t *row_ptr;
+    const int32_t *orig;
+    const void *p0, *p1, *pk;  // per-site parameters (samples with params_mode 2)
+    const ResidentInst *insts; // [n_items], largest first
+    const int32_t *cstart;     // class starts (global sites), n_colours + 1 per sample
+    const double *sched;       // [n_steps][n_inst][2]
+    double *hist;              // [records][n_inst][4]
+    uint32_t *queue;           // work counter, zero before the launch
+    uint32_t *err;
+    uint8_t *alog;
+    uint64_t seed;
+    int64_t alog_stride;
+    uint32_t alog_mcs;
+    int32_t n_items, n_inst, log2R;
+    uint32_t t0;               // global MCS index of the launch's first MCS
+    int32_t mcs;               // MCS in this launch
+    int32_t rec0;              // history record of the first MCS
+    int32_t step;              // schedule row
+};
+
 // ------------------------------------------------------------------ launchers
 
 // Sweep launch of one colour class; lower_mode, params_mode and deg pick the compiled variant.
@@ -164,5 +204,9 @@ void launch_scatter(void *spins, int precision, int64_t site_off, int64_t n, int
 
 // Blocks per SM the pass kernels reach at kThreads threads (occupancy query).
 int pass_blocks_per_sm(int precision, const PassArgs &a);
+
+// Resident sweep with `threads` per block (256, 512 or 1024).
+void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream);
+int resident_blocks_per_sm(int threads);
 
 }  // namespace vegas

@@ -304,6 +304,39 @@ __device__ __forceinline__ Site32 site_params32(const PassArgs &a, int PMv, int 
     return p;
 }
 
+// One attempt of the direct path: gathers the neighbour rows with plain loads (row order),
+// draws the trial, decides, writes, and adds the site's share of E and M. Returns the
+// decision.
+template <int PM, int LM>
+__device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const int64_t *row_ptr, int g, int r, int R,
+                                               int lower_end, uint32_t orig, const Site32 &p, float beta, float B,
+                                               uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1, Acc32 &acc,
+                                               bool &nan_seen) {
+    const int64_t si = (int64_t)g * R + r;
+    const float4 Si = S[si];
+    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+    const int64_t e0 = __ldg(row_ptr + g), e1 = __ldg(row_ptr + g + 1);
+    for (int64_t e = e0; e < e1; ++e) {
+        const int2 ed = __ldg(E + e);
+        link32(__ldg(S + (int64_t)ed.x * R + r), __int_as_float(ed.y), LM == 2 && ed.x < lower_end, hx, hy, hz, lx,
+               ly, lz);
+    }
+    if (LM == 1) {
+        lx = hx;
+        ly = hy;
+        lz = hz;
+    }
+    const uint4 rw = philox10(make_uint4(orig, t, inst, kPurposeTrial32), k0, k1);
+    float4 Sn;
+    bool ok, bad;
+    float e_i;
+    attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, rw, Sn, ok, e_i, bad);
+    nan_seen |= bad;
+    if (ok) S[si] = Sn;
+    acc.add(e_i, Sn);
+    return ok;
+}
+
 // ------------------------------------------------------------------ FP32 colour pass (direct)
 // Any row length: reads row_ptr and gathers neighbours with plain loads.
 // PM: params_mode (0 uniform without anisotropy, 1 uniform, 2 per site).
@@ -329,31 +362,12 @@ __global__ void __launch_bounds__(kThreads) pass32_kernel(const PassArgs a) {
     for (int64_t w = w0; w < n_work; w += stride) {
         const int g = a.g_begin + (int)(w >> a.log2R);
         const uint32_t orig = (uint32_t)__ldg(a.orig + g);
-        const Site32 p = site_params32(a, PM, g);
-        const int64_t si = (int64_t)g * R + r;
-        const float4 Si = S[si];
-        float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-        const int64_t e0 = __ldg(a.row_ptr + g), e1 = __ldg(a.row_ptr + g + 1);
-        for (int64_t e = e0; e < e1; ++e) {
-            const int2 ed = __ldg(E + e);
-            link32(__ldg(S + (int64_t)ed.x * R + r), __int_as_float(ed.y), LM == 2 && ed.x < a.lower_end, hx, hy,
-                   hz, lx, ly, lz);
-        }
-        if (LM == 1) {
-            lx = hx;
-            ly = hy;
-            lz = hz;
-        }
-        const uint4 rw = philox10(make_uint4(orig, t, inst, kPurposeTrial32), k0, k1);
-        float4 Sn;
-        bool ok, bad;
-        float e_i;
-        attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, rw, Sn, ok, e_i, bad);
-        if (bad) atomicOr(a.err, kErrNaN);
-        if (ok) S[si] = Sn;
+        bool nan_seen = false;
+        const bool ok = direct_attempt<PM, LM>(S, E, a.row_ptr, g, r, R, a.lower_end, orig, site_params32(a, PM, g), beta,
+                                               B, t, inst, k0, k1, acc, nan_seen);
+        if (nan_seen) atomicOr(a.err, kErrNaN);
         if (a.alog && t < a.alog_mcs)
             a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
-        acc.add(e_i, Sn);
     }
     acc.flush();
     block_partials(acc.d, R, a.partial + (int64_t)blockIdx.x * R * 4);
@@ -706,6 +720,92 @@ __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
     block_partials(acc.d, R, a.partial + (int64_t)blockIdx.x * R * 4);
 }
 
+// ------------------------------------------------------------------ resident (persistent) sweep
+// Every block takes instances from a queue (largest first; an atomic ticket, no waiting)
+// and runs all MCS of the step on it: colour class after colour class with __syncthreads
+// in between, then a fixed-order block sum of E and M written straight into the history.
+// Used for batches of many small, uneven samples, where one launch per colour class of
+// every sample would cost far more than the sweep itself.
+__device__ __forceinline__ Site32 resident_params(const ResidentArgs &a, const ResidentInst &I, int g) {
+    if (I.params_mode == 2) {
+        const float4 p0 = __ldg((const float4 *)a.p0 + g), p1 = __ldg((const float4 *)a.p1 + g);
+        return Site32{p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, __ldg((const float *)a.pk + g)};
+    }
+    return Site32{I.u.nx, I.u.ny, I.u.nz, I.u.s, I.u.ex, I.u.ey, I.u.ez, I.u.k, I.u.kc};
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
+    __shared__ int s_item;
+    __shared__ double s_red[NT / 32][4];
+    float4 *S = (float4 *)a.spins;
+    const int2 *E = (const int2 *)a.edges;
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    const int R = 1 << a.log2R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool nan_seen = false;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(a.queue, 1u);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= a.n_items) break;
+        const ResidentInst I = a.insts[item];
+        const double *sc = a.sched + ((int64_t)a.step * a.n_inst + I.inst_local) * 2;
+        const float beta = (float)sc[0], B = (float)sc[1];
+        const uint32_t inst = (uint32_t)I.inst_id;
+        for (int m = 0; m < a.mcs; ++m) {
+            const uint32_t t = a.t0 + (uint32_t)m;
+            const bool log_accepts = a.alog && t < a.alog_mcs;
+            Acc32 acc;
+            for (int c = 0; c < I.n_colours; ++c) {
+                const int cb = a.cstart[I.cls_off + c], ce = a.cstart[I.cls_off + c + 1];
+                for (int g = cb + (int)threadIdx.x; g < ce; g += NT) {
+                    const uint32_t orig = (uint32_t)__ldg(a.orig + g);
+                    const Site32 p = resident_params(a, I, g);
+                    bool ok;
+                    if (I.params_mode == 2)
+                        ok = direct_attempt<2, 2>(S, E, a.row_ptr, g, I.r, R, cb, orig, p, beta, B, t, inst, k0, k1, acc,
+                                                  nan_seen);
+                    else if (I.params_mode == 1)
+                        ok = direct_attempt<1, 2>(S, E, a.row_ptr, g, I.r, R, cb, orig, p, beta, B, t, inst, k0, k1, acc,
+                                                  nan_seen);
+                    else
+                        ok = direct_attempt<0, 2>(S, E, a.row_ptr, g, I.r, R, cb, orig, p, beta, B, t, inst, k0, k1, acc,
+                                                  nan_seen);
+                    if (log_accepts)
+                        a.alog[(int64_t)t * a.alog_stride + I.alog_base + (int64_t)I.r * I.n_sample_sites + orig] =
+                            ok ? 1 : 0;
+                }
+                __syncthreads();
+            }
+            acc.flush();
+            double v[4] = {acc.d[0], acc.d[1], acc.d[2], acc.d[3]};
+            for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s_red[warp][q] = v[q];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double sum[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int w = 0; w < NT / 32; ++w) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) sum[q] += s_red[w][q];
+                }
+                double *h = a.hist + ((int64_t)(a.rec0 + m) * a.n_inst + I.inst_local) * 4;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) h[q] = sum[q];
+            }
+            __syncthreads();
+        }
+    }
+    if (nan_seen) atomicOr(a.err, kErrNaN);
+}
+
 // ------------------------------------------------------------------ per-MCS reduction
 // One warp per instance sums its sample's block partials over every colour class in a
 // fixed order and appends the record; the last block to finish advances the MCS
@@ -924,6 +1024,26 @@ void launch_gather(void *spins, int precision, int64_t site_off, int64_t n, int3
 void launch_scatter(void *spins, int precision, int64_t site_off, int64_t n, int32_t log2R, int32_t r,
                     const double *in3, int grid, void *stream) {
     scatter_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(spins, precision, site_off, n, log2R, r, in3);
+}
+
+void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream) {
+    if (threads >= 1024)
+        resident32_kernel<1024><<<grid, 1024, 0, (cudaStream_t)stream>>>(a);
+    else if (threads >= 512)
+        resident32_kernel<512><<<grid, 512, 0, (cudaStream_t)stream>>>(a);
+    else
+        resident32_kernel<256><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+}
+
+int resident_blocks_per_sm(int threads) {
+    int nb = 0;
+    if (threads >= 1024)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, resident32_kernel<1024>, 1024, 0);
+    else if (threads >= 512)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, resident32_kernel<512>, 512, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, resident32_kernel<256>, 256, 0);
+    return nb > 0 ? nb : 1;
 }
 
 int pass_blocks_per_sm(int precision, const PassArgs &a) {

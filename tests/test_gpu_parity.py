@@ -206,6 +206,55 @@ def test_fp64_many_items_per_thread_bitwise():
             assert np.array_equal(c.spins(i), ref["spins"][i])
 
 
+# --------------------------------------------------------------------------- resident sweep
+# One persistent launch per temperature/field step: each block takes whole instances
+# (largest first) and runs every MCS on them. Same per-site arithmetic and random numbers
+# as the per-class sweep, so the spins must agree bit for bit.
+
+def _uneven_batch():
+    return nanoparticle_batch(7, seed=11, r_max=7.0) + [core_shell_particle(seed=2, radius=5.0, core_radius=3.5)]
+
+
+@pytest.mark.parametrize("R", [1, 4])
+def test_resident_sweep_equals_per_class_sweep(R):
+    samples = _uneven_batch()
+    n = len(samples) * R
+    T = np.stack([np.linspace(0.3, 2.5, 3) * (1 + 0.05 * i) for i in range(n)])
+    B = np.stack([np.array([0.4, -0.2, 0.1]) * (1 + 0.1 * i) for i in range(n)])
+    with ctx(samples, replicas=R, seed=13, variant=0, accept_log_mcs=3) as a, \
+            ctx(samples, replicas=R, seed=13, variant=1, accept_log_mcs=3) as b:
+        a.run(T, B, 7)
+        b.run(T, B, 7)
+        assert a.stats()["variant"] == 0 and b.stats()["variant"] == 1
+        for i in range(n):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+        for i in range(n):
+            assert_fp32_history_close(a.history()[i], b.history()[i], samples[i // R].n_sites)
+        assert np.array_equal(a.accept_log(), b.accept_log())
+
+
+def test_resident_split_runs_and_autotune():
+    samples = _uneven_batch()
+    T = np.linspace(0.5, 2.0, len(samples))[:, None] * np.ones((1, 2))
+    with ctx(samples, seed=17, variant=1) as a, ctx(samples, seed=17, variant=-1) as b, \
+            ctx(samples, seed=17, variant=1) as c:
+        a.run(T, np.zeros_like(T), 12)
+        b.run(T, np.zeros_like(T), 12)  # first run times both sweeps, then keeps the faster
+        c.run(T[:, :1], np.zeros((len(samples), 1)), 12)
+        c.run(T[:, 1:], np.zeros((len(samples), 1)), 12)
+        assert b.stats()["variant"] in (0, 1)
+        for i in range(len(samples)):
+            assert np.array_equal(a.spins(i), b.spins(i))
+            assert np.array_equal(a.spins(i), c.spins(i))
+        assert np.array_equal(a.history(), c.history())
+
+
+def test_resident_rejected_for_fp64():
+    with pytest.raises(vb.VegasError) as e:
+        ctx([sc_periodic(4)], precision=64, variant=1)
+    assert e.value.status == vb.EINVAL
+
+
 # --------------------------------------------------------------------------- FP32 batching
 
 def test_fp32_replica_batch_equals_plain_runs():
