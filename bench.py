@@ -64,6 +64,24 @@ def dist_env():
     return rank, world, local
 
 
+def rank_instances(rank: int, world: int, replicas: int = REPLICAS) -> list:
+    """Instance ids a rank sweeps: every rank owns its own block of replicas (weak scaling;
+    instances are independent, so no data-path collective is needed)."""
+    return list(range(rank * replicas, (rank + 1) * replicas))
+
+
+def slowest_rank_ms(ms: float, world: int, device=None) -> float:
+    """Max over ranks of the timed region (the job ends with its slowest rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -210,7 +228,7 @@ def run_ours(args):
     T = temperatures()[:, None]
     B = np.zeros_like(T)
     stream = torch.cuda.current_stream()
-    inst_base = rank * REPLICAS
+    inst_base = rank_instances(rank, world)[0]
     t0 = time.perf_counter()
     ctx = vg.Context([s], precision=32, replicas=REPLICAS, seed=SEED, inst_base=inst_base, device=dev,
                      stream=int(stream.cuda_stream), timing=True)
@@ -233,11 +251,7 @@ def run_ours(args):
         ev1.record(stream)
         barrier()
     st1 = ctx.stats()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank_ms(ev0.elapsed_time(ev1), world, device="cuda")
     attempts_rank = REPLICAS * s.n_sites * mcs * args.steps
     value = attempts_rank * world / (ms / 1000.0)
     launches = st1["kernel_launches"] - st0["kernel_launches"]
@@ -317,6 +331,70 @@ def run_ours(args):
     return 0
 
 
+def run_workload(args):
+    """One step = one vegas_run of the whole schedule of a secondary workload (the 8^3 FP64
+    ferromagnet, the 64^3 hysteresis loop, the field-cooled core/shell particle, the 256
+    nanoparticles). For np256 the plain comparison runs every particle in its own context,
+    one after another, for a bounded number of MCS."""
+    import torch
+    import paper_1803_07030_gb300 as vg
+    from lattices import workload
+
+    vg.build()
+    torch.cuda.set_device(0)
+    w = workload(args.workload, mcs=args.mcs if args.mcs != MCS else None)
+    stream = torch.cuda.current_stream()
+    ctx = vg.Context(w.samples, precision=w.precision, replicas=w.replicas, seed=w.seed,
+                     stream=int(stream.cuda_stream))
+    for _ in range(args.warmup):
+        ctx.run(w.T, w.B, w.mcs)
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        a.record(stream)
+        for _ in range(args.steps):
+            ctx.run(w.T, w.B, w.mcs)
+        b.record(stream)
+        torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    st1 = ctx.stats()
+    value = w.attempts() * args.steps / (ms / 1000.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if w.precision == 64 else "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "instances": w.n_inst, "sites": w.n_sites_total,
+                   "steps_x_mcs": [w.n_steps, w.mcs], "attempts_per_step": w.attempts(),
+                   "l2": "working set inside L2" if w.n_sites_total * 16 < 100e6 else "larger than L2"},
+        "variant": st1["variant"], "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
+        "clocks": clk.summary(),
+    }
+    ctx.close()
+    if args.workload == "np256":
+        plain_mcs = min(w.mcs, 100)
+        plain_ms, plain_att = 0.0, 0
+        for p, smp in enumerate(w.samples):
+            with vg.Context([smp], precision=32, seed=w.seed, inst_base=p, variant=0,
+                            stream=int(stream.cuda_stream)) as q:
+                Tp, Bp = w.T[p:p + 1], w.B[p:p + 1]
+                q.run(Tp, Bp, 2)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                q.run(Tp, Bp, plain_mcs)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                plain_ms += e0.elapsed_time(e1)
+                plain_att += smp.n_sites * plain_mcs
+        line["plain"] = {"value": plain_att / (plain_ms / 1000.0), "unit": UNIT,
+                         "note": f"each of the {len(w.samples)} particles in its own context, one launch per colour "
+                                 f"class, {plain_mcs} MCS each, run one after another"}
+        line["batched_over_plain"] = value / line["plain"]["value"]
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     global L_SIDE
     ap = argparse.ArgumentParser()
@@ -326,12 +404,17 @@ def main():
     ap.add_argument("--mcs", type=int, default=MCS)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", type=int, default=L_SIDE, help="lattice side (smaller cases for ncu captures)")
+    ap.add_argument("--workload", default="sg256x32",
+                    choices=["sg256x32", "sc8_fp64", "sc64_hyst", "coreshell_fc", "np256"],
+                    help="sg256x32 is the headline line; the others time one run of their schedule")
     ap.add_argument("--quick", action="store_true",
                     help="time the sweep only (no e2e, plain-path or CPU-baseline legs); for profiling runs")
     args = ap.parse_args()
     L_SIDE = args.side
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "sg256x32":
+        return run_workload(args)
     return run_ours(args)
 
 

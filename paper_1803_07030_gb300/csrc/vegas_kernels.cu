@@ -304,6 +304,8 @@ __device__ __forceinline__ Site32 site_params32(const PassArgs &a, int PMv, int 
     return p;
 }
 
+constexpr int kDirectRow = 12;  // rows up to this length gather all neighbours at once
+
 // One attempt of the direct path: gathers the neighbour rows with plain loads (row order),
 // draws the trial, decides, writes, and adds the site's share of E and M. Returns the
 // decision.
@@ -316,10 +318,33 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
     const float4 Si = S[si];
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
     const int64_t e0 = __ldg(row_ptr + g), e1 = __ldg(row_ptr + g + 1);
-    for (int64_t e = e0; e < e1; ++e) {
-        const int2 ed = __ldg(E + e);
-        link32(__ldg(S + (int64_t)ed.x * R + r), __int_as_float(ed.y), LM == 2 && ed.x < lower_end, hx, hy, hz, lx,
-               ly, lz);
+    const int deg = (int)(e1 - e0);
+    if (deg <= kDirectRow) {
+        // all links first, then the neighbour rows with every load in flight together; the
+        // field still sums in row order
+        int2 ed[kDirectRow];
+#pragma unroll
+        for (int k = 0; k < kDirectRow; ++k)
+            if (k < deg) ed[k] = __ldg(E + e0 + k);
+#pragma unroll
+        for (int k0 = 0; k0 < kDirectRow; k0 += 4) {  // neighbour rows four at a time
+            if (k0 >= deg) break;
+            float4 Sj[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k0 + k < deg) Sj[k] = __ldg(S + (int64_t)ed[k0 + k].x * R + r);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k0 + k < deg)
+                    link32(Sj[k], __int_as_float(ed[k0 + k].y), LM == 2 && ed[k0 + k].x < lower_end, hx, hy, hz, lx, ly,
+                           lz);
+        }
+    } else {
+        for (int64_t e = e0; e < e1; ++e) {
+            const int2 ed = __ldg(E + e);
+            link32(__ldg(S + (int64_t)ed.x * R + r), __int_as_float(ed.y), LM == 2 && ed.x < lower_end, hx, hy, hz,
+                   lx, ly, lz);
+        }
     }
     if (LM == 1) {
         lx = hx;
@@ -762,17 +787,11 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
                 const int cb = a.cstart[I.cls_off + c], ce = a.cstart[I.cls_off + c + 1];
                 for (int g = cb + (int)threadIdx.x; g < ce; g += NT) {
                     const uint32_t orig = (uint32_t)__ldg(a.orig + g);
+                    // one code path for every parameter mode: with k = kc = 0 the anisotropy terms
+                    // add signed zeros only, so spins and decisions equal the specialised paths'
                     const Site32 p = resident_params(a, I, g);
-                    bool ok;
-                    if (I.params_mode == 2)
-                        ok = direct_attempt<2, 2>(S, E, a.row_ptr, g, I.r, R, cb, orig, p, beta, B, t, inst, k0, k1, acc,
-                                                  nan_seen);
-                    else if (I.params_mode == 1)
-                        ok = direct_attempt<1, 2>(S, E, a.row_ptr, g, I.r, R, cb, orig, p, beta, B, t, inst, k0, k1, acc,
-                                                  nan_seen);
-                    else
-                        ok = direct_attempt<0, 2>(S, E, a.row_ptr, g, I.r, R, cb, orig, p, beta, B, t, inst, k0, k1, acc,
-                                                  nan_seen);
+                    const bool ok = direct_attempt<2, 2>(S, E, a.row_ptr, g, I.r, R, cb, orig, p, beta, B, t, inst, k0,
+                                                         k1, acc, nan_seen);
                     if (log_accepts)
                         a.alog[(int64_t)t * a.alog_stride + I.alog_base + (int64_t)I.r * I.n_sample_sites + orig] =
                             ok ? 1 : 0;
