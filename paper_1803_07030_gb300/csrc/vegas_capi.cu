@@ -68,9 +68,10 @@ struct vegas_ctx {
     bool res_eligible = false, tuned = false;
     int32_t max_instance_sites = 0;
     double tune_ms[2] = {0.0, 0.0};  // per-MCS time of the stream and resident sweeps when tuned
-    // graph of one MCS
+    // graph of one MCS (per-class sweep), and graphs of a whole temperature/field step
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    std::vector<std::pair<int64_t, cudaGraphExec_t>> step_graphs;  // key: mcs * 2 + variant
     // host state
     std::vector<std::vector<double>> hist;  // per instance: records * 4
     int64_t records = 0;
@@ -113,6 +114,7 @@ cudaError_t dalloc(vegas_ctx *c, T **p, size_t bytes) {
 }
 
 void free_all(vegas_ctx *c) {
+    for (auto &kv : c->step_graphs) cudaGraphExecDestroy(kv.second);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
     void *bufs[] = {c->d_spins, c->d_edges, c->d_p0, c->d_p1, c->d_pk, c->d_rowptr, c->d_slot_base, c->d_orig,
@@ -150,6 +152,60 @@ void enqueue_mcs(vegas_ctx *c, cudaStream_t st, std::vector<cudaEvent_t> *ev) {
     }
     ReduceArgs ra{c->d_partial, c->d_slot_base, c->d_slot_count, c->d_run, c->R, c->n_inst};
     launch_reduce(ra, st);
+}
+
+// One persistent launch for n MCS of the current step; the run state advances afterwards.
+void enqueue_resident(vegas_ctx *c, cudaStream_t st, int32_t n) {
+    cudaMemsetAsync(c->d_queue, 0, sizeof(uint32_t), st);
+    ResidentArgs a = c->res;
+    a.mcs = n;
+    launch_resident(a, c->res_grid, c->res_threads, st);
+    launch_advance(c->d_run, n, st);
+}
+
+void enqueue_renorm(vegas_ctx *c, cudaStream_t st) {
+    RenormArgs ra{c->d_spins, c->d_norm, c->n_sites * c->R, c->log2R};
+    const int grid = (int)std::min<int64_t>((ra.n_work + 255) / 256, (int64_t)c->sm_count * 8);
+    if (c->precision == 64)
+        launch_renorm64(ra, grid, st);
+    else
+        launch_renorm32(ra, grid, st);
+}
+
+constexpr int64_t kMaxStepGraphNodes = 20000;
+
+// Launches of one whole step (mcs MCS and the renormalisation) for the chosen variant, or
+// -1 when such a graph would be too large.
+int64_t step_graph_nodes(const vegas_ctx *c, int32_t mcs) {
+    const int64_t n = c->variant == 1 ? 4 : (int64_t)mcs * ((int64_t)c->passes.size() + 1) + 1;
+    return n <= kMaxStepGraphNodes ? n : -1;
+}
+
+// Graph of one temperature/field step; every kernel reads the step from the run state, so
+// the same graph serves every step with this MCS count.
+vegas_status step_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
+    const int64_t key = (int64_t)mcs * 2 + c->variant;
+    for (auto &kv : c->step_graphs)
+        if (kv.first == key) {
+            *out = kv.second;
+            return VEGAS_OK;
+        }
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    if (c->variant == 1) {
+        enqueue_resident(c, c->cap_stream, mcs);
+    } else {
+        for (int32_t m = 0; m < mcs; ++m) enqueue_mcs(c, c->cap_stream, nullptr);
+    }
+    enqueue_renorm(c, c->cap_stream);
+    CK(c, cudaStreamEndCapture(c->cap_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CK(c, e);
+    c->step_graphs.emplace_back(key, ge);
+    *out = ge;
+    return VEGAS_OK;
 }
 
 vegas_status build_graph(vegas_ctx *c) {
@@ -549,6 +605,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         ra.insts = c->d_insts;
         ra.cstart = c->d_cstart;
         ra.queue = c->d_queue;
+        ra.run = c->d_run;
         ra.err = c->d_err;
         ra.alog = c->d_alog;
         ra.seed = o.seed;
@@ -679,19 +736,9 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
     CK(c, cudaEventRecord(e0, c->stream));
-    RenormArgs ra{c->d_spins, c->d_norm, c->n_sites * c->R, c->log2R};
-    const int rgrid = (int)std::min<int64_t>((ra.n_work + 255) / 256, (int64_t)c->sm_count * 8);
     double sweep_ms = 0.0;
-    const uint32_t t_run = c->t;
-    // device run state for the per-class sweep (the resident sweep takes its own arguments)
-    auto set_state = [&](uint32_t t, uint32_t rec) -> vegas_status {
-        RunState r2 = rs;
-        r2.t = t;
-        r2.rec = rec;
-        CK(c, cudaMemcpyAsync(c->d_run, &r2, sizeof r2, cudaMemcpyHostToDevice, c->stream));
-        return VEGAS_OK;
-    };
-    // MCS m0 .. m0+n-1 of the current step with one launch per colour class
+    // the kernels read the MCS counter, record index and schedule from the run state, which
+    // the reductions (per-class sweep) and the advance kernel (resident sweep) move forward
     auto stream_mcs = [&](int32_t m0, int32_t n) -> vegas_status {
         for (int32_t m = m0; m < m0 + n; ++m) {
             if (use_graph) {
@@ -708,21 +755,13 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
         }
         return VEGAS_OK;
     };
-    // MCS m0 .. m0+n-1 of step s in one persistent launch
-    auto resident = [&](int32_t s, int32_t m0, int32_t n) -> vegas_status {
+    auto resident = [&](int32_t n) -> vegas_status {
         if (n <= 0) return VEGAS_OK;
-        CK(c, cudaMemsetAsync(c->d_queue, 0, sizeof(uint32_t), c->stream));
-        ResidentArgs a = c->res;
-        a.sched = c->d_sched;
-        a.hist = c->d_hist;
-        a.t0 = t_run + (uint32_t)s * (uint32_t)mcs + (uint32_t)m0;
-        a.mcs = n;
-        a.rec0 = s * mcs + m0;
-        a.step = s;
         if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 2], c->stream));
-        launch_resident(a, c->res_grid, c->res_threads, c->stream);
+        enqueue_resident(c, c->stream, n);
         if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 1], c->stream));
-        c->kernel_launches++;
+        CK(c, cudaGetLastError());
+        c->kernel_launches += 2;
         c->sweep_launches++;
         return VEGAS_OK;
     };
@@ -738,11 +777,8 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             CK(c, cudaEventCreate(&b0));
             CK(c, cudaEventCreate(&b1));
             CK(c, cudaEventRecord(a0, c->stream));
-            if ((st = resident(s, 0, probe)) != VEGAS_OK) return st;
+            if ((st = resident(probe)) != VEGAS_OK) return st;
             CK(c, cudaEventRecord(a1, c->stream));
-            if ((st = set_state(t_run + (uint32_t)s * (uint32_t)mcs + (uint32_t)probe, (uint32_t)(s * mcs + probe))) !=
-                VEGAS_OK)
-                return st;
             CK(c, cudaEventRecord(b0, c->stream));
             if ((st = stream_mcs(probe, probe)) != VEGAS_OK) return st;
             CK(c, cudaEventRecord(b1, c->stream));
@@ -761,17 +797,22 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             sweep_ms += tr + ts;
             m0 = 2 * probe;
         }
+        if (m0 == 0 && c->tuned && use_graph && step_graph_nodes(c, mcs) > 0) {
+            // the whole step as one graph
+            cudaGraphExec_t ge;
+            if ((st = step_graph(c, mcs, &ge)) != VEGAS_OK) return st;
+            CK(c, cudaGraphLaunch(ge, c->stream));
+            const int64_t nodes = step_graph_nodes(c, mcs);
+            c->kernel_launches += c->variant == 1 ? 3 : nodes;
+            c->sweep_launches += c->variant == 1 ? 1 : (int64_t)mcs * (int64_t)c->passes.size();
+            continue;
+        }
         if (c->variant == 1) {
-            if ((st = resident(s, m0, mcs - m0)) != VEGAS_OK) return st;
+            if ((st = resident(mcs - m0)) != VEGAS_OK) return st;
         } else {
-            if ((st = set_state(t_run + (uint32_t)s * (uint32_t)mcs + (uint32_t)m0, (uint32_t)(s * mcs + m0))) != VEGAS_OK)
-                return st;
             if ((st = stream_mcs(m0, mcs - m0)) != VEGAS_OK) return st;
         }
-        if (c->precision == 64)
-            launch_renorm64(ra, rgrid, c->stream);
-        else
-            launch_renorm32(ra, rgrid, c->stream);
+        enqueue_renorm(c, c->stream);
         c->kernel_launches++;
         if (c->opt.timing) {  // read this step's sweep timings before the events are reused
             CK(c, cudaStreamSynchronize(c->stream));

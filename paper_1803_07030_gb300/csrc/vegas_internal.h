@@ -172,8 +172,6 @@ struct ResidentArgs {
     const void *p0, *p1, *pk;  // per-site parameters (samples with params_mode 2)
     const ResidentInst *insts; // [n_items], largest first
     const int32_t *cstart;     // class starts (global sites), n_colours + 1 per sample
-    const double *sched;       // [n_steps][n_inst][2]
-    double *hist;              // [records][n_inst][4]
     uint32_t *queue;           // work counter, zero before the launch
     uint32_t *err;
     uint8_t *alog;
@@ -181,10 +179,8 @@ struct ResidentArgs {
     int64_t alog_stride;
     uint32_t alog_mcs;
     int32_t n_items, n_inst, log2R;
-    uint32_t t0;               // global MCS index of the launch's first MCS
-    int32_t mcs;               // MCS in this launch
-    int32_t rec0;              // history record of the first MCS
-    int32_t step;              // schedule row
+    const RunState *run;       // MCS counter t, record index, MCS per step, schedule, history
+    int32_t mcs;               // MCS in this launch (all inside one temperature/field step)
 };
 
 // ------------------------------------------------------------------ launchers
@@ -207,6 +203,8 @@ int pass_blocks_per_sm(int precision, const PassArgs &a);
 
 // Resident sweep with `threads` per block (256, 512 or 1024).
 void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream);
+// Adds n to the run state's MCS counter and record index (after a resident launch).
+void launch_advance(RunState *run, int32_t n, void *stream);
 int resident_blocks_per_sm(int threads);
 
 }  // namespace vegas

@@ -776,11 +776,13 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
         __syncthreads();
         if (item >= a.n_items) break;
         const ResidentInst I = a.insts[item];
-        const double *sc = a.sched + ((int64_t)a.step * a.n_inst + I.inst_local) * 2;
+        const uint32_t t0 = a.run->t, rec0 = a.run->rec;
+        const uint32_t step = rec0 / a.run->mcs;
+        const double *sc = a.run->sched + ((int64_t)step * a.n_inst + I.inst_local) * 2;
         const float beta = (float)sc[0], B = (float)sc[1];
         const uint32_t inst = (uint32_t)I.inst_id;
         for (int m = 0; m < a.mcs; ++m) {
-            const uint32_t t = a.t0 + (uint32_t)m;
+            const uint32_t t = t0 + (uint32_t)m;
             const bool log_accepts = a.alog && t < a.alog_mcs;
             Acc32 acc;
             for (int c = 0; c < I.n_colours; ++c) {
@@ -815,7 +817,7 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) sum[q] += s_red[w][q];
                 }
-                double *h = a.hist + ((int64_t)(a.rec0 + m) * a.n_inst + I.inst_local) * 4;
+                double *h = a.run->hist + ((int64_t)(rec0 + m) * a.n_inst + I.inst_local) * 4;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) h[q] = sum[q];
             }
@@ -1044,6 +1046,13 @@ void launch_scatter(void *spins, int precision, int64_t site_off, int64_t n, int
                     const double *in3, int grid, void *stream) {
     scatter_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(spins, precision, site_off, n, log2R, r, in3);
 }
+
+__global__ void advance_kernel(RunState *run, int32_t n) {
+    run->t += (uint32_t)n;
+    run->rec += (uint32_t)n;
+}
+
+void launch_advance(RunState *run, int32_t n, void *stream) { advance_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(run, n); }
 
 void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream) {
     if (threads >= 1024)
