@@ -48,7 +48,7 @@ typedef enum {
     VEGAS_EINVAL = 1,   /* invalid argument or sample (message says which) */
     VEGAS_ENOMEM = 2,   /* host or device allocation failed */
     VEGAS_ECUDA = 3,    /* a CUDA runtime call failed (no device, launch error, ...) */
-    VEGAS_ETIMEOUT = 4, /* a bounded device wait ran out */
+    VEGAS_ETIMEOUT = 4, /* a bounded device wait ran out (grid barrier of the cooperative sweep) */
     VEGAS_EDEVICE = 5,  /* a kernel flagged an error: NaN energy change, sampler cap */
     VEGAS_ESTATE = 6    /* context poisoned by an earlier ECUDA/EDEVICE */
 } vegas_status;
@@ -90,8 +90,10 @@ typedef struct {
     int32_t inst_base;      /* id of the first instance. Default 0. */
     int32_t device;         /* CUDA device ordinal, -1 = current. Default -1. */
     void *cuda_stream;      /* cudaStream_t to run on, NULL = a stream of the library */
-    int32_t variant;        /* -1 automatic, 0 one launch per colour class ("stream"),
-                               1 one persistent launch per step ("resident"). Default -1. */
+    int32_t variant;        /* -1 automatic (timed on the first run), 0 one launch per colour
+                               class, 1 resident: one persistent launch per step, a block per
+                               instance (FP32), 2 cooperative: one launch per step, all blocks
+                               sweep one sample class by class (FP32, one sample). Default -1. */
     int32_t accept_log_mcs; /* > 0: keep the accept/reject bit of every attempt of the
                                first accept_log_mcs MCS (debugging and parity). Default 0. */
     int32_t timing;         /* 1: time every sweep launch with CUDA events. Default 0. */
@@ -101,6 +103,11 @@ typedef struct {
     int32_t pipeline_depth; /* FP32 sweeps of rows with six links: groups of rows kept in
                                flight per warp, 2 or 3; 1 = no staging (direct kernel);
                                0 = automatic. Default 0. */
+    int64_t timeout_ns;     /* longest wait of a block at a grid barrier of the cooperative
+                               sweep before the run fails with VEGAS_ETIMEOUT; 0 = 2 s. */
+    int32_t fault_inject;   /* testing only: 1 = in the cooperative sweep one block leaves
+                               before its first grid barrier, so the others time out.
+                               Default 0. */
 } vegas_options;
 
 typedef struct {
@@ -112,7 +119,7 @@ typedef struct {
     int64_t records;            /* history records per instance so far */
     uint32_t mcs_done;          /* global MCS counter t */
     uint32_t device_error;      /* error bits set by kernels (1 NaN dE, 2 sampler cap,
-                                   4 index check failed in a debug build) */
+                                   4 index check failed in a debug build, 8 barrier timeout) */
     int64_t kernel_launches;    /* kernels launched by the library so far */
     int64_t sweep_launches;     /* colour-pass (or resident) sweep launches so far */
     double sweep_ms;            /* summed event time of sweep launches (timing = 1) */

@@ -67,7 +67,13 @@ struct vegas_ctx {
     int res_threads = 256, res_grid = 1;
     bool res_eligible = false, tuned = false;
     int32_t max_instance_sites = 0;
-    double tune_ms[2] = {0.0, 0.0};  // per-MCS time of the stream and resident sweeps when tuned
+    double tune_ms[3] = {0.0, 0.0, 0.0};  // per-MCS time of each sweep when tuned
+    // cooperative sweep
+    bool coop_eligible = false;
+    CoopArgs coop{};
+    int coop_grid = 1;
+    GridBarrier *d_bar = nullptr;
+    double *d_coop_partial = nullptr;
     // graph of one MCS (per-class sweep), and graphs of a whole temperature/field step
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -119,7 +125,7 @@ void free_all(vegas_ctx *c) {
     if (c->graph) cudaGraphDestroy(c->graph);
     void *bufs[] = {c->d_spins, c->d_edges, c->d_p0, c->d_p1, c->d_pk, c->d_rowptr, c->d_slot_base, c->d_orig,
                     c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog,
-                    c->d_insts, c->d_cstart, c->d_queue};
+                    c->d_insts, c->d_cstart, c->d_queue, c->d_bar, c->d_coop_partial};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -163,6 +169,15 @@ void enqueue_resident(vegas_ctx *c, cudaStream_t st, int32_t n) {
     launch_advance(c->d_run, n, st);
 }
 
+// One cooperative launch for n MCS of the current step; the run state advances afterwards.
+void enqueue_coop(vegas_ctx *c, cudaStream_t st, int32_t n) {
+    cudaMemsetAsync(c->d_bar, 0, sizeof(GridBarrier), st);
+    CoopArgs a = c->coop;
+    a.mcs = n;
+    launch_coop(a, c->coop_grid, st);
+    launch_advance(c->d_run, n, st);
+}
+
 void enqueue_renorm(vegas_ctx *c, cudaStream_t st) {
     RenormArgs ra{c->d_spins, c->d_norm, c->n_sites * c->R, c->log2R};
     const int grid = (int)std::min<int64_t>((ra.n_work + 255) / 256, (int64_t)c->sm_count * 8);
@@ -177,14 +192,14 @@ constexpr int64_t kMaxStepGraphNodes = 20000;
 // Launches of one whole step (mcs MCS and the renormalisation) for the chosen variant, or
 // -1 when such a graph would be too large.
 int64_t step_graph_nodes(const vegas_ctx *c, int32_t mcs) {
-    const int64_t n = c->variant == 1 ? 4 : (int64_t)mcs * ((int64_t)c->passes.size() + 1) + 1;
+    const int64_t n = c->variant >= 1 ? 4 : (int64_t)mcs * ((int64_t)c->passes.size() + 1) + 1;
     return n <= kMaxStepGraphNodes ? n : -1;
 }
 
 // Graph of one temperature/field step; every kernel reads the step from the run state, so
 // the same graph serves every step with this MCS count.
 vegas_status step_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
-    const int64_t key = (int64_t)mcs * 2 + c->variant;
+    const int64_t key = (int64_t)mcs * 4 + c->variant;
     for (auto &kv : c->step_graphs)
         if (kv.first == key) {
             *out = kv.second;
@@ -195,6 +210,8 @@ vegas_status step_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
     CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     if (c->variant == 1) {
         enqueue_resident(c, c->cap_stream, mcs);
+    } else if (c->variant == 2) {
+        enqueue_coop(c, c->cap_stream, mcs);
     } else {
         for (int32_t m = 0; m < mcs; ++m) enqueue_mcs(c, c->cap_stream, nullptr);
     }
@@ -248,6 +265,8 @@ extern "C" void vegas_default_options(vegas_options *o) {
     o->graphs = 1;
     o->max_blocks = 0;
     o->pipeline_depth = 0;
+    o->timeout_ns = 0;
+    o->fault_inject = 0;
 }
 
 extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samples, const vegas_options *opt,
@@ -262,7 +281,10 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     if (o.replicas < 1 || o.replicas > 32 || (o.replicas & (o.replicas - 1)))
         return fail(nullptr, VEGAS_EINVAL, "replicas must be 1, 2, 4, 8, 16 or 32");
     if (o.accept_log_mcs < 0 || o.inst_base < 0 || o.max_blocks < 0) return fail(nullptr, VEGAS_EINVAL, "negative option");
-    if (o.variant < -1 || o.variant > 1) return fail(nullptr, VEGAS_EINVAL, "variant must be -1, 0 or 1");
+    if (o.variant < -1 || o.variant > 2) return fail(nullptr, VEGAS_EINVAL, "variant must be -1, 0, 1 or 2");
+    if (o.timeout_ns < 0 || o.fault_inject < 0 || o.fault_inject > 1) return fail(nullptr, VEGAS_EINVAL, "bad timeout or fault_inject");
+    if (o.variant == 2 && (o.precision != 32 || n_samples != 1))
+        return fail(nullptr, VEGAS_EINVAL, "the cooperative sweep (variant 2) is FP32 with one sample");
     if (o.pipeline_depth < 0 || o.pipeline_depth > 3) return fail(nullptr, VEGAS_EINVAL, "pipeline_depth must be 0..3");
     if (o.variant == 1 && o.precision != 32)
         return fail(nullptr, VEGAS_EINVAL, "the resident sweep (variant 1) is FP32 only");
@@ -617,14 +639,35 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         // one block per instance only pays while instances are small
         c->res_eligible = c->max_instance_sites <= (1 << 18);
     }
-    if (o.variant == 1) {
+    // ---- cooperative sweep: one sample, every block on every class
+    if (!p64 && n_samples == 1 && !c->passes.empty()) {
+        c->coop_grid = c->sm_count * coop_blocks_per_sm();
+        if (o.max_blocks > 0) c->coop_grid = std::min(c->coop_grid, o.max_blocks);
+        DALLOC(c->d_bar, sizeof(GridBarrier));
+        DALLOC(c->d_coop_partial, sizeof(double) * 4 * (size_t)c->coop_grid * R);
+        CoopArgs &ca = c->coop;
+        std::memset(&ca, 0, sizeof ca);
+        ca.pass = c->passes[0].args;
+        ca.pass.lower_mode = 2;
+        ca.cstart = c->d_cstart;
+        ca.n_colours = c->samples[0].n_colours;
+        ca.bar = c->d_bar;
+        ca.partial = c->d_coop_partial;
+        ca.timeout_ns = o.timeout_ns > 0 ? o.timeout_ns : 2000000000LL;
+        ca.skip_block = o.fault_inject == 1 ? 0 : -1;
+        c->coop_eligible = true;
+    }
+    if (o.variant == 2) {
+        c->variant = 2;
+        c->tuned = true;
+    } else if (o.variant == 1) {
         if (!c->res_eligible) {
             c->err = "variant 1 (resident) needs FP32 and samples of at most 262144 sites";
             return bail(VEGAS_EINVAL);
         }
         c->variant = 1;
         c->tuned = true;
-    } else if (o.variant == 0 || !c->res_eligible) {
+    } else if (o.variant == 0 || (!c->res_eligible && !c->coop_eligible)) {
         c->variant = 0;
         c->tuned = true;
     } else {
@@ -765,58 +808,77 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
         c->sweep_launches++;
         return VEGAS_OK;
     };
+    auto coop = [&](int32_t n) -> vegas_status {
+        if (n <= 0) return VEGAS_OK;
+        if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 2], c->stream));
+        enqueue_coop(c, c->stream, n);
+        if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 1], c->stream));
+        CK(c, cudaGetLastError());
+        c->kernel_launches += 2;
+        c->sweep_launches++;
+        return VEGAS_OK;
+    };
+    auto run_variant = [&](int v, int32_t m0, int32_t n) -> vegas_status {
+        if (v == 1) return resident(n);
+        if (v == 2) return coop(n);
+        return stream_mcs(m0, n);
+    };
     for (int32_t s = 0; s < n_steps; ++s) {
         int32_t m0 = 0;
         if (!c->tuned && mcs >= 2) {
-            // autotune: time a few MCS of each sweep on the real chain (both give the same
-            // spins) and keep the faster for this context
-            const int32_t probe = std::max(1, std::min(4, mcs / 4));
-            cudaEvent_t a0, a1, b0, b1;
-            CK(c, cudaEventCreate(&a0));
-            CK(c, cudaEventCreate(&a1));
-            CK(c, cudaEventCreate(&b0));
-            CK(c, cudaEventCreate(&b1));
-            CK(c, cudaEventRecord(a0, c->stream));
-            if ((st = resident(probe)) != VEGAS_OK) return st;
-            CK(c, cudaEventRecord(a1, c->stream));
-            CK(c, cudaEventRecord(b0, c->stream));
-            if ((st = stream_mcs(probe, probe)) != VEGAS_OK) return st;
-            CK(c, cudaEventRecord(b1, c->stream));
-            CK(c, cudaStreamSynchronize(c->stream));
-            float tr = 0.f, ts = 0.f;
-            CK(c, cudaEventElapsedTime(&tr, a0, a1));
-            CK(c, cudaEventElapsedTime(&ts, b0, b1));
-            cudaEventDestroy(a0);
-            cudaEventDestroy(a1);
-            cudaEventDestroy(b0);
-            cudaEventDestroy(b1);
-            c->tune_ms[0] = ts / probe;
-            c->tune_ms[1] = tr / probe;
-            c->variant = (tr < ts) ? 1 : 0;
+            // autotune: time a few MCS of each eligible sweep on the real chain (all give the
+            // same spins) and keep the fastest for this context
+            std::vector<int> cand{0};
+            if (c->res_eligible) cand.push_back(1);
+            if (c->coop_eligible) cand.push_back(2);
+            const int32_t probe = std::max(1, std::min(4, mcs / (2 * (int32_t)cand.size())));
+            if (probe * (int32_t)cand.size() <= mcs) {
+                float best = 0.f;
+                int best_v = c->variant;
+                for (int v : cand) {
+                    cudaEvent_t x0, x1;
+                    CK(c, cudaEventCreate(&x0));
+                    CK(c, cudaEventCreate(&x1));
+                    CK(c, cudaEventRecord(x0, c->stream));
+                    if ((st = run_variant(v, m0, probe)) != VEGAS_OK) return st;
+                    CK(c, cudaEventRecord(x1, c->stream));
+                    CK(c, cudaStreamSynchronize(c->stream));
+                    float ms = 0.f;
+                    CK(c, cudaEventElapsedTime(&ms, x0, x1));
+                    cudaEventDestroy(x0);
+                    cudaEventDestroy(x1);
+                    c->tune_ms[v] = ms / probe;
+                    sweep_ms += ms;
+                    if (v == cand[0] || ms < best) {
+                        best = ms;
+                        best_v = v;
+                    }
+                    m0 += probe;
+                    uint32_t e4 = 0;
+                    CK(c, cudaMemcpy(&e4, c->d_err, sizeof e4, cudaMemcpyDeviceToHost));
+                    if (e4) break;  // report the device error below
+                }
+                c->variant = best_v;
+            }
             c->tuned = true;
-            sweep_ms += tr + ts;
-            m0 = 2 * probe;
         }
-        if (m0 == 0 && c->tuned && use_graph && step_graph_nodes(c, mcs) > 0) {
-            // the whole step as one graph
+
+        if (m0 == 0 && c->tuned && use_graph && c->variant != 2 && step_graph_nodes(c, mcs) > 0) {
+            // the whole step as one graph (the cooperative launch stays a direct launch)
             cudaGraphExec_t ge;
             if ((st = step_graph(c, mcs, &ge)) != VEGAS_OK) return st;
             CK(c, cudaGraphLaunch(ge, c->stream));
             const int64_t nodes = step_graph_nodes(c, mcs);
-            c->kernel_launches += c->variant == 1 ? 3 : nodes;
-            c->sweep_launches += c->variant == 1 ? 1 : (int64_t)mcs * (int64_t)c->passes.size();
+            c->kernel_launches += c->variant >= 1 ? 3 : nodes;
+            c->sweep_launches += c->variant >= 1 ? 1 : (int64_t)mcs * (int64_t)c->passes.size();
             continue;
         }
-        if (c->variant == 1) {
-            if ((st = resident(mcs - m0)) != VEGAS_OK) return st;
-        } else {
-            if ((st = stream_mcs(m0, mcs - m0)) != VEGAS_OK) return st;
-        }
+        if ((st = run_variant(c->variant, m0, mcs - m0)) != VEGAS_OK) return st;
         enqueue_renorm(c, c->stream);
         c->kernel_launches++;
         if (c->opt.timing) {  // read this step's sweep timings before the events are reused
             CK(c, cudaStreamSynchronize(c->stream));
-            if (c->variant == 1) {
+            if (c->variant >= 1) {
                 float ms = 0.f;
                 CK(c, cudaEventElapsedTime(&ms, ev[ev.size() - 2], ev[ev.size() - 1]));
                 sweep_ms += ms;
@@ -855,6 +917,8 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
     c->records += nrec;
     c->t += (uint32_t)nrec;
     c->device_error |= derr;
+    if (derr & kErrTimeout)
+        return fail(c, VEGAS_ETIMEOUT, "a grid barrier of the cooperative sweep waited longer than timeout_ns");
     if (derr) {
         char msg[200];
         std::snprintf(msg, sizeof msg,

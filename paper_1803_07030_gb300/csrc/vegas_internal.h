@@ -24,6 +24,7 @@ constexpr uint32_t kInitT = 0xFFFFFFFFu;
 constexpr uint32_t kErrNaN = 1u;
 constexpr uint32_t kErrSphere = 2u;
 constexpr uint32_t kErrIndex = 4u;  // debug builds: an index or alignment check failed
+constexpr uint32_t kErrTimeout = 8u;  // a bounded grid-barrier wait ran out
 
 // ------------------------------------------------------------------ host-side sample
 
@@ -183,6 +184,27 @@ struct ResidentArgs {
     int32_t mcs;               // MCS in this launch (all inside one temperature/field step)
 };
 
+// Grid barrier of the cooperative sweep (zeroed before every launch).
+struct GridBarrier {
+    uint32_t count;  // blocks arrived at the current barrier
+    uint32_t gen;    // completed barriers
+    uint32_t abort;  // set when a wait timed out: every block leaves
+    uint32_t pad_;
+};
+
+// Cooperative sweep of one sample (R replicas): all blocks sweep each colour class together
+// and meet at a bounded grid barrier between classes; every MCS of the step in one launch.
+struct CoopArgs {
+    PassArgs pass;             // site range of class 0 .. per class below, links, parameters
+    const int32_t *cstart;     // class starts (global sites), n_colours + 1
+    int32_t n_colours;
+    int32_t mcs;               // MCS in this launch
+    GridBarrier *bar;
+    double *partial;           // [block][R][4]
+    int64_t timeout_ns;        // longest wait at one barrier
+    int32_t skip_block;        // fault injection: this block never arrives (-1: none)
+};
+
 // ------------------------------------------------------------------ launchers
 
 // Sweep launch of one colour class; lower_mode, params_mode and deg pick the compiled variant.
@@ -205,6 +227,10 @@ int pass_blocks_per_sm(int precision, const PassArgs &a);
 void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream);
 // Adds n to the run state's MCS counter and record index (after a resident launch).
 void launch_advance(RunState *run, int32_t n, void *stream);
+
+// Cooperative launch (all blocks co-resident); returns the CUDA error of the launch.
+int launch_coop(const CoopArgs &a, int grid, void *stream);
+int coop_blocks_per_sm();
 int resident_blocks_per_sm(int threads);
 
 }  // namespace vegas

@@ -827,6 +827,123 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }
 
+// ------------------------------------------------------------------ cooperative sweep
+// One sample, all blocks: class c of MCS m is swept by the whole grid, then the grid meets
+// at a barrier. The barrier's wait is bounded by the global timer: a block that waits
+// longer than timeout_ns sets kErrTimeout and the abort flag, and every block returns at
+// its next barrier (or while waiting), so a lost block never hangs the GPU.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ bool grid_barrier(GridBarrier *b, uint32_t nblocks, int64_t timeout_ns, uint32_t *err, bool skip) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile GridBarrier *vb = b;
+        const uint32_t gen = vb->gen;
+        __threadfence();
+        if (!skip) {
+            const uint32_t arrived = atomicAdd(&b->count, 1u);
+            if (arrived == nblocks - 1) {
+                atomicExch(&b->count, 0u);
+                __threadfence();
+                atomicAdd(&b->gen, 1u);
+            } else {
+                const uint64_t t0 = global_ns();
+                while (vb->gen == gen) {
+                    if (vb->abort) {
+                        ok = 0;
+                        break;
+                    }
+                    if ((int64_t)(global_ns() - t0) > timeout_ns) {
+                        atomicOr(err, kErrTimeout);
+                        atomicExch(&b->abort, 1u);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        } else {
+            ok = 0;  // fault injection: leave without arriving
+        }
+        __threadfence();
+        if (vb->abort) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
+    const PassArgs &a = ca.pass;
+    const RunState *rs = a.run;
+    const uint32_t t0 = rs->t, rec0 = rs->rec;
+    const uint32_t step = rec0 / rs->mcs;
+    const int R = 1 << a.log2R;
+    float4 *S = (float4 *)a.spins;
+    const int2 *E = (const int2 *)a.edges;
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    const int64_t stride = (int64_t)gridDim.x * NT;
+    const int64_t w0 = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const int r = (int)(w0 & (R - 1));  // fixed per thread (the stride is a multiple of 32 >= R)
+    const uint32_t inst = (uint32_t)(a.inst0 + r);
+    const double *sc = rs->sched + ((int64_t)step * a.n_inst + a.inst_local0 + r) * 2;
+    const float beta = (float)sc[0], B = (float)sc[1];
+    const bool skip = (int)blockIdx.x == ca.skip_block;
+    bool nan_seen = false;
+    for (int m = 0; m < ca.mcs; ++m) {
+        const uint32_t t = t0 + (uint32_t)m;
+        const bool log_accepts = a.alog && t < a.alog_mcs;
+        Acc32 acc;
+        for (int c = 0; c < ca.n_colours; ++c) {
+            const int cb = ca.cstart[c], ce = ca.cstart[c + 1];
+            const int64_t n_work = (int64_t)(ce - cb) << a.log2R;
+            for (int64_t w = w0; w < n_work; w += stride) {
+                const int g = cb + (int)(w >> a.log2R);
+                const uint32_t orig = (uint32_t)__ldg(a.orig + g);
+                Site32 p{a.u32.nx, a.u32.ny, a.u32.nz, a.u32.s, a.u32.ex, a.u32.ey, a.u32.ez, a.u32.k, a.u32.kc};
+                if (a.params_mode == 2) p = site_params32(a, 2, g);
+                // one code path for every parameter mode (zero constants add signed zeros)
+                const bool ok = direct_attempt<2, 2>(S, E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t, inst, k0, k1,
+                                                     acc, nan_seen);
+                if (log_accepts)
+                    a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
+            }
+            if (!grid_barrier(ca.bar, gridDim.x, ca.timeout_ns, a.err, skip)) return;
+        }
+        // per-MCS sums: block partials per replica, then a fixed-order sum by R threads
+        acc.flush();
+        block_partials(acc.d, R, ca.partial + (int64_t)blockIdx.x * R * 4);
+        if (!grid_barrier(ca.bar, gridDim.x, ca.timeout_ns, a.err, skip)) return;
+        if (blockIdx.x == 0) {  // one warp per replica: lanes stride over blocks, fixed tree
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            for (int rr = warp; rr < R; rr += NT / 32) {
+                double v[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int b = lane; b < (int)gridDim.x; b += 32) {
+                    const double *p = ca.partial + ((int64_t)b * R + rr) * 4;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) v[q] += p[q];
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+                }
+                if (lane == 0) {
+                    double *h = rs->hist + ((int64_t)(rec0 + m) * a.n_inst + a.inst_local0 + rr) * 4;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) h[q] = v[q];
+                }
+            }
+        }
+    }
+    if (nan_seen) atomicOr(a.err, kErrNaN);
+}
+
 // ------------------------------------------------------------------ per-MCS reduction
 // One warp per instance sums its sample's block partials over every colour class in a
 // fixed order and appends the record; the last block to finish advances the MCS
@@ -1053,6 +1170,28 @@ __global__ void advance_kernel(RunState *run, int32_t n) {
 }
 
 void launch_advance(RunState *run, int32_t n, void *stream) { advance_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(run, n); }
+
+constexpr int kCoopThreads = 256;
+
+int launch_coop(const CoopArgs &a, int grid, void *stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kCoopThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return (int)cudaLaunchKernelEx(&cfg, coop32_kernel<kCoopThreads>, a);
+}
+
+int coop_blocks_per_sm() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop32_kernel<kCoopThreads>, kCoopThreads, 0);
+    return nb > 0 ? nb : 1;
+}
 
 void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream) {
     if (threads >= 1024)

@@ -55,6 +55,8 @@ class vegas_options(C.Structure):
         ("graphs", C.c_int32),
         ("max_blocks", C.c_int32),
         ("pipeline_depth", C.c_int32),
+        ("timeout_ns", C.c_int64),
+        ("fault_inject", C.c_int32),
     ]
 
 
@@ -283,7 +285,8 @@ class Context:
     def __init__(self, samples: Sequence, precision: int = 32, replicas: int = 1, seed: int = 1,
                  inst_base: int = 0, device: int = -1, stream="torch", variant: int = -1,
                  accept_log_mcs: int = 0, timing: bool = False, graphs: bool = True, max_blocks: int = 0,
-                 pipeline_depth: int = 0, library: Optional[str] = None):
+                 pipeline_depth: int = 0, timeout_ns: int = 0, fault_inject: int = 0,
+                 library: Optional[str] = None):
         self.samples = list(samples)
         self.n_sites = [int(np.asarray(s.row_ptr).shape[0] - 1) for s in self.samples]
         if library is not None:
@@ -301,6 +304,8 @@ class Context:
         o.graphs = 1 if graphs else 0
         o.max_blocks = max_blocks
         o.pipeline_depth = pipeline_depth
+        o.timeout_ns = timeout_ns
+        o.fault_inject = fault_inject
         o.cuda_stream = _current_stream() if stream == "torch" else stream
         self.replicas = replicas
         self.ptr = None

@@ -249,6 +249,51 @@ def test_resident_split_runs_and_autotune():
         assert np.array_equal(a.history(), c.history())
 
 
+# --------------------------------------------------------------------------- cooperative sweep
+# One launch per step for one sample: all blocks sweep every class together and meet at a
+# bounded grid barrier. Same arithmetic and random numbers: spins equal the per-class sweep.
+
+@pytest.mark.parametrize("make,R", [(lambda: sc_periodic(16, k_uni=0.05), 1), (lambda: sc_periodic(12, bimodal_seed=2), 4),
+                                    (lambda: core_shell_particle(seed=3, radius=5.0, core_radius=3.5), 2)])
+def test_cooperative_sweep_equals_per_class_sweep(make, R):
+    s = make()
+    T = np.stack([np.array([2.0, 0.9, 0.5]) * (1 + 0.1 * i) for i in range(R)])
+    B = np.stack([np.array([0.5, -0.5, 1.0]) for _ in range(R)])
+    with ctx([s], replicas=R, seed=21, variant=0, accept_log_mcs=2) as a, \
+            ctx([s], replicas=R, seed=21, variant=2, accept_log_mcs=2) as b:
+        a.run(T, B, 9)
+        b.run(T, B, 9)
+        assert b.stats()["variant"] == 2
+        for i in range(R):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+        assert_fp32_history_close(a.history(), b.history(), s.n_sites)
+        assert np.array_equal(a.accept_log(), b.accept_log())
+
+
+def test_cooperative_barrier_timeout_is_reported_not_hung():
+    """One block leaves before its first grid barrier (host-requested fault injection): the
+    other blocks give up after timeout_ns, the run fails with ETIMEOUT, and the context
+    refuses further work. No trap, no hang."""
+    s = sc_periodic(12)
+    with ctx([s], seed=1, variant=2, timeout_ns=50_000_000, fault_inject=1) as c:
+        with pytest.raises(vb.VegasError) as e:
+            c.run([[1.0]], [[0.0]], 3)
+        assert e.value.status == vb.ETIMEOUT
+        assert c.stats()["device_error"] & 8
+        with pytest.raises(vb.VegasError) as e2:
+            c.run([[1.0]], [[0.0]], 1)
+        assert e2.value.status == vb.ESTATE
+
+
+def test_autotuner_three_way():
+    s = sc_periodic(10, k_uni=0.1)
+    with ctx([s], seed=23, variant=-1) as a, ctx([s], seed=23, variant=0) as b:
+        a.run([[1.0, 0.7]], [[0.2, 0.1]], 24)
+        b.run([[1.0, 0.7]], [[0.2, 0.1]], 24)
+        assert a.stats()["variant"] in (0, 1, 2)
+        assert np.array_equal(a.spins(0), b.spins(0))
+
+
 def test_resident_rejected_for_fp64():
     with pytest.raises(vb.VegasError) as e:
         ctx([sc_periodic(4)], precision=64, variant=1)
