@@ -23,7 +23,11 @@ class Sample:
     spin_norm float64[n] (default 1), field_axis float64[n,3] (default +z),
     k_uni float64[n] (default 0), e_uni float64[n,3] (default +z), k_cub float64[n]
     (default 0), colour int32[n] (default: greedy colouring), positions float64[n,3]
-    (geometry only, never used by the method).
+    (geometry only, never used by the method). Update policy per site type (Sec. II):
+    type_policy int32[n_types] (0 random, 1 spin flip, 2 small step, 3 Gaussian,
+    4 Hinzke-Nowak, 5 adaptive) and type_param float64[n_types] (cap half-angle in radians
+    for 2 and 4, Gaussian width for 3 and the starting width for 5); None means random for
+    every site.
     """
 
     name: str
@@ -38,7 +42,15 @@ class Sample:
     k_cub: Optional[np.ndarray] = None
     colour: Optional[np.ndarray] = None
     positions: Optional[np.ndarray] = None
+    type_policy: Optional[np.ndarray] = None
+    type_param: Optional[np.ndarray] = None
     meta: dict = field(default_factory=dict)
+
+    def with_policy(self, policies, params) -> "Sample":
+        """Set the update policy table (one entry per site type) and return self."""
+        self.type_policy = np.asarray(np.atleast_1d(policies), dtype=np.int32)
+        self.type_param = np.asarray(np.broadcast_to(np.atleast_1d(params), self.type_policy.shape), dtype=np.float64)
+        return self
 
     @property
     def n_sites(self) -> int:

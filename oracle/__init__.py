@@ -5,15 +5,24 @@ this package. The CUDA library never does, and shares no code with it.
 """
 
 from .oracle import (  # noqa: F401
+    ADAPTIVE,
+    GAUSSIAN,
+    HINZKE_NOWAK,
+    RANDOM,
+    SMALL_STEP,
+    SPIN_FLIP,
     build,
+    cap_height,
     delta_e,
     energy,
     greedy_colour,
     init_spins,
+    log,
     magnetisation,
     philox4x32_10,
     renormalise,
     run,
     sphere,
+    trial,
     uniform,
 )

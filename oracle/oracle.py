@@ -35,7 +35,14 @@ class _Sample(C.Structure):
         ("k_uni", C.c_void_p),
         ("e_uni", C.c_void_p),
         ("k_cub", C.c_void_p),
+        ("type", C.c_void_p),
+        ("type_policy", C.c_void_p),
+        ("type_param", C.c_void_p),
+        ("n_policy_types", C.c_int32),
+        ("pad2_", C.c_int32),
     ]
+
+RANDOM, SPIN_FLIP, SMALL_STEP, GAUSSIAN, HINZKE_NOWAK, ADAPTIVE = range(6)
 
 
 def build(force: bool = False) -> str:
@@ -70,6 +77,14 @@ def _configure(lib):
     lib.vo_run.argtypes = [P, P, C.c_uint64, C.c_int32, C.c_int32, P, P, C.c_int32, C.c_int32,
                            C.c_uint32, P, C.c_int32, P, P, C.c_int32, C.c_int32, C.c_int32]
     lib.vo_run.restype = C.c_int
+    lib.vo_run2.argtypes = lib.vo_run.argtypes + [P, P]
+    lib.vo_run2.restype = C.c_int
+    lib.vo_log.argtypes = [C.c_double]
+    lib.vo_log.restype = C.c_double
+    lib.vo_cap_height.argtypes = [C.c_double]
+    lib.vo_cap_height.restype = C.c_double
+    lib.vo_trial.argtypes = [P, P, C.c_int32, C.c_uint64, C.c_uint32, C.c_int32, C.c_double, P]
+    lib.vo_trial.restype = C.c_int
     return lib
 
 
@@ -134,8 +149,14 @@ class _Bound:
         self.k_uni = f64(s.k_uni)
         self.e_uni = f64(s.e_uni, (n, 3))
         self.k_cub = f64(s.k_cub)
+        tp = getattr(s, "type_policy", None)
+        self.type = None if s.type is None else np.ascontiguousarray(s.type, dtype=np.int32)
+        self.type_policy = None if tp is None else np.ascontiguousarray(tp, dtype=np.int32)
+        self.type_param = None if tp is None else f64(s.type_param)
+        nt = 0 if tp is None else int(self.type_policy.shape[0])
         self.c = _Sample(n, 0, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.J), _ptr(self.spin_norm),
-                         _ptr(self.field_axis), _ptr(self.k_uni), _ptr(self.e_uni), _ptr(self.k_cub))
+                         _ptr(self.field_axis), _ptr(self.k_uni), _ptr(self.e_uni), _ptr(self.k_cub),
+                         _ptr(self.type), _ptr(self.type_policy), _ptr(self.type_param), nt, 0)
 
     @property
     def ref(self):
@@ -206,13 +227,33 @@ def init_spins(sample, seed: int, inst: int) -> np.ndarray:
     return S
 
 
+def log(x: float) -> float:
+    """The oracle's own natural logarithm (atanh series)."""
+    return _load().vo_log(float(x))
+
+
+def cap_height(theta: float) -> float:
+    return _load().vo_cap_height(float(theta))
+
+
+def trial(sample, S, i: int, seed: int, t: int, inst: int, sigma: float = 0.0):
+    """Trial unit vector of site i under its policy (counters i, t, inst); returns (vector, err)."""
+    b = _Bound(sample)
+    S = np.ascontiguousarray(S, dtype=np.float64).reshape(sample.n_sites, 3)
+    o = np.zeros(3)
+    err = _load().vo_trial(b.ref, _ptr(S), int(i), seed, t, inst, float(sigma), _ptr(o))
+    return o, err
+
+
 def run(sample, T, B, mcs: int, seed: int = 1, spins=None, inst_base: int = 0, t0: int = 0,
-        colour=None, log_mcs: int = 0, mode: int = 0, n_threads: int = 1):
+        colour=None, log_mcs: int = 0, mode: int = 0, n_threads: int = 1, sigma=None):
     """Run the chain for every instance in T's first axis.
 
     T, B: [n_inst, n_steps]. spins: None (Philox initial state) or [n_inst, n, 3].
-    Returns dict(spins=[n_inst,n,3], history=[n_inst, n_steps*mcs, 4], accept_log=
-    [n_inst, log_mcs, n] uint8 or None, err=int).
+    sigma: None or [n_inst] starting widths of the adaptive policy (<= 0: the policy's
+    parameter). Returns dict(spins=[n_inst,n,3], history=[n_inst, n_steps*mcs, 4],
+    accepted=[n_inst, n_steps*mcs] int64, sigma=[n_inst], accept_log=[n_inst, log_mcs, n]
+    uint8 or None, err=int).
     """
     T = np.ascontiguousarray(np.atleast_2d(T), dtype=np.float64)
     B = np.ascontiguousarray(np.broadcast_to(np.atleast_2d(B), T.shape), dtype=np.float64)
@@ -222,10 +263,12 @@ def run(sample, T, B, mcs: int, seed: int = 1, spins=None, inst_base: int = 0, t
     init = 1 if spins is None else 0
     S = np.zeros((n_inst, n, 3)) if spins is None else np.array(spins, dtype=np.float64).reshape(n_inst, n, 3)
     hist = np.zeros((n_inst, n_steps * mcs, 4))
-    log = np.zeros((n_inst, log_mcs, n), dtype=np.uint8) if log_mcs > 0 else None
+    alog = np.zeros((n_inst, log_mcs, n), dtype=np.uint8) if log_mcs > 0 else None
     cl = None if colour is None else np.ascontiguousarray(colour, dtype=np.int32)
-    err = _load().vo_run(b.ref, _ptr(cl), seed, n_inst, inst_base, _ptr(T), _ptr(B), n_steps, mcs, t0, _ptr(S),
-                         init, _ptr(hist), _ptr(log), log_mcs, mode, n_threads)
+    acc = np.zeros((n_inst, n_steps * mcs), dtype=np.int64)
+    sg = np.zeros(n_inst) if sigma is None else np.array(np.broadcast_to(sigma, (n_inst,)), dtype=np.float64)
+    err = _load().vo_run2(b.ref, _ptr(cl), seed, n_inst, inst_base, _ptr(T), _ptr(B), n_steps, mcs, t0, _ptr(S),
+                          init, _ptr(hist), _ptr(alog), log_mcs, mode, n_threads, _ptr(acc), _ptr(sg))
     if err < 0:
         raise ValueError("oracle rejected its arguments")
-    return {"spins": S, "history": hist, "accept_log": log, "err": err}
+    return {"spins": S, "history": hist, "accepted": acc, "sigma": sg, "accept_log": alog, "err": err}

@@ -34,6 +34,28 @@
  * Sphere sampler: Marsaglia, Ann. Math. Stat. 43 (1972) 645: a, b uniform in [0,1) from
  *   53-bit words, u1 = 2a-1, u2 = 2b-1, s = u1^2+u2^2, reject s >= 1, then
  *   (2 u1 sqrt(1-s), 2 u2 sqrt(1-s), 1-2s). Uses only correctly rounded operations.
+ *
+ * Update policies (Sec. II, Sec. III.B, Sec. IV.C; the paper names them without formulas,
+ * these are the readings; every proposal depends only on the angle between S and S', so it
+ * is symmetric and plain Metropolis acceptance stays exact):
+ *   0 random        S' uniform on the sphere (Marsaglia, above)
+ *   1 spin flip     S' = -S
+ *   2 small step    S' uniform in the cap of half-angle theta around S: a disk point
+ *                   (u1, u2) as in Marsaglia gives s uniform in [0,1) and an azimuth, and
+ *                   z = 1 - s h, (x, y) = (u1, u2) sqrt(h (2 - s h)) with h = 1 - cos theta,
+ *                   placed in an orthonormal frame (e1, e2, S/|S|)
+ *   3 Gaussian      S' = s_i (S/|S| + sigma g)/|...|, g three standard normals by the polar
+ *                   method (Marsaglia & Bray 1964) with candidates of purpose 0x00000|k and
+ *                   0x08000|k
+ *   4 Hinzke-Nowak  one of spin flip, random, small step with probability 1/3 each, chosen by
+ *                   the uniform of purpose 0x0C000 (Hinzke & Nowak 1999 combinational move)
+ *   5 adaptive      Gaussian whose width sigma (one per instance) is rescaled after each MCS by
+ *                   0.5 / max(1 - R, 0.01), R the MCS's acceptance rate, clamped to
+ *                   [1e-4, 100], during the first fifth of every temperature/field step only;
+ *                   it is then frozen, so the measured part is a plain Metropolis chain.
+ * The policy of a site comes from its type through a table (a policy per magnetic phase).
+ * Logarithms are computed here with the atanh series (Abramowitz & Stegun 4.1.27), not libm,
+ * so that any implementation of the same series gives the same bits.
  */
 #include <math.h>
 #include <pthread.h>
@@ -52,7 +74,14 @@ typedef struct {
     const double *k_uni;      /* NULL: all 0 */
     const double *e_uni;      /* NULL: all +z */
     const double *k_cub;      /* NULL: all 0 */
+    const int32_t *type;      /* NULL: all 0 */
+    const int32_t *type_policy; /* [n_policy_types] or NULL: every site random */
+    const double *type_param;   /* [n_policy_types]: theta (2, 4) or sigma (3, 5) */
+    int32_t n_policy_types;
+    int32_t pad2_;
 } vo_sample;
+
+enum { VO_RANDOM = 0, VO_FLIP = 1, VO_SMALL_STEP = 2, VO_GAUSSIAN = 3, VO_HINZKE_NOWAK = 4, VO_ADAPTIVE = 5 };
 
 enum { VO_ERR_NAN = 1, VO_ERR_SPHERE = 2 };
 
@@ -122,6 +151,99 @@ double vo_uniform(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t
     philox(seed, c0, c1, c2, c3, w);
     return u53(w[0], w[1]);
 }
+
+/* ---------------------------------------------------------------- policy helpers */
+
+/* ln x for finite x > 0 (normal): x = m 2^e with m in [sqrt(1/2), sqrt 2), ln m = 2 atanh t,
+ * t = (m-1)/(m+1), atanh t = sum t^(2j+1)/(2j+1) to j = 13 (|t| <= 0.172: error < 1e-20). */
+double vo_log(double x) {
+    uint64_t bits;
+    memcpy(&bits, &x, sizeof bits);
+    int32_t e = (int32_t)((bits >> 52) & 0x7FF) - 1023;
+    bits = (bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    double m;
+    memcpy(&m, &bits, sizeof m);
+    if (m > 1.4142135623730951) {
+        m = m * 0.5;
+        e = e + 1;
+    }
+    const double t = (m - 1.0) / (m + 1.0);
+    const double t2 = t * t;
+    double p = 1.0 / 27.0;
+    for (int32_t k = 25; k >= 1; k -= 2) p = p * t2 + 1.0 / (double)k;
+    return (2.0 * t) * p + (double)e * 0.6931471805599453;
+}
+
+/* Two standard normals by the polar method; candidates k use counter word 3 = purpose|k.
+ * Returns 0 past 64 candidates (then both are 0). */
+static int normal_pair(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t purpose, double g[2]) {
+    for (uint32_t k = 0; k < 64; ++k) {
+        uint32_t w[4];
+        philox(seed, c0, c1, c2, purpose | k, w);
+        const double u1 = 2.0 * u53(w[0], w[1]) - 1.0;
+        const double u2 = 2.0 * u53(w[2], w[3]) - 1.0;
+        const double s = u1 * u1 + u2 * u2;
+        if (s >= 1.0 || s == 0.0) continue;
+        const double f = sqrt((-2.0 * vo_log(s)) / s);
+        g[0] = u1 * f;
+        g[1] = u2 * f;
+        return 1;
+    }
+    g[0] = g[1] = 0.0;
+    return 0;
+}
+
+static void unit_of(const double v[3], double u[3]) {
+    const double q = sqrt((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
+    u[0] = v[0] / q;
+    u[1] = v[1] / q;
+    u[2] = v[2] / q;
+}
+
+/* Orthonormal frame around the unit vector u: e1 = unit(a x u) with a the coordinate axis of
+ * the smallest |u_k| (first on ties), e2 = u x e1. */
+static void frame_of(const double u[3], double e1[3], double e2[3]) {
+    const double ax = fabs(u[0]), ay = fabs(u[1]), az = fabs(u[2]);
+    double c[3];
+    if (ax <= ay && ax <= az) {
+        c[0] = 0.0; c[1] = -u[2]; c[2] = u[1];
+    } else if (ay <= az) {
+        c[0] = u[2]; c[1] = 0.0; c[2] = -u[0];
+    } else {
+        c[0] = -u[1]; c[1] = u[0]; c[2] = 0.0;
+    }
+    unit_of(c, e1);
+    e2[0] = u[1] * e1[2] - u[2] * e1[1];
+    e2[1] = u[2] * e1[0] - u[0] * e1[2];
+    e2[2] = u[0] * e1[1] - u[1] * e1[0];
+}
+
+/* Point uniform in the cap of height h = 1 - cos(theta) around the unit vector u. */
+static int cap_point(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t purpose, const double u[3],
+                     double h, double out[3]) {
+    for (uint32_t k = 0; k < 64; ++k) {
+        uint32_t w[4];
+        philox(seed, c0, c1, c2, purpose | k, w);
+        const double u1 = 2.0 * u53(w[0], w[1]) - 1.0;
+        const double u2 = 2.0 * u53(w[2], w[3]) - 1.0;
+        const double s = u1 * u1 + u2 * u2;
+        if (s >= 1.0) continue;
+        const double sh = s * h;
+        const double z = 1.0 - sh;
+        const double r = sqrt(h * (2.0 - sh));
+        const double x = u1 * r, y = u2 * r;
+        double e1[3], e2[3];
+        frame_of(u, e1, e2);
+        for (int q = 0; q < 3; ++q) out[q] = (x * e1[q] + y * e2[q]) + z * u[q];
+        return 1;
+    }
+    out[0] = u[0];
+    out[1] = u[1];
+    out[2] = u[2];
+    return 0;
+}
+
+double vo_cap_height(double theta) { return 1.0 - cos(theta); }
 
 /* ---------------------------------------------------------------- colouring */
 
@@ -280,7 +402,74 @@ typedef struct {
     int32_t log_mcs;
     int32_t mode;
     int err;
+    int64_t *acc_hist;      /* n_steps*mcs accepted attempts, or NULL */
+    double sigma;           /* adaptive width of this instance */
+    int has_adaptive;
 } vo_job;
+
+static void policy_of(const vo_sample *s, int32_t i, int32_t *pol, double *par) {
+    *pol = VO_RANDOM;
+    *par = 0.0;
+    if (!s->type_policy) return;
+    const int32_t ty = s->type ? s->type[i] : 0;
+    if (ty >= 0 && ty < s->n_policy_types) {
+        *pol = s->type_policy[ty];
+        *par = s->type_param[ty];
+    }
+}
+
+/* Trial state of site i under its update policy (unit vector before the spin norm). */
+static void trial_of(vo_job *jb, int32_t i, uint32_t c0, uint32_t t, uint32_t p_trial, double out[3]) {
+    const vo_sample *s = jb->s;
+    const uint32_t inst = (uint32_t)jb->inst;
+    int32_t pol;
+    double par;
+    policy_of(s, i, &pol, &par);
+    const double *Si = jb->S + 3 * (int64_t)i;
+    if (pol == VO_HINZKE_NOWAK) {
+        const double v = vo_uniform(jb->seed, c0, t, inst, 0x0C000u) * 3.0;
+        pol = v < 1.0 ? VO_FLIP : (v < 2.0 ? VO_RANDOM : VO_SMALL_STEP);
+    }
+    if (pol == VO_FLIP) {
+        const double sn = norm_of(s, i);
+        out[0] = -Si[0] / sn;
+        out[1] = -Si[1] / sn;
+        out[2] = -Si[2] / sn;
+        return;
+    }
+    if (pol == VO_SMALL_STEP) {
+        double u[3];
+        unit_of(Si, u);
+        if (!cap_point(jb->seed, c0, t, inst, p_trial, u, vo_cap_height(par), out)) jb->err |= VO_ERR_SPHERE;
+        return;
+    }
+    if (pol == VO_GAUSSIAN || pol == VO_ADAPTIVE) {
+        const double sigma = pol == VO_ADAPTIVE ? jb->sigma : par;
+        double u[3], g0[2], g1[2];
+        unit_of(Si, u);
+        if (!normal_pair(jb->seed, c0, t, inst, p_trial, g0)) jb->err |= VO_ERR_SPHERE;
+        if (!normal_pair(jb->seed, c0, t, inst, p_trial | 0x08000u, g1)) jb->err |= VO_ERR_SPHERE;
+        const double v[3] = {u[0] + sigma * g0[0], u[1] + sigma * g0[1], u[2] + sigma * g1[0]};
+        unit_of(v, out);
+        return;
+    }
+    if (vo_sphere(jb->seed, c0, t, inst, p_trial, out) < 0) jb->err |= VO_ERR_SPHERE;
+}
+
+/* Trial state of site i (unit vector) for the given spins and adaptive width, counters
+ * (i, t, inst, purpose 0): the sampler attempts use, exposed for the distribution pins. */
+int vo_trial(const vo_sample *s, const double *S, int32_t i, uint64_t seed, uint32_t t, int32_t inst, double sigma,
+             double *out) {
+    vo_job jb;
+    memset(&jb, 0, sizeof jb);
+    jb.s = s;
+    jb.S = (double *)S;
+    jb.seed = seed;
+    jb.inst = inst;
+    jb.sigma = sigma;
+    trial_of(&jb, i, (uint32_t)i, t, 0x00000u, out);
+    return jb.err;
+}
 
 /* One Metropolis attempt on site i (Eq. 4). Trial and acceptance counters are
  * (c0, t, inst, purpose). Returns 1 when accepted. */
@@ -288,7 +477,7 @@ static int attempt(vo_job *jb, int32_t i, uint32_t c0, uint32_t t, double beta, 
                    uint32_t p_accept) {
     const vo_sample *s = jb->s;
     double u[3];
-    if (vo_sphere(jb->seed, c0, t, (uint32_t)jb->inst, p_trial, u) < 0) jb->err |= VO_ERR_SPHERE;
+    trial_of(jb, i, c0, t, p_trial, u);
     const double sn = norm_of(s, i);
     const double Sp[3] = {sn * u[0], sn * u[1], sn * u[2]};
     const double dE = vo_delta_e(s, jb->S, i, Sp, B);
@@ -324,10 +513,12 @@ static void *run_job(void *arg) {
         for (int32_t m = 0; m < jb->mcs; ++m) {
             const int64_t mrun = (int64_t)st * jb->mcs + m;
             uint8_t *log = (jb->accept_log && mrun < jb->log_mcs) ? jb->accept_log + mrun * n : NULL;
+            int64_t accepted = 0;
             if (jb->mode == 0) {
                 for (int32_t q = 0; q < n; ++q) {
                     const int32_t i = jb->order[q];
                     const int a = attempt(jb, i, (uint32_t)i, t, beta, B, 0x00000u, 0x10000u);
+                    accepted += a;
                     if (log) log[i] = (uint8_t)a;
                 }
             } else {
@@ -335,8 +526,18 @@ static void *run_job(void *arg) {
                     const double r = vo_uniform(jb->seed, (uint32_t)a, t, (uint32_t)jb->inst, 0x50000u);
                     int32_t i = (int32_t)(r * (double)n);
                     if (i >= n) i = n - 1;
-                    attempt(jb, i, (uint32_t)a, t, beta, B, 0x60000u, 0x70000u);
+                    accepted += attempt(jb, i, (uint32_t)a, t, beta, B, 0x60000u, 0x70000u);
                 }
+            }
+            if (jb->acc_hist) jb->acc_hist[rec] = accepted;
+            if (jb->has_adaptive && m < jb->mcs / 5) {  /* adapt during the first fifth of the step */
+                const double rate = (double)accepted / (double)n;
+                double f = 1.0 - rate;
+                if (f < 0.01) f = 0.01;
+                double sg = jb->sigma * (0.5 / f);
+                if (sg < 1e-4) sg = 1e-4;
+                if (sg > 100.0) sg = 100.0;
+                jb->sigma = sg;
             }
             double M[3];
             vo_magnetisation(n, jb->S, M);
@@ -364,9 +565,25 @@ static void *run_job(void *arg) {
  *             that MCS was accepted (mode 0 only)
  * Returns the OR of VO_ERR_* over instances, or -1 on invalid arguments.
  */
+int vo_run2(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t n_inst, int32_t inst_base,
+            const double *T, const double *B, int32_t n_steps, int32_t mcs, uint32_t t0, double *spins, int32_t init,
+            double *history, uint8_t *accept_log, int32_t log_mcs, int32_t mode, int32_t n_threads,
+            int64_t *acc_hist, double *sigma_inout);
+
 int vo_run(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t n_inst, int32_t inst_base,
            const double *T, const double *B, int32_t n_steps, int32_t mcs, uint32_t t0, double *spins, int32_t init,
            double *history, uint8_t *accept_log, int32_t log_mcs, int32_t mode, int32_t n_threads) {
+    return vo_run2(s, colour, seed, n_inst, inst_base, T, B, n_steps, mcs, t0, spins, init, history, accept_log,
+                   log_mcs, mode, n_threads, NULL, NULL);
+}
+
+/* As vo_run, plus: acc_hist NULL or [n_inst][n_steps*mcs] accepted attempts per MCS;
+ * sigma_inout NULL or [n_inst] adaptive widths (in: start values, or <= 0 for the policy
+ * parameter; out: the widths after the run). */
+int vo_run2(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t n_inst, int32_t inst_base,
+            const double *T, const double *B, int32_t n_steps, int32_t mcs, uint32_t t0, double *spins, int32_t init,
+            double *history, uint8_t *accept_log, int32_t log_mcs, int32_t mode, int32_t n_threads,
+            int64_t *acc_hist, double *sigma_inout) {
     if (!s || s->n < 0 || n_inst < 1 || n_steps < 0 || mcs < 0 || !T || !B || !spins || !history) return -1;
     const int32_t n = s->n;
     int32_t *col_own = NULL;
@@ -404,6 +621,16 @@ int vo_run(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t n_i
         jb->accept_log = accept_log ? accept_log + (int64_t)r * log_mcs * n : NULL;
         jb->log_mcs = log_mcs;
         jb->mode = mode;
+        jb->acc_hist = acc_hist ? acc_hist + (int64_t)r * n_steps * mcs : NULL;
+        jb->has_adaptive = 0;
+        jb->sigma = 0.0;
+        if (s->type_policy)
+            for (int32_t ty = 0; ty < s->n_policy_types; ++ty)
+                if (s->type_policy[ty] == VO_ADAPTIVE && !jb->has_adaptive) {
+                    jb->has_adaptive = 1;
+                    jb->sigma = s->type_param[ty];
+                }
+        if (sigma_inout && sigma_inout[r] > 0.0) jb->sigma = sigma_inout[r];
         if (init) err |= vo_init_spins(s, seed, jb->inst, jb->S);
     }
     if (n_threads < 1) n_threads = 1;
@@ -422,7 +649,10 @@ int vo_run(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t n_i
         if (n_threads > 1)
             for (int32_t k = 0; k < cnt; ++k) pthread_join(th[k], NULL);
     }
-    for (int32_t r = 0; r < n_inst; ++r) err |= jobs[r].err;
+    for (int32_t r = 0; r < n_inst; ++r) {
+        err |= jobs[r].err;
+        if (sigma_inout) sigma_inout[r] = jobs[r].sigma;
+    }
     free(jobs);
     free(order);
     free(col_own);

@@ -14,6 +14,7 @@ import pytest
 import oracle
 from oracle import oracle as ora
 import test_oracle_pins as pins
+import test_oracle_policies as pol
 
 SRC = open(os.path.join(os.path.dirname(ora.__file__), "vegas_oracle.c")).read()
 
@@ -43,6 +44,20 @@ MUTANTS = [
     ("colouring not greedy", "while (c < cap && mark[c] == i) ++c;", "while (c < cap && mark[c] == i) c += 2;",
      [lambda: pins.test_greedy_colouring_matches_networkx(lambda: pins.sc_periodic(5))]),
     ("exchange sign", "ex += s->J[e] *", "ex -= s->J[e] *", [lambda: pins.test_three_spin_ring(-1.0)]),
+    ("cap height not scaled by s", "const double z = 1.0 - sh;", "const double z = 1.0 - h;",
+     [lambda: pol.test_small_step_uniform_in_cap(1.0)]),
+    ("cap radius factor", "const double r = sqrt(h * (2.0 - sh));", "const double r = sqrt(h * (1.0 - sh));",
+     [lambda: pol.test_small_step_uniform_in_cap(1.0)]),
+    ("polar method factor", "sqrt((-2.0 * vo_log(s)) / s)", "sqrt((-1.0 * vo_log(s)) / s)",
+     [pol.test_gaussian_offsets_are_standard_normals]),
+    ("log series term dropped", "k >= 1; k -= 2", "k >= 3; k -= 2", [pol.test_log_series_matches_libm]),
+    ("Gaussian third normal reused", "sigma * g1[0]}", "sigma * g0[0]}", [pol.test_gaussian_wide_is_uniform]),
+    ("Hinzke-Nowak thirds", "vo_uniform(jb->seed, c0, t, inst, 0x0C000u) * 3.0", "vo_uniform(jb->seed, c0, t, inst, 0x0C000u) * 2.5",
+     [pol.test_hinzke_nowak_mixture]),
+    ("adaptive law inverted", "jb->sigma * (0.5 / f)", "jb->sigma * (f / 0.5)",
+     [pol.test_adaptive_acceptance_and_control_law]),
+    ("adaptation never frozen", "m < jb->mcs / 5", "m < jb->mcs", [pol.test_adaptive_acceptance_and_control_law]),
+    ("flip keeps the spin", "out[0] = -Si[0] / sn;", "out[0] = Si[0] / sn;", [pol.test_spin_flip_trial_is_minus_s]),
 ]
 
 
