@@ -12,7 +12,24 @@
  *       - sum_i k_i (S_i.e_i)^2 - sum_i kc_i (Sx^2 Sy^2 + Sy^2 Sz^2 + Sx^2 Sz^2)_i
  *   S_i = s_i * (unit vector); B is a scalar field intensity and n_i the per-site field
  *   axis (Sec. III.C material file); k > 0 is an easy axis. k_B = 1.
- * Update policy: "random" (trial uniform on the sphere of radius s_i, Sec. III.B).
+ * Update policies (Sec. II; Sec. IV.C), chosen per site type through a table in the sample
+ *   (a policy per magnetic phase). Each proposes S_i' = s_i * (unit vector u') from the
+ *   current direction u = S_i/|S_i|; the proposal density depends only on the angle between
+ *   u and u', so Metropolis acceptance (Eq. 4) is unchanged:
+ *   VEGAS_POLICY_RANDOM        u' uniform on the sphere (the default, Sec. III.B)
+ *   VEGAS_POLICY_SPIN_FLIP     u' = -u
+ *   VEGAS_POLICY_SMALL_STEP    u' uniform in the cap of half-angle theta (param) around u
+ *   VEGAS_POLICY_GAUSSIAN      u' = direction of u + sigma g, g three standard normals,
+ *                              sigma = param
+ *   VEGAS_POLICY_HINZKE_NOWAK  spin flip, random or small step (cap half-angle = param),
+ *                              each with probability 1/3 (Hinzke & Nowak's combination)
+ *   VEGAS_POLICY_ADAPTIVE      Gaussian with one width sigma per instance (starting at the
+ *                              param of the first adaptive type); after each MCS of the
+ *                              first fifth of every temperature/field step, sigma <-
+ *                              sigma * 0.5 / max(1 - R, 0.01), R the MCS's acceptance rate
+ *                              over all sites of the instance, clamped to [1e-4, 100]; then
+ *                              frozen, so the rest of the step is a plain Metropolis chain
+ *                              whose acceptance rate sits near 1/2.
  * Sweep order: one MCS visits every site once, colour class by colour class of a proper
  *   colouring (greedy in site order unless the caller gives one). Sites of one class
  *   share no link, so they are updated in parallel with exactly the result of any
@@ -60,14 +77,23 @@ typedef enum {
  * no duplicate links, col in [0, n_sites). Optional arrays may be NULL (default noted).
  * The order of a row is kept: the local field sums neighbours in that order.
  */
+typedef enum {
+    VEGAS_POLICY_RANDOM = 0,
+    VEGAS_POLICY_SPIN_FLIP = 1,
+    VEGAS_POLICY_SMALL_STEP = 2,
+    VEGAS_POLICY_GAUSSIAN = 3,
+    VEGAS_POLICY_HINZKE_NOWAK = 4,
+    VEGAS_POLICY_ADAPTIVE = 5
+} vegas_policy;
+
 typedef struct {
     int32_t n_sites;           /* >= 1 and < 2^31 */
-    int32_t pad_;
+    int32_t n_policy_types;    /* entries of type_policy and type_param; 0: every site random */
     int64_t n_edges;           /* == row_ptr[n_sites] */
     const int64_t *row_ptr;    /* [n_sites + 1], row_ptr[0] == 0, non-decreasing */
     const int32_t *col;        /* [n_edges] neighbour site */
     const double *J;           /* [n_edges] exchange J_ij (Eq. 1) */
-    const int32_t *type;       /* [n_sites] or NULL (all 0); kept for per-type output */
+    const int32_t *type;       /* [n_sites] or NULL (all 0); selects the update policy */
     const double *spin_norm;   /* [n_sites] s_i > 0, or NULL (all 1) */
     const double *field_axis;  /* [n_sites][3] n_i, or NULL (all +z) */
     const double *k_uni;       /* [n_sites] uniaxial constant k_i (Eq. 2), or NULL (0) */
@@ -80,6 +106,12 @@ typedef struct {
                                   sites in device memory (a Morton curve inside each colour
                                   class) so that a sweep's neighbour reads stay in L2; results
                                   do not depend on it. */
+    const int32_t *type_policy; /* [n_policy_types] vegas_policy of each site type, or NULL
+                                   when n_policy_types == 0. With a table, every type must
+                                   lie in [0, n_policy_types). */
+    const double *type_param;   /* [n_policy_types]: cap half-angle theta in (0, pi] radians
+                                   (small step, Hinzke-Nowak), width sigma > 0 (Gaussian,
+                                   adaptive), ignored (random, spin flip) */
 } vegas_sample;
 
 typedef struct {
@@ -93,7 +125,8 @@ typedef struct {
     int32_t variant;        /* -1 automatic (timed on the first run), 0 one launch per colour
                                class, 1 resident: one persistent launch per step, a block per
                                instance (FP32), 2 cooperative: one launch per step, all blocks
-                               sweep one sample class by class (FP32, one sample). Default -1. */
+                               sweep one sample class by class (FP32, one sample, no adaptive
+                               policy). Default -1. */
     int32_t accept_log_mcs; /* > 0: keep the accept/reject bit of every attempt of the
                                first accept_log_mcs MCS (debugging and parity). Default 0. */
     int32_t timing;         /* 1: time every sweep launch with CUDA events. Default 0. */
@@ -139,7 +172,8 @@ void vegas_default_options(vegas_options *opt);
  * Returns VEGAS_EINVAL for: n_samples < 1; a NULL required array; row_ptr not starting
  * at 0, decreasing, or not ending at n_edges; col out of range; a self-link; a duplicate
  * link; J not symmetric; a non-finite parameter; spin_norm <= 0; a colouring
- * that is not proper; bad options. On failure *out is NULL.
+ * that is not proper; a policy table with an unknown policy, a parameter out of range or
+ * a site type outside it; bad options. On failure *out is NULL.
  */
 vegas_status vegas_create(const vegas_sample *samples, int32_t n_samples, const vegas_options *opt,
                           vegas_ctx **out);
@@ -177,6 +211,21 @@ vegas_status vegas_set_spins(vegas_ctx *ctx, int32_t instance, const double *in)
  * out == NULL: size query.
  */
 vegas_status vegas_accept_log(const vegas_ctx *ctx, uint8_t *out, size_t capacity, size_t *n_written);
+
+/*
+ * Accepted attempts of every MCS, as [n_instances][records] counts (one per history
+ * record, same order); acceptance rate = count / n_sites of the instance's sample.
+ * out == NULL: size query (*n_written = number of counts).
+ */
+vegas_status vegas_accept_history(const vegas_ctx *ctx, uint32_t *out, size_t capacity, size_t *n_written);
+
+/*
+ * Width sigma of the adaptive policy of every instance ([n_instances] doubles; 0 for
+ * instances whose sample has no adaptive type). _set replaces them (checkpoint/resume);
+ * values must be finite and > 0 where the sample adapts, and are ignored elsewhere.
+ */
+vegas_status vegas_adaptive_width(const vegas_ctx *ctx, double *out);
+vegas_status vegas_set_adaptive_width(vegas_ctx *ctx, const double *in);
 
 /* Counters and sizes of the context (valid also on a poisoned context). */
 vegas_status vegas_stats(const vegas_ctx *ctx, vegas_stats_t *out);

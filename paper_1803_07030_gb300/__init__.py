@@ -6,10 +6,18 @@ binding. Importing the package does not build anything; call build.build() first
 
 from .build import LIB, build  # noqa: F401
 from .vegas import (  # noqa: F401
+    POLICY_ADAPTIVE,
+    POLICY_GAUSSIAN,
+    POLICY_HINZKE_NOWAK,
+    POLICY_RANDOM,
+    POLICY_SMALL_STEP,
+    POLICY_SPIN_FLIP,
     Context,
     VegasError,
     load_library,
+    vegas_accept_history,
     vegas_accept_log,
+    vegas_adaptive_width,
     vegas_create,
     vegas_default_options,
     vegas_destroy,
@@ -18,6 +26,7 @@ from .vegas import (  # noqa: F401
     vegas_history,
     vegas_last_error,
     vegas_run,
+    vegas_set_adaptive_width,
     vegas_set_spins,
     vegas_sweep_noalloc,
     vegas_stats,

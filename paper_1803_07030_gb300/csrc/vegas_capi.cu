@@ -25,6 +25,8 @@ struct SampleInfo {
     int64_t edge_off = 0;      // first global edge
     std::vector<int32_t> cstart, lower_mode, orig;
     bool uniform_params = false, has_anisotropy = false;
+    bool has_policy = false, has_adaptive = false;
+    double sigma0 = 0.0;
     SiteParams64 u{};
     int64_t slot_base = 0;     // first partial slot (blocks)
     int32_t slot_count = 0;
@@ -54,6 +56,13 @@ struct vegas_ctx {
     int32_t *d_orig = nullptr, *d_slot_count = nullptr;
     double *d_norm = nullptr, *d_partial = nullptr, *d_sched = nullptr, *d_hist = nullptr;
     size_t sched_cap = 0, hist_cap = 0;
+    // acceptance counts and update policies
+    uint32_t *d_acc = nullptr, *d_acc_hist = nullptr;
+    size_t acc_hist_cap = 0;
+    PolicySite *d_pol = nullptr;
+    double *d_sigma = nullptr;
+    int32_t *d_adapt_n = nullptr;
+    bool any_adaptive = false;
     RunState *d_run = nullptr;
     uint32_t *d_err = nullptr;
     uint8_t *d_alog = nullptr;
@@ -80,6 +89,7 @@ struct vegas_ctx {
     std::vector<std::pair<int64_t, cudaGraphExec_t>> step_graphs;  // key: mcs * 2 + variant
     // host state
     std::vector<std::vector<double>> hist;  // per instance: records * 4
+    std::vector<std::vector<uint32_t>> acc_hist;  // per instance: accepted attempts per record
     int64_t records = 0;
     uint32_t t = 0;
     uint32_t device_error = 0;
@@ -125,7 +135,8 @@ void free_all(vegas_ctx *c) {
     if (c->graph) cudaGraphDestroy(c->graph);
     void *bufs[] = {c->d_spins, c->d_edges, c->d_p0, c->d_p1, c->d_pk, c->d_rowptr, c->d_slot_base, c->d_orig,
                     c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog,
-                    c->d_insts, c->d_cstart, c->d_queue, c->d_bar, c->d_coop_partial};
+                    c->d_insts, c->d_cstart, c->d_queue, c->d_bar, c->d_coop_partial, c->d_acc, c->d_acc_hist,
+                    c->d_pol, c->d_sigma, c->d_adapt_n};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -156,7 +167,7 @@ void enqueue_mcs(vegas_ctx *c, cudaStream_t st, std::vector<cudaEvent_t> *ev) {
         if (ev) cudaEventRecord((*ev)[2 * k + 1], st);
         ++k;
     }
-    ReduceArgs ra{c->d_partial, c->d_slot_base, c->d_slot_count, c->d_run, c->R, c->n_inst};
+    ReduceArgs ra{c->d_partial, c->d_slot_base, c->d_slot_count, c->d_run, c->d_adapt_n, c->R, c->n_inst};
     launch_reduce(ra, st);
 }
 
@@ -363,8 +374,12 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     // ---- pack samples (host staging)
     const int R = c->R;
     const bool p64 = c->precision == 64;
-    bool any_site_params = false;
-    for (auto &l : L) any_site_params |= !l.uniform_params;
+    bool any_site_params = false, any_policy = false;
+    for (auto &l : L) {
+        any_site_params |= !l.uniform_params;
+        any_policy |= !l.policy.empty();
+    }
+    std::vector<PolicySite> h_pol(any_policy ? (size_t)n_sites : 0, PolicySite{0.0, 0.f, kPolRandom});
     std::vector<int32_t> h_orig((size_t)n_sites);
     std::vector<int64_t> h_rowptr((size_t)n_sites + 1);
     std::vector<double> h_norm((size_t)n_sites);
@@ -404,6 +419,14 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         si.orig = l.orig;
         si.uniform_params = l.uniform_params;
         si.has_anisotropy = l.has_anisotropy;
+        si.has_policy = !l.policy.empty();
+        si.has_adaptive = l.has_adaptive;
+        si.sigma0 = l.sigma0;
+        c->any_adaptive |= l.has_adaptive;
+        if (si.has_policy)
+            for (int32_t g = 0; g < l.n; ++g)
+                h_pol[(size_t)(site_off + g)] = PolicySite{l.policy_param[(size_t)g], (float)l.policy_param[(size_t)g],
+                                                           l.policy[(size_t)g]};
         si.u = SiteParams64{l.field_axis[0], l.field_axis[1], l.field_axis[2], l.spin_norm[0],
                             l.e_uni[0],      l.e_uni[1],      l.e_uni[2],      l.k_uni[0], l.k_cub[0]};
         c->max_colours = std::max(c->max_colours, l.n_colours);
@@ -480,6 +503,29 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         H2D(c->d_p1, p64 ? (const void *)h_p1d.data() : (const void *)h_p1f.data(), pv * (size_t)n_sites);
         H2D(c->d_pk, p64 ? (const void *)h_pkd.data() : (const void *)h_pkf.data(), ps * (size_t)n_sites);
     }
+    if (any_policy) {
+        DALLOC(c->d_pol, sizeof(PolicySite) * (size_t)n_sites);
+        H2D(c->d_pol, h_pol.data(), sizeof(PolicySite) * (size_t)n_sites);
+    }
+    {  // accepted-attempt counters; widths of the adaptive policy and the sites they divide by
+        DALLOC(c->d_acc, sizeof(uint32_t) * (size_t)c->n_inst);
+        DALLOC(c->d_sigma, sizeof(double) * (size_t)c->n_inst);
+        DALLOC(c->d_adapt_n, sizeof(int32_t) * (size_t)c->n_inst);
+        std::vector<double> h_sigma((size_t)c->n_inst, 0.0);
+        std::vector<int32_t> h_an((size_t)c->n_inst, 0);
+        for (int32_t s = 0; s < n_samples; ++s)
+            for (int32_t r = 0; r < R; ++r) {
+                const SampleInfo &si = c->samples[(size_t)s];
+                h_sigma[(size_t)(s * R + r)] = si.has_adaptive ? si.sigma0 : 0.0;
+                h_an[(size_t)(s * R + r)] = si.has_adaptive ? si.n : 0;
+            }
+        H2D(c->d_sigma, h_sigma.data(), sizeof(double) * (size_t)c->n_inst);
+        H2D(c->d_adapt_n, h_an.data(), sizeof(int32_t) * (size_t)c->n_inst);
+        if (cudaMemsetAsync(c->d_acc, 0, sizeof(uint32_t) * (size_t)c->n_inst, c->stream) != cudaSuccess) {
+            c->err = "memset failed";
+            return bail(VEGAS_ECUDA);
+        }
+    }
     if (cudaMemsetAsync(c->d_err, 0, 4 * sizeof(uint32_t), c->stream) != cudaSuccess) {
         c->err = "memset failed";
         return bail(VEGAS_ECUDA);
@@ -512,6 +558,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
             a.p0 = si.uniform_params ? nullptr : c->d_p0;
             a.p1 = si.uniform_params ? nullptr : c->d_p1;
             a.pk = si.uniform_params ? nullptr : c->d_pk;
+            a.pol = si.has_policy ? c->d_pol : nullptr;
             a.run = c->d_run;
             a.err = c->d_err;
             a.alog = c->d_alog;
@@ -597,6 +644,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
                 I.r = r;
                 I.params_mode = si.uniform_params ? (si.has_anisotropy ? 1 : 0) : 2;
                 I.n_sample_sites = si.n;
+                I.adaptive = si.has_adaptive ? 1 : 0;
                 I.alog_base = alog_off;
                 I.u = SiteParams32{(float)si.u.nx, (float)si.u.ny, (float)si.u.nz, (float)si.u.s, (float)si.u.ex,
                                    (float)si.u.ey, (float)si.u.ez, (float)si.u.k,  (float)si.u.kc};
@@ -613,8 +661,8 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         H2D(c->d_insts, insts.data(), sizeof(ResidentInst) * insts.size());
         H2D(c->d_cstart, h_cs.data(), sizeof(int32_t) * h_cs.size());
         c->res_threads = c->max_instance_sites >= 4096 ? 512 : 256;
-        c->res_grid = (int)std::min<int64_t>((int64_t)insts.size(), (int64_t)c->sm_count *
-                                                                       resident_blocks_per_sm(c->res_threads));
+        c->res_grid = (int)std::min<int64_t>((int64_t)insts.size(),
+                                             (int64_t)c->sm_count * resident_blocks_per_sm(c->res_threads, any_policy));
         ResidentArgs &ra = c->res;
         std::memset(&ra, 0, sizeof ra);
         ra.spins = c->d_spins;
@@ -624,6 +672,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         ra.p0 = c->d_p0;
         ra.p1 = c->d_p1;
         ra.pk = c->d_pk;
+        ra.pol = any_policy ? c->d_pol : nullptr;
         ra.insts = c->d_insts;
         ra.cstart = c->d_cstart;
         ra.queue = c->d_queue;
@@ -640,8 +689,8 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         c->res_eligible = c->max_instance_sites <= (1 << 18);
     }
     // ---- cooperative sweep: one sample, every block on every class
-    if (!p64 && n_samples == 1 && !c->passes.empty()) {
-        c->coop_grid = c->sm_count * coop_blocks_per_sm();
+    if (!p64 && n_samples == 1 && !c->passes.empty() && !c->any_adaptive) {
+        c->coop_grid = c->sm_count * coop_blocks_per_sm(any_policy);
         if (o.max_blocks > 0) c->coop_grid = std::min(c->coop_grid, o.max_blocks);
         DALLOC(c->d_bar, sizeof(GridBarrier));
         DALLOC(c->d_coop_partial, sizeof(double) * 4 * (size_t)c->coop_grid * R);
@@ -658,6 +707,10 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         c->coop_eligible = true;
     }
     if (o.variant == 2) {
+        if (!c->coop_eligible) {
+            c->err = "variant 2 (cooperative) does not run samples with the adaptive policy";
+            return bail(VEGAS_EINVAL);
+        }
         c->variant = 2;
         c->tuned = true;
     } else if (o.variant == 1) {
@@ -712,6 +765,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         return bail(VEGAS_ECUDA);
     }
     c->hist.assign((size_t)c->n_inst, std::vector<double>());
+    c->acc_hist.assign((size_t)c->n_inst, std::vector<uint32_t>());
 #undef TRY
 #undef DALLOC
 #undef H2D
@@ -758,6 +812,16 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
         CK(c, dalloc(c, &c->d_hist, sizeof(double) * hneed));
         c->hist_cap = hneed;
     }
+    const size_t aneed = (size_t)nrec * NI;
+    if (aneed > c->acc_hist_cap) {
+        if (c->d_acc_hist) {
+            cudaFree(c->d_acc_hist);
+            c->device_bytes -= (int64_t)(c->acc_hist_cap * sizeof(uint32_t));
+        }
+        c->acc_hist_cap = 0;
+        CK(c, dalloc(c, &c->d_acc_hist, sizeof(uint32_t) * aneed));
+        c->acc_hist_cap = aneed;
+    }
     CK(c, cudaMemcpyAsync(c->d_sched, sched.data(), sizeof(double) * sched.size(), cudaMemcpyHostToDevice, c->stream));
     RunState rs{};
     rs.t = c->t;
@@ -766,6 +830,9 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
     rs.mcs = (uint32_t)mcs;
     rs.sched = c->d_sched;
     rs.hist = c->d_hist;
+    rs.acc = c->d_acc;
+    rs.acc_hist = c->d_acc_hist;
+    rs.sigma = c->d_sigma;
     CK(c, cudaMemcpyAsync(c->d_run, &rs, sizeof rs, cudaMemcpyHostToDevice, c->stream));
 
     const bool use_graph = c->opt.graphs && !c->opt.timing;
@@ -914,6 +981,14 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
         for (int64_t r = 0; r < nrec; ++r)
             std::memcpy(&v[old + (size_t)r * 4], &h[((size_t)r * NI + i) * 4], 4 * sizeof(double));
     }
+    std::vector<uint32_t> ha(aneed);
+    CK(c, cudaMemcpy(ha.data(), c->d_acc_hist, sizeof(uint32_t) * aneed, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < NI; ++i) {
+        auto &v = c->acc_hist[(size_t)i];
+        const size_t old = v.size();
+        v.resize(old + (size_t)nrec);
+        for (int64_t r = 0; r < nrec; ++r) v[old + (size_t)r] = ha[(size_t)r * NI + i];
+    }
     c->records += nrec;
     c->t += (uint32_t)nrec;
     c->device_error |= derr;
@@ -940,6 +1015,44 @@ extern "C" vegas_status vegas_history(const vegas_ctx *cc, double *out, size_t c
     if (capacity < need) return fail(c, VEGAS_EINVAL, "history buffer too small");
     for (int i = 0; i < c->n_inst; ++i)
         std::memcpy(out + (size_t)i * c->records * 4, c->hist[(size_t)i].data(), sizeof(double) * c->records * 4);
+    return VEGAS_OK;
+}
+
+extern "C" vegas_status vegas_accept_history(const vegas_ctx *cc, uint32_t *out, size_t capacity, size_t *n_written) {
+    vegas_ctx *c = const_cast<vegas_ctx *>(cc);
+    vegas_status st = check_usable(c);
+    if (st != VEGAS_OK) return st;
+    const size_t need = (size_t)c->n_inst * (size_t)c->records;
+    if (n_written) *n_written = need;
+    if (!out) return VEGAS_OK;
+    if (capacity < need) return fail(c, VEGAS_EINVAL, "acceptance buffer too small");
+    for (int i = 0; i < c->n_inst; ++i)
+        std::memcpy(out + (size_t)i * c->records, c->acc_hist[(size_t)i].data(), sizeof(uint32_t) * c->records);
+    return VEGAS_OK;
+}
+
+extern "C" vegas_status vegas_adaptive_width(const vegas_ctx *cc, double *out) {
+    vegas_ctx *c = const_cast<vegas_ctx *>(cc);
+    vegas_status st = check_usable(c);
+    if (st != VEGAS_OK) return st;
+    if (!out) return fail(c, VEGAS_EINVAL, "out is NULL");
+    if ((st = set_device(c)) != VEGAS_OK) return st;
+    CK(c, cudaMemcpy(out, c->d_sigma, sizeof(double) * (size_t)c->n_inst, cudaMemcpyDeviceToHost));
+    return VEGAS_OK;
+}
+
+extern "C" vegas_status vegas_set_adaptive_width(vegas_ctx *c, const double *in) {
+    vegas_status st = check_usable(c);
+    if (st != VEGAS_OK) return st;
+    if (!in) return fail(c, VEGAS_EINVAL, "in is NULL");
+    std::vector<double> h((size_t)c->n_inst, 0.0);
+    for (int32_t i = 0; i < c->n_inst; ++i) {
+        if (!c->samples[(size_t)(i / c->R)].has_adaptive) continue;
+        if (!(in[i] > 0.0) || !std::isfinite(in[i])) return fail(c, VEGAS_EINVAL, "width must be finite and > 0");
+        h[(size_t)i] = in[i];
+    }
+    if ((st = set_device(c)) != VEGAS_OK) return st;
+    CK(c, cudaMemcpy(c->d_sigma, h.data(), sizeof(double) * (size_t)c->n_inst, cudaMemcpyHostToDevice));
     return VEGAS_OK;
 }
 

@@ -18,7 +18,13 @@ constexpr uint32_t kPurposeTrial64 = 0x00000u;   // FP64 sphere candidates
 constexpr uint32_t kPurposeAccept64 = 0x10000u;  // FP64 acceptance uniform
 constexpr uint32_t kPurposeInit = 0x20000u;      // initial spins (t = 0xFFFFFFFF)
 constexpr uint32_t kPurposeTrial32 = 0x40000u;   // FP32 trial (z, azimuth) + acceptance
+constexpr uint32_t kPurposeGauss2 = 0x08000u;    // second pair of normals (FP64 | k; FP32 | trial32)
+constexpr uint32_t kPurposeChoice = 0x0C000u;    // FP64 Hinzke-Nowak choice
 constexpr uint32_t kInitT = 0xFFFFFFFFu;
+
+// Update policies (vegas_policy in the C-ABI).
+constexpr int32_t kPolRandom = 0, kPolFlip = 1, kPolSmallStep = 2, kPolGaussian = 3, kPolHinzkeNowak = 4,
+                  kPolAdaptive = 5;
 
 // Error bits set by kernels in the device error word.
 constexpr uint32_t kErrNaN = 1u;
@@ -46,6 +52,13 @@ struct LoadedSample {
     std::vector<double> init_spins;  // empty: Philox initial state
     bool uniform_params = false;     // every site has the same (s, n, k, e, kc)
     bool has_anisotropy = false;     // some k or kc is non-zero
+    // update policy per site (new numbering): code and parameter (cap height 1 - cos theta
+    // for small step and Hinzke-Nowak, width for Gaussian and adaptive); empty when every
+    // site is random
+    std::vector<int32_t> policy;
+    std::vector<double> policy_param;
+    bool has_adaptive = false;
+    double sigma0 = 0.0;             // starting width: the first adaptive type's parameter
     // per colour class: 0 = no neighbour of a lower colour, 1 = every neighbour lower,
     // 2 = mixed (tested per link)
     std::vector<int32_t> lower_mode;
@@ -68,6 +81,12 @@ struct SiteParams64 {
     double kc;
 };
 
+struct PolicySite {  // update policy of one site (samples with a policy table)
+    double par;      // cap height 1 - cos theta (small step, Hinzke-Nowak) or width (Gaussian)
+    float par32;     // the same, rounded for the FP32 path
+    int32_t code;    // kPolRandom .. kPolAdaptive
+};
+
 struct Edge64 {  // one directed link, FP64 path
     double J;
     int32_t col;  // global (packed) site index
@@ -83,6 +102,9 @@ struct RunState {
     uint32_t mcs;     // MCS per temperature/field step of the current run
     const double *sched;  // [n_steps][n_inst][2] = (beta, B)
     double *hist;         // [records][n_inst][4]
+    uint32_t *acc;        // [n_inst] accepted attempts of the current MCS, or NULL (not counted)
+    uint32_t *acc_hist;   // [records][n_inst] accepted attempts per MCS
+    double *sigma;        // [n_inst] width of the adaptive policy, or NULL
 };
 
 // One colour class of one sample: everything a sweep launch needs.
@@ -94,6 +116,7 @@ struct PassArgs {
     const void *p0;            // per-site (n, s): float4/double4_32a, or NULL when uniform
     const void *p1;            // per-site (e, k)
     const void *pk;            // per-site kc (float/double)
+    const PolicySite *pol;     // per-site update policy, or NULL (every site random)
     RunState *run;
     double *partial;           // [block][replica][4] of this pass
     uint32_t *err;
@@ -126,6 +149,7 @@ struct ReduceArgs {
     const int64_t *slot_base;  // [n_samples] first block slot of the sample
     const int32_t *slot_count; // [n_samples] block slots of the sample (all colours)
     RunState *run;
+    const int32_t *adapt_n;    // [n_inst] sites of the instance's sample if it adapts a width, else 0
     int32_t R, n_inst;
 };
 
@@ -158,7 +182,7 @@ struct ResidentInst {
     int32_t r;                 // replica within the sample
     int32_t params_mode;       // 0, 1, 2 as for PassArgs
     int32_t n_sample_sites;
-    int32_t pad_;
+    int32_t adaptive;          // 1: the sample adapts the width of its adaptive sites
     int64_t alog_base;         // accept-log offset of replica 0 of the sample
     SiteParams32 u;
 };
@@ -171,6 +195,7 @@ struct ResidentArgs {
     const int64_t *row_ptr;
     const int32_t *orig;
     const void *p0, *p1, *pk;  // per-site parameters (samples with params_mode 2)
+    const PolicySite *pol;     // per-site update policy, or NULL (every site random)
     const ResidentInst *insts; // [n_items], largest first
     const int32_t *cstart;     // class starts (global sites), n_colours + 1 per sample
     uint32_t *queue;           // work counter, zero before the launch
@@ -180,7 +205,7 @@ struct ResidentArgs {
     int64_t alog_stride;
     uint32_t alog_mcs;
     int32_t n_items, n_inst, log2R;
-    const RunState *run;       // MCS counter t, record index, MCS per step, schedule, history
+    RunState *run;             // MCS counter t, record index, MCS per step, schedule, history
     int32_t mcs;               // MCS in this launch (all inside one temperature/field step)
 };
 
@@ -223,14 +248,14 @@ void launch_scatter(void *spins, int precision, int64_t site_off, int64_t n, int
 // Blocks per SM the pass kernels reach at kThreads threads (occupancy query).
 int pass_blocks_per_sm(int precision, const PassArgs &a);
 
-// Resident sweep with `threads` per block (256, 512 or 1024).
+// Resident sweep with `threads` per block (256 or 512).
 void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream);
 // Adds n to the run state's MCS counter and record index (after a resident launch).
 void launch_advance(RunState *run, int32_t n, void *stream);
 
 // Cooperative launch (all blocks co-resident); returns the CUDA error of the launch.
 int launch_coop(const CoopArgs &a, int grid, void *stream);
-int coop_blocks_per_sm();
-int resident_blocks_per_sm(int threads);
+int coop_blocks_per_sm(bool pol);
+int resident_blocks_per_sm(int threads, bool pol);
 
 }  // namespace vegas

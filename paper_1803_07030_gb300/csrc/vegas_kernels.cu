@@ -84,31 +84,163 @@ __device__ __forceinline__ float cub32(float x, float y, float z) {
     return fmaf(xx, yy, fmaf(yy, zz, xx * zz));
 }
 
+// ------------------------------------------------------------------ FP64 update policies
+// Trial generators of the policies other than "random" (Sec. II), evaluated with the same
+// operations in the same order as the CPU oracle, so that the FP64 path stays bit-exact.
+
+// ln x for a normal x > 0: x = m 2^e with m in [sqrt(1/2), sqrt 2), ln m = 2 atanh t for
+// t = (m - 1)/(m + 1), atanh t = sum_j t^(2j+1)/(2j+1) up to j = 13 (Abramowitz & Stegun
+// 4.1.27; |t| <= 0.172, so the remainder is below 1e-20).
+__device__ double log_series64(double x) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    int e = (int)((bits >> 52) & 0x7FFull) - 1023;
+    bits = (bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    double m = __longlong_as_double((long long)bits);
+    if (m > 1.4142135623730951) {
+        m = dm(m, 0.5);
+        e += 1;
+    }
+    const double t = __ddiv_rn(ds(m, 1.0), da(m, 1.0));
+    const double t2 = dm(t, t);
+    double p = 1.0 / 27.0;
+#pragma unroll
+    for (int k = 25; k >= 1; k -= 2) p = da(dm(p, t2), 1.0 / (double)k);
+    return da(dm(dm(2.0, t), p), dm((double)e, 0.6931471805599453));
+}
+
+// Two standard normals by the polar method (Marsaglia & Bray 1964): (u1, u2) uniform in the
+// unit disk (candidate k uses counter word 3 = purpose|k), f = sqrt(-2 ln s / s).
+__device__ bool normal_pair64(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t purpose, uint32_t k0, uint32_t k1,
+                              double &g0, double &g1) {
+    for (uint32_t k = 0; k < 64; ++k) {
+        const uint4 w = philox10(make_uint4(c0, c1, c2, purpose | k), k0, k1);
+        const double u1 = ds(dm(2.0, u53(w.x, w.y)), 1.0);
+        const double u2 = ds(dm(2.0, u53(w.z, w.w)), 1.0);
+        const double s = da(dm(u1, u1), dm(u2, u2));
+        if (s >= 1.0 || s == 0.0) continue;
+        const double f = __dsqrt_rn(__ddiv_rn(dm(-2.0, log_series64(s)), s));
+        g0 = dm(u1, f);
+        g1 = dm(u2, f);
+        return true;
+    }
+    g0 = g1 = 0.0;
+    return false;
+}
+
+__device__ __forceinline__ double3 unit64(double x, double y, double z) {
+    const double q = __dsqrt_rn(da(da(dm(x, x), dm(y, y)), dm(z, z)));
+    return make_double3(__ddiv_rn(x, q), __ddiv_rn(y, q), __ddiv_rn(z, q));
+}
+
+// Orthonormal frame around the unit vector u: e1 = unit(a x u) with a the coordinate axis of
+// the smallest |u_k| (the first on ties), e2 = u x e1.
+__device__ __forceinline__ void frame64(const double3 u, double3 &e1, double3 &e2) {
+    const double ax = fabs(u.x), ay = fabs(u.y), az = fabs(u.z);
+    if (ax <= ay && ax <= az)
+        e1 = unit64(0.0, -u.z, u.y);
+    else if (ay <= az)
+        e1 = unit64(u.z, 0.0, -u.x);
+    else
+        e1 = unit64(-u.y, u.x, 0.0);
+    e2 = make_double3(ds(dm(u.y, e1.z), dm(u.z, e1.y)), ds(dm(u.z, e1.x), dm(u.x, e1.z)),
+                      ds(dm(u.x, e1.y), dm(u.y, e1.x)));
+}
+
+// Point uniform in the cap of height h = 1 - cos(theta) around the unit vector u: a disk
+// point (u1, u2) gives s = u1^2 + u2^2 uniform in [0, 1) and the azimuth; z = 1 - s h and
+// (x, y) = (u1, u2) sqrt(h (2 - s h)).
+__device__ double3 cap64(const double3 u, double h, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t purpose,
+                         uint32_t k0, uint32_t k1, uint32_t *err) {
+    for (uint32_t k = 0; k < 64; ++k) {
+        const uint4 w = philox10(make_uint4(c0, c1, c2, purpose | k), k0, k1);
+        const double u1 = ds(dm(2.0, u53(w.x, w.y)), 1.0);
+        const double u2 = ds(dm(2.0, u53(w.z, w.w)), 1.0);
+        const double s = da(dm(u1, u1), dm(u2, u2));
+        if (s >= 1.0) continue;
+        const double sh = dm(s, h);
+        const double z = ds(1.0, sh);
+        const double r = __dsqrt_rn(dm(h, ds(2.0, sh)));
+        const double x = dm(u1, r), y = dm(u2, r);
+        double3 e1, e2;
+        frame64(u, e1, e2);
+        return make_double3(da(da(dm(x, e1.x), dm(y, e2.x)), dm(z, u.x)), da(da(dm(x, e1.y), dm(y, e2.y)), dm(z, u.y)),
+                            da(da(dm(x, e1.z), dm(y, e2.z)), dm(z, u.z)));
+    }
+    atomicOr(err, kErrSphere);
+    return u;
+}
+
+// Trial direction (unit vector) of a site under its policy; the caller scales it by s_i.
+__device__ double3 policy_trial64(const PolicySite ps, double sigma, const double4_32a Si, double sn, uint32_t orig,
+                                  uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1, uint32_t *err) {
+    int code = ps.code;
+    if (code == kPolHinzkeNowak) {  // flip, random or small step with probability 1/3 each
+        const uint4 w = philox10(make_uint4(orig, t, inst, kPurposeChoice), k0, k1);
+        const double v = dm(u53(w.x, w.y), 3.0);
+        code = v < 1.0 ? kPolFlip : (v < 2.0 ? kPolRandom : kPolSmallStep);
+    }
+    if (code == kPolFlip) return make_double3(__ddiv_rn(-Si.x, sn), __ddiv_rn(-Si.y, sn), __ddiv_rn(-Si.z, sn));
+    if (code == kPolSmallStep) return cap64(unit64(Si.x, Si.y, Si.z), ps.par, orig, t, inst, kPurposeTrial64, k0, k1, err);
+    if (code == kPolGaussian || code == kPolAdaptive) {
+        const double sg = code == kPolAdaptive ? sigma : ps.par;
+        const double3 u = unit64(Si.x, Si.y, Si.z);
+        double g0, g1, g2, g3;
+        if (!normal_pair64(orig, t, inst, kPurposeTrial64, k0, k1, g0, g1)) atomicOr(err, kErrSphere);
+        if (!normal_pair64(orig, t, inst, kPurposeTrial64 | kPurposeGauss2, k0, k1, g2, g3)) atomicOr(err, kErrSphere);
+        return unit64(da(u.x, dm(sg, g0)), da(u.y, dm(sg, g1)), da(u.z, dm(sg, g2)));
+    }
+    return sphere64(orig, t, inst, kPurposeTrial64, k0, k1, err);
+}
+
+// Adaptive width after an MCS with `accepted` of n attempts accepted: sigma * 0.5 / max(1 - R,
+// 0.01) clamped to [1e-4, 100], R = accepted / n (the oracle's control law, same roundings).
+__device__ __forceinline__ double adapt_width(double sigma, uint32_t accepted, int32_t n) {
+    const double rate = __ddiv_rn((double)accepted, (double)n);
+    double f = ds(1.0, rate);
+    if (f < 0.01) f = 0.01;
+    double sg = dm(sigma, __ddiv_rn(0.5, f));
+    if (sg < 1e-4) sg = 1e-4;
+    if (sg > 100.0) sg = 100.0;
+    return sg;
+}
+
 // ------------------------------------------------------------------ block partials
 // Per-block sums of (E, Mx, My, Mz) for each replica. Lanes whose index agrees modulo R
 // hold the same replica; a fixed butterfly and a fixed warp order make the result
-// deterministic. out points at this block's [R][4] slot.
-__device__ __forceinline__ void block_partials(double v[4], int R, double *out) {
+// deterministic. out points at this block's [R][4] slot. The accepted attempts of the block
+// are added to acc[replica] (integers: the order does not matter), when acc is not NULL.
+__device__ __forceinline__ void block_partials(double v[4], uint32_t nacc, int R, double *out, uint32_t *acc) {
     __shared__ double sm[kThreads / 32][32][4];
+    __shared__ uint32_t sn[kThreads / 32][32];
     for (int off = 16; off >= R; off >>= 1) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+        nacc += __shfl_xor_sync(0xFFFFFFFFu, nacc, off);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane < R) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) sm[warp][lane][q] = v[q];
+        sn[warp][lane] = nacc;
     }
     __syncthreads();
     if ((int)threadIdx.x < R) {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        double a4[4] = {0.0, 0.0, 0.0, 0.0};
+        uint32_t na = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] += sm[w][threadIdx.x][q];
+            for (int q = 0; q < 4; ++q) a4[q] += sm[w][threadIdx.x][q];
+            na += sn[w][threadIdx.x];
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) out[threadIdx.x * 4 + q] = acc[q];
+        for (int q = 0; q < 4; ++q) out[threadIdx.x * 4 + q] = a4[q];
+        if (acc && na) atomicAdd(acc + threadIdx.x, na);
     }
+}
+
+// Accepted-attempt counters of replica 0 of a pass's sample (NULL when not counted).
+__device__ __forceinline__ uint32_t *acc_counters(const RunState *rs, int inst_local0) {
+    return rs->acc ? rs->acc + inst_local0 : nullptr;
 }
 
 // ------------------------------------------------------------------ FP64 colour pass
@@ -124,6 +256,7 @@ __global__ void __launch_bounds__(kThreads) pass64_kernel(const PassArgs a) {
     const Edge64 *E = (const Edge64 *)a.edges;
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     double acc4[4] = {0.0, 0.0, 0.0, 0.0};
+    uint32_t nacc = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += stride) {
         const int g = a.g_begin + (int)(w >> a.log2R);
@@ -161,8 +294,10 @@ __global__ void __launch_bounds__(kThreads) pass64_kernel(const PassArgs a) {
         hx = da(hx, dm(B, nx));
         hy = da(hy, dm(B, ny));
         hz = da(hz, dm(B, nz));
-        // trial: uniform on the sphere of radius s_i
-        const double3 u = sphere64(orig, t, inst, kPurposeTrial64, k0, k1, a.err);
+        // trial: uniform on the sphere of radius s_i, or the site's update policy
+        const double3 u = a.pol ? policy_trial64(a.pol[g], rs->sigma ? rs->sigma[a.inst_local0 + r] : 0.0, Si, sn, orig,
+                                                 t, inst, k0, k1, a.err)
+                                : sphere64(orig, t, inst, kPurposeTrial64, k0, k1, a.err);
         const double px = dm(sn, u.x), py = dm(sn, u.y), pz = dm(sn, u.z);
         // energy change (Eq. 1-3) in a fixed order
         const double dx = ds(px, Si.x), dy = ds(py, Si.y), dz = ds(pz, Si.z);
@@ -201,8 +336,9 @@ __global__ void __launch_bounds__(kThreads) pass64_kernel(const PassArgs a) {
         acc4[1] += qx;
         acc4[2] += qy;
         acc4[3] += qz;
+        nacc += acc ? 1u : 0u;
     }
-    block_partials(acc4, R, a.partial + (int64_t)blockIdx.x * R * 4);
+    block_partials(acc4, nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs, a.inst_local0));
 }
 
 // ------------------------------------------------------------------ FP32 attempt
@@ -214,15 +350,11 @@ struct Site32 {
     float nx, ny, nz, sn, ex, ey, ez, k, kc;
 };
 
-template <int PM, int LM>
-__device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, float hz, float lx, float ly, float lz,
-                                          const Site32 &p, float beta, float B, uint4 rw, float4 &Sn, bool &acc,
-                                          float &e_i, bool &nan_seen) {
-    const float Hx = fmaf(B, p.nx, hx), Hy = fmaf(B, p.ny, hy), Hz = fmaf(B, p.nz, hz);
-    // trial: z uniform in (-1, 1), azimuth uniform in (-pi, pi): by Archimedes' theorem the
-    // point (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z) is uniform on the sphere. Each
-    // uniform takes 23 random bits as the mantissa of a float in [1, 2): f = 1 + k 2^-23,
-    // so z = 2 (f - 1.5) + 2^-23 = (2k + 1) 2^-23 - 1 exactly (midpoints of 2^23 cells).
+// Random trial (Sec. III.B): z uniform in (-1, 1), azimuth uniform in (-pi, pi): by
+// Archimedes' theorem (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z) is uniform on the sphere.
+// Each uniform takes 23 random bits as the mantissa of a float in [1, 2): f = 1 + k 2^-23,
+// so z = 2 (f - 1.5) + 2^-23 = (2k + 1) 2^-23 - 1 exactly (midpoints of 2^23 cells).
+__device__ __forceinline__ float3 trial_random32(uint4 rw, float sn) {
     const float fz = __uint_as_float(0x3F800000u | (rw.x >> 9));
     const float fp = __uint_as_float(0x3F800000u | (rw.y >> 9));
     const float z = fmaf(__fsub_rn(fz, 1.5f), 2.0f, 0x1p-23f);
@@ -231,9 +363,20 @@ __device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, f
     __sincosf(phi, &sphi, &cphi);
     const float rho2 = fmaf(-z, z, 1.0f);
     const float rho = __fmul_rn(rho2, rsqrtf(rho2));
-    const float px = __fmul_rn(p.sn, __fmul_rn(rho, cphi));
-    const float py = __fmul_rn(p.sn, __fmul_rn(rho, sphi));
-    const float pz = __fmul_rn(p.sn, z);
+    return make_float3(__fmul_rn(sn, __fmul_rn(rho, cphi)), __fmul_rn(sn, __fmul_rn(rho, sphi)), __fmul_rn(sn, z));
+}
+
+// One Metropolis attempt in FP32 on the trial P, written with explicit roundings (fmaf
+// where a fused multiply-add is meant, __fmul_rn / __fadd_rn elsewhere) so that every
+// kernel that calls it computes bit-identical results for the same inputs, whatever the
+// surrounding code. h is the exchange field sum_j J_ij S_j (row order), l its part over
+// lower colours; wacc is the random word of the acceptance uniform.
+template <int PM, int LM>
+__device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, float hz, float lx, float ly, float lz,
+                                          const Site32 &p, float beta, float B, const float3 P, uint32_t wacc,
+                                          float4 &Sn, bool &acc, float &e_i, bool &nan_seen) {
+    const float Hx = fmaf(B, p.nx, hx), Hy = fmaf(B, p.ny, hy), Hz = fmaf(B, p.nz, hz);
+    const float px = P.x, py = P.y, pz = P.z;
     const float dx = __fsub_rn(px, Si.x), dy = __fsub_rn(py, Si.y), dz = __fsub_rn(pz, Si.z);
     float dE = -fmaf(dx, Hx, fmaf(dy, Hy, __fmul_rn(dz, Hz)));
     if (PM != 0) {
@@ -242,8 +385,8 @@ __device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, f
         dE = fmaf(-p.k, __fmul_rn(__fsub_rn(pn, po), __fadd_rn(pn, po)), dE);
         dE = fmaf(-p.kc, __fsub_rn(cub32(px, py, pz), cub32(Si.x, Si.y, Si.z)), dE);
     }
-    // Metropolis acceptance (Eq. 4) with the third word as the uniform; NaN rejects
-    const float u = __fsub_rn(__uint_as_float(0x3F800000u | (rw.z >> 9)), 1.0f);  // k 2^-23 in [0, 1)
+    // Metropolis acceptance (Eq. 4); NaN rejects
+    const float u = __fsub_rn(__uint_as_float(0x3F800000u | (wacc >> 9)), 1.0f);  // k 2^-23 in [0, 1)
     acc = (dE <= 0.f) || (u < __expf(__fmul_rn(-beta, dE)));
     nan_seen = (dE != dE);
     if (nan_seen) acc = false;
@@ -259,13 +402,76 @@ __device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, f
     e_i = e;
 }
 
+// ------------------------------------------------------------------ FP32 update policies
+// The same proposals as the FP64 path, from the attempt's Philox block (words x, y: the two
+// uniforms; z: acceptance; w: the Hinzke-Nowak choice) plus, for the Gaussian, a second block
+// (purpose kPurposeTrial32 | kPurposeGauss2) for the third normal. Normals by Box-Muller.
+__device__ __forceinline__ float u23(uint32_t w) {  // k 2^-23 in [0, 1)
+    return __fsub_rn(__uint_as_float(0x3F800000u | (w >> 9)), 1.0f);
+}
+
+__device__ __forceinline__ float3 unit32(float x, float y, float z) {
+    const float q = rsqrtf(fmaf(x, x, fmaf(y, y, __fmul_rn(z, z))));
+    return make_float3(__fmul_rn(x, q), __fmul_rn(y, q), __fmul_rn(z, q));
+}
+
+__device__ __forceinline__ float3 policy_trial32(const PolicySite ps, float sigma, const float4 Si, float sn, uint4 rw,
+                                                 uint32_t orig, uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1) {
+    int code = ps.code;
+    if (code == kPolHinzkeNowak) {
+        const float v = __fmul_rn(u23(rw.w), 3.0f);
+        code = v < 1.0f ? kPolFlip : (v < 2.0f ? kPolRandom : kPolSmallStep);
+    }
+    if (code == kPolFlip) return make_float3(-Si.x, -Si.y, -Si.z);
+    if (code == kPolRandom) return trial_random32(rw, sn);
+    const float3 u = unit32(Si.x, Si.y, Si.z);
+    float sphi, cphi;
+    const float phi = fmaf(__fsub_rn(__uint_as_float(0x3F800000u | (rw.y >> 9)), 1.5f), 6.28318530717959f,
+                           3.14159265358979f * 0x1p-23f);
+    __sincosf(phi, &sphi, &cphi);
+    if (code == kPolSmallStep) {  // uniform in the cap of height h around u
+        const float h = ps.par32;
+        const float sh = __fmul_rn(u23(rw.x), h);
+        const float z = __fsub_rn(1.0f, sh);
+        const float r = sqrtf(__fmul_rn(sh, __fsub_rn(2.0f, sh)));
+        float3 e1;
+        const float ax = fabsf(u.x), ay = fabsf(u.y), az = fabsf(u.z);
+        if (ax <= ay && ax <= az)
+            e1 = unit32(0.f, -u.z, u.y);
+        else if (ay <= az)
+            e1 = unit32(u.z, 0.f, -u.x);
+        else
+            e1 = unit32(-u.y, u.x, 0.f);
+        const float3 e2 = make_float3(fmaf(u.y, e1.z, -__fmul_rn(u.z, e1.y)), fmaf(u.z, e1.x, -__fmul_rn(u.x, e1.z)),
+                                      fmaf(u.x, e1.y, -__fmul_rn(u.y, e1.x)));
+        const float x = __fmul_rn(r, cphi), y = __fmul_rn(r, sphi);
+        return make_float3(__fmul_rn(sn, fmaf(x, e1.x, fmaf(y, e2.x, __fmul_rn(z, u.x)))),
+                           __fmul_rn(sn, fmaf(x, e1.y, fmaf(y, e2.y, __fmul_rn(z, u.y)))),
+                           __fmul_rn(sn, fmaf(x, e1.z, fmaf(y, e2.z, __fmul_rn(z, u.z)))));
+    }
+    // Gaussian (fixed width) or adaptive (the instance's width): direction of u + sigma g
+    const float sg = code == kPolAdaptive ? sigma : ps.par32;
+    const float rad = sqrtf(-2.0f * logf(__fsub_rn(1.0f, u23(rw.x))));  // 1 - u in (0, 1]
+    const uint4 w2 = philox10(make_uint4(orig, t, inst, kPurposeTrial32 | kPurposeGauss2), k0, k1);
+    float s2, c2;
+    __sincosf(fmaf(__fsub_rn(__uint_as_float(0x3F800000u | (w2.y >> 9)), 1.5f), 6.28318530717959f,
+                   3.14159265358979f * 0x1p-23f),
+              &s2, &c2);
+    const float g2 = __fmul_rn(sqrtf(-2.0f * logf(__fsub_rn(1.0f, u23(w2.x)))), c2);
+    const float3 v = unit32(fmaf(sg, __fmul_rn(rad, cphi), u.x), fmaf(sg, __fmul_rn(rad, sphi), u.y), fmaf(sg, g2, u.z));
+    return make_float3(__fmul_rn(sn, v.x), __fmul_rn(sn, v.y), __fmul_rn(sn, v.z));
+}
+
 // Per-thread sums of E and M: runs of at most 64 attempts in FP32, then FP64 (a run's
 // rounding error is below 64 * 2^-24 of its absolute sum, < 1e-5 of E/N).
+// Also counts the accepted attempts.
 struct Acc32 {
     double d[4] = {0.0, 0.0, 0.0, 0.0};
     float f[4] = {0.f, 0.f, 0.f, 0.f};
     int n = 0;
-    __device__ __forceinline__ void add(float e, float4 q) {
+    uint32_t nacc = 0;
+    __device__ __forceinline__ void add(float e, float4 q, bool ok) {
+        nacc += ok ? 1u : 0u;
         f[0] = __fadd_rn(f[0], e);
         f[1] = __fadd_rn(f[1], q.x);
         f[2] = __fadd_rn(f[2], q.y);
@@ -309,11 +515,12 @@ constexpr int kDirectRow = 12;  // rows up to this length gather all neighbours 
 // One attempt of the direct path: gathers the neighbour rows with plain loads (row order),
 // draws the trial, decides, writes, and adds the site's share of E and M. Returns the
 // decision.
-template <int PM, int LM>
+// POL = 1: the sample has an update-policy table (pol[g], the instance's width sigma).
+template <int PM, int LM, int POL>
 __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const int64_t *row_ptr, int g, int r, int R,
                                                int lower_end, uint32_t orig, const Site32 &p, float beta, float B,
                                                uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1, Acc32 &acc,
-                                               bool &nan_seen) {
+                                               bool &nan_seen, const PolicySite *pol, float sigma) {
     const int64_t si = (int64_t)g * R + r;
     const float4 Si = S[si];
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
@@ -352,13 +559,14 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
         lz = hz;
     }
     const uint4 rw = philox10(make_uint4(orig, t, inst, kPurposeTrial32), k0, k1);
+    const float3 P = POL ? policy_trial32(pol[g], sigma, Si, p.sn, rw, orig, t, inst, k0, k1) : trial_random32(rw, p.sn);
     float4 Sn;
     bool ok, bad;
     float e_i;
-    attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, rw, Sn, ok, e_i, bad);
+    attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, P, rw.z, Sn, ok, e_i, bad);
     nan_seen |= bad;
     if (ok) S[si] = Sn;
-    acc.add(e_i, Sn);
+    acc.add(e_i, Sn, ok);
     return ok;
 }
 
@@ -366,7 +574,7 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
 // Any row length: reads row_ptr and gathers neighbours with plain loads.
 // PM: params_mode (0 uniform without anisotropy, 1 uniform, 2 per site).
 // LM: lower_mode (0 no lower links, 1 all links lower, 2 test each link).
-template <int PM, int LM>
+template <int PM, int LM, int POL>
 __global__ void __launch_bounds__(kThreads) pass32_kernel(const PassArgs a) {
     const RunState *rs = a.run;
     const uint32_t t = rs->t;
@@ -383,19 +591,20 @@ __global__ void __launch_bounds__(kThreads) pass32_kernel(const PassArgs a) {
     const uint32_t inst = (uint32_t)(a.inst0 + r);
     const double *sc = rs->sched + ((int64_t)step * a.n_inst + a.inst_local0 + r) * 2;
     const float beta = (float)sc[0], B = (float)sc[1];
+    const float sigma = (POL && rs->sigma) ? (float)rs->sigma[a.inst_local0 + r] : 0.f;
     Acc32 acc;
     for (int64_t w = w0; w < n_work; w += stride) {
         const int g = a.g_begin + (int)(w >> a.log2R);
         const uint32_t orig = (uint32_t)__ldg(a.orig + g);
         bool nan_seen = false;
-        const bool ok = direct_attempt<PM, LM>(S, E, a.row_ptr, g, r, R, a.lower_end, orig, site_params32(a, PM, g), beta,
-                                               B, t, inst, k0, k1, acc, nan_seen);
+        const bool ok = direct_attempt<PM, LM, POL>(S, E, a.row_ptr, g, r, R, a.lower_end, orig, site_params32(a, PM, g),
+                                                    beta, B, t, inst, k0, k1, acc, nan_seen, a.pol, sigma);
         if (nan_seen) atomicOr(a.err, kErrNaN);
         if (a.alog && t < a.alog_mcs)
             a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
     }
     acc.flush();
-    block_partials(acc.d, R, a.partial + (int64_t)blockIdx.x * R * 4);
+    block_partials(acc.d, acc.nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs, a.inst_local0));
 }
 
 // ------------------------------------------------------------------ FP32 colour pass (staged)
@@ -450,12 +659,12 @@ __device__ __forceinline__ void staged_attempt(const PassArgs &a, const int4 *lk
     float4 Sn;
     bool ok, bad;
     float e_i;
-    attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, c, Sn, ok, e_i, bad);
+    attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, trial_random32(c, p.sn), c.z, Sn, ok, e_i, bad);
     nan_seen |= bad;
     if (ok) S[(int64_t)g * R + r] = Sn;
     if (log_accepts)
         a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
-    acc.add(e_i, Sn);
+    acc.add(e_i, Sn, ok);
 }
 
 // Geometry of the staged kernel. A group is 32 work items (spg = 32/R sites x R replicas);
@@ -634,7 +843,7 @@ __global__ void __launch_bounds__(kThreads, D == 2 ? 3 : 2) pass32_staged(const 
     cp_wait<0>();
     if (nan_seen) atomicOr(a.err, kErrNaN);
     acc.flush();
-    block_partials(acc.d, R, a.partial + (int64_t)blockIdx.x * R * 4);
+    block_partials(acc.d, acc.nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs_, a.inst_local0));
 }
 
 // Replica-batched sweep (R = 32): one warp = one site x 32 replicas, depth-2 pipeline. A
@@ -742,7 +951,7 @@ __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
     cp_wait<0>();
     if (nan_seen) atomicOr(a.err, kErrNaN);
     acc.flush();
-    block_partials(acc.d, R, a.partial + (int64_t)blockIdx.x * R * 4);
+    block_partials(acc.d, acc.nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs_, a.inst_local0));
 }
 
 // ------------------------------------------------------------------ resident (persistent) sweep
@@ -759,15 +968,17 @@ __device__ __forceinline__ Site32 resident_params(const ResidentArgs &a, const R
     return Site32{I.u.nx, I.u.ny, I.u.nz, I.u.s, I.u.ex, I.u.ey, I.u.ez, I.u.k, I.u.kc};
 }
 
-template <int NT>
+template <int NT, int POL>
 __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
     __shared__ int s_item;
     __shared__ double s_red[NT / 32][4];
+    __shared__ uint32_t s_acc[NT / 32];
     float4 *S = (float4 *)a.spins;
     const int2 *E = (const int2 *)a.edges;
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     const int R = 1 << a.log2R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    RunState *rs = a.run;
     bool nan_seen = false;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(a.queue, 1u);
@@ -776,14 +987,16 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
         __syncthreads();
         if (item >= a.n_items) break;
         const ResidentInst I = a.insts[item];
-        const uint32_t t0 = a.run->t, rec0 = a.run->rec;
-        const uint32_t step = rec0 / a.run->mcs;
-        const double *sc = a.run->sched + ((int64_t)step * a.n_inst + I.inst_local) * 2;
+        const uint32_t t0 = rs->t, rec0 = rs->rec;
+        const uint32_t step = rec0 / rs->mcs;
+        const double *sc = rs->sched + ((int64_t)step * a.n_inst + I.inst_local) * 2;
         const float beta = (float)sc[0], B = (float)sc[1];
         const uint32_t inst = (uint32_t)I.inst_id;
         for (int m = 0; m < a.mcs; ++m) {
             const uint32_t t = t0 + (uint32_t)m;
             const bool log_accepts = a.alog && t < a.alog_mcs;
+            // the width is read after the barrier that ends the previous MCS (thread 0 wrote it)
+            const float sigma = (POL && rs->sigma) ? (float)rs->sigma[I.inst_local] : 0.f;
             Acc32 acc;
             for (int c = 0; c < I.n_colours; ++c) {
                 const int cb = a.cstart[I.cls_off + c], ce = a.cstart[I.cls_off + c + 1];
@@ -792,8 +1005,8 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
                     // one code path for every parameter mode: with k = kc = 0 the anisotropy terms
                     // add signed zeros only, so spins and decisions equal the specialised paths'
                     const Site32 p = resident_params(a, I, g);
-                    const bool ok = direct_attempt<2, 2>(S, E, a.row_ptr, g, I.r, R, cb, orig, p, beta, B, t, inst, k0,
-                                                         k1, acc, nan_seen);
+                    const bool ok = direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, I.r, R, cb, orig, p, beta, B, t, inst,
+                                                              k0, k1, acc, nan_seen, a.pol, sigma);
                     if (log_accepts)
                         a.alog[(int64_t)t * a.alog_stride + I.alog_base + (int64_t)I.r * I.n_sample_sites + orig] =
                             ok ? 1 : 0;
@@ -802,24 +1015,33 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
             }
             acc.flush();
             double v[4] = {acc.d[0], acc.d[1], acc.d[2], acc.d[3]};
+            uint32_t na = acc.nacc;
             for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+                na += __shfl_xor_sync(0xFFFFFFFFu, na, off);
             }
             if (lane == 0) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) s_red[warp][q] = v[q];
+                s_acc[warp] = na;
             }
             __syncthreads();
             if (threadIdx.x == 0) {
                 double sum[4] = {0.0, 0.0, 0.0, 0.0};
+                uint32_t nsum = 0;
                 for (int w = 0; w < NT / 32; ++w) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) sum[q] += s_red[w][q];
+                    nsum += s_acc[w];
                 }
-                double *h = a.run->hist + ((int64_t)(rec0 + m) * a.n_inst + I.inst_local) * 4;
+                const int64_t rec = (int64_t)rec0 + m;
+                double *h = rs->hist + (rec * a.n_inst + I.inst_local) * 4;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) h[q] = sum[q];
+                if (rs->acc_hist) rs->acc_hist[rec * a.n_inst + I.inst_local] = nsum;
+                if (I.adaptive && rs->sigma && (uint32_t)(rec % rs->mcs) < rs->mcs / 5)
+                    rs->sigma[I.inst_local] = adapt_width(rs->sigma[I.inst_local], nsum, I.n_sample_sites);
             }
             __syncthreads();
         }
@@ -878,10 +1100,10 @@ __device__ bool grid_barrier(GridBarrier *b, uint32_t nblocks, int64_t timeout_n
     return s_ok != 0;
 }
 
-template <int NT>
+template <int NT, int POL>
 __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
     const PassArgs &a = ca.pass;
-    const RunState *rs = a.run;
+    RunState *rs = a.run;
     const uint32_t t0 = rs->t, rec0 = rs->rec;
     const uint32_t step = rec0 / rs->mcs;
     const int R = 1 << a.log2R;
@@ -909,8 +1131,8 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
                 Site32 p{a.u32.nx, a.u32.ny, a.u32.nz, a.u32.s, a.u32.ex, a.u32.ey, a.u32.ez, a.u32.k, a.u32.kc};
                 if (a.params_mode == 2) p = site_params32(a, 2, g);
                 // one code path for every parameter mode (zero constants add signed zeros)
-                const bool ok = direct_attempt<2, 2>(S, E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t, inst, k0, k1,
-                                                     acc, nan_seen);
+                const bool ok = direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t, inst, k0,
+                                                          k1, acc, nan_seen, a.pol, 0.f);
                 if (log_accepts)
                     a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
             }
@@ -918,7 +1140,7 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
         }
         // per-MCS sums: block partials per replica, then a fixed-order sum by R threads
         acc.flush();
-        block_partials(acc.d, R, ca.partial + (int64_t)blockIdx.x * R * 4);
+        block_partials(acc.d, acc.nacc, R, ca.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs, a.inst_local0));
         if (!grid_barrier(ca.bar, gridDim.x, ca.timeout_ns, a.err, skip)) return;
         if (blockIdx.x == 0) {  // one warp per replica: lanes stride over blocks, fixed tree
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -937,6 +1159,13 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
                     double *h = rs->hist + ((int64_t)(rec0 + m) * a.n_inst + a.inst_local0 + rr) * 4;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) h[q] = v[q];
+                    // every block added its count before the barrier; the next MCS adds only
+                    // after the first barrier of that MCS, which this block reaches later
+                    if (rs->acc) {
+                        const uint32_t n = rs->acc[a.inst_local0 + rr];
+                        rs->acc[a.inst_local0 + rr] = 0;
+                        if (rs->acc_hist) rs->acc_hist[(int64_t)(rec0 + m) * a.n_inst + a.inst_local0 + rr] = n;
+                    }
                 }
             }
         }
@@ -971,6 +1200,13 @@ __global__ void __launch_bounds__(256) reduce_kernel(const ReduceArgs a) {
             double *h = rs->hist + ((int64_t)rec * a.n_inst + il) * 4;
 #pragma unroll
             for (int q = 0; q < 4; ++q) h[q] = v[q];
+            if (rs->acc) {  // accepted attempts of this MCS; the adaptive width follows them
+                const uint32_t n = rs->acc[il];
+                rs->acc[il] = 0;
+                if (rs->acc_hist) rs->acc_hist[(int64_t)rec * a.n_inst + il] = n;
+                if (a.adapt_n && a.adapt_n[il] > 0 && rs->sigma && rec % rs->mcs < rs->mcs / 5)
+                    rs->sigma[il] = adapt_width(rs->sigma[il], n, a.adapt_n[il]);
+            }
         }
     }
     __syncthreads();
@@ -1076,13 +1312,20 @@ __global__ void scatter_kernel(void *spins, int precision, int64_t site_off, int
 // ------------------------------------------------------------------ variant table
 using PassFn = void (*)(PassArgs);
 
-PassFn select_direct(int pm, int lm) {
-    static const PassFn tab[3][3] = {
-        {pass32_kernel<0, 0>, pass32_kernel<0, 1>, pass32_kernel<0, 2>},
-        {pass32_kernel<1, 0>, pass32_kernel<1, 1>, pass32_kernel<1, 2>},
-        {pass32_kernel<2, 0>, pass32_kernel<2, 1>, pass32_kernel<2, 2>},
+PassFn select_direct(int pm, int lm, bool pol) {
+    static const PassFn tab[2][3][3] = {
+        {
+            {pass32_kernel<0, 0, 0>, pass32_kernel<0, 1, 0>, pass32_kernel<0, 2, 0>},
+            {pass32_kernel<1, 0, 0>, pass32_kernel<1, 1, 0>, pass32_kernel<1, 2, 0>},
+            {pass32_kernel<2, 0, 0>, pass32_kernel<2, 1, 0>, pass32_kernel<2, 2, 0>},
+        },
+        {
+            {pass32_kernel<0, 0, 1>, pass32_kernel<0, 1, 1>, pass32_kernel<0, 2, 1>},
+            {pass32_kernel<1, 0, 1>, pass32_kernel<1, 1, 1>, pass32_kernel<1, 2, 1>},
+            {pass32_kernel<2, 0, 1>, pass32_kernel<2, 1, 1>, pass32_kernel<2, 2, 1>},
+        },
     };
-    return tab[pm][lm];
+    return tab[pol ? 1 : 0][pm][lm];
 }
 
 template <int D>
@@ -1104,7 +1347,8 @@ PassFn select_r32(int pm, int lm) {
     return tab[pm][lm];
 }
 
-bool use_staged(const PassArgs &a) { return a.deg == 6 && a.depth >= 2; }
+// The staged kernels serve samples without a policy table only (random trials).
+bool use_staged(const PassArgs &a) { return a.deg == 6 && a.depth >= 2 && !a.pol; }
 bool use_r32(const PassArgs &a) { return use_staged(a) && a.log2R == 5 && a.depth == 2; }
 
 int staged_smem(const PassArgs &a) {
@@ -1118,7 +1362,7 @@ PassFn select_staged(const PassArgs &a) {
 }
 
 PassFn select32(const PassArgs &a) {
-    return use_staged(a) ? select_staged(a) : select_direct(a.params_mode, a.lower_mode);
+    return use_staged(a) ? select_staged(a) : select_direct(a.params_mode, a.lower_mode, a.pol != nullptr);
 }
 
 int smem32(const PassArgs &a) { return use_staged(a) ? staged_smem(a) : 0; }
@@ -1184,32 +1428,35 @@ int launch_coop(const CoopArgs &a, int grid, void *stream) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return (int)cudaLaunchKernelEx(&cfg, coop32_kernel<kCoopThreads>, a);
+    if (a.pass.pol) return (int)cudaLaunchKernelEx(&cfg, coop32_kernel<kCoopThreads, 1>, a);
+    return (int)cudaLaunchKernelEx(&cfg, coop32_kernel<kCoopThreads, 0>, a);
 }
 
-int coop_blocks_per_sm() {
+int coop_blocks_per_sm(bool pol) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop32_kernel<kCoopThreads>, kCoopThreads, 0);
+    if (pol)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop32_kernel<kCoopThreads, 1>, kCoopThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop32_kernel<kCoopThreads, 0>, kCoopThreads, 0);
     return nb > 0 ? nb : 1;
 }
 
-void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream) {
-    if (threads >= 1024)
-        resident32_kernel<1024><<<grid, 1024, 0, (cudaStream_t)stream>>>(a);
-    else if (threads >= 512)
-        resident32_kernel<512><<<grid, 512, 0, (cudaStream_t)stream>>>(a);
-    else
-        resident32_kernel<256><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+using ResFn = void (*)(ResidentArgs);
+
+ResFn select_resident(int threads, bool pol) {
+    if (threads >= 512) return pol ? resident32_kernel<512, 1> : resident32_kernel<512, 0>;
+    return pol ? resident32_kernel<256, 1> : resident32_kernel<256, 0>;
 }
 
-int resident_blocks_per_sm(int threads) {
+void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream) {
+    const int nt = threads >= 512 ? 512 : 256;
+    select_resident(nt, a.pol != nullptr)<<<grid, nt, 0, (cudaStream_t)stream>>>(a);
+}
+
+int resident_blocks_per_sm(int threads, bool pol) {
     int nb = 0;
-    if (threads >= 1024)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, resident32_kernel<1024>, 1024, 0);
-    else if (threads >= 512)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, resident32_kernel<512>, 512, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, resident32_kernel<256>, 256, 0);
+    const int nt = threads >= 512 ? 512 : 256;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_resident(nt, pol), nt, 0);
     return nb > 0 ? nb : 1;
 }
 

@@ -260,6 +260,47 @@ bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err) {
     }
     L.uniform_params = uni;
     L.has_anisotropy = ani;
+    // update policies per type (Sec. II): per-site code and parameter in the new numbering
+    L.policy.clear();
+    L.policy_param.clear();
+    L.has_adaptive = false;
+    L.sigma0 = 0.0;
+    if (s.n_policy_types < 0) { err = "n_policy_types < 0"; return false; }
+    if (s.n_policy_types > 0) {
+        const int32_t nt = s.n_policy_types;
+        if (!s.type_policy || !s.type_param) { err = "type_policy or type_param is NULL"; return false; }
+        std::vector<double> par((size_t)nt);
+        bool any = false;
+        for (int32_t q = 0; q < nt; ++q) {
+            const int32_t code = s.type_policy[q];
+            const double v = s.type_param[q];
+            if (code < kPolRandom || code > kPolAdaptive) { err = at("unknown update policy for type", q); return false; }
+            if ((code == kPolSmallStep || code == kPolHinzkeNowak) && !(v > 0.0 && v <= 3.141592653589793))
+                { err = at("cap half-angle outside (0, pi] for type", q); return false; }
+            if ((code == kPolGaussian || code == kPolAdaptive) && !(v > 0.0 && std::isfinite(v)))
+                { err = at("Gaussian width not finite and > 0 for type", q); return false; }
+            // the cap height 1 - cos(theta) is computed once here, in FP64 with the host libm
+            par[(size_t)q] = (code == kPolSmallStep || code == kPolHinzkeNowak) ? 1.0 - std::cos(v) : v;
+            if (code != kPolRandom) any = true;
+            if (code == kPolAdaptive && !L.has_adaptive) {
+                L.has_adaptive = true;
+                L.sigma0 = v;
+            }
+        }
+        for (int32_t i = 0; i < n; ++i) {
+            const int32_t ty = s.type ? s.type[i] : 0;
+            if (ty < 0 || ty >= nt) { err = at("site type outside the policy table at site", i); return false; }
+        }
+        if (any) {
+            L.policy.resize((size_t)n);
+            L.policy_param.resize((size_t)n);
+            for (int32_t g = 0; g < n; ++g) {
+                const int32_t ty = s.type ? s.type[L.orig[(size_t)g]] : 0;
+                L.policy[(size_t)g] = s.type_policy[ty];
+                L.policy_param[(size_t)g] = par[(size_t)ty];
+            }
+        }
+    }
     if (s.init_spins) {
         L.init_spins.resize(3 * (size_t)n);
         for (int32_t g = 0; g < n; ++g)

@@ -24,7 +24,7 @@ P = C.c_void_p
 class vegas_sample(C.Structure):
     _fields_ = [
         ("n_sites", C.c_int32),
-        ("pad_", C.c_int32),
+        ("n_policy_types", C.c_int32),
         ("n_edges", C.c_int64),
         ("row_ptr", P),
         ("col", P),
@@ -38,7 +38,12 @@ class vegas_sample(C.Structure):
         ("color", P),
         ("init_spins", P),
         ("positions", P),
+        ("type_policy", P),
+        ("type_param", P),
     ]
+
+# update policies (vegas_policy)
+POLICY_RANDOM, POLICY_SPIN_FLIP, POLICY_SMALL_STEP, POLICY_GAUSSIAN, POLICY_HINZKE_NOWAK, POLICY_ADAPTIVE = range(6)
 
 
 class vegas_options(C.Structure):
@@ -90,6 +95,9 @@ SIGNATURES = {
     "vegas_get_spins": (C.c_int, [P, C.c_int32, P]),
     "vegas_set_spins": (C.c_int, [P, C.c_int32, P]),
     "vegas_accept_log": (C.c_int, [P, P, C.c_size_t, P]),
+    "vegas_accept_history": (C.c_int, [P, P, C.c_size_t, P]),
+    "vegas_adaptive_width": (C.c_int, [P, P]),
+    "vegas_set_adaptive_width": (C.c_int, [P, P]),
     "vegas_stats": (C.c_int, [P, P]),
     "vegas_greedy_colour": (C.c_int32, [C.c_int32, P, P, P]),
     "vegas_last_error": (C.c_char_p, [P]),
@@ -179,10 +187,13 @@ class _SampleArrays:
         self.color = _arr(g("colour"), np.int32)
         self.init_spins = _arr(g("init_spins"), np.float64)
         self.positions = _arr(g("positions"), np.float64, (n, 3) if g("positions") is not None else None)
-        self.c = vegas_sample(n, 0, int(self.col.shape[0]), _ptr(self.row_ptr), _ptr(self.col), _ptr(self.J),
+        self.type_policy = _arr(g("type_policy"), np.int32)
+        self.type_param = _arr(g("type_param"), np.float64)
+        nt = 0 if self.type_policy is None else int(self.type_policy.shape[0])
+        self.c = vegas_sample(n, nt, int(self.col.shape[0]), _ptr(self.row_ptr), _ptr(self.col), _ptr(self.J),
                               _ptr(self.type), _ptr(self.spin_norm), _ptr(self.field_axis), _ptr(self.k_uni),
                               _ptr(self.e_uni), _ptr(self.k_cub), _ptr(self.color), _ptr(self.init_spins),
-                              _ptr(self.positions))
+                              _ptr(self.positions), _ptr(self.type_policy), _ptr(self.type_param))
 
 
 def vegas_create(samples: Sequence, options: vegas_options):
@@ -229,6 +240,27 @@ def vegas_accept_log(ctx) -> np.ndarray:
     if n.value:
         _check(lib.vegas_accept_log(ctx, _ptr(out), n.value, C.byref(n)), ctx)
     return out
+
+
+def vegas_accept_history(ctx) -> np.ndarray:
+    lib = load_library()
+    n = C.c_size_t()
+    _check(lib.vegas_accept_history(ctx, None, 0, C.byref(n)), ctx)
+    out = np.zeros(n.value, dtype=np.uint32)
+    if n.value:
+        _check(lib.vegas_accept_history(ctx, _ptr(out), n.value, C.byref(n)), ctx)
+    return out
+
+
+def vegas_adaptive_width(ctx, n_instances: int) -> np.ndarray:
+    out = np.zeros(n_instances, dtype=np.float64)
+    _check(load_library().vegas_adaptive_width(ctx, _ptr(out)), ctx)
+    return out
+
+
+def vegas_set_adaptive_width(ctx, widths) -> None:
+    w = _arr(widths, np.float64)
+    _check(load_library().vegas_set_adaptive_width(ctx, _ptr(w)), ctx)
 
 
 def vegas_stats(ctx) -> dict:
@@ -278,7 +310,8 @@ class Context:
     """One vegas context: samples x replicas instances on one GPU.
 
     samples: objects with numpy attributes row_ptr, col, J and optionally type, spin_norm,
-    field_axis, k_uni, e_uni, k_cub, colour, init_spins (the vegas_sample fields).
+    field_axis, k_uni, e_uni, k_cub, colour, init_spins, positions, type_policy, type_param
+    (the vegas_sample fields).
     stream: a cudaStream_t as int, 'torch' for torch's current stream, or None (own stream).
     """
 
@@ -338,6 +371,16 @@ class Context:
 
     def accept_log(self) -> np.ndarray:
         return vegas_accept_log(self.ptr)
+
+    def accept_history(self) -> np.ndarray:
+        """[n_instances, records] accepted attempts per MCS."""
+        return vegas_accept_history(self.ptr).reshape(self.n_instances, -1)
+
+    def adaptive_width(self) -> np.ndarray:
+        return vegas_adaptive_width(self.ptr, self.n_instances)
+
+    def set_adaptive_width(self, widths) -> None:
+        vegas_set_adaptive_width(self.ptr, np.broadcast_to(np.asarray(widths, dtype=np.float64), (self.n_instances,)))
 
     def stats(self) -> dict:
         return vegas_stats(self.ptr)

@@ -99,6 +99,46 @@ def test_invalid_samples_rejected(lib, name, mut, needle):
     assert needle in msg
 
 
+def _with_table(policies, params, types=None):
+    s = sc_periodic(4)
+    if types is not None:
+        s.type = np.asarray(types, dtype=np.int32)
+    return s.with_policy(policies, params)
+
+
+@pytest.mark.parametrize(
+    "name,make,needle",
+    [
+        ("unknown policy", lambda: _with_table([7], [0.0]), "unknown update policy"),
+        ("negative policy", lambda: _with_table([-1], [0.0]), "unknown update policy"),
+        ("cap angle zero", lambda: _with_table([2], [0.0]), "cap half-angle"),
+        ("cap angle above pi", lambda: _with_table([4], [3.2]), "cap half-angle"),
+        ("gaussian width zero", lambda: _with_table([3], [0.0]), "Gaussian width"),
+        ("adaptive width nan", lambda: _with_table([5], [np.nan]), "Gaussian width"),
+        ("type outside table", lambda: _with_table([0, 1], [0.0, 0.0], np.full(64, 2)), "outside the policy table"),
+        ("negative type", lambda: _with_table([0, 1], [0.0, 0.0], np.full(64, -1)), "outside the policy table"),
+    ],
+)
+def test_invalid_policy_tables_rejected(lib, name, make, needle):
+    st, msg = _create_status([make()])
+    assert st == vb.EINVAL, (name, st, msg)
+    assert needle in msg, msg
+
+
+def test_policy_table_without_params_rejected(lib):
+    import ctypes as C
+
+    s = sc_periodic(4)
+    keep = vb._SampleArrays(s)
+    pol = np.zeros(1, dtype=np.int32)
+    keep.c.n_policy_types = 1
+    keep.c.type_policy = pol.ctypes.data
+    arr = (vb.vegas_sample * 1)(keep.c)
+    out = C.c_void_p()
+    st = lib.vegas_create(arr, 1, None, C.byref(out))
+    assert st == vb.EINVAL and b"type_param is NULL" in lib.vegas_last_error(None)
+
+
 @pytest.mark.parametrize("opt", [{"precision": 16}, {"replicas": 3}, {"replicas": 64}, {"variant": 7},
                                  {"accept_log_mcs": -1}])
 def test_invalid_options_rejected(lib, opt):
