@@ -175,6 +175,28 @@ def cpu_baseline_run(sample, n_threads, mcs=1):
     return n_threads * sample.n_sites * mcs / dt, dt
 
 
+POLICY_CODES = {"random": 0, "flip": 1, "small": 2, "gauss": 3, "hn": 4, "adaptive": 5}
+POLICY_DEFAULT_PARAM = {"random": 0.0, "flip": 0.0, "small": 0.5, "gauss": 0.4, "hn": 0.5, "adaptive": 1.0}
+
+
+def apply_policy(samples, spec):
+    """spec: comma list of policy[:param], one per site type (the last one repeats for higher
+    types), e.g. "adaptive" or "random,hn:0.26". Sets each sample's policy table."""
+    if not spec:
+        return None
+    entries = []
+    for item in spec.split(","):
+        name, _, par = item.partition(":")
+        if name not in POLICY_CODES:
+            raise SystemExit(f"unknown policy {name!r}; choose from {sorted(POLICY_CODES)}")
+        entries.append((POLICY_CODES[name], float(par) if par else POLICY_DEFAULT_PARAM[name]))
+    for smp in samples:
+        n_types = int(smp.type.max()) + 1 if smp.type is not None else 1
+        table = [entries[min(k, len(entries) - 1)] for k in range(max(n_types, len(entries)))]
+        smp.with_policy([c for c, _ in table], [p for _, p in table])
+    return spec
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -225,6 +247,7 @@ def run_ours(args):
     vg.build()
     mcs = args.mcs
     s = sc_periodic(L_SIDE, bimodal_seed=SEED)
+    policy = apply_policy([s], args.policy)
     T = temperatures()[:, None]
     B = np.zeros_like(T)
     stream = torch.cuda.current_stream()
@@ -262,11 +285,15 @@ def run_ours(args):
     achieved = BYTES_PER_ATTEMPT * attempts_per_launch / (sweep_ms / 1000.0) / 1e9
     traffic = profiled_traffic()
 
-    if args.quick:
+    if args.quick or policy:
         if rank == 0:
+            cfg = dict(workload_desc(mcs))
+            if policy:
+                cfg["policy"] = policy
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms / args.steps,
-                              "config": workload_desc(mcs), "quick": True, "avg_launch_ms": sweep_ms,
-                              "achieved_gbs": achieved, "gpu_launches": launches}), flush=True)
+                              "config": cfg, "quick": True, "avg_launch_ms": sweep_ms,
+                              "achieved_gbs": achieved, "gpu_launches": launches, "clocks": clk.summary()}),
+                  flush=True)
         ctx.close()
         return 0
 
@@ -343,6 +370,7 @@ def run_workload(args):
     vg.build()
     torch.cuda.set_device(0)
     w = workload(args.workload, mcs=args.mcs if args.mcs != MCS else None)
+    policy = apply_policy(w.samples, args.policy)
     stream = torch.cuda.current_stream()
     ctx = vg.Context(w.samples, precision=w.precision, replicas=w.replicas, seed=w.seed,
                      stream=int(stream.cuda_stream))
@@ -366,12 +394,13 @@ def run_workload(args):
         "dtype": "f64" if w.precision == 64 else "f32", "data": "synthetic",
         "config": {"workload": args.workload, "instances": w.n_inst, "sites": w.n_sites_total,
                    "steps_x_mcs": [w.n_steps, w.mcs], "attempts_per_step": w.attempts(),
-                   "l2": "working set inside L2" if w.n_sites_total * 16 < 100e6 else "larger than L2"},
+                   "l2": "working set inside L2" if w.n_sites_total * 16 < 100e6 else "larger than L2",
+                   "policy": policy or "random"},
         "variant": st1["variant"], "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
         "clocks": clk.summary(),
     }
     ctx.close()
-    if args.workload == "np256":
+    if args.workload == "np256" and not policy:
         plain_mcs = min(w.mcs, 100)
         plain_ms, plain_att = 0.0, 0
         for p, smp in enumerate(w.samples):
@@ -407,6 +436,9 @@ def main():
     ap.add_argument("--workload", default="sg256x32",
                     choices=["sg256x32", "sc8_fp64", "sc64_hyst", "coreshell_fc", "np256"],
                     help="sg256x32 is the headline line; the others time one run of their schedule")
+    ap.add_argument("--policy", default="",
+                    help="update policy per site type, e.g. 'adaptive' or 'random,hn:0.26' (policy[:param], one "
+                         "per type; names: " + ", ".join(POLICY_CODES) + "); the line then reports that path")
     ap.add_argument("--quick", action="store_true",
                     help="time the sweep only (no e2e, plain-path or CPU-baseline legs); for profiling runs")
     args = ap.parse_args()

@@ -59,7 +59,8 @@ struct vegas_ctx {
     // acceptance counts and update policies
     uint32_t *d_acc = nullptr, *d_acc_hist = nullptr;
     size_t acc_hist_cap = 0;
-    PolicySite *d_pol = nullptr;
+    PolicySite *d_pol = nullptr;      // FP64 contexts
+    PolicySite32 *d_pol32 = nullptr;  // FP32 contexts
     double *d_sigma = nullptr;
     int32_t *d_adapt_n = nullptr;
     bool any_adaptive = false;
@@ -136,7 +137,7 @@ void free_all(vegas_ctx *c) {
     void *bufs[] = {c->d_spins, c->d_edges, c->d_p0, c->d_p1, c->d_pk, c->d_rowptr, c->d_slot_base, c->d_orig,
                     c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog,
                     c->d_insts, c->d_cstart, c->d_queue, c->d_bar, c->d_coop_partial, c->d_acc, c->d_acc_hist,
-                    c->d_pol, c->d_sigma, c->d_adapt_n};
+                    c->d_pol, c->d_pol32, c->d_sigma, c->d_adapt_n};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -379,7 +380,8 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         any_site_params |= !l.uniform_params;
         any_policy |= !l.policy.empty();
     }
-    std::vector<PolicySite> h_pol(any_policy ? (size_t)n_sites : 0, PolicySite{0.0, 0.f, kPolRandom});
+    std::vector<PolicySite> h_pol(any_policy && p64 ? (size_t)n_sites : 0, PolicySite{0.0, kPolRandom, 0});
+    std::vector<PolicySite32> h_pol32(any_policy && !p64 ? (size_t)n_sites : 0, PolicySite32{0.f, kPolRandom});
     std::vector<int32_t> h_orig((size_t)n_sites);
     std::vector<int64_t> h_rowptr((size_t)n_sites + 1);
     std::vector<double> h_norm((size_t)n_sites);
@@ -424,9 +426,14 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         si.sigma0 = l.sigma0;
         c->any_adaptive |= l.has_adaptive;
         if (si.has_policy)
-            for (int32_t g = 0; g < l.n; ++g)
-                h_pol[(size_t)(site_off + g)] = PolicySite{l.policy_param[(size_t)g], (float)l.policy_param[(size_t)g],
-                                                           l.policy[(size_t)g]};
+            for (int32_t g = 0; g < l.n; ++g) {
+                const double par = l.policy_param[(size_t)g];
+                const int32_t code = l.policy[(size_t)g];
+                if (p64)
+                    h_pol[(size_t)(site_off + g)] = PolicySite{par, code, 0};
+                else
+                    h_pol32[(size_t)(site_off + g)] = PolicySite32{(float)par, code};
+            }
         si.u = SiteParams64{l.field_axis[0], l.field_axis[1], l.field_axis[2], l.spin_norm[0],
                             l.e_uni[0],      l.e_uni[1],      l.e_uni[2],      l.k_uni[0], l.k_cub[0]};
         c->max_colours = std::max(c->max_colours, l.n_colours);
@@ -503,9 +510,12 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         H2D(c->d_p1, p64 ? (const void *)h_p1d.data() : (const void *)h_p1f.data(), pv * (size_t)n_sites);
         H2D(c->d_pk, p64 ? (const void *)h_pkd.data() : (const void *)h_pkf.data(), ps * (size_t)n_sites);
     }
-    if (any_policy) {
+    if (any_policy && p64) {
         DALLOC(c->d_pol, sizeof(PolicySite) * (size_t)n_sites);
         H2D(c->d_pol, h_pol.data(), sizeof(PolicySite) * (size_t)n_sites);
+    } else if (any_policy) {
+        DALLOC(c->d_pol32, sizeof(PolicySite32) * (size_t)n_sites);
+        H2D(c->d_pol32, h_pol32.data(), sizeof(PolicySite32) * (size_t)n_sites);
     }
     {  // accepted-attempt counters; widths of the adaptive policy and the sites they divide by
         DALLOC(c->d_acc, sizeof(uint32_t) * (size_t)c->n_inst);
@@ -559,6 +569,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
             a.p1 = si.uniform_params ? nullptr : c->d_p1;
             a.pk = si.uniform_params ? nullptr : c->d_pk;
             a.pol = si.has_policy ? c->d_pol : nullptr;
+            a.pol32 = si.has_policy ? c->d_pol32 : nullptr;
             a.run = c->d_run;
             a.err = c->d_err;
             a.alog = c->d_alog;
@@ -672,7 +683,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         ra.p0 = c->d_p0;
         ra.p1 = c->d_p1;
         ra.pk = c->d_pk;
-        ra.pol = any_policy ? c->d_pol : nullptr;
+        ra.pol = any_policy ? c->d_pol32 : nullptr;
         ra.insts = c->d_insts;
         ra.cstart = c->d_cstart;
         ra.queue = c->d_queue;

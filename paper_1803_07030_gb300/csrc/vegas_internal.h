@@ -81,10 +81,15 @@ struct SiteParams64 {
     double kc;
 };
 
-struct PolicySite {  // update policy of one site (samples with a policy table)
+struct PolicySite {  // update policy of one site (samples with a policy table), FP64 path
     double par;      // cap height 1 - cos theta (small step, Hinzke-Nowak) or width (Gaussian)
-    float par32;     // the same, rounded for the FP32 path
     int32_t code;    // kPolRandom .. kPolAdaptive
+    int32_t pad;
+};
+
+struct PolicySite32 {  // the same for the FP32 path (8 bytes: staged with the links)
+    float par;
+    int32_t code;
 };
 
 struct Edge64 {  // one directed link, FP64 path
@@ -116,7 +121,8 @@ struct PassArgs {
     const void *p0;            // per-site (n, s): float4/double4_32a, or NULL when uniform
     const void *p1;            // per-site (e, k)
     const void *pk;            // per-site kc (float/double)
-    const PolicySite *pol;     // per-site update policy, or NULL (every site random)
+    const PolicySite *pol;     // FP64: per-site update policy, or NULL (every site random)
+    const PolicySite32 *pol32; // FP32: the same
     RunState *run;
     double *partial;           // [block][replica][4] of this pass
     uint32_t *err;
@@ -195,7 +201,7 @@ struct ResidentArgs {
     const int64_t *row_ptr;
     const int32_t *orig;
     const void *p0, *p1, *pk;  // per-site parameters (samples with params_mode 2)
-    const PolicySite *pol;     // per-site update policy, or NULL (every site random)
+    const PolicySite32 *pol;   // per-site update policy, or NULL (every site random)
     const ResidentInst *insts; // [n_items], largest first
     const int32_t *cstart;     // class starts (global sites), n_colours + 1 per sample
     uint32_t *queue;           // work counter, zero before the launch

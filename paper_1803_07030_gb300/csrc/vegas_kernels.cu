@@ -415,7 +415,7 @@ __device__ __forceinline__ float3 unit32(float x, float y, float z) {
     return make_float3(__fmul_rn(x, q), __fmul_rn(y, q), __fmul_rn(z, q));
 }
 
-__device__ __forceinline__ float3 policy_trial32(const PolicySite ps, float sigma, const float4 Si, float sn, uint4 rw,
+__device__ __forceinline__ float3 policy_trial32(const PolicySite32 ps, float sigma, const float4 Si, float sn, uint4 rw,
                                                  uint32_t orig, uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1) {
     int code = ps.code;
     if (code == kPolHinzkeNowak) {
@@ -430,7 +430,7 @@ __device__ __forceinline__ float3 policy_trial32(const PolicySite ps, float sigm
                            3.14159265358979f * 0x1p-23f);
     __sincosf(phi, &sphi, &cphi);
     if (code == kPolSmallStep) {  // uniform in the cap of height h around u
-        const float h = ps.par32;
+        const float h = ps.par;
         const float sh = __fmul_rn(u23(rw.x), h);
         const float z = __fsub_rn(1.0f, sh);
         const float r = sqrtf(__fmul_rn(sh, __fsub_rn(2.0f, sh)));
@@ -450,7 +450,7 @@ __device__ __forceinline__ float3 policy_trial32(const PolicySite ps, float sigm
                            __fmul_rn(sn, fmaf(x, e1.z, fmaf(y, e2.z, __fmul_rn(z, u.z)))));
     }
     // Gaussian (fixed width) or adaptive (the instance's width): direction of u + sigma g
-    const float sg = code == kPolAdaptive ? sigma : ps.par32;
+    const float sg = code == kPolAdaptive ? sigma : ps.par;
     const float rad = sqrtf(-2.0f * logf(__fsub_rn(1.0f, u23(rw.x))));  // 1 - u in (0, 1]
     const uint4 w2 = philox10(make_uint4(orig, t, inst, kPurposeTrial32 | kPurposeGauss2), k0, k1);
     float s2, c2;
@@ -520,7 +520,7 @@ template <int PM, int LM, int POL>
 __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const int64_t *row_ptr, int g, int r, int R,
                                                int lower_end, uint32_t orig, const Site32 &p, float beta, float B,
                                                uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1, Acc32 &acc,
-                                               bool &nan_seen, const PolicySite *pol, float sigma) {
+                                               bool &nan_seen, const PolicySite32 *pol, float sigma) {
     const int64_t si = (int64_t)g * R + r;
     const float4 Si = S[si];
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
@@ -575,7 +575,7 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
 // PM: params_mode (0 uniform without anisotropy, 1 uniform, 2 per site).
 // LM: lower_mode (0 no lower links, 1 all links lower, 2 test each link).
 template <int PM, int LM, int POL>
-__global__ void __launch_bounds__(kThreads) pass32_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) pass32_kernel(const PassArgs a) {
     const RunState *rs = a.run;
     const uint32_t t = rs->t;
     const uint32_t step = rs->rec / rs->mcs;
@@ -598,7 +598,7 @@ __global__ void __launch_bounds__(kThreads) pass32_kernel(const PassArgs a) {
         const uint32_t orig = (uint32_t)__ldg(a.orig + g);
         bool nan_seen = false;
         const bool ok = direct_attempt<PM, LM, POL>(S, E, a.row_ptr, g, r, R, a.lower_end, orig, site_params32(a, PM, g),
-                                                    beta, B, t, inst, k0, k1, acc, nan_seen, a.pol, sigma);
+                                                    beta, B, t, inst, k0, k1, acc, nan_seen, a.pol32, sigma);
         if (nan_seen) atomicOr(a.err, kErrNaN);
         if (a.alog && t < a.alog_mcs)
             a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
@@ -622,6 +622,10 @@ __device__ __forceinline__ void cp4(void *smem, const void *gmem) {
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp8(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -629,12 +633,13 @@ __device__ __forceinline__ void cp_wait() {
 }
 
 // One staged attempt: links lk (int4 pairs), rows row[j*32] (neighbour j) and row[DEG*32]
-// (own) already in shared memory.
-template <int DEG, int PM, int LM>
+// (own) already in shared memory; with POL, the site's update policy *ps too.
+template <int DEG, int PM, int LM, int POL = 0>
 __device__ __forceinline__ void staged_attempt(const PassArgs &a, const int4 *lk, const float4 *row, uint32_t orig,
                                                int g, int r, int R, uint32_t t, uint32_t inst, const uint32_t *rk0,
                                                const uint32_t *rk1, float beta, float B, float4 *S, Acc32 &acc,
-                                               bool &nan_seen, bool log_accepts) {
+                                               bool &nan_seen, bool log_accepts, const PolicySite32 *ps = nullptr,
+                                               float sigma = 0.f) {
     const Site32 p = site_params32(a, PM, g);
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
 #pragma unroll
@@ -659,7 +664,9 @@ __device__ __forceinline__ void staged_attempt(const PassArgs &a, const int4 *lk
     float4 Sn;
     bool ok, bad;
     float e_i;
-    attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, trial_random32(c, p.sn), c.z, Sn, ok, e_i, bad);
+    const float3 P =
+        POL ? policy_trial32(*ps, sigma, Si, p.sn, c, orig, t, inst, rk0[0], rk1[0]) : trial_random32(c, p.sn);
+    attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, P, c.z, Sn, ok, e_i, bad);
     nan_seen |= bad;
     if (ok) S[(int64_t)g * R + r] = Sn;
     if (log_accepts)
@@ -852,12 +859,14 @@ __global__ void __launch_bounds__(kThreads, D == 2 ? 3 : 2) pass32_staged(const 
 // group j of block b computes from row slot j & 1 and link slot b & 1; at j = 4 the links of
 // the next block are copied; rows of group j + 2 (the next block's first two at j = 6, 7)
 // are copied at the end of group j.
-template <int PM, int LM>
+// POL = 1 adds the sites' update policies (8 bytes each, staged with the caller ids).
+template <int PM, int LM, int POL>
 __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
     constexpr int DEG = 6, D = 2, BS = 8, R = 32;
     constexpr int ROWS = D * (DEG + 1) * 32 * 16;
     constexpr int LINK_BYTES = BS * DEG * 8;
-    constexpr int SLOT = LINK_BYTES + BS * 4;
+    constexpr int POL_OFF = LINK_BYTES + BS * 4;
+    constexpr int SLOT = POL_OFF + (POL ? BS * 8 : 0);
     constexpr int WARP_BYTES = ROWS + 2 * SLOT;
     extern __shared__ __align__(16) unsigned char smem[];
     const RunState *rs_ = a.run;
@@ -874,6 +883,7 @@ __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
     const uint32_t inst = (uint32_t)(a.inst0 + r);
     const double *sc = rs_->sched + ((int64_t)step_idx * a.n_inst + a.inst_local0 + r) * 2;
     const float beta = (float)sc[0], B = (float)sc[1];
+    const float sigma = (POL && rs_->sigma) ? (float)rs_->sigma[a.inst_local0 + r] : 0.f;
     const int g_end = a.g_end;
     const int nwarps = blockDim.x >> 5;
     const int bstride = gridDim.x * nwarps * BS;
@@ -899,6 +909,7 @@ __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
         VEGAS_CHECK(((uintptr_t)src & 15) == 0, 13, sb);
         if (lane < ns * (DEG / 2)) cp16(dst + 16 * lane, src + 16 * lane);
         if (lane < ns) cp4(dst + LINK_BYTES + 4 * lane, a.orig + sb + lane);
+        if (POL && lane < ns) cp8(dst + POL_OFF + 8 * lane, a.pol32 + sb + lane);
     };
     auto issue_rows = [&](int g, int lslot, int j, int rslot) {
         if (g >= g_end) return;
@@ -936,8 +947,10 @@ __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
             if (g < g_end) {
                 const unsigned char *slot = lslots + ls * SLOT;
                 const uint32_t orig = ((const uint32_t *)(slot + LINK_BYTES))[j];
-                staged_attempt<DEG, PM, LM>(a, (const int4 *)slot + j * (DEG / 2), rows + (j & 1) * (DEG + 1) * 32 + lane,
-                                            orig, g, r, R, t, inst, rk0, rk1, beta, B, S, acc, nan_seen, log_accepts);
+                staged_attempt<DEG, PM, LM, POL>(a, (const int4 *)slot + j * (DEG / 2),
+                                                 rows + (j & 1) * (DEG + 1) * 32 + lane, orig, g, r, R, t, inst, rk0, rk1,
+                                                 beta, B, S, acc, nan_seen, log_accepts,
+                                                 (const PolicySite32 *)(slot + POL_OFF) + j, sigma);
             }
             __syncwarp();
             if (j == 4) issue_links(sb + bstride, ls ^ 1);
@@ -1132,7 +1145,7 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
                 if (a.params_mode == 2) p = site_params32(a, 2, g);
                 // one code path for every parameter mode (zero constants add signed zeros)
                 const bool ok = direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t, inst, k0,
-                                                          k1, acc, nan_seen, a.pol, 0.f);
+                                                          k1, acc, nan_seen, a.pol32, 0.f);
                 if (log_accepts)
                     a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
             }
@@ -1338,31 +1351,39 @@ PassFn select_staged6(int pm, int lm) {
     return tab[pm][lm];
 }
 
-PassFn select_r32(int pm, int lm) {
-    static const PassFn tab[3][3] = {
-        {pass32_r32<0, 0>, pass32_r32<0, 1>, pass32_r32<0, 2>},
-        {pass32_r32<1, 0>, pass32_r32<1, 1>, pass32_r32<1, 2>},
-        {pass32_r32<2, 0>, pass32_r32<2, 1>, pass32_r32<2, 2>},
+PassFn select_r32(int pm, int lm, bool pol) {
+    static const PassFn tab[2][3][3] = {
+        {
+            {pass32_r32<0, 0, 0>, pass32_r32<0, 1, 0>, pass32_r32<0, 2, 0>},
+            {pass32_r32<1, 0, 0>, pass32_r32<1, 1, 0>, pass32_r32<1, 2, 0>},
+            {pass32_r32<2, 0, 0>, pass32_r32<2, 1, 0>, pass32_r32<2, 2, 0>},
+        },
+        {
+            {pass32_r32<0, 0, 1>, pass32_r32<0, 1, 1>, pass32_r32<0, 2, 1>},
+            {pass32_r32<1, 0, 1>, pass32_r32<1, 1, 1>, pass32_r32<1, 2, 1>},
+            {pass32_r32<2, 0, 1>, pass32_r32<2, 1, 1>, pass32_r32<2, 2, 1>},
+        },
     };
-    return tab[pm][lm];
+    return tab[pol ? 1 : 0][pm][lm];
 }
 
-// The staged kernels serve samples without a policy table only (random trials).
-bool use_staged(const PassArgs &a) { return a.deg == 6 && a.depth >= 2 && !a.pol; }
-bool use_r32(const PassArgs &a) { return use_staged(a) && a.log2R == 5 && a.depth == 2; }
+bool staged_shape(const PassArgs &a) { return a.deg == 6 && a.depth >= 2; }
+bool use_r32(const PassArgs &a) { return staged_shape(a) && a.log2R == 5 && a.depth == 2; }
+// Samples with a policy table take the staged path only through the R = 32 kernel.
+bool use_staged(const PassArgs &a) { return staged_shape(a) && (!a.pol32 || use_r32(a)); }
 
 int staged_smem(const PassArgs &a) {
-    if (use_r32(a)) return (kThreads / 32) * (2 * 7 * 32 * 16 + 2 * (8 * 6 * 8 + 8 * 4));
+    if (use_r32(a)) return (kThreads / 32) * (2 * 7 * 32 * 16 + 2 * (8 * 6 * 8 + 8 * 4 + (a.pol32 ? 8 * 8 : 0)));
     return (kThreads / 32) * staged_geom(6, a.depth, a.log2R).warp_bytes;
 }
 
 PassFn select_staged(const PassArgs &a) {
-    if (use_r32(a)) return select_r32(a.params_mode, a.lower_mode);
+    if (use_r32(a)) return select_r32(a.params_mode, a.lower_mode, a.pol32 != nullptr);
     return a.depth == 2 ? select_staged6<2>(a.params_mode, a.lower_mode) : select_staged6<3>(a.params_mode, a.lower_mode);
 }
 
 PassFn select32(const PassArgs &a) {
-    return use_staged(a) ? select_staged(a) : select_direct(a.params_mode, a.lower_mode, a.pol != nullptr);
+    return use_staged(a) ? select_staged(a) : select_direct(a.params_mode, a.lower_mode, a.pol32 != nullptr);
 }
 
 int smem32(const PassArgs &a) { return use_staged(a) ? staged_smem(a) : 0; }
@@ -1428,7 +1449,7 @@ int launch_coop(const CoopArgs &a, int grid, void *stream) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (a.pass.pol) return (int)cudaLaunchKernelEx(&cfg, coop32_kernel<kCoopThreads, 1>, a);
+    if (a.pass.pol32) return (int)cudaLaunchKernelEx(&cfg, coop32_kernel<kCoopThreads, 1>, a);
     return (int)cudaLaunchKernelEx(&cfg, coop32_kernel<kCoopThreads, 0>, a);
 }
 

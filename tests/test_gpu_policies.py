@@ -273,3 +273,18 @@ def test_invalid_policy_tables_rejected_on_device_context():
     with pytest.raises(vg.VegasError) as e:
         ctx([s])
     assert "outside the policy table" in str(e.value)
+
+
+def test_replica_batched_policy_kernel_equals_direct_kernel():
+    """R = 32 on six-link rows: the staged kernel with policies against the direct kernel."""
+    s = mixed_sc(L=16, seed=12)
+    T = np.linspace(0.3, 2.5, 32)[:, None]
+    B = np.full_like(T, 0.1)
+    with ctx([s], replicas=32, seed=35, variant=0) as a, \
+            ctx([s], replicas=32, seed=35, variant=0, pipeline_depth=1) as b:
+        a.run(T, B, 10)
+        b.run(T, B, 10)
+        assert np.array_equal(a.accept_history(), b.accept_history())
+        assert np.array_equal(a.adaptive_width(), b.adaptive_width())
+        for i in (0, 13, 31):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
