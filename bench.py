@@ -254,7 +254,7 @@ def run_ours(args):
     inst_base = rank_instances(rank, world)[0]
     t0 = time.perf_counter()
     ctx = vg.Context([s], precision=32, replicas=REPLICAS, seed=SEED, inst_base=inst_base, device=dev,
-                     stream=int(stream.cuda_stream), timing=True)
+                     stream=int(stream.cuda_stream), timing=True, variant=args.variant)
     create_s = time.perf_counter() - t0
 
     def barrier():
@@ -292,7 +292,8 @@ def run_ours(args):
                 cfg["policy"] = policy
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms / args.steps,
                               "config": cfg, "quick": True, "avg_launch_ms": sweep_ms,
-                              "achieved_gbs": achieved, "gpu_launches": launches, "clocks": clk.summary()}),
+                              "achieved_gbs": achieved, "gpu_launches": launches, "variant": st1["variant"],
+                              "clocks": clk.summary()}),
                   flush=True)
         ctx.close()
         return 0
@@ -349,6 +350,7 @@ def run_ours(args):
                       "note": "same lattice, one replica per context (R = 1), one launch per colour class"},
             "batched_over_plain": value / world / plain_value,
             "gpu_launches": launches,
+            "variant": st1["variant"],
             "create_s": create_s,
             "clocks": clk.summary(),
         }
@@ -373,7 +375,7 @@ def run_workload(args):
     policy = apply_policy(w.samples, args.policy)
     stream = torch.cuda.current_stream()
     ctx = vg.Context(w.samples, precision=w.precision, replicas=w.replicas, seed=w.seed,
-                     stream=int(stream.cuda_stream))
+                     stream=int(stream.cuda_stream), variant=args.variant)
     for _ in range(args.warmup):
         ctx.run(w.T, w.B, w.mcs)
     torch.cuda.synchronize()
@@ -439,6 +441,9 @@ def main():
     ap.add_argument("--policy", default="",
                     help="update policy per site type, e.g. 'adaptive' or 'random,hn:0.26' (policy[:param], one "
                          "per type; names: " + ", ".join(POLICY_CODES) + "); the line then reports that path")
+    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="sweep variant: -1 automatic (timed on the first run), 0 per colour class, 1 resident, "
+                         "2 cooperative; profiling commands fix it because ncu distorts the automatic timing")
     ap.add_argument("--quick", action="store_true",
                     help="time the sweep only (no e2e, plain-path or CPU-baseline legs); for profiling runs")
     args = ap.parse_args()

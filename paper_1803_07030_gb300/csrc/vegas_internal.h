@@ -18,7 +18,7 @@ constexpr uint32_t kPurposeTrial64 = 0x00000u;   // FP64 sphere candidates
 constexpr uint32_t kPurposeAccept64 = 0x10000u;  // FP64 acceptance uniform
 constexpr uint32_t kPurposeInit = 0x20000u;      // initial spins (t = 0xFFFFFFFF)
 constexpr uint32_t kPurposeTrial32 = 0x40000u;   // FP32 trial (z, azimuth) + acceptance
-constexpr uint32_t kPurposeGauss2 = 0x08000u;    // second pair of normals (FP64 | k; FP32 | trial32)
+constexpr uint32_t kPurposeGauss2 = 0x08000u;    // FP64 Gaussian: second pair of normals (| k)
 constexpr uint32_t kPurposeChoice = 0x0C000u;    // FP64 Hinzke-Nowak choice
 constexpr uint32_t kInitT = 0xFFFFFFFFu;
 

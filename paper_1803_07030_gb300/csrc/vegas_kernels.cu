@@ -403,9 +403,10 @@ __device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, f
 }
 
 // ------------------------------------------------------------------ FP32 update policies
-// The same proposals as the FP64 path, from the attempt's Philox block (words x, y: the two
-// uniforms; z: acceptance; w: the Hinzke-Nowak choice) plus, for the Gaussian, a second block
-// (purpose kPurposeTrial32 | kPurposeGauss2) for the third normal. Normals by Box-Muller.
+// The same proposals as the FP64 path, drawn from the attempt's one Philox block: words x and
+// y are the two uniforms, z the acceptance uniform, w the Hinzke-Nowak choice or, for the
+// Gaussian, the third normal (inverse error function of a 23-bit uniform; the first two
+// come from Box-Muller on x and y).
 __device__ __forceinline__ float u23(uint32_t w) {  // k 2^-23 in [0, 1)
     return __fsub_rn(__uint_as_float(0x3F800000u | (w >> 9)), 1.0f);
 }
@@ -415,12 +416,16 @@ __device__ __forceinline__ float3 unit32(float x, float y, float z) {
     return make_float3(__fmul_rn(x, q), __fmul_rn(y, q), __fmul_rn(z, q));
 }
 
-__device__ __forceinline__ float3 policy_trial32(const PolicySite32 ps, float sigma, const float4 Si, float sn, uint4 rw,
-                                                 uint32_t orig, uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1) {
+constexpr int kPolCapSphere = 6;  // internal: the random third of Hinzke-Nowak, as a cap of height 2
+
+__device__ __forceinline__ float3 policy_trial32(const PolicySite32 ps, float sigma, const float4 Si, float sn,
+                                                 uint4 rw) {
     int code = ps.code;
     if (code == kPolHinzkeNowak) {
+        // a uniform point on the sphere is the cap of height 2 around any axis, so the random
+        // and small-step thirds share one code path (no divergence between them in a warp)
         const float v = __fmul_rn(u23(rw.w), 3.0f);
-        code = v < 1.0f ? kPolFlip : (v < 2.0f ? kPolRandom : kPolSmallStep);
+        code = v < 1.0f ? kPolFlip : (v < 2.0f ? kPolCapSphere : kPolSmallStep);
     }
     if (code == kPolFlip) return make_float3(-Si.x, -Si.y, -Si.z);
     if (code == kPolRandom) return trial_random32(rw, sn);
@@ -429,11 +434,11 @@ __device__ __forceinline__ float3 policy_trial32(const PolicySite32 ps, float si
     const float phi = fmaf(__fsub_rn(__uint_as_float(0x3F800000u | (rw.y >> 9)), 1.5f), 6.28318530717959f,
                            3.14159265358979f * 0x1p-23f);
     __sincosf(phi, &sphi, &cphi);
-    if (code == kPolSmallStep) {  // uniform in the cap of height h around u
-        const float h = ps.par;
+    if (code == kPolSmallStep || code == kPolCapSphere) {  // uniform in the cap of height h around u
+        const float h = code == kPolCapSphere ? 2.0f : ps.par;
         const float sh = __fmul_rn(u23(rw.x), h);
         const float z = __fsub_rn(1.0f, sh);
-        const float r = sqrtf(__fmul_rn(sh, __fsub_rn(2.0f, sh)));
+        const float r = sqrtf(fmaxf(__fmul_rn(sh, __fsub_rn(2.0f, sh)), 0.0f));
         float3 e1;
         const float ax = fabsf(u.x), ay = fabsf(u.y), az = fabsf(u.z);
         if (ax <= ay && ax <= az)
@@ -452,12 +457,8 @@ __device__ __forceinline__ float3 policy_trial32(const PolicySite32 ps, float si
     // Gaussian (fixed width) or adaptive (the instance's width): direction of u + sigma g
     const float sg = code == kPolAdaptive ? sigma : ps.par;
     const float rad = sqrtf(-2.0f * logf(__fsub_rn(1.0f, u23(rw.x))));  // 1 - u in (0, 1]
-    const uint4 w2 = philox10(make_uint4(orig, t, inst, kPurposeTrial32 | kPurposeGauss2), k0, k1);
-    float s2, c2;
-    __sincosf(fmaf(__fsub_rn(__uint_as_float(0x3F800000u | (w2.y >> 9)), 1.5f), 6.28318530717959f,
-                   3.14159265358979f * 0x1p-23f),
-              &s2, &c2);
-    const float g2 = __fmul_rn(sqrtf(-2.0f * logf(__fsub_rn(1.0f, u23(w2.x)))), c2);
+    // (2k + 1) 2^-23 - 1 lies strictly inside (-1, 1); sqrt 2 erfinv of it is standard normal
+    const float g2 = __fmul_rn(1.41421356237310f, erfinvf(fmaf(u23(rw.w), 2.0f, -1.0f + 0x1p-23f)));
     const float3 v = unit32(fmaf(sg, __fmul_rn(rad, cphi), u.x), fmaf(sg, __fmul_rn(rad, sphi), u.y), fmaf(sg, g2, u.z));
     return make_float3(__fmul_rn(sn, v.x), __fmul_rn(sn, v.y), __fmul_rn(sn, v.z));
 }
@@ -559,7 +560,7 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
         lz = hz;
     }
     const uint4 rw = philox10(make_uint4(orig, t, inst, kPurposeTrial32), k0, k1);
-    const float3 P = POL ? policy_trial32(pol[g], sigma, Si, p.sn, rw, orig, t, inst, k0, k1) : trial_random32(rw, p.sn);
+    const float3 P = POL ? policy_trial32(pol[g], sigma, Si, p.sn, rw) : trial_random32(rw, p.sn);
     float4 Sn;
     bool ok, bad;
     float e_i;
@@ -665,7 +666,7 @@ __device__ __forceinline__ void staged_attempt(const PassArgs &a, const int4 *lk
     bool ok, bad;
     float e_i;
     const float3 P =
-        POL ? policy_trial32(*ps, sigma, Si, p.sn, c, orig, t, inst, rk0[0], rk1[0]) : trial_random32(c, p.sn);
+        POL ? policy_trial32(*ps, sigma, Si, p.sn, c) : trial_random32(c, p.sn);
     attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, P, c.z, Sn, ok, e_i, bad);
     nan_seen |= bad;
     if (ok) S[(int64_t)g * R + r] = Sn;
