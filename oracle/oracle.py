@@ -45,6 +45,17 @@ class _Sample(C.Structure):
 RANDOM, SPIN_FLIP, SMALL_STEP, GAUSSIAN, HINZKE_NOWAK, ADAPTIVE = range(6)
 
 
+class _Extra(C.Structure):
+    _fields_ = [
+        ("acc_hist", C.c_void_p),
+        ("sigma_inout", C.c_void_p),
+        ("type_hist", C.c_void_p),
+        ("n_types", C.c_int32),
+        ("pad_", C.c_int32),
+        ("snaps", C.c_void_p),
+    ]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with FMA contraction off; returns the path of the .so."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
@@ -77,8 +88,8 @@ def _configure(lib):
     lib.vo_run.argtypes = [P, P, C.c_uint64, C.c_int32, C.c_int32, P, P, C.c_int32, C.c_int32,
                            C.c_uint32, P, C.c_int32, P, P, C.c_int32, C.c_int32, C.c_int32]
     lib.vo_run.restype = C.c_int
-    lib.vo_run2.argtypes = lib.vo_run.argtypes + [P, P]
-    lib.vo_run2.restype = C.c_int
+    lib.vo_run_ex.argtypes = lib.vo_run.argtypes + [P]
+    lib.vo_run_ex.restype = C.c_int
     lib.vo_log.argtypes = [C.c_double]
     lib.vo_log.restype = C.c_double
     lib.vo_cap_height.argtypes = [C.c_double]
@@ -246,14 +257,17 @@ def trial(sample, S, i: int, seed: int, t: int, inst: int, sigma: float = 0.0):
 
 
 def run(sample, T, B, mcs: int, seed: int = 1, spins=None, inst_base: int = 0, t0: int = 0,
-        colour=None, log_mcs: int = 0, mode: int = 0, n_threads: int = 1, sigma=None):
+        colour=None, log_mcs: int = 0, mode: int = 0, n_threads: int = 1, sigma=None, n_types: int = 0,
+        snapshots: bool = False):
     """Run the chain for every instance in T's first axis.
 
     T, B: [n_inst, n_steps]. spins: None (Philox initial state) or [n_inst, n, 3].
     sigma: None or [n_inst] starting widths of the adaptive policy (<= 0: the policy's
-    parameter). Returns dict(spins=[n_inst,n,3], history=[n_inst, n_steps*mcs, 4],
-    accepted=[n_inst, n_steps*mcs] int64, sigma=[n_inst], accept_log=[n_inst, log_mcs, n]
-    uint8 or None, err=int).
+    parameter). n_types > 0: also the magnetization per site type after every MCS.
+    snapshots: also the spins at the end of every step. Returns dict(spins=[n_inst,n,3],
+    history=[n_inst, n_steps*mcs, 4], accepted=[n_inst, n_steps*mcs] int64, sigma=[n_inst],
+    accept_log=[n_inst, log_mcs, n] uint8 or None, type_history=[n_inst, n_steps*mcs,
+    n_types, 3] or None, snapshots=[n_inst, n_steps, n, 3] or None, err=int).
     """
     T = np.ascontiguousarray(np.atleast_2d(T), dtype=np.float64)
     B = np.ascontiguousarray(np.broadcast_to(np.atleast_2d(B), T.shape), dtype=np.float64)
@@ -267,8 +281,12 @@ def run(sample, T, B, mcs: int, seed: int = 1, spins=None, inst_base: int = 0, t
     cl = None if colour is None else np.ascontiguousarray(colour, dtype=np.int32)
     acc = np.zeros((n_inst, n_steps * mcs), dtype=np.int64)
     sg = np.zeros(n_inst) if sigma is None else np.array(np.broadcast_to(sigma, (n_inst,)), dtype=np.float64)
-    err = _load().vo_run2(b.ref, _ptr(cl), seed, n_inst, inst_base, _ptr(T), _ptr(B), n_steps, mcs, t0, _ptr(S),
-                          init, _ptr(hist), _ptr(alog), log_mcs, mode, n_threads, _ptr(acc), _ptr(sg))
+    th = np.zeros((n_inst, n_steps * mcs, n_types, 3)) if n_types > 0 else None
+    snaps = np.zeros((n_inst, n_steps, n, 3)) if snapshots else None
+    x = _Extra(_ptr(acc), _ptr(sg), _ptr(th), int(n_types), 0, _ptr(snaps))
+    err = _load().vo_run_ex(b.ref, _ptr(cl), seed, n_inst, inst_base, _ptr(T), _ptr(B), n_steps, mcs, t0, _ptr(S),
+                            init, _ptr(hist), _ptr(alog), log_mcs, mode, n_threads, C.byref(x))
     if err < 0:
         raise ValueError("oracle rejected its arguments")
-    return {"spins": S, "history": hist, "accepted": acc, "sigma": sg, "accept_log": alog, "err": err}
+    return {"spins": S, "history": hist, "accepted": acc, "sigma": sg, "accept_log": alog, "type_history": th,
+            "snapshots": snaps, "err": err}

@@ -405,7 +405,21 @@ typedef struct {
     int64_t *acc_hist;      /* n_steps*mcs accepted attempts, or NULL */
     double sigma;           /* adaptive width of this instance */
     int has_adaptive;
+    double *type_hist;      /* n_steps*mcs*n_types*3 magnetization per site type, or NULL */
+    int32_t n_types;
+    double *snaps;          /* n_steps*n*3 spins after every step, or NULL */
 } vo_job;
+
+/* Optional outputs of vo_run_ex (any pointer may be NULL). */
+typedef struct {
+    int64_t *acc_hist;      /* [n_inst][n_steps*mcs] accepted attempts per MCS */
+    double *sigma_inout;    /* [n_inst] adaptive widths: in (<= 0: the policy's parameter), out */
+    double *type_hist;      /* [n_inst][n_steps*mcs][n_types][3] sum of S_i over the sites of each type */
+    int32_t n_types;
+    int32_t pad_;
+    double *snaps;          /* [n_inst][n_steps][n][3] spins at the end of every step (after the
+                               renormalisation): the final state per temperature/field step */
+} vo_extra;
 
 static void policy_of(const vo_sample *s, int32_t i, int32_t *pol, double *par) {
     *pol = VO_RANDOM;
@@ -546,10 +560,20 @@ static void *run_job(void *arg) {
             h[1] = M[0];
             h[2] = M[1];
             h[3] = M[2];
+            if (jb->type_hist) {  /* statistics of each magnetic phase (Sec. II): M per type */
+                double *th = jb->type_hist + rec * jb->n_types * 3;
+                for (int32_t k = 0; k < 3 * jb->n_types; ++k) th[k] = 0.0;
+                for (int32_t i = 0; i < n; ++i) {
+                    const int32_t ty = s->type ? s->type[i] : 0;
+                    if (ty < 0 || ty >= jb->n_types) continue;
+                    for (int q = 0; q < 3; ++q) th[3 * ty + q] += jb->S[3 * (int64_t)i + q];
+                }
+            }
             ++rec;
             ++t;
         }
         vo_renormalise(s, jb->S);
+        if (jb->snaps) memcpy(jb->snaps + (int64_t)st * n * 3, jb->S, sizeof(double) * 3 * (size_t)n);
     }
     return NULL;
 }
@@ -565,25 +589,25 @@ static void *run_job(void *arg) {
  *             that MCS was accepted (mode 0 only)
  * Returns the OR of VO_ERR_* over instances, or -1 on invalid arguments.
  */
-int vo_run2(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t n_inst, int32_t inst_base,
-            const double *T, const double *B, int32_t n_steps, int32_t mcs, uint32_t t0, double *spins, int32_t init,
-            double *history, uint8_t *accept_log, int32_t log_mcs, int32_t mode, int32_t n_threads,
-            int64_t *acc_hist, double *sigma_inout);
+int vo_run_ex(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t n_inst, int32_t inst_base,
+              const double *T, const double *B, int32_t n_steps, int32_t mcs, uint32_t t0, double *spins,
+              int32_t init, double *history, uint8_t *accept_log, int32_t log_mcs, int32_t mode, int32_t n_threads,
+              const vo_extra *x);
 
 int vo_run(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t n_inst, int32_t inst_base,
            const double *T, const double *B, int32_t n_steps, int32_t mcs, uint32_t t0, double *spins, int32_t init,
            double *history, uint8_t *accept_log, int32_t log_mcs, int32_t mode, int32_t n_threads) {
-    return vo_run2(s, colour, seed, n_inst, inst_base, T, B, n_steps, mcs, t0, spins, init, history, accept_log,
-                   log_mcs, mode, n_threads, NULL, NULL);
+    return vo_run_ex(s, colour, seed, n_inst, inst_base, T, B, n_steps, mcs, t0, spins, init, history, accept_log,
+                     log_mcs, mode, n_threads, NULL);
 }
 
-/* As vo_run, plus: acc_hist NULL or [n_inst][n_steps*mcs] accepted attempts per MCS;
- * sigma_inout NULL or [n_inst] adaptive widths (in: start values, or <= 0 for the policy
- * parameter; out: the widths after the run). */
-int vo_run2(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t n_inst, int32_t inst_base,
-            const double *T, const double *B, int32_t n_steps, int32_t mcs, uint32_t t0, double *spins, int32_t init,
-            double *history, uint8_t *accept_log, int32_t log_mcs, int32_t mode, int32_t n_threads,
-            int64_t *acc_hist, double *sigma_inout) {
+/* As vo_run, plus the optional outputs of x (see vo_extra). */
+int vo_run_ex(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t n_inst, int32_t inst_base,
+              const double *T, const double *B, int32_t n_steps, int32_t mcs, uint32_t t0, double *spins,
+              int32_t init, double *history, uint8_t *accept_log, int32_t log_mcs, int32_t mode, int32_t n_threads,
+              const vo_extra *x) {
+    int64_t *acc_hist = x ? x->acc_hist : NULL;
+    double *sigma_inout = x ? x->sigma_inout : NULL;
     if (!s || s->n < 0 || n_inst < 1 || n_steps < 0 || mcs < 0 || !T || !B || !spins || !history) return -1;
     const int32_t n = s->n;
     int32_t *col_own = NULL;
@@ -622,6 +646,10 @@ int vo_run2(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t n_
         jb->log_mcs = log_mcs;
         jb->mode = mode;
         jb->acc_hist = acc_hist ? acc_hist + (int64_t)r * n_steps * mcs : NULL;
+        jb->n_types = x ? x->n_types : 0;
+        jb->type_hist = (x && x->type_hist && x->n_types > 0)
+                            ? x->type_hist + (int64_t)r * n_steps * mcs * x->n_types * 3 : NULL;
+        jb->snaps = (x && x->snaps) ? x->snaps + (int64_t)r * n_steps * s->n * 3 : NULL;
         jb->has_adaptive = 0;
         jb->sigma = 0.0;
         if (s->type_policy)

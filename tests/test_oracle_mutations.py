@@ -15,6 +15,7 @@ import oracle
 from oracle import oracle as ora
 import test_oracle_pins as pins
 import test_oracle_policies as pol
+import test_oracle_outputs as outs
 
 SRC = open(os.path.join(os.path.dirname(ora.__file__), "vegas_oracle.c")).read()
 
@@ -58,6 +59,15 @@ MUTANTS = [
      [pol.test_adaptive_acceptance_and_control_law]),
     ("adaptation never frozen", "m < jb->mcs / 5", "m < jb->mcs", [pol.test_adaptive_acceptance_and_control_law]),
     ("flip keeps the spin", "out[0] = -Si[0] / sn;", "out[0] = Si[0] / sn;", [pol.test_spin_flip_trial_is_minus_s]),
+    ("type magnetization in one slot", "th[3 * ty + q] += jb->S[3 * (int64_t)i + q];",
+     "th[q] += jb->S[3 * (int64_t)i + q];", [outs.test_type_magnetizations_add_up_and_match_the_final_states]),
+    ("type magnetization components transposed", "th[3 * ty + q] += jb->S[3 * (int64_t)i + q];",
+     "th[3 * ty + q] += jb->S[3 * (int64_t)i + 2 - q];", [outs.test_two_phases_follow_their_own_field_axes]),
+    ("snapshot before the renormalisation",
+     "        vo_renormalise(s, jb->S);\n        if (jb->snaps) memcpy(",
+     "        if (jb->snaps) memcpy(jb->snaps + (int64_t)st * n * 3, jb->S, sizeof(double) * 3 * (size_t)n);\n"
+     "        vo_renormalise(s, jb->S);\n        if (0) memcpy(",
+     [outs.test_snapshots_are_the_final_states_per_step]),
 ]
 
 
