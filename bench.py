@@ -38,7 +38,8 @@ L_SIDE, REPLICAS, MCS, SEED = 256, 32, 200, 1
 BYTES_PER_ATTEMPT = 16 + 16 + 48.0 / REPLICAS
 PASS_KERNEL = "pass32_r32"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pass32_r32_sg256x32.txt")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_1803_07030_gb300", "csrc", "vegas_kernels.cu")
+# the source of the profiled sweep kernel (pass32_r32) and the device helpers it uses
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1803_07030_gb300", "csrc", f) for f in ("vegas_staged.cu", "vegas_device.cuh")]
 
 
 def workload_desc(mcs):
@@ -92,8 +93,11 @@ def peaks():
 
 
 def kernel_hash():
-    with open(KERNEL_SOURCE, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in KERNEL_SOURCES:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic():

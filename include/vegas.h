@@ -141,6 +141,15 @@ typedef struct {
     int32_t fault_inject;   /* testing only: 1 = in the cooperative sweep one block leaves
                                before its first grid barrier, so the others time out.
                                Default 0. */
+    int32_t type_stats;     /* 1: also record the magnetization of every site type (magnetic
+                               phase, Sec. II) after every MCS (vegas_type_history). Sites are
+                               then stored type by type inside each colour class, and the
+                               cooperative sweep is not used. Default 0. */
+    int32_t snapshots;      /* 1: keep every instance's spins at the end of every
+                               temperature/field step (after the renormalisation; Sec. II, the
+                               final state per step), read with vegas_get_snapshot. Costs a
+                               device copy of the spins per step and host memory for all of
+                               them. Default 0. */
 } vegas_options;
 
 typedef struct {
@@ -158,6 +167,9 @@ typedef struct {
     double sweep_ms;            /* summed event time of sweep launches (timing = 1) */
     double last_run_ms;         /* event time of the last vegas_run on the device */
     int64_t device_bytes;       /* device memory held by the context */
+    int32_t n_types;            /* site types tracked per instance (type_stats), else 0 */
+    int32_t pad_;
+    int64_t snapshot_steps;     /* steps with a stored final state per instance (snapshots) */
 } vegas_stats_t;
 
 /* Fills *opt with the defaults listed above. */
@@ -184,8 +196,10 @@ vegas_status vegas_create(const vegas_sample *samples, int32_t n_samples, const 
  * [n_instances][n_steps] host arrays (row-major), T > 0 and finite, B finite. The state
  * carries over between steps and between calls; one call with n_steps = a + b gives the
  * same spins and history as a call with the first a steps followed by a call with the
- * remaining b. After every MCS one history record (E, Mx, My, Mz) per instance is kept;
- * after the last MCS of every step each spin is rescaled to its norm s_i in FP64.
+ * remaining b. After every MCS one history record (E, Mx, My, Mz) per instance is kept,
+ * with the number of accepted attempts (and, with type_stats, the magnetization of every
+ * site type); after the last MCS of every step each spin is rescaled to its norm s_i in
+ * FP64 (and, with snapshots, the spins are kept).
  * Blocking: returns when the device work is done.
  */
 vegas_status vegas_run(vegas_ctx *ctx, const double *T, const double *B, int32_t n_steps, int32_t mcs_per_step);
@@ -226,6 +240,22 @@ vegas_status vegas_accept_history(const vegas_ctx *ctx, uint32_t *out, size_t ca
  */
 vegas_status vegas_adaptive_width(const vegas_ctx *ctx, double *out);
 vegas_status vegas_set_adaptive_width(vegas_ctx *ctx, const double *in);
+
+/*
+ * Magnetization of every site type after every MCS (option type_stats), as
+ * [n_instances][records][n_types][3] doubles: the sum of S_i over the instance's sites of
+ * type k (types 0 .. n_types-1, n_types = 1 + the largest type over all samples; a sample
+ * without types has every site in type 0). Summed over k it equals the history's
+ * (Mx, My, Mz). out == NULL: size query. VEGAS_EINVAL without type_stats.
+ */
+vegas_status vegas_type_history(const vegas_ctx *ctx, double *out, size_t capacity, size_t *n_written);
+
+/*
+ * Spins of one instance at the end of temperature/field step `step` (0 = the first step
+ * ever run on this context; option snapshots), as [n_sites][3] doubles in the caller's site
+ * order. VEGAS_EINVAL without snapshots or for a step not yet run.
+ */
+vegas_status vegas_get_snapshot(const vegas_ctx *ctx, int32_t instance, int64_t step, double *out);
 
 /* Counters and sizes of the context (valid also on a poisoned context). */
 vegas_status vegas_stats(const vegas_ctx *ctx, vegas_stats_t *out);

@@ -21,6 +21,7 @@ from .vegas import (  # noqa: F401
     vegas_create,
     vegas_default_options,
     vegas_destroy,
+    vegas_get_snapshot,
     vegas_get_spins,
     vegas_greedy_colour,
     vegas_history,
@@ -30,4 +31,5 @@ from .vegas import (  # noqa: F401
     vegas_set_spins,
     vegas_sweep_noalloc,
     vegas_stats,
+    vegas_type_history,
 )

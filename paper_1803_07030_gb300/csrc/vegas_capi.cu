@@ -28,13 +28,15 @@ struct SampleInfo {
     bool has_policy = false, has_adaptive = false;
     double sigma0 = 0.0;
     SiteParams64 u{};
-    int64_t slot_base = 0;     // first partial slot (blocks)
-    int32_t slot_count = 0;
+    std::vector<int32_t> type;  // per site (new numbering)
 };
 
 struct PassLaunch {
     PassArgs args;
     int grid;
+    int32_t sample, group;     // partial slots are grouped by (sample, type group)
+    int32_t col;               // colour class
+    int64_t slot = 0;          // first block slot
 };
 
 }  // namespace
@@ -53,6 +55,13 @@ struct vegas_ctx {
     // device buffers
     void *d_spins = nullptr, *d_edges = nullptr, *d_p0 = nullptr, *d_p1 = nullptr, *d_pk = nullptr;
     int64_t *d_rowptr = nullptr, *d_slot_base = nullptr;
+    int32_t n_groups = 1;      // type groups of the partial slots (n_types with type_stats)
+    int32_t n_types = 0;       // tracked site types (type_stats), else 0
+    double *d_type_hist = nullptr;
+    size_t type_hist_cap = 0;
+    void *d_snap = nullptr;
+    size_t snap_cap = 0;       // bytes
+    int4 *d_segs = nullptr;
     int32_t *d_orig = nullptr, *d_slot_count = nullptr;
     double *d_norm = nullptr, *d_partial = nullptr, *d_sched = nullptr, *d_hist = nullptr;
     size_t sched_cap = 0, hist_cap = 0;
@@ -91,6 +100,9 @@ struct vegas_ctx {
     // host state
     std::vector<std::vector<double>> hist;  // per instance: records * 4
     std::vector<std::vector<uint32_t>> acc_hist;  // per instance: accepted attempts per record
+    std::vector<std::vector<double>> type_hist;   // per instance: records * n_types * 3
+    std::vector<std::vector<double>> snaps;       // per instance: steps * n_sites * 3 (caller order)
+    int64_t snapshot_steps = 0;
     int64_t records = 0;
     uint32_t t = 0;
     uint32_t device_error = 0;
@@ -137,7 +149,7 @@ void free_all(vegas_ctx *c) {
     void *bufs[] = {c->d_spins, c->d_edges, c->d_p0, c->d_p1, c->d_pk, c->d_rowptr, c->d_slot_base, c->d_orig,
                     c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog,
                     c->d_insts, c->d_cstart, c->d_queue, c->d_bar, c->d_coop_partial, c->d_acc, c->d_acc_hist,
-                    c->d_pol, c->d_pol32, c->d_sigma, c->d_adapt_n};
+                    c->d_pol, c->d_pol32, c->d_sigma, c->d_adapt_n, c->d_type_hist, c->d_snap, c->d_segs};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -168,7 +180,8 @@ void enqueue_mcs(vegas_ctx *c, cudaStream_t st, std::vector<cudaEvent_t> *ev) {
         if (ev) cudaEventRecord((*ev)[2 * k + 1], st);
         ++k;
     }
-    ReduceArgs ra{c->d_partial, c->d_slot_base, c->d_slot_count, c->d_run, c->d_adapt_n, c->R, c->n_inst};
+    ReduceArgs ra{c->d_partial, c->d_slot_base, c->d_slot_count, c->d_run, c->d_adapt_n, c->R, c->n_inst,
+                  c->n_groups, c->n_types};
     launch_reduce(ra, st);
 }
 
@@ -190,6 +203,7 @@ void enqueue_coop(vegas_ctx *c, cudaStream_t st, int32_t n) {
     launch_advance(c->d_run, n, st);
 }
 
+// Renormalisation at the end of a step, then (option snapshots) the copy of the final state.
 void enqueue_renorm(vegas_ctx *c, cudaStream_t st) {
     RenormArgs ra{c->d_spins, c->d_norm, c->n_sites * c->R, c->log2R};
     const int grid = (int)std::min<int64_t>((ra.n_work + 255) / 256, (int64_t)c->sm_count * 8);
@@ -197,6 +211,11 @@ void enqueue_renorm(vegas_ctx *c, cudaStream_t st) {
         launch_renorm64(ra, grid, st);
     else
         launch_renorm32(ra, grid, st);
+    if (c->opt.snapshots) {
+        const int64_t n16 = c->n_sites * c->R * (c->precision == 64 ? 2 : 1);
+        const int g2 = (int)std::min<int64_t>((n16 + 255) / 256, (int64_t)c->sm_count * 8);
+        launch_snapshot(c->d_spins, c->d_snap, n16, c->d_run, g2, st);
+    }
 }
 
 constexpr int64_t kMaxStepGraphNodes = 20000;
@@ -204,7 +223,7 @@ constexpr int64_t kMaxStepGraphNodes = 20000;
 // Launches of one whole step (mcs MCS and the renormalisation) for the chosen variant, or
 // -1 when such a graph would be too large.
 int64_t step_graph_nodes(const vegas_ctx *c, int32_t mcs) {
-    const int64_t n = c->variant >= 1 ? 4 : (int64_t)mcs * ((int64_t)c->passes.size() + 1) + 1;
+    const int64_t n = (c->variant >= 1 ? 4 : (int64_t)mcs * ((int64_t)c->passes.size() + 1) + 1) + (c->opt.snapshots ? 1 : 0);
     return n <= kMaxStepGraphNodes ? n : -1;
 }
 
@@ -279,6 +298,8 @@ extern "C" void vegas_default_options(vegas_options *o) {
     o->pipeline_depth = 0;
     o->timeout_ns = 0;
     o->fault_inject = 0;
+    o->type_stats = 0;
+    o->snapshots = 0;
 }
 
 extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samples, const vegas_options *opt,
@@ -295,6 +316,10 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     if (o.accept_log_mcs < 0 || o.inst_base < 0 || o.max_blocks < 0) return fail(nullptr, VEGAS_EINVAL, "negative option");
     if (o.variant < -1 || o.variant > 2) return fail(nullptr, VEGAS_EINVAL, "variant must be -1, 0, 1 or 2");
     if (o.timeout_ns < 0 || o.fault_inject < 0 || o.fault_inject > 1) return fail(nullptr, VEGAS_EINVAL, "bad timeout or fault_inject");
+    if (o.type_stats < 0 || o.type_stats > 1 || o.snapshots < 0 || o.snapshots > 1)
+        return fail(nullptr, VEGAS_EINVAL, "type_stats and snapshots must be 0 or 1");
+    if (o.variant == 2 && o.type_stats)
+        return fail(nullptr, VEGAS_EINVAL, "the cooperative sweep (variant 2) does not record per-type statistics");
     if (o.variant == 2 && (o.precision != 32 || n_samples != 1))
         return fail(nullptr, VEGAS_EINVAL, "the cooperative sweep (variant 2) is FP32 with one sample");
     if (o.pipeline_depth < 0 || o.pipeline_depth > 3) return fail(nullptr, VEGAS_EINVAL, "pipeline_depth must be 0..3");
@@ -308,13 +333,16 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     int64_t n_sites = 0, n_edges = 0;
     for (int32_t s = 0; s < n_samples; ++s) {
         std::string e;
-        if (!load_sample(samples[s], L[(size_t)s], e))
+        if (!load_sample(samples[s], L[(size_t)s], e, o.type_stats != 0))
             return fail(nullptr, VEGAS_EINVAL, "sample " + std::to_string(s) + ": " + e);
         n_sites += L[(size_t)s].n;
         n_edges += L[(size_t)s].n_edges + (L[(size_t)s].n_edges & 1);  // keep every sample 16-byte aligned
     }
     if (n_sites * o.replicas > ((int64_t)1 << 40) || n_sites > INT32_MAX - (1 << 24) || n_edges >= INT32_MAX)
         return fail(nullptr, VEGAS_EINVAL, "too many sites or links for one context");
+    int32_t n_types = 0;
+    if (o.type_stats)
+        for (auto &l : L) n_types = std::max(n_types, l.n_types);
 
     vegas_ctx *c = new (std::nothrow) vegas_ctx();
     if (!c) return fail(nullptr, VEGAS_ENOMEM, "host allocation failed");
@@ -327,6 +355,8 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     c->n_sites = n_sites;
     c->n_edges = n_edges;
     c->variant = 0;
+    c->n_types = n_types;
+    c->n_groups = n_types > 0 ? n_types : 1;
 
     auto bail = [&](vegas_status st) {
         g_create_error = c->err;
@@ -421,6 +451,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         si.orig = l.orig;
         si.uniform_params = l.uniform_params;
         si.has_anisotropy = l.has_anisotropy;
+        if (o.type_stats) si.type = l.type;
         si.has_policy = !l.policy.empty();
         si.has_adaptive = l.has_adaptive;
         si.sigma0 = l.sigma0;
@@ -549,16 +580,26 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         }
     }
 
-    // ---- sweep launches, one per non-empty colour class of each sample
-    int64_t slots = 0;
+    // ---- sweep launches, one per non-empty colour class of each sample (per type segment of a
+    // class with per-type statistics: sites are stored type by type inside each class)
     int64_t alog_base = 0;
     for (int32_t s = 0; s < n_samples; ++s) {
         SampleInfo &si = c->samples[(size_t)s];
-        si.slot_base = slots;
-        for (int32_t col = 0; col < si.n_colours; ++col) {
-            const int32_t nc = si.cstart[(size_t)col + 1] - si.cstart[(size_t)col];
-            if (nc == 0) continue;
+        for (int32_t col = 0; col < si.n_colours; ++col)
+          for (int32_t sb = si.cstart[(size_t)col]; sb < si.cstart[(size_t)col + 1];) {
+            int32_t se = si.cstart[(size_t)col + 1];
+            const int32_t ty = si.type.empty() ? 0 : si.type[(size_t)sb];
+            if (!si.type.empty())
+                for (int32_t g = sb; g < se; ++g)
+                    if (si.type[(size_t)g] != ty) {
+                        se = g;
+                        break;
+                    }
+            const int32_t nc = se - sb;
             PassLaunch pl;
+            pl.sample = s;
+            pl.group = ty;
+            pl.col = col;
             PassArgs &a = pl.args;
             std::memset(&a, 0, sizeof a);
             a.spins = c->d_spins;
@@ -576,9 +617,9 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
             a.seed = o.seed;
             a.edge_base = si.edge_off;
             a.site_off = si.site_off;
-            a.g_begin = si.site_off + si.cstart[(size_t)col];
-            a.g_end = si.site_off + si.cstart[(size_t)col + 1];
-            a.lower_end = a.g_begin;
+            a.g_begin = si.site_off + sb;
+            a.g_end = si.site_off + se;
+            a.lower_end = si.site_off + si.cstart[(size_t)col];  // the class start: lower colours below
             a.log2R = c->log2R;
             a.inst0 = o.inst_base + s * R;
             a.inst_local0 = s * R;
@@ -605,30 +646,32 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
             if (o.max_blocks > 0) cap = std::min<int64_t>(cap, o.max_blocks);
             pl.grid = (int)std::max<int64_t>(1, std::min(need, cap));
             a.partial = nullptr;  // set below, once the slot buffer exists
-            si.slot_count += pl.grid;
-            slots += pl.grid;
             c->passes.push_back(pl);
-        }
+            sb = se;
+          }
         alog_base += (int64_t)si.n * R;
     }
-    DALLOC(c->d_partial, sizeof(double) * 4 * (size_t)slots * R);
-    {
-        int64_t off = 0;
-        for (PassLaunch &pl : c->passes) {
-            pl.args.partial = c->d_partial + off * R * 4;
-            off += pl.grid;
+    // block slots grouped by (sample, type group), passes of a group in sweep order
+    const int32_t NG = c->n_groups;
+    std::vector<int64_t> h_sb((size_t)n_samples * NG, 0);
+    std::vector<int32_t> h_sc((size_t)n_samples * NG, 0);
+    int64_t slots = 0;
+    for (int32_t s = 0; s < n_samples; ++s)
+        for (int32_t k = 0; k < NG; ++k) {
+            h_sb[(size_t)(s * NG + k)] = slots;
+            for (PassLaunch &pl : c->passes)
+                if (pl.sample == s && (NG == 1 || pl.group == k)) {
+                    pl.slot = slots;
+                    h_sc[(size_t)(s * NG + k)] += pl.grid;
+                    slots += pl.grid;
+                }
         }
-    }
-    std::vector<int64_t> h_sb((size_t)n_samples);
-    std::vector<int32_t> h_sc((size_t)n_samples);
-    for (int32_t s = 0; s < n_samples; ++s) {
-        h_sb[(size_t)s] = c->samples[(size_t)s].slot_base;
-        h_sc[(size_t)s] = c->samples[(size_t)s].slot_count;
-    }
-    DALLOC(c->d_slot_base, sizeof(int64_t) * (size_t)n_samples);
-    DALLOC(c->d_slot_count, sizeof(int32_t) * (size_t)n_samples);
-    H2D(c->d_slot_base, h_sb.data(), sizeof(int64_t) * (size_t)n_samples);
-    H2D(c->d_slot_count, h_sc.data(), sizeof(int32_t) * (size_t)n_samples);
+    DALLOC(c->d_partial, sizeof(double) * 4 * (size_t)std::max<int64_t>(slots, 1) * R);
+    for (PassLaunch &pl : c->passes) pl.args.partial = c->d_partial + pl.slot * R * 4;
+    DALLOC(c->d_slot_base, sizeof(int64_t) * h_sb.size());
+    DALLOC(c->d_slot_count, sizeof(int32_t) * h_sc.size());
+    H2D(c->d_slot_base, h_sb.data(), sizeof(int64_t) * h_sb.size());
+    H2D(c->d_slot_count, h_sc.data(), sizeof(int32_t) * h_sc.size());
     RunState rs0{};
     rs0.mcs = 1;
     H2D(c->d_run, &rs0, sizeof rs0);
@@ -636,20 +679,28 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     // ---- resident sweep: one entry per instance, largest first
     if (!p64) {
         std::vector<ResidentInst> insts;
-        std::vector<int32_t> h_cs;
+        std::vector<int32_t> h_cs;  // class starts (cooperative sweep)
+        std::vector<int4> h_segs;   // sweep segments (resident sweep)
         int64_t alog_off = 0;
         for (int32_t s = 0; s < n_samples; ++s) {
             const SampleInfo &si = c->samples[(size_t)s];
-            const int32_t cls_off = (int32_t)h_cs.size();
+            const int32_t seg_off = (int32_t)h_segs.size();
             for (int32_t q = 0; q <= si.n_colours; ++q) h_cs.push_back(si.site_off + si.cstart[(size_t)q]);
+            for (const PassLaunch &pl : c->passes)  // the passes of this sample, in sweep order
+                if (pl.sample == s) {
+                    const bool last = pl.args.g_end == si.site_off + si.cstart[(size_t)pl.col + 1];
+                    h_segs.push_back(make_int4(pl.args.g_begin, pl.args.g_end, pl.args.lower_end,
+                                               pl.group | ((last ? 1 : 0) << 16)));
+                }
+            const int32_t n_segs = (int32_t)h_segs.size() - seg_off;
             c->max_instance_sites = std::max(c->max_instance_sites, si.n);
             for (int32_t r = 0; r < R; ++r) {
                 ResidentInst I;
                 std::memset(&I, 0, sizeof I);
                 I.g_begin = si.site_off;
                 I.g_end = si.site_off + si.n;
-                I.cls_off = cls_off;
-                I.n_colours = si.n_colours;
+                I.seg_off = seg_off;
+                I.n_segs = n_segs;
                 I.inst_id = o.inst_base + s * R + r;
                 I.inst_local = s * R + r;
                 I.r = r;
@@ -668,9 +719,11 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         });
         DALLOC(c->d_insts, sizeof(ResidentInst) * insts.size());
         DALLOC(c->d_cstart, sizeof(int32_t) * h_cs.size());
+        DALLOC(c->d_segs, sizeof(int4) * std::max<size_t>(h_segs.size(), 1));
         DALLOC(c->d_queue, sizeof(uint32_t));
         H2D(c->d_insts, insts.data(), sizeof(ResidentInst) * insts.size());
         H2D(c->d_cstart, h_cs.data(), sizeof(int32_t) * h_cs.size());
+        if (!h_segs.empty()) H2D(c->d_segs, h_segs.data(), sizeof(int4) * h_segs.size());
         c->res_threads = c->max_instance_sites >= 4096 ? 512 : 256;
         c->res_grid = (int)std::min<int64_t>((int64_t)insts.size(),
                                              (int64_t)c->sm_count * resident_blocks_per_sm(c->res_threads, any_policy));
@@ -685,7 +738,8 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         ra.pk = c->d_pk;
         ra.pol = any_policy ? c->d_pol32 : nullptr;
         ra.insts = c->d_insts;
-        ra.cstart = c->d_cstart;
+        ra.segs = c->d_segs;
+        ra.n_types = c->n_types;
         ra.queue = c->d_queue;
         ra.run = c->d_run;
         ra.err = c->d_err;
@@ -696,11 +750,12 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         ra.n_items = (int32_t)insts.size();
         ra.n_inst = c->n_inst;
         ra.log2R = c->log2R;
-        // one block per instance only pays while instances are small
-        c->res_eligible = c->max_instance_sites <= (1 << 18);
+        // one block per instance only pays while instances are small; the resident sweep keeps
+        // per-type sums for at most 8 types
+        c->res_eligible = c->max_instance_sites <= (1 << 18) && c->n_types <= 8;
     }
     // ---- cooperative sweep: one sample, every block on every class
-    if (!p64 && n_samples == 1 && !c->passes.empty() && !c->any_adaptive) {
+    if (!p64 && n_samples == 1 && !c->passes.empty() && !c->any_adaptive && !o.type_stats) {
         c->coop_grid = c->sm_count * coop_blocks_per_sm(any_policy);
         if (o.max_blocks > 0) c->coop_grid = std::min(c->coop_grid, o.max_blocks);
         DALLOC(c->d_bar, sizeof(GridBarrier));
@@ -726,7 +781,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         c->tuned = true;
     } else if (o.variant == 1) {
         if (!c->res_eligible) {
-            c->err = "variant 1 (resident) needs FP32 and samples of at most 262144 sites";
+            c->err = "variant 1 (resident) needs FP32, samples of at most 262144 sites and at most 8 tracked types";
             return bail(VEGAS_EINVAL);
         }
         c->variant = 1;
@@ -777,6 +832,8 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     }
     c->hist.assign((size_t)c->n_inst, std::vector<double>());
     c->acc_hist.assign((size_t)c->n_inst, std::vector<uint32_t>());
+    c->type_hist.assign((size_t)c->n_inst, std::vector<double>());
+    c->snaps.assign((size_t)c->n_inst, std::vector<double>());
 #undef TRY
 #undef DALLOC
 #undef H2D
@@ -833,6 +890,27 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
         CK(c, dalloc(c, &c->d_acc_hist, sizeof(uint32_t) * aneed));
         c->acc_hist_cap = aneed;
     }
+    const size_t tneed = (size_t)nrec * NI * (size_t)c->n_types * 3;
+    if (tneed > c->type_hist_cap) {
+        if (c->d_type_hist) {
+            cudaFree(c->d_type_hist);
+            c->device_bytes -= (int64_t)(c->type_hist_cap * sizeof(double));
+        }
+        c->type_hist_cap = 0;
+        CK(c, dalloc(c, &c->d_type_hist, sizeof(double) * tneed));
+        c->type_hist_cap = tneed;
+    }
+    const int64_t vbytes = c->precision == 64 ? 32 : 16;
+    const size_t sneed = c->opt.snapshots ? (size_t)n_steps * (size_t)(c->n_sites * c->R * vbytes) : 0;
+    if (sneed > c->snap_cap) {
+        if (c->d_snap) {
+            cudaFree(c->d_snap);
+            c->device_bytes -= (int64_t)c->snap_cap;
+        }
+        c->snap_cap = 0;
+        CK(c, dalloc(c, &c->d_snap, sneed));
+        c->snap_cap = sneed;
+    }
     CK(c, cudaMemcpyAsync(c->d_sched, sched.data(), sizeof(double) * sched.size(), cudaMemcpyHostToDevice, c->stream));
     RunState rs{};
     rs.t = c->t;
@@ -844,6 +922,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
     rs.acc = c->d_acc;
     rs.acc_hist = c->d_acc_hist;
     rs.sigma = c->d_sigma;
+    rs.type_hist = c->n_types > 0 ? c->d_type_hist : nullptr;
     CK(c, cudaMemcpyAsync(c->d_run, &rs, sizeof rs, cudaMemcpyHostToDevice, c->stream));
 
     const bool use_graph = c->opt.graphs && !c->opt.timing;
@@ -947,13 +1026,13 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             if ((st = step_graph(c, mcs, &ge)) != VEGAS_OK) return st;
             CK(c, cudaGraphLaunch(ge, c->stream));
             const int64_t nodes = step_graph_nodes(c, mcs);
-            c->kernel_launches += c->variant >= 1 ? 3 : nodes;
+            c->kernel_launches += c->variant >= 1 ? 3 + (c->opt.snapshots ? 1 : 0) : nodes;
             c->sweep_launches += c->variant >= 1 ? 1 : (int64_t)mcs * (int64_t)c->passes.size();
             continue;
         }
         if ((st = run_variant(c->variant, m0, mcs - m0)) != VEGAS_OK) return st;
         enqueue_renorm(c, c->stream);
-        c->kernel_launches++;
+        c->kernel_launches += c->opt.snapshots ? 2 : 1;
         if (c->opt.timing) {  // read this step's sweep timings before the events are reused
             CK(c, cudaStreamSynchronize(c->stream));
             if (c->variant >= 1) {
@@ -1000,6 +1079,45 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
         v.resize(old + (size_t)nrec);
         for (int64_t r = 0; r < nrec; ++r) v[old + (size_t)r] = ha[(size_t)r * NI + i];
     }
+    if (tneed > 0) {  // [rec][inst][type][3] -> per instance, appended
+        std::vector<double> ht(tneed);
+        CK(c, cudaMemcpy(ht.data(), c->d_type_hist, sizeof(double) * tneed, cudaMemcpyDeviceToHost));
+        const size_t per = (size_t)c->n_types * 3;
+        for (int64_t i = 0; i < NI; ++i) {
+            auto &v = c->type_hist[(size_t)i];
+            const size_t old = v.size();
+            v.resize(old + (size_t)nrec * per);
+            for (int64_t r = 0; r < nrec; ++r)
+                std::memcpy(&v[old + (size_t)r * per], &ht[((size_t)r * NI + i) * per], per * sizeof(double));
+        }
+    }
+    if (sneed > 0) {  // [step][site][replica] in the device layout -> per instance, caller order
+        std::vector<unsigned char> hs(sneed);
+        CK(c, cudaMemcpy(hs.data(), c->d_snap, sneed, cudaMemcpyDeviceToHost));
+        const size_t step_bytes = (size_t)(c->n_sites * c->R * vbytes);
+        for (int32_t sm = 0; sm < c->n_samples; ++sm) {
+            const SampleInfo &si = c->samples[(size_t)sm];
+            for (int32_t r = 0; r < c->R; ++r) {
+                auto &v = c->snaps[(size_t)(sm * c->R + r)];
+                const size_t old = v.size();
+                v.resize(old + (size_t)n_steps * (size_t)si.n * 3);
+                for (int32_t st = 0; st < n_steps; ++st)
+                    for (int32_t g = 0; g < si.n; ++g) {
+                        const unsigned char *p =
+                            hs.data() + (size_t)st * step_bytes + ((size_t)(si.site_off + g) * c->R + r) * vbytes;
+                        double *o3 = &v[old + ((size_t)st * si.n + (size_t)si.orig[(size_t)g]) * 3];
+                        if (c->precision == 64) {
+                            std::memcpy(o3, p, 3 * sizeof(double));
+                        } else {
+                            float f[3];
+                            std::memcpy(f, p, sizeof f);
+                            for (int q = 0; q < 3; ++q) o3[q] = f[q];
+                        }
+                    }
+            }
+        }
+        c->snapshot_steps += n_steps;
+    }
     c->records += nrec;
     c->t += (uint32_t)nrec;
     c->device_error |= derr;
@@ -1039,6 +1157,34 @@ extern "C" vegas_status vegas_accept_history(const vegas_ctx *cc, uint32_t *out,
     if (capacity < need) return fail(c, VEGAS_EINVAL, "acceptance buffer too small");
     for (int i = 0; i < c->n_inst; ++i)
         std::memcpy(out + (size_t)i * c->records, c->acc_hist[(size_t)i].data(), sizeof(uint32_t) * c->records);
+    return VEGAS_OK;
+}
+
+extern "C" vegas_status vegas_type_history(const vegas_ctx *cc, double *out, size_t capacity, size_t *n_written) {
+    vegas_ctx *c = const_cast<vegas_ctx *>(cc);
+    vegas_status st = check_usable(c);
+    if (st != VEGAS_OK) return st;
+    if (c->n_types == 0) return fail(c, VEGAS_EINVAL, "per-type statistics need the option type_stats");
+    const size_t per = (size_t)c->records * (size_t)c->n_types * 3;
+    const size_t need = (size_t)c->n_inst * per;
+    if (n_written) *n_written = need;
+    if (!out) return VEGAS_OK;
+    if (capacity < need) return fail(c, VEGAS_EINVAL, "type history buffer too small");
+    for (int i = 0; i < c->n_inst; ++i)
+        std::memcpy(out + (size_t)i * per, c->type_hist[(size_t)i].data(), sizeof(double) * per);
+    return VEGAS_OK;
+}
+
+extern "C" vegas_status vegas_get_snapshot(const vegas_ctx *cc, int32_t inst, int64_t step, double *out) {
+    vegas_ctx *c = const_cast<vegas_ctx *>(cc);
+    vegas_status st = check_usable(c);
+    if (st != VEGAS_OK) return st;
+    if (!c->opt.snapshots) return fail(c, VEGAS_EINVAL, "snapshots need the option snapshots");
+    if (inst < 0 || inst >= c->n_inst) return fail(c, VEGAS_EINVAL, "instance out of range");
+    if (step < 0 || step >= c->snapshot_steps) return fail(c, VEGAS_EINVAL, "no snapshot for this step");
+    if (!out) return fail(c, VEGAS_EINVAL, "out is NULL");
+    const size_t n3 = (size_t)c->samples[(size_t)(inst / c->R)].n * 3;
+    std::memcpy(out, c->snaps[(size_t)inst].data() + (size_t)step * n3, sizeof(double) * n3);
     return VEGAS_OK;
 }
 
@@ -1154,6 +1300,8 @@ extern "C" vegas_status vegas_stats(const vegas_ctx *c, vegas_stats_t *o) {
     o->sweep_ms = c->sweep_ms;
     o->last_run_ms = c->last_run_ms;
     o->device_bytes = c->device_bytes;
+    o->n_types = c->n_types;
+    o->snapshot_steps = c->snapshot_steps;
     return VEGAS_OK;
 }
 

@@ -1,0 +1,246 @@
+// Device helpers shared by the sweep kernels (the FP32 attempt and its trials, Philox,
+// the block partials). Included by vegas_kernels.cu and vegas_staged.cu; everything here has
+// internal linkage in each translation unit.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "vegas_internal.h"
+
+namespace vegas {
+namespace {
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11:
+// ten rounds of two 32x32->64 multiplies (M0 = 0xD2511F53, M1 = 0xCD9E8D57) with the key
+// bumped by the Weyl constants (0x9E3779B9, 0xBB67AE85) between rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ float cub32(float x, float y, float z) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    return fmaf(xx, yy, fmaf(yy, zz, xx * zz));
+}
+
+// ------------------------------------------------------------------ block partials
+// Per-block sums of (E, Mx, My, Mz) for each replica. Lanes whose index agrees modulo R
+// hold the same replica; a fixed butterfly and a fixed warp order make the result
+// deterministic. out points at this block's [R][4] slot. The accepted attempts of the block
+// are added to acc[replica] (integers: the order does not matter), when acc is not NULL.
+__device__ __forceinline__ void block_partials(double v[4], uint32_t nacc, int R, double *out, uint32_t *acc) {
+    __shared__ double sm[kThreads / 32][32][4];
+    __shared__ uint32_t sn[kThreads / 32][32];
+    for (int off = 16; off >= R; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+        nacc += __shfl_xor_sync(0xFFFFFFFFu, nacc, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < R) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sm[warp][lane][q] = v[q];
+        sn[warp][lane] = nacc;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < R) {
+        double a4[4] = {0.0, 0.0, 0.0, 0.0};
+        uint32_t na = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a4[q] += sm[w][threadIdx.x][q];
+            na += sn[w][threadIdx.x];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[threadIdx.x * 4 + q] = a4[q];
+        if (acc && na) atomicAdd(acc + threadIdx.x, na);
+    }
+}
+
+// Accepted-attempt counters of replica 0 of a pass's sample (NULL when not counted).
+__device__ __forceinline__ uint32_t *acc_counters(const RunState *rs, int inst_local0) {
+    return rs->acc ? rs->acc + inst_local0 : nullptr;
+}
+
+// ------------------------------------------------------------------ FP32 attempt
+// One Metropolis attempt in FP32, written with explicit roundings (fmaf where a fused
+// multiply-add is meant, __fmul_rn / __fadd_rn elsewhere) so that every kernel that calls
+// it computes bit-identical results for the same inputs, whatever the surrounding code.
+// h is the exchange field sum_j J_ij S_j (row order), l its part over lower colours.
+struct Site32 {
+    float nx, ny, nz, sn, ex, ey, ez, k, kc;
+};
+
+// Random trial (Sec. III.B): z uniform in (-1, 1), azimuth uniform in (-pi, pi): by
+// Archimedes' theorem (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z) is uniform on the sphere.
+// Each uniform takes 23 random bits as the mantissa of a float in [1, 2): f = 1 + k 2^-23,
+// so z = 2 (f - 1.5) + 2^-23 = (2k + 1) 2^-23 - 1 exactly (midpoints of 2^23 cells).
+__device__ __forceinline__ float3 trial_random32(uint4 rw, float sn) {
+    const float fz = __uint_as_float(0x3F800000u | (rw.x >> 9));
+    const float fp = __uint_as_float(0x3F800000u | (rw.y >> 9));
+    const float z = fmaf(__fsub_rn(fz, 1.5f), 2.0f, 0x1p-23f);
+    const float phi = fmaf(__fsub_rn(fp, 1.5f), 6.28318530717959f, 3.14159265358979f * 0x1p-23f);
+    float sphi, cphi;
+    __sincosf(phi, &sphi, &cphi);
+    const float rho2 = fmaf(-z, z, 1.0f);
+    const float rho = __fmul_rn(rho2, rsqrtf(rho2));
+    return make_float3(__fmul_rn(sn, __fmul_rn(rho, cphi)), __fmul_rn(sn, __fmul_rn(rho, sphi)), __fmul_rn(sn, z));
+}
+
+// One Metropolis attempt in FP32 on the trial P, written with explicit roundings (fmaf
+// where a fused multiply-add is meant, __fmul_rn / __fadd_rn elsewhere) so that every
+// kernel that calls it computes bit-identical results for the same inputs, whatever the
+// surrounding code. h is the exchange field sum_j J_ij S_j (row order), l its part over
+// lower colours; wacc is the random word of the acceptance uniform.
+template <int PM, int LM>
+__device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, float hz, float lx, float ly, float lz,
+                                          const Site32 &p, float beta, float B, const float3 P, uint32_t wacc,
+                                          float4 &Sn, bool &acc, float &e_i, bool &nan_seen) {
+    const float Hx = fmaf(B, p.nx, hx), Hy = fmaf(B, p.ny, hy), Hz = fmaf(B, p.nz, hz);
+    const float px = P.x, py = P.y, pz = P.z;
+    const float dx = __fsub_rn(px, Si.x), dy = __fsub_rn(py, Si.y), dz = __fsub_rn(pz, Si.z);
+    float dE = -fmaf(dx, Hx, fmaf(dy, Hy, __fmul_rn(dz, Hz)));
+    if (PM != 0) {
+        const float pn = fmaf(px, p.ex, fmaf(py, p.ey, __fmul_rn(pz, p.ez)));
+        const float po = fmaf(Si.x, p.ex, fmaf(Si.y, p.ey, __fmul_rn(Si.z, p.ez)));
+        dE = fmaf(-p.k, __fmul_rn(__fsub_rn(pn, po), __fadd_rn(pn, po)), dE);
+        dE = fmaf(-p.kc, __fsub_rn(cub32(px, py, pz), cub32(Si.x, Si.y, Si.z)), dE);
+    }
+    // Metropolis acceptance (Eq. 4); NaN rejects
+    const float u = __fsub_rn(__uint_as_float(0x3F800000u | (wacc >> 9)), 1.0f);  // k 2^-23 in [0, 1)
+    acc = (dE <= 0.f) || (u < __expf(__fmul_rn(-beta, dE)));
+    nan_seen = (dE != dE);
+    if (nan_seen) acc = false;
+    const float qx = acc ? px : Si.x, qy = acc ? py : Si.y, qz = acc ? pz : Si.z;
+    Sn = make_float4(qx, qy, qz, 0.f);
+    // this site's share of the energy after the MCS: -S.l - B S.n - k (S.e)^2 - kc cub(S)
+    float e = __fmul_rn(-B, fmaf(qx, p.nx, fmaf(qy, p.ny, __fmul_rn(qz, p.nz))));
+    if (LM != 0) e = __fsub_rn(e, fmaf(qx, lx, fmaf(qy, ly, __fmul_rn(qz, lz))));
+    if (PM != 0) {
+        const float pe = fmaf(qx, p.ex, fmaf(qy, p.ey, __fmul_rn(qz, p.ez)));
+        e = __fsub_rn(e, fmaf(__fmul_rn(p.k, pe), pe, __fmul_rn(p.kc, cub32(qx, qy, qz))));
+    }
+    e_i = e;
+}
+
+// ------------------------------------------------------------------ FP32 update policies
+// The same proposals as the FP64 path, drawn from the attempt's one Philox block: words x and
+// y are the two uniforms, z the acceptance uniform, w the Hinzke-Nowak choice or, for the
+// Gaussian, the third normal (inverse error function of a 23-bit uniform; the first two
+// come from Box-Muller on x and y).
+__device__ __forceinline__ float u23(uint32_t w) {  // k 2^-23 in [0, 1)
+    return __fsub_rn(__uint_as_float(0x3F800000u | (w >> 9)), 1.0f);
+}
+
+__device__ __forceinline__ float3 unit32(float x, float y, float z) {
+    const float q = rsqrtf(fmaf(x, x, fmaf(y, y, __fmul_rn(z, z))));
+    return make_float3(__fmul_rn(x, q), __fmul_rn(y, q), __fmul_rn(z, q));
+}
+
+constexpr int kPolCapSphere = 6;  // internal: the random third of Hinzke-Nowak, as a cap of height 2
+
+__device__ __forceinline__ float3 policy_trial32(const PolicySite32 ps, float sigma, const float4 Si, float sn,
+                                                 uint4 rw) {
+    int code = ps.code;
+    if (code == kPolHinzkeNowak) {
+        // a uniform point on the sphere is the cap of height 2 around any axis, so the random
+        // and small-step thirds share one code path (no divergence between them in a warp)
+        const float v = __fmul_rn(u23(rw.w), 3.0f);
+        code = v < 1.0f ? kPolFlip : (v < 2.0f ? kPolCapSphere : kPolSmallStep);
+    }
+    if (code == kPolFlip) return make_float3(-Si.x, -Si.y, -Si.z);
+    if (code == kPolRandom) return trial_random32(rw, sn);
+    const float3 u = unit32(Si.x, Si.y, Si.z);
+    float sphi, cphi;
+    const float phi = fmaf(__fsub_rn(__uint_as_float(0x3F800000u | (rw.y >> 9)), 1.5f), 6.28318530717959f,
+                           3.14159265358979f * 0x1p-23f);
+    __sincosf(phi, &sphi, &cphi);
+    if (code == kPolSmallStep || code == kPolCapSphere) {  // uniform in the cap of height h around u
+        const float h = code == kPolCapSphere ? 2.0f : ps.par;
+        const float sh = __fmul_rn(u23(rw.x), h);
+        const float z = __fsub_rn(1.0f, sh);
+        const float r = sqrtf(fmaxf(__fmul_rn(sh, __fsub_rn(2.0f, sh)), 0.0f));
+        float3 e1;
+        const float ax = fabsf(u.x), ay = fabsf(u.y), az = fabsf(u.z);
+        if (ax <= ay && ax <= az)
+            e1 = unit32(0.f, -u.z, u.y);
+        else if (ay <= az)
+            e1 = unit32(u.z, 0.f, -u.x);
+        else
+            e1 = unit32(-u.y, u.x, 0.f);
+        const float3 e2 = make_float3(fmaf(u.y, e1.z, -__fmul_rn(u.z, e1.y)), fmaf(u.z, e1.x, -__fmul_rn(u.x, e1.z)),
+                                      fmaf(u.x, e1.y, -__fmul_rn(u.y, e1.x)));
+        const float x = __fmul_rn(r, cphi), y = __fmul_rn(r, sphi);
+        return make_float3(__fmul_rn(sn, fmaf(x, e1.x, fmaf(y, e2.x, __fmul_rn(z, u.x)))),
+                           __fmul_rn(sn, fmaf(x, e1.y, fmaf(y, e2.y, __fmul_rn(z, u.y)))),
+                           __fmul_rn(sn, fmaf(x, e1.z, fmaf(y, e2.z, __fmul_rn(z, u.z)))));
+    }
+    // Gaussian (fixed width) or adaptive (the instance's width): direction of u + sigma g
+    const float sg = code == kPolAdaptive ? sigma : ps.par;
+    const float rad = sqrtf(-2.0f * logf(__fsub_rn(1.0f, u23(rw.x))));  // 1 - u in (0, 1]
+    // (2k + 1) 2^-23 - 1 lies strictly inside (-1, 1); sqrt 2 erfinv of it is standard normal
+    const float g2 = __fmul_rn(1.41421356237310f, erfinvf(fmaf(u23(rw.w), 2.0f, -1.0f + 0x1p-23f)));
+    const float3 v = unit32(fmaf(sg, __fmul_rn(rad, cphi), u.x), fmaf(sg, __fmul_rn(rad, sphi), u.y), fmaf(sg, g2, u.z));
+    return make_float3(__fmul_rn(sn, v.x), __fmul_rn(sn, v.y), __fmul_rn(sn, v.z));
+}
+
+// Per-thread sums of E and M: runs of at most 64 attempts in FP32, then FP64 (a run's
+// rounding error is below 64 * 2^-24 of its absolute sum, < 1e-5 of E/N).
+// Also counts the accepted attempts.
+struct Acc32 {
+    double d[4] = {0.0, 0.0, 0.0, 0.0};
+    float f[4] = {0.f, 0.f, 0.f, 0.f};
+    int n = 0;
+    uint32_t nacc = 0;
+    __device__ __forceinline__ void add(float e, float4 q, bool ok) {
+        nacc += ok ? 1u : 0u;
+        f[0] = __fadd_rn(f[0], e);
+        f[1] = __fadd_rn(f[1], q.x);
+        f[2] = __fadd_rn(f[2], q.y);
+        f[3] = __fadd_rn(f[3], q.z);
+        if (++n == 64) flush();
+    }
+
+    __device__ __forceinline__ void flush() {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            d[q] += (double)f[q];
+            f[q] = 0.f;
+        }
+        n = 0;
+    }
+};
+
+__device__ __forceinline__ void link32(const float4 Sj, float J, bool lower, float &hx, float &hy, float &hz,
+                                       float &lx, float &ly, float &lz) {
+    hx = fmaf(J, Sj.x, hx);
+    hy = fmaf(J, Sj.y, hy);
+    hz = fmaf(J, Sj.z, hz);
+    if (lower) {
+        lx = fmaf(J, Sj.x, lx);
+        ly = fmaf(J, Sj.y, ly);
+        lz = fmaf(J, Sj.z, lz);
+    }
+}
+
+__device__ __forceinline__ Site32 site_params32(const PassArgs &a, int PMv, int g) {
+    Site32 p{a.u32.nx, a.u32.ny, a.u32.nz, a.u32.s, a.u32.ex, a.u32.ey, a.u32.ez, a.u32.k, a.u32.kc};
+    if (PMv == 2) {
+        const float4 p0 = __ldg((const float4 *)a.p0 + g), p1 = __ldg((const float4 *)a.p1 + g);
+        p = Site32{p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, __ldg((const float *)a.pk + g)};
+    }
+    return p;
+}
+
+}  // namespace
+}  // namespace vegas

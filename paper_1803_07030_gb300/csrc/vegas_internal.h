@@ -6,11 +6,14 @@
 #include <string>
 #include <vector>
 
+#include <vector_types.h>  // int4 (CUDA headers; also used by the host-only loader)
+
 #include "../../include/vegas.h"
 
 namespace vegas {
 
 constexpr int kMaxColours = 64;
+constexpr int kMaxTypes = 64;   // site types tracked by the per-type statistics
 constexpr int kThreads = 256;  // threads per block of the sweep kernels
 
 // Random-number purposes (fourth Philox counter word; low 16 bits hold a candidate index).
@@ -50,6 +53,8 @@ struct LoadedSample {
     // per-site parameters in new numbering (always filled; defaults where NULL)
     std::vector<double> spin_norm, field_axis, k_uni, e_uni, k_cub;
     std::vector<double> init_spins;  // empty: Philox initial state
+    std::vector<int32_t> type;       // per site (new numbering); all 0 without a type array
+    int32_t n_types = 1;             // 1 + the largest type
     bool uniform_params = false;     // every site has the same (s, n, k, e, kc)
     bool has_anisotropy = false;     // some k or kc is non-zero
     // update policy per site (new numbering): code and parameter (cap height 1 - cos theta
@@ -64,8 +69,9 @@ struct LoadedSample {
     std::vector<int32_t> lower_mode;
 };
 
-// Validates and renumbers; on failure returns false and sets err.
-bool load_sample(const vegas_sample &s, LoadedSample &out, std::string &err);
+// Validates and renumbers; on failure returns false and sets err. type_major: inside each
+// colour class, sites are ordered by type first (then Morton order or caller id).
+bool load_sample(const vegas_sample &s, LoadedSample &out, std::string &err, bool type_major = false);
 
 // ------------------------------------------------------------------ device-side layouts
 
@@ -110,6 +116,7 @@ struct RunState {
     uint32_t *acc;        // [n_inst] accepted attempts of the current MCS, or NULL (not counted)
     uint32_t *acc_hist;   // [records][n_inst] accepted attempts per MCS
     double *sigma;        // [n_inst] width of the adaptive policy, or NULL
+    double *type_hist;    // [records][n_inst][n_types][3] magnetization per site type, or NULL
 };
 
 // One colour class of one sample: everything a sweep launch needs.
@@ -150,13 +157,17 @@ struct PassArgs {
     SiteParams64 u64;
 };
 
+// Block slots are grouped by sample and, with per-type statistics, by site type: group
+// (s, k) holds the partials of every pass over type-k sites of sample s.
 struct ReduceArgs {
     const double *partial;     // all passes
-    const int64_t *slot_base;  // [n_samples] first block slot of the sample
-    const int32_t *slot_count; // [n_samples] block slots of the sample (all colours)
+    const int64_t *slot_base;  // [n_samples][n_groups] first block slot of the group
+    const int32_t *slot_count; // [n_samples][n_groups] block slots of the group
     RunState *run;
     const int32_t *adapt_n;    // [n_inst] sites of the instance's sample if it adapts a width, else 0
     int32_t R, n_inst;
+    int32_t n_groups;          // type groups per sample (1 without per-type statistics)
+    int32_t n_types;           // > 0: write the magnetization of each group to run->type_hist
 };
 
 struct RenormArgs {
@@ -181,8 +192,8 @@ struct InitArgs {
 // One instance of the resident sweep: a sample's sites and one of its replicas.
 struct ResidentInst {
     int32_t g_begin, g_end;    // the sample's global sites
-    int32_t cls_off;           // first entry of the sample's class starts in ResidentArgs::cstart
-    int32_t n_colours;
+    int32_t seg_off;           // first segment of the sample in ResidentArgs::segs
+    int32_t n_segs;
     int32_t inst_id;           // Philox instance id
     int32_t inst_local;        // schedule and history column
     int32_t r;                 // replica within the sample
@@ -203,7 +214,9 @@ struct ResidentArgs {
     const void *p0, *p1, *pk;  // per-site parameters (samples with params_mode 2)
     const PolicySite32 *pol;   // per-site update policy, or NULL (every site random)
     const ResidentInst *insts; // [n_items], largest first
-    const int32_t *cstart;     // class starts (global sites), n_colours + 1 per sample
+    // segments of a sample in sweep order: {begin, end, class begin, type | last-of-class << 16}
+    // (global sites); one per colour class, or per (class, type) with per-type statistics
+    const int4 *segs;
     uint32_t *queue;           // work counter, zero before the launch
     uint32_t *err;
     uint8_t *alog;
@@ -211,6 +224,7 @@ struct ResidentArgs {
     int64_t alog_stride;
     uint32_t alog_mcs;
     int32_t n_items, n_inst, log2R;
+    int32_t n_types;           // > 0: per-type magnetization into run->type_hist
     RunState *run;             // MCS counter t, record index, MCS per step, schedule, history
     int32_t mcs;               // MCS in this launch (all inside one temperature/field step)
 };
@@ -238,6 +252,13 @@ struct CoopArgs {
 
 // ------------------------------------------------------------------ launchers
 
+using PassFn = void (*)(PassArgs);
+// FP32 colour-pass kernel for a pass (staged for rows of six links, else direct) and its
+// dynamic shared memory; the direct kernel for a parameter mode, lower mode and policy flag.
+PassFn select_pass32(const PassArgs &a);
+int pass32_smem(const PassArgs &a);
+PassFn select_direct(int pm, int lm, bool pol);
+
 // Sweep launch of one colour class; lower_mode, params_mode and deg pick the compiled variant.
 void launch_pass32(const PassArgs &a, int grid, void *stream);
 void launch_pass64(const PassArgs &a, int grid, void *stream);
@@ -258,6 +279,8 @@ int pass_blocks_per_sm(int precision, const PassArgs &a);
 void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream);
 // Adds n to the run state's MCS counter and record index (after a resident launch).
 void launch_advance(RunState *run, int32_t n, void *stream);
+// Copies the spins into the snapshot slot of the step that just ended (read from the run state).
+void launch_snapshot(const void *spins, void *snap, int64_t n16, const RunState *run, int grid, void *stream);
 
 // Cooperative launch (all blocks co-resident); returns the CUDA error of the launch.
 int launch_coop(const CoopArgs &a, int grid, void *stream);

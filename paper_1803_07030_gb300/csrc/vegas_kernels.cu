@@ -22,26 +22,11 @@
 
 #include <cstdint>
 
+#include "vegas_device.cuh"
 #include "vegas_internal.h"
 
 namespace vegas {
 namespace {
-
-// ------------------------------------------------------------------ Philox4x32-10
-// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11:
-// ten rounds of two 32x32->64 multiplies (M0 = 0xD2511F53, M1 = 0xCD9E8D57) with the key
-// bumped by the Weyl constants (0x9E3779B9, 0xBB67AE85) between rounds.
-__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c;
-}
 
 // ------------------------------------------------------------------ FP64 helpers
 // Explicit round-to-nearest operations: the compiler may not fuse them, which keeps the
@@ -77,11 +62,6 @@ __device__ double3 sphere64(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t purp
 __device__ __forceinline__ double cub64(double x, double y, double z) {
     const double xx = dm(x, x), yy = dm(y, y), zz = dm(z, z);
     return da(da(dm(xx, yy), dm(yy, zz)), dm(xx, zz));
-}
-
-__device__ __forceinline__ float cub32(float x, float y, float z) {
-    const float xx = x * x, yy = y * y, zz = z * z;
-    return fmaf(xx, yy, fmaf(yy, zz, xx * zz));
 }
 
 // ------------------------------------------------------------------ FP64 update policies
@@ -204,45 +184,6 @@ __device__ __forceinline__ double adapt_width(double sigma, uint32_t accepted, i
     return sg;
 }
 
-// ------------------------------------------------------------------ block partials
-// Per-block sums of (E, Mx, My, Mz) for each replica. Lanes whose index agrees modulo R
-// hold the same replica; a fixed butterfly and a fixed warp order make the result
-// deterministic. out points at this block's [R][4] slot. The accepted attempts of the block
-// are added to acc[replica] (integers: the order does not matter), when acc is not NULL.
-__device__ __forceinline__ void block_partials(double v[4], uint32_t nacc, int R, double *out, uint32_t *acc) {
-    __shared__ double sm[kThreads / 32][32][4];
-    __shared__ uint32_t sn[kThreads / 32][32];
-    for (int off = 16; off >= R; off >>= 1) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
-        nacc += __shfl_xor_sync(0xFFFFFFFFu, nacc, off);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane < R) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) sm[warp][lane][q] = v[q];
-        sn[warp][lane] = nacc;
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < R) {
-        double a4[4] = {0.0, 0.0, 0.0, 0.0};
-        uint32_t na = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) a4[q] += sm[w][threadIdx.x][q];
-            na += sn[w][threadIdx.x];
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) out[threadIdx.x * 4 + q] = a4[q];
-        if (acc && na) atomicAdd(acc + threadIdx.x, na);
-    }
-}
-
-// Accepted-attempt counters of replica 0 of a pass's sample (NULL when not counted).
-__device__ __forceinline__ uint32_t *acc_counters(const RunState *rs, int inst_local0) {
-    return rs->acc ? rs->acc + inst_local0 : nullptr;
-}
-
 // ------------------------------------------------------------------ FP64 colour pass
 
 __global__ void __launch_bounds__(kThreads) pass64_kernel(const PassArgs a) {
@@ -341,176 +282,6 @@ __global__ void __launch_bounds__(kThreads) pass64_kernel(const PassArgs a) {
     block_partials(acc4, nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs, a.inst_local0));
 }
 
-// ------------------------------------------------------------------ FP32 attempt
-// One Metropolis attempt in FP32, written with explicit roundings (fmaf where a fused
-// multiply-add is meant, __fmul_rn / __fadd_rn elsewhere) so that every kernel that calls
-// it computes bit-identical results for the same inputs, whatever the surrounding code.
-// h is the exchange field sum_j J_ij S_j (row order), l its part over lower colours.
-struct Site32 {
-    float nx, ny, nz, sn, ex, ey, ez, k, kc;
-};
-
-// Random trial (Sec. III.B): z uniform in (-1, 1), azimuth uniform in (-pi, pi): by
-// Archimedes' theorem (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z) is uniform on the sphere.
-// Each uniform takes 23 random bits as the mantissa of a float in [1, 2): f = 1 + k 2^-23,
-// so z = 2 (f - 1.5) + 2^-23 = (2k + 1) 2^-23 - 1 exactly (midpoints of 2^23 cells).
-__device__ __forceinline__ float3 trial_random32(uint4 rw, float sn) {
-    const float fz = __uint_as_float(0x3F800000u | (rw.x >> 9));
-    const float fp = __uint_as_float(0x3F800000u | (rw.y >> 9));
-    const float z = fmaf(__fsub_rn(fz, 1.5f), 2.0f, 0x1p-23f);
-    const float phi = fmaf(__fsub_rn(fp, 1.5f), 6.28318530717959f, 3.14159265358979f * 0x1p-23f);
-    float sphi, cphi;
-    __sincosf(phi, &sphi, &cphi);
-    const float rho2 = fmaf(-z, z, 1.0f);
-    const float rho = __fmul_rn(rho2, rsqrtf(rho2));
-    return make_float3(__fmul_rn(sn, __fmul_rn(rho, cphi)), __fmul_rn(sn, __fmul_rn(rho, sphi)), __fmul_rn(sn, z));
-}
-
-// One Metropolis attempt in FP32 on the trial P, written with explicit roundings (fmaf
-// where a fused multiply-add is meant, __fmul_rn / __fadd_rn elsewhere) so that every
-// kernel that calls it computes bit-identical results for the same inputs, whatever the
-// surrounding code. h is the exchange field sum_j J_ij S_j (row order), l its part over
-// lower colours; wacc is the random word of the acceptance uniform.
-template <int PM, int LM>
-__device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, float hz, float lx, float ly, float lz,
-                                          const Site32 &p, float beta, float B, const float3 P, uint32_t wacc,
-                                          float4 &Sn, bool &acc, float &e_i, bool &nan_seen) {
-    const float Hx = fmaf(B, p.nx, hx), Hy = fmaf(B, p.ny, hy), Hz = fmaf(B, p.nz, hz);
-    const float px = P.x, py = P.y, pz = P.z;
-    const float dx = __fsub_rn(px, Si.x), dy = __fsub_rn(py, Si.y), dz = __fsub_rn(pz, Si.z);
-    float dE = -fmaf(dx, Hx, fmaf(dy, Hy, __fmul_rn(dz, Hz)));
-    if (PM != 0) {
-        const float pn = fmaf(px, p.ex, fmaf(py, p.ey, __fmul_rn(pz, p.ez)));
-        const float po = fmaf(Si.x, p.ex, fmaf(Si.y, p.ey, __fmul_rn(Si.z, p.ez)));
-        dE = fmaf(-p.k, __fmul_rn(__fsub_rn(pn, po), __fadd_rn(pn, po)), dE);
-        dE = fmaf(-p.kc, __fsub_rn(cub32(px, py, pz), cub32(Si.x, Si.y, Si.z)), dE);
-    }
-    // Metropolis acceptance (Eq. 4); NaN rejects
-    const float u = __fsub_rn(__uint_as_float(0x3F800000u | (wacc >> 9)), 1.0f);  // k 2^-23 in [0, 1)
-    acc = (dE <= 0.f) || (u < __expf(__fmul_rn(-beta, dE)));
-    nan_seen = (dE != dE);
-    if (nan_seen) acc = false;
-    const float qx = acc ? px : Si.x, qy = acc ? py : Si.y, qz = acc ? pz : Si.z;
-    Sn = make_float4(qx, qy, qz, 0.f);
-    // this site's share of the energy after the MCS: -S.l - B S.n - k (S.e)^2 - kc cub(S)
-    float e = __fmul_rn(-B, fmaf(qx, p.nx, fmaf(qy, p.ny, __fmul_rn(qz, p.nz))));
-    if (LM != 0) e = __fsub_rn(e, fmaf(qx, lx, fmaf(qy, ly, __fmul_rn(qz, lz))));
-    if (PM != 0) {
-        const float pe = fmaf(qx, p.ex, fmaf(qy, p.ey, __fmul_rn(qz, p.ez)));
-        e = __fsub_rn(e, fmaf(__fmul_rn(p.k, pe), pe, __fmul_rn(p.kc, cub32(qx, qy, qz))));
-    }
-    e_i = e;
-}
-
-// ------------------------------------------------------------------ FP32 update policies
-// The same proposals as the FP64 path, drawn from the attempt's one Philox block: words x and
-// y are the two uniforms, z the acceptance uniform, w the Hinzke-Nowak choice or, for the
-// Gaussian, the third normal (inverse error function of a 23-bit uniform; the first two
-// come from Box-Muller on x and y).
-__device__ __forceinline__ float u23(uint32_t w) {  // k 2^-23 in [0, 1)
-    return __fsub_rn(__uint_as_float(0x3F800000u | (w >> 9)), 1.0f);
-}
-
-__device__ __forceinline__ float3 unit32(float x, float y, float z) {
-    const float q = rsqrtf(fmaf(x, x, fmaf(y, y, __fmul_rn(z, z))));
-    return make_float3(__fmul_rn(x, q), __fmul_rn(y, q), __fmul_rn(z, q));
-}
-
-constexpr int kPolCapSphere = 6;  // internal: the random third of Hinzke-Nowak, as a cap of height 2
-
-__device__ __forceinline__ float3 policy_trial32(const PolicySite32 ps, float sigma, const float4 Si, float sn,
-                                                 uint4 rw) {
-    int code = ps.code;
-    if (code == kPolHinzkeNowak) {
-        // a uniform point on the sphere is the cap of height 2 around any axis, so the random
-        // and small-step thirds share one code path (no divergence between them in a warp)
-        const float v = __fmul_rn(u23(rw.w), 3.0f);
-        code = v < 1.0f ? kPolFlip : (v < 2.0f ? kPolCapSphere : kPolSmallStep);
-    }
-    if (code == kPolFlip) return make_float3(-Si.x, -Si.y, -Si.z);
-    if (code == kPolRandom) return trial_random32(rw, sn);
-    const float3 u = unit32(Si.x, Si.y, Si.z);
-    float sphi, cphi;
-    const float phi = fmaf(__fsub_rn(__uint_as_float(0x3F800000u | (rw.y >> 9)), 1.5f), 6.28318530717959f,
-                           3.14159265358979f * 0x1p-23f);
-    __sincosf(phi, &sphi, &cphi);
-    if (code == kPolSmallStep || code == kPolCapSphere) {  // uniform in the cap of height h around u
-        const float h = code == kPolCapSphere ? 2.0f : ps.par;
-        const float sh = __fmul_rn(u23(rw.x), h);
-        const float z = __fsub_rn(1.0f, sh);
-        const float r = sqrtf(fmaxf(__fmul_rn(sh, __fsub_rn(2.0f, sh)), 0.0f));
-        float3 e1;
-        const float ax = fabsf(u.x), ay = fabsf(u.y), az = fabsf(u.z);
-        if (ax <= ay && ax <= az)
-            e1 = unit32(0.f, -u.z, u.y);
-        else if (ay <= az)
-            e1 = unit32(u.z, 0.f, -u.x);
-        else
-            e1 = unit32(-u.y, u.x, 0.f);
-        const float3 e2 = make_float3(fmaf(u.y, e1.z, -__fmul_rn(u.z, e1.y)), fmaf(u.z, e1.x, -__fmul_rn(u.x, e1.z)),
-                                      fmaf(u.x, e1.y, -__fmul_rn(u.y, e1.x)));
-        const float x = __fmul_rn(r, cphi), y = __fmul_rn(r, sphi);
-        return make_float3(__fmul_rn(sn, fmaf(x, e1.x, fmaf(y, e2.x, __fmul_rn(z, u.x)))),
-                           __fmul_rn(sn, fmaf(x, e1.y, fmaf(y, e2.y, __fmul_rn(z, u.y)))),
-                           __fmul_rn(sn, fmaf(x, e1.z, fmaf(y, e2.z, __fmul_rn(z, u.z)))));
-    }
-    // Gaussian (fixed width) or adaptive (the instance's width): direction of u + sigma g
-    const float sg = code == kPolAdaptive ? sigma : ps.par;
-    const float rad = sqrtf(-2.0f * logf(__fsub_rn(1.0f, u23(rw.x))));  // 1 - u in (0, 1]
-    // (2k + 1) 2^-23 - 1 lies strictly inside (-1, 1); sqrt 2 erfinv of it is standard normal
-    const float g2 = __fmul_rn(1.41421356237310f, erfinvf(fmaf(u23(rw.w), 2.0f, -1.0f + 0x1p-23f)));
-    const float3 v = unit32(fmaf(sg, __fmul_rn(rad, cphi), u.x), fmaf(sg, __fmul_rn(rad, sphi), u.y), fmaf(sg, g2, u.z));
-    return make_float3(__fmul_rn(sn, v.x), __fmul_rn(sn, v.y), __fmul_rn(sn, v.z));
-}
-
-// Per-thread sums of E and M: runs of at most 64 attempts in FP32, then FP64 (a run's
-// rounding error is below 64 * 2^-24 of its absolute sum, < 1e-5 of E/N).
-// Also counts the accepted attempts.
-struct Acc32 {
-    double d[4] = {0.0, 0.0, 0.0, 0.0};
-    float f[4] = {0.f, 0.f, 0.f, 0.f};
-    int n = 0;
-    uint32_t nacc = 0;
-    __device__ __forceinline__ void add(float e, float4 q, bool ok) {
-        nacc += ok ? 1u : 0u;
-        f[0] = __fadd_rn(f[0], e);
-        f[1] = __fadd_rn(f[1], q.x);
-        f[2] = __fadd_rn(f[2], q.y);
-        f[3] = __fadd_rn(f[3], q.z);
-        if (++n == 64) flush();
-    }
-
-    __device__ __forceinline__ void flush() {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            d[q] += (double)f[q];
-            f[q] = 0.f;
-        }
-        n = 0;
-    }
-};
-
-__device__ __forceinline__ void link32(const float4 Sj, float J, bool lower, float &hx, float &hy, float &hz,
-                                       float &lx, float &ly, float &lz) {
-    hx = fmaf(J, Sj.x, hx);
-    hy = fmaf(J, Sj.y, hy);
-    hz = fmaf(J, Sj.z, hz);
-    if (lower) {
-        lx = fmaf(J, Sj.x, lx);
-        ly = fmaf(J, Sj.y, ly);
-        lz = fmaf(J, Sj.z, lz);
-    }
-}
-
-__device__ __forceinline__ Site32 site_params32(const PassArgs &a, int PMv, int g) {
-    Site32 p{a.u32.nx, a.u32.ny, a.u32.nz, a.u32.s, a.u32.ex, a.u32.ey, a.u32.ez, a.u32.k, a.u32.kc};
-    if (PMv == 2) {
-        const float4 p0 = __ldg((const float4 *)a.p0 + g), p1 = __ldg((const float4 *)a.p1 + g);
-        p = Site32{p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, __ldg((const float *)a.pk + g)};
-    }
-    return p;
-}
-
 constexpr int kDirectRow = 12;  // rows up to this length gather all neighbours at once
 
 // One attempt of the direct path: gathers the neighbour rows with plain loads (row order),
@@ -521,7 +292,7 @@ template <int PM, int LM, int POL>
 __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const int64_t *row_ptr, int g, int r, int R,
                                                int lower_end, uint32_t orig, const Site32 &p, float beta, float B,
                                                uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1, Acc32 &acc,
-                                               bool &nan_seen, const PolicySite32 *pol, float sigma) {
+                                               bool &nan_seen, const PolicySite32 *pol, float sigma, float4 &Sq) {
     const int64_t si = (int64_t)g * R + r;
     const float4 Si = S[si];
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
@@ -568,6 +339,7 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
     nan_seen |= bad;
     if (ok) S[si] = Sn;
     acc.add(e_i, Sn, ok);
+    Sq = Sn;
     return ok;
 }
 
@@ -598,374 +370,15 @@ __global__ void __launch_bounds__(kThreads, 2) pass32_kernel(const PassArgs a) {
         const int g = a.g_begin + (int)(w >> a.log2R);
         const uint32_t orig = (uint32_t)__ldg(a.orig + g);
         bool nan_seen = false;
+        float4 Sq;
         const bool ok = direct_attempt<PM, LM, POL>(S, E, a.row_ptr, g, r, R, a.lower_end, orig, site_params32(a, PM, g),
-                                                    beta, B, t, inst, k0, k1, acc, nan_seen, a.pol32, sigma);
+                                                    beta, B, t, inst, k0, k1, acc, nan_seen, a.pol32, sigma, Sq);
         if (nan_seen) atomicOr(a.err, kErrNaN);
         if (a.alog && t < a.alog_mcs)
             a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
     }
     acc.flush();
     block_partials(acc.d, acc.nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs, a.inst_local0));
-}
-
-// ------------------------------------------------------------------ FP32 colour pass (staged)
-// Rows of exactly DEG links. Each warp walks its share of the class in "groups" of 32
-// work items (32/R sites x R replicas) and keeps a software pipeline in shared memory:
-// the links and caller ids of group k+2D and the neighbour and own spin rows of group k+D
-// are copied with cp.async while group k is computed, so DRAM latency overlaps compute
-// instead of stalling the warp. Group k's rows are complete once all but the last D-1
-// committed copy groups have landed (cp.async.wait_group D-1).
-__device__ __forceinline__ void cp16(void *smem, const void *gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp4(void *smem, const void *gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp8(void *smem, const void *gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// One staged attempt: links lk (int4 pairs), rows row[j*32] (neighbour j) and row[DEG*32]
-// (own) already in shared memory; with POL, the site's update policy *ps too.
-template <int DEG, int PM, int LM, int POL = 0>
-__device__ __forceinline__ void staged_attempt(const PassArgs &a, const int4 *lk, const float4 *row, uint32_t orig,
-                                               int g, int r, int R, uint32_t t, uint32_t inst, const uint32_t *rk0,
-                                               const uint32_t *rk1, float beta, float B, float4 *S, Acc32 &acc,
-                                               bool &nan_seen, bool log_accepts, const PolicySite32 *ps = nullptr,
-                                               float sigma = 0.f) {
-    const Site32 p = site_params32(a, PM, g);
-    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-#pragma unroll
-    for (int j = 0; j < DEG / 2; ++j) {
-        const int4 q = lk[j];
-        link32(row[(2 * j) * 32], __int_as_float(q.y), LM == 2 && q.x < a.lower_end, hx, hy, hz, lx, ly, lz);
-        link32(row[(2 * j + 1) * 32], __int_as_float(q.w), LM == 2 && q.z < a.lower_end, hx, hy, hz, lx, ly, lz);
-    }
-    if (LM == 1) {
-        lx = hx;
-        ly = hy;
-        lz = hz;
-    }
-    const float4 Si = row[DEG * 32];
-    uint4 c = make_uint4(orig, t, inst, kPurposeTrial32);
-#pragma unroll
-    for (int q = 0; q < 10; ++q) {  // Philox4x32-10 with precomputed round keys
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ rk0[q], lo1, hi0 ^ c.w ^ rk1[q], lo0);
-    }
-    float4 Sn;
-    bool ok, bad;
-    float e_i;
-    const float3 P =
-        POL ? policy_trial32(*ps, sigma, Si, p.sn, c) : trial_random32(c, p.sn);
-    attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, P, c.z, Sn, ok, e_i, bad);
-    nan_seen |= bad;
-    if (ok) S[(int64_t)g * R + r] = Sn;
-    if (log_accepts)
-        a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
-    acc.add(e_i, Sn, ok);
-}
-
-// Geometry of the staged kernel. A group is 32 work items (spg = 32/R sites x R replicas);
-// a block is NB consecutive groups (BS = NB * spg >= 8 consecutive sites) whose links and
-// caller ids are staged together. NLS block slots cover the 2D-group lookahead of links.
-struct StagedGeom {
-    int spg, BS, NB, NLS, link_bytes, slot_bytes, rows_bytes, warp_bytes;
-};
-
-__host__ __device__ inline StagedGeom staged_geom(int deg, int D, int log2R) {
-    StagedGeom g;
-    g.spg = 32 >> log2R;
-    g.BS = g.spg > 8 ? g.spg : 8;
-    g.NB = g.BS / g.spg;
-    g.NLS = (2 * D + g.NB - 1) / g.NB + 1;
-    g.link_bytes = ((g.BS * deg * 8 + 15) / 16) * 16;
-    g.slot_bytes = g.link_bytes + ((g.BS * 4 + 15) / 16) * 16;
-    g.rows_bytes = D * (deg + 1) * 32 * 16;
-    g.warp_bytes = g.rows_bytes + g.NLS * g.slot_bytes;
-    return g;
-}
-
-// Debug builds (VEGAS_DEBUG_CHECKS) check every staged copy: a failed check sets
-// kErrIndex, records a code and a value, and skips the access.
-#ifdef VEGAS_DEBUG_CHECKS
-#define VEGAS_CHECK(cond, code, val)                   \
-    if (!(cond)) {                                     \
-        atomicOr(a.err, kErrIndex);                    \
-        atomicCAS(a.err + 1, 0u, (uint32_t)(code));    \
-        a.err[2] = (uint32_t)(val);                    \
-        return;                                        \
-    }
-#else
-#define VEGAS_CHECK(cond, code, val)
-#endif
-
-// Position of one group in the warp's sequence: first site, index inside its block, and
-// the slot holding its block's links. Groups are visited in increasing site order.
-struct GroupPos {
-    int sbase, j, lslot;
-    __device__ __forceinline__ void next(const StagedGeom &G, int bstride) {
-        if (++j == G.NB) {
-            j = 0;
-            sbase += bstride - (G.NB - 1) * G.spg;
-            lslot = (lslot + 1 == G.NLS) ? 0 : lslot + 1;
-        } else {
-            sbase += G.spg;
-        }
-    }
-};
-
-// LOG2R >= 0 fixes the replica count at compile time (the batched case R = 32); -1 reads it
-// from the arguments.
-// Depth 2 fits three blocks per SM in shared memory; the register cap keeps them resident.
-template <int DEG, int PM, int LM, int D, int LOG2R>
-__global__ void __launch_bounds__(kThreads, D == 2 ? 3 : 2) pass32_staged(const PassArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const RunState *rs_ = a.run;
-    const uint32_t t = rs_->t;
-    const uint32_t step_idx = rs_->rec / rs_->mcs;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int log2R = LOG2R >= 0 ? LOG2R : a.log2R, R = 1 << log2R;
-    const StagedGeom G = staged_geom(DEG, D, log2R);
-    const int r = lane & (R - 1), my = lane >> log2R;  // replica, site within the group
-    unsigned char *wbase = smem + (size_t)warp * G.warp_bytes;
-    float4 *rows = (float4 *)wbase;                     // [D][DEG+1][32]
-    unsigned char *lslots = wbase + G.rows_bytes;       // [NLS][links | caller ids]
-    float4 *S = (float4 *)a.spins;
-    const float4 *Sr = S + r;
-    const int2 *E = (const int2 *)a.edges;
-    const uint32_t inst = (uint32_t)(a.inst0 + r);
-    const double *sc = rs_->sched + ((int64_t)step_idx * a.n_inst + a.inst_local0 + r) * 2;
-    const float beta = (float)sc[0], B = (float)sc[1];
-    const int g_end = a.g_end;
-    const int nwarps = blockDim.x >> 5;
-    const int W = blockIdx.x * nwarps + warp;
-    const int bstride = gridDim.x * nwarps * G.BS;  // sites between this warp's blocks
-    uint32_t rk0[10], rk1[10];                      // Philox round keys, kept in registers
-    {
-        uint32_t x = (uint32_t)a.seed, y = (uint32_t)(a.seed >> 32);
-#pragma unroll
-        for (int q = 0; q < 10; ++q) {
-            rk0[q] = x;
-            rk1[q] = y;
-            x += 0x9E3779B9u;
-            y += 0xBB67AE85u;
-        }
-    }
-
-    auto issue_links = [&](int sb, int slot) {  // links and caller ids of the block at sb
-        if (sb >= g_end) return;
-        const int ns = min(G.BS, g_end - sb);
-        unsigned char *dst = lslots + slot * G.slot_bytes;
-        const unsigned char *src = (const unsigned char *)(E + a.edge_base + (int64_t)(sb - a.site_off) * DEG);
-        const int nch = ns * (DEG / 2);
-        VEGAS_CHECK(sb >= a.g_begin && slot >= 0 && slot < G.NLS, 1, sb);
-        VEGAS_CHECK(a.edge_base + (int64_t)(sb - a.site_off) * DEG + (int64_t)ns * DEG <= a.n_edges_total, 2, sb);
-        VEGAS_CHECK(((uintptr_t)src & 15) == 0 && ((uintptr_t)dst & 15) == 0, 3, sb);
-        VEGAS_CHECK(sb + ns <= a.n_sites_total, 4, sb);
-        for (int c = lane; c < nch; c += 32) cp16(dst + 16 * c, src + 16 * c);
-        if (lane < ns) cp4(dst + G.link_bytes + 4 * lane, a.orig + sb + lane);
-    };
-    auto issue_rows = [&](const GroupPos &p, int rslot) {  // rows of a group (its links have landed)
-        const int g = p.sbase + my;
-        if (g >= g_end) return;
-        const int4 *lk = (const int4 *)(lslots + p.lslot * G.slot_bytes) + (p.j * G.spg + my) * (DEG / 2);
-        float4 *dst = rows + rslot * (DEG + 1) * 32 + lane;
-        VEGAS_CHECK(p.lslot >= 0 && p.lslot < G.NLS && rslot >= 0 && rslot < D, 5, p.lslot * 16 + rslot);
-        VEGAS_CHECK(g < a.n_sites_total, 6, g);
-#pragma unroll
-        for (int j = 0; j < DEG / 2; ++j) {
-            const int4 q = lk[j];
-            VEGAS_CHECK(q.x >= 0 && q.x < a.n_sites_total && q.z >= 0 && q.z < a.n_sites_total, 7, q.x);
-            cp16(dst + (2 * j) * 32, Sr + (int64_t)q.x * R);
-            cp16(dst + (2 * j + 1) * 32, Sr + (int64_t)q.z * R);
-        }
-        cp16(dst + DEG * 32, Sr + (int64_t)g * R);
-    };
-
-    // prologue: links of every block whose first group is among the first 2D, then the
-    // rows of the first D groups
-    const int g0 = a.g_begin + W * G.BS;
-    const int nb_pro = (2 * D + G.NB - 1) / G.NB;
-    for (int b = 0; b < nb_pro; ++b) issue_links(g0 + b * bstride, b);
-    cp_commit();
-    cp_wait<0>();
-    __syncwarp();
-    GroupPos pk{g0, 0, 0};  // group k (computed now)
-    GroupPos pd = pk;       // group k + D (rows issued at the end of this iteration)
-    for (int q = 0; q < D; ++q) {
-        issue_rows(pd, q);
-        cp_commit();
-        pd.next(G, bstride);
-    }
-    int k_issue = nb_pro * G.NB - 2 * D;  // iteration whose end issues the next block's links
-    int sb_next = g0 + nb_pro * bstride, ls_next = nb_pro;
-    int rsl = 0;
-    Acc32 acc;
-    bool nan_seen = false;
-    const bool log_accepts = a.alog && t < a.alog_mcs;
-    for (int k = 0; pk.sbase < g_end; ++k) {
-        cp_wait<D - 1>();
-        __syncwarp();
-        const int g = pk.sbase + my;
-        if (g < g_end) {
-            const unsigned char *slot = lslots + pk.lslot * G.slot_bytes;
-            const int li = pk.j * G.spg + my;
-            const int4 *lk = (const int4 *)slot + li * (DEG / 2);
-            const float4 *row = rows + rsl * (DEG + 1) * 32 + lane;
-            const uint32_t orig = ((const uint32_t *)(slot + G.link_bytes))[li];
-            bool skip = false;
-#ifdef VEGAS_DEBUG_CHECKS
-            if (orig >= (uint32_t)a.n_sample_sites || g >= a.n_sites_total) {
-                atomicOr(a.err, kErrIndex);
-                atomicCAS(a.err + 1, 0u, 8u);
-                a.err[2] = orig;
-                skip = true;
-            }
-#endif
-            if (!skip) staged_attempt<DEG, PM, LM>(a, lk, row, orig, g, r, R, t, inst, rk0, rk1, beta, B, S, acc, nan_seen,
-                                              log_accepts);
-        }
-        __syncwarp();
-        if (k == k_issue) {
-            issue_links(sb_next, ls_next);
-            k_issue += G.NB;
-            sb_next += bstride;
-            ls_next = (ls_next + 1 == G.NLS) ? 0 : ls_next + 1;
-        }
-        issue_rows(pd, rsl);
-        cp_commit();
-        pk.next(G, bstride);
-        pd.next(G, bstride);
-        rsl = (rsl + 1 == D) ? 0 : rsl + 1;
-    }
-    cp_wait<0>();
-    if (nan_seen) atomicOr(a.err, kErrNaN);
-    acc.flush();
-    block_partials(acc.d, acc.nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs_, a.inst_local0));
-}
-
-// Replica-batched sweep (R = 32): one warp = one site x 32 replicas, depth-2 pipeline. A
-// warp owns blocks of eight consecutive sites (block b starts at g0 + b * bstride); the
-// eight groups of a block are unrolled, so every ring slot and offset is a constant:
-// group j of block b computes from row slot j & 1 and link slot b & 1; at j = 4 the links of
-// the next block are copied; rows of group j + 2 (the next block's first two at j = 6, 7)
-// are copied at the end of group j.
-// POL = 1 adds the sites' update policies (8 bytes each, staged with the caller ids).
-template <int PM, int LM, int POL>
-__global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
-    constexpr int DEG = 6, D = 2, BS = 8, R = 32;
-    constexpr int ROWS = D * (DEG + 1) * 32 * 16;
-    constexpr int LINK_BYTES = BS * DEG * 8;
-    constexpr int POL_OFF = LINK_BYTES + BS * 4;
-    constexpr int SLOT = POL_OFF + (POL ? BS * 8 : 0);
-    constexpr int WARP_BYTES = ROWS + 2 * SLOT;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const RunState *rs_ = a.run;
-    const uint32_t t = rs_->t;
-    const uint32_t step_idx = rs_->rec / rs_->mcs;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r = lane;
-    unsigned char *wbase = smem + warp * WARP_BYTES;
-    float4 *rows = (float4 *)wbase;
-    unsigned char *lslots = wbase + ROWS;
-    float4 *S = (float4 *)a.spins;
-    const float4 *Sr = S + r;
-    const int2 *E = (const int2 *)a.edges;
-    const uint32_t inst = (uint32_t)(a.inst0 + r);
-    const double *sc = rs_->sched + ((int64_t)step_idx * a.n_inst + a.inst_local0 + r) * 2;
-    const float beta = (float)sc[0], B = (float)sc[1];
-    const float sigma = (POL && rs_->sigma) ? (float)rs_->sigma[a.inst_local0 + r] : 0.f;
-    const int g_end = a.g_end;
-    const int nwarps = blockDim.x >> 5;
-    const int bstride = gridDim.x * nwarps * BS;
-    const int g0 = a.g_begin + (blockIdx.x * nwarps + warp) * BS;
-    uint32_t rk0[10], rk1[10];
-    {
-        uint32_t x = (uint32_t)a.seed, y = (uint32_t)(a.seed >> 32);
-#pragma unroll
-        for (int q = 0; q < 10; ++q) {
-            rk0[q] = x;
-            rk1[q] = y;
-            x += 0x9E3779B9u;
-            y += 0xBB67AE85u;
-        }
-    }
-    auto issue_links = [&](int sb, int slot) {
-        if (sb >= g_end) return;
-        const int ns = min(BS, g_end - sb);
-        unsigned char *dst = lslots + slot * SLOT;
-        const unsigned char *src = (const unsigned char *)(E + a.edge_base + (int64_t)(sb - a.site_off) * DEG);
-        VEGAS_CHECK(sb >= a.g_begin && sb + ns <= a.n_sites_total, 11, sb);
-        VEGAS_CHECK(a.edge_base + (int64_t)(sb - a.site_off + ns) * DEG <= a.n_edges_total, 12, sb);
-        VEGAS_CHECK(((uintptr_t)src & 15) == 0, 13, sb);
-        if (lane < ns * (DEG / 2)) cp16(dst + 16 * lane, src + 16 * lane);
-        if (lane < ns) cp4(dst + LINK_BYTES + 4 * lane, a.orig + sb + lane);
-        if (POL && lane < ns) cp8(dst + POL_OFF + 8 * lane, a.pol32 + sb + lane);
-    };
-    auto issue_rows = [&](int g, int lslot, int j, int rslot) {
-        if (g >= g_end) return;
-        const int4 *lk = (const int4 *)(lslots + lslot * SLOT) + j * (DEG / 2);
-        float4 *dst = rows + rslot * (DEG + 1) * 32 + lane;
-        VEGAS_CHECK(g < a.n_sites_total, 14, g);
-#pragma unroll
-        for (int q = 0; q < DEG / 2; ++q) {
-            const int4 l = lk[q];
-            VEGAS_CHECK(l.x >= 0 && l.x < a.n_sites_total && l.z >= 0 && l.z < a.n_sites_total, 15, l.x);
-            cp16(dst + (2 * q) * 32, Sr + (int64_t)l.x * R);
-            cp16(dst + (2 * q + 1) * 32, Sr + (int64_t)l.z * R);
-        }
-        cp16(dst + DEG * 32, Sr + (int64_t)g * R);
-    };
-
-    issue_links(g0, 0);
-    cp_commit();
-    cp_wait<0>();
-    __syncwarp();
-    issue_rows(g0, 0, 0, 0);
-    cp_commit();
-    issue_rows(g0 + 1, 0, 1, 1);
-    cp_commit();
-    Acc32 acc;
-    bool nan_seen = false;
-    const bool log_accepts = a.alog && t < a.alog_mcs;
-    int ls = 0;
-    for (int sb = g0; sb < g_end; sb += bstride, ls ^= 1) {
-#pragma unroll
-        for (int j = 0; j < BS; ++j) {
-            cp_wait<D - 1>();
-            __syncwarp();
-            const int g = sb + j;
-            if (g < g_end) {
-                const unsigned char *slot = lslots + ls * SLOT;
-                const uint32_t orig = ((const uint32_t *)(slot + LINK_BYTES))[j];
-                staged_attempt<DEG, PM, LM, POL>(a, (const int4 *)slot + j * (DEG / 2),
-                                                 rows + (j & 1) * (DEG + 1) * 32 + lane, orig, g, r, R, t, inst, rk0, rk1,
-                                                 beta, B, S, acc, nan_seen, log_accepts,
-                                                 (const PolicySite32 *)(slot + POL_OFF) + j, sigma);
-            }
-            __syncwarp();
-            if (j == 4) issue_links(sb + bstride, ls ^ 1);
-            if (j + 2 < BS)
-                issue_rows(sb + j + 2, ls, j + 2, j & 1);
-            else
-                issue_rows(sb + bstride + j + 2 - BS, ls ^ 1, j + 2 - BS, j & 1);
-            cp_commit();
-        }
-    }
-    cp_wait<0>();
-    if (nan_seen) atomicOr(a.err, kErrNaN);
-    acc.flush();
-    block_partials(acc.d, acc.nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs_, a.inst_local0));
 }
 
 // ------------------------------------------------------------------ resident (persistent) sweep
@@ -982,20 +395,25 @@ __device__ __forceinline__ Site32 resident_params(const ResidentArgs &a, const R
     return Site32{I.u.nx, I.u.ny, I.u.nz, I.u.s, I.u.ex, I.u.ey, I.u.ez, I.u.k, I.u.kc};
 }
 
+constexpr int kResidentMaxTypes = 8;  // per-type statistics in the resident sweep
+
 template <int NT, int POL>
 __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
     __shared__ int s_item;
     __shared__ double s_red[NT / 32][4];
     __shared__ uint32_t s_acc[NT / 32];
+    __shared__ double s_tm[NT / 32][kResidentMaxTypes][3];  // per warp and type, segment order
     float4 *S = (float4 *)a.spins;
     const int2 *E = (const int2 *)a.edges;
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     const int R = 1 << a.log2R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n_types = a.n_types;
     RunState *rs = a.run;
     bool nan_seen = false;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(a.queue, 1u);
+        for (int q = threadIdx.x; q < (NT / 32) * kResidentMaxTypes * 3; q += NT) (&s_tm[0][0][0])[q] = 0.0;
         __syncthreads();
         const int item = s_item;
         __syncthreads();
@@ -1012,20 +430,37 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
             // the width is read after the barrier that ends the previous MCS (thread 0 wrote it)
             const float sigma = (POL && rs->sigma) ? (float)rs->sigma[I.inst_local] : 0.f;
             Acc32 acc;
-            for (int c = 0; c < I.n_colours; ++c) {
-                const int cb = a.cstart[I.cls_off + c], ce = a.cstart[I.cls_off + c + 1];
-                for (int g = cb + (int)threadIdx.x; g < ce; g += NT) {
+            for (int q = 0; q < I.n_segs; ++q) {
+                const int4 sg = a.segs[I.seg_off + q];  // {begin, end, class begin, type | last << 16}
+                float tm[3] = {0.f, 0.f, 0.f};
+                for (int g = sg.x + (int)threadIdx.x; g < sg.y; g += NT) {
                     const uint32_t orig = (uint32_t)__ldg(a.orig + g);
                     // one code path for every parameter mode: with k = kc = 0 the anisotropy terms
                     // add signed zeros only, so spins and decisions equal the specialised paths'
                     const Site32 p = resident_params(a, I, g);
-                    const bool ok = direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, I.r, R, cb, orig, p, beta, B, t, inst,
-                                                              k0, k1, acc, nan_seen, a.pol, sigma);
+                    float4 Sq;
+                    const bool ok = direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, I.r, R, sg.z, orig, p, beta, B, t,
+                                                              inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq);
+                    tm[0] = __fadd_rn(tm[0], Sq.x);
+                    tm[1] = __fadd_rn(tm[1], Sq.y);
+                    tm[2] = __fadd_rn(tm[2], Sq.z);
                     if (log_accepts)
                         a.alog[(int64_t)t * a.alog_stride + I.alog_base + (int64_t)I.r * I.n_sample_sites + orig] =
                             ok ? 1 : 0;
                 }
-                __syncthreads();
+                if (n_types > 0) {  // this segment's magnetization into its type (fixed order)
+                    double d[3] = {(double)tm[0], (double)tm[1], (double)tm[2]};
+                    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) d[c] += __shfl_xor_sync(0xFFFFFFFFu, d[c], off);
+                    }
+                    const int ty = sg.w & 0xFFFF;
+                    if (lane == 0 && ty < kResidentMaxTypes) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) s_tm[warp][ty][c] += d[c];
+                    }
+                }
+                if (sg.w >> 16) __syncthreads();  // the last segment of a colour class
             }
             acc.flush();
             double v[4] = {acc.d[0], acc.d[1], acc.d[2], acc.d[3]};
@@ -1056,6 +491,18 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
                 if (rs->acc_hist) rs->acc_hist[rec * a.n_inst + I.inst_local] = nsum;
                 if (I.adaptive && rs->sigma && (uint32_t)(rec % rs->mcs) < rs->mcs / 5)
                     rs->sigma[I.inst_local] = adapt_width(rs->sigma[I.inst_local], nsum, I.n_sample_sites);
+                if (n_types > 0 && rs->type_hist) {
+                    double *th = rs->type_hist + (rec * a.n_inst + I.inst_local) * n_types * 3;
+                    for (int k = 0; k < n_types; ++k)
+                        for (int c = 0; c < 3; ++c) {
+                            double x = 0.0;
+                            for (int w = 0; w < NT / 32; ++w) {
+                                x += s_tm[w][k][c];
+                                s_tm[w][k][c] = 0.0;
+                            }
+                            th[k * 3 + c] = x;
+                        }
+                }
             }
             __syncthreads();
         }
@@ -1145,8 +592,9 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
                 Site32 p{a.u32.nx, a.u32.ny, a.u32.nz, a.u32.s, a.u32.ex, a.u32.ey, a.u32.ez, a.u32.k, a.u32.kc};
                 if (a.params_mode == 2) p = site_params32(a, 2, g);
                 // one code path for every parameter mode (zero constants add signed zeros)
+                float4 Sq;
                 const bool ok = direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t, inst, k0,
-                                                          k1, acc, nan_seen, a.pol32, 0.f);
+                                                          k1, acc, nan_seen, a.pol32, 0.f, Sq);
                 if (log_accepts)
                     a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
             }
@@ -1198,17 +646,27 @@ __global__ void __launch_bounds__(256) reduce_kernel(const ReduceArgs a) {
     const uint32_t rec = rs->rec;
     if (il < a.n_inst) {
         const int s = il / a.R, r = il % a.R;
-        const int64_t base = a.slot_base[s];
-        const int32_t cnt = a.slot_count[s];
         double v[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int32_t j = lane; j < cnt; j += 32) {
-            const double *p = a.partial + ((base + j) * a.R + r) * 4;
+        for (int k = 0; k < a.n_groups; ++k) {  // type groups in order, then their total
+            const int64_t base = a.slot_base[s * a.n_groups + k];
+            const int32_t cnt = a.slot_count[s * a.n_groups + k];
+            double u[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int32_t j = lane; j < cnt; j += 32) {
+                const double *p = a.partial + ((base + j) * a.R + r) * 4;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] += p[q];
-        }
-        for (int off = 16; off > 0; off >>= 1) {
+                for (int q = 0; q < 4; ++q) u[q] += p[q];
+            }
+            for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+                for (int q = 0; q < 4; ++q) u[q] += __shfl_xor_sync(0xFFFFFFFFu, u[q], off);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] += u[q];
+            if (lane == 0 && a.n_types > 0 && rs->type_hist) {
+                double *th = rs->type_hist + (((int64_t)rec * a.n_inst + il) * a.n_types + k) * 3;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) th[c] = u[c + 1];
+            }
         }
         if (lane == 0) {
             double *h = rs->hist + ((int64_t)rec * a.n_inst + il) * 4;
@@ -1323,9 +781,9 @@ __global__ void scatter_kernel(void *spins, int precision, int64_t site_off, int
     }
 }
 
-// ------------------------------------------------------------------ variant table
-using PassFn = void (*)(PassArgs);
+}  // namespace
 
+// Direct FP32 sweep kernel for a parameter mode, lower mode and policy flag.
 PassFn select_direct(int pm, int lm, bool pol) {
     static const PassFn tab[2][3][3] = {
         {
@@ -1342,57 +800,8 @@ PassFn select_direct(int pm, int lm, bool pol) {
     return tab[pol ? 1 : 0][pm][lm];
 }
 
-template <int D>
-PassFn select_staged6(int pm, int lm) {
-    static const PassFn tab[3][3] = {
-        {pass32_staged<6, 0, 0, D, -1>, pass32_staged<6, 0, 1, D, -1>, pass32_staged<6, 0, 2, D, -1>},
-        {pass32_staged<6, 1, 0, D, -1>, pass32_staged<6, 1, 1, D, -1>, pass32_staged<6, 1, 2, D, -1>},
-        {pass32_staged<6, 2, 0, D, -1>, pass32_staged<6, 2, 1, D, -1>, pass32_staged<6, 2, 2, D, -1>},
-    };
-    return tab[pm][lm];
-}
-
-PassFn select_r32(int pm, int lm, bool pol) {
-    static const PassFn tab[2][3][3] = {
-        {
-            {pass32_r32<0, 0, 0>, pass32_r32<0, 1, 0>, pass32_r32<0, 2, 0>},
-            {pass32_r32<1, 0, 0>, pass32_r32<1, 1, 0>, pass32_r32<1, 2, 0>},
-            {pass32_r32<2, 0, 0>, pass32_r32<2, 1, 0>, pass32_r32<2, 2, 0>},
-        },
-        {
-            {pass32_r32<0, 0, 1>, pass32_r32<0, 1, 1>, pass32_r32<0, 2, 1>},
-            {pass32_r32<1, 0, 1>, pass32_r32<1, 1, 1>, pass32_r32<1, 2, 1>},
-            {pass32_r32<2, 0, 1>, pass32_r32<2, 1, 1>, pass32_r32<2, 2, 1>},
-        },
-    };
-    return tab[pol ? 1 : 0][pm][lm];
-}
-
-bool staged_shape(const PassArgs &a) { return a.deg == 6 && a.depth >= 2; }
-bool use_r32(const PassArgs &a) { return staged_shape(a) && a.log2R == 5 && a.depth == 2; }
-// Samples with a policy table take the staged path only through the R = 32 kernel.
-bool use_staged(const PassArgs &a) { return staged_shape(a) && (!a.pol32 || use_r32(a)); }
-
-int staged_smem(const PassArgs &a) {
-    if (use_r32(a)) return (kThreads / 32) * (2 * 7 * 32 * 16 + 2 * (8 * 6 * 8 + 8 * 4 + (a.pol32 ? 8 * 8 : 0)));
-    return (kThreads / 32) * staged_geom(6, a.depth, a.log2R).warp_bytes;
-}
-
-PassFn select_staged(const PassArgs &a) {
-    if (use_r32(a)) return select_r32(a.params_mode, a.lower_mode, a.pol32 != nullptr);
-    return a.depth == 2 ? select_staged6<2>(a.params_mode, a.lower_mode) : select_staged6<3>(a.params_mode, a.lower_mode);
-}
-
-PassFn select32(const PassArgs &a) {
-    return use_staged(a) ? select_staged(a) : select_direct(a.params_mode, a.lower_mode, a.pol32 != nullptr);
-}
-
-int smem32(const PassArgs &a) { return use_staged(a) ? staged_smem(a) : 0; }
-
-}  // namespace
-
 void launch_pass32(const PassArgs &a, int grid, void *stream) {
-    select32(a)<<<grid, kThreads, smem32(a), (cudaStream_t)stream>>>(a);
+    select_pass32(a)<<<grid, kThreads, pass32_smem(a), (cudaStream_t)stream>>>(a);
 }
 
 void launch_pass64(const PassArgs &a, int grid, void *stream) {
@@ -1436,6 +845,19 @@ __global__ void advance_kernel(RunState *run, int32_t n) {
 }
 
 void launch_advance(RunState *run, int32_t n, void *stream) { advance_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(run, n); }
+
+// Copies the spins (n16 16-byte words) into slot (rec / mcs - 1) of the snapshot buffer: the
+// step whose last MCS and renormalisation just ran.
+__global__ void snapshot_kernel(const uint4 *spins, uint4 *snap, int64_t n16, const RunState *run) {
+    const int64_t step = (int64_t)(run->rec / run->mcs) - 1;
+    uint4 *dst = snap + step * n16;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n16; w += (int64_t)gridDim.x * blockDim.x)
+        dst[w] = spins[w];
+}
+
+void launch_snapshot(const void *spins, void *snap, int64_t n16, const RunState *run, int grid, void *stream) {
+    snapshot_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>((const uint4 *)spins, (uint4 *)snap, n16, run);
+}
 
 constexpr int kCoopThreads = 256;
 
@@ -1487,9 +909,9 @@ int pass_blocks_per_sm(int precision, const PassArgs &a) {
     if (precision == 64)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass64_kernel, kThreads, 0);
     else {
-        const int sm = smem32(a);
-        if (sm > 0) cudaFuncSetAttribute(select32(a), cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select32(a), kThreads, sm);
+        const int sm = pass32_smem(a);
+        if (sm > 0) cudaFuncSetAttribute(select_pass32(a), cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_pass32(a), kThreads, sm);
     }
     return nb > 0 ? nb : 1;
 }

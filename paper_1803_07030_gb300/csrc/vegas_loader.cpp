@@ -88,7 +88,7 @@ extern "C" int32_t vegas_greedy_colour(int32_t n, const int64_t *row_ptr, const 
 
 namespace vegas {
 
-bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err) {
+bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err, bool type_major) {
     const int32_t n = s.n_sites;
     if (n < 1) { err = "n_sites must be >= 1"; return false; }
     if (!s.row_ptr) { err = "row_ptr is NULL"; return false; }
@@ -199,7 +199,23 @@ bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err) {
             std::stable_sort(L.orig.begin() + L.cstart[(size_t)c], L.orig.begin() + L.cstart[(size_t)c + 1],
                              [&](int32_t x, int32_t y) { return key[(size_t)x] < key[(size_t)y]; });
     }
+    L.n_types = 1;
+    if (s.type)
+        for (int32_t i = 0; i < n; ++i) {
+            if (type_major && (s.type[i] < 0 || s.type[i] >= kMaxTypes)) {
+                err = at("site type outside [0, 64) (per-type statistics) at site", i);
+                return false;
+            }
+            L.n_types = std::max(L.n_types, s.type[i] + 1);
+        }
+    if (type_major && s.type)  // type by type inside each class, keeping the order above
+        for (int32_t c = 0; c < nc; ++c)
+            std::stable_sort(L.orig.begin() + L.cstart[(size_t)c], L.orig.begin() + L.cstart[(size_t)c + 1],
+                             [&](int32_t x, int32_t y) { return s.type[x] < s.type[y]; });
     for (int32_t g = 0; g < n; ++g) L.inv[(size_t)L.orig[(size_t)g]] = g;
+    L.type.assign((size_t)n, 0);
+    if (s.type)
+        for (int32_t g = 0; g < n; ++g) L.type[(size_t)g] = s.type[L.orig[(size_t)g]];
     L.row_ptr.resize((size_t)n + 1);
     L.col.resize((size_t)E);
     L.J.resize((size_t)E);

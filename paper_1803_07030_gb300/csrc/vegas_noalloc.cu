@@ -71,6 +71,7 @@ __global__ void noalloc_setup(const SetupArgs s) {
         h->run.acc = nullptr;  // no acceptance counts, no adaptive policy here
         h->run.acc_hist = nullptr;
         h->run.sigma = nullptr;
+        h->run.type_hist = nullptr;
         for (int q = 0; q < 4; ++q) h->err[q] = 0;
         h->slot_base[0] = 0;
         h->slot_count[0] = s.blocks;
@@ -200,7 +201,7 @@ extern "C" vegas_status vegas_sweep_noalloc(void *spins, const void *links, cons
         launch_pass32(a, grids[c], st);
         slot += grids[c];
     }
-    ReduceArgs ra{partial, hdr->slot_base, hdr->slot_count, &hdr->run, nullptr, replicas, replicas};
+    ReduceArgs ra{partial, hdr->slot_base, hdr->slot_count, &hdr->run, nullptr, replicas, replicas, 1, 0};
     launch_reduce(ra, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("launch: ") + cudaGetErrorString(e));

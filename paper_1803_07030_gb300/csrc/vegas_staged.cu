@@ -1,0 +1,424 @@
+// Staged FP32 sweep kernels for rows of six links (simple cubic lattices): a cp.async pipeline
+// in shared memory per warp, for any replica count (pass32_staged) and the replica-batched
+// R = 32 case (pass32_r32), and the choice between them and the direct kernel.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "vegas_device.cuh"
+#include "vegas_internal.h"
+
+namespace vegas {
+namespace {
+
+// ------------------------------------------------------------------ FP32 colour pass (staged)
+// Rows of exactly DEG links. Each warp walks its share of the class in "groups" of 32
+// work items (32/R sites x R replicas) and keeps a software pipeline in shared memory:
+// the links and caller ids of group k+2D and the neighbour and own spin rows of group k+D
+// are copied with cp.async while group k is computed, so DRAM latency overlaps compute
+// instead of stalling the warp. Group k's rows are complete once all but the last D-1
+// committed copy groups have landed (cp.async.wait_group D-1).
+__device__ __forceinline__ void cp16(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp4(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp8(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One staged attempt: links lk (int4 pairs), rows row[j*32] (neighbour j) and row[DEG*32]
+// (own) already in shared memory; with POL, the site's update policy *ps too.
+template <int DEG, int PM, int LM, int POL = 0>
+__device__ __forceinline__ void staged_attempt(const PassArgs &a, const int4 *lk, const float4 *row, uint32_t orig,
+                                               int g, int r, int R, uint32_t t, uint32_t inst, const uint32_t *rk0,
+                                               const uint32_t *rk1, float beta, float B, float4 *S, Acc32 &acc,
+                                               bool &nan_seen, bool log_accepts, const PolicySite32 *ps = nullptr,
+                                               float sigma = 0.f) {
+    const Site32 p = site_params32(a, PM, g);
+    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+#pragma unroll
+    for (int j = 0; j < DEG / 2; ++j) {
+        const int4 q = lk[j];
+        link32(row[(2 * j) * 32], __int_as_float(q.y), LM == 2 && q.x < a.lower_end, hx, hy, hz, lx, ly, lz);
+        link32(row[(2 * j + 1) * 32], __int_as_float(q.w), LM == 2 && q.z < a.lower_end, hx, hy, hz, lx, ly, lz);
+    }
+    if (LM == 1) {
+        lx = hx;
+        ly = hy;
+        lz = hz;
+    }
+    const float4 Si = row[DEG * 32];
+    uint4 c = make_uint4(orig, t, inst, kPurposeTrial32);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {  // Philox4x32-10 with precomputed round keys
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk0[q], lo1, hi0 ^ c.w ^ rk1[q], lo0);
+    }
+    float4 Sn;
+    bool ok, bad;
+    float e_i;
+    const float3 P =
+        POL ? policy_trial32(*ps, sigma, Si, p.sn, c) : trial_random32(c, p.sn);
+    attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, P, c.z, Sn, ok, e_i, bad);
+    nan_seen |= bad;
+    if (ok) S[(int64_t)g * R + r] = Sn;
+    if (log_accepts)
+        a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
+    acc.add(e_i, Sn, ok);
+}
+
+// Geometry of the staged kernel. A group is 32 work items (spg = 32/R sites x R replicas);
+// a block is NB consecutive groups (BS = NB * spg >= 8 consecutive sites) whose links and
+// caller ids are staged together. NLS block slots cover the 2D-group lookahead of links.
+struct StagedGeom {
+    int spg, BS, NB, NLS, link_bytes, slot_bytes, rows_bytes, warp_bytes;
+};
+
+__host__ __device__ inline StagedGeom staged_geom(int deg, int D, int log2R) {
+    StagedGeom g;
+    g.spg = 32 >> log2R;
+    g.BS = g.spg > 8 ? g.spg : 8;
+    g.NB = g.BS / g.spg;
+    g.NLS = (2 * D + g.NB - 1) / g.NB + 1;
+    g.link_bytes = ((g.BS * deg * 8 + 15) / 16) * 16;
+    g.slot_bytes = g.link_bytes + ((g.BS * 4 + 15) / 16) * 16;
+    g.rows_bytes = D * (deg + 1) * 32 * 16;
+    g.warp_bytes = g.rows_bytes + g.NLS * g.slot_bytes;
+    return g;
+}
+
+// Debug builds (VEGAS_DEBUG_CHECKS) check every staged copy: a failed check sets
+// kErrIndex, records a code and a value, and skips the access.
+#ifdef VEGAS_DEBUG_CHECKS
+#define VEGAS_CHECK(cond, code, val)                   \
+    if (!(cond)) {                                     \
+        atomicOr(a.err, kErrIndex);                    \
+        atomicCAS(a.err + 1, 0u, (uint32_t)(code));    \
+        a.err[2] = (uint32_t)(val);                    \
+        return;                                        \
+    }
+#else
+#define VEGAS_CHECK(cond, code, val)
+#endif
+
+// Position of one group in the warp's sequence: first site, index inside its block, and
+// the slot holding its block's links. Groups are visited in increasing site order.
+struct GroupPos {
+    int sbase, j, lslot;
+    __device__ __forceinline__ void next(const StagedGeom &G, int bstride) {
+        if (++j == G.NB) {
+            j = 0;
+            sbase += bstride - (G.NB - 1) * G.spg;
+            lslot = (lslot + 1 == G.NLS) ? 0 : lslot + 1;
+        } else {
+            sbase += G.spg;
+        }
+    }
+};
+
+// LOG2R >= 0 fixes the replica count at compile time (the batched case R = 32); -1 reads it
+// from the arguments.
+// Depth 2 fits three blocks per SM in shared memory; the register cap keeps them resident.
+template <int DEG, int PM, int LM, int D, int LOG2R>
+__global__ void __launch_bounds__(kThreads, D == 2 ? 3 : 2) pass32_staged(const PassArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const RunState *rs_ = a.run;
+    const uint32_t t = rs_->t;
+    const uint32_t step_idx = rs_->rec / rs_->mcs;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int log2R = LOG2R >= 0 ? LOG2R : a.log2R, R = 1 << log2R;
+    const StagedGeom G = staged_geom(DEG, D, log2R);
+    const int r = lane & (R - 1), my = lane >> log2R;  // replica, site within the group
+    unsigned char *wbase = smem + (size_t)warp * G.warp_bytes;
+    float4 *rows = (float4 *)wbase;                     // [D][DEG+1][32]
+    unsigned char *lslots = wbase + G.rows_bytes;       // [NLS][links | caller ids]
+    float4 *S = (float4 *)a.spins;
+    const float4 *Sr = S + r;
+    const int2 *E = (const int2 *)a.edges;
+    const uint32_t inst = (uint32_t)(a.inst0 + r);
+    const double *sc = rs_->sched + ((int64_t)step_idx * a.n_inst + a.inst_local0 + r) * 2;
+    const float beta = (float)sc[0], B = (float)sc[1];
+    const int g_end = a.g_end;
+    const int nwarps = blockDim.x >> 5;
+    const int W = blockIdx.x * nwarps + warp;
+    const int bstride = gridDim.x * nwarps * G.BS;  // sites between this warp's blocks
+    uint32_t rk0[10], rk1[10];                      // Philox round keys, kept in registers
+    {
+        uint32_t x = (uint32_t)a.seed, y = (uint32_t)(a.seed >> 32);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            rk0[q] = x;
+            rk1[q] = y;
+            x += 0x9E3779B9u;
+            y += 0xBB67AE85u;
+        }
+    }
+
+    auto issue_links = [&](int sb, int slot) {  // links and caller ids of the block at sb
+        if (sb >= g_end) return;
+        const int ns = min(G.BS, g_end - sb);
+        unsigned char *dst = lslots + slot * G.slot_bytes;
+        const unsigned char *src = (const unsigned char *)(E + a.edge_base + (int64_t)(sb - a.site_off) * DEG);
+        const int nch = ns * (DEG / 2);
+        VEGAS_CHECK(sb >= a.g_begin && slot >= 0 && slot < G.NLS, 1, sb);
+        VEGAS_CHECK(a.edge_base + (int64_t)(sb - a.site_off) * DEG + (int64_t)ns * DEG <= a.n_edges_total, 2, sb);
+        VEGAS_CHECK(((uintptr_t)src & 15) == 0 && ((uintptr_t)dst & 15) == 0, 3, sb);
+        VEGAS_CHECK(sb + ns <= a.n_sites_total, 4, sb);
+        for (int c = lane; c < nch; c += 32) cp16(dst + 16 * c, src + 16 * c);
+        if (lane < ns) cp4(dst + G.link_bytes + 4 * lane, a.orig + sb + lane);
+    };
+    auto issue_rows = [&](const GroupPos &p, int rslot) {  // rows of a group (its links have landed)
+        const int g = p.sbase + my;
+        if (g >= g_end) return;
+        const int4 *lk = (const int4 *)(lslots + p.lslot * G.slot_bytes) + (p.j * G.spg + my) * (DEG / 2);
+        float4 *dst = rows + rslot * (DEG + 1) * 32 + lane;
+        VEGAS_CHECK(p.lslot >= 0 && p.lslot < G.NLS && rslot >= 0 && rslot < D, 5, p.lslot * 16 + rslot);
+        VEGAS_CHECK(g < a.n_sites_total, 6, g);
+#pragma unroll
+        for (int j = 0; j < DEG / 2; ++j) {
+            const int4 q = lk[j];
+            VEGAS_CHECK(q.x >= 0 && q.x < a.n_sites_total && q.z >= 0 && q.z < a.n_sites_total, 7, q.x);
+            cp16(dst + (2 * j) * 32, Sr + (int64_t)q.x * R);
+            cp16(dst + (2 * j + 1) * 32, Sr + (int64_t)q.z * R);
+        }
+        cp16(dst + DEG * 32, Sr + (int64_t)g * R);
+    };
+
+    // prologue: links of every block whose first group is among the first 2D, then the
+    // rows of the first D groups
+    const int g0 = a.g_begin + W * G.BS;
+    const int nb_pro = (2 * D + G.NB - 1) / G.NB;
+    for (int b = 0; b < nb_pro; ++b) issue_links(g0 + b * bstride, b);
+    cp_commit();
+    cp_wait<0>();
+    __syncwarp();
+    GroupPos pk{g0, 0, 0};  // group k (computed now)
+    GroupPos pd = pk;       // group k + D (rows issued at the end of this iteration)
+    for (int q = 0; q < D; ++q) {
+        issue_rows(pd, q);
+        cp_commit();
+        pd.next(G, bstride);
+    }
+    int k_issue = nb_pro * G.NB - 2 * D;  // iteration whose end issues the next block's links
+    int sb_next = g0 + nb_pro * bstride, ls_next = nb_pro;
+    int rsl = 0;
+    Acc32 acc;
+    bool nan_seen = false;
+    const bool log_accepts = a.alog && t < a.alog_mcs;
+    for (int k = 0; pk.sbase < g_end; ++k) {
+        cp_wait<D - 1>();
+        __syncwarp();
+        const int g = pk.sbase + my;
+        if (g < g_end) {
+            const unsigned char *slot = lslots + pk.lslot * G.slot_bytes;
+            const int li = pk.j * G.spg + my;
+            const int4 *lk = (const int4 *)slot + li * (DEG / 2);
+            const float4 *row = rows + rsl * (DEG + 1) * 32 + lane;
+            const uint32_t orig = ((const uint32_t *)(slot + G.link_bytes))[li];
+            bool skip = false;
+#ifdef VEGAS_DEBUG_CHECKS
+            if (orig >= (uint32_t)a.n_sample_sites || g >= a.n_sites_total) {
+                atomicOr(a.err, kErrIndex);
+                atomicCAS(a.err + 1, 0u, 8u);
+                a.err[2] = orig;
+                skip = true;
+            }
+#endif
+            if (!skip) staged_attempt<DEG, PM, LM>(a, lk, row, orig, g, r, R, t, inst, rk0, rk1, beta, B, S, acc, nan_seen,
+                                              log_accepts);
+        }
+        __syncwarp();
+        if (k == k_issue) {
+            issue_links(sb_next, ls_next);
+            k_issue += G.NB;
+            sb_next += bstride;
+            ls_next = (ls_next + 1 == G.NLS) ? 0 : ls_next + 1;
+        }
+        issue_rows(pd, rsl);
+        cp_commit();
+        pk.next(G, bstride);
+        pd.next(G, bstride);
+        rsl = (rsl + 1 == D) ? 0 : rsl + 1;
+    }
+    cp_wait<0>();
+    if (nan_seen) atomicOr(a.err, kErrNaN);
+    acc.flush();
+    block_partials(acc.d, acc.nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs_, a.inst_local0));
+}
+
+// Replica-batched sweep (R = 32): one warp = one site x 32 replicas, depth-2 pipeline. A
+// warp owns blocks of eight consecutive sites (block b starts at g0 + b * bstride); the
+// eight groups of a block are unrolled, so every ring slot and offset is a constant:
+// group j of block b computes from row slot j & 1 and link slot b & 1; at j = 4 the links of
+// the next block are copied; rows of group j + 2 (the next block's first two at j = 6, 7)
+// are copied at the end of group j.
+// POL = 1 adds the sites' update policies (8 bytes each, staged with the caller ids).
+template <int PM, int LM, int POL>
+__global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
+    constexpr int DEG = 6, D = 2, BS = 8, R = 32;
+    constexpr int ROWS = D * (DEG + 1) * 32 * 16;
+    constexpr int LINK_BYTES = BS * DEG * 8;
+    constexpr int POL_OFF = LINK_BYTES + BS * 4;
+    constexpr int SLOT = POL_OFF + (POL ? BS * 8 : 0);
+    constexpr int WARP_BYTES = ROWS + 2 * SLOT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const RunState *rs_ = a.run;
+    const uint32_t t = rs_->t;
+    const uint32_t step_idx = rs_->rec / rs_->mcs;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = lane;
+    unsigned char *wbase = smem + warp * WARP_BYTES;
+    float4 *rows = (float4 *)wbase;
+    unsigned char *lslots = wbase + ROWS;
+    float4 *S = (float4 *)a.spins;
+    const float4 *Sr = S + r;
+    const int2 *E = (const int2 *)a.edges;
+    const uint32_t inst = (uint32_t)(a.inst0 + r);
+    const double *sc = rs_->sched + ((int64_t)step_idx * a.n_inst + a.inst_local0 + r) * 2;
+    const float beta = (float)sc[0], B = (float)sc[1];
+    const float sigma = (POL && rs_->sigma) ? (float)rs_->sigma[a.inst_local0 + r] : 0.f;
+    const int g_end = a.g_end;
+    const int nwarps = blockDim.x >> 5;
+    const int bstride = gridDim.x * nwarps * BS;
+    const int g0 = a.g_begin + (blockIdx.x * nwarps + warp) * BS;
+    uint32_t rk0[10], rk1[10];
+    {
+        uint32_t x = (uint32_t)a.seed, y = (uint32_t)(a.seed >> 32);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            rk0[q] = x;
+            rk1[q] = y;
+            x += 0x9E3779B9u;
+            y += 0xBB67AE85u;
+        }
+    }
+    auto issue_links = [&](int sb, int slot) {
+        if (sb >= g_end) return;
+        const int ns = min(BS, g_end - sb);
+        unsigned char *dst = lslots + slot * SLOT;
+        const unsigned char *src = (const unsigned char *)(E + a.edge_base + (int64_t)(sb - a.site_off) * DEG);
+        VEGAS_CHECK(sb >= a.g_begin && sb + ns <= a.n_sites_total, 11, sb);
+        VEGAS_CHECK(a.edge_base + (int64_t)(sb - a.site_off + ns) * DEG <= a.n_edges_total, 12, sb);
+        VEGAS_CHECK(((uintptr_t)src & 15) == 0, 13, sb);
+        if (lane < ns * (DEG / 2)) cp16(dst + 16 * lane, src + 16 * lane);
+        if (lane < ns) cp4(dst + LINK_BYTES + 4 * lane, a.orig + sb + lane);
+        if (POL && lane < ns) cp8(dst + POL_OFF + 8 * lane, a.pol32 + sb + lane);
+    };
+    auto issue_rows = [&](int g, int lslot, int j, int rslot) {
+        if (g >= g_end) return;
+        const int4 *lk = (const int4 *)(lslots + lslot * SLOT) + j * (DEG / 2);
+        float4 *dst = rows + rslot * (DEG + 1) * 32 + lane;
+        VEGAS_CHECK(g < a.n_sites_total, 14, g);
+#pragma unroll
+        for (int q = 0; q < DEG / 2; ++q) {
+            const int4 l = lk[q];
+            VEGAS_CHECK(l.x >= 0 && l.x < a.n_sites_total && l.z >= 0 && l.z < a.n_sites_total, 15, l.x);
+            cp16(dst + (2 * q) * 32, Sr + (int64_t)l.x * R);
+            cp16(dst + (2 * q + 1) * 32, Sr + (int64_t)l.z * R);
+        }
+        cp16(dst + DEG * 32, Sr + (int64_t)g * R);
+    };
+
+    issue_links(g0, 0);
+    cp_commit();
+    cp_wait<0>();
+    __syncwarp();
+    issue_rows(g0, 0, 0, 0);
+    cp_commit();
+    issue_rows(g0 + 1, 0, 1, 1);
+    cp_commit();
+    Acc32 acc;
+    bool nan_seen = false;
+    const bool log_accepts = a.alog && t < a.alog_mcs;
+    int ls = 0;
+    for (int sb = g0; sb < g_end; sb += bstride, ls ^= 1) {
+#pragma unroll
+        for (int j = 0; j < BS; ++j) {
+            cp_wait<D - 1>();
+            __syncwarp();
+            const int g = sb + j;
+            if (g < g_end) {
+                const unsigned char *slot = lslots + ls * SLOT;
+                const uint32_t orig = ((const uint32_t *)(slot + LINK_BYTES))[j];
+                staged_attempt<DEG, PM, LM, POL>(a, (const int4 *)slot + j * (DEG / 2),
+                                                 rows + (j & 1) * (DEG + 1) * 32 + lane, orig, g, r, R, t, inst, rk0, rk1,
+                                                 beta, B, S, acc, nan_seen, log_accepts,
+                                                 (const PolicySite32 *)(slot + POL_OFF) + j, sigma);
+            }
+            __syncwarp();
+            if (j == 4) issue_links(sb + bstride, ls ^ 1);
+            if (j + 2 < BS)
+                issue_rows(sb + j + 2, ls, j + 2, j & 1);
+            else
+                issue_rows(sb + bstride + j + 2 - BS, ls ^ 1, j + 2 - BS, j & 1);
+            cp_commit();
+        }
+    }
+    cp_wait<0>();
+    if (nan_seen) atomicOr(a.err, kErrNaN);
+    acc.flush();
+    block_partials(acc.d, acc.nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs_, a.inst_local0));
+}
+
+// ------------------------------------------------------------------ variant table
+template <int D>
+PassFn select_staged6(int pm, int lm) {
+    static const PassFn tab[3][3] = {
+        {pass32_staged<6, 0, 0, D, -1>, pass32_staged<6, 0, 1, D, -1>, pass32_staged<6, 0, 2, D, -1>},
+        {pass32_staged<6, 1, 0, D, -1>, pass32_staged<6, 1, 1, D, -1>, pass32_staged<6, 1, 2, D, -1>},
+        {pass32_staged<6, 2, 0, D, -1>, pass32_staged<6, 2, 1, D, -1>, pass32_staged<6, 2, 2, D, -1>},
+    };
+    return tab[pm][lm];
+}
+
+PassFn select_r32(int pm, int lm, bool pol) {
+    static const PassFn tab[2][3][3] = {
+        {
+            {pass32_r32<0, 0, 0>, pass32_r32<0, 1, 0>, pass32_r32<0, 2, 0>},
+            {pass32_r32<1, 0, 0>, pass32_r32<1, 1, 0>, pass32_r32<1, 2, 0>},
+            {pass32_r32<2, 0, 0>, pass32_r32<2, 1, 0>, pass32_r32<2, 2, 0>},
+        },
+        {
+            {pass32_r32<0, 0, 1>, pass32_r32<0, 1, 1>, pass32_r32<0, 2, 1>},
+            {pass32_r32<1, 0, 1>, pass32_r32<1, 1, 1>, pass32_r32<1, 2, 1>},
+            {pass32_r32<2, 0, 1>, pass32_r32<2, 1, 1>, pass32_r32<2, 2, 1>},
+        },
+    };
+    return tab[pol ? 1 : 0][pm][lm];
+}
+
+bool staged_shape(const PassArgs &a) { return a.deg == 6 && a.depth >= 2; }
+bool use_r32(const PassArgs &a) { return staged_shape(a) && a.log2R == 5 && a.depth == 2; }
+// Samples with a policy table take the staged path only through the R = 32 kernel.
+bool use_staged(const PassArgs &a) { return staged_shape(a) && (!a.pol32 || use_r32(a)); }
+
+int staged_smem(const PassArgs &a) {
+    if (use_r32(a)) return (kThreads / 32) * (2 * 7 * 32 * 16 + 2 * (8 * 6 * 8 + 8 * 4 + (a.pol32 ? 8 * 8 : 0)));
+    return (kThreads / 32) * staged_geom(6, a.depth, a.log2R).warp_bytes;
+}
+
+PassFn select_staged(const PassArgs &a) {
+    if (use_r32(a)) return select_r32(a.params_mode, a.lower_mode, a.pol32 != nullptr);
+    return a.depth == 2 ? select_staged6<2>(a.params_mode, a.lower_mode) : select_staged6<3>(a.params_mode, a.lower_mode);
+}
+
+}  // namespace
+
+PassFn select_pass32(const PassArgs &a) {
+    return use_staged(a) ? select_staged(a) : select_direct(a.params_mode, a.lower_mode, a.pol32 != nullptr);
+}
+
+int pass32_smem(const PassArgs &a) { return use_staged(a) ? staged_smem(a) : 0; }
+
+}  // namespace vegas

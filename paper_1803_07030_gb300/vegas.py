@@ -62,6 +62,8 @@ class vegas_options(C.Structure):
         ("pipeline_depth", C.c_int32),
         ("timeout_ns", C.c_int64),
         ("fault_inject", C.c_int32),
+        ("type_stats", C.c_int32),
+        ("snapshots", C.c_int32),
     ]
 
 
@@ -83,6 +85,9 @@ class vegas_stats_t(C.Structure):
         ("sweep_ms", C.c_double),
         ("last_run_ms", C.c_double),
         ("device_bytes", C.c_int64),
+        ("n_types", C.c_int32),
+        ("pad_", C.c_int32),
+        ("snapshot_steps", C.c_int64),
     ]
 
 
@@ -97,6 +102,8 @@ SIGNATURES = {
     "vegas_accept_log": (C.c_int, [P, P, C.c_size_t, P]),
     "vegas_accept_history": (C.c_int, [P, P, C.c_size_t, P]),
     "vegas_adaptive_width": (C.c_int, [P, P]),
+    "vegas_type_history": (C.c_int, [P, P, C.c_size_t, P]),
+    "vegas_get_snapshot": (C.c_int, [P, C.c_int32, C.c_int64, P]),
     "vegas_set_adaptive_width": (C.c_int, [P, P]),
     "vegas_stats": (C.c_int, [P, P]),
     "vegas_greedy_colour": (C.c_int32, [C.c_int32, P, P, P]),
@@ -252,6 +259,22 @@ def vegas_accept_history(ctx) -> np.ndarray:
     return out
 
 
+def vegas_type_history(ctx) -> np.ndarray:
+    lib = load_library()
+    n = C.c_size_t()
+    _check(lib.vegas_type_history(ctx, None, 0, C.byref(n)), ctx)
+    out = np.zeros(n.value, dtype=np.float64)
+    if n.value:
+        _check(lib.vegas_type_history(ctx, _ptr(out), n.value, C.byref(n)), ctx)
+    return out
+
+
+def vegas_get_snapshot(ctx, inst: int, step: int, n_sites: int) -> np.ndarray:
+    out = np.zeros((n_sites, 3), dtype=np.float64)
+    _check(load_library().vegas_get_snapshot(ctx, inst, step, _ptr(out)), ctx)
+    return out
+
+
 def vegas_adaptive_width(ctx, n_instances: int) -> np.ndarray:
     out = np.zeros(n_instances, dtype=np.float64)
     _check(load_library().vegas_adaptive_width(ctx, _ptr(out)), ctx)
@@ -319,7 +342,7 @@ class Context:
                  inst_base: int = 0, device: int = -1, stream="torch", variant: int = -1,
                  accept_log_mcs: int = 0, timing: bool = False, graphs: bool = True, max_blocks: int = 0,
                  pipeline_depth: int = 0, timeout_ns: int = 0, fault_inject: int = 0,
-                 library: Optional[str] = None):
+                 type_stats: bool = False, snapshots: bool = False, library: Optional[str] = None):
         self.samples = list(samples)
         self.n_sites = [int(np.asarray(s.row_ptr).shape[0] - 1) for s in self.samples]
         if library is not None:
@@ -339,6 +362,8 @@ class Context:
         o.pipeline_depth = pipeline_depth
         o.timeout_ns = timeout_ns
         o.fault_inject = fault_inject
+        o.type_stats = 1 if type_stats else 0
+        o.snapshots = 1 if snapshots else 0
         o.cuda_stream = _current_stream() if stream == "torch" else stream
         self.replicas = replicas
         self.ptr = None
@@ -375,6 +400,16 @@ class Context:
     def accept_history(self) -> np.ndarray:
         """[n_instances, records] accepted attempts per MCS."""
         return vegas_accept_history(self.ptr).reshape(self.n_instances, -1)
+
+    def type_history(self) -> np.ndarray:
+        """[n_instances, records, n_types, 3] magnetization of every site type (type_stats)."""
+        h = vegas_type_history(self.ptr)
+        n_types = self.stats()["n_types"]
+        return h.reshape(self.n_instances, -1, n_types, 3)
+
+    def snapshot(self, inst: int, step: int) -> np.ndarray:
+        """Spins of instance inst at the end of temperature/field step `step` (snapshots)."""
+        return vegas_get_snapshot(self.ptr, inst, step, self.n_sites[inst // self.replicas])
 
     def adaptive_width(self) -> np.ndarray:
         return vegas_adaptive_width(self.ptr, self.n_instances)

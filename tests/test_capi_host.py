@@ -125,6 +125,16 @@ def test_invalid_policy_tables_rejected(lib, name, make, needle):
     assert needle in msg, msg
 
 
+def test_type_statistics_reject_bad_types(lib):
+    s = sc_periodic(4)
+    s.type = np.full(64, -1, dtype=np.int32)
+    st, msg = _create_status([s], type_stats=1)
+    assert st == vb.EINVAL and "site type outside [0, 64)" in msg
+    s.type = np.full(64, 64, dtype=np.int32)
+    st, msg = _create_status([s], type_stats=1)
+    assert st == vb.EINVAL
+
+
 def test_policy_table_without_params_rejected(lib):
     import ctypes as C
 
@@ -140,7 +150,8 @@ def test_policy_table_without_params_rejected(lib):
 
 
 @pytest.mark.parametrize("opt", [{"precision": 16}, {"replicas": 3}, {"replicas": 64}, {"variant": 7},
-                                 {"accept_log_mcs": -1}])
+                                 {"accept_log_mcs": -1}, {"type_stats": 2}, {"snapshots": -1},
+                                 {"variant": 2, "type_stats": 1}])
 def test_invalid_options_rejected(lib, opt):
     st, msg = _create_status([sc_periodic(4)], **opt)
     assert st == vb.EINVAL, (opt, msg)
