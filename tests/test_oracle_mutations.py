@@ -89,3 +89,43 @@ def test_pins_catch_mutant(name, old, new, checks):
         path = oracle.oracle.compile_source(text, os.path.join(d, "mutant.so"))
         with ora.use_library(path):
             assert any(_fails(c) for c in checks), f"no pin caught: {name}"
+
+
+# --------------------------------------------------------------------------- analysis (numpy)
+
+import types  # noqa: E402
+
+import test_oracle_analysis as ana  # noqa: E402
+from oracle import analysis as _analysis  # noqa: E402
+
+ASRC = open(_analysis.__file__).read()
+
+ANALYSIS_MUTANTS = [
+    ("specific heat without T^2", "c = np.var(E) / (N * T * T)", "c = np.var(E) / (N * T)",
+     [ana.test_thermal_averages_of_gaussian_series]),
+    ("Binder factor", "u4 = 1.0 - np.mean(M2 * M2) / (3.0 * np.mean(M2) ** 2)",
+     "u4 = 1.0 - np.mean(M2 * M2) / (2.0 * np.mean(M2) ** 2)", [ana.test_thermal_averages_of_gaussian_series]),
+    ("cumulant sign", 'out["v1"] = E.mean() - np.mean(A * E) / A.mean()',
+     'out["v1"] = np.mean(A * E) / A.mean() - E.mean()', [ana.test_cumulants_v1_v2_of_independent_ising_spins]),
+    ("autocorrelation doubled", "        tau += rho", "        tau += 2.0 * rho", [ana.test_tau_of_ar1_series]),
+    ("jackknife factor", "np.sqrt((n_bins - 1) / n_bins *", "np.sqrt(1.0 / n_bins *",
+     [ana.test_thermal_averages_of_gaussian_series]),
+    ("reweighting sign", "g_new = np.logaddexp.reduce(-np.outer(bk, Ei) - D[None, :], axis=1)",
+     "g_new = np.logaddexp.reduce(np.outer(bk, Ei) - D[None, :], axis=1)",
+     [ana.test_multiple_histogram_interpolation_and_free_energies]),
+    ("reweighting weight of the target", "        lw = -b * Ei - D", "        lw = -b * Ei + D",
+     [ana.test_single_histogram_reweighting_of_free_spins]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,checks", ANALYSIS_MUTANTS, ids=[m[0] for m in ANALYSIS_MUTANTS])
+def test_analysis_pins_catch_mutant(name, old, new, checks):
+    assert ASRC.count(old) == 1, name
+    mod = types.ModuleType("analysis_mutant")
+    exec(compile(ASRC.replace(old, new), "analysis_mutant.py", "exec"), mod.__dict__)
+    saved = ana.analysis
+    ana.analysis = mod
+    try:
+        assert any(_fails(c) for c in checks), f"no pin caught: {name}"
+    finally:
+        ana.analysis = saved
