@@ -379,7 +379,8 @@ def run_workload(args):
     policy = apply_policy(w.samples, args.policy)
     stream = torch.cuda.current_stream()
     ctx = vg.Context(w.samples, precision=w.precision, replicas=w.replicas, seed=w.seed,
-                     stream=int(stream.cuda_stream), variant=args.variant)
+                     stream=int(stream.cuda_stream), variant=args.variant, type_stats=args.type_stats,
+                     snapshots=args.snapshots)
     for _ in range(args.warmup):
         ctx.run(w.T, w.B, w.mcs)
     torch.cuda.synchronize()
@@ -401,12 +402,13 @@ def run_workload(args):
         "config": {"workload": args.workload, "instances": w.n_inst, "sites": w.n_sites_total,
                    "steps_x_mcs": [w.n_steps, w.mcs], "attempts_per_step": w.attempts(),
                    "l2": "working set inside L2" if w.n_sites_total * 16 < 100e6 else "larger than L2",
-                   "policy": policy or "random"},
+                   "policy": policy or "random", "type_stats": bool(args.type_stats),
+                   "snapshots": bool(args.snapshots)},
         "variant": st1["variant"], "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
         "clocks": clk.summary(),
     }
     ctx.close()
-    if args.workload == "np256" and not policy:
+    if args.workload == "np256" and not policy and not args.type_stats and not args.snapshots:
         plain_mcs = min(w.mcs, 100)
         plain_ms, plain_att = 0.0, 0
         for p, smp in enumerate(w.samples):
@@ -430,6 +432,61 @@ def run_workload(args):
     return 0
 
 
+def run_analysis(args):
+    """Times the history analysis on the GPU (C-ABI, host arrays in and out, copies included):
+    thermal averages of 1024 histories of 10,000 records (AR(1) energies with tau ~ 10), and
+    multiple-histogram reweighting of 32 runs x 20,000 samples. The oracle (numpy) is timed on
+    a bounded sample of the same work."""
+    import torch
+    import paper_1803_07030_gb300 as vg
+
+    vg.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(SEED)
+    ns, ln, phi = 1024, 10000, 0.9
+    x = np.zeros((ns, ln))
+    xi = rng.normal(size=(ns, ln)) * np.sqrt(1 - phi * phi)
+    for i in range(1, ln):
+        x[:, i] = phi * x[:, i - 1] + xi[:, i]
+    H = np.stack([-3000.0 + 30.0 * x, 50.0 * rng.normal(size=(ns, ln)), 50.0 * x, 300.0 + 40.0 * x], axis=2)
+    Tv = np.linspace(0.5, 2.5, ns)
+    for _ in range(args.warmup):
+        vg.thermal_averages(H, 2000, 20, Tv, 1000.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vg.thermal_averages(H, 2000, 20, Tv, 1000.0)
+    ta = (time.perf_counter() - t0) / args.steps
+    K, n = 32, 20000
+    betas = np.linspace(0.4, 1.2, K)
+    E = np.stack([rng.normal(-1000.0 * b, 30.0, n) for b in betas])
+    O = np.stack([np.column_stack([E[k], E[k] ** 2]) for k in range(K)])
+    vg.reweight(E, O, betas, betas, max_iter=50, tol=1e-300)
+    t0 = time.perf_counter()
+    _, _, it = vg.reweight(E, O, betas, np.linspace(0.4, 1.2, 64), max_iter=200, tol=1e-300)
+    tr = time.perf_counter() - t0
+    from oracle import analysis as ora_an
+
+    t0 = time.perf_counter()
+    for s_ in range(8):
+        ora_an.thermal_averages(H[s_], 2000, 20, Tv[s_], 1000.0)
+    to = (time.perf_counter() - t0) / 8
+    t0 = time.perf_counter()
+    ora_an.reweight(E, O, betas, np.linspace(0.4, 1.2, 64), max_iter=5, tol=1e-300)
+    tro = (time.perf_counter() - t0) / 5
+    line = {
+        "metric": "history records analysed/s (thermal averages, errors, tau) on 1 GB300", "value": ns * ln / ta,
+        "unit": "records/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * ta,
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "1024 histories x 10,000 records (AR(1), tau ~ 10), cut 2000, 20 bins; "
+                               "reweighting 32 runs x 20,000 samples to 64 temperatures"},
+        "reweight": {"iterations": it, "s": tr, "sample_iterations_per_s": K * n * it / tr},
+        "cpu_baseline": {"value": ln / to, "unit": "records/s", "cores": 1, "kind": "oracle",
+                         "sample": "8 of the 1024 histories", "reweight_sample_iterations_per_s": K * n / tro},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     global L_SIDE
     ap = argparse.ArgumentParser()
@@ -448,12 +505,17 @@ def main():
     ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="sweep variant: -1 automatic (timed on the first run), 0 per colour class, 1 resident, "
                          "2 cooperative; profiling commands fix it because ncu distorts the automatic timing")
+    ap.add_argument("--analysis", action="store_true", help="time the history analysis instead of the sweep")
+    ap.add_argument("--type-stats", action="store_true", help="secondary workloads: record per-type magnetization")
+    ap.add_argument("--snapshots", action="store_true", help="secondary workloads: keep the final state of every step")
     ap.add_argument("--quick", action="store_true",
                     help="time the sweep only (no e2e, plain-path or CPU-baseline legs); for profiling runs")
     args = ap.parse_args()
     L_SIDE = args.side
     if args.impl == "reference":
         return run_reference(args)
+    if args.analysis:
+        return run_analysis(args)
     if args.workload != "sg256x32":
         return run_workload(args)
     return run_ours(args)

@@ -257,6 +257,53 @@ vegas_status vegas_type_history(const vegas_ctx *ctx, double *out, size_t capaci
  */
 vegas_status vegas_get_snapshot(const vegas_ctx *ctx, int32_t instance, int64_t step, double *out);
 
+/* ---------------------------------------------------------------- history analysis
+ * Stand-alone (no context): host arrays in and out, device temporaries allocated and freed
+ * inside the call, FP64 throughout. Errors: the status and vegas_analysis_last_error().
+ */
+
+/* Fields per series of vegas_thermal_averages, in this order. */
+#define VEGAS_AVG_FIELDS 16
+/*   0 e     = <E>/N            1 e_err  (binned standard error)
+ *   2 m     = <|M|>/N          3 m_err  (binned)
+ *   4 c     = (<E^2> - <E>^2) / (N T^2)      5 c_err   (jackknife over the bins)
+ *   6 chi   = (<M^2> - <|M|>^2) / (N T)      7 chi_err (jackknife)
+ *   8 u4    = 1 - <M^4> / (3 <M^2>^2)        9 u4_err  (jackknife; Binder cumulant)
+ *  10 v1    = <E> - <|M| E> / <|M|>         11 v2 = <E> - <M^2 E> / <M^2>
+ *           (v_j = d ln<|M|^j> / d beta, the cumulants of finite-size scaling, Sec. IV.B)
+ *  12 tau_e, 13 tau_m: integrated autocorrelation times of E and |M| in MCS (Sec. II), with
+ *           Sokal's automatic window (the smallest W >= 6 tau(W), at most n/2)
+ *  14 n (records used), 15 n_bins. k_B = 1; E, M are the totals of a history record. */
+
+/*
+ * Thermal averages of n_series histories (one temperature/field step of one instance each),
+ * series = [n_series][len][4] (E, Mx, My, Mz after every MCS, as from vegas_history), the
+ * first `cut` records of each dropped (thermalisation). Bins: b = (len - cut) / n_bins
+ * records each over the first b * n_bins records after the cut. T[s] and n_sites[s] are the
+ * series' temperature and site count. out = [n_series][VEGAS_AVG_FIELDS]. cuda_stream: a
+ * cudaStream_t or NULL. Returns VEGAS_EINVAL for 0 > cut >= len, n_bins outside [2, 64],
+ * fewer records than bins, T or n_sites <= 0 or non-finite.
+ */
+vegas_status vegas_thermal_averages(const double *series, int64_t n_series, int64_t len, int64_t cut,
+                                    int32_t n_bins, const double *T, const double *n_sites, double *out,
+                                    void *cuda_stream);
+
+/*
+ * Single and multiple histogram reweighting (Sec. IV.E; Ferrenberg & Swendsen 1988, 1989):
+ * K runs at inverse temperatures betas_k with n samples each, energies E = [K][n] and
+ * observables O = [K][n][n_obs] (n_obs <= 8, may be 0). The free energies g_k = ln Z_k -
+ * ln Z_0 solve g_k = ln sum_i exp(-beta_k E_i - D_i), D_i = ln sum_j n exp(-beta_j E_i -
+ * g_j), iterated from g = 0 until max |change| < tol or max_iter iterations; then
+ * out[b][q] = <O_q> at betas_out[b]. K = 1 is the single-histogram method. g_out ([K]) and
+ * iters_out may be NULL.
+ */
+vegas_status vegas_reweight(const double *E, const double *O, int32_t K, int64_t n, int32_t n_obs,
+                            const double *betas_k, const double *betas_out, int32_t n_out, int32_t max_iter,
+                            double tol, double *out, double *g_out, int32_t *iters_out, void *cuda_stream);
+
+/* Message of the last failed analysis call on this thread. */
+const char *vegas_analysis_last_error(void);
+
 /* Counters and sizes of the context (valid also on a poisoned context). */
 vegas_status vegas_stats(const vegas_ctx *ctx, vegas_stats_t *out);
 

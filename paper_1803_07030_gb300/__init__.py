@@ -6,6 +6,7 @@ binding. Importing the package does not build anything; call build.build() first
 
 from .build import LIB, build  # noqa: F401
 from .vegas import (  # noqa: F401
+    AVG_FIELDS,
     POLICY_ADAPTIVE,
     POLICY_GAUSSIAN,
     POLICY_HINZKE_NOWAK,
@@ -15,6 +16,8 @@ from .vegas import (  # noqa: F401
     Context,
     VegasError,
     load_library,
+    reweight,
+    thermal_averages,
     vegas_accept_history,
     vegas_accept_log,
     vegas_adaptive_width,

@@ -112,7 +112,14 @@ SIGNATURES = {
     "vegas_sweep_noalloc": (C.c_int, [P, P, P, P, C.c_int32, P, C.c_int32, C.c_int32, P, P, P, C.c_uint64,
                                       C.c_int32, C.c_uint32, P, P]),
     "vegas_noalloc_last_error": (C.c_char_p, []),
+    "vegas_thermal_averages": (C.c_int, [P, C.c_int64, C.c_int64, C.c_int64, C.c_int32, P, P, P, P]),
+    "vegas_reweight": (C.c_int, [P, P, C.c_int32, C.c_int64, C.c_int32, P, P, C.c_int32, C.c_int32, C.c_double, P,
+                                 P, P, P]),
+    "vegas_analysis_last_error": (C.c_char_p, []),
 }
+
+AVG_FIELDS = ("e", "e_err", "m", "m_err", "c", "c_err", "chi", "chi_err", "u4", "u4_err", "v1", "v2", "tau_e",
+              "tau_m", "n", "bins")
 
 _lib = None
 
@@ -306,6 +313,43 @@ def vegas_sweep_noalloc(spins_ptr: int, links_ptr: int, row_ptr_ptr: int, site_i
     if st != OK:
         m = lib.vegas_noalloc_last_error()
         raise VegasError(st, m.decode() if m else "")
+
+
+def _check_analysis(st: int) -> None:
+    if st != OK:
+        msg = load_library().vegas_analysis_last_error()
+        raise VegasError(st, msg.decode() if msg else "")
+
+
+def thermal_averages(series, cut: int, n_bins: int, T, n_sites, stream=None) -> np.ndarray:
+    """series [n_series, len, 4] (E, Mx, My, Mz per MCS); T, n_sites per series (or scalars).
+    Returns [n_series, 16] in the order of AVG_FIELDS, computed on the GPU."""
+    h = _arr(series, np.float64)
+    if h.ndim == 2:
+        h = h[None]
+    ns, ln = h.shape[0], h.shape[1]
+    Tv = _arr(np.broadcast_to(np.asarray(T, dtype=np.float64), (ns,)), np.float64)
+    Nv = _arr(np.broadcast_to(np.asarray(n_sites, dtype=np.float64), (ns,)), np.float64)
+    out = np.zeros((ns, len(AVG_FIELDS)))
+    _check_analysis(load_library().vegas_thermal_averages(_ptr(h), ns, ln, int(cut), int(n_bins), _ptr(Tv), _ptr(Nv),
+                                                          _ptr(out), stream))
+    return out
+
+
+def reweight(E, O, betas_k, betas_out, max_iter: int = 10000, tol: float = 1e-12, stream=None):
+    """E [K, n], O [K, n, n_obs]; returns (<O> at betas_out [n_out, n_obs], g [K], iterations)."""
+    Ea = _arr(E, np.float64)
+    K, n = Ea.shape
+    Oa = _arr(O, np.float64).reshape(K, n, -1)
+    n_obs = Oa.shape[2]
+    bk = _arr(betas_k, np.float64)
+    bo = _arr(np.atleast_1d(betas_out), np.float64)
+    out = np.zeros((bo.shape[0], max(n_obs, 1)))
+    g = np.zeros(K)
+    it = C.c_int32()
+    _check_analysis(load_library().vegas_reweight(_ptr(Ea), _ptr(Oa), K, n, n_obs, _ptr(bk), _ptr(bo), bo.shape[0],
+                                                  int(max_iter), float(tol), _ptr(out), _ptr(g), C.byref(it), stream))
+    return out[:, :n_obs], g, it.value
 
 
 def vegas_last_error(ctx=None) -> str:

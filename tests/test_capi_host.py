@@ -178,3 +178,38 @@ def test_no_device_is_an_error_not_a_fallback(lib):
         pass
     st, msg = _create_status([sc_periodic(4)])
     assert st == vb.ECUDA and "no CUDA device" in msg
+
+
+def test_analysis_arguments_rejected_before_the_device(lib):
+    import ctypes as C
+
+    h = np.zeros((2, 50, 4))
+    T = np.ones(2)
+    N = np.ones(2)
+    out = np.zeros((2, vb.AVG_FIELDS.__len__()))
+    P = lambda a: a.ctypes.data  # noqa: E731
+    for cut, nb, Tv in ((50, 10, T), (0, 1, T), (0, 65, T), (45, 10, T), (0, 10, np.array([1.0, 0.0]))):
+        st = lib.vegas_thermal_averages(P(h), 2, 50, cut, nb, P(Tv), P(N), P(out), None)
+        assert st == vb.EINVAL, (cut, nb)
+    E = np.zeros((2, 10))
+    O = np.zeros((2, 10, 9))
+    bk = np.ones(2)
+    bo = np.ones(1)
+    assert lib.vegas_reweight(P(E), P(O), 2, 10, 9, P(bk), P(bo), 1, 10, 1e-9, P(out), None, None, None) == vb.EINVAL
+    assert lib.vegas_reweight(P(E), P(O), 2, 10, 1, P(bk), P(bo), 1, 10, 0.0, P(out), None, None, None) == vb.EINVAL
+    E[0, 3] = np.nan
+    assert lib.vegas_reweight(P(E), P(O), 2, 10, 1, P(bk), P(bo), 1, 10, 1e-9, P(out), None, None, None) == vb.EINVAL
+    assert b"non-finite" in lib.vegas_analysis_last_error()
+
+
+def test_analysis_without_a_device_is_an_error(lib):
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(vb.VegasError) as e:
+        vb.thermal_averages(np.ones((1, 40, 4)), 0, 4, 1.0, 1.0)
+    assert e.value.status == vb.ECUDA
