@@ -18,6 +18,7 @@ from .oracle import (  # noqa: F401
     energy,
     greedy_colour,
     init_spins,
+    ising_run,
     log,
     magnetisation,
     philox4x32_10,

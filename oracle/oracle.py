@@ -96,6 +96,9 @@ def _configure(lib):
     lib.vo_cap_height.restype = C.c_double
     lib.vo_trial.argtypes = [P, P, C.c_int32, C.c_uint64, C.c_uint32, C.c_int32, C.c_double, P]
     lib.vo_trial.restype = C.c_int
+    lib.vo_ising_run.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_uint64, C.c_int32, C.c_int32, P, P, C.c_int32,
+                                 C.c_int32, C.c_uint32, P, C.c_int32, P]
+    lib.vo_ising_run.restype = C.c_int
     return lib
 
 
@@ -290,3 +293,24 @@ def run(sample, T, B, mcs: int, seed: int = 1, spins=None, inst_base: int = 0, t
         raise ValueError("oracle rejected its arguments")
     return {"spins": S, "history": hist, "accepted": acc, "sigma": sg, "accept_log": alog, "type_history": th,
             "snapshots": snaps, "err": err}
+
+
+def ising_run(dims: int, L: int, J: float, T, h, mcs: int, seed: int = 1, inst_base: int = 0, spins=None,
+              t0: int = 0):
+    """Ising chain (spin flip) on the periodic square (dims 2) or cubic (dims 3) lattice.
+
+    T, h: [n_rep, n_steps]. spins: None (Philox initial state) or int8 [n_rep, L^dims].
+    Returns dict(spins=int8 [n_rep, n], history=[n_rep, n_steps*mcs, 2] = (E, M)).
+    """
+    T = np.ascontiguousarray(np.atleast_2d(T), dtype=np.float64)
+    h = np.ascontiguousarray(np.broadcast_to(np.atleast_2d(h), T.shape), dtype=np.float64)
+    n_rep, n_steps = T.shape
+    n = L ** dims
+    init = 1 if spins is None else 0
+    S = np.zeros((n_rep, n), dtype=np.int8) if spins is None else np.array(spins, dtype=np.int8).reshape(n_rep, n)
+    hist = np.zeros((n_rep, n_steps * mcs, 2))
+    err = _load().vo_ising_run(dims, L, J, seed, n_rep, inst_base, _ptr(T), _ptr(h), n_steps, mcs, t0, _ptr(S), init,
+                               _ptr(hist))
+    if err < 0:
+        raise ValueError("oracle rejected its arguments")
+    return {"spins": S, "history": hist}

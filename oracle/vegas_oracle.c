@@ -686,3 +686,95 @@ int vo_run_ex(const vo_sample *s, const int32_t *colour, uint64_t seed, int32_t 
     free(col_own);
     return err;
 }
+
+/* ---------------------------------------------------------------- Ising model (spin flip)
+ * The Ising limit of Eq. 1 (Sec. II: Ising systems updated with the spin-flip policy):
+ * s_i = +-1 on a periodic square (dims 2) or simple cubic (dims 3) lattice of even side L,
+ * site id i = x + L (y + L z), E = -J sum_<ij> s_i s_j - h sum_i s_i (each bond once).
+ * One MCS: every site of colour 0 ((x + y + z) even) in increasing id, then colour 1.
+ * Attempt (Eq. 4): dE = 2 s_i (J sum_j s_j + h); accept iff dE <= 0 or u < exp(-(beta dE)),
+ * where u = w 2^-32 and w is word (inst & 3) of Philox(seed; i, t, inst >> 2, 0x80000).
+ * Initial state: s_i = +1 iff bit 31 of word (inst & 3) of Philox(seed; i, 0xFFFFFFFF,
+ * inst >> 2, 0x90000) is set.
+ */
+static void ising_coords(int32_t dims, int32_t L, int32_t i, int32_t c[3]) {
+    c[0] = i % L;
+    c[1] = (i / L) % L;
+    c[2] = dims == 3 ? i / (L * L) : 0;
+}
+
+static int32_t ising_id(int32_t dims, int32_t L, const int32_t c[3]) {
+    (void)dims;
+    return c[0] + L * (c[1] + L * c[2]);
+}
+
+/* Neighbour ids of site i: -x, +x, -y, +y (, -z, +z); returns the count. */
+static int ising_neighbours(int32_t dims, int32_t L, int32_t i, int32_t nb[6]) {
+    int32_t c[3];
+    ising_coords(dims, L, i, c);
+    int k = 0;
+    for (int d = 0; d < dims; ++d)
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            int32_t q[3] = {c[0], c[1], c[2]};
+            q[d] = (q[d] + sgn + L) % L;
+            nb[k++] = ising_id(dims, L, q);
+        }
+    return k;
+}
+
+int vo_ising_run(int32_t dims, int32_t L, double J, uint64_t seed, int32_t n_rep, int32_t inst_base,
+                 const double *T, const double *h, int32_t n_steps, int32_t mcs, uint32_t t0, int8_t *spins,
+                 int32_t init, double *history) {
+    if ((dims != 2 && dims != 3) || L < 4 || (L & 1) || n_rep < 1 || inst_base < 0) return -1;
+    const int32_t n = dims == 3 ? L * L * L : L * L;
+    for (int32_t r = 0; r < n_rep; ++r) {
+        const uint32_t inst = (uint32_t)(inst_base + r);
+        int8_t *s = spins + (int64_t)r * n;
+        if (init)
+            for (int32_t i = 0; i < n; ++i) {
+                uint32_t w[4];
+                philox(seed, (uint32_t)i, 0xFFFFFFFFu, inst >> 2, 0x90000u, w);
+                s[i] = (w[inst & 3u] >> 31) ? 1 : -1;
+            }
+        uint32_t t = t0;
+        int64_t rec = 0;
+        for (int32_t st = 0; st < n_steps; ++st) {
+            const double beta = 1.0 / T[(int64_t)r * n_steps + st];
+            const double hh = h[(int64_t)r * n_steps + st];
+            for (int32_t m = 0; m < mcs; ++m) {
+                for (int32_t colour = 0; colour < 2; ++colour)
+                    for (int32_t i = 0; i < n; ++i) {
+                        int32_t c[3], nb[6];
+                        ising_coords(dims, L, i, c);
+                        if (((c[0] + c[1] + c[2]) & 1) != colour) continue;
+                        const int z = ising_neighbours(dims, L, i, nb);
+                        int32_t sum = 0;
+                        for (int k = 0; k < z; ++k) sum += s[nb[k]];
+                        const double si = (double)s[i];
+                        const double dE = 2.0 * si * (J * (double)sum + hh);
+                        int acc = dE <= 0.0;
+                        if (!acc) {
+                            uint32_t w[4];
+                            philox(seed, (uint32_t)i, t, inst >> 2, 0x80000u, w);
+                            acc = (double)w[inst & 3u] * 0x1p-32 < exp(-(beta * dE));
+                        }
+                        if (acc) s[i] = (int8_t)(-s[i]);
+                    }
+                /* E and M after the MCS: bonds along +x, +y (, +z) from every site */
+                int64_t bsum = 0, msum = 0;
+                for (int32_t i = 0; i < n; ++i) {
+                    int32_t nb[6];
+                    ising_neighbours(dims, L, i, nb);
+                    for (int d = 0; d < dims; ++d) bsum += (int64_t)s[i] * s[nb[2 * d + 1]];
+                    msum += s[i];
+                }
+                double *hr = history + ((int64_t)r * n_steps * mcs + rec) * 2;
+                hr[0] = -J * (double)bsum - hh * (double)msum;
+                hr[1] = (double)msum;
+                ++rec;
+                ++t;
+            }
+        }
+    }
+    return 0;
+}

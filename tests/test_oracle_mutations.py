@@ -16,6 +16,7 @@ from oracle import oracle as ora
 import test_oracle_pins as pins
 import test_oracle_policies as pol
 import test_oracle_outputs as outs
+import test_oracle_ising as ising
 
 SRC = open(os.path.join(os.path.dirname(ora.__file__), "vegas_oracle.c")).read()
 
@@ -68,6 +69,15 @@ MUTANTS = [
      "        if (jb->snaps) memcpy(jb->snaps + (int64_t)st * n * 3, jb->S, sizeof(double) * 3 * (size_t)n);\n"
      "        vo_renormalise(s, jb->S);\n        if (0) memcpy(",
      [outs.test_snapshots_are_the_final_states_per_step]),
+    ("Ising field sign", "const double dE = 2.0 * si * (J * (double)sum + hh);",
+     "const double dE = 2.0 * si * (J * (double)sum - hh);", [ising.test_paramagnet_tanh_law]),
+    ("Ising bonds counted twice", "for (int d = 0; d < dims; ++d) bsum += (int64_t)s[i] * s[nb[2 * d + 1]];",
+     "for (int d = 0; d < 2 * dims; ++d) bsum += (int64_t)s[i] * s[nb[d]];",
+     [ising.test_four_by_four_exact_averages]),
+    ("Ising acceptance without beta", "acc = (double)w[inst & 3u] * 0x1p-32 < exp(-(beta * dE));",
+     "acc = (double)w[inst & 3u] * 0x1p-32 < exp(-(dE));", [ising.test_paramagnet_tanh_law]),
+    ("Ising neighbour along the wrong axis", "q[d] = (q[d] + sgn + L) % L;", "q[0] = (q[0] + sgn + L) % L;",
+     [ising.test_four_by_four_exact_averages, ising.test_onsager_energy_and_spontaneous_magnetization]),
 ]
 
 
