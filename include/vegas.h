@@ -304,6 +304,51 @@ vegas_status vegas_reweight(const double *E, const double *O, int32_t K, int64_t
 /* Message of the last failed analysis call on this thread. */
 const char *vegas_analysis_last_error(void);
 
+/* ---------------------------------------------------------------- Ising model
+ * Ising systems with the spin-flip policy (Sec. II; the 2D Ising workloads of Sec. IV.B and
+ * IV.E): s = +-1 on a periodic square (dims 2) or simple cubic (dims 3) lattice of side L,
+ * E = -J sum_<ij> s_i s_j - h sum_i s_i (each bond once), site id i = x + L (y + L z).
+ * One MCS = every site of colour 0 ((x + y + z) even), then every site of colour 1, each
+ * with one flip attempt: dE = 2 s_i (J sum_j s_j + h); accepted iff dE <= 0 or
+ * u < exp(-dE / T), u = w 2^-32 with w the word (inst & 3) of Philox4x32-10(seed; i, t,
+ * inst >> 2, 0x80000), t the global MCS counter. Initial state: s_i = +1 iff bit 31 of word
+ * (inst & 3) of Philox(seed; i, 0xFFFFFFFF, inst >> 2, 0x90000) is set (or all +1).
+ * Device layout: 32 sites of one replica per 32-bit word (multi-spin coding along x, one
+ * array per colour); acceptance by integer thresholds computed on the host, so the result
+ * is the same bit for bit as the definition above. Replicas are independent instances with
+ * their own temperature and field.
+ */
+typedef struct vegas_ising vegas_ising;
+
+typedef struct {
+    int32_t dims;        /* 2 or 3 */
+    int32_t L;           /* side: a multiple of 64, L^dims < 2^31 */
+    double J;            /* exchange (finite) */
+    int32_t replicas;    /* a multiple of 4, at most 512 */
+    int32_t inst_base;   /* id of replica 0: a multiple of 4 */
+    uint64_t seed;       /* Philox key */
+    int32_t device;      /* CUDA device ordinal, -1 = current */
+    void *cuda_stream;   /* cudaStream_t, NULL = a stream of the library */
+    int32_t init_up;     /* 1: every spin +1; 0: the Philox initial state */
+    int32_t timing;      /* 1: time every sweep launch with CUDA events */
+} vegas_ising_options;
+
+void vegas_ising_default_options(vegas_ising_options *opt);
+vegas_status vegas_ising_create(const vegas_ising_options *opt, vegas_ising **out);
+/* T, h: [replicas][n_steps] (T > 0); records (E, M) after every MCS. Blocking. */
+vegas_status vegas_ising_run(vegas_ising *ctx, const double *T, const double *h, int32_t n_steps,
+                             int32_t mcs_per_step);
+/* History as [replicas][records][2] doubles (E, M); out == NULL: size query. */
+vegas_status vegas_ising_history(const vegas_ising *ctx, double *out, size_t capacity, size_t *n_written);
+/* Spins of one replica as L^dims int8 (+1 / -1) in site-id order. */
+vegas_status vegas_ising_get_spins(const vegas_ising *ctx, int32_t replica, int8_t *out);
+vegas_status vegas_ising_set_spins(vegas_ising *ctx, int32_t replica, const int8_t *in);
+/* n_instances, n_sites, records, mcs_done, kernel_launches, sweep_launches, sweep_ms,
+ * last_run_ms, device_bytes are filled; the other fields are 0. */
+vegas_status vegas_ising_stats(const vegas_ising *ctx, vegas_stats_t *out);
+const char *vegas_ising_last_error(const vegas_ising *ctx);
+void vegas_ising_destroy(vegas_ising *ctx);
+
 /* Counters and sizes of the context (valid also on a poisoned context). */
 vegas_status vegas_stats(const vegas_ctx *ctx, vegas_stats_t *out);
 

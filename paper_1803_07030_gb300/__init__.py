@@ -14,6 +14,7 @@ from .vegas import (  # noqa: F401
     POLICY_SMALL_STEP,
     POLICY_SPIN_FLIP,
     Context,
+    IsingContext,
     VegasError,
     load_library,
     reweight,

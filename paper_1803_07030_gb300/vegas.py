@@ -91,6 +91,21 @@ class vegas_stats_t(C.Structure):
     ]
 
 
+class vegas_ising_options(C.Structure):
+    _fields_ = [
+        ("dims", C.c_int32),
+        ("L", C.c_int32),
+        ("J", C.c_double),
+        ("replicas", C.c_int32),
+        ("inst_base", C.c_int32),
+        ("seed", C.c_uint64),
+        ("device", C.c_int32),
+        ("cuda_stream", P),
+        ("init_up", C.c_int32),
+        ("timing", C.c_int32),
+    ]
+
+
 # every function declared in include/vegas.h, with its ctypes signature
 SIGNATURES = {
     "vegas_default_options": (None, [P]),
@@ -116,6 +131,15 @@ SIGNATURES = {
     "vegas_reweight": (C.c_int, [P, P, C.c_int32, C.c_int64, C.c_int32, P, P, C.c_int32, C.c_int32, C.c_double, P,
                                  P, P, P]),
     "vegas_analysis_last_error": (C.c_char_p, []),
+    "vegas_ising_default_options": (None, [P]),
+    "vegas_ising_create": (C.c_int, [P, P]),
+    "vegas_ising_run": (C.c_int, [P, P, P, C.c_int32, C.c_int32]),
+    "vegas_ising_history": (C.c_int, [P, P, C.c_size_t, P]),
+    "vegas_ising_get_spins": (C.c_int, [P, C.c_int32, P]),
+    "vegas_ising_set_spins": (C.c_int, [P, C.c_int32, P]),
+    "vegas_ising_stats": (C.c_int, [P, P]),
+    "vegas_ising_last_error": (C.c_char_p, [P]),
+    "vegas_ising_destroy": (None, [P]),
 }
 
 AVG_FIELDS = ("e", "e_err", "m", "m_err", "c", "c_err", "chi", "chi_err", "u4", "u4_err", "v1", "v2", "tau_e",
@@ -467,6 +491,87 @@ class Context:
     def close(self) -> None:
         if self.ptr:
             vegas_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class IsingContext:
+    """Ising model (spin-flip policy) on a periodic square (dims 2) or cubic (dims 3) lattice,
+    replicas multi-spin coded on the GPU (see include/vegas.h)."""
+
+    def __init__(self, dims: int = 2, L: int = 64, J: float = 1.0, replicas: int = 32, seed: int = 1,
+                 inst_base: int = 0, device: int = -1, stream=None, init_up: bool = False, timing: bool = False):
+        lib = load_library()
+        o = vegas_ising_options()
+        lib.vegas_ising_default_options(C.byref(o))
+        o.dims, o.L, o.J, o.replicas, o.seed, o.inst_base, o.device = dims, L, J, replicas, seed, inst_base, device
+        o.cuda_stream = _current_stream() if stream == "torch" else stream
+        o.init_up = 1 if init_up else 0
+        o.timing = 1 if timing else 0
+        self.dims, self.L, self.replicas = dims, L, replicas
+        self.n_sites = L ** dims
+        self.ptr = None
+        ptr = P()
+        st = lib.vegas_ising_create(C.byref(o), C.byref(ptr))
+        if st != OK:
+            msg = lib.vegas_ising_last_error(None)
+            raise VegasError(st, msg.decode() if msg else "")
+        self.ptr = ptr.value
+
+    def _check(self, st):
+        if st != OK:
+            msg = load_library().vegas_ising_last_error(self.ptr)
+            raise VegasError(st, msg.decode() if msg else "")
+
+    def run(self, T, h, mcs: int) -> None:
+        T = np.asarray(T, dtype=np.float64)
+        T = T.reshape(1, 1) if T.ndim == 0 else (T[None, :] if T.ndim == 1 else T)
+        n_steps = T.shape[1]
+        T = np.ascontiguousarray(np.broadcast_to(T, (self.replicas, n_steps)))
+        hv = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64).reshape(-1, n_steps)
+                                                  if np.ndim(h) else np.full((1, n_steps), float(h)),
+                                                  (self.replicas, n_steps)))
+        self._check(load_library().vegas_ising_run(self.ptr, _ptr(T), _ptr(hv), n_steps, mcs))
+
+    def history(self) -> np.ndarray:
+        """[replicas, records, 2] = (E, M) after every MCS."""
+        lib = load_library()
+        n = C.c_size_t()
+        self._check(lib.vegas_ising_history(self.ptr, None, 0, C.byref(n)))
+        out = np.zeros(n.value)
+        if n.value:
+            self._check(lib.vegas_ising_history(self.ptr, _ptr(out), n.value, C.byref(n)))
+        return out.reshape(self.replicas, -1, 2)
+
+    def spins(self, replica: int) -> np.ndarray:
+        out = np.zeros(self.n_sites, dtype=np.int8)
+        self._check(load_library().vegas_ising_get_spins(self.ptr, replica, _ptr(out)))
+        return out
+
+    def set_spins(self, replica: int, spins) -> None:
+        s = np.ascontiguousarray(spins, dtype=np.int8)
+        self._check(load_library().vegas_ising_set_spins(self.ptr, replica, _ptr(s)))
+
+    def stats(self) -> dict:
+        s = vegas_stats_t()
+        self._check(load_library().vegas_ising_stats(self.ptr, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in vegas_stats_t._fields_}
+
+    def close(self) -> None:
+        if self.ptr:
+            load_library().vegas_ising_destroy(self.ptr)
             self.ptr = None
 
     def __enter__(self):

@@ -213,3 +213,11 @@ def test_analysis_without_a_device_is_an_error(lib):
     with pytest.raises(vb.VegasError) as e:
         vb.thermal_averages(np.ones((1, 40, 4)), 0, 4, 1.0, 1.0)
     assert e.value.status == vb.ECUDA
+
+
+def test_ising_options_rejected_before_the_device(lib):
+    for kw in ({"L": 96}, {"L": 0}, {"replicas": 6}, {"replicas": 1024}, {"inst_base": 2}, {"dims": 1},
+               {"J": float("nan")}, {"L": 65536}):
+        with pytest.raises(vb.VegasError) as e:
+            vb.IsingContext(**kw)
+        assert e.value.status == vb.EINVAL, kw
