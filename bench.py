@@ -487,6 +487,77 @@ def run_analysis(args):
     return 0
 
 
+ISING_PROFILE = os.path.join(ROOT, "profiles", "ising_pass_2d16384x32.txt")
+
+
+def run_ising(args):
+    """The Ising workload (spin flip, Sec. II; the 2D Ising systems of Sec. IV.B, IV.E): a
+    periodic 16384^2 square lattice, 32 replicas (temperatures 1.5 .. 3.5), multi-spin coded.
+    A step is one vegas_ising_run of --mcs MCS (default 20). The kernel is bound by integer
+    issue (Philox and the bit logic), not by HBM: the roofline is warp instructions per second
+    against the issue peak, 152 SMs x 4 schedulers x the median SM clock."""
+    import torch
+    import paper_1803_07030_gb300 as vg
+
+    vg.build()
+    torch.cuda.set_device(0)
+    L, R = 16384, 32
+    mcs = args.mcs if args.mcs != MCS else 20
+    T = np.linspace(1.5, 3.5, R)[:, None]
+    h = np.zeros_like(T)
+    stream = torch.cuda.current_stream()
+    with vg.IsingContext(2, L, replicas=R, seed=SEED, stream=int(stream.cuda_stream), timing=True) as c:
+        for _ in range(args.warmup):
+            c.run(T, h, mcs)
+        torch.cuda.synchronize()
+        st0 = c.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                c.run(T, h, mcs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        st1 = c.stats()
+        ms = e0.elapsed_time(e1)
+    attempts = L * L * R * mcs * args.steps
+    value = attempts / (ms / 1000.0)
+    sweeps = st1["sweep_launches"] - st0["sweep_launches"]
+    launch_ms = (st1["sweep_ms"] - st0["sweep_ms"]) / max(sweeps, 1)
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    peak = 152 * 4 * sm_mhz * 1e6 / 1e9  # G warp-instructions/s
+    inst = None
+    if os.path.exists(ISING_PROFILE):
+        for line in open(ISING_PROFILE):
+            if line.startswith("warp_instructions_per_attempt:"):
+                inst = float(line.split(":", 1)[1])
+    per_launch = L * L * R // 2
+    achieved = None if inst is None else inst * per_launch / (launch_ms / 1000.0) / 1e9
+    from oracle import ising_run
+
+    t0 = time.perf_counter()
+    ising_run(2, 256, 1.0, np.full((4, 1), 2.27), np.zeros((4, 1)), 10, seed=SEED)
+    cpu_dt = time.perf_counter() - t0
+    line = {
+        "metric": "Ising spin-flip attempts/s on 1 GB300", "value": value, "unit": "attempts/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "2D Ising, periodic 16384^2, 32 replicas (T 1.5..3.5), J = 1, h = 0, "
+                               f"{mcs} MCS per step, multi-spin coded", "l2": "inputs larger than L2 (1 GiB)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G warp-instructions/s",
+                     "frac": None if achieved is None else achieved / peak,
+                     "peak_source": "152 SMs x 4 issue slots x median SM clock (derived)",
+                     "kernel": "ising_pass_kernel<2>", "warp_instructions_per_attempt": inst,
+                     "attempts_per_launch": per_launch, "avg_launch_ms": launch_ms},
+        "cpu_baseline": {"value": 256 * 256 * 4 * 10 / cpu_dt, "unit": "attempts/s", "cores": 1, "kind": "oracle",
+                         "sample": "256^2 x 4 replicas x 10 MCS"},
+        "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"], "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     global L_SIDE
     ap = argparse.ArgumentParser()
@@ -506,6 +577,7 @@ def main():
                     help="sweep variant: -1 automatic (timed on the first run), 0 per colour class, 1 resident, "
                          "2 cooperative; profiling commands fix it because ncu distorts the automatic timing")
     ap.add_argument("--analysis", action="store_true", help="time the history analysis instead of the sweep")
+    ap.add_argument("--ising", action="store_true", help="time the multi-spin-coded Ising workload")
     ap.add_argument("--type-stats", action="store_true", help="secondary workloads: record per-type magnetization")
     ap.add_argument("--snapshots", action="store_true", help="secondary workloads: keep the final state of every step")
     ap.add_argument("--quick", action="store_true",
@@ -516,6 +588,8 @@ def main():
         return run_reference(args)
     if args.analysis:
         return run_analysis(args)
+    if args.ising:
+        return run_ising(args)
     if args.workload != "sg256x32":
         return run_workload(args)
     return run_ours(args)
