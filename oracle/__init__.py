@@ -9,6 +9,7 @@ from .oracle import (  # noqa: F401
     ADAPTIVE,
     GAUSSIAN,
     HINZKE_NOWAK,
+    QISING,
     RANDOM,
     SMALL_STEP,
     SPIN_FLIP,

@@ -42,7 +42,7 @@ class _Sample(C.Structure):
         ("pad2_", C.c_int32),
     ]
 
-RANDOM, SPIN_FLIP, SMALL_STEP, GAUSSIAN, HINZKE_NOWAK, ADAPTIVE = range(6)
+RANDOM, SPIN_FLIP, SMALL_STEP, GAUSSIAN, HINZKE_NOWAK, ADAPTIVE, QISING = range(7)
 
 
 class _Extra(C.Structure):

@@ -49,6 +49,12 @@
  *                   0x08000|k
  *   4 Hinzke-Nowak  one of spin flip, random, small step with probability 1/3 each, chosen by
  *                   the uniform of purpose 0x0C000 (Hinzke & Nowak 1999 combinational move)
+ *   6 qIsing        mixed-spin Ising (Sec. II): S = (0, 0, m) with m in {-s, -s + 1, ..., s}
+ *                   (s = the spin norm, 2 s a positive integer); the trial m' is uniform over
+ *                   the 2 s other values: k = floor(u * 2 s) from the uniform of purpose
+ *                   0x00000, m' = k - s if k < index(m) else k + 1 - s. Such sites start at a
+ *                   uniform value (the init uniform u, index floor(u (2 s + 1))) and are never
+ *                   renormalised.
  *   5 adaptive      Gaussian whose width sigma (one per instance) is rescaled after each MCS by
  *                   0.5 / max(1 - R, 0.01), R the MCS's acceptance rate, clamped to
  *                   [1e-4, 100], during the first fifth of every temperature/field step only;
@@ -81,7 +87,8 @@ typedef struct {
     int32_t pad2_;
 } vo_sample;
 
-enum { VO_RANDOM = 0, VO_FLIP = 1, VO_SMALL_STEP = 2, VO_GAUSSIAN = 3, VO_HINZKE_NOWAK = 4, VO_ADAPTIVE = 5 };
+enum { VO_RANDOM = 0, VO_FLIP = 1, VO_SMALL_STEP = 2, VO_GAUSSIAN = 3, VO_HINZKE_NOWAK = 4, VO_ADAPTIVE = 5,
+       VO_QISING = 6 };
 
 enum { VO_ERR_NAN = 1, VO_ERR_SPHERE = 2 };
 
@@ -361,8 +368,16 @@ double vo_delta_e(const vo_sample *s, const double *S, int32_t i, const double S
 }
 
 /* S_i <- s_i * S_i / |S_i|, with f = s_i / sqrt((x^2 + y^2) + z^2). */
+/* 1 when site i follows the qIsing policy (discrete values along z). */
+static int is_qising(const vo_sample *s, int32_t i) {
+    if (!s->type_policy) return 0;
+    const int32_t ty = s->type ? s->type[i] : 0;
+    return ty >= 0 && ty < s->n_policy_types && s->type_policy[ty] == VO_QISING;
+}
+
 void vo_renormalise(const vo_sample *s, double *S) {
     for (int32_t i = 0; i < s->n; ++i) {
+        if (is_qising(s, i)) continue;  /* discrete values keep their length */
         double *v = S + 3 * (int64_t)i;
         const double n2 = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
         const double f = norm_of(s, i) / sqrt(n2);
@@ -376,9 +391,18 @@ void vo_renormalise(const vo_sample *s, double *S) {
 int vo_init_spins(const vo_sample *s, uint64_t seed, int32_t inst, double *S) {
     int err = 0;
     for (int32_t i = 0; i < s->n; ++i) {
+        const double sn = norm_of(s, i);
+        if (is_qising(s, i)) {  /* a uniform value of {-s, ..., s} along z */
+            const int32_t nv = (int32_t)(2.0 * sn) + 1;
+            int32_t k = (int32_t)(vo_uniform(seed, (uint32_t)i, 0xFFFFFFFFu, (uint32_t)inst, 0x20000u) * (double)nv);
+            if (k >= nv) k = nv - 1;
+            S[3 * (int64_t)i] = 0.0;
+            S[3 * (int64_t)i + 1] = 0.0;
+            S[3 * (int64_t)i + 2] = (double)k - sn;
+            continue;
+        }
         double u[3];
         if (vo_sphere(seed, (uint32_t)i, 0xFFFFFFFFu, (uint32_t)inst, 0x20000u, u) < 0) err |= VO_ERR_SPHERE;
-        const double sn = norm_of(s, i);
         S[3 * (int64_t)i] = sn * u[0];
         S[3 * (int64_t)i + 1] = sn * u[1];
         S[3 * (int64_t)i + 2] = sn * u[2];
@@ -490,10 +514,24 @@ int vo_trial(const vo_sample *s, const double *S, int32_t i, uint64_t seed, uint
 static int attempt(vo_job *jb, int32_t i, uint32_t c0, uint32_t t, double beta, double B, uint32_t p_trial,
                    uint32_t p_accept) {
     const vo_sample *s = jb->s;
-    double u[3];
-    trial_of(jb, i, c0, t, p_trial, u);
     const double sn = norm_of(s, i);
-    const double Sp[3] = {sn * u[0], sn * u[1], sn * u[2]};
+    double Sp[3];
+    if (is_qising(s, i)) {  /* another of the 2 s + 1 values along z, uniformly */
+        const int32_t n2 = (int32_t)(2.0 * sn);
+        const int32_t idx = (int32_t)(jb->S[3 * (int64_t)i + 2] + sn + 0.5);
+        int32_t k = (int32_t)(vo_uniform(jb->seed, c0, t, (uint32_t)jb->inst, p_trial) * (double)n2);
+        if (k >= n2) k = n2 - 1;
+        if (k >= idx) k += 1;
+        Sp[0] = 0.0;
+        Sp[1] = 0.0;
+        Sp[2] = (double)k - sn;
+    } else {
+        double u[3];
+        trial_of(jb, i, c0, t, p_trial, u);
+        Sp[0] = sn * u[0];
+        Sp[1] = sn * u[1];
+        Sp[2] = sn * u[2];
+    }
     const double dE = vo_delta_e(s, jb->S, i, Sp, B);
     int acc;
     if (dE <= 0.0) {

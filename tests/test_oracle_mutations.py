@@ -41,8 +41,8 @@ MUTANTS = [
      [pins.test_philox_matches_triton_interpreter]),
     ("philox output words transposed", "c[1] = lo1;\n    c[2] = n2;\n    c[3] = lo0;",
      "c[1] = lo0;\n    c[2] = n2;\n    c[3] = lo1;", [pins.test_philox_matches_triton_interpreter]),
-    ("spin norm ignored in trial", "const double Sp[3] = {sn * u[0], sn * u[1], sn * u[2]};",
-     "const double Sp[3] = {u[0], u[1], u[2]};", [pins.test_langevin_law_spin_norm]),
+    ("spin norm ignored in trial", "        Sp[0] = sn * u[0];\n        Sp[1] = sn * u[1];\n        Sp[2] = sn * u[2];",
+     "        Sp[0] = u[0];\n        Sp[1] = u[1];\n        Sp[2] = u[2];", [pins.test_langevin_law_spin_norm]),
     ("colouring not greedy", "while (c < cap && mark[c] == i) ++c;", "while (c < cap && mark[c] == i) c += 2;",
      [lambda: pins.test_greedy_colouring_matches_networkx(lambda: pins.sc_periodic(5))]),
     ("exchange sign", "ex += s->J[e] *", "ex -= s->J[e] *", [lambda: pins.test_three_spin_ring(-1.0)]),
@@ -69,6 +69,12 @@ MUTANTS = [
      "        if (jb->snaps) memcpy(jb->snaps + (int64_t)st * n * 3, jb->S, sizeof(double) * 3 * (size_t)n);\n"
      "        vo_renormalise(s, jb->S);\n        if (0) memcpy(",
      [outs.test_snapshots_are_the_final_states_per_step]),
+    ("qIsing proposal skips no value", "        if (k >= idx) k += 1;\n", "",
+     [lambda: pol.test_qising_free_spins_boltzmann(1.0, 0.6, 0.8)]),
+    ("qIsing sites renormalised", "        if (is_qising(s, i)) continue;  /* discrete values keep their length */", "",
+     [pol.test_qising_values_stay_discrete_and_start_uniform, lambda: pol.test_qising_free_spins_boltzmann(1.5, 0.4, -0.3)]),
+    ("qIsing start misses the top value", "0x20000u) * (double)nv);", "0x20000u) * (double)(nv - 1));",
+     [pol.test_qising_values_stay_discrete_and_start_uniform]),
     ("Ising field sign", "const double dE = 2.0 * si * (J * (double)sum + hh);",
      "const double dE = 2.0 * si * (J * (double)sum - hh);", [ising.test_paramagnet_tanh_law]),
     ("Ising bonds counted twice", "for (int d = 0; d < dims; ++d) bsum += (int64_t)s[i] * s[nb[2 * d + 1]];",

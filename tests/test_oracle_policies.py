@@ -284,3 +284,59 @@ def test_per_type_policies_apply_per_type():
     assert np.all(np.abs(np.abs(cosang[shell]) - 1.0) < 1e-12)
     assert np.mean(np.abs(cosang[~shell]) < 0.99) > 0.5  # the core moved
     assert np.any(cosang[shell] < 0) and np.any(cosang[shell] > 0)
+
+
+# --------------------------------------------------------------------------- qIsing (mixed spin Ising)
+
+def _qising_free(n, s, B=0.0, k=0.0):
+    fs = free_spins(n, spin_norm=s, k_uni=k, e_uni=(0.0, 0.0, 1.0))
+    return fs.with_policy([oracle.QISING], [0.0])
+
+
+def _brillouin_like(s, beta, B, k):
+    m = np.arange(-s, s + 0.5, 1.0)
+    w = np.exp(beta * (B * m + k * m * m))
+    w /= w.sum()
+    return m, w
+
+
+def test_qising_values_stay_discrete_and_start_uniform():
+    s = 1.5
+    fs = _qising_free(6000, s)
+    S0 = oracle.init_spins(fs, 31, 0)
+    assert np.all(S0[:, :2] == 0.0)
+    vals, counts = np.unique(S0[:, 2], return_counts=True)
+    assert np.array_equal(vals, [-1.5, -0.5, 0.5, 1.5])
+    assert stats.chisquare(counts).pvalue > 1e-3
+    r = oracle.run(fs, [[1.0, 0.7]], [[0.3, -0.2]], 20, seed=31)
+    S = r["spins"][0]
+    assert np.all(S[:, :2] == 0.0) and set(np.unique(S[:, 2])) == {-1.5, -0.5, 0.5, 1.5}
+
+
+@pytest.mark.parametrize("s,B,k", [(1.0, 0.6, 0.8), (1.5, 0.4, -0.3), (0.5, 1.0, 0.0)])
+def test_qising_free_spins_boltzmann(s, B, k):
+    n, T = 4000, 1.0
+    fs = _qising_free(n, s, B, k)
+    mcs = 300
+    r = oracle.run(fs, [[T]], [[B]], mcs, seed=32)
+    m, w = _brillouin_like(s, 1.0 / T, B, k)
+    mean_m = (w * m).sum()
+    got, se = binned(r["history"][0, :, 3] / n)
+    assert abs(got - mean_m) < 4 * se + 1e-4, (got, se, mean_m)
+    e_exact = -(B * mean_m + k * (w * m * m).sum())
+    ge, see = binned(r["history"][0, :, 0] / n)
+    assert abs(ge - e_exact) < 4 * see + 1e-4, (ge, see, e_exact)
+    # detailed balance: the distribution of m over the final states
+    obs = np.array([(r["spins"][0][:, 2] == v).sum() for v in m])
+    assert stats.chisquare(obs, n * w).pvalue > 1e-4
+
+
+def test_qising_half_spin_chain_is_the_ising_chain():
+    N, T, J = 2000, 0.6, 1.0
+    ch = chain_open(N, J=J)
+    ch.spin_norm = np.full(N, 0.5)
+    ch.with_policy([oracle.QISING], [0.0])
+    r = oracle.run(ch, [[T]], [[0.0]], 400, seed=33)
+    m, se = binned(r["history"][0, :, 0])
+    U = -(N - 1) * (J / 4) * math.tanh(J / (4 * T))
+    assert abs(m - U) < 4 * se + 1e-6, (m, se, U)
