@@ -23,6 +23,10 @@
  *                              sigma = param
  *   VEGAS_POLICY_HINZKE_NOWAK  spin flip, random or small step (cap half-angle = param),
  *                              each with probability 1/3 (Hinzke & Nowak's combination)
+ *   VEGAS_POLICY_QISING        mixed-spin Ising: S_i = (0, 0, m), m in {-s_i, -s_i + 1, ..., s_i}
+ *                              (2 s_i a whole number from 1 to 64); the trial is one of the 2 s_i
+ *                              other values, uniformly; such sites start at a uniform value and
+ *                              are not renormalised (their length is |m|)
  *   VEGAS_POLICY_ADAPTIVE      Gaussian with one width sigma per instance (starting at the
  *                              param of the first adaptive type); after each MCS of the
  *                              first fifth of every temperature/field step, sigma <-
@@ -83,7 +87,8 @@ typedef enum {
     VEGAS_POLICY_SMALL_STEP = 2,
     VEGAS_POLICY_GAUSSIAN = 3,
     VEGAS_POLICY_HINZKE_NOWAK = 4,
-    VEGAS_POLICY_ADAPTIVE = 5
+    VEGAS_POLICY_ADAPTIVE = 5,
+    VEGAS_POLICY_QISING = 6
 } vegas_policy;
 
 typedef struct {
@@ -111,7 +116,7 @@ typedef struct {
                                    lie in [0, n_policy_types). */
     const double *type_param;   /* [n_policy_types]: cap half-angle theta in (0, pi] radians
                                    (small step, Hinzke-Nowak), width sigma > 0 (Gaussian,
-                                   adaptive), ignored (random, spin flip) */
+                                   adaptive), ignored (random, spin flip, qIsing) */
 } vegas_sample;
 
 typedef struct {

@@ -10,6 +10,7 @@ from .vegas import (  # noqa: F401
     POLICY_ADAPTIVE,
     POLICY_GAUSSIAN,
     POLICY_HINZKE_NOWAK,
+    POLICY_QISING,
     POLICY_RANDOM,
     POLICY_SMALL_STEP,
     POLICY_SPIN_FLIP,

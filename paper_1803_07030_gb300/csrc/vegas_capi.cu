@@ -70,6 +70,7 @@ struct vegas_ctx {
     size_t acc_hist_cap = 0;
     PolicySite *d_pol = nullptr;      // FP64 contexts
     PolicySite32 *d_pol32 = nullptr;  // FP32 contexts
+    int32_t *d_qis = nullptr;         // [global site] 1 for qIsing sites, or NULL
     double *d_sigma = nullptr;
     int32_t *d_adapt_n = nullptr;
     bool any_adaptive = false;
@@ -149,7 +150,7 @@ void free_all(vegas_ctx *c) {
     void *bufs[] = {c->d_spins, c->d_edges, c->d_p0, c->d_p1, c->d_pk, c->d_rowptr, c->d_slot_base, c->d_orig,
                     c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog,
                     c->d_insts, c->d_cstart, c->d_queue, c->d_bar, c->d_coop_partial, c->d_acc, c->d_acc_hist,
-                    c->d_pol, c->d_pol32, c->d_sigma, c->d_adapt_n, c->d_type_hist, c->d_snap, c->d_segs};
+                    c->d_pol, c->d_pol32, c->d_qis, c->d_sigma, c->d_adapt_n, c->d_type_hist, c->d_snap, c->d_segs};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -205,7 +206,7 @@ void enqueue_coop(vegas_ctx *c, cudaStream_t st, int32_t n) {
 
 // Renormalisation at the end of a step, then (option snapshots) the copy of the final state.
 void enqueue_renorm(vegas_ctx *c, cudaStream_t st) {
-    RenormArgs ra{c->d_spins, c->d_norm, c->n_sites * c->R, c->log2R};
+    RenormArgs ra{c->d_spins, c->d_norm, c->n_sites * c->R, c->log2R, c->d_qis};
     const int grid = (int)std::min<int64_t>((ra.n_work + 255) / 256, (int64_t)c->sm_count * 8);
     if (c->precision == 64)
         launch_renorm64(ra, grid, st);
@@ -412,6 +413,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     }
     std::vector<PolicySite> h_pol(any_policy && p64 ? (size_t)n_sites : 0, PolicySite{0.0, kPolRandom, 0});
     std::vector<PolicySite32> h_pol32(any_policy && !p64 ? (size_t)n_sites : 0, PolicySite32{0.f, kPolRandom});
+    std::vector<int32_t> h_qis;  // filled only when some site is qIsing
     std::vector<int32_t> h_orig((size_t)n_sites);
     std::vector<int64_t> h_rowptr((size_t)n_sites + 1);
     std::vector<double> h_norm((size_t)n_sites);
@@ -464,6 +466,10 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
                     h_pol[(size_t)(site_off + g)] = PolicySite{par, code, 0};
                 else
                     h_pol32[(size_t)(site_off + g)] = PolicySite32{(float)par, code};
+                if (code == kPolQIsing) {
+                    if (h_qis.empty()) h_qis.assign((size_t)n_sites, 0);
+                    h_qis[(size_t)(site_off + g)] = 1;
+                }
             }
         si.u = SiteParams64{l.field_axis[0], l.field_axis[1], l.field_axis[2], l.spin_norm[0],
                             l.e_uni[0],      l.e_uni[1],      l.e_uni[2],      l.k_uni[0], l.k_cub[0]};
@@ -540,6 +546,10 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         H2D(c->d_p0, p64 ? (const void *)h_p0d.data() : (const void *)h_p0f.data(), pv * (size_t)n_sites);
         H2D(c->d_p1, p64 ? (const void *)h_p1d.data() : (const void *)h_p1f.data(), pv * (size_t)n_sites);
         H2D(c->d_pk, p64 ? (const void *)h_pkd.data() : (const void *)h_pkf.data(), ps * (size_t)n_sites);
+    }
+    if (!h_qis.empty()) {
+        DALLOC(c->d_qis, sizeof(int32_t) * (size_t)n_sites);
+        H2D(c->d_qis, h_qis.data(), sizeof(int32_t) * (size_t)n_sites);
     }
     if (any_policy && p64) {
         DALLOC(c->d_pol, sizeof(PolicySite) * (size_t)n_sites);
@@ -807,7 +817,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
             H2D(d_given, l.init_spins.data(), sizeof(double) * l.init_spins.size());
         }
         InitArgs ia{c->d_spins, c->d_orig, c->d_norm, d_given, c->d_err, o.seed, si.site_off, si.site_off + si.n,
-                    o.inst_base + s * R, c->log2R};
+                    o.inst_base + s * R, c->log2R, c->d_qis};
         const int64_t work = (int64_t)si.n * R;
         const int grid = (int)std::min<int64_t>((work + 255) / 256, (int64_t)c->sm_count * 8);
         if (p64)

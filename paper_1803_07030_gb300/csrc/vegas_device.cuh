@@ -152,6 +152,13 @@ constexpr int kPolCapSphere = 6;  // internal: the random third of Hinzke-Nowak,
 __device__ __forceinline__ float3 policy_trial32(const PolicySite32 ps, float sigma, const float4 Si, float sn,
                                                  uint4 rw) {
     int code = ps.code;
+    if (code == kPolQIsing) {  // another of the 2 s + 1 values along z, uniformly
+        const int n2 = (int)(2.0f * sn);
+        const int idx = (int)(Si.z + sn + 0.5f);
+        int k = min((int)(u23(rw.x) * (float)n2), n2 - 1);
+        if (k >= idx) k += 1;
+        return make_float3(0.f, 0.f, (float)k - sn);
+    }
     if (code == kPolHinzkeNowak) {
         // a uniform point on the sphere is the cap of height 2 around any axis, so the random
         // and small-step thirds share one code path (no divergence between them in a warp)

@@ -27,7 +27,7 @@ constexpr uint32_t kInitT = 0xFFFFFFFFu;
 
 // Update policies (vegas_policy in the C-ABI).
 constexpr int32_t kPolRandom = 0, kPolFlip = 1, kPolSmallStep = 2, kPolGaussian = 3, kPolHinzkeNowak = 4,
-                  kPolAdaptive = 5;
+                  kPolAdaptive = 5, kPolQIsing = 6;
 
 // Error bits set by kernels in the device error word.
 constexpr uint32_t kErrNaN = 1u;
@@ -175,6 +175,7 @@ struct RenormArgs {
     const double *norm;      // [global site] spin norm s_i
     int64_t n_work;          // global sites * R
     int32_t log2R;
+    const int32_t *qis;      // [global site] 1 for qIsing sites (left as they are), or NULL
 };
 
 struct InitArgs {
@@ -187,6 +188,7 @@ struct InitArgs {
     int32_t g_begin, g_end;  // global sites of the sample
     int32_t inst0;           // instance id of replica 0
     int32_t log2R;
+    const int32_t *qis;      // [global site] 1 for qIsing sites (a uniform value along z), or NULL
 };
 
 // One instance of the resident sweep: a sample's sites and one of its replicas.

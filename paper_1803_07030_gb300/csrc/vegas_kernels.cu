@@ -236,10 +236,25 @@ __global__ void __launch_bounds__(kThreads) pass64_kernel(const PassArgs a) {
         hy = da(hy, dm(B, ny));
         hz = da(hz, dm(B, nz));
         // trial: uniform on the sphere of radius s_i, or the site's update policy
-        const double3 u = a.pol ? policy_trial64(a.pol[g], rs->sigma ? rs->sigma[a.inst_local0 + r] : 0.0, Si, sn, orig,
-                                                 t, inst, k0, k1, a.err)
-                                : sphere64(orig, t, inst, kPurposeTrial64, k0, k1, a.err);
-        const double px = dm(sn, u.x), py = dm(sn, u.y), pz = dm(sn, u.z);
+        double px, py, pz;
+        if (a.pol && a.pol[g].code == kPolQIsing) {  // another of the 2 s + 1 values along z
+            const int n2 = (int)dm(2.0, sn);
+            const int idx = (int)da(da(Si.z, sn), 0.5);
+            const uint4 w = philox10(make_uint4(orig, t, inst, kPurposeTrial64), k0, k1);
+            int k = (int)dm(u53(w.x, w.y), (double)n2);
+            if (k >= n2) k = n2 - 1;
+            if (k >= idx) k += 1;
+            px = 0.0;
+            py = 0.0;
+            pz = ds((double)k, sn);
+        } else {
+            const double3 u = a.pol ? policy_trial64(a.pol[g], rs->sigma ? rs->sigma[a.inst_local0 + r] : 0.0, Si, sn,
+                                                     orig, t, inst, k0, k1, a.err)
+                                    : sphere64(orig, t, inst, kPurposeTrial64, k0, k1, a.err);
+            px = dm(sn, u.x);
+            py = dm(sn, u.y);
+            pz = dm(sn, u.z);
+        }
         // energy change (Eq. 1-3) in a fixed order
         const double dx = ds(px, Si.x), dy = ds(py, Si.y), dz = ds(pz, Si.z);
         const double dEex = -da(da(dm(dx, hx), dm(dy, hy)), dm(dz, hz));
@@ -700,6 +715,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const ReduceArgs a) {
 __global__ void renorm64_kernel(const RenormArgs a) {
     double4_32a *S = (double4_32a *)a.spins;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < a.n_work; w += (int64_t)gridDim.x * blockDim.x) {
+        if (a.qis && a.qis[w >> a.log2R]) continue;  // discrete values keep their length
         const double4_32a v = S[w];
         const double n2 = da(da(dm(v.x, v.x), dm(v.y, v.y)), dm(v.z, v.z));
         const double f = __ddiv_rn(a.norm[w >> a.log2R], __dsqrt_rn(n2));
@@ -710,6 +726,7 @@ __global__ void renorm64_kernel(const RenormArgs a) {
 __global__ void renorm32_kernel(const RenormArgs a) {
     float4 *S = (float4 *)a.spins;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < a.n_work; w += (int64_t)gridDim.x * blockDim.x) {
+        if (a.qis && a.qis[w >> a.log2R]) continue;  // discrete values keep their length
         const float4 v = S[w];
         const double x = v.x, y = v.y, z = v.z;
         const double f = a.norm[w >> a.log2R] / sqrt(x * x + y * y + z * z);
@@ -735,6 +752,15 @@ __global__ void init_kernel(const InitArgs a) {
             x = p[0];
             y = p[1];
             z = p[2];
+        } else if (a.qis && a.qis[g]) {  // qIsing: a uniform value of {-s, ..., s} along z
+            const double s = a.norm[g];
+            const int nv = (int)dm(2.0, s) + 1;
+            const uint4 wq = philox10(make_uint4((uint32_t)a.orig[g], kInitT, (uint32_t)(a.inst0 + r), kPurposeInit), k0, k1);
+            int k = (int)dm(u53(wq.x, wq.y), (double)nv);
+            if (k >= nv) k = nv - 1;
+            x = 0.0;
+            y = 0.0;
+            z = ds((double)k, s);
         } else {
             const double s = a.norm[g];
             const double3 u = sphere64((uint32_t)a.orig[g], kInitT, (uint32_t)(a.inst0 + r), kPurposeInit, k0, k1, a.err);

@@ -290,7 +290,7 @@ bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err, bool 
         for (int32_t q = 0; q < nt; ++q) {
             const int32_t code = s.type_policy[q];
             const double v = s.type_param[q];
-            if (code < kPolRandom || code > kPolAdaptive) { err = at("unknown update policy for type", q); return false; }
+            if (code < kPolRandom || code > kPolQIsing) { err = at("unknown update policy for type", q); return false; }
             if ((code == kPolSmallStep || code == kPolHinzkeNowak) && !(v > 0.0 && v <= 3.141592653589793))
                 { err = at("cap half-angle outside (0, pi] for type", q); return false; }
             if ((code == kPolGaussian || code == kPolAdaptive) && !(v > 0.0 && std::isfinite(v)))
@@ -306,6 +306,13 @@ bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err, bool 
         for (int32_t i = 0; i < n; ++i) {
             const int32_t ty = s.type ? s.type[i] : 0;
             if (ty < 0 || ty >= nt) { err = at("site type outside the policy table at site", i); return false; }
+            if (s.type_policy[ty] == kPolQIsing) {  // 2 s must be a whole number of values, 1 .. 64
+                const double two_s = 2.0 * (s.spin_norm ? s.spin_norm[i] : 1.0);
+                if (two_s != std::floor(two_s) || two_s < 1.0 || two_s > 64.0) {
+                    err = at("qIsing site needs a spin norm in {1/2, 1, ..., 32} at site", i);
+                    return false;
+                }
+            }
         }
         if (any) {
             L.policy.resize((size_t)n);

@@ -43,7 +43,8 @@ class vegas_sample(C.Structure):
     ]
 
 # update policies (vegas_policy)
-POLICY_RANDOM, POLICY_SPIN_FLIP, POLICY_SMALL_STEP, POLICY_GAUSSIAN, POLICY_HINZKE_NOWAK, POLICY_ADAPTIVE = range(6)
+(POLICY_RANDOM, POLICY_SPIN_FLIP, POLICY_SMALL_STEP, POLICY_GAUSSIAN, POLICY_HINZKE_NOWAK, POLICY_ADAPTIVE,
+ POLICY_QISING) = range(7)
 
 
 class vegas_options(C.Structure):

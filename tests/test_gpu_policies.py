@@ -288,3 +288,70 @@ def test_replica_batched_policy_kernel_equals_direct_kernel():
         assert np.array_equal(a.adaptive_width(), b.adaptive_width())
         for i in (0, 13, 31):
             assert np.array_equal(a.spins(i), b.spins(i)), i
+
+
+# --------------------------------------------------------------------------- qIsing
+
+def _mixed_spin_lattice(L=6, seed=4):
+    """Ferrimagnet-like sc lattice: sublattice A spin 1/2, sublattice B spin 1 (both qIsing),
+    a few random Heisenberg sites of norm 1; field and crystal field along z."""
+    s = sc_periodic(L, J=-1.0, k_uni=0.4)
+    idx = np.arange(s.n_sites)
+    x, y, z = idx % L, (idx // L) % L, idx // (L * L)
+    s.type = ((x + y + z) % 2).astype(np.int32)
+    rng = np.random.default_rng(seed)
+    s.type[rng.choice(s.n_sites, 10, replace=False)] = 2
+    s.spin_norm = np.where(s.type == 0, 0.5, 1.0)
+    return s.with_policy([oracle.QISING, oracle.QISING, oracle.RANDOM], [0.0, 0.0, 0.0])
+
+
+def test_fp64_qising_bitwise():
+    s = _mixed_spin_lattice()
+    T = np.array([[1.2, 0.5], [2.0, 0.8]])
+    B = np.array([[0.3, -0.2], [0.0, 0.5]])
+    with ctx([s], precision=64, replicas=2, seed=41, accept_log_mcs=6) as c:
+        c.run(T, B, 6)
+        ref = oracle.run(s, T, B, 6, seed=41, log_mcs=6, n_threads=2)
+        assert first_divergence(c.accept_log().reshape(6, 2, -1), ref["accept_log"].transpose(1, 0, 2)) is None
+        for r in range(2):
+            assert first_divergence(c.spins(r), ref["spins"][r]) is None, r
+        assert np.array_equal(c.accept_history(), ref["accepted"])
+        S = c.spins(0)
+        q = s.type < 2
+        assert np.all(S[q, :2] == 0.0) and np.all(np.isin(S[q, 2], [-1.0, -0.5, 0.0, 0.5, 1.0]))
+
+
+@pytest.mark.parametrize("sn,B,k", [(1.0, 0.6, 0.8), (1.5, 0.4, -0.3)])
+def test_fp32_qising_free_spins_boltzmann(sn, B, k):
+    n, T, mcs = 8000, 1.0, 300
+    fs = free_spins(n, spin_norm=sn, k_uni=k, e_uni=(0.0, 0.0, 1.0)).with_policy([oracle.QISING], [0.0])
+    with ctx([fs], precision=32, seed=42) as c:
+        c.run([[T]], [[B]], mcs)
+        H = c.history()[0]
+        S = c.spins(0)
+    m = np.arange(-sn, sn + 0.5, 1.0)
+    w = np.exp((B * m + k * m * m) / T)
+    w /= w.sum()
+    got, se = binned(H[:, 3] / n)
+    assert abs(got - (w * m).sum()) < 4 * se + 1e-4, (got, se)
+    assert np.all(S[:, :2] == 0.0) and np.all(np.isin(S[:, 2], m))
+
+
+def test_qising_replica_batched_kernel_equals_direct_kernel():
+    s = _mixed_spin_lattice(L=16, seed=5)
+    T = np.linspace(0.4, 2.4, 32)[:, None]
+    B = np.full_like(T, 0.2)
+    with ctx([s], replicas=32, seed=43, variant=0) as a, \
+            ctx([s], replicas=32, seed=43, variant=0, pipeline_depth=1) as b:
+        a.run(T, B, 6)
+        b.run(T, B, 6)
+        assert np.array_equal(a.accept_history(), b.accept_history())
+        for i in (0, 17, 31):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+
+
+def test_qising_needs_half_integer_norms():
+    s = free_spins(10, spin_norm=0.7).with_policy([oracle.QISING], [0.0])
+    with pytest.raises(vg.VegasError) as e:
+        ctx([s])
+    assert "qIsing" in str(e.value)
