@@ -573,8 +573,8 @@ def main():
     ap.add_argument("--policy", default="",
                     help="update policy per site type, e.g. 'adaptive' or 'random,hn:0.26' (policy[:param], one "
                          "per type; names: " + ", ".join(POLICY_CODES) + "); the line then reports that path")
-    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2],
-                    help="sweep variant: -1 automatic (timed on the first run), 0 per colour class, 1 resident, "
+    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+                    help="sweep variant: -1 automatic (timed on the first run), 0 per colour class, 1 resident, 3 cluster, "
                          "2 cooperative; profiling commands fix it because ncu distorts the automatic timing")
     ap.add_argument("--analysis", action="store_true", help="time the history analysis instead of the sweep")
     ap.add_argument("--ising", action="store_true", help="time the multi-spin-coded Ising workload")

@@ -131,7 +131,10 @@ typedef struct {
                                class, 1 resident: one persistent launch per step, a block per
                                instance (FP32), 2 cooperative: one launch per step, all blocks
                                sweep one sample class by class (FP32, one sample, no adaptive
-                               policy). Default -1. */
+                               policy), 3 cluster: one persistent launch per step, a thread-
+                               block cluster of 2 .. 16 blocks per instance, the blocks meeting at
+                               the hardware cluster barrier between colour classes (FP32).
+                               Default -1. */
     int32_t accept_log_mcs; /* > 0: keep the accept/reject bit of every attempt of the
                                first accept_log_mcs MCS (debugging and parity). Default 0. */
     int32_t timing;         /* 1: time every sweep launch with CUDA events. Default 0. */

@@ -87,7 +87,10 @@ struct vegas_ctx {
     int res_threads = 256, res_grid = 1;
     bool res_eligible = false, tuned = false;
     int32_t max_instance_sites = 0;
-    double tune_ms[3] = {0.0, 0.0, 0.0};  // per-MCS time of each sweep when tuned
+    double tune_ms[4] = {0.0, 0.0, 0.0, 0.0};  // per-MCS time of each sweep when tuned
+    // cluster sweep: clusters of cluster_cs blocks, cluster_n of them at once
+    bool cluster_eligible = false;
+    int cluster_cs = 0, cluster_n = 0, cluster_threads = 256;
     // cooperative sweep
     bool coop_eligible = false;
     CoopArgs coop{};
@@ -204,6 +207,15 @@ void enqueue_coop(vegas_ctx *c, cudaStream_t st, int32_t n) {
     launch_advance(c->d_run, n, st);
 }
 
+// One cluster-sweep launch for n MCS of the current step; the run state advances afterwards.
+void enqueue_cluster(vegas_ctx *c, cudaStream_t st, int32_t n) {
+    cudaMemsetAsync(c->d_queue, 0, sizeof(uint32_t), st);
+    ResidentArgs a = c->res;
+    a.mcs = n;
+    launch_cluster(a, c->cluster_n, c->cluster_cs, c->cluster_threads, st);
+    launch_advance(c->d_run, n, st);
+}
+
 // Renormalisation at the end of a step, then (option snapshots) the copy of the final state.
 void enqueue_renorm(vegas_ctx *c, cudaStream_t st) {
     RenormArgs ra{c->d_spins, c->d_norm, c->n_sites * c->R, c->log2R, c->d_qis};
@@ -315,7 +327,9 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     if (o.replicas < 1 || o.replicas > 32 || (o.replicas & (o.replicas - 1)))
         return fail(nullptr, VEGAS_EINVAL, "replicas must be 1, 2, 4, 8, 16 or 32");
     if (o.accept_log_mcs < 0 || o.inst_base < 0 || o.max_blocks < 0) return fail(nullptr, VEGAS_EINVAL, "negative option");
-    if (o.variant < -1 || o.variant > 2) return fail(nullptr, VEGAS_EINVAL, "variant must be -1, 0, 1 or 2");
+    if (o.variant < -1 || o.variant > 3) return fail(nullptr, VEGAS_EINVAL, "variant must be -1, 0, 1, 2 or 3");
+    if (o.variant == 3 && o.precision != 32)
+        return fail(nullptr, VEGAS_EINVAL, "the cluster sweep (variant 3) is FP32 only");
     if (o.timeout_ns < 0 || o.fault_inject < 0 || o.fault_inject > 1) return fail(nullptr, VEGAS_EINVAL, "bad timeout or fault_inject");
     if (o.type_stats < 0 || o.type_stats > 1 || o.snapshots < 0 || o.snapshots > 1)
         return fail(nullptr, VEGAS_EINVAL, "type_stats and snapshots must be 0 or 1");
@@ -763,6 +777,26 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         // one block per instance only pays while instances are small; the resident sweep keeps
         // per-type sums for at most 8 types
         c->res_eligible = c->max_instance_sites <= (1 << 18) && c->n_types <= 8;
+        // cluster sweep: about 2048 sites per block of the cluster, 2 .. 16 blocks of 256 threads
+        // (measured on the 29k-site core/shell particle: 0.63 G attempts/s with 16 x 256 threads,
+        // 0.54 with 16 x 512)
+        if (c->n_types <= 8) {
+            int cs = 2;
+            while (cs < 16 && (int64_t)cs * 2048 < c->max_instance_sites) cs *= 2;
+            const int nt = 256;
+            int cap = cluster_capacity(cs, nt, any_policy);
+            if (cap == 0 && cs == 16) {
+                cs = 8;
+                cap = cluster_capacity(cs, nt, any_policy);
+            }
+            c->cluster_threads = nt;
+            if (cap > 0) {
+                c->cluster_cs = cs;
+                c->cluster_n = (int)std::min<int64_t>((int64_t)insts.size(), cap);
+                c->cluster_eligible = true;
+            }
+            cudaGetLastError();  // an unsupported cluster shape only makes the sweep ineligible
+        }
     }
     // ---- cooperative sweep: one sample, every block on every class
     if (!p64 && n_samples == 1 && !c->passes.empty() && !c->any_adaptive && !o.type_stats) {
@@ -789,6 +823,13 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         }
         c->variant = 2;
         c->tuned = true;
+    } else if (o.variant == 3) {
+        if (!c->cluster_eligible) {
+            c->err = "variant 3 (cluster) needs FP32, at most 8 tracked types and a device with thread-block clusters";
+            return bail(VEGAS_EINVAL);
+        }
+        c->variant = 3;
+        c->tuned = true;
     } else if (o.variant == 1) {
         if (!c->res_eligible) {
             c->err = "variant 1 (resident) needs FP32, samples of at most 262144 sites and at most 8 tracked types";
@@ -796,7 +837,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         }
         c->variant = 1;
         c->tuned = true;
-    } else if (o.variant == 0 || (!c->res_eligible && !c->coop_eligible)) {
+    } else if (o.variant == 0 || (!c->res_eligible && !c->coop_eligible && !c->cluster_eligible)) {
         c->variant = 0;
         c->tuned = true;
     } else {
@@ -985,9 +1026,20 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
         c->sweep_launches++;
         return VEGAS_OK;
     };
+    auto cluster = [&](int32_t n) -> vegas_status {
+        if (n <= 0) return VEGAS_OK;
+        if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 2], c->stream));
+        enqueue_cluster(c, c->stream, n);
+        if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 1], c->stream));
+        CK(c, cudaGetLastError());
+        c->kernel_launches += 2;
+        c->sweep_launches++;
+        return VEGAS_OK;
+    };
     auto run_variant = [&](int v, int32_t m0, int32_t n) -> vegas_status {
         if (v == 1) return resident(n);
         if (v == 2) return coop(n);
+        if (v == 3) return cluster(n);
         return stream_mcs(m0, n);
     };
     for (int32_t s = 0; s < n_steps; ++s) {
@@ -998,6 +1050,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             std::vector<int> cand{0};
             if (c->res_eligible) cand.push_back(1);
             if (c->coop_eligible) cand.push_back(2);
+            if (c->cluster_eligible) cand.push_back(3);
             const int32_t probe = std::max(1, std::min(4, mcs / (2 * (int32_t)cand.size())));
             if (probe * (int32_t)cand.size() <= mcs) {
                 float best = 0.f;
@@ -1030,8 +1083,8 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             c->tuned = true;
         }
 
-        if (m0 == 0 && c->tuned && use_graph && c->variant != 2 && step_graph_nodes(c, mcs) > 0) {
-            // the whole step as one graph (the cooperative launch stays a direct launch)
+        if (m0 == 0 && c->tuned && use_graph && c->variant < 2 && step_graph_nodes(c, mcs) > 0) {
+            // the whole step as one graph (the cooperative and cluster launches stay direct launches)
             cudaGraphExec_t ge;
             if ((st = step_graph(c, mcs, &ge)) != VEGAS_OK) return st;
             CK(c, cudaGraphLaunch(ge, c->stream));

@@ -288,5 +288,10 @@ void launch_snapshot(const void *spins, void *snap, int64_t n16, const RunState 
 int launch_coop(const CoopArgs &a, int grid, void *stream);
 int coop_blocks_per_sm(bool pol);
 int resident_blocks_per_sm(int threads, bool pol);
+// Cluster sweep: n_clusters clusters of cs blocks of `threads` (256 or 512); returns the CUDA
+// error of the launch.
+int launch_cluster(const ResidentArgs &a, int n_clusters, int cs, int threads, void *stream);
+// Clusters of cs blocks of `threads` that fit on the device at once (0 when none or on error).
+int cluster_capacity(int cs, int threads, bool pol);
 
 }  // namespace vegas

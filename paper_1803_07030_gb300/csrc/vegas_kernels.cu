@@ -18,6 +18,7 @@
 // operation order, Marsaglia sampler, correctly rounded sqrt and divide), so its spins and
 // accept decisions match the oracle bit for bit. The FP32 kernels draw one Philox block per
 // attempt (uniform z and azimuth, the acceptance uniform) and use FMA.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -303,7 +304,9 @@ constexpr int kDirectRow = 12;  // rows up to this length gather all neighbours 
 // draws the trial, decides, writes, and adds the site's share of E and M. Returns the
 // decision.
 // POL = 1: the sample has an update-policy table (pol[g], the instance's width sigma).
-template <int PM, int LM, int POL>
+// CG = 1: neighbour spins are read with ld.global.cg (L2 only) because other blocks of the same
+// launch write them (cooperative and cluster sweeps); otherwise through the read-only path.
+template <int PM, int LM, int POL, int CG = 0>
 __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const int64_t *row_ptr, int g, int r, int R,
                                                int lower_end, uint32_t orig, const Site32 &p, float beta, float B,
                                                uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1, Acc32 &acc,
@@ -326,7 +329,10 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
             float4 Sj[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (k0 + k < deg) Sj[k] = __ldg(S + (int64_t)ed[k0 + k].x * R + r);
+                if (k0 + k < deg) {
+                    const float4 *q = S + (int64_t)ed[k0 + k].x * R + r;
+                    Sj[k] = CG ? __ldcg(q) : __ldg(q);
+                }
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (k0 + k < deg)
@@ -336,7 +342,8 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
     } else {
         for (int64_t e = e0; e < e1; ++e) {
             const int2 ed = __ldg(E + e);
-            link32(__ldg(S + (int64_t)ed.x * R + r), __int_as_float(ed.y), LM == 2 && ed.x < lower_end, hx, hy, hz,
+            const float4 *q = S + (int64_t)ed.x * R + r;
+            link32(CG ? __ldcg(q) : __ldg(q), __int_as_float(ed.y), LM == 2 && ed.x < lower_end, hx, hy, hz,
                    lx, ly, lz);
         }
     }
@@ -525,6 +532,145 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }
 
+// ------------------------------------------------------------------ cluster sweep
+// As the resident sweep, but a thread-block cluster of CS blocks (on CS SMs) takes each
+// instance: the blocks split every colour segment, meet at the hardware cluster barrier
+// between classes, and rank 0 sums the blocks' per-MCS totals from their shared memory in
+// rank order. For instances too large for one block and too small to fill the GPU per class.
+// Every block of a cluster runs the same loop (rank 0 fetches the instance and the others
+// read it from rank 0's shared memory), so all of them reach every barrier.
+template <int NT, int POL>
+__global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentArgs a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    constexpr int NB = 5 + kResidentMaxTypes * 3;  // E, Mx, My, Mz, accepted, per-type M
+    __shared__ int s_item;
+    __shared__ double s_red[NT / 32][4];
+    __shared__ uint32_t s_acc[NT / 32];
+    __shared__ double s_tm[NT / 32][kResidentMaxTypes][3];
+    __shared__ double s_blk[NB];  // this block's totals of the MCS
+    __shared__ double s_tot[NB];  // rank 0: the cluster's totals
+    float4 *S = (float4 *)a.spins;
+    const int2 *E = (const int2 *)a.edges;
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    const int R = 1 << a.log2R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n_types = a.n_types;
+    RunState *rs = a.run;
+    bool nan_seen = false;
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) s_item = (int)atomicAdd(a.queue, 1u);
+        for (int q = threadIdx.x; q < (NT / 32) * kResidentMaxTypes * 3; q += NT) (&s_tm[0][0][0])[q] = 0.0;
+        cl.sync();
+        const int item = *cl.map_shared_rank(&s_item, 0);
+        cl.sync();  // every block has read the item before rank 0 fetches the next
+        if (item >= a.n_items) break;
+        const ResidentInst I = a.insts[item];
+        const uint32_t t0 = rs->t, rec0 = rs->rec;
+        const uint32_t step = rec0 / rs->mcs;
+        const double *sc = rs->sched + ((int64_t)step * a.n_inst + I.inst_local) * 2;
+        const float beta = (float)sc[0], B = (float)sc[1];
+        const uint32_t inst = (uint32_t)I.inst_id;
+        for (int m = 0; m < a.mcs; ++m) {
+            const uint32_t t = t0 + (uint32_t)m;
+            const bool log_accepts = a.alog && t < a.alog_mcs;
+            const float sigma = (POL && rs->sigma) ? (float)rs->sigma[I.inst_local] : 0.f;
+            Acc32 acc;
+            for (int q = 0; q < I.n_segs; ++q) {
+                const int4 sg = a.segs[I.seg_off + q];  // {begin, end, class begin, type | last << 16}
+                float tm[3] = {0.f, 0.f, 0.f};
+                for (int g = sg.x + rank * NT + (int)threadIdx.x; g < sg.y; g += CS * NT) {
+                    const uint32_t orig = (uint32_t)__ldg(a.orig + g);
+                    const Site32 p = resident_params(a, I, g);
+                    float4 Sq;
+                    const bool ok = direct_attempt<2, 2, POL, 1>(S, E, a.row_ptr, g, I.r, R, sg.z, orig, p, beta, B, t,
+                                                                 inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq);
+                    tm[0] = __fadd_rn(tm[0], Sq.x);
+                    tm[1] = __fadd_rn(tm[1], Sq.y);
+                    tm[2] = __fadd_rn(tm[2], Sq.z);
+                    if (log_accepts)
+                        a.alog[(int64_t)t * a.alog_stride + I.alog_base + (int64_t)I.r * I.n_sample_sites + orig] =
+                            ok ? 1 : 0;
+                }
+                if (n_types > 0) {
+                    double d[3] = {(double)tm[0], (double)tm[1], (double)tm[2]};
+                    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) d[c] += __shfl_xor_sync(0xFFFFFFFFu, d[c], off);
+                    }
+                    const int ty = sg.w & 0xFFFF;
+                    if (lane == 0 && ty < kResidentMaxTypes) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) s_tm[warp][ty][c] += d[c];
+                    }
+                }
+                if (sg.w >> 16) cl.sync();  // a colour class ends: its spins are final for the cluster
+            }
+            acc.flush();
+            double v[4] = {acc.d[0], acc.d[1], acc.d[2], acc.d[3]};
+            uint32_t na = acc.nacc;
+            for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+                na += __shfl_xor_sync(0xFFFFFFFFu, na, off);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s_red[warp][q] = v[q];
+                s_acc[warp] = na;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {  // this block's totals, warps in order
+                double sum[4] = {0.0, 0.0, 0.0, 0.0};
+                uint32_t nsum = 0;
+                for (int w = 0; w < NT / 32; ++w) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) sum[q] += s_red[w][q];
+                    nsum += s_acc[w];
+                }
+                for (int q = 0; q < 4; ++q) s_blk[q] = sum[q];
+                s_blk[4] = (double)nsum;
+                for (int k = 0; k < kResidentMaxTypes; ++k)
+                    for (int c = 0; c < 3; ++c) {
+                        double x = 0.0;
+                        for (int w = 0; w < NT / 32; ++w) {
+                            x += s_tm[w][k][c];
+                            s_tm[w][k][c] = 0.0;
+                        }
+                        s_blk[5 + k * 3 + c] = x;
+                    }
+            }
+            cl.sync();
+            if (rank == 0) {  // the cluster's totals: thread q sums quantity q over the blocks in rank order
+                if ((int)threadIdx.x < NB) {
+                    double x = 0.0;
+                    for (int b = 0; b < CS; ++b) x += cl.map_shared_rank(s_blk, b)[threadIdx.x];
+                    s_tot[threadIdx.x] = x;
+                }
+                __syncthreads();
+            }
+            if (rank == 0 && threadIdx.x == 0) {
+                const double *tot = s_tot;
+                const int64_t rec = (int64_t)rec0 + m;
+                double *h = rs->hist + (rec * a.n_inst + I.inst_local) * 4;
+                for (int q = 0; q < 4; ++q) h[q] = tot[q];
+                const uint32_t nsum = (uint32_t)tot[4];
+                if (rs->acc_hist) rs->acc_hist[rec * a.n_inst + I.inst_local] = nsum;
+                if (I.adaptive && rs->sigma && (uint32_t)(rec % rs->mcs) < rs->mcs / 5)
+                    rs->sigma[I.inst_local] = adapt_width(rs->sigma[I.inst_local], nsum, I.n_sample_sites);
+                if (n_types > 0 && rs->type_hist) {
+                    double *th = rs->type_hist + (rec * a.n_inst + I.inst_local) * n_types * 3;
+                    for (int k = 0; k < n_types && k < kResidentMaxTypes; ++k)
+                        for (int c = 0; c < 3; ++c) th[k * 3 + c] = tot[5 + k * 3 + c];
+                }
+            }
+            cl.sync();  // the width and the totals' buffers are ready for the next MCS
+        }
+    }
+    if (nan_seen) atomicOr(a.err, kErrNaN);
+}
+
 // ------------------------------------------------------------------ cooperative sweep
 // One sample, all blocks: class c of MCS m is swept by the whole grid, then the grid meets
 // at a barrier. The barrier's wait is bounded by the global timer: a block that waits
@@ -608,7 +754,7 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
                 if (a.params_mode == 2) p = site_params32(a, 2, g);
                 // one code path for every parameter mode (zero constants add signed zeros)
                 float4 Sq;
-                const bool ok = direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t, inst, k0,
+                const bool ok = direct_attempt<2, 2, POL, 1>(S, E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t, inst, k0,
                                                           k1, acc, nan_seen, a.pol32, 0.f, Sq);
                 if (log_accepts)
                     a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
@@ -921,6 +1067,46 @@ ResFn select_resident(int threads, bool pol) {
 void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream) {
     const int nt = threads >= 512 ? 512 : 256;
     select_resident(nt, a.pol != nullptr)<<<grid, nt, 0, (cudaStream_t)stream>>>(a);
+}
+
+using ClusterFn = void (*)(ResidentArgs);
+
+ClusterFn select_cluster(int threads, bool pol) {
+    if (threads >= 512) return pol ? cluster32_kernel<512, 1> : cluster32_kernel<512, 0>;
+    return pol ? cluster32_kernel<256, 1> : cluster32_kernel<256, 0>;
+}
+
+int launch_cluster(const ResidentArgs &a, int n_clusters, int cs, int threads, void *stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_clusters * cs);
+    cfg.blockDim = dim3(threads >= 512 ? 512 : 256);
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return (int)cudaLaunchKernelEx(&cfg, select_cluster(threads, a.pol != nullptr), a);
+}
+
+int cluster_capacity(int cs, int threads, bool pol) {
+    ClusterFn k = select_cluster(threads, pol);
+    if (cs > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(threads >= 512 ? 512 : 256);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) return 0;
+    return n;
 }
 
 int resident_blocks_per_sm(int threads, bool pol) {

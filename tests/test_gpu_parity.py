@@ -290,8 +290,55 @@ def test_autotuner_three_way():
     with ctx([s], seed=23, variant=-1) as a, ctx([s], seed=23, variant=0) as b:
         a.run([[1.0, 0.7]], [[0.2, 0.1]], 24)
         b.run([[1.0, 0.7]], [[0.2, 0.1]], 24)
-        assert a.stats()["variant"] in (0, 1, 2)
+        assert a.stats()["variant"] in (0, 1, 2, 3)
         assert np.array_equal(a.spins(0), b.spins(0))
+
+
+# --------------------------------------------------------------------------- cluster sweep
+# A thread-block cluster per instance, the hardware cluster barrier between colour classes.
+
+@pytest.mark.parametrize("make,R", [(lambda: core_shell_particle(seed=3, radius=7.0, core_radius=5.0), 1),
+                                    (lambda: sc_periodic(24, bimodal_seed=2, k_uni=0.1), 4),
+                                    (lambda: fcc_sphere(5.5), 2)])
+def test_cluster_sweep_equals_per_class_sweep(make, R):
+    s = make()
+    T = np.stack([np.array([2.0, 0.9, 0.5]) * (1 + 0.1 * i) for i in range(R)])
+    B = np.stack([np.array([0.5, -0.5, 1.0]) for _ in range(R)])
+    with ctx([s], replicas=R, seed=24, variant=0, accept_log_mcs=2) as a, \
+            ctx([s], replicas=R, seed=24, variant=3, accept_log_mcs=2) as b:
+        a.run(T, B, 9)
+        b.run(T, B, 9)
+        assert b.stats()["variant"] == 3
+        for i in range(R):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+        assert_fp32_history_close(a.history(), b.history(), s.n_sites)
+        assert np.array_equal(a.accept_log(), b.accept_log())
+        assert np.array_equal(a.accept_history(), b.accept_history())
+
+
+def test_cluster_sweep_batch_with_policies_and_types():
+    ps = nanoparticle_batch(6, seed=6, r_max=9.0)
+    for p in ps:
+        p.type = (np.arange(p.n_sites) % 2).astype(np.int32)
+        p.with_policy([oracle.ADAPTIVE, oracle.HINZKE_NOWAK], [0.8, 0.4])
+    T = np.linspace(0.4, 2.0, 12)[:, None]
+    B = np.full_like(T, 0.2)
+    with ctx(ps, replicas=2, seed=25, variant=0, type_stats=True) as a, \
+            ctx(ps, replicas=2, seed=25, variant=3, type_stats=True) as b:
+        a.run(T, B, 10)
+        b.run(T, B, 10)
+        assert np.array_equal(a.accept_history(), b.accept_history())
+        assert np.array_equal(a.adaptive_width(), b.adaptive_width())
+        for i in range(12):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+            n = ps[i // 2].n_sites
+            assert np.all(np.abs(a.type_history()[i] - b.type_history()[i]) <= 1e-6 * n)
+
+
+def test_cluster_rejected_for_fp64():
+    with pytest.raises(vb.VegasError) as e:
+        ctx([sc_periodic(4)], precision=64, variant=3)
+    assert e.value.status == vb.EINVAL
 
 
 def test_resident_rejected_for_fp64():
