@@ -3,8 +3,10 @@
 FP64: spins, accept/reject decisions and history must match the oracle bit for bit
 (history energy and magnetization to 1e-12 relative: the GPU sums per colour class in a
 different order). FP32: bitwise independence of batching and of run splitting, the
-history's E/N against the oracle's energy of the same spins (|d(E/N)| < 1e-3), and the
-observables against the oracle and closed forms within 4 standard errors.
+history's E/N against the oracle's energy of the same spins (|d(E/N)| < 1e-3), the
+observables <E>/N, <|M|>/N, C_v, chi against the FP64 oracle within 3 binned standard errors
+(independent seeds; |d(E/N)| between the chains is printed per result), and closed forms
+within 4 standard errors.
 """
 
 import numpy as np
@@ -448,10 +450,14 @@ def test_fp32_observables_match_oracle(T, B):
     Hr = ref["history"]
     g = _series_stats(H[:, :, 0] / N, np.linalg.norm(H[:, :, 1:], axis=2) / N, N, T)
     o = _series_stats(Hr[:, :, 0] / N, np.linalg.norm(Hr[:, :, 1:], axis=2) / N, N, T)
+    # within 3 binned standard errors of the FP64 oracle (independent seeds)
     for k in ("e", "m", "cv", "chi"):
         (a, sa), (b, sb) = g[k], o[k]
-        assert abs(a - b) < 4 * np.hypot(sa, sb), (k, a, sa, b, sb)
-    assert abs(g["e"][0] - o["e"][0]) < 1e-3 or abs(g["e"][0] - o["e"][0]) < 4 * np.hypot(g["e"][1], o["e"][1])
+        assert abs(a - b) < 3 * np.hypot(sa, sb), (k, a, sa, b, sb)
+    # the energy per site of the two chains: |d(E/N)| below 1e-3 (or within their errors)
+    d_e = abs(g["e"][0] - o["e"][0])
+    print(f"T={T} B={B}: |d(E/N)| = {d_e:.2e} (errors {g['e'][1]:.1e}, {o['e'][1]:.1e})")
+    assert d_e < 1e-3 or d_e < 3 * np.hypot(g["e"][1], o["e"][1])
 
 
 def test_fp32_closed_forms():
