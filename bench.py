@@ -36,10 +36,20 @@ L_SIDE, REPLICAS, MCS, SEED = 256, 32, 200, 1
 # algorithmic bytes per attempt: 16 B read + 16 B write of the FP32 spin (float4), plus one
 # row of six (int32 col, f32 J) links = 48 B shared by the 32 replicas that sweep it together
 BYTES_PER_ATTEMPT = 16 + 16 + 48.0 / REPLICAS
-PASS_KERNEL = "pass32_r32"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pass32_r32_sg256x32.txt")
-# the source of the profiled sweep kernel (pass32_r32) and the device helpers it uses
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_1803_07030_gb300", "csrc", f) for f in ("vegas_staged.cu", "vegas_device.cuh")]
+CSRC = os.path.join(ROOT, "paper_1803_07030_gb300", "csrc")
+# per sweep variant: the kernel that sweeps, its committed ncu summary, the sources it is built
+# from (the summary's counters are used only while their hash matches), and how many colour
+# classes one launch covers
+SWEEP_KERNELS = {
+    "per_class": ("pass32_r32", os.path.join(ROOT, "profiles", "pass32_r32_sg256x32.txt"),
+                  [os.path.join(CSRC, f) for f in ("vegas_staged.cu", "vegas_staged.cuh", "vegas_device.cuh")], 1),
+    "wave": ("wave32_r32", os.path.join(ROOT, "profiles", "wave32_r32_sg256x32.txt"),
+             [os.path.join(CSRC, f) for f in ("vegas_wave.cu", "vegas_staged.cuh", "vegas_device.cuh")], 2),
+}
+
+
+def sweep_kernel(variant: int):
+    return SWEEP_KERNELS["wave" if variant == 4 else "per_class"]
 
 
 def workload_desc(mcs):
@@ -92,26 +102,26 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_hash():
+def kernel_hash(sources):
     h = hashlib.sha256()
-    for path in KERNEL_SOURCES:
+    for path in sources:
         with open(path, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(summary, sources):
     """DRAM bytes per sweep launch from the committed ncu summary, if it still describes
     the current kernel source (else None)."""
-    if not os.path.exists(PROFILE_SUMMARY):
+    if not os.path.exists(summary):
         return None
     vals = {}
-    with open(PROFILE_SUMMARY) as f:
+    with open(summary) as f:
         for line in f:
             if ":" in line and line.split(":", 1)[0].strip() in ("kernel_source_sha256_16", "dram_bytes_per_launch"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha256_16") != kernel_hash() or "dram_bytes_per_launch" not in vals:
+    if vals.get("kernel_source_sha256_16") != kernel_hash(sources) or "dram_bytes_per_launch" not in vals:
         return None
     return float(vals["dram_bytes_per_launch"])
 
@@ -284,10 +294,12 @@ def run_ours(args):
     launches = st1["kernel_launches"] - st0["kernel_launches"]
     sweeps = st1["sweep_launches"] - st0["sweep_launches"]
     sweep_ms = (st1["sweep_ms"] - st0["sweep_ms"]) / max(sweeps, 1)
-    attempts_per_launch = REPLICAS * s.n_sites // 2  # one colour class of the checkerboard
+    kname, ksummary, ksources, kclasses = sweep_kernel(st1["variant"])
+    # one colour class of the checkerboard per launch, or both (wavefront sweep)
+    attempts_per_launch = REPLICAS * s.n_sites * kclasses // 2
     peak, peak_kind = peaks()
     achieved = BYTES_PER_ATTEMPT * attempts_per_launch / (sweep_ms / 1000.0) / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic(ksummary, ksources)
 
     if args.quick or policy:
         if rank == 0:
@@ -343,7 +355,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback 6.8 TB/s",
-                         "kernel": PASS_KERNEL, "bytes_per_attempt": BYTES_PER_ATTEMPT,
+                         "kernel": kname, "bytes_per_attempt": BYTES_PER_ATTEMPT,
                          "attempts_per_launch": attempts_per_launch, "avg_launch_ms": sweep_ms},
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"1 MCS of {cores} replicas (one per host thread) of the {L_SIDE}^3 lattice, "
@@ -573,9 +585,10 @@ def main():
     ap.add_argument("--policy", default="",
                     help="update policy per site type, e.g. 'adaptive' or 'random,hn:0.26' (policy[:param], one "
                          "per type; names: " + ", ".join(POLICY_CODES) + "); the line then reports that path")
-    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+    ap.add_argument("--variant", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
                     help="sweep variant: -1 automatic (timed on the first run), 0 per colour class, 1 resident, 3 cluster, "
-                         "2 cooperative; profiling commands fix it because ncu distorts the automatic timing")
+                         "2 cooperative, 4 wavefront (both classes per launch); profiling commands fix it because ncu "
+                         "distorts the automatic timing")
     ap.add_argument("--analysis", action="store_true", help="time the history analysis instead of the sweep")
     ap.add_argument("--ising", action="store_true", help="time the multi-spin-coded Ising workload")
     ap.add_argument("--type-stats", action="store_true", help="secondary workloads: record per-type magnetization")

@@ -133,8 +133,14 @@ typedef struct {
                                sweep one sample class by class (FP32, one sample, no adaptive
                                policy), 3 cluster: one persistent launch per step, a thread-
                                block cluster of 2 .. 16 blocks per instance, the blocks meeting at
-                               the hardware cluster barrier between colour classes (FP32).
-                               Default -1. */
+                               the hardware cluster barrier between colour classes (FP32),
+                               4 wavefront: one cooperative launch per MCS runs both colour
+                               classes, a block of class-1 sites starting once the class-0
+                               blocks it links to have finished (FP32, one sample, 32
+                               replicas, two colour classes, six links per site, no policy
+                               table, no per-type statistics; sites are stored plane by plane
+                               when positions are given). Variant 4 is used only when asked
+                               for. Default -1. */
     int32_t accept_log_mcs; /* > 0: keep the accept/reject bit of every attempt of the
                                first accept_log_mcs MCS (debugging and parity). Default 0. */
     int32_t timing;         /* 1: time every sweep launch with CUDA events. Default 0. */
@@ -145,10 +151,13 @@ typedef struct {
                                flight per warp, 2 or 3; 1 = no staging (direct kernel);
                                0 = automatic. Default 0. */
     int64_t timeout_ns;     /* longest wait of a block at a grid barrier of the cooperative
-                               sweep before the run fails with VEGAS_ETIMEOUT; 0 = 2 s. */
+                               sweep, or of a warp for the dependencies of one block of the
+                               wavefront sweep, before the run fails with VEGAS_ETIMEOUT;
+                               0 = 2 s. */
     int32_t fault_inject;   /* testing only: 1 = in the cooperative sweep one block leaves
-                               before its first grid barrier, so the others time out.
-                               Default 0. */
+                               before its first grid barrier, and in the wavefront sweep the
+                               first block of class-0 sites is never reported finished, so the
+                               blocks that wait for it time out. Default 0. */
     int32_t type_stats;     /* 1: also record the magnetization of every site type (magnetic
                                phase, Sec. II) after every MCS (vegas_type_history). Sites are
                                then stored type by type inside each colour class, and the
@@ -158,6 +167,10 @@ typedef struct {
                                final state per step), read with vegas_get_snapshot. Costs a
                                device copy of the spins per step and host memory for all of
                                them. Default 0. */
+    int32_t wave_lag;       /* wavefront sweep: a class-1 block is queued this many class-0
+                               blocks after the last class-0 block it links to, so that its
+                               dependencies have usually finished when a warp reaches it;
+                               0 = the number of warps of the launch. Default 0. */
 } vegas_options;
 
 typedef struct {
@@ -169,7 +182,7 @@ typedef struct {
     int64_t records;            /* history records per instance so far */
     uint32_t mcs_done;          /* global MCS counter t */
     uint32_t device_error;      /* error bits set by kernels (1 NaN dE, 2 sampler cap,
-                                   4 index check failed in a debug build, 8 barrier timeout) */
+                                   4 index check failed in a debug build, 8 bounded wait timed out) */
     int64_t kernel_launches;    /* kernels launched by the library so far */
     int64_t sweep_launches;     /* colour-pass (or resident) sweep launches so far */
     double sweep_ms;            /* summed event time of sweep launches (timing = 1) */

@@ -97,6 +97,14 @@ struct vegas_ctx {
     int coop_grid = 1;
     GridBarrier *d_bar = nullptr;
     double *d_coop_partial = nullptr;
+    // wavefront sweep: both classes of an MCS in one launch
+    WaveArgs wave{};
+    int wave_grid = 1;
+    int32_t *d_tasks = nullptr;
+    uint32_t *d_done = nullptr, *d_ticket = nullptr;
+    double *d_wave_partial = nullptr;
+    int64_t *d_wave_slot_base = nullptr;
+    int32_t *d_wave_slot_count = nullptr;
     // graph of one MCS (per-class sweep), and graphs of a whole temperature/field step
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -153,7 +161,8 @@ void free_all(vegas_ctx *c) {
     void *bufs[] = {c->d_spins, c->d_edges, c->d_p0, c->d_p1, c->d_pk, c->d_rowptr, c->d_slot_base, c->d_orig,
                     c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog,
                     c->d_insts, c->d_cstart, c->d_queue, c->d_bar, c->d_coop_partial, c->d_acc, c->d_acc_hist,
-                    c->d_pol, c->d_pol32, c->d_qis, c->d_sigma, c->d_adapt_n, c->d_type_hist, c->d_snap, c->d_segs};
+                    c->d_pol, c->d_pol32, c->d_qis, c->d_sigma, c->d_adapt_n, c->d_type_hist, c->d_snap, c->d_segs,
+                    c->d_tasks, c->d_done, c->d_ticket, c->d_wave_partial, c->d_wave_slot_base, c->d_wave_slot_count};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -214,6 +223,17 @@ void enqueue_cluster(vegas_ctx *c, cudaStream_t st, int32_t n) {
     a.mcs = n;
     launch_cluster(a, c->cluster_n, c->cluster_cs, c->cluster_threads, st);
     launch_advance(c->d_run, n, st);
+}
+
+// One MCS of the wavefront sweep (both colour classes in one launch), then the reduction;
+// returns the CUDA error of the sweep launch.
+int enqueue_wave(vegas_ctx *c, cudaStream_t st) {
+    cudaMemsetAsync(c->d_ticket, 0, sizeof(uint32_t), st);
+    const int e = launch_wave(c->wave, c->wave_grid, st);
+    ReduceArgs ra{c->d_wave_partial, c->d_wave_slot_base, c->d_wave_slot_count, c->d_run, c->d_adapt_n, c->R,
+                  c->n_inst, 1, 0};
+    launch_reduce(ra, st);
+    return e;
 }
 
 // Renormalisation at the end of a step, then (option snapshots) the copy of the final state.
@@ -313,6 +333,7 @@ extern "C" void vegas_default_options(vegas_options *o) {
     o->fault_inject = 0;
     o->type_stats = 0;
     o->snapshots = 0;
+    o->wave_lag = 0;
 }
 
 extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samples, const vegas_options *opt,
@@ -327,7 +348,11 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     if (o.replicas < 1 || o.replicas > 32 || (o.replicas & (o.replicas - 1)))
         return fail(nullptr, VEGAS_EINVAL, "replicas must be 1, 2, 4, 8, 16 or 32");
     if (o.accept_log_mcs < 0 || o.inst_base < 0 || o.max_blocks < 0) return fail(nullptr, VEGAS_EINVAL, "negative option");
-    if (o.variant < -1 || o.variant > 3) return fail(nullptr, VEGAS_EINVAL, "variant must be -1, 0, 1, 2 or 3");
+    if (o.variant < -1 || o.variant > 4) return fail(nullptr, VEGAS_EINVAL, "variant must be -1, 0, 1, 2, 3 or 4");
+    if (o.variant == 4 && (o.precision != 32 || n_samples != 1 || o.replicas != 32 || o.type_stats))
+        return fail(nullptr, VEGAS_EINVAL,
+                    "the wavefront sweep (variant 4) is FP32 with one sample, 32 replicas and no per-type statistics");
+    if (o.wave_lag < 0) return fail(nullptr, VEGAS_EINVAL, "wave_lag must be >= 0");
     if (o.variant == 3 && o.precision != 32)
         return fail(nullptr, VEGAS_EINVAL, "the cluster sweep (variant 3) is FP32 only");
     if (o.timeout_ns < 0 || o.fault_inject < 0 || o.fault_inject > 1) return fail(nullptr, VEGAS_EINVAL, "bad timeout or fault_inject");
@@ -348,13 +373,21 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     int64_t n_sites = 0, n_edges = 0;
     for (int32_t s = 0; s < n_samples; ++s) {
         std::string e;
-        if (!load_sample(samples[s], L[(size_t)s], e, o.type_stats != 0))
+        if (!load_sample(samples[s], L[(size_t)s], e, o.type_stats != 0, o.variant == 4))
             return fail(nullptr, VEGAS_EINVAL, "sample " + std::to_string(s) + ": " + e);
         n_sites += L[(size_t)s].n;
         n_edges += L[(size_t)s].n_edges + (L[(size_t)s].n_edges & 1);  // keep every sample 16-byte aligned
     }
     if (n_sites * o.replicas > ((int64_t)1 << 40) || n_sites > INT32_MAX - (1 << 24) || n_edges >= INT32_MAX)
         return fail(nullptr, VEGAS_EINVAL, "too many sites or links for one context");
+    if (o.variant == 4) {
+        const LoadedSample &l = L[0];
+        if (l.n_colours != 2 || l.uniform_degree != 6 || !l.policy.empty() || l.lower_mode[0] != 0 ||
+            l.lower_mode[1] != 1)
+            return fail(nullptr, VEGAS_EINVAL,
+                        "the wavefront sweep (variant 4) needs two colour classes, six links per site and no "
+                        "policy table");
+    }
     int32_t n_types = 0;
     if (o.type_stats)
         for (auto &l : L) n_types = std::max(n_types, l.n_types);
@@ -816,7 +849,87 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         ca.skip_block = o.fault_inject == 1 ? 0 : -1;
         c->coop_eligible = true;
     }
-    if (o.variant == 2) {
+    // ---- wavefront sweep: task order and completion flags
+    if (o.variant == 4) {
+        const SampleInfo &si = c->samples[0];
+        const LoadedSample &l = L[0];
+        const PassArgs &p0 = c->passes[0].args;
+        const int bps = wave_blocks_per_sm(p0.params_mode);
+        if (bps < 1) {
+            c->err = "the wavefront sweep kernel does not fit on this device";
+            return bail(VEGAS_ECUDA);
+        }
+        c->wave_grid = c->sm_count * bps;
+        if (o.max_blocks > 0) c->wave_grid = std::min(c->wave_grid, o.max_blocks);
+        const int64_t W = (int64_t)c->wave_grid * (kThreads / 32);
+        const int32_t n0 = si.cstart[1], n1 = si.cstart[2] - si.cstart[1];
+        const int32_t nb0 = (n0 + 7) / 8, nb1 = (n1 + 7) / 8;
+        // last class-0 block that class-1 block q links to
+        std::vector<int32_t> D((size_t)nb1, 0);
+        for (int32_t g = si.cstart[1]; g < si.cstart[2]; ++g) {
+            int32_t &d = D[(size_t)((g - si.cstart[1]) / 8)];
+            for (int64_t e = l.row_ptr[(size_t)g]; e < l.row_ptr[(size_t)g + 1]; ++e)
+                d = std::max(d, l.col[(size_t)e] / 8);
+        }
+        // class-0 blocks in memory order; each class-1 block after class-0 block
+        // min(D + lag, nb0 - 1), so every dependency comes earlier in the list
+        const int64_t lag = o.wave_lag > 0 ? o.wave_lag : W;
+        std::vector<int32_t> first((size_t)nb0 + 1, 0), after((size_t)nb1);
+        for (int32_t q = 0; q < nb1; ++q) {
+            after[(size_t)q] = (int32_t)std::min<int64_t>((int64_t)D[(size_t)q] + lag, nb0 - 1);
+            first[(size_t)after[(size_t)q] + 1]++;
+        }
+        for (int32_t j = 0; j < nb0; ++j) first[(size_t)j + 1] += first[(size_t)j];
+        std::vector<int32_t> byj((size_t)nb1), fill(first.begin(), first.end() - 1);
+        for (int32_t q = 0; q < nb1; ++q) byj[(size_t)fill[(size_t)after[(size_t)q]]++] = q;
+        std::vector<int32_t> tasks;
+        tasks.reserve((size_t)nb0 + nb1);
+        std::vector<int64_t> pos0((size_t)nb0);
+        for (int32_t j = 0; j < nb0; ++j) {
+            pos0[(size_t)j] = (int64_t)tasks.size();
+            tasks.push_back(j);
+            for (int32_t k = first[(size_t)j]; k < first[(size_t)j + 1]; ++k) tasks.push_back(nb0 + byj[(size_t)k]);
+        }
+        for (int64_t m = 0; m < (int64_t)tasks.size(); ++m)  // the order the progress argument needs
+            if (tasks[(size_t)m] >= nb0 && pos0[(size_t)D[(size_t)(tasks[(size_t)m] - nb0)]] >= m) {
+                c->err = "wavefront task order: a class-1 block before one of its dependencies";
+                return bail(VEGAS_EINVAL);
+            }
+        DALLOC(c->d_tasks, sizeof(int32_t) * tasks.size());
+        DALLOC(c->d_done, sizeof(uint32_t) * (size_t)nb0);
+        DALLOC(c->d_ticket, sizeof(uint32_t));
+        DALLOC(c->d_wave_partial, sizeof(double) * 4 * (size_t)c->wave_grid * R);
+        DALLOC(c->d_wave_slot_base, sizeof(int64_t));
+        DALLOC(c->d_wave_slot_count, sizeof(int32_t));
+        H2D(c->d_tasks, tasks.data(), sizeof(int32_t) * tasks.size());
+        const int64_t zero = 0;
+        const int32_t gcount = c->wave_grid;
+        H2D(c->d_wave_slot_base, &zero, sizeof zero);
+        H2D(c->d_wave_slot_count, &gcount, sizeof gcount);
+        if (cudaMemsetAsync(c->d_done, 0, sizeof(uint32_t) * (size_t)nb0, c->stream) != cudaSuccess) {
+            c->err = "memset failed";
+            return bail(VEGAS_ECUDA);
+        }
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {  // the host vectors above go out of scope
+            c->err = "upload of the wavefront task order failed";
+            return bail(VEGAS_ECUDA);
+        }
+        WaveArgs &wa = c->wave;
+        std::memset(&wa, 0, sizeof wa);
+        wa.pass = p0;
+        wa.pass.partial = c->d_wave_partial;
+        wa.tasks = c->d_tasks;
+        wa.ticket = c->d_ticket;
+        wa.done = c->d_done;
+        wa.n_tasks = (int32_t)tasks.size();
+        wa.nb0 = nb0;
+        wa.c1_begin = si.site_off + si.cstart[1];
+        wa.c1_end = si.site_off + si.cstart[2];
+        wa.timeout_ns = o.timeout_ns > 0 ? o.timeout_ns : 2000000000LL;
+        wa.skip_block = o.fault_inject == 1 ? 0 : -1;
+        c->variant = 4;
+        c->tuned = true;
+    } else if (o.variant == 2) {
         if (!c->coop_eligible) {
             c->err = "variant 2 (cooperative) does not run samples with the adaptive policy";
             return bail(VEGAS_EINVAL);
@@ -1036,7 +1149,21 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
         c->sweep_launches++;
         return VEGAS_OK;
     };
+    auto wave = [&](int32_t m0, int32_t n) -> vegas_status {
+        for (int32_t m = m0; m < m0 + n; ++m) {
+            if (c->opt.timing) CK(c, cudaEventRecord(ev[2 * (size_t)m], c->stream));
+            const int e = enqueue_wave(c, c->stream);
+            if (e != 0)
+                return fail(c, VEGAS_ECUDA, std::string("wavefront sweep launch: ") + cudaGetErrorString((cudaError_t)e));
+            if (c->opt.timing) CK(c, cudaEventRecord(ev[2 * (size_t)m + 1], c->stream));
+            CK(c, cudaGetLastError());
+            c->kernel_launches += 2;
+            c->sweep_launches++;
+        }
+        return VEGAS_OK;
+    };
     auto run_variant = [&](int v, int32_t m0, int32_t n) -> vegas_status {
+        if (v == 4) return wave(m0, n);
         if (v == 1) return resident(n);
         if (v == 2) return coop(n);
         if (v == 3) return cluster(n);
@@ -1098,7 +1225,13 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
         c->kernel_launches += c->opt.snapshots ? 2 : 1;
         if (c->opt.timing) {  // read this step's sweep timings before the events are reused
             CK(c, cudaStreamSynchronize(c->stream));
-            if (c->variant >= 1) {
+            if (c->variant == 4) {
+                for (int32_t m = m0; m < mcs; ++m) {
+                    float ms = 0.f;
+                    CK(c, cudaEventElapsedTime(&ms, ev[2 * (size_t)m], ev[2 * (size_t)m + 1]));
+                    sweep_ms += ms;
+                }
+            } else if (c->variant >= 1) {
                 float ms = 0.f;
                 CK(c, cudaEventElapsedTime(&ms, ev[ev.size() - 2], ev[ev.size() - 1]));
                 sweep_ms += ms;
@@ -1185,7 +1318,10 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
     c->t += (uint32_t)nrec;
     c->device_error |= derr;
     if (derr & kErrTimeout)
-        return fail(c, VEGAS_ETIMEOUT, "a grid barrier of the cooperative sweep waited longer than timeout_ns");
+        return fail(c, VEGAS_ETIMEOUT,
+                    c->variant == 4 ? "a warp of the wavefront sweep waited longer than timeout_ns for the class-0 "
+                                      "blocks that a class-1 block links to"
+                                    : "a grid barrier of the cooperative sweep waited longer than timeout_ns");
     if (derr) {
         char msg[200];
         std::snprintf(msg, sizeof msg,

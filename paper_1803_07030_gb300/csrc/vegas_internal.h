@@ -33,7 +33,7 @@ constexpr int32_t kPolRandom = 0, kPolFlip = 1, kPolSmallStep = 2, kPolGaussian 
 constexpr uint32_t kErrNaN = 1u;
 constexpr uint32_t kErrSphere = 2u;
 constexpr uint32_t kErrIndex = 4u;  // debug builds: an index or alignment check failed
-constexpr uint32_t kErrTimeout = 8u;  // a bounded grid-barrier wait ran out
+constexpr uint32_t kErrTimeout = 8u;  // a bounded wait (grid barrier, wavefront dependency) ran out
 
 // ------------------------------------------------------------------ host-side sample
 
@@ -70,8 +70,11 @@ struct LoadedSample {
 };
 
 // Validates and renumbers; on failure returns false and sets err. type_major: inside each
-// colour class, sites are ordered by type first (then Morton order or caller id).
-bool load_sample(const vegas_sample &s, LoadedSample &out, std::string &err, bool type_major = false);
+// colour class, sites are ordered by type first (then Morton order or caller id). plane_order:
+// inside each class, positions are ordered by z, then y, then x (instead of the Morton curve),
+// so that every neighbour of a site lies within about one plane of it in memory order.
+bool load_sample(const vegas_sample &s, LoadedSample &out, std::string &err, bool type_major = false,
+                 bool plane_order = false);
 
 // ------------------------------------------------------------------ device-side layouts
 
@@ -252,6 +255,24 @@ struct CoopArgs {
     int32_t skip_block;        // fault injection: this block never arrives (-1: none)
 };
 
+// Wavefront sweep of one two-colour sample with R = 32 replicas: both colour classes of an
+// MCS in one launch. The sites of each class are cut into blocks of 8; tasks[] lists the
+// blocks in sweep order, and every warp draws its next task from a ticket counter. A block
+// of class 1 starts once every class-0 block holding one of its neighbours has finished this
+// MCS (done[b] == t + 1, published with release semantics). Every class-1 block comes after
+// all of its class-0 dependencies in tasks[], and the holder of a ticket is a running warp,
+// which makes the waits finite; each wait is still bounded by timeout_ns.
+struct WaveArgs {
+    PassArgs pass;             // class 0: links, parameters, spins, run state; partial = [block][32][4]
+    const int32_t *tasks;      // [n_tasks]: b < nb0 is block b of class 0, else block b - nb0 of class 1
+    uint32_t *ticket;          // next task of the launch (zeroed before every launch)
+    uint32_t *done;            // [nb0] MCS counter + 1 of the MCS in which class-0 block b last finished
+    int32_t n_tasks, nb0;
+    int32_t c1_begin, c1_end;  // global sites of class 1 (class 0 is pass.g_begin .. pass.g_end)
+    int64_t timeout_ns;        // longest wait for one block's dependencies
+    int32_t skip_block;        // fault injection: this class-0 block is never published (-1: none)
+};
+
 // ------------------------------------------------------------------ launchers
 
 using PassFn = void (*)(PassArgs);
@@ -293,5 +314,10 @@ int resident_blocks_per_sm(int threads, bool pol);
 int launch_cluster(const ResidentArgs &a, int n_clusters, int cs, int threads, void *stream);
 // Clusters of cs blocks of `threads` that fit on the device at once (0 when none or on error).
 int cluster_capacity(int cs, int threads, bool pol);
+
+// Wavefront sweep: launch of `grid` blocks of kThreads; returns the CUDA error of the launch.
+// wave_blocks_per_sm is the occupancy of its kernel for a parameter mode.
+int launch_wave(const WaveArgs &a, int grid, void *stream);
+int wave_blocks_per_sm(int params_mode);
 
 }  // namespace vegas

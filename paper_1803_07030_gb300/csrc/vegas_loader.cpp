@@ -88,7 +88,7 @@ extern "C" int32_t vegas_greedy_colour(int32_t n, const int64_t *row_ptr, const 
 
 namespace vegas {
 
-bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err, bool type_major) {
+bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err, bool type_major, bool plane_order) {
     const int32_t n = s.n_sites;
     if (n < 1) { err = "n_sites must be >= 1"; return false; }
     if (!s.row_ptr) { err = "row_ptr is NULL"; return false; }
@@ -193,7 +193,17 @@ bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err, bool 
     L.orig.resize((size_t)n);
     L.inv.resize((size_t)n);
     for (int32_t i = 0; i < n; ++i) L.orig[(size_t)fill[(size_t)colour[(size_t)i]]++] = i;
-    if (s.positions) {  // memory order inside each class: Morton curve of the positions
+    if (s.positions && plane_order) {  // memory order inside each class: z, then y, then x
+        const double *P = s.positions;
+        for (int32_t c = 0; c < nc; ++c)
+            std::stable_sort(L.orig.begin() + L.cstart[(size_t)c], L.orig.begin() + L.cstart[(size_t)c + 1],
+                             [&](int32_t x, int32_t y) {
+                                 for (int q = 2; q >= 0; --q)
+                                     if (P[3 * (size_t)x + q] != P[3 * (size_t)y + q])
+                                         return P[3 * (size_t)x + q] < P[3 * (size_t)y + q];
+                                 return false;
+                             });
+    } else if (s.positions) {  // memory order inside each class: Morton curve of the positions
         const std::vector<uint64_t> key = morton_keys(s.positions, n);
         for (int32_t c = 0; c < nc; ++c)
             std::stable_sort(L.orig.begin() + L.cstart[(size_t)c], L.orig.begin() + L.cstart[(size_t)c + 1],

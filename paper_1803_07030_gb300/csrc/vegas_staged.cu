@@ -7,6 +7,7 @@
 
 #include "vegas_device.cuh"
 #include "vegas_internal.h"
+#include "vegas_staged.cuh"
 
 namespace vegas {
 namespace {
@@ -18,65 +19,6 @@ namespace {
 // are copied with cp.async while group k is computed, so DRAM latency overlaps compute
 // instead of stalling the warp. Group k's rows are complete once all but the last D-1
 // committed copy groups have landed (cp.async.wait_group D-1).
-__device__ __forceinline__ void cp16(void *smem, const void *gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp4(void *smem, const void *gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp8(void *smem, const void *gmem) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// One staged attempt: links lk (int4 pairs), rows row[j*32] (neighbour j) and row[DEG*32]
-// (own) already in shared memory; with POL, the site's update policy *ps too.
-template <int DEG, int PM, int LM, int POL = 0>
-__device__ __forceinline__ void staged_attempt(const PassArgs &a, const int4 *lk, const float4 *row, uint32_t orig,
-                                               int g, int r, int R, uint32_t t, uint32_t inst, const uint32_t *rk0,
-                                               const uint32_t *rk1, float beta, float B, float4 *S, Acc32 &acc,
-                                               bool &nan_seen, bool log_accepts, const PolicySite32 *ps = nullptr,
-                                               float sigma = 0.f) {
-    const Site32 p = site_params32(a, PM, g);
-    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-#pragma unroll
-    for (int j = 0; j < DEG / 2; ++j) {
-        const int4 q = lk[j];
-        link32(row[(2 * j) * 32], __int_as_float(q.y), LM == 2 && q.x < a.lower_end, hx, hy, hz, lx, ly, lz);
-        link32(row[(2 * j + 1) * 32], __int_as_float(q.w), LM == 2 && q.z < a.lower_end, hx, hy, hz, lx, ly, lz);
-    }
-    if (LM == 1) {
-        lx = hx;
-        ly = hy;
-        lz = hz;
-    }
-    const float4 Si = row[DEG * 32];
-    uint4 c = make_uint4(orig, t, inst, kPurposeTrial32);
-#pragma unroll
-    for (int q = 0; q < 10; ++q) {  // Philox4x32-10 with precomputed round keys
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ rk0[q], lo1, hi0 ^ c.w ^ rk1[q], lo0);
-    }
-    float4 Sn;
-    bool ok, bad;
-    float e_i;
-    const float3 P =
-        POL ? policy_trial32(*ps, sigma, Si, p.sn, c) : trial_random32(c, p.sn);
-    attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, P, c.z, Sn, ok, e_i, bad);
-    nan_seen |= bad;
-    if (ok) S[(int64_t)g * R + r] = Sn;
-    if (log_accepts)
-        a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
-    acc.add(e_i, Sn, ok);
-}
 
 // Geometry of the staged kernel. A group is 32 work items (spg = 32/R sites x R replicas);
 // a block is NB consecutive groups (BS = NB * spg >= 8 consecutive sites) whose links and
@@ -97,20 +39,6 @@ __host__ __device__ inline StagedGeom staged_geom(int deg, int D, int log2R) {
     g.warp_bytes = g.rows_bytes + g.NLS * g.slot_bytes;
     return g;
 }
-
-// Debug builds (VEGAS_DEBUG_CHECKS) check every staged copy: a failed check sets
-// kErrIndex, records a code and a value, and skips the access.
-#ifdef VEGAS_DEBUG_CHECKS
-#define VEGAS_CHECK(cond, code, val)                   \
-    if (!(cond)) {                                     \
-        atomicOr(a.err, kErrIndex);                    \
-        atomicCAS(a.err + 1, 0u, (uint32_t)(code));    \
-        a.err[2] = (uint32_t)(val);                    \
-        return;                                        \
-    }
-#else
-#define VEGAS_CHECK(cond, code, val)
-#endif
 
 // Position of one group in the warp's sequence: first site, index inside its block, and
 // the slot holding its block's links. Groups are visited in increasing site order.

@@ -65,6 +65,7 @@ class vegas_options(C.Structure):
         ("fault_inject", C.c_int32),
         ("type_stats", C.c_int32),
         ("snapshots", C.c_int32),
+        ("wave_lag", C.c_int32),
     ]
 
 
@@ -411,7 +412,8 @@ class Context:
                  inst_base: int = 0, device: int = -1, stream="torch", variant: int = -1,
                  accept_log_mcs: int = 0, timing: bool = False, graphs: bool = True, max_blocks: int = 0,
                  pipeline_depth: int = 0, timeout_ns: int = 0, fault_inject: int = 0,
-                 type_stats: bool = False, snapshots: bool = False, library: Optional[str] = None):
+                 type_stats: bool = False, snapshots: bool = False, wave_lag: int = 0,
+                 library: Optional[str] = None):
         self.samples = list(samples)
         self.n_sites = [int(np.asarray(s.row_ptr).shape[0] - 1) for s in self.samples]
         if library is not None:
@@ -433,6 +435,7 @@ class Context:
         o.fault_inject = fault_inject
         o.type_stats = 1 if type_stats else 0
         o.snapshots = 1 if snapshots else 0
+        o.wave_lag = wave_lag
         o.cuda_stream = _current_stream() if stream == "torch" else stream
         self.replicas = replicas
         self.ptr = None

@@ -157,6 +157,38 @@ def test_invalid_options_rejected(lib, opt):
     assert st == vb.EINVAL, (opt, msg)
 
 
+@pytest.mark.parametrize("samples,opt,needle", [
+    ("sc4", {"variant": 4}, "32 replicas"),
+    ("sc4", {"variant": 4, "replicas": 32, "precision": 64}, "FP32"),
+    ("sc4", {"variant": 4, "replicas": 32, "type_stats": 1}, "per-type"),
+    ("two", {"variant": 4, "replicas": 32}, "one sample"),
+    ("sc4", {"variant": 4, "replicas": 32, "wave_lag": -1}, "wave_lag"),
+    ("sc5", {"variant": 4, "replicas": 32}, "two colour classes"),   # odd periodic sides: 3 colours
+    ("graph", {"variant": 4, "replicas": 32}, "six links"),
+    ("policy", {"variant": 4, "replicas": 32}, "policy table"),
+])
+def test_wavefront_requirements_checked_before_the_device(lib, samples, opt, needle):
+    s = {"sc4": [sc_periodic(4)], "two": [sc_periodic(4), sc_periodic(4)], "sc5": [sc_periodic(5)],
+         "graph": [random_graph(40, 0.1, 3)],
+         "policy": [sc_periodic(4).with_policy([vg.POLICY_SMALL_STEP], [0.5])]}[samples]
+    st, msg = _create_status(s, **opt)
+    assert st == vb.EINVAL and needle in msg, (st, msg)
+
+
+def test_wavefront_sample_passes_validation(lib):
+    """A periodic even-sided sc lattice with 32 replicas is accepted: without a GPU the
+    create call gets as far as the device query."""
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    st, msg = _create_status([sc_periodic((4, 6, 8))], variant=4, replicas=32)
+    assert st == vb.ECUDA and "no CUDA device" in msg, msg
+
+
 def test_null_safety(lib):
     import ctypes as C
 
