@@ -55,6 +55,7 @@ struct vegas_ctx {
     // device buffers
     void *d_spins = nullptr, *d_edges = nullptr, *d_p0 = nullptr, *d_p1 = nullptr, *d_pk = nullptr;
     int64_t *d_rowptr = nullptr, *d_slot_base = nullptr;
+    uint32_t *d_pass_tickets = nullptr;  // [passes] block counters of the R = 32 staged kernel
     int32_t n_groups = 1;      // type groups of the partial slots (n_types with type_stats)
     int32_t n_types = 0;       // tracked site types (type_stats), else 0
     double *d_type_hist = nullptr;
@@ -162,7 +163,7 @@ void free_all(vegas_ctx *c) {
                     c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog,
                     c->d_insts, c->d_cstart, c->d_queue, c->d_bar, c->d_coop_partial, c->d_acc, c->d_acc_hist,
                     c->d_pol, c->d_pol32, c->d_qis, c->d_sigma, c->d_adapt_n, c->d_type_hist, c->d_snap, c->d_segs,
-                    c->d_tasks, c->d_done, c->d_ticket, c->d_wave_partial, c->d_wave_slot_base, c->d_wave_slot_count};
+                    c->d_tasks, c->d_done, c->d_ticket, c->d_pass_tickets, c->d_wave_partial, c->d_wave_slot_base, c->d_wave_slot_count};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -183,6 +184,7 @@ int ilog2(int v) {
 
 // Launch one MCS: every colour class of every sample, then the reduction.
 void enqueue_mcs(vegas_ctx *c, cudaStream_t st, std::vector<cudaEvent_t> *ev) {
+    cudaMemsetAsync(c->d_pass_tickets, 0, sizeof(uint32_t) * c->passes.size(), st);
     int k = 0;
     for (const PassLaunch &p : c->passes) {
         if (ev) cudaEventRecord((*ev)[2 * k], st);
@@ -725,6 +727,8 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         }
     DALLOC(c->d_partial, sizeof(double) * 4 * (size_t)std::max<int64_t>(slots, 1) * R);
     for (PassLaunch &pl : c->passes) pl.args.partial = c->d_partial + pl.slot * R * 4;
+    DALLOC(c->d_pass_tickets, sizeof(uint32_t) * std::max<size_t>(c->passes.size(), 1));
+    for (size_t k = 0; k < c->passes.size(); ++k) c->passes[k].args.ticket = c->d_pass_tickets + k;
     DALLOC(c->d_slot_base, sizeof(int64_t) * h_sb.size());
     DALLOC(c->d_slot_count, sizeof(int32_t) * h_sc.size());
     H2D(c->d_slot_base, h_sb.data(), sizeof(int64_t) * h_sb.size());

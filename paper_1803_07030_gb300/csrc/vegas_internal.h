@@ -156,6 +156,8 @@ struct PassArgs {
     int32_t lower_mode;        // 0: no link to a lower colour, 1: every link, 2: test each
     int32_t params_mode;       // 0: uniform, no anisotropy; 1: uniform; 2: per site
     int32_t depth;             // staged FP32 kernel: cp.async pipeline depth (2..4); 0 = direct kernel
+    uint32_t *ticket;          // R = 32 staged kernel: next block of 8 sites of this pass (zeroed
+                               // before every MCS); unused by the other kernels
     SiteParams32 u32;
     SiteParams64 u64;
 };

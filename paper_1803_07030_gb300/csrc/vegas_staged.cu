@@ -186,11 +186,13 @@ __global__ void __launch_bounds__(kThreads, D == 2 ? 3 : 2) pass32_staged(const 
 }
 
 // Replica-batched sweep (R = 32): one warp = one site x 32 replicas, depth-2 pipeline. A
-// warp owns blocks of eight consecutive sites (block b starts at g0 + b * bstride); the
-// eight groups of a block are unrolled, so every ring slot and offset is a constant:
-// group j of block b computes from row slot j & 1 and link slot b & 1; at j = 4 the links of
-// the next block are copied; rows of group j + 2 (the next block's first two at j = 6, 7)
-// are copied at the end of group j.
+// warp takes blocks of eight consecutive sites from the pass's ticket counter, so the blocks
+// in flight stay about one per warp and consecutive in memory order however unevenly the
+// warps progress: the neighbour rows they share are still in L2 when the last of them reads
+// them. The eight groups of a block are unrolled, so every ring slot and offset is a
+// constant: group j of a block computes from row slot j & 1 and its link slot; the next
+// ticket is drawn at j = 0 and its block's links copied at j = 4; rows of group j + 2 (the
+// next block's first two at j = 6, 7) are copied at the end of group j.
 // POL = 1 adds the sites' update policies (8 bytes each, staged with the caller ids).
 template <int PM, int LM, int POL>
 __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
@@ -217,9 +219,6 @@ __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
     const float beta = (float)sc[0], B = (float)sc[1];
     const float sigma = (POL && rs_->sigma) ? (float)rs_->sigma[a.inst_local0 + r] : 0.f;
     const int g_end = a.g_end;
-    const int nwarps = blockDim.x >> 5;
-    const int bstride = gridDim.x * nwarps * BS;
-    const int g0 = a.g_begin + (blockIdx.x * nwarps + warp) * BS;
     uint32_t rk0[10], rk1[10];
     {
         uint32_t x = (uint32_t)a.seed, y = (uint32_t)(a.seed >> 32);
@@ -258,19 +257,24 @@ __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
         cp16(dst + DEG * 32, Sr + (int64_t)g * R);
     };
 
-    issue_links(g0, 0);
+    const uint32_t n_blocks = (uint32_t)(g_end - a.g_begin + BS - 1) / BS;  // a ticket past them ends the warp
+    uint32_t tk = 0;
+    if (lane == 0) tk = atomicAdd(a.ticket, 1u);
+    int sb = a.g_begin + (int)min(__shfl_sync(0xFFFFFFFFu, tk, 0), n_blocks) * BS;
+    issue_links(sb, 0);
     cp_commit();
     cp_wait<0>();
     __syncwarp();
-    issue_rows(g0, 0, 0, 0);
+    issue_rows(sb, 0, 0, 0);
     cp_commit();
-    issue_rows(g0 + 1, 0, 1, 1);
+    issue_rows(sb + 1, 0, 1, 1);
     cp_commit();
     Acc32 acc;
     bool nan_seen = false;
     const bool log_accepts = a.alog && t < a.alog_mcs;
     int ls = 0;
-    for (int sb = g0; sb < g_end; sb += bstride, ls ^= 1) {
+    while (sb < g_end) {
+        int sb2 = g_end;  // the next block (drawn at j = 0, known from j = 4)
 #pragma unroll
         for (int j = 0; j < BS; ++j) {
             cp_wait<D - 1>();
@@ -285,13 +289,19 @@ __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
                                                  (const PolicySite32 *)(slot + POL_OFF) + j, sigma);
             }
             __syncwarp();
-            if (j == 4) issue_links(sb + bstride, ls ^ 1);
+            if (j == 0 && lane == 0) tk = atomicAdd(a.ticket, 1u);
+            if (j == 4) {
+                sb2 = a.g_begin + (int)min(__shfl_sync(0xFFFFFFFFu, tk, 0), n_blocks) * BS;
+                issue_links(sb2, ls ^ 1);
+            }
             if (j + 2 < BS)
                 issue_rows(sb + j + 2, ls, j + 2, j & 1);
             else
-                issue_rows(sb + bstride + j + 2 - BS, ls ^ 1, j + 2 - BS, j & 1);
+                issue_rows(sb2 + j + 2 - BS, ls ^ 1, j + 2 - BS, j & 1);
             cp_commit();
         }
+        sb = sb2;
+        ls ^= 1;
     }
     cp_wait<0>();
     if (nan_seen) atomicOr(a.err, kErrNaN);
