@@ -420,7 +420,7 @@ def run_workload(args):
         "clocks": clk.summary(),
     }
     ctx.close()
-    if args.workload == "np256" and not policy and not args.type_stats and not args.snapshots:
+    if args.workload == "np256" and not policy and not args.type_stats and not args.snapshots and not args.quick:
         plain_mcs = min(w.mcs, 100)
         plain_ms, plain_att = 0.0, 0
         for p, smp in enumerate(w.samples):
