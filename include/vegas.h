@@ -127,16 +127,18 @@ typedef struct {
     int32_t inst_base;      /* id of the first instance. Default 0. */
     int32_t device;         /* CUDA device ordinal, -1 = current. Default -1. */
     void *cuda_stream;      /* cudaStream_t to run on, NULL = a stream of the library */
-    int32_t variant;        /* -1 automatic (timed on the first run), 0 one launch per colour
+    int32_t variant;        /* -1 automatic: the first run times each eligible sweep and block
+                               shape on a few MCS of the real chain and keeps the fastest
+                               (vegas_stats reports the choice); 0 one launch per colour
                                class, 1 resident: one persistent launch per step, a block per
                                instance (FP32), 2 cooperative: one launch per step, all blocks
                                sweep one sample class by class (FP32, one sample, no adaptive
                                policy), 3 cluster: one persistent launch per step, a thread-
                                block cluster of 2 .. 16 blocks per instance, the blocks meeting at
                                the hardware cluster barrier between colour classes (FP32),
-                               4 wavefront: one cooperative launch per MCS runs both colour
-                               classes, a block of class-1 sites starting once the class-0
-                               blocks it links to have finished (FP32, one sample, 32
+                               4 wavefront: one launch per MCS runs both colour classes,
+                               a block of class-1 sites starting once the class-0 blocks
+                               it links to have finished (FP32, one sample, 32
                                replicas, two colour classes, six links per site, no policy
                                table, no per-type statistics; sites are stored plane by plane
                                when positions are given). Variant 4 is used only when asked
@@ -191,6 +193,10 @@ typedef struct {
     int32_t n_types;            /* site types tracked per instance (type_stats), else 0 */
     int32_t pad_;
     int64_t snapshot_steps;     /* steps with a stored final state per instance (snapshots) */
+    int32_t block_threads;      /* threads per block of the sweep in use (the resident sweep's
+                                   is chosen by the autotuner: 256 or 512) */
+    int32_t cluster_blocks;     /* blocks per cluster of the cluster sweep when it is in use
+                                   (chosen by the autotuner), else 0 */
 } vegas_stats_t;
 
 /* Fills *opt with the defaults listed above. */

@@ -86,6 +86,8 @@ struct vegas_ctx {
     uint32_t *d_queue = nullptr;
     ResidentArgs res{};
     int res_threads = 256, res_grid = 1;
+    int res_items = 0;          // instances of the resident and cluster sweeps
+    bool res_policy = false;    // some sample has a policy table (kernel choice for the shapes)
     bool res_eligible = false, tuned = false;
     int32_t max_instance_sites = 0;
     double tune_ms[4] = {0.0, 0.0, 0.0, 0.0};  // per-MCS time of each sweep when tuned
@@ -180,6 +182,24 @@ int ilog2(int v) {
     int l = 0;
     while ((1 << l) < v) ++l;
     return l;
+}
+
+// Block shape of the resident sweep: threads per block, and as many blocks as fit (at most one
+// per instance).
+void set_resident_shape(vegas_ctx *c, int threads) {
+    c->res_threads = threads;
+    c->res_grid = (int)std::min<int64_t>((int64_t)c->res_items,
+                                         (int64_t)c->sm_count * resident_blocks_per_sm(threads, c->res_policy));
+}
+
+// Cluster size of the cluster sweep (blocks of cluster_threads); false if no such cluster fits.
+bool set_cluster_shape(vegas_ctx *c, int cs) {
+    const int cap = cluster_capacity(cs, c->cluster_threads, c->res_policy);
+    cudaGetLastError();
+    if (cap <= 0) return false;
+    c->cluster_cs = cs;
+    c->cluster_n = (int)std::min<int64_t>((int64_t)c->res_items, cap);
+    return true;
 }
 
 // Launch one MCS: every colour class of every sample, then the reduction.
@@ -785,9 +805,9 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         H2D(c->d_insts, insts.data(), sizeof(ResidentInst) * insts.size());
         H2D(c->d_cstart, h_cs.data(), sizeof(int32_t) * h_cs.size());
         if (!h_segs.empty()) H2D(c->d_segs, h_segs.data(), sizeof(int4) * h_segs.size());
-        c->res_threads = c->max_instance_sites >= 4096 ? 512 : 256;
-        c->res_grid = (int)std::min<int64_t>((int64_t)insts.size(),
-                                             (int64_t)c->sm_count * resident_blocks_per_sm(c->res_threads, any_policy));
+        c->res_items = (int)insts.size();
+        c->res_policy = any_policy;
+        set_resident_shape(c, c->max_instance_sites >= 4096 ? 512 : 256);
         ResidentArgs &ra = c->res;
         std::memset(&ra, 0, sizeof ra);
         ra.spins = c->d_spins;
@@ -828,9 +848,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
             }
             c->cluster_threads = nt;
             if (cap > 0) {
-                c->cluster_cs = cs;
-                c->cluster_n = (int)std::min<int64_t>((int64_t)insts.size(), cap);
-                c->cluster_eligible = true;
+                c->cluster_eligible = set_cluster_shape(c, cs);
             }
             cudaGetLastError();  // an unsupported cluster shape only makes the sweep ineligible
         }
@@ -1176,17 +1194,30 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
     for (int32_t s = 0; s < n_steps; ++s) {
         int32_t m0 = 0;
         if (!c->tuned && mcs >= 2) {
-            // autotune: time a few MCS of each eligible sweep on the real chain (all give the
-            // same spins) and keep the fastest for this context
-            std::vector<int> cand{0};
-            if (c->res_eligible) cand.push_back(1);
-            if (c->coop_eligible) cand.push_back(2);
-            if (c->cluster_eligible) cand.push_back(3);
+            // autotune: time a few MCS of each eligible sweep and block shape on the real chain
+            // (all give the same spins) and keep the fastest for this context. Shapes: threads
+            // per block of the resident sweep (so sites per thread), blocks per cluster of the
+            // cluster sweep.
+            std::vector<std::pair<int, int>> cand{{0, 0}};
+            if (c->res_eligible) {
+                cand.push_back({1, 256});
+                cand.push_back({1, 512});
+            }
+            if (c->coop_eligible) cand.push_back({2, 0});
+            if (c->cluster_eligible) {
+                const int cs0 = c->cluster_cs;
+                cand.push_back({3, cs0});
+                if (cs0 / 2 >= 2) cand.push_back({3, cs0 / 2});
+            }
             const int32_t probe = std::max(1, std::min(4, mcs / (2 * (int32_t)cand.size())));
             if (probe * (int32_t)cand.size() <= mcs) {
                 float best = 0.f;
-                int best_v = c->variant;
-                for (int v : cand) {
+                int best_v = c->variant, best_shape = 0;
+                const int cs_rule = c->cluster_cs, rt_rule = c->res_threads;
+                for (const auto &vc : cand) {
+                    const int v = vc.first;
+                    if (v == 1) set_resident_shape(c, vc.second);
+                    if (v == 3 && !set_cluster_shape(c, vc.second)) continue;
                     cudaEvent_t x0, x1;
                     CK(c, cudaEventCreate(&x0));
                     CK(c, cudaEventCreate(&x1));
@@ -1198,11 +1229,12 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     CK(c, cudaEventElapsedTime(&ms, x0, x1));
                     cudaEventDestroy(x0);
                     cudaEventDestroy(x1);
-                    c->tune_ms[v] = ms / probe;
+                    if (c->tune_ms[v] == 0.0 || ms / probe < c->tune_ms[v]) c->tune_ms[v] = ms / probe;
                     sweep_ms += ms;
-                    if (v == cand[0] || ms < best) {
+                    if (v == cand[0].first || ms < best) {
                         best = ms;
                         best_v = v;
+                        best_shape = vc.second;
                     }
                     m0 += probe;
                     uint32_t e4 = 0;
@@ -1210,6 +1242,8 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     if (e4) break;  // report the device error below
                 }
                 c->variant = best_v;
+                set_resident_shape(c, best_v == 1 ? best_shape : rt_rule);
+                if (c->cluster_eligible) set_cluster_shape(c, best_v == 3 ? best_shape : cs_rule);
             }
             c->tuned = true;
         }
@@ -1505,6 +1539,8 @@ extern "C" vegas_status vegas_stats(const vegas_ctx *c, vegas_stats_t *o) {
     o->device_bytes = c->device_bytes;
     o->n_types = c->n_types;
     o->snapshot_steps = c->snapshot_steps;
+    o->block_threads = c->variant == 1 ? c->res_threads : (c->variant == 3 ? c->cluster_threads : kThreads);
+    o->cluster_blocks = c->variant == 3 ? c->cluster_cs : 0;
     return VEGAS_OK;
 }
 

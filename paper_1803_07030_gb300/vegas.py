@@ -90,6 +90,8 @@ class vegas_stats_t(C.Structure):
         ("n_types", C.c_int32),
         ("pad_", C.c_int32),
         ("snapshot_steps", C.c_int64),
+        ("block_threads", C.c_int32),
+        ("cluster_blocks", C.c_int32),
     ]
 
 

@@ -287,6 +287,33 @@ def test_cooperative_barrier_timeout_is_reported_not_hung():
         assert e2.value.status == vb.ESTATE
 
 
+def test_autotuner_picks_a_sweep_and_block_shape():
+    """The first run times every eligible sweep and block shape (threads per block of the
+    resident sweep, blocks per cluster of the cluster sweep) on the real chain; whatever it
+    keeps, the chain is the per-class sweep's bit for bit, and the stats name the shape."""
+    ps = nanoparticle_batch(12, seed=9, r_max=6.5)
+    T = np.linspace(0.4, 2.0, len(ps))[:, None]
+    B = np.full_like(T, 0.1)
+    with ctx(ps, seed=24, variant=-1) as a, ctx(ps, seed=24, variant=0) as b:
+        a.run(T, B, 40)
+        b.run(T, B, 40)
+        st = a.stats()
+        assert st["variant"] in (0, 1, 2, 3)
+        if st["variant"] == 1:
+            assert st["block_threads"] in (256, 512) and st["cluster_blocks"] == 0
+        elif st["variant"] == 3:
+            assert st["cluster_blocks"] >= 2 and st["block_threads"] == 256
+        else:
+            assert st["block_threads"] == 256 and st["cluster_blocks"] == 0
+        for i in range(len(ps)):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+        a.run(T, B, 10)  # the chosen shape keeps serving later runs (step graphs included)
+        b.run(T, B, 10)
+        assert a.stats()["variant"] == st["variant"] and a.stats()["block_threads"] == st["block_threads"]
+        for i in range(len(ps)):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+
+
 def test_autotuner_three_way():
     s = sc_periodic(10, k_uni=0.1)
     with ctx([s], seed=23, variant=-1) as a, ctx([s], seed=23, variant=0) as b:
