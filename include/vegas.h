@@ -146,7 +146,10 @@ typedef struct {
     int32_t accept_log_mcs; /* > 0: keep the accept/reject bit of every attempt of the
                                first accept_log_mcs MCS (debugging and parity). Default 0. */
     int32_t timing;         /* 1: time every sweep launch with CUDA events. Default 0. */
-    int32_t graphs;         /* 1: replay the per-MCS launches as a CUDA graph. Default 1. */
+    int32_t graphs;         /* 1: launch the sweeps as CUDA graphs: a whole run of the per-class
+                               sweep as one graph (a conditional while node over its
+                               temperature/field steps), the other sweeps one graph per step;
+                               2: one graph per step for every sweep; 0: no graphs. Default 1. */
     int32_t max_blocks;     /* > 0: at most this many thread blocks per sweep launch (tests,
                                tuning); 0 = as many as fit on the device. Default 0. */
     int32_t pipeline_depth; /* FP32 sweeps of rows with six links: groups of rows kept in
@@ -197,6 +200,9 @@ typedef struct {
                                    is chosen by the autotuner: 256 or 512) */
     int32_t cluster_blocks;     /* blocks per cluster of the cluster sweep when it is in use
                                    (chosen by the autotuner), else 0 */
+    int64_t graph_launches;     /* CUDA graph launches so far: with graphs = 1 a run of the
+                                   per-class sweep is one launch of a graph whose conditional
+                                   while node repeats one temperature/field step */
 } vegas_stats_t;
 
 /* Fills *opt with the defaults listed above. */

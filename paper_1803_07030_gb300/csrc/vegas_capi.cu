@@ -112,6 +112,11 @@ struct vegas_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<std::pair<int64_t, cudaGraphExec_t>> step_graphs;  // key: mcs * 2 + variant
+    // run graphs of the per-class sweep: a conditional while node over temperature/field steps
+    // whose body is one whole step; key: mcs
+    std::vector<std::pair<int64_t, cudaGraphExec_t>> run_graphs;
+    std::vector<cudaGraph_t> run_graph_defs;
+    bool run_graph_failed = false;
     // host state
     std::vector<std::vector<double>> hist;  // per instance: records * 4
     std::vector<std::vector<uint32_t>> acc_hist;  // per instance: accepted attempts per record
@@ -121,7 +126,7 @@ struct vegas_ctx {
     int64_t records = 0;
     uint32_t t = 0;
     uint32_t device_error = 0;
-    int64_t kernel_launches = 0, sweep_launches = 0;
+    int64_t kernel_launches = 0, sweep_launches = 0, graph_launches = 0;
     double sweep_ms = 0.0, last_run_ms = 0.0;
     int variant = 0;
     bool poisoned = false;
@@ -159,6 +164,8 @@ cudaError_t dalloc(vegas_ctx *c, T **p, size_t bytes) {
 
 void free_all(vegas_ctx *c) {
     for (auto &kv : c->step_graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : c->run_graphs) cudaGraphExecDestroy(kv.second);
+    for (cudaGraph_t g : c->run_graph_defs) cudaGraphDestroy(g);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
     void *bufs[] = {c->d_spins, c->d_edges, c->d_p0, c->d_p1, c->d_pk, c->d_rowptr, c->d_slot_base, c->d_orig,
@@ -204,7 +211,6 @@ bool set_cluster_shape(vegas_ctx *c, int cs) {
 
 // Launch one MCS: every colour class of every sample, then the reduction.
 void enqueue_mcs(vegas_ctx *c, cudaStream_t st, std::vector<cudaEvent_t> *ev) {
-    cudaMemsetAsync(c->d_pass_tickets, 0, sizeof(uint32_t) * c->passes.size(), st);
     int k = 0;
     for (const PassLaunch &p : c->passes) {
         if (ev) cudaEventRecord((*ev)[2 * k], st);
@@ -215,8 +221,9 @@ void enqueue_mcs(vegas_ctx *c, cudaStream_t st, std::vector<cudaEvent_t> *ev) {
         if (ev) cudaEventRecord((*ev)[2 * k + 1], st);
         ++k;
     }
+    // the reduction also zeroes the R = 32 kernel's block counters for the next MCS
     ReduceArgs ra{c->d_partial, c->d_slot_base, c->d_slot_count, c->d_run, c->d_adapt_n, c->R, c->n_inst,
-                  c->n_groups, c->n_types};
+                  c->n_groups, c->n_types, c->d_pass_tickets, (int32_t)c->passes.size()};
     launch_reduce(ra, st);
 }
 
@@ -253,7 +260,7 @@ int enqueue_wave(vegas_ctx *c, cudaStream_t st) {
     cudaMemsetAsync(c->d_ticket, 0, sizeof(uint32_t), st);
     const int e = launch_wave(c->wave, c->wave_grid, st);
     ReduceArgs ra{c->d_wave_partial, c->d_wave_slot_base, c->d_wave_slot_count, c->d_run, c->d_adapt_n, c->R,
-                  c->n_inst, 1, 0};
+                  c->n_inst, 1, 0, nullptr, 0};
     launch_reduce(ra, st);
     return e;
 }
@@ -309,6 +316,59 @@ vegas_status step_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
     c->step_graphs.emplace_back(key, ge);
     *out = ge;
     return VEGAS_OK;
+}
+
+// Graph of a whole run of the per-class sweep: a conditional while node whose body is one
+// temperature/field step (mcs MCS, the renormalisation, the snapshot) followed by the loop
+// control kernel, so one launch runs every step of the schedule (the step index, schedule
+// and record count come from the run state). Returns false, leaving no capture open, when
+// the device or driver cannot build it; the caller then launches the step graph per step.
+bool run_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
+    for (auto &kv : c->run_graphs)
+        if (kv.first == mcs) {
+            *out = kv.second;
+            return true;
+        }
+    if (c->run_graph_failed) return false;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    bool capturing = false;
+    auto give_up = [&]() {
+        if (capturing) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(c->cap_stream, &junk);
+            if (junk) cudaGraphDestroy(junk);
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        c->run_graph_failed = true;
+        return false;
+    };
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return give_up();
+    cudaGraphConditionalHandle loop;
+    if (cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) return give_up();
+    cudaGraphNodeParams wp = {cudaGraphNodeTypeConditional};  // the other members zero
+    wp.conditional.handle = loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    if (cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp) != cudaSuccess) return give_up();
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+        return give_up();
+    capturing = true;
+    for (int32_t m = 0; m < mcs; ++m) enqueue_mcs(c, c->cap_stream, nullptr);
+    enqueue_renorm(c, c->cap_stream);
+    launch_run_ctrl(c->d_run, (unsigned long long)loop, c->cap_stream);
+    cudaGraph_t captured = nullptr;
+    capturing = false;
+    if (cudaStreamEndCapture(c->cap_stream, &captured) != cudaSuccess) return give_up();
+    if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) return give_up();
+    c->run_graph_defs.push_back(g);
+    c->run_graphs.emplace_back(mcs, ge);
+    *out = ge;
+    return true;
 }
 
 vegas_status build_graph(vegas_ctx *c) {
@@ -378,6 +438,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     if (o.variant == 3 && o.precision != 32)
         return fail(nullptr, VEGAS_EINVAL, "the cluster sweep (variant 3) is FP32 only");
     if (o.timeout_ns < 0 || o.fault_inject < 0 || o.fault_inject > 1) return fail(nullptr, VEGAS_EINVAL, "bad timeout or fault_inject");
+    if (o.graphs < 0 || o.graphs > 2) return fail(nullptr, VEGAS_EINVAL, "graphs must be 0, 1 or 2");
     if (o.type_stats < 0 || o.type_stats > 1 || o.snapshots < 0 || o.snapshots > 1)
         return fail(nullptr, VEGAS_EINVAL, "type_stats and snapshots must be 0 or 1");
     if (o.variant == 2 && o.type_stats)
@@ -748,6 +809,11 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     DALLOC(c->d_partial, sizeof(double) * 4 * (size_t)std::max<int64_t>(slots, 1) * R);
     for (PassLaunch &pl : c->passes) pl.args.partial = c->d_partial + pl.slot * R * 4;
     DALLOC(c->d_pass_tickets, sizeof(uint32_t) * std::max<size_t>(c->passes.size(), 1));
+    if (cudaMemsetAsync(c->d_pass_tickets, 0, sizeof(uint32_t) * std::max<size_t>(c->passes.size(), 1), c->stream) !=
+        cudaSuccess) {
+        c->err = "memset failed";
+        return bail(VEGAS_ECUDA);
+    }
     for (size_t k = 0; k < c->passes.size(); ++k) c->passes[k].args.ticket = c->d_pass_tickets + k;
     DALLOC(c->d_slot_base, sizeof(int64_t) * h_sb.size());
     DALLOC(c->d_slot_count, sizeof(int32_t) * h_sc.size());
@@ -1109,9 +1175,10 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
     rs.acc_hist = c->d_acc_hist;
     rs.sigma = c->d_sigma;
     rs.type_hist = c->n_types > 0 ? c->d_type_hist : nullptr;
+    rs.rec_end = (uint32_t)nrec;
     CK(c, cudaMemcpyAsync(c->d_run, &rs, sizeof rs, cudaMemcpyHostToDevice, c->stream));
 
-    const bool use_graph = c->opt.graphs && !c->opt.timing;
+    const bool use_graph = c->opt.graphs != 0 && !c->opt.timing;
     if (use_graph && (st = build_graph(c)) != VEGAS_OK) return st;
     std::vector<cudaEvent_t> ev;
     if (c->opt.timing) {
@@ -1129,6 +1196,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
         for (int32_t m = m0; m < m0 + n; ++m) {
             if (use_graph) {
                 CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
+                c->graph_launches++;
             } else if (c->opt.timing) {
                 std::vector<cudaEvent_t> sub(ev.begin() + (size_t)m * 2 * c->passes.size(),
                                              ev.begin() + (size_t)(m + 1) * 2 * c->passes.size());
@@ -1248,11 +1316,24 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             c->tuned = true;
         }
 
+        if (m0 == 0 && c->tuned && use_graph && c->opt.graphs == 1 && c->variant == 0 && step_graph_nodes(c, mcs) > 0) {
+            // every remaining step in one launch of the run graph
+            cudaGraphExec_t ge;
+            if (run_graph(c, mcs, &ge)) {
+                CK(c, cudaGraphLaunch(ge, c->stream));
+                c->graph_launches++;
+                const int64_t left = n_steps - s;
+                c->kernel_launches += left * (step_graph_nodes(c, mcs) + 1);
+                c->sweep_launches += left * (int64_t)mcs * (int64_t)c->passes.size();
+                break;
+            }
+        }
         if (m0 == 0 && c->tuned && use_graph && c->variant < 2 && step_graph_nodes(c, mcs) > 0) {
             // the whole step as one graph (the cooperative and cluster launches stay direct launches)
             cudaGraphExec_t ge;
             if ((st = step_graph(c, mcs, &ge)) != VEGAS_OK) return st;
             CK(c, cudaGraphLaunch(ge, c->stream));
+            c->graph_launches++;
             const int64_t nodes = step_graph_nodes(c, mcs);
             c->kernel_launches += c->variant >= 1 ? 3 + (c->opt.snapshots ? 1 : 0) : nodes;
             c->sweep_launches += c->variant >= 1 ? 1 : (int64_t)mcs * (int64_t)c->passes.size();
@@ -1541,6 +1622,7 @@ extern "C" vegas_status vegas_stats(const vegas_ctx *c, vegas_stats_t *o) {
     o->snapshot_steps = c->snapshot_steps;
     o->block_threads = c->variant == 1 ? c->res_threads : (c->variant == 3 ? c->cluster_threads : kThreads);
     o->cluster_blocks = c->variant == 3 ? c->cluster_cs : 0;
+    o->graph_launches = c->graph_launches;
     return VEGAS_OK;
 }
 

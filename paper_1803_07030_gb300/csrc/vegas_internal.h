@@ -120,6 +120,8 @@ struct RunState {
     uint32_t *acc_hist;   // [records][n_inst] accepted attempts per MCS
     double *sigma;        // [n_inst] width of the adaptive policy, or NULL
     double *type_hist;    // [records][n_inst][n_types][3] magnetization per site type, or NULL
+    uint32_t rec_end;     // records of the current run (n_steps * mcs): where the run graph stops
+    uint32_t pad_;
 };
 
 // One colour class of one sample: everything a sweep launch needs.
@@ -157,7 +159,7 @@ struct PassArgs {
     int32_t params_mode;       // 0: uniform, no anisotropy; 1: uniform; 2: per site
     int32_t depth;             // staged FP32 kernel: cp.async pipeline depth (2..4); 0 = direct kernel
     uint32_t *ticket;          // R = 32 staged kernel: next block of 8 sites of this pass (zeroed
-                               // before every MCS); unused by the other kernels
+                               // by the MCS's reduction); unused by the other kernels
     SiteParams32 u32;
     SiteParams64 u64;
 };
@@ -173,6 +175,8 @@ struct ReduceArgs {
     int32_t R, n_inst;
     int32_t n_groups;          // type groups per sample (1 without per-type statistics)
     int32_t n_types;           // > 0: write the magnetization of each group to run->type_hist
+    uint32_t *tickets;         // block counters of the MCS's passes, zeroed here for the next MCS, or NULL
+    int32_t n_tickets;
 };
 
 struct RenormArgs {
@@ -304,6 +308,9 @@ int pass_blocks_per_sm(int precision, const PassArgs &a);
 void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream);
 // Adds n to the run state's MCS counter and record index (after a resident launch).
 void launch_advance(RunState *run, int32_t n, void *stream);
+// Loop control of the run graph (a conditional while node over temperature/field steps):
+// sets the node's handle to 1 while the run has records left (run->rec < run->rec_end).
+void launch_run_ctrl(const RunState *run, unsigned long long loop_handle, void *stream);
 // Copies the spins into the snapshot slot of the step that just ended (read from the run state).
 void launch_snapshot(const void *spins, void *snap, int64_t n16, const RunState *run, int grid, void *stream);
 

@@ -799,12 +799,15 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
 // ------------------------------------------------------------------ per-MCS reduction
 // One warp per instance sums its sample's block partials over every colour class in a
 // fixed order and appends the record; the last block to finish advances the MCS
-// counter and the record index (no waiting: a ticket counter, not a barrier).
+// counter and the record index (no waiting: a ticket counter, not a barrier). Block 0 also
+// zeroes the passes' block counters: every pass of this MCS has finished.
 __global__ void __launch_bounds__(256) reduce_kernel(const ReduceArgs a) {
     RunState *rs = a.run;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int il = blockIdx.x * 8 + warp;
     const uint32_t rec = rs->rec;
+    if (blockIdx.x == 0 && a.tickets)
+        for (int k = threadIdx.x; k < a.n_tickets; k += blockDim.x) a.tickets[k] = 0u;
     if (il < a.n_inst) {
         const int s = il / a.R, r = il % a.R;
         double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -1017,6 +1020,16 @@ __global__ void advance_kernel(RunState *run, int32_t n) {
 }
 
 void launch_advance(RunState *run, int32_t n, void *stream) { advance_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(run, n); }
+
+// Runs after a step's last MCS and renormalisation inside the run graph: another step while
+// records are left in the run.
+__global__ void run_ctrl_kernel(const RunState *run, cudaGraphConditionalHandle loop) {
+    cudaGraphSetConditional(loop, run->rec < run->rec_end ? 1u : 0u);
+}
+
+void launch_run_ctrl(const RunState *run, unsigned long long loop_handle, void *stream) {
+    run_ctrl_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(run, (cudaGraphConditionalHandle)loop_handle);
+}
 
 // Copies the spins (n16 16-byte words) into slot (rec / mcs - 1) of the snapshot buffer: the
 // step whose last MCS and renormalisation just ran.

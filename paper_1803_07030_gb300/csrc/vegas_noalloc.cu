@@ -201,7 +201,7 @@ extern "C" vegas_status vegas_sweep_noalloc(void *spins, const void *links, cons
         launch_pass32(a, grids[c], st);
         slot += grids[c];
     }
-    ReduceArgs ra{partial, hdr->slot_base, hdr->slot_count, &hdr->run, nullptr, replicas, replicas, 1, 0};
+    ReduceArgs ra{partial, hdr->slot_base, hdr->slot_count, &hdr->run, nullptr, replicas, replicas, 1, 0, nullptr, 0};
     launch_reduce(ra, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("launch: ") + cudaGetErrorString(e));

@@ -92,6 +92,7 @@ class vegas_stats_t(C.Structure):
         ("snapshot_steps", C.c_int64),
         ("block_threads", C.c_int32),
         ("cluster_blocks", C.c_int32),
+        ("graph_launches", C.c_int64),
     ]
 
 
@@ -412,7 +413,7 @@ class Context:
 
     def __init__(self, samples: Sequence, precision: int = 32, replicas: int = 1, seed: int = 1,
                  inst_base: int = 0, device: int = -1, stream="torch", variant: int = -1,
-                 accept_log_mcs: int = 0, timing: bool = False, graphs: bool = True, max_blocks: int = 0,
+                 accept_log_mcs: int = 0, timing: bool = False, graphs: int = 1, max_blocks: int = 0,
                  pipeline_depth: int = 0, timeout_ns: int = 0, fault_inject: int = 0,
                  type_stats: bool = False, snapshots: bool = False, wave_lag: int = 0,
                  library: Optional[str] = None):
@@ -430,7 +431,7 @@ class Context:
         o.variant = variant
         o.accept_log_mcs = accept_log_mcs
         o.timing = 1 if timing else 0
-        o.graphs = 1 if graphs else 0
+        o.graphs = int(graphs)  # True = 1: a run as one graph; 2: a graph per step; False = 0
         o.max_blocks = max_blocks
         o.pipeline_depth = pipeline_depth
         o.timeout_ns = timeout_ns

@@ -287,6 +287,36 @@ def test_cooperative_barrier_timeout_is_reported_not_hung():
         assert e2.value.status == vb.ESTATE
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+def test_whole_run_is_one_graph_launch(precision):
+    """With graphs on, a run of the per-class sweep is one launch of a graph whose conditional
+    while node repeats one temperature/field step; spins, history and snapshots equal the
+    launch-by-launch path, and later runs with other step counts reuse the graph."""
+    s = sc_periodic(6, k_uni=0.1)
+    T = np.array([[2.0, 1.5, 1.0, 0.7, 0.5]])
+    B = np.array([[0.2, 0.1, 0.0, -0.1, -0.2]])
+    with ctx([s], precision=precision, seed=27, variant=0, snapshots=True) as a, \
+            ctx([s], precision=precision, seed=27, variant=0, snapshots=True, graphs=False) as b, \
+            ctx([s], precision=precision, seed=27, variant=0, snapshots=True, graphs=2) as c:
+        g0 = a.stats()["graph_launches"]
+        a.run(T, B, 7)
+        assert a.stats()["graph_launches"] == g0 + 1
+        a.run(T[:, :2], B[:, :2], 7)
+        assert a.stats()["graph_launches"] == g0 + 2
+        b.run(T, B, 7)
+        b.run(T[:, :2], B[:, :2], 7)
+        assert b.stats()["graph_launches"] == 0
+        c.run(T, B, 7)
+        c.run(T[:, :2], B[:, :2], 7)
+        assert c.stats()["graph_launches"] == 7  # one per step
+        assert np.array_equal(c.spins(0), b.spins(0)) and np.array_equal(c.history(), b.history())
+        assert np.array_equal(a.spins(0), b.spins(0))
+        assert np.array_equal(a.history(), b.history())
+        assert np.array_equal(a.accept_history(), b.accept_history())
+        for k in range(7):
+            assert np.array_equal(a.snapshot(0, k), b.snapshot(0, k)), k
+
+
 def test_autotuner_picks_a_sweep_and_block_shape():
     """The first run times every eligible sweep and block shape (threads per block of the
     resident sweep, blocks per cluster of the cluster sweep) on the real chain; whatever it
