@@ -416,7 +416,9 @@ def run_workload(args):
                    "l2": "working set inside L2" if w.n_sites_total * 16 < 100e6 else "larger than L2",
                    "policy": policy or "random", "type_stats": bool(args.type_stats),
                    "snapshots": bool(args.snapshots)},
-        "variant": st1["variant"], "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
+        "variant": st1["variant"], "block_threads": st1["block_threads"], "cluster_blocks": st1["cluster_blocks"],
+        "split_sites": st1["split_sites"],
+        "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
         "clocks": clk.summary(),
     }
     ctx.close()

@@ -172,6 +172,13 @@ typedef struct {
                                final state per step), read with vegas_get_snapshot. Costs a
                                device copy of the spins per step and host memory for all of
                                them. Default 0. */
+    int32_t cluster_blocks; /* cluster sweep (variant 3): blocks per cluster, 2 .. 16;
+                               0 = by instance size (about 2048 sites per block) */
+    int32_t cluster_threads;/* cluster sweep: threads per block, 256 or 512; 0 = 256 */
+    int32_t cluster_split;  /* cluster sweep (variant 3): instances of at most this many sites
+                               are swept by one block each, larger ones by a whole cluster;
+                               0 = every instance by a cluster. The automatic choice (variant
+                               -1) picks its own. Default 0. */
     int32_t wave_lag;       /* wavefront sweep: a class-1 block is queued this many class-0
                                blocks after the last class-0 block it links to, so that its
                                dependencies have usually finished when a warp reaches it;
@@ -203,6 +210,10 @@ typedef struct {
     int64_t graph_launches;     /* CUDA graph launches so far: with graphs = 1 a run of the
                                    per-class sweep is one launch of a graph whose conditional
                                    while node repeats one temperature/field step */
+    int32_t split_sites;        /* cluster sweep in use: instances of at most this many sites
+                                   are swept by one block each, larger ones by a whole cluster
+                                   (chosen by the autotuner; 0 = every instance by a cluster) */
+    int32_t pad2_;
 } vegas_stats_t;
 
 /* Fills *opt with the defaults listed above. */

@@ -199,13 +199,17 @@ void set_resident_shape(vegas_ctx *c, int threads) {
                                          (int64_t)c->sm_count * resident_blocks_per_sm(threads, c->res_policy));
 }
 
-// Cluster size of the cluster sweep (blocks of cluster_threads); false if no such cluster fits.
-bool set_cluster_shape(vegas_ctx *c, int cs) {
-    const int cap = cluster_capacity(cs, c->cluster_threads, c->res_policy);
+// Shape of the cluster sweep: cs blocks of `threads` per cluster, as many clusters as fit,
+// and instances of at most `split` sites swept by one block each (0: all by clusters);
+// false (shape unchanged) if no such cluster fits.
+bool set_cluster_shape(vegas_ctx *c, int cs, int threads, int split = 0) {
+    const int cap = cluster_capacity(cs, threads, c->res_policy);
     cudaGetLastError();
     if (cap <= 0) return false;
     c->cluster_cs = cs;
+    c->cluster_threads = threads;
     c->cluster_n = (int)std::min<int64_t>((int64_t)c->res_items, cap);
+    c->res.split_sites = split;
     return true;
 }
 
@@ -415,6 +419,9 @@ extern "C" void vegas_default_options(vegas_options *o) {
     o->fault_inject = 0;
     o->type_stats = 0;
     o->snapshots = 0;
+    o->cluster_blocks = 0;
+    o->cluster_threads = 0;
+    o->cluster_split = 0;
     o->wave_lag = 0;
 }
 
@@ -435,6 +442,11 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         return fail(nullptr, VEGAS_EINVAL,
                     "the wavefront sweep (variant 4) is FP32 with one sample, 32 replicas and no per-type statistics");
     if (o.wave_lag < 0) return fail(nullptr, VEGAS_EINVAL, "wave_lag must be >= 0");
+    if (o.cluster_split < 0) return fail(nullptr, VEGAS_EINVAL, "cluster_split must be >= 0");
+    if (o.cluster_blocks != 0 && (o.cluster_blocks < 2 || o.cluster_blocks > 16))
+        return fail(nullptr, VEGAS_EINVAL, "cluster_blocks must be 0 or 2 .. 16");
+    if (o.cluster_threads != 0 && o.cluster_threads != 256 && o.cluster_threads != 512)
+        return fail(nullptr, VEGAS_EINVAL, "cluster_threads must be 0, 256 or 512");
     if (o.variant == 3 && o.precision != 32)
         return fail(nullptr, VEGAS_EINVAL, "the cluster sweep (variant 3) is FP32 only");
     if (o.timeout_ns < 0 || o.fault_inject < 0 || o.fault_inject > 1) return fail(nullptr, VEGAS_EINVAL, "bad timeout or fault_inject");
@@ -906,15 +918,16 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         if (c->n_types <= 8) {
             int cs = 2;
             while (cs < 16 && (int64_t)cs * 2048 < c->max_instance_sites) cs *= 2;
-            const int nt = 256;
+            const int nt = o.cluster_threads > 0 ? o.cluster_threads : 256;
+            if (o.cluster_blocks > 0) cs = o.cluster_blocks;
             int cap = cluster_capacity(cs, nt, any_policy);
-            if (cap == 0 && cs == 16) {
+            if (cap == 0 && cs == 16 && o.cluster_blocks == 0) {
                 cs = 8;
                 cap = cluster_capacity(cs, nt, any_policy);
             }
             c->cluster_threads = nt;
             if (cap > 0) {
-                c->cluster_eligible = set_cluster_shape(c, cs);
+                c->cluster_eligible = set_cluster_shape(c, cs, nt, o.cluster_split);
             }
             cudaGetLastError();  // an unsupported cluster shape only makes the sweep ineligible
         }
@@ -1266,26 +1279,37 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             // (all give the same spins) and keep the fastest for this context. Shapes: threads
             // per block of the resident sweep (so sites per thread), blocks per cluster of the
             // cluster sweep.
-            std::vector<std::pair<int, int>> cand{{0, 0}};
+            struct Cand {
+                int v, a, b, split;  // sweep; threads (resident) or blocks per cluster, threads
+            };
+            std::vector<Cand> cand{{0, 0, 0, 0}};
             if (c->res_eligible) {
-                cand.push_back({1, 256});
-                cand.push_back({1, 512});
+                cand.push_back({1, 256, 0, 0});
+                cand.push_back({1, 512, 0, 0});
             }
-            if (c->coop_eligible) cand.push_back({2, 0});
+            if (c->coop_eligible) cand.push_back({2, 0, 0, 0});
             if (c->cluster_eligible) {
-                const int cs0 = c->cluster_cs;
-                cand.push_back({3, cs0});
-                if (cs0 / 2 >= 2) cand.push_back({3, cs0 / 2});
+                const int cs0 = c->cluster_cs, big = c->max_instance_sites;
+                cand.push_back({3, cs0, 256, 0});
+                if (cs0 / 2 >= 2) cand.push_back({3, cs0 / 2, 256, 0});
+                // batches of uneven instances: clusters for the largest, one block for the rest
+                if (c->res_items > 1)
+                    for (int sp : {big / 2, big / 4})
+                        if (sp > 0) {
+                            cand.push_back({3, 2, 512, sp});
+                            cand.push_back({3, 4, 256, sp});
+                        }
             }
             const int32_t probe = std::max(1, std::min(4, mcs / (2 * (int32_t)cand.size())));
             if (probe * (int32_t)cand.size() <= mcs) {
                 float best = 0.f;
-                int best_v = c->variant, best_shape = 0;
-                const int cs_rule = c->cluster_cs, rt_rule = c->res_threads;
-                for (const auto &vc : cand) {
-                    const int v = vc.first;
-                    if (v == 1) set_resident_shape(c, vc.second);
-                    if (v == 3 && !set_cluster_shape(c, vc.second)) continue;
+                int best_v = c->variant;
+                Cand best_c = cand[0];
+                const int cs_rule = c->cluster_cs, ct_rule = c->cluster_threads, rt_rule = c->res_threads;
+                for (const Cand &vc : cand) {
+                    const int v = vc.v;
+                    if (v == 1) set_resident_shape(c, vc.a);
+                    if (v == 3 && !set_cluster_shape(c, vc.a, vc.b, vc.split)) continue;
                     cudaEvent_t x0, x1;
                     CK(c, cudaEventCreate(&x0));
                     CK(c, cudaEventCreate(&x1));
@@ -1299,10 +1323,10 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     cudaEventDestroy(x1);
                     if (c->tune_ms[v] == 0.0 || ms / probe < c->tune_ms[v]) c->tune_ms[v] = ms / probe;
                     sweep_ms += ms;
-                    if (v == cand[0].first || ms < best) {
+                    if (v == cand[0].v || ms < best) {
                         best = ms;
                         best_v = v;
-                        best_shape = vc.second;
+                        best_c = vc;
                     }
                     m0 += probe;
                     uint32_t e4 = 0;
@@ -1310,8 +1334,13 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     if (e4) break;  // report the device error below
                 }
                 c->variant = best_v;
-                set_resident_shape(c, best_v == 1 ? best_shape : rt_rule);
-                if (c->cluster_eligible) set_cluster_shape(c, best_v == 3 ? best_shape : cs_rule);
+                set_resident_shape(c, best_v == 1 ? best_c.a : rt_rule);
+                if (c->cluster_eligible) {
+                    if (best_v == 3)
+                        set_cluster_shape(c, best_c.a, best_c.b, best_c.split);
+                    else
+                        set_cluster_shape(c, cs_rule, ct_rule);
+                }
             }
             c->tuned = true;
         }
@@ -1622,6 +1651,7 @@ extern "C" vegas_status vegas_stats(const vegas_ctx *c, vegas_stats_t *o) {
     o->snapshot_steps = c->snapshot_steps;
     o->block_threads = c->variant == 1 ? c->res_threads : (c->variant == 3 ? c->cluster_threads : kThreads);
     o->cluster_blocks = c->variant == 3 ? c->cluster_cs : 0;
+    o->split_sites = c->variant == 3 ? c->res.split_sites : 0;
     o->graph_launches = c->graph_launches;
     return VEGAS_OK;
 }

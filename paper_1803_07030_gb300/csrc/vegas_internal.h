@@ -238,6 +238,8 @@ struct ResidentArgs {
     int32_t n_types;           // > 0: per-type magnetization into run->type_hist
     RunState *run;             // MCS counter t, record index, MCS per step, schedule, history
     int32_t mcs;               // MCS in this launch (all inside one temperature/field step)
+    int32_t split_sites;       // cluster sweep: instances of at most this many sites are swept by
+                               // one block each (0: every instance by a whole cluster)
 };
 
 // Grid barrier of the cooperative sweep (zeroed before every launch).

@@ -419,12 +419,12 @@ __device__ __forceinline__ Site32 resident_params(const ResidentArgs &a, const R
 
 constexpr int kResidentMaxTypes = 8;  // per-type statistics in the resident sweep
 
+// Every MCS of the current step on instance I by this block alone: colour class after
+// colour class with __syncthreads between them, then a fixed-order block sum of E and M (and
+// the per-type magnetization, with s_tm zeroed by the caller) written into the history.
 template <int NT, int POL>
-__global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
-    __shared__ int s_item;
-    __shared__ double s_red[NT / 32][4];
-    __shared__ uint32_t s_acc[NT / 32];
-    __shared__ double s_tm[NT / 32][kResidentMaxTypes][3];  // per warp and type, segment order
+__device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, const ResidentInst &I, double (*s_red)[4], uint32_t *s_acc,
+                                     double (*s_tm)[kResidentMaxTypes][3], bool &nan_seen) {
     float4 *S = (float4 *)a.spins;
     const int2 *E = (const int2 *)a.edges;
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
@@ -432,6 +432,110 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n_types = a.n_types;
     RunState *rs = a.run;
+    const uint32_t t0 = rs->t, rec0 = rs->rec;
+    const uint32_t step = rec0 / rs->mcs;
+    const double *sc = rs->sched + ((int64_t)step * a.n_inst + I.inst_local) * 2;
+    const float beta = (float)sc[0], B = (float)sc[1];
+    const uint32_t inst = (uint32_t)I.inst_id;
+    for (int m = 0; m < a.mcs; ++m) {
+        const uint32_t t = t0 + (uint32_t)m;
+        const bool log_accepts = a.alog && t < a.alog_mcs;
+        // the width is read after the barrier that ends the previous MCS (thread 0 wrote it)
+        const float sigma = (POL && rs->sigma) ? (float)rs->sigma[I.inst_local] : 0.f;
+        Acc32 acc;
+        for (int q = 0; q < I.n_segs; ++q) {
+            const int4 sg = a.segs[I.seg_off + q];  // {begin, end, class begin, type | last << 16}
+            float tm[3] = {0.f, 0.f, 0.f};
+            for (int g = sg.x + (int)threadIdx.x; g < sg.y; g += NT) {
+                const uint32_t orig = (uint32_t)__ldg(a.orig + g);
+                // one code path for every parameter mode: with k = kc = 0 the anisotropy terms
+                // add signed zeros only, so spins and decisions equal the specialised paths'
+                const Site32 p = resident_params(a, I, g);
+                float4 Sq;
+                const bool ok = direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, I.r, R, sg.z, orig, p, beta, B, t,
+                                                          inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq);
+                tm[0] = __fadd_rn(tm[0], Sq.x);
+                tm[1] = __fadd_rn(tm[1], Sq.y);
+                tm[2] = __fadd_rn(tm[2], Sq.z);
+                if (log_accepts)
+                    a.alog[(int64_t)t * a.alog_stride + I.alog_base + (int64_t)I.r * I.n_sample_sites + orig] =
+                        ok ? 1 : 0;
+            }
+            if (n_types > 0) {  // this segment's magnetization into its type (fixed order)
+                double d[3] = {(double)tm[0], (double)tm[1], (double)tm[2]};
+                for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) d[c] += __shfl_xor_sync(0xFFFFFFFFu, d[c], off);
+                }
+                const int ty = sg.w & 0xFFFF;
+                if (lane == 0 && ty < kResidentMaxTypes) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) s_tm[warp][ty][c] += d[c];
+                }
+            }
+            if (sg.w >> 16) __syncthreads();  // the last segment of a colour class
+        }
+        acc.flush();
+        double v[4] = {acc.d[0], acc.d[1], acc.d[2], acc.d[3]};
+        uint32_t na = acc.nacc;
+        for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+            na += __shfl_xor_sync(0xFFFFFFFFu, na, off);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s_red[warp][q] = v[q];
+            s_acc[warp] = na;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum[4] = {0.0, 0.0, 0.0, 0.0};
+            uint32_t nsum = 0;
+            for (int w = 0; w < NT / 32; ++w) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) sum[q] += s_red[w][q];
+                nsum += s_acc[w];
+            }
+            const int64_t rec = (int64_t)rec0 + m;
+            double *h = rs->hist + (rec * a.n_inst + I.inst_local) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) h[q] = sum[q];
+            if (rs->acc_hist) rs->acc_hist[rec * a.n_inst + I.inst_local] = nsum;
+            if (I.adaptive && rs->sigma && (uint32_t)(rec % rs->mcs) < rs->mcs / 5)
+                rs->sigma[I.inst_local] = adapt_width(rs->sigma[I.inst_local], nsum, I.n_sample_sites);
+            if (n_types > 0 && rs->type_hist) {
+                double *th = rs->type_hist + (rec * a.n_inst + I.inst_local) * n_types * 3;
+                for (int k = 0; k < n_types; ++k)
+                    for (int c = 0; c < 3; ++c) {
+                        double x = 0.0;
+                        for (int w = 0; w < NT / 32; ++w) {
+                            x += s_tm[w][k][c];
+                            s_tm[w][k][c] = 0.0;
+                        }
+                        th[k * 3 + c] = x;
+                    }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// The same as a separate function, for the cluster sweep's second phase: its registers are
+// then allocated apart from the cluster phase's.
+template <int NT, int POL>
+__device__ __noinline__ void resident_sweep_block_call(const ResidentArgs &a, const ResidentInst &I,
+                                                       double (*s_red)[4], uint32_t *s_acc,
+                                                       double (*s_tm)[kResidentMaxTypes][3], bool &nan_seen) {
+    resident_sweep_block<NT, POL>(a, I, s_red, s_acc, s_tm, nan_seen);
+}
+
+template <int NT, int POL>
+__global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
+    __shared__ int s_item;
+    __shared__ double s_red[NT / 32][4];
+    __shared__ uint32_t s_acc[NT / 32];
+    __shared__ double s_tm[NT / 32][kResidentMaxTypes][3];  // per warp and type, segment order
     bool nan_seen = false;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(a.queue, 1u);
@@ -441,93 +545,7 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
         __syncthreads();
         if (item >= a.n_items) break;
         const ResidentInst I = a.insts[item];
-        const uint32_t t0 = rs->t, rec0 = rs->rec;
-        const uint32_t step = rec0 / rs->mcs;
-        const double *sc = rs->sched + ((int64_t)step * a.n_inst + I.inst_local) * 2;
-        const float beta = (float)sc[0], B = (float)sc[1];
-        const uint32_t inst = (uint32_t)I.inst_id;
-        for (int m = 0; m < a.mcs; ++m) {
-            const uint32_t t = t0 + (uint32_t)m;
-            const bool log_accepts = a.alog && t < a.alog_mcs;
-            // the width is read after the barrier that ends the previous MCS (thread 0 wrote it)
-            const float sigma = (POL && rs->sigma) ? (float)rs->sigma[I.inst_local] : 0.f;
-            Acc32 acc;
-            for (int q = 0; q < I.n_segs; ++q) {
-                const int4 sg = a.segs[I.seg_off + q];  // {begin, end, class begin, type | last << 16}
-                float tm[3] = {0.f, 0.f, 0.f};
-                for (int g = sg.x + (int)threadIdx.x; g < sg.y; g += NT) {
-                    const uint32_t orig = (uint32_t)__ldg(a.orig + g);
-                    // one code path for every parameter mode: with k = kc = 0 the anisotropy terms
-                    // add signed zeros only, so spins and decisions equal the specialised paths'
-                    const Site32 p = resident_params(a, I, g);
-                    float4 Sq;
-                    const bool ok = direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, I.r, R, sg.z, orig, p, beta, B, t,
-                                                              inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq);
-                    tm[0] = __fadd_rn(tm[0], Sq.x);
-                    tm[1] = __fadd_rn(tm[1], Sq.y);
-                    tm[2] = __fadd_rn(tm[2], Sq.z);
-                    if (log_accepts)
-                        a.alog[(int64_t)t * a.alog_stride + I.alog_base + (int64_t)I.r * I.n_sample_sites + orig] =
-                            ok ? 1 : 0;
-                }
-                if (n_types > 0) {  // this segment's magnetization into its type (fixed order)
-                    double d[3] = {(double)tm[0], (double)tm[1], (double)tm[2]};
-                    for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) d[c] += __shfl_xor_sync(0xFFFFFFFFu, d[c], off);
-                    }
-                    const int ty = sg.w & 0xFFFF;
-                    if (lane == 0 && ty < kResidentMaxTypes) {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) s_tm[warp][ty][c] += d[c];
-                    }
-                }
-                if (sg.w >> 16) __syncthreads();  // the last segment of a colour class
-            }
-            acc.flush();
-            double v[4] = {acc.d[0], acc.d[1], acc.d[2], acc.d[3]};
-            uint32_t na = acc.nacc;
-            for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
-                na += __shfl_xor_sync(0xFFFFFFFFu, na, off);
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) s_red[warp][q] = v[q];
-                s_acc[warp] = na;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double sum[4] = {0.0, 0.0, 0.0, 0.0};
-                uint32_t nsum = 0;
-                for (int w = 0; w < NT / 32; ++w) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) sum[q] += s_red[w][q];
-                    nsum += s_acc[w];
-                }
-                const int64_t rec = (int64_t)rec0 + m;
-                double *h = rs->hist + (rec * a.n_inst + I.inst_local) * 4;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) h[q] = sum[q];
-                if (rs->acc_hist) rs->acc_hist[rec * a.n_inst + I.inst_local] = nsum;
-                if (I.adaptive && rs->sigma && (uint32_t)(rec % rs->mcs) < rs->mcs / 5)
-                    rs->sigma[I.inst_local] = adapt_width(rs->sigma[I.inst_local], nsum, I.n_sample_sites);
-                if (n_types > 0 && rs->type_hist) {
-                    double *th = rs->type_hist + (rec * a.n_inst + I.inst_local) * n_types * 3;
-                    for (int k = 0; k < n_types; ++k)
-                        for (int c = 0; c < 3; ++c) {
-                            double x = 0.0;
-                            for (int w = 0; w < NT / 32; ++w) {
-                                x += s_tm[w][k][c];
-                                s_tm[w][k][c] = 0.0;
-                            }
-                            th[k * 3 + c] = x;
-                        }
-                }
-            }
-            __syncthreads();
-        }
+        resident_sweep_block<NT, POL>(a, I, s_red, s_acc, s_tm, nan_seen);
     }
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }
@@ -538,7 +556,10 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
 // between classes, and rank 0 sums the blocks' per-MCS totals from their shared memory in
 // rank order. For instances too large for one block and too small to fill the GPU per class.
 // Every block of a cluster runs the same loop (rank 0 fetches the instance and the others
-// read it from rank 0's shared memory), so all of them reach every barrier.
+// read it from rank 0's shared memory), so all of them reach every barrier. Instances are
+// queued largest first: from the first one with at most split_sites sites on, the blocks of
+// a cluster leave the loop together and sweep instances alone, as the resident sweep does
+// (rank 0 keeps the one just drawn), so small instances do not hold a whole cluster.
 template <int NT, int POL>
 __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentArgs a) {
     namespace cg = cooperative_groups;
@@ -559,6 +580,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
     const int n_types = a.n_types;
     RunState *rs = a.run;
     bool nan_seen = false;
+    int alone = -2;  // >= -1: the blocks sweep alone from now on (-1: draw the next instance)
     for (;;) {
         if (rank == 0 && threadIdx.x == 0) s_item = (int)atomicAdd(a.queue, 1u);
         for (int q = threadIdx.x; q < (NT / 32) * kResidentMaxTypes * 3; q += NT) (&s_tm[0][0][0])[q] = 0.0;
@@ -567,6 +589,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
         cl.sync();  // every block has read the item before rank 0 fetches the next
         if (item >= a.n_items) break;
         const ResidentInst I = a.insts[item];
+        if (a.split_sites > 0 && I.g_end - I.g_begin <= a.split_sites) {
+            alone = rank == 0 ? item : -1;
+            break;
+        }
         const uint32_t t0 = rs->t, rec0 = rs->rec;
         const uint32_t step = rec0 / rs->mcs;
         const double *sc = rs->sched + ((int64_t)step * a.n_inst + I.inst_local) * 2;
@@ -667,6 +693,21 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
             }
             cl.sync();  // the width and the totals' buffers are ready for the next MCS
         }
+    }
+    // small instances: no shared memory of another block is read from here on
+    for (int item = alone; alone >= -1;) {
+        if (item < 0) {
+            if (threadIdx.x == 0) s_item = (int)atomicAdd(a.queue, 1u);
+            __syncthreads();
+            item = s_item;
+            __syncthreads();
+        }
+        if (item >= a.n_items) break;
+        for (int q = threadIdx.x; q < (NT / 32) * kResidentMaxTypes * 3; q += NT) (&s_tm[0][0][0])[q] = 0.0;
+        __syncthreads();
+        const ResidentInst I = a.insts[item];
+        resident_sweep_block_call<NT, POL>(a, I, s_red, s_acc, s_tm, nan_seen);
+        item = -1;
     }
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }

@@ -65,6 +65,9 @@ class vegas_options(C.Structure):
         ("fault_inject", C.c_int32),
         ("type_stats", C.c_int32),
         ("snapshots", C.c_int32),
+        ("cluster_blocks", C.c_int32),
+        ("cluster_threads", C.c_int32),
+        ("cluster_split", C.c_int32),
         ("wave_lag", C.c_int32),
     ]
 
@@ -93,6 +96,8 @@ class vegas_stats_t(C.Structure):
         ("block_threads", C.c_int32),
         ("cluster_blocks", C.c_int32),
         ("graph_launches", C.c_int64),
+        ("split_sites", C.c_int32),
+        ("pad2_", C.c_int32),
     ]
 
 
@@ -415,7 +420,8 @@ class Context:
                  inst_base: int = 0, device: int = -1, stream="torch", variant: int = -1,
                  accept_log_mcs: int = 0, timing: bool = False, graphs: int = 1, max_blocks: int = 0,
                  pipeline_depth: int = 0, timeout_ns: int = 0, fault_inject: int = 0,
-                 type_stats: bool = False, snapshots: bool = False, wave_lag: int = 0,
+                 type_stats: bool = False, snapshots: bool = False, cluster_blocks: int = 0, cluster_threads: int = 0, cluster_split: int = 0,
+                 wave_lag: int = 0,
                  library: Optional[str] = None):
         self.samples = list(samples)
         self.n_sites = [int(np.asarray(s.row_ptr).shape[0] - 1) for s in self.samples]
@@ -438,6 +444,9 @@ class Context:
         o.fault_inject = fault_inject
         o.type_stats = 1 if type_stats else 0
         o.snapshots = 1 if snapshots else 0
+        o.cluster_blocks = cluster_blocks
+        o.cluster_threads = cluster_threads
+        o.cluster_split = cluster_split
         o.wave_lag = wave_lag
         o.cuda_stream = _current_stream() if stream == "torch" else stream
         self.replicas = replicas

@@ -332,7 +332,7 @@ def test_autotuner_picks_a_sweep_and_block_shape():
         if st["variant"] == 1:
             assert st["block_threads"] in (256, 512) and st["cluster_blocks"] == 0
         elif st["variant"] == 3:
-            assert st["cluster_blocks"] >= 2 and st["block_threads"] == 256
+            assert st["cluster_blocks"] >= 2 and st["block_threads"] in (256, 512)
         else:
             assert st["block_threads"] == 256 and st["cluster_blocks"] == 0
         for i in range(len(ps)):
@@ -372,6 +372,25 @@ def test_cluster_sweep_equals_per_class_sweep(make, R):
             assert np.array_equal(a.spins(i), b.spins(i)), i
         assert_fp32_history_close(a.history(), b.history(), s.n_sites)
         assert np.array_equal(a.accept_log(), b.accept_log())
+        assert np.array_equal(a.accept_history(), b.accept_history())
+
+
+@pytest.mark.parametrize("split", [0, 200, 10**6])
+def test_cluster_sweep_splits_small_instances_to_single_blocks(split):
+    """Instances of at most cluster_split sites are swept by one block each (the blocks of a
+    cluster leave the cluster loop at the first one: instances are queued largest first),
+    larger ones by the whole cluster; either way the chain is the per-class sweep's."""
+    ps = nanoparticle_batch(9, seed=12, r_max=6.5)
+    T = np.linspace(0.4, 2.0, len(ps))[:, None] * np.array([[1.0, 0.7]])
+    B = np.full_like(T, 0.2)
+    with ctx(ps, seed=28, variant=3, cluster_split=split) as a, ctx(ps, seed=28, variant=0) as b:
+        a.run(T, B, 6)
+        b.run(T, B, 6)
+        assert a.stats()["variant"] == 3 and a.stats()["split_sites"] == split
+        for i in range(len(ps)):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+        Ha, Hb = a.history(), b.history()
+        assert np.all(np.abs(Ha - Hb) <= 1e-6 * max(p.n_sites for p in ps))
         assert np.array_equal(a.accept_history(), b.accept_history())
 
 
