@@ -417,7 +417,7 @@ def run_workload(args):
                    "policy": policy or "random", "type_stats": bool(args.type_stats),
                    "snapshots": bool(args.snapshots)},
         "variant": st1["variant"], "block_threads": st1["block_threads"], "cluster_blocks": st1["cluster_blocks"],
-        "split_sites": st1["split_sites"],
+        "split_sites": st1["split_sites"], "group_threads": st1["group_threads"], "group_sites": st1["group_sites"],
         "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
         "clocks": clk.summary(),
     }

@@ -175,6 +175,12 @@ typedef struct {
     int32_t cluster_blocks; /* cluster sweep (variant 3): blocks per cluster, 2 .. 16;
                                0 = by instance size (about 2048 sites per block) */
     int32_t cluster_threads;/* cluster sweep: threads per block, 256 or 512; 0 = 256 */
+    int32_t group_threads;  /* resident sweep (variant 1) and the single-block phase of the
+                               cluster sweep: instances of at most group_sites sites are swept
+                               several to a block, group_threads threads (64, 128 or 256) each,
+                               each group meeting at its own named barrier; 0 = one instance
+                               per block. The automatic choice picks its own. Default 0. */
+    int32_t group_sites;    /* see group_threads. Default 0. */
     int32_t cluster_split;  /* cluster sweep (variant 3): instances of at most this many sites
                                are swept by one block each, larger ones by a whole cluster;
                                0 = every instance by a cluster. The automatic choice (variant
@@ -213,6 +219,9 @@ typedef struct {
     int32_t split_sites;        /* cluster sweep in use: instances of at most this many sites
                                    are swept by one block each, larger ones by a whole cluster
                                    (chosen by the autotuner; 0 = every instance by a cluster) */
+    int32_t group_threads;      /* resident or cluster sweep in use: threads per small instance
+                                   swept several to a block (0 = one instance per block) */
+    int32_t group_sites;        /* the largest instance swept that way */
     int32_t pad2_;
 } vegas_stats_t;
 

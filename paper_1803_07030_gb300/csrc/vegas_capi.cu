@@ -191,12 +191,17 @@ int ilog2(int v) {
     return l;
 }
 
-// Block shape of the resident sweep: threads per block, and as many blocks as fit (at most one
-// per instance).
-void set_resident_shape(vegas_ctx *c, int threads) {
+// Block shape of the resident sweep: threads per block, as many blocks as fit (at most one
+// per instance), and the grouping of small instances (group_threads threads per instance of
+// at most group_sites sites, several per block; 0 = one instance per block).
+void set_resident_shape(vegas_ctx *c, int threads, int group_threads = 0, int group_sites = 0) {
     c->res_threads = threads;
     c->res_grid = (int)std::min<int64_t>((int64_t)c->res_items,
                                          (int64_t)c->sm_count * resident_blocks_per_sm(threads, c->res_policy));
+    const bool grouped = group_threads > 0 && group_threads < threads && threads % group_threads == 0 &&
+                         threads / group_threads <= 15;
+    c->res.group_threads = grouped ? group_threads : 0;
+    c->res.group_sites = grouped ? group_sites : 0;
 }
 
 // Shape of the cluster sweep: cs blocks of `threads` per cluster, as many clusters as fit,
@@ -422,6 +427,8 @@ extern "C" void vegas_default_options(vegas_options *o) {
     o->cluster_blocks = 0;
     o->cluster_threads = 0;
     o->cluster_split = 0;
+    o->group_threads = 0;
+    o->group_sites = 0;
     o->wave_lag = 0;
 }
 
@@ -443,6 +450,9 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
                     "the wavefront sweep (variant 4) is FP32 with one sample, 32 replicas and no per-type statistics");
     if (o.wave_lag < 0) return fail(nullptr, VEGAS_EINVAL, "wave_lag must be >= 0");
     if (o.cluster_split < 0) return fail(nullptr, VEGAS_EINVAL, "cluster_split must be >= 0");
+    if (o.group_threads != 0 && o.group_threads != 64 && o.group_threads != 128 && o.group_threads != 256)
+        return fail(nullptr, VEGAS_EINVAL, "group_threads must be 0, 64, 128 or 256");
+    if (o.group_sites < 0) return fail(nullptr, VEGAS_EINVAL, "group_sites must be >= 0");
     if (o.cluster_blocks != 0 && (o.cluster_blocks < 2 || o.cluster_blocks > 16))
         return fail(nullptr, VEGAS_EINVAL, "cluster_blocks must be 0 or 2 .. 16");
     if (o.cluster_threads != 0 && o.cluster_threads != 256 && o.cluster_threads != 512)
@@ -885,9 +895,9 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         if (!h_segs.empty()) H2D(c->d_segs, h_segs.data(), sizeof(int4) * h_segs.size());
         c->res_items = (int)insts.size();
         c->res_policy = any_policy;
-        set_resident_shape(c, c->max_instance_sites >= 4096 ? 512 : 256);
         ResidentArgs &ra = c->res;
         std::memset(&ra, 0, sizeof ra);
+        set_resident_shape(c, c->max_instance_sites >= 4096 ? 512 : 256, o.group_threads, o.group_sites);
         ra.spins = c->d_spins;
         ra.edges = c->d_edges;
         ra.row_ptr = c->d_rowptr;
@@ -1280,27 +1290,36 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             // per block of the resident sweep (so sites per thread), blocks per cluster of the
             // cluster sweep.
             struct Cand {
-                int v, a, b, split;  // sweep; threads (resident) or blocks per cluster, threads
+                int v, a, b, split, group;  // sweep; threads (resident) or blocks per cluster,
+                                            // threads; cluster split; threads per small instance
             };
-            std::vector<Cand> cand{{0, 0, 0, 0}};
+            std::vector<Cand> cand{{0, 0, 0, 0, 0}};
+            const bool uneven = c->res_items > 1;
             if (c->res_eligible) {
-                cand.push_back({1, 256, 0, 0});
-                cand.push_back({1, 512, 0, 0});
+                cand.push_back({1, 256, 0, 0, 0});
+                cand.push_back({1, 512, 0, 0, 0});
+                if (uneven) {  // small instances several to a block
+                    cand.push_back({1, 512, 0, 0, 128});
+                    cand.push_back({1, 512, 0, 0, 256});
+                }
             }
-            if (c->coop_eligible) cand.push_back({2, 0, 0, 0});
+            if (c->coop_eligible) cand.push_back({2, 0, 0, 0, 0});
             if (c->cluster_eligible) {
                 const int cs0 = c->cluster_cs, big = c->max_instance_sites;
-                cand.push_back({3, cs0, 256, 0});
-                if (cs0 / 2 >= 2) cand.push_back({3, cs0 / 2, 256, 0});
-                // batches of uneven instances: clusters for the largest, one block for the rest
-                if (c->res_items > 1)
+                cand.push_back({3, cs0, 256, 0, 0});
+                if (cs0 / 2 >= 2) cand.push_back({3, cs0 / 2, 256, 0, 0});
+                // batches of uneven instances: clusters for the largest, blocks (and groups of a
+                // block) for the rest
+                if (uneven)
                     for (int sp : {big / 2, big / 4})
                         if (sp > 0) {
-                            cand.push_back({3, 2, 512, sp});
-                            cand.push_back({3, 4, 256, sp});
+                            cand.push_back({3, 2, 512, sp, 128});
+                            cand.push_back({3, 4, 256, sp, 0});
                         }
             }
-            const int32_t probe = std::max(1, std::min(4, mcs / (2 * (int32_t)cand.size())));
+            // longer probes when the step allows (less noise between close candidates), at most
+            // a quarter of the step
+            const int32_t probe = std::max(1, std::min(16, mcs / (4 * (int32_t)cand.size())));
             if (probe * (int32_t)cand.size() <= mcs) {
                 float best = 0.f;
                 int best_v = c->variant;
@@ -1308,8 +1327,13 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                 const int cs_rule = c->cluster_cs, ct_rule = c->cluster_threads, rt_rule = c->res_threads;
                 for (const Cand &vc : cand) {
                     const int v = vc.v;
-                    if (v == 1) set_resident_shape(c, vc.a);
-                    if (v == 3 && !set_cluster_shape(c, vc.a, vc.b, vc.split)) continue;
+                    // grouped instances: group_threads threads for up to 16 sites each per thread
+                    if (v == 1) set_resident_shape(c, vc.a, vc.group, vc.group * 16);
+                    if (v == 3) {
+                        if (!set_cluster_shape(c, vc.a, vc.b, vc.split)) continue;
+                        c->res.group_threads = vc.group < vc.b ? vc.group : 0;
+                        c->res.group_sites = c->res.group_threads * 16;
+                    }
                     cudaEvent_t x0, x1;
                     CK(c, cudaEventCreate(&x0));
                     CK(c, cudaEventCreate(&x1));
@@ -1334,12 +1358,18 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     if (e4) break;  // report the device error below
                 }
                 c->variant = best_v;
-                set_resident_shape(c, best_v == 1 ? best_c.a : rt_rule);
+                if (best_v == 1)
+                    set_resident_shape(c, best_c.a, best_c.group, best_c.group * 16);
+                else
+                    set_resident_shape(c, rt_rule);
                 if (c->cluster_eligible) {
-                    if (best_v == 3)
+                    if (best_v == 3) {
                         set_cluster_shape(c, best_c.a, best_c.b, best_c.split);
-                    else
+                        c->res.group_threads = best_c.group < best_c.b ? best_c.group : 0;
+                        c->res.group_sites = c->res.group_threads * 16;
+                    } else {
                         set_cluster_shape(c, cs_rule, ct_rule);
+                    }
                 }
             }
             c->tuned = true;
@@ -1652,6 +1682,8 @@ extern "C" vegas_status vegas_stats(const vegas_ctx *c, vegas_stats_t *o) {
     o->block_threads = c->variant == 1 ? c->res_threads : (c->variant == 3 ? c->cluster_threads : kThreads);
     o->cluster_blocks = c->variant == 3 ? c->cluster_cs : 0;
     o->split_sites = c->variant == 3 ? c->res.split_sites : 0;
+    o->group_threads = (c->variant == 1 || c->variant == 3) ? c->res.group_threads : 0;
+    o->group_sites = (c->variant == 1 || c->variant == 3) ? c->res.group_sites : 0;
     o->graph_launches = c->graph_launches;
     return VEGAS_OK;
 }

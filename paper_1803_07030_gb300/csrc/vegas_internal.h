@@ -240,6 +240,8 @@ struct ResidentArgs {
     int32_t mcs;               // MCS in this launch (all inside one temperature/field step)
     int32_t split_sites;       // cluster sweep: instances of at most this many sites are swept by
                                // one block each (0: every instance by a whole cluster)
+    int32_t group_threads;     // > 0: a block sweeps instances of at most group_sites sites
+    int32_t group_sites;       // NT / group_threads at a time, group_threads threads each
 };
 
 // Grid barrier of the cooperative sweep (zeroed before every launch).

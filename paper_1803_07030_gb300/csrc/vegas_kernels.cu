@@ -419,12 +419,23 @@ __device__ __forceinline__ Site32 resident_params(const ResidentArgs &a, const R
 
 constexpr int kResidentMaxTypes = 8;  // per-type statistics in the resident sweep
 
-// Every MCS of the current step on instance I by this block alone: colour class after
-// colour class with __syncthreads between them, then a fixed-order block sum of E and M (and
-// the per-type magnetization, with s_tm zeroed by the caller) written into the history.
+// Every MCS of the current step on instance I by a group of gthreads threads of the block
+// (the whole block: gbar = 0; else warps gtid / 32 .. of a group meeting at named barrier
+// gbar): colour class after colour class with a barrier between them, then a fixed-order
+// sum of the group's warps' E and M (and per-type magnetization, s_tm zeroed by the caller)
+// written into the history.
+__device__ __forceinline__ void group_sync(int bar, int nthreads) {
+    if (bar == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
+}
+
+
 template <int NT, int POL>
 __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, const ResidentInst &I, double (*s_red)[4], uint32_t *s_acc,
-                                     double (*s_tm)[kResidentMaxTypes][3], bool &nan_seen) {
+                                     double (*s_tm)[kResidentMaxTypes][3], bool &nan_seen, int gtid, int gthreads,
+                                     int gbar) {
     float4 *S = (float4 *)a.spins;
     const int2 *E = (const int2 *)a.edges;
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
@@ -432,6 +443,7 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n_types = a.n_types;
     RunState *rs = a.run;
+    const int gw0 = (threadIdx.x - gtid) >> 5;  // the group's first warp
     const uint32_t t0 = rs->t, rec0 = rs->rec;
     const uint32_t step = rec0 / rs->mcs;
     const double *sc = rs->sched + ((int64_t)step * a.n_inst + I.inst_local) * 2;
@@ -446,7 +458,7 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
         for (int q = 0; q < I.n_segs; ++q) {
             const int4 sg = a.segs[I.seg_off + q];  // {begin, end, class begin, type | last << 16}
             float tm[3] = {0.f, 0.f, 0.f};
-            for (int g = sg.x + (int)threadIdx.x; g < sg.y; g += NT) {
+            for (int g = sg.x + gtid; g < sg.y; g += gthreads) {
                 const uint32_t orig = (uint32_t)__ldg(a.orig + g);
                 // one code path for every parameter mode: with k = kc = 0 the anisotropy terms
                 // add signed zeros only, so spins and decisions equal the specialised paths'
@@ -473,7 +485,7 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
                     for (int c = 0; c < 3; ++c) s_tm[warp][ty][c] += d[c];
                 }
             }
-            if (sg.w >> 16) __syncthreads();  // the last segment of a colour class
+            if (sg.w >> 16) group_sync(gbar, gthreads);  // the last segment of a colour class
         }
         acc.flush();
         double v[4] = {acc.d[0], acc.d[1], acc.d[2], acc.d[3]};
@@ -488,11 +500,11 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
             for (int q = 0; q < 4; ++q) s_red[warp][q] = v[q];
             s_acc[warp] = na;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        group_sync(gbar, gthreads);
+        if (gtid == 0) {
             double sum[4] = {0.0, 0.0, 0.0, 0.0};
             uint32_t nsum = 0;
-            for (int w = 0; w < NT / 32; ++w) {
+            for (int w = gw0; w < gw0 + (gthreads >> 5); ++w) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) sum[q] += s_red[w][q];
                 nsum += s_acc[w];
@@ -509,7 +521,7 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
                 for (int k = 0; k < n_types; ++k)
                     for (int c = 0; c < 3; ++c) {
                         double x = 0.0;
-                        for (int w = 0; w < NT / 32; ++w) {
+                        for (int w = gw0; w < gw0 + (gthreads >> 5); ++w) {
                             x += s_tm[w][k][c];
                             s_tm[w][k][c] = 0.0;
                         }
@@ -517,36 +529,62 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
                     }
             }
         }
+        group_sync(gbar, gthreads);
+    }
+}
+
+// Draws instances from the queue and sweeps them until it is empty (first >= 0: start with
+// that one). An instance of at most group_sites sites comes with NT / group_threads - 1 more
+// (the queue is largest first, so they are no larger), and the block sweeps them at once,
+// a group of group_threads threads each; larger instances take the whole block.
+template <int NT, int POL>
+__device__ __forceinline__ void resident_loop(const ResidentArgs &a, int first, double (*s_red)[4], uint32_t *s_acc,
+                                              double (*s_tm)[kResidentMaxTypes][3], int *s_items, bool &nan_seen) {
+    const int GT = a.group_threads;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int it = first >= 0 ? first : (int)atomicAdd(a.queue, 1u);
+            int ng = 1;
+            if (GT > 0 && GT < NT && it < a.n_items && a.insts[it].g_end - a.insts[it].g_begin <= a.group_sites) {
+                ng = NT / GT;
+                const int more = (int)atomicAdd(a.queue, (uint32_t)(ng - 1));
+                for (int k = 1; k < ng; ++k) s_items[k] = more + k - 1;
+            }
+            s_items[0] = it;
+            s_items[NT / 32] = ng;
+        }
+        first = -1;
+        for (int q = threadIdx.x; q < (NT / 32) * kResidentMaxTypes * 3; q += NT) (&s_tm[0][0][0])[q] = 0.0;
         __syncthreads();
+        const int ng = s_items[NT / 32];
+        if (s_items[0] >= a.n_items) break;
+        // one group per instance drawn (the whole block when ng = 1, named barrier 0)
+        const int gt = NT / ng, gi = (int)threadIdx.x / gt, item = s_items[gi];
+        if (item < a.n_items) {
+            const ResidentInst I = a.insts[item];
+            resident_sweep_block<NT, POL>(a, I, s_red, s_acc, s_tm, nan_seen, (int)threadIdx.x - gi * gt, gt,
+                                          ng == 1 ? 0 : 1 + gi);
+        }
+        __syncthreads();  // every group is done before the items are drawn again
     }
 }
 
 // The same as a separate function, for the cluster sweep's second phase: its registers are
 // then allocated apart from the cluster phase's.
 template <int NT, int POL>
-__device__ __noinline__ void resident_sweep_block_call(const ResidentArgs &a, const ResidentInst &I,
-                                                       double (*s_red)[4], uint32_t *s_acc,
-                                                       double (*s_tm)[kResidentMaxTypes][3], bool &nan_seen) {
-    resident_sweep_block<NT, POL>(a, I, s_red, s_acc, s_tm, nan_seen);
+__device__ __noinline__ void resident_loop_call(const ResidentArgs &a, int first, double (*s_red)[4], uint32_t *s_acc,
+                                                double (*s_tm)[kResidentMaxTypes][3], int *s_items, bool &nan_seen) {
+    resident_loop<NT, POL>(a, first, s_red, s_acc, s_tm, s_items, nan_seen);
 }
 
 template <int NT, int POL>
 __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
-    __shared__ int s_item;
+    __shared__ int s_items[NT / 32 + 1];  // the instances drawn (one per group) and their count
     __shared__ double s_red[NT / 32][4];
     __shared__ uint32_t s_acc[NT / 32];
     __shared__ double s_tm[NT / 32][kResidentMaxTypes][3];  // per warp and type, segment order
     bool nan_seen = false;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(a.queue, 1u);
-        for (int q = threadIdx.x; q < (NT / 32) * kResidentMaxTypes * 3; q += NT) (&s_tm[0][0][0])[q] = 0.0;
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
-        if (item >= a.n_items) break;
-        const ResidentInst I = a.insts[item];
-        resident_sweep_block<NT, POL>(a, I, s_red, s_acc, s_tm, nan_seen);
-    }
+    resident_loop<NT, POL>(a, -1, s_red, s_acc, s_tm, s_items, nan_seen);
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }
 
@@ -695,19 +733,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
         }
     }
     // small instances: no shared memory of another block is read from here on
-    for (int item = alone; alone >= -1;) {
-        if (item < 0) {
-            if (threadIdx.x == 0) s_item = (int)atomicAdd(a.queue, 1u);
-            __syncthreads();
-            item = s_item;
-            __syncthreads();
-        }
-        if (item >= a.n_items) break;
-        for (int q = threadIdx.x; q < (NT / 32) * kResidentMaxTypes * 3; q += NT) (&s_tm[0][0][0])[q] = 0.0;
-        __syncthreads();
-        const ResidentInst I = a.insts[item];
-        resident_sweep_block_call<NT, POL>(a, I, s_red, s_acc, s_tm, nan_seen);
-        item = -1;
+    if (alone >= -1) {
+        __shared__ int s_items[NT / 32 + 1];
+        resident_loop_call<NT, POL>(a, alone, s_red, s_acc, s_tm, s_items, nan_seen);
     }
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }

@@ -67,6 +67,8 @@ class vegas_options(C.Structure):
         ("snapshots", C.c_int32),
         ("cluster_blocks", C.c_int32),
         ("cluster_threads", C.c_int32),
+        ("group_threads", C.c_int32),
+        ("group_sites", C.c_int32),
         ("cluster_split", C.c_int32),
         ("wave_lag", C.c_int32),
     ]
@@ -97,6 +99,8 @@ class vegas_stats_t(C.Structure):
         ("cluster_blocks", C.c_int32),
         ("graph_launches", C.c_int64),
         ("split_sites", C.c_int32),
+        ("group_threads", C.c_int32),
+        ("group_sites", C.c_int32),
         ("pad2_", C.c_int32),
     ]
 
@@ -421,6 +425,7 @@ class Context:
                  accept_log_mcs: int = 0, timing: bool = False, graphs: int = 1, max_blocks: int = 0,
                  pipeline_depth: int = 0, timeout_ns: int = 0, fault_inject: int = 0,
                  type_stats: bool = False, snapshots: bool = False, cluster_blocks: int = 0, cluster_threads: int = 0, cluster_split: int = 0,
+                 group_threads: int = 0, group_sites: int = 0,
                  wave_lag: int = 0,
                  library: Optional[str] = None):
         self.samples = list(samples)
@@ -447,6 +452,8 @@ class Context:
         o.cluster_blocks = cluster_blocks
         o.cluster_threads = cluster_threads
         o.cluster_split = cluster_split
+        o.group_threads = group_threads
+        o.group_sites = group_sites
         o.wave_lag = wave_lag
         o.cuda_stream = _current_stream() if stream == "torch" else stream
         self.replicas = replicas

@@ -394,6 +394,36 @@ def test_cluster_sweep_splits_small_instances_to_single_blocks(split):
         assert np.array_equal(a.accept_history(), b.accept_history())
 
 
+@pytest.mark.parametrize("variant,group,kw", [
+    (1, 128, {}), (1, 64, {}), (1, 256, {}),
+    (3, 128, dict(cluster_blocks=2, cluster_threads=512, cluster_split=700)),
+])
+def test_small_instances_several_to_a_block(variant, group, kw):
+    """Instances of at most group_sites sites are swept several to a block, group_threads
+    threads each meeting at their own named barrier (the resident sweep, and the single-block
+    phase of the cluster sweep); the chain stays the per-class sweep's, with the acceptance
+    counts and (with per-type statistics) the magnetization of every type."""
+    ps = nanoparticle_batch(11, seed=13, r_max=6.0)
+    for p in ps:
+        p.type = (np.arange(p.n_sites) % 2).astype(np.int32)
+    T = np.linspace(0.4, 2.0, len(ps))[:, None] * np.array([[1.0, 0.8]])
+    B = np.full_like(T, 0.1)
+    with ctx(ps, seed=29, variant=variant, group_threads=group, group_sites=600, type_stats=True, **kw) as a, \
+            ctx(ps, seed=29, variant=0, type_stats=True) as b:
+        a.run(T, B, 5)
+        b.run(T, B, 5)
+        st = a.stats()
+        grouped = group < (256 if variant == 1 else 512)  # the blocks' threads (256: instances < 4096 sites)
+        assert st["variant"] == variant and st["group_threads"] == (group if grouped else 0)
+        assert st["group_sites"] == (600 if grouped else 0)
+        for i in range(len(ps)):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+        n = max(p.n_sites for p in ps)
+        assert np.all(np.abs(a.history() - b.history()) <= 1e-6 * n)
+        assert np.all(np.abs(a.type_history() - b.type_history()) <= 1e-6 * n)
+        assert np.array_equal(a.accept_history(), b.accept_history())
+
+
 def test_cluster_sweep_batch_with_policies_and_types():
     ps = nanoparticle_batch(6, seed=6, r_max=9.0)
     for p in ps:
