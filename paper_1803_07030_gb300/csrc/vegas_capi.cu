@@ -89,7 +89,7 @@ struct vegas_ctx {
     int res_items = 0;          // instances of the resident and cluster sweeps
     bool res_policy = false;    // some sample has a policy table (kernel choice for the shapes)
     bool res_eligible = false, tuned = false;
-    int32_t max_instance_sites = 0;
+    int32_t max_instance_sites = 0, min_instance_sites = 0;
     double tune_ms[4] = {0.0, 0.0, 0.0, 0.0};  // per-MCS time of each sweep when tuned
     // cluster sweep: clusters of cluster_cs blocks, cluster_n of them at once
     bool cluster_eligible = false;
@@ -863,6 +863,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
                 }
             const int32_t n_segs = (int32_t)h_segs.size() - seg_off;
             c->max_instance_sites = std::max(c->max_instance_sites, si.n);
+            c->min_instance_sites = c->min_instance_sites == 0 ? si.n : std::min(c->min_instance_sites, si.n);
             for (int32_t r = 0; r < R; ++r) {
                 ResidentInst I;
                 std::memset(&I, 0, sizeof I);
@@ -1294,7 +1295,8 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                                             // threads; cluster split; threads per small instance
             };
             std::vector<Cand> cand{{0, 0, 0, 0, 0}};
-            const bool uneven = c->res_items > 1;
+            // instances of very different sizes (split and grouping candidates)
+            const bool uneven = c->res_items > 1 && 4 * (int64_t)c->min_instance_sites < c->max_instance_sites;
             if (c->res_eligible) {
                 cand.push_back({1, 256, 0, 0, 0});
                 cand.push_back({1, 512, 0, 0, 0});
