@@ -34,6 +34,7 @@ struct SampleInfo {
 struct PassLaunch {
     PassArgs args;
     int grid;
+    int threads = kThreads;    // threads per block (FP64 passes of small classes use fewer)
     int32_t sample, group;     // partial slots are grouped by (sample, type group)
     int32_t col;               // colour class
     int64_t slot = 0;          // first block slot
@@ -224,7 +225,7 @@ void enqueue_mcs(vegas_ctx *c, cudaStream_t st, std::vector<cudaEvent_t> *ev) {
     for (const PassLaunch &p : c->passes) {
         if (ev) cudaEventRecord((*ev)[2 * k], st);
         if (c->precision == 64)
-            launch_pass64(p.args, p.grid, st);
+            launch_pass64(p.args, p.grid, p.threads, st);
         else
             launch_pass32(p.args, p.grid, st);
         if (ev) cudaEventRecord((*ev)[2 * k + 1], st);
@@ -803,7 +804,13 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
             a.u32 = SiteParams32{(float)si.u.nx, (float)si.u.ny, (float)si.u.nz, (float)si.u.s, (float)si.u.ex,
                                  (float)si.u.ey, (float)si.u.ez, (float)si.u.k,  (float)si.u.kc};
             const int64_t work = (int64_t)nc * R;
-            const int64_t need = (work + kThreads - 1) / kThreads;
+            if (c->precision == 64) {
+                // an SM runs few FP64 operations per clock: spread a small class over many SMs
+                // (blocks of 32 .. kThreads threads, about one block per SM)
+                const int64_t per_sm = (work + c->sm_count - 1) / c->sm_count;
+                pl.threads = (int)std::min<int64_t>(kThreads, std::max<int64_t>(32, (per_sm + 31) / 32 * 32));
+            }
+            const int64_t need = (work + pl.threads - 1) / pl.threads;
             int64_t cap = (int64_t)c->sm_count * pass_blocks_per_sm(c->precision, a);
             if (o.max_blocks > 0) cap = std::min<int64_t>(cap, o.max_blocks);
             pl.grid = (int)std::max<int64_t>(1, std::min(need, cap));

@@ -294,7 +294,7 @@ PassFn select_direct(int pm, int lm, bool pol);
 
 // Sweep launch of one colour class; lower_mode, params_mode and deg pick the compiled variant.
 void launch_pass32(const PassArgs &a, int grid, void *stream);
-void launch_pass64(const PassArgs &a, int grid, void *stream);
+void launch_pass64(const PassArgs &a, int grid, int threads, void *stream);  // threads: 32 .. kThreads
 void launch_reduce(const ReduceArgs &a, void *stream);
 void launch_renorm32(const RenormArgs &a, int grid, void *stream);
 void launch_renorm64(const RenormArgs &a, int grid, void *stream);

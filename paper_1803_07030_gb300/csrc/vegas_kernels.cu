@@ -1048,8 +1048,8 @@ void launch_pass32(const PassArgs &a, int grid, void *stream) {
     select_pass32(a)<<<grid, kThreads, pass32_smem(a), (cudaStream_t)stream>>>(a);
 }
 
-void launch_pass64(const PassArgs &a, int grid, void *stream) {
-    pass64_kernel<<<grid, kThreads, 0, (cudaStream_t)stream>>>(a);
+void launch_pass64(const PassArgs &a, int grid, int threads, void *stream) {
+    pass64_kernel<<<grid, threads, 0, (cudaStream_t)stream>>>(a);
 }
 
 void launch_reduce(const ReduceArgs &a, void *stream) {
