@@ -955,7 +955,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         c->coop_grid = c->sm_count * coop_blocks_per_sm(any_policy);
         if (o.max_blocks > 0) c->coop_grid = std::min(c->coop_grid, o.max_blocks);
         DALLOC(c->d_bar, sizeof(GridBarrier));
-        DALLOC(c->d_coop_partial, sizeof(double) * 4 * (size_t)c->coop_grid * R);
+        DALLOC(c->d_coop_partial, sizeof(double) * 4 * 2 * (size_t)c->coop_grid * R);  // two MCS in turn
         CoopArgs &ca = c->coop;
         std::memset(&ca, 0, sizeof ca);
         ca.pass = c->passes[0].args;

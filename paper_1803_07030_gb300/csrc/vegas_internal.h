@@ -260,7 +260,7 @@ struct CoopArgs {
     int32_t n_colours;
     int32_t mcs;               // MCS in this launch
     GridBarrier *bar;
-    double *partial;           // [block][R][4]
+    double *partial;           // [2][block][R][4]: the partials of two MCS in turn
     int64_t timeout_ns;        // longest wait at one barrier
     int32_t skip_block;        // fault injection: this block never arrives (-1: none)
 };

@@ -809,6 +809,40 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
     const float beta = (float)sc[0], B = (float)sc[1];
     const bool skip = (int)blockIdx.x == ca.skip_block;
     bool nan_seen = false;
+    // block 0 adds the block partials of MCS mm (buffer mm & 1) into the history: one warp per
+    // replica, lanes striding over the blocks, a fixed tree
+    auto record = [&](int mm) {
+        if (blockIdx.x != 0) return;
+        const double *part = ca.partial + (int64_t)(mm & 1) * gridDim.x * R * 4;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int rr = warp; rr < R; rr += NT / 32) {
+            double v[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int b = lane; b < (int)gridDim.x; b += 32) {
+                const double *p = part + ((int64_t)b * R + rr) * 4;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] += p[q];
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+            }
+            if (lane == 0) {
+                double *h = rs->hist + ((int64_t)(rec0 + mm) * a.n_inst + a.inst_local0 + rr) * 4;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) h[q] = v[q];
+                if (rs->acc) {
+                    const uint32_t n = rs->acc[a.inst_local0 + rr];
+                    rs->acc[a.inst_local0 + rr] = 0;
+                    if (rs->acc_hist) rs->acc_hist[(int64_t)(rec0 + mm) * a.n_inst + a.inst_local0 + rr] = n;
+                }
+            }
+        }
+    };
+    // With two or more classes the record of MCS m is taken after the first class barrier of
+    // MCS m + 1: every block wrote its partials and counts of MCS m before reaching it, and
+    // none adds the counts of MCS m + 1 before the next barrier, which block 0 reaches only
+    // after recording. That saves one grid barrier per MCS.
+    const bool deferred = ca.n_colours >= 2;
     for (int m = 0; m < ca.mcs; ++m) {
         const uint32_t t = t0 + (uint32_t)m;
         const bool log_accepts = a.alog && t < a.alog_mcs;
@@ -829,38 +863,20 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
                     a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
             }
             if (!grid_barrier(ca.bar, gridDim.x, ca.timeout_ns, a.err, skip)) return;
+            if (deferred && c == 0 && m > 0) record(m - 1);
         }
-        // per-MCS sums: block partials per replica, then a fixed-order sum by R threads
+        // per-MCS sums: block partials per replica into buffer m & 1
         acc.flush();
-        block_partials(acc.d, acc.nacc, R, ca.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs, a.inst_local0));
-        if (!grid_barrier(ca.bar, gridDim.x, ca.timeout_ns, a.err, skip)) return;
-        if (blockIdx.x == 0) {  // one warp per replica: lanes stride over blocks, fixed tree
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            for (int rr = warp; rr < R; rr += NT / 32) {
-                double v[4] = {0.0, 0.0, 0.0, 0.0};
-                for (int b = lane; b < (int)gridDim.x; b += 32) {
-                    const double *p = ca.partial + ((int64_t)b * R + rr) * 4;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) v[q] += p[q];
-                }
-                for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
-                }
-                if (lane == 0) {
-                    double *h = rs->hist + ((int64_t)(rec0 + m) * a.n_inst + a.inst_local0 + rr) * 4;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) h[q] = v[q];
-                    // every block added its count before the barrier; the next MCS adds only
-                    // after the first barrier of that MCS, which this block reaches later
-                    if (rs->acc) {
-                        const uint32_t n = rs->acc[a.inst_local0 + rr];
-                        rs->acc[a.inst_local0 + rr] = 0;
-                        if (rs->acc_hist) rs->acc_hist[(int64_t)(rec0 + m) * a.n_inst + a.inst_local0 + rr] = n;
-                    }
-                }
-            }
+        block_partials(acc.d, acc.nacc, R, ca.partial + ((int64_t)(m & 1) * gridDim.x + blockIdx.x) * R * 4,
+                       acc_counters(rs, a.inst_local0));
+        if (!deferred) {
+            if (!grid_barrier(ca.bar, gridDim.x, ca.timeout_ns, a.err, skip)) return;
+            record(m);
         }
+    }
+    if (deferred && ca.mcs > 0) {
+        if (!grid_barrier(ca.bar, gridDim.x, ca.timeout_ns, a.err, skip)) return;
+        record(ca.mcs - 1);
     }
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }

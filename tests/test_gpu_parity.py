@@ -270,6 +270,7 @@ def test_cooperative_sweep_equals_per_class_sweep(make, R):
             assert np.array_equal(a.spins(i), b.spins(i)), i
         assert_fp32_history_close(a.history(), b.history(), s.n_sites)
         assert np.array_equal(a.accept_log(), b.accept_log())
+        assert np.array_equal(a.accept_history(), b.accept_history())  # recorded one MCS late, in order
 
 
 def test_cooperative_barrier_timeout_is_reported_not_hung():
