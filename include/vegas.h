@@ -147,8 +147,8 @@ typedef struct {
                                first accept_log_mcs MCS (debugging and parity). Default 0. */
     int32_t timing;         /* 1: time every sweep launch with CUDA events. Default 0. */
     int32_t graphs;         /* 1: launch the sweeps as CUDA graphs: a whole run of the per-class
-                               sweep as one graph (a conditional while node over its
-                               temperature/field steps), the other sweeps one graph per step;
+                               or resident sweep as one graph (a conditional while node over its
+                               temperature/field steps), the other sweeps directly;
                                2: one graph per step for every sweep; 0: no graphs. Default 1. */
     int32_t max_blocks;     /* > 0: at most this many thread blocks per sweep launch (tests,
                                tuning); 0 = as many as fit on the device. Default 0. */
@@ -214,8 +214,8 @@ typedef struct {
     int32_t cluster_blocks;     /* blocks per cluster of the cluster sweep when it is in use
                                    (chosen by the autotuner), else 0 */
     int64_t graph_launches;     /* CUDA graph launches so far: with graphs = 1 a run of the
-                                   per-class sweep is one launch of a graph whose conditional
-                                   while node repeats one temperature/field step */
+                                   per-class or resident sweep is one launch of a graph whose
+                                   conditional while node repeats one temperature/field step */
     int32_t split_sites;        /* cluster sweep in use: instances of at most this many sites
                                    are swept by one block each, larger ones by a whole cluster
                                    (chosen by the autotuner; 0 = every instance by a cluster) */

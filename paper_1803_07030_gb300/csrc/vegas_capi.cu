@@ -113,8 +113,8 @@ struct vegas_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<std::pair<int64_t, cudaGraphExec_t>> step_graphs;  // key: mcs * 2 + variant
-    // run graphs of the per-class sweep: a conditional while node over temperature/field steps
-    // whose body is one whole step; key: mcs
+    // run graphs of the per-class and resident sweeps: a conditional while node over
+    // temperature/field steps whose body is one whole step; key: mcs * 4 + variant
     std::vector<std::pair<int64_t, cudaGraphExec_t>> run_graphs;
     std::vector<cudaGraph_t> run_graph_defs;
     bool run_graph_failed = false;
@@ -328,14 +328,15 @@ vegas_status step_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
     return VEGAS_OK;
 }
 
-// Graph of a whole run of the per-class sweep: a conditional while node whose body is one
-// temperature/field step (mcs MCS, the renormalisation, the snapshot) followed by the loop
+// Graph of a whole run of the per-class or resident sweep: a conditional while node whose body
+// is one temperature/field step (mcs MCS, the renormalisation, the snapshot) followed by the loop
 // control kernel, so one launch runs every step of the schedule (the step index, schedule
 // and record count come from the run state). Returns false, leaving no capture open, when
 // the device or driver cannot build it; the caller then launches the step graph per step.
 bool run_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
+    const int64_t key = (int64_t)mcs * 4 + c->variant;
     for (auto &kv : c->run_graphs)
-        if (kv.first == mcs) {
+        if (kv.first == key) {
             *out = kv.second;
             return true;
         }
@@ -368,7 +369,11 @@ bool run_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
         cudaSuccess)
         return give_up();
     capturing = true;
-    for (int32_t m = 0; m < mcs; ++m) enqueue_mcs(c, c->cap_stream, nullptr);
+    if (c->variant == 1) {
+        enqueue_resident(c, c->cap_stream, mcs);
+    } else {
+        for (int32_t m = 0; m < mcs; ++m) enqueue_mcs(c, c->cap_stream, nullptr);
+    }
     enqueue_renorm(c, c->cap_stream);
     launch_run_ctrl(c->d_run, (unsigned long long)loop, c->cap_stream);
     cudaGraph_t captured = nullptr;
@@ -376,7 +381,7 @@ bool run_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
     if (cudaStreamEndCapture(c->cap_stream, &captured) != cudaSuccess) return give_up();
     if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) return give_up();
     c->run_graph_defs.push_back(g);
-    c->run_graphs.emplace_back(mcs, ge);
+    c->run_graphs.emplace_back(key, ge);
     *out = ge;
     return true;
 }
@@ -1384,15 +1389,18 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             c->tuned = true;
         }
 
-        if (m0 == 0 && c->tuned && use_graph && c->opt.graphs == 1 && c->variant == 0 && step_graph_nodes(c, mcs) > 0) {
+        if (m0 == 0 && c->tuned && use_graph && c->opt.graphs == 1 && c->variant <= 1 && step_graph_nodes(c, mcs) > 0) {
             // every remaining step in one launch of the run graph
             cudaGraphExec_t ge;
             if (run_graph(c, mcs, &ge)) {
                 CK(c, cudaGraphLaunch(ge, c->stream));
                 c->graph_launches++;
                 const int64_t left = n_steps - s;
-                c->kernel_launches += left * (step_graph_nodes(c, mcs) + 1);
-                c->sweep_launches += left * (int64_t)mcs * (int64_t)c->passes.size();
+                // kernels per step: the sweep's (resident + advance, or mcs x (passes + reduction)),
+                // the renormalisation, the snapshot, the loop control
+                const int64_t sweep_k = c->variant == 1 ? 2 : (int64_t)mcs * ((int64_t)c->passes.size() + 1);
+                c->kernel_launches += left * (sweep_k + 2 + (c->opt.snapshots ? 1 : 0));
+                c->sweep_launches += c->variant == 1 ? left : left * (int64_t)mcs * (int64_t)c->passes.size();
                 break;
             }
         }

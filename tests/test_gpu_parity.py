@@ -318,6 +318,23 @@ def test_whole_run_is_one_graph_launch(precision):
             assert np.array_equal(a.snapshot(0, k), b.snapshot(0, k)), k
 
 
+def test_resident_run_is_one_graph_launch():
+    """The resident sweep's run graph: one launch per run (a persistent launch per step
+    inside the conditional loop), the same chain as without graphs."""
+    ps = nanoparticle_batch(6, seed=14, r_max=5.5)
+    T = np.linspace(0.4, 2.0, len(ps))[:, None] * np.array([[1.0, 0.8, 0.6, 0.5]])
+    B = np.full_like(T, 0.1)
+    with ctx(ps, seed=30, variant=1, snapshots=True) as a, ctx(ps, seed=30, variant=1, snapshots=True, graphs=False) as b:
+        a.run(T, B, 6)
+        b.run(T, B, 6)
+        assert a.stats()["graph_launches"] == 1 and b.stats()["graph_launches"] == 0
+        for i in range(len(ps)):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+            for k in range(4):
+                assert np.array_equal(a.snapshot(i, k), b.snapshot(i, k)), (i, k)
+        assert np.array_equal(a.history(), b.history())
+
+
 def test_autotuner_picks_a_sweep_and_block_shape():
     """The first run times every eligible sweep and block shape (threads per block of the
     resident sweep, blocks per cluster of the cluster sweep) on the real chain; whatever it
