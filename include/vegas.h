@@ -146,10 +146,12 @@ typedef struct {
     int32_t accept_log_mcs; /* > 0: keep the accept/reject bit of every attempt of the
                                first accept_log_mcs MCS (debugging and parity). Default 0. */
     int32_t timing;         /* 1: time every sweep launch with CUDA events. Default 0. */
-    int32_t graphs;         /* 1: launch the sweeps as CUDA graphs: a whole run of the per-class
-                               or resident sweep as one graph (a conditional while node over its
-                               temperature/field steps), the other sweeps directly;
-                               2: one graph per step for every sweep; 0: no graphs. Default 1. */
+    int32_t graphs;         /* 1: launch a whole run as one CUDA graph (a conditional while
+                               node over its temperature/field steps; the launches of one step
+                               as its body), falling back to the next form if the device or
+                               driver cannot build it;
+                               2: one graph per step (per-class and resident sweeps; the others
+                               launch directly); 0: no graphs. Default 1. */
     int32_t max_blocks;     /* > 0: at most this many thread blocks per sweep launch (tests,
                                tuning); 0 = as many as fit on the device. Default 0. */
     int32_t pipeline_depth; /* FP32 sweeps of rows with six links: groups of rows kept in
@@ -213,9 +215,9 @@ typedef struct {
                                    is chosen by the autotuner: 256 or 512) */
     int32_t cluster_blocks;     /* blocks per cluster of the cluster sweep when it is in use
                                    (chosen by the autotuner), else 0 */
-    int64_t graph_launches;     /* CUDA graph launches so far: with graphs = 1 a run of the
-                                   per-class or resident sweep is one launch of a graph whose
-                                   conditional while node repeats one temperature/field step */
+    int64_t graph_launches;     /* CUDA graph launches so far: with graphs = 1 a run is one
+                                   launch of a graph whose conditional while node repeats one
+                                   temperature/field step */
     int32_t split_sites;        /* cluster sweep in use: instances of at most this many sites
                                    are swept by one block each, larger ones by a whole cluster
                                    (chosen by the autotuner; 0 = every instance by a cluster) */

@@ -295,7 +295,9 @@ constexpr int64_t kMaxStepGraphNodes = 20000;
 // Launches of one whole step (mcs MCS and the renormalisation) for the chosen variant, or
 // -1 when such a graph would be too large.
 int64_t step_graph_nodes(const vegas_ctx *c, int32_t mcs) {
-    const int64_t n = (c->variant >= 1 ? 4 : (int64_t)mcs * ((int64_t)c->passes.size() + 1) + 1) + (c->opt.snapshots ? 1 : 0);
+    const int64_t sweep = c->variant == 4 ? 3 * (int64_t)mcs
+                                         : (c->variant >= 1 ? 3 : (int64_t)mcs * ((int64_t)c->passes.size() + 1));
+    const int64_t n = sweep + 1 + (c->opt.snapshots ? 1 : 0);
     return n <= kMaxStepGraphNodes ? n : -1;
 }
 
@@ -328,8 +330,8 @@ vegas_status step_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
     return VEGAS_OK;
 }
 
-// Graph of a whole run of the per-class or resident sweep: a conditional while node whose body
-// is one temperature/field step (mcs MCS, the renormalisation, the snapshot) followed by the loop
+// Graph of a whole run of a sweep: a conditional while node whose body is one
+// temperature/field step (mcs MCS, the renormalisation, the snapshot) followed by the loop
 // control kernel, so one launch runs every step of the schedule (the step index, schedule
 // and record count come from the run state). Returns false, leaving no capture open, when
 // the device or driver cannot build it; the caller then launches the step graph per step.
@@ -371,6 +373,12 @@ bool run_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
     capturing = true;
     if (c->variant == 1) {
         enqueue_resident(c, c->cap_stream, mcs);
+    } else if (c->variant == 2) {
+        enqueue_coop(c, c->cap_stream, mcs);
+    } else if (c->variant == 3) {
+        enqueue_cluster(c, c->cap_stream, mcs);
+    } else if (c->variant == 4) {
+        for (int32_t m = 0; m < mcs; ++m) enqueue_wave(c, c->cap_stream);
     } else {
         for (int32_t m = 0; m < mcs; ++m) enqueue_mcs(c, c->cap_stream, nullptr);
     }
@@ -1389,7 +1397,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             c->tuned = true;
         }
 
-        if (m0 == 0 && c->tuned && use_graph && c->opt.graphs == 1 && c->variant <= 1 && step_graph_nodes(c, mcs) > 0) {
+        if (m0 == 0 && c->tuned && use_graph && c->opt.graphs == 1 && step_graph_nodes(c, mcs) > 0) {
             // every remaining step in one launch of the run graph
             cudaGraphExec_t ge;
             if (run_graph(c, mcs, &ge)) {
@@ -1398,9 +1406,11 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                 const int64_t left = n_steps - s;
                 // kernels per step: the sweep's (resident + advance, or mcs x (passes + reduction)),
                 // the renormalisation, the snapshot, the loop control
-                const int64_t sweep_k = c->variant == 1 ? 2 : (int64_t)mcs * ((int64_t)c->passes.size() + 1);
+                const int64_t sweep_k = c->variant == 4 ? 2 * (int64_t)mcs
+                                        : (c->variant >= 1 ? 2 : (int64_t)mcs * ((int64_t)c->passes.size() + 1));
                 c->kernel_launches += left * (sweep_k + 2 + (c->opt.snapshots ? 1 : 0));
-                c->sweep_launches += c->variant == 1 ? left : left * (int64_t)mcs * (int64_t)c->passes.size();
+                c->sweep_launches += c->variant == 4 ? left * (int64_t)mcs
+                                     : (c->variant >= 1 ? left : left * (int64_t)mcs * (int64_t)c->passes.size());
                 break;
             }
         }

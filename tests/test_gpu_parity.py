@@ -318,16 +318,20 @@ def test_whole_run_is_one_graph_launch(precision):
             assert np.array_equal(a.snapshot(0, k), b.snapshot(0, k)), k
 
 
-def test_resident_run_is_one_graph_launch():
-    """The resident sweep's run graph: one launch per run (a persistent launch per step
-    inside the conditional loop), the same chain as without graphs."""
-    ps = nanoparticle_batch(6, seed=14, r_max=5.5)
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_persistent_run_is_one_graph_launch(variant):
+    """The run graph of the resident, cooperative and cluster sweeps: one launch per run (a
+    persistent launch per step inside the conditional loop), the same chain as without
+    graphs."""
+    ps = nanoparticle_batch(6, seed=14, r_max=5.5) if variant != 2 else [sc_periodic(10, k_uni=0.1)]
     T = np.linspace(0.4, 2.0, len(ps))[:, None] * np.array([[1.0, 0.8, 0.6, 0.5]])
     B = np.full_like(T, 0.1)
-    with ctx(ps, seed=30, variant=1, snapshots=True) as a, ctx(ps, seed=30, variant=1, snapshots=True, graphs=False) as b:
+    with ctx(ps, seed=30, variant=variant, snapshots=True) as a, \
+            ctx(ps, seed=30, variant=variant, snapshots=True, graphs=False) as b:
         a.run(T, B, 6)
         b.run(T, B, 6)
         assert a.stats()["graph_launches"] == 1 and b.stats()["graph_launches"] == 0
+        assert a.stats()["variant"] == variant
         for i in range(len(ps)):
             assert np.array_equal(a.spins(i), b.spins(i)), i
             for k in range(4):

@@ -112,6 +112,16 @@ def test_wave_continues_across_runs_and_set_spins():
         assert_same_chain(a, b, s.n_sites)
 
 
+def test_wave_run_is_one_graph_launch():
+    s = lattice((8, 8, 12), 1)
+    T, B = schedule(3)
+    with ctx([s], seed=46, variant=4) as a, ctx([s], seed=46, variant=4, graphs=False) as b:
+        a.run(T, B, 4)
+        b.run(T, B, 4)
+        assert a.stats()["graph_launches"] == 1 and b.stats()["graph_launches"] == 0
+        assert_same_chain(a, b, s.n_sites)
+
+
 def test_wave_accept_log_matches():
     s = lattice((8, 6, 10), 1)
     T, B = schedule(1)
