@@ -234,7 +234,8 @@ def fcc_sphere(radius: float, a: float = 1.0, centre: Sequence[float] = (0.0, 0.
     Lattice points are (a/2)*(i, j, k) with i+j+k even; nearest neighbours sit at the 12
     offsets (+-1, +-1, 0) and permutations (distance a/sqrt 2). Sites are kept when
     |r - centre| <= radius and numbered in (i, j, k) lexicographic order; each row lists
-    the neighbours present in the fixed offset order.
+    the neighbours present in the fixed offset order. The sample carries the sublattice
+    colouring (4 colour classes).
     """
     c = np.asarray(centre, dtype=np.float64)
     h = a / 2.0
@@ -259,7 +260,12 @@ def fcc_sphere(radius: float, a: float = 1.0, centre: Sequence[float] = (0.0, 0.
         nbr[inside, k] = index[qq[:, 0], qq[:, 1], qq[:, 2]]
     row_ptr, col, Jv = _csr_from_neighbour_table(nbr, np.full((n, 12), float(J)))
     s = Sample(name=f"fcc_r{radius:g}", row_ptr=row_ptr, col=col, J=Jv)
-    s.positions = (coords + lo).astype(np.float64) * h
+    ijk = coords + lo
+    s.positions = ijk.astype(np.float64) * h
+    # the four simple-cubic sublattices of the fcc lattice: every nearest-neighbour offset
+    # changes the parity of exactly two of i, j, k, so (i mod 2) + 2 (j mod 2) is a proper
+    # colouring with 4 classes (the greedy colouring in site order needs 7 on these spheres)
+    s.colour = ((ijk[:, 0] & 1) + 2 * (ijk[:, 1] & 1)).astype(np.int32)
     s.meta = {"radius": radius, "a": a, "centre": c.tolist()}
     return s
 

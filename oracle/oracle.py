@@ -265,6 +265,8 @@ def run(sample, T, B, mcs: int, seed: int = 1, spins=None, inst_base: int = 0, t
     """Run the chain for every instance in T's first axis.
 
     T, B: [n_inst, n_steps]. spins: None (Philox initial state) or [n_inst, n, 3].
+    colour: the colour classes of the sweep, [n] (default: the sample's own colouring if it
+    carries one, as the library takes it, else the greedy colouring in site order).
     sigma: None or [n_inst] starting widths of the adaptive policy (<= 0: the policy's
     parameter). n_types > 0: also the magnetization per site type after every MCS.
     snapshots: also the spins at the end of every step. Returns dict(spins=[n_inst,n,3],
@@ -281,6 +283,8 @@ def run(sample, T, B, mcs: int, seed: int = 1, spins=None, inst_base: int = 0, t
     S = np.zeros((n_inst, n, 3)) if spins is None else np.array(spins, dtype=np.float64).reshape(n_inst, n, 3)
     hist = np.zeros((n_inst, n_steps * mcs, 4))
     alog = np.zeros((n_inst, log_mcs, n), dtype=np.uint8) if log_mcs > 0 else None
+    if colour is None:
+        colour = getattr(sample, "colour", None)
     cl = None if colour is None else np.ascontiguousarray(colour, dtype=np.int32)
     acc = np.zeros((n_inst, n_steps * mcs), dtype=np.int64)
     sg = np.zeros(n_inst) if sigma is None else np.array(np.broadcast_to(sigma, (n_inst,)), dtype=np.float64)
