@@ -418,16 +418,22 @@ class Context:
     field_axis, k_uni, e_uni, k_cub, colour, init_spins, positions, type_policy, type_param
     (the vegas_sample fields).
     stream: a cudaStream_t as int, 'torch' for torch's current stream, or None (own stream).
+    The other keywords are the vegas_options fields of the same names (include/vegas.h):
+    variant (-1 automatic, 0 per class, 1 resident, 2 cooperative, 3 cluster, 4 wavefront),
+    graphs (1 a run as one graph, 2 a graph per step, 0 none), the cluster and grouping shapes
+    (cluster_blocks, cluster_threads, cluster_split, group_threads, group_sites; 0 =
+    automatic or off), wave_lag, and the testing options max_blocks, pipeline_depth,
+    timeout_ns, fault_inject. library: load another build (the debug build) for this and
+    later contexts.
     """
 
     def __init__(self, samples: Sequence, precision: int = 32, replicas: int = 1, seed: int = 1,
                  inst_base: int = 0, device: int = -1, stream="torch", variant: int = -1,
                  accept_log_mcs: int = 0, timing: bool = False, graphs: int = 1, max_blocks: int = 0,
                  pipeline_depth: int = 0, timeout_ns: int = 0, fault_inject: int = 0,
-                 type_stats: bool = False, snapshots: bool = False, cluster_blocks: int = 0, cluster_threads: int = 0, cluster_split: int = 0,
-                 group_threads: int = 0, group_sites: int = 0,
-                 wave_lag: int = 0,
-                 library: Optional[str] = None):
+                 type_stats: bool = False, snapshots: bool = False, cluster_blocks: int = 0,
+                 cluster_threads: int = 0, cluster_split: int = 0, group_threads: int = 0, group_sites: int = 0,
+                 wave_lag: int = 0, library: Optional[str] = None):
         self.samples = list(samples)
         self.n_sites = [int(np.asarray(s.row_ptr).shape[0] - 1) for s in self.samples]
         if library is not None:
