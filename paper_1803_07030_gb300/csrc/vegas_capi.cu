@@ -967,6 +967,14 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     if (!p64 && n_samples == 1 && !c->passes.empty() && !c->any_adaptive && !o.type_stats) {
         c->coop_grid = c->sm_count * coop_blocks_per_sm(any_policy);
         if (o.max_blocks > 0) c->coop_grid = std::min(c->coop_grid, o.max_blocks);
+        {  // no more blocks than one thread per site and replica of the largest class: a small
+           // sample's grid barriers then wait on the blocks that have work only
+            const SampleInfo &si = c->samples[0];
+            int64_t widest = 0;
+            for (int32_t q = 0; q < si.n_colours; ++q)
+                widest = std::max<int64_t>(widest, (int64_t)(si.cstart[(size_t)q + 1] - si.cstart[(size_t)q]) * R);
+            c->coop_grid = (int)std::max<int64_t>(1, std::min<int64_t>(c->coop_grid, (widest + kCoopThreads - 1) / kCoopThreads));
+        }
         DALLOC(c->d_bar, sizeof(GridBarrier));
         DALLOC(c->d_coop_partial, sizeof(double) * 4 * 2 * (size_t)c->coop_grid * R);  // two MCS in turn
         CoopArgs &ca = c->coop;

@@ -15,6 +15,7 @@ namespace vegas {
 constexpr int kMaxColours = 64;
 constexpr int kMaxTypes = 64;   // site types tracked by the per-type statistics
 constexpr int kThreads = 256;  // threads per block of the sweep kernels
+constexpr int kCoopThreads = 256;  // threads per block of the cooperative sweep
 
 // Random-number purposes (fourth Philox counter word; low 16 bits hold a candidate index).
 constexpr uint32_t kPurposeTrial64 = 0x00000u;   // FP64 sphere candidates

@@ -1129,7 +1129,6 @@ void launch_snapshot(const void *spins, void *snap, int64_t n16, const RunState 
     snapshot_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>((const uint4 *)spins, (uint4 *)snap, n16, run);
 }
 
-constexpr int kCoopThreads = 256;
 
 int launch_coop(const CoopArgs &a, int grid, void *stream) {
     cudaLaunchConfig_t cfg = {};
