@@ -151,7 +151,10 @@ def test_policy_table_without_params_rejected(lib):
 
 @pytest.mark.parametrize("opt", [{"precision": 16}, {"replicas": 3}, {"replicas": 64}, {"variant": 7},
                                  {"accept_log_mcs": -1}, {"type_stats": 2}, {"snapshots": -1},
-                                 {"variant": 2, "type_stats": 1}, {"graphs": 3}, {"graphs": -1}])
+                                 {"variant": 2, "type_stats": 1}, {"graphs": 3}, {"graphs": -1},
+                                 {"cluster_blocks": 1}, {"cluster_blocks": 17}, {"cluster_threads": 300},
+                                 {"cluster_split": -1}, {"group_threads": 100}, {"group_sites": -1},
+                                 {"wave_lag": -1}, {"variant": 5}])
 def test_invalid_options_rejected(lib, opt):
     st, msg = _create_status([sc_periodic(4)], **opt)
     assert st == vb.EINVAL, (opt, msg)
