@@ -334,7 +334,8 @@ vegas_status step_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
 // temperature/field step (mcs MCS, the renormalisation, the snapshot) followed by the loop
 // control kernel, so one launch runs every step of the schedule (the step index, schedule
 // and record count come from the run state). Returns false, leaving no capture open, when
-// the device or driver cannot build it; the caller then launches the step graph per step.
+// the device or driver cannot build it; the caller then falls back to one graph per step
+// (per-class and resident sweeps) or direct launches.
 bool run_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
     const int64_t key = (int64_t)mcs * 4 + c->variant;
     for (auto &kv : c->run_graphs)
@@ -1412,8 +1413,9 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                 CK(c, cudaGraphLaunch(ge, c->stream));
                 c->graph_launches++;
                 const int64_t left = n_steps - s;
-                // kernels per step: the sweep's (resident + advance, or mcs x (passes + reduction)),
-                // the renormalisation, the snapshot, the loop control
+                // kernels per step: the sweep's (a persistent launch + advance; mcs x (wavefront +
+                // reduction); or mcs x (passes + reduction)), the renormalisation, the snapshot,
+                // the loop control
                 const int64_t sweep_k = c->variant == 4 ? 2 * (int64_t)mcs
                                         : (c->variant >= 1 ? 2 : (int64_t)mcs * ((int64_t)c->passes.size() + 1));
                 c->kernel_launches += left * (sweep_k + 2 + (c->opt.snapshots ? 1 : 0));
