@@ -211,6 +211,27 @@ def apply_policy(samples, spec):
     return spec
 
 
+def host_description() -> dict:
+    """The host the CPU baseline ran on: CPU model and the oracle's compiler (best effort; a
+    missing tool leaves its field empty)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    compiler = ""
+    try:
+        compiler = subprocess.run(["gcc", "--version"], capture_output=True, text=True, timeout=10).stdout.splitlines()[0]
+    except (OSError, subprocess.SubprocessError, IndexError):
+        pass
+    return {"cpu_model": model, "logical_cpus": os.cpu_count() or 0, "compiler": compiler,
+            "build": "gcc -O2 -ffp-contract=off (oracle)"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -236,7 +257,8 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_desc(args.mcs),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_threads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_threads, "kind": "oracle", "sample": sample,
+                         "host": host_description()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -357,7 +379,7 @@ def run_ours(args):
                          else "fallback 6.8 TB/s",
                          "kernel": kname, "bytes_per_attempt": BYTES_PER_ATTEMPT,
                          "attempts_per_launch": attempts_per_launch, "avg_launch_ms": sweep_ms},
-            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "host": host_description(),
                              "sample": f"1 MCS of {cores} replicas (one per host thread) of the {L_SIDE}^3 lattice, "
                                        f"{cpu_dt:.1f} s"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -494,7 +516,7 @@ def run_analysis(args):
         "config": {"workload": "1024 histories x 10,000 records (AR(1), tau ~ 10), cut 2000, 20 bins; "
                                "reweighting 32 runs x 20,000 samples to 64 temperatures"},
         "reweight": {"iterations": it, "s": tr, "sample_iterations_per_s": K * n * it / tr},
-        "cpu_baseline": {"value": ln / to, "unit": "records/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": ln / to, "unit": "records/s", "cores": 1, "kind": "oracle", "host": host_description(),
                          "sample": "8 of the 1024 histories", "reweight_sample_iterations_per_s": K * n / tro},
     }
     print(json.dumps(line), flush=True)
@@ -564,7 +586,7 @@ def run_ising(args):
                      "peak_source": "152 SMs x 4 issue slots x median SM clock (derived)",
                      "kernel": "ising_pass_kernel<2>", "warp_instructions_per_attempt": inst,
                      "attempts_per_launch": per_launch, "avg_launch_ms": launch_ms},
-        "cpu_baseline": {"value": 256 * 256 * 4 * 10 / cpu_dt, "unit": "attempts/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": 256 * 256 * 4 * 10 / cpu_dt, "unit": "attempts/s", "cores": 1, "kind": "oracle", "host": host_description(),
                          "sample": "256^2 x 4 replicas x 10 MCS"},
         "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"], "clocks": clocks,
     }
