@@ -81,6 +81,38 @@ def rank_instances(rank: int, world: int, replicas: int = REPLICAS) -> list:
     return list(range(rank * replicas, (rank + 1) * replicas))
 
 
+def workload_share(w, rank: int, world: int) -> dict:
+    """The part of a secondary workload one rank runs. A workload of several samples is split
+    into contiguous blocks of samples balanced by attempts (total work fixed: strong scaling);
+    a workload of one sample runs whole on every rank as an independent copy whose instance ids
+    start at rank * n_inst (weak scaling). Instance ids keep the sample-major numbering either
+    way, so a rank's results are those of the same instances in a single run."""
+    from paper_1803_07030_gb300.shard import contiguous_shards, sample_costs
+
+    R = w.replicas
+    costs = sample_costs(w.samples, R, w.n_steps, w.mcs)
+    if len(w.samples) > 1:
+        shards = contiguous_shards(costs, world)
+        b, e = shards[rank]
+        loads = [sum(costs[x:y]) for x, y in shards]
+        return {"samples": w.samples[b:e], "T": w.T[b * R:e * R], "B": w.B[b * R:e * R], "inst_base": b * R,
+                "range": (b, e), "attempts": loads[rank], "job_attempts": sum(costs), "scaling": "strong",
+                "max_over_mean": max(loads) * world / max(1, sum(costs))}
+    return {"samples": w.samples, "T": w.T, "B": w.B, "inst_base": rank * w.n_inst, "range": (0, len(w.samples)),
+            "attempts": sum(costs), "job_attempts": sum(costs) * world, "scaling": "weak", "max_over_mean": 1.0}
+
+
+def sum_over_ranks(x: float, world: int, device=None) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
 def slowest_rank_ms(ms: float, world: int, device=None) -> float:
     """Max over ranks of the timed region (the job ends with its slowest rank)."""
     if world <= 1:
@@ -321,7 +353,8 @@ def run_ours(args):
     attempts_per_launch = REPLICAS * s.n_sites * kclasses // 2
     peak, peak_kind = peaks()
     achieved = BYTES_PER_ATTEMPT * attempts_per_launch / (sweep_ms / 1000.0) / 1e9
-    traffic = profiled_traffic(ksummary, ksources)
+    # the committed counters are those of the 256^3 workload; another side has none
+    traffic = profiled_traffic(ksummary, ksources) if L_SIDE == 256 else None
 
     if args.quick or policy:
         if rank == 0:
@@ -401,70 +434,106 @@ def run_ours(args):
 def run_workload(args):
     """One step = one vegas_run of the whole schedule of a secondary workload (the 8^3 FP64
     ferromagnet, the 64^3 hysteresis loop, the field-cooled core/shell particle, the 256
-    nanoparticles). For np256 the plain comparison runs every particle in its own context,
-    one after another, for a bounded number of MCS."""
+    nanoparticles). Under torchrun the 256 nanoparticles are split over the ranks in contiguous
+    blocks balanced by attempts, and a one-sample workload runs as an independent copy per rank
+    (`workload_share`); no collective touches the data path. For np256 at one GPU the plain
+    comparison runs every particle in its own context, one after another, for a bounded number
+    of MCS."""
     import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
     import paper_1803_07030_gb300 as vg
     from lattices import workload
 
     vg.build()
-    torch.cuda.set_device(0)
     w = workload(args.workload, mcs=args.mcs if args.mcs != MCS else None)
     policy = apply_policy(w.samples, args.policy)
+    share = workload_share(w, rank, world)
     stream = torch.cuda.current_stream()
-    ctx = vg.Context(w.samples, precision=w.precision, replicas=w.replicas, seed=w.seed,
-                     stream=int(stream.cuda_stream), variant=args.variant, type_stats=args.type_stats,
-                     snapshots=args.snapshots)
+    ctx = None
+    if share["samples"]:
+        ctx = vg.Context(share["samples"], precision=w.precision, replicas=w.replicas, seed=w.seed,
+                         inst_base=share["inst_base"], device=dev, stream=int(stream.cuda_stream),
+                         variant=args.variant, type_stats=args.type_stats, snapshots=args.snapshots)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
     for _ in range(args.warmup):
-        ctx.run(w.T, w.B, w.mcs)
-    torch.cuda.synchronize()
-    st0 = ctx.stats()
+        if ctx is not None:
+            ctx.run(share["T"], share["B"], w.mcs)
+    barrier()
+    st0 = ctx.stats() if ctx is not None else None
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(torch.cuda.current_device()) as clk:
+    with ClockSampler(dev) as clk:
         a.record(stream)
         for _ in range(args.steps):
-            ctx.run(w.T, w.B, w.mcs)
+            if ctx is not None:
+                ctx.run(share["T"], share["B"], w.mcs)
         b.record(stream)
-        torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
-    st1 = ctx.stats()
-    value = w.attempts() * args.steps / (ms / 1000.0)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if w.precision == 64 else "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "instances": w.n_inst, "sites": w.n_sites_total,
-                   "steps_x_mcs": [w.n_steps, w.mcs], "attempts_per_step": w.attempts(),
-                   "l2": "working set inside L2" if w.n_sites_total * 16 < 100e6 else "larger than L2",
-                   "policy": policy or "random", "type_stats": bool(args.type_stats),
-                   "snapshots": bool(args.snapshots)},
-        "variant": st1["variant"], "block_threads": st1["block_threads"], "cluster_blocks": st1["cluster_blocks"],
-        "split_sites": st1["split_sites"], "group_threads": st1["group_threads"], "group_sites": st1["group_sites"],
-        "gpu_launches": st1["kernel_launches"] - st0["kernel_launches"],
-        "clocks": clk.summary(),
-    }
-    ctx.close()
-    if args.workload == "np256" and not policy and not args.type_stats and not args.snapshots and not args.quick:
-        plain_mcs = min(w.mcs, 100)
-        plain_ms, plain_att = 0.0, 0
-        for p, smp in enumerate(w.samples):
-            with vg.Context([smp], precision=32, seed=w.seed, inst_base=p, variant=0,
-                            stream=int(stream.cuda_stream)) as q:
-                Tp, Bp = w.T[p:p + 1], w.B[p:p + 1]
-                q.run(Tp, Bp, 2)
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                q.run(Tp, Bp, plain_mcs)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                plain_ms += e0.elapsed_time(e1)
-                plain_att += smp.n_sites * plain_mcs
-        line["plain"] = {"value": plain_att / (plain_ms / 1000.0), "unit": UNIT,
-                         "note": f"each of the {len(w.samples)} particles in its own context, one launch per colour "
-                                 f"class, {plain_mcs} MCS each, run one after another"}
-        line["batched_over_plain"] = value / line["plain"]["value"]
-    print(json.dumps(line), flush=True)
+        barrier()
+    ms = slowest_rank_ms(a.elapsed_time(b), world, device="cuda")
+    st1 = ctx.stats() if ctx is not None else None
+    mine = float(st1["kernel_launches"] - st0["kernel_launches"]) if ctx is not None else 0.0
+    launches = sum_over_ranks(mine, world, device="cuda")
+    value = share["job_attempts"] * args.steps / (ms / 1000.0)
+    if ctx is not None:
+        ctx.close()
+    if rank == 0:
+        shape = {k: st1[k] for k in ("variant", "block_threads", "cluster_blocks", "split_sites", "group_threads",
+                                     "group_sites")} if st1 else {}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": share["scaling"], "vs_baseline": None, "dtype": "f64" if w.precision == 64 else "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "instances": w.n_inst, "sites": w.n_sites_total,
+                       "steps_x_mcs": [w.n_steps, w.mcs], "attempts_per_step": share["job_attempts"],
+                       "l2": "working set inside L2" if w.n_sites_total * 16 < 100e6 else "larger than L2",
+                       "policy": policy or "random", "type_stats": bool(args.type_stats),
+                       "snapshots": bool(args.snapshots)},
+            **shape,
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        if world > 1:
+            line["config"]["sharding"] = {
+                "by": "contiguous sample blocks balanced by attempts" if share["scaling"] == "strong"
+                else "one independent copy per rank", "max_over_mean_attempts": share["max_over_mean"]}
+        if args.workload == "np256" and world == 1 and not policy and not args.type_stats and not args.snapshots \
+                and not args.quick:
+            plain_mcs = min(w.mcs, 100)
+            plain_ms, plain_att = 0.0, 0
+            for p, smp in enumerate(w.samples):
+                with vg.Context([smp], precision=32, seed=w.seed, inst_base=p, variant=0,
+                                stream=int(stream.cuda_stream)) as q:
+                    Tp, Bp = w.T[p:p + 1], w.B[p:p + 1]
+                    q.run(Tp, Bp, 2)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    q.run(Tp, Bp, plain_mcs)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    plain_ms += e0.elapsed_time(e1)
+                    plain_att += smp.n_sites * plain_mcs
+            line["plain"] = {"value": plain_att / (plain_ms / 1000.0), "unit": UNIT,
+                             "note": f"each of the {len(w.samples)} particles in its own context, one launch per "
+                                     f"colour class, {plain_mcs} MCS each, run one after another"}
+            line["batched_over_plain"] = value / line["plain"]["value"]
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 

@@ -5,6 +5,7 @@ binding. Importing the package does not build anything; call build.build() first
 """
 
 from .build import LIB, build  # noqa: F401
+from .shard import contiguous_shards, rank_shard, sample_costs  # noqa: F401
 from .vegas import (  # noqa: F401
     AVG_FIELDS,
     POLICY_ADAPTIVE,

@@ -1,0 +1,182 @@
+"""The benchmark line's host logic on the CPU, with the device and the context faked.
+
+The fakes stand in for torch.cuda (events on a fake clock that each run advances) and for
+vg.Context (counts launches, returns an empty history); nothing of the method runs except
+the oracle's CPU baseline. The checks are the fields the line must carry, the arithmetic
+that turns the counted attempts and the timed milliseconds into `value`, the roofline
+fraction, and that the secondary workloads give every sample, with its instance ids, to the
+context.
+"""
+
+import json
+import sys
+import types
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+RUN_MS = 7.0      # fake device time of one run
+SWEEP_MS = 0.25   # fake device time of one sweep launch
+
+
+class Clock:
+    now = 0.0
+
+
+class FakeEvent:
+    def __init__(self, enable_timing=False):
+        self.t = None
+
+    def record(self, stream=None):
+        self.t = Clock.now
+
+    def elapsed_time(self, other):
+        return other.t - self.t
+
+
+class FakeContext:
+    made = []
+
+    def __init__(self, samples, precision=32, replicas=1, seed=1, inst_base=0, device=-1, stream=None,
+                 timing=False, variant=-1, type_stats=False, snapshots=False):
+        self.samples, self.R, self.inst_base, self.precision = list(samples), replicas, inst_base, precision
+        self.launches = self.sweeps = 0
+        self.sweep_ms = 0.0
+        self.hist_rows = 0
+        FakeContext.made.append(self)
+
+    @property
+    def n_inst(self):
+        return len(self.samples) * self.R
+
+    def run(self, T, B, mcs):
+        T, B = np.asarray(T), np.asarray(B)
+        assert T.shape == B.shape and T.shape[0] == self.n_inst
+        Clock.now += RUN_MS
+        n = T.shape[1] * mcs
+        self.launches += 3 * n
+        self.sweeps += 2 * n
+        self.sweep_ms += 2 * n * SWEEP_MS
+        self.hist_rows += n
+
+    def history(self):
+        return np.zeros((self.n_inst, self.hist_rows, 4))
+
+    def stats(self):
+        return {"kernel_launches": self.launches, "sweep_launches": self.sweeps, "sweep_ms": self.sweep_ms,
+                "variant": 0, "block_threads": 256, "cluster_blocks": 0, "split_sites": 0, "group_threads": 0,
+                "group_sites": 0}
+
+    def close(self):
+        pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+
+@pytest.fixture
+def fake_device(monkeypatch):
+    torch = pytest.importorskip("torch")
+    import paper_1803_07030_gb300 as vg
+
+    Clock.now = 0.0
+    FakeContext.made = []
+    for name, fn in (("set_device", lambda d: None), ("current_device", lambda: 0), ("synchronize", lambda: None),
+                     ("current_stream", lambda: types.SimpleNamespace(cuda_stream=0)), ("Event", FakeEvent)):
+        monkeypatch.setattr(torch.cuda, name, fn)
+    monkeypatch.setattr(vg, "build", lambda *a, **k: None)
+    monkeypatch.setattr(vg, "Context", FakeContext)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    return vg
+
+
+def args(**kw):
+    a = dict(gpus=1, steps=3, warmup=2, mcs=bench.MCS, impl="ours", side=bench.L_SIDE, workload="sg256x32",
+             policy="", variant=-1, analysis=False, ising=False, type_stats=False, snapshots=False, quick=False)
+    a.update(kw)
+    return types.SimpleNamespace(**a)
+
+
+def last_json(capsys):
+    return json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+
+
+def test_headline_line_fields_and_arithmetic(fake_device, capsys, monkeypatch):
+    side, mcs = 8, 4
+    monkeypatch.setattr(bench, "L_SIDE", side)
+    bench.run_ours(args(mcs=mcs, side=side))
+    line = last_json(capsys)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"):
+        assert k in line, k
+    n = side ** 3
+    attempts = bench.REPLICAS * n * mcs * 3
+    assert line["value"] == pytest.approx(attempts / (3 * RUN_MS / 1000.0))
+    assert line["ms_per_step"] == pytest.approx(RUN_MS)
+    assert line["n_gpus"] == 1 and line["steps"] == 3 and line["warmup"] == 2 and line["higher_is_better"]
+    assert line["gpu_launches"] == 3 * 3 * mcs and line["vs_baseline"] is None
+    r = line["roofline"]
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["kernel"] == "pass32_r32"
+    assert r["attempts_per_launch"] == bench.REPLICAS * n // 2
+    assert r["achieved"] == pytest.approx(bench.BYTES_PER_ATTEMPT * r["attempts_per_launch"] / (SWEEP_MS / 1e3) / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["traffic"] is None  # the committed counters describe the 256^3 lattice only
+    c = line["cpu_baseline"]
+    assert c["kind"] == "oracle" and c["cores"] >= 1 and c["value"] > 0 and "host" in c
+    e = line["e2e"]
+    assert e["h2d_bytes_per_step"] == bench.REPLICAS * 2 * 8 + 40
+    assert e["d2h_bytes_per_step"] == bench.REPLICAS * mcs * 4 * 8 + 4
+    made = FakeContext.made
+    assert made[0].R == bench.REPLICAS and made[0].inst_base == 0
+    assert [m.inst_base for m in made[1:]] == [0, bench.REPLICAS - 1]  # the plain leg's two replicas
+
+
+def test_quick_line(fake_device, capsys, monkeypatch):
+    monkeypatch.setattr(bench, "L_SIDE", 6)
+    bench.run_ours(args(mcs=1, steps=1, warmup=0, quick=True, side=6))
+    line = last_json(capsys)
+    assert line["quick"] and line["gpu_launches"] == 3 and line["avg_launch_ms"] == pytest.approx(SWEEP_MS)
+
+
+def test_traffic_is_read_only_while_the_summary_matches_the_source(tmp_path):
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1")
+    summary = tmp_path / "k.txt"
+    summary.write_text(f"kernel_source_sha256_16: {bench.kernel_hash([str(src)])}\ndram_bytes_per_launch: 1234\n")
+    assert bench.profiled_traffic(str(summary), [str(src)]) == 1234.0
+    src.write_text("kernel v2")
+    assert bench.profiled_traffic(str(summary), [str(src)]) is None
+    assert bench.profiled_traffic(str(tmp_path / "none.txt"), [str(src)]) is None
+    for name, (kernel, path, sources, classes) in bench.SWEEP_KERNELS.items():
+        text = open(path).read()
+        assert kernel in text and "kernel_source_sha256_16:" in text and "dram_bytes_per_launch:" in text, name
+
+
+@pytest.mark.parametrize("name", ["np256", "sc8_fp64"])
+def test_secondary_workload_line(fake_device, capsys, name):
+    from lattices import workload
+
+    bench.run_workload(args(workload=name, steps=2, warmup=1))
+    line = last_json(capsys)
+    w = workload(name)
+    main = FakeContext.made[0]
+    assert len(main.samples) == len(w.samples) and main.inst_base == 0 and main.precision == w.precision
+    assert line["value"] == pytest.approx(w.attempts() * 2 / (2 * RUN_MS / 1000.0))
+    assert line["config"]["attempts_per_step"] == w.attempts()
+    assert line["scaling"] == ("strong" if name == "np256" else "weak")
+    assert line["dtype"] == ("f64" if name == "sc8_fp64" else "f32")
+    assert line["gpu_launches"] == 3 * 2 * w.n_steps * w.mcs
+    if name == "np256":
+        plain = FakeContext.made[1:]
+        assert [m.inst_base for m in plain] == list(range(len(w.samples)))
+        assert line["batched_over_plain"] > 0
