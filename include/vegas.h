@@ -48,7 +48,7 @@
  *   the call. The library owns all device memory and frees it in vegas_destroy.
  * Errors: a call that fails returns a non-zero vegas_status and stores a message
  *   readable with vegas_last_error(ctx) (vegas_last_error(NULL) for vegas_create).
- *   After VEGAS_ECUDA or VEGAS_EDEVICE the context is poisoned: later calls return
+ *   After VEGAS_ECUDA, VEGAS_EDEVICE or VEGAS_ETIMEOUT the context is poisoned: later calls return
  *   VEGAS_ESTATE, except vegas_last_error, vegas_stats and vegas_destroy.
  * Threads: one context must not be used from two threads at once.
  */
@@ -69,9 +69,10 @@ typedef enum {
     VEGAS_EINVAL = 1,   /* invalid argument or sample (message says which) */
     VEGAS_ENOMEM = 2,   /* host or device allocation failed */
     VEGAS_ECUDA = 3,    /* a CUDA runtime call failed (no device, launch error, ...) */
-    VEGAS_ETIMEOUT = 4, /* a bounded device wait ran out (grid barrier of the cooperative sweep) */
+    VEGAS_ETIMEOUT = 4, /* a bounded device wait ran out (grid barrier of the cooperative sweep,
+                           dependency wait of the wavefront sweep) */
     VEGAS_EDEVICE = 5,  /* a kernel flagged an error: NaN energy change, sampler cap */
-    VEGAS_ESTATE = 6    /* context poisoned by an earlier ECUDA/EDEVICE */
+    VEGAS_ESTATE = 6    /* context poisoned by an earlier ECUDA/EDEVICE/ETIMEOUT */
 } vegas_status;
 
 /*
