@@ -1,6 +1,6 @@
 """Builds the CUDA library (libvegas.so) in-tree for sm_103a with nvcc and g++.
 
-The three translation units compile in parallel; the CUDA runtime is linked statically, so
+The translation units compile in parallel; the CUDA runtime is linked statically, so
 the library needs only the NVIDIA driver at run time.
 """
 
