@@ -411,7 +411,9 @@ vegas_status vegas_stats(const vegas_ctx *ctx, vegas_stats_t *out);
 /*
  * Greedy colouring used by vegas_create when a sample has no colouring: sites in index
  * order, each takes the smallest colour not used by an already coloured neighbour.
- * Host only (no device needed). Returns the number of colours, or -1 on invalid input.
+ * Host only (no device needed). Returns the number of colours, or -1 on invalid input
+ * (n_sites < 0, a NULL array, row_ptr not starting at 0 or decreasing, col out of range);
+ * row_ptr must hold n_sites + 1 entries and col row_ptr[n_sites].
  */
 int32_t vegas_greedy_colour(int32_t n_sites, const int64_t *row_ptr, const int32_t *col, int32_t *color_out);
 

@@ -65,6 +65,10 @@ std::vector<uint64_t> morton_keys(const double *pos, int32_t n) {
 
 extern "C" int32_t vegas_greedy_colour(int32_t n, const int64_t *row_ptr, const int32_t *col, int32_t *color) {
     if (n < 0 || (n > 0 && (!row_ptr || !color))) return -1;
+    if (n > 0 && row_ptr[0] != 0) return -1;
+    for (int32_t i = 0; i < n; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return -1;
+    if (n > 0 && row_ptr[n] > 0 && !col) return -1;
     std::vector<int32_t> seen;  // seen[c] == i  <=>  colour c is used by a coloured neighbour of i
     int32_t nc = 0;
     for (int32_t i = 0; i < n; ++i) color[i] = -1;
