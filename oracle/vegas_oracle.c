@@ -367,7 +367,6 @@ double vo_delta_e(const vo_sample *s, const double *S, int32_t i, const double S
     return (dEex + dEan) + dEcub;
 }
 
-/* S_i <- s_i * S_i / |S_i|, with f = s_i / sqrt((x^2 + y^2) + z^2). */
 /* 1 when site i follows the qIsing policy (discrete values along z). */
 static int is_qising(const vo_sample *s, int32_t i) {
     if (!s->type_policy) return 0;
@@ -375,6 +374,8 @@ static int is_qising(const vo_sample *s, int32_t i) {
     return ty >= 0 && ty < s->n_policy_types && s->type_policy[ty] == VO_QISING;
 }
 
+/* Renormalisation once per temperature/field step: S_i <- s_i * S_i / |S_i|, with
+ * f = s_i / sqrt((x^2 + y^2) + z^2); qIsing sites keep their length. */
 void vo_renormalise(const vo_sample *s, double *S) {
     for (int32_t i = 0; i < s->n; ++i) {
         if (is_qising(s, i)) continue;  /* discrete values keep their length */
