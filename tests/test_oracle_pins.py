@@ -31,7 +31,7 @@ import numpy as np
 import pytest
 from scipy import integrate, special, stats
 
-from conftest import ROOT, binned
+from conftest import binned
 
 import oracle
 from lattices import chain_open, dimers, free_spins, random_graph, sc_periodic, triangles
