@@ -276,6 +276,15 @@ vegas_status vegas_get_spins(const vegas_ctx *ctx, int32_t instance, double *out
 vegas_status vegas_set_spins(vegas_ctx *ctx, int32_t instance, const double *in);
 
 /*
+ * Set the global MCS counter t that keys the random numbers of the next MCS (the value
+ * vegas_stats reports as mcs_done). With the spins (vegas_set_spins) and, for adaptive
+ * policies, the widths (vegas_set_adaptive_width) of a checkpoint, a new context continues
+ * the chain bit for bit where the checkpointed one stopped. t < 2^32 - 1; VEGAS_EINVAL
+ * otherwise.
+ */
+vegas_status vegas_set_mcs_counter(vegas_ctx *ctx, uint32_t t);
+
+/*
  * Accept/reject bits of the first accept_log_mcs MCS (option), as
  * [mcs][n_instances][n_sites] bytes (1 = accepted) in the caller's site order.
  * out == NULL: size query.
@@ -399,6 +408,8 @@ vegas_status vegas_ising_history(const vegas_ising *ctx, double *out, size_t cap
 /* Spins of one replica as L^dims int8 (+1 / -1) in site-id order. */
 vegas_status vegas_ising_get_spins(const vegas_ising *ctx, int32_t replica, int8_t *out);
 vegas_status vegas_ising_set_spins(vegas_ising *ctx, int32_t replica, const int8_t *in);
+/* Global MCS counter of the next MCS, as vegas_set_mcs_counter (checkpoint/resume). */
+vegas_status vegas_ising_set_mcs_counter(vegas_ising *ctx, uint32_t t);
 /* n_instances, n_sites, records, mcs_done, kernel_launches, sweep_launches, sweep_ms,
  * last_run_ms, device_bytes are filled; the other fields are 0. */
 vegas_status vegas_ising_stats(const vegas_ising *ctx, vegas_stats_t *out);

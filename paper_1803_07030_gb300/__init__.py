@@ -34,6 +34,7 @@ from .vegas import (  # noqa: F401
     vegas_last_error,
     vegas_run,
     vegas_set_adaptive_width,
+    vegas_set_mcs_counter,
     vegas_set_spins,
     vegas_sweep_noalloc,
     vegas_stats,

@@ -1627,6 +1627,21 @@ extern "C" vegas_status vegas_set_adaptive_width(vegas_ctx *c, const double *in)
     return VEGAS_OK;
 }
 
+extern "C" vegas_status vegas_set_mcs_counter(vegas_ctx *c, uint32_t t) {
+    vegas_status st = check_usable(c);
+    if (st != VEGAS_OK) return st;
+    if (t == UINT32_MAX) return fail(c, VEGAS_EINVAL, "MCS counter must be below 2^32 - 1");
+    if (c->d_done) {
+        // the wavefront sweep's completion words hold t + 1 of past MCS; cleared, none can
+        // match an MCS of the new count before its class-0 block has finished
+        if ((st = set_device(c)) != VEGAS_OK) return st;
+        CK(c, cudaMemsetAsync(c->d_done, 0, sizeof(uint32_t) * (size_t)c->wave.nb0, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    c->t = t;
+    return VEGAS_OK;
+}
+
 namespace {
 
 vegas_status spins_io(vegas_ctx *c, int32_t inst, double *out, const double *in) {

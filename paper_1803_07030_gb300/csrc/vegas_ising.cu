@@ -559,6 +559,14 @@ extern "C" vegas_status vegas_ising_set_spins(vegas_ising *c, int32_t replica, c
     return ising_spins_io(c, replica, nullptr, in);
 }
 
+extern "C" vegas_status vegas_ising_set_mcs_counter(vegas_ising *c, uint32_t t) {
+    vegas_status st = ising_usable(c);
+    if (st != VEGAS_OK) return st;
+    if (t == UINT32_MAX) return ifail(c, VEGAS_EINVAL, "MCS counter must be below 2^32 - 1");
+    c->t = t;
+    return VEGAS_OK;
+}
+
 extern "C" vegas_status vegas_ising_stats(const vegas_ising *c, vegas_stats_t *o) {
     if (!c || !o) return VEGAS_EINVAL;
     std::memset(o, 0, sizeof *o);

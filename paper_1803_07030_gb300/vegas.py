@@ -128,6 +128,7 @@ SIGNATURES = {
     "vegas_history": (C.c_int, [P, P, C.c_size_t, P]),
     "vegas_get_spins": (C.c_int, [P, C.c_int32, P]),
     "vegas_set_spins": (C.c_int, [P, C.c_int32, P]),
+    "vegas_set_mcs_counter": (C.c_int, [P, C.c_uint32]),
     "vegas_accept_log": (C.c_int, [P, P, C.c_size_t, P]),
     "vegas_accept_history": (C.c_int, [P, P, C.c_size_t, P]),
     "vegas_adaptive_width": (C.c_int, [P, P]),
@@ -151,6 +152,7 @@ SIGNATURES = {
     "vegas_ising_history": (C.c_int, [P, P, C.c_size_t, P]),
     "vegas_ising_get_spins": (C.c_int, [P, C.c_int32, P]),
     "vegas_ising_set_spins": (C.c_int, [P, C.c_int32, P]),
+    "vegas_ising_set_mcs_counter": (C.c_int, [P, C.c_uint32]),
     "vegas_ising_stats": (C.c_int, [P, P]),
     "vegas_ising_last_error": (C.c_char_p, [P]),
     "vegas_ising_destroy": (None, [P]),
@@ -282,6 +284,10 @@ def vegas_get_spins(ctx, inst: int, n_sites: int) -> np.ndarray:
 def vegas_set_spins(ctx, inst: int, spins) -> None:
     s = _arr(spins, np.float64)
     _check(load_library().vegas_set_spins(ctx, inst, _ptr(s)), ctx)
+
+
+def vegas_set_mcs_counter(ctx, t: int) -> None:
+    _check(load_library().vegas_set_mcs_counter(ctx, int(t)), ctx)
 
 
 def vegas_accept_log(ctx) -> np.ndarray:
@@ -491,6 +497,27 @@ class Context:
     def set_spins(self, inst: int, spins) -> None:
         vegas_set_spins(self.ptr, inst, spins)
 
+    def set_mcs_counter(self, t: int) -> None:
+        """Global MCS counter of the next MCS (keys its random numbers)."""
+        vegas_set_mcs_counter(self.ptr, t)
+
+    def checkpoint(self) -> dict:
+        """Everything a new context over the same samples and options needs to continue the
+        chain bit for bit: every instance's spins, the MCS counter and the adaptive widths."""
+        return {"spins": [self.spins(i) for i in range(self.n_instances)], "mcs": self.stats()["mcs_done"],
+                "widths": self.adaptive_width()}
+
+    def restore(self, state: dict) -> None:
+        """Load a checkpoint() of a context over the same samples and options."""
+        if len(state["spins"]) != self.n_instances:
+            raise ValueError("checkpoint has a different number of instances")
+        for i, x in enumerate(state["spins"]):
+            self.set_spins(i, x)
+        w = np.asarray(state["widths"], dtype=np.float64)
+        if np.any(w > 0):
+            self.set_adaptive_width(np.where(w > 0, w, 1.0))
+        self.set_mcs_counter(state["mcs"])
+
     def accept_log(self) -> np.ndarray:
         return vegas_accept_log(self.ptr)
 
@@ -592,6 +619,10 @@ class IsingContext:
     def set_spins(self, replica: int, spins) -> None:
         s = np.ascontiguousarray(spins, dtype=np.int8)
         self._check(load_library().vegas_ising_set_spins(self.ptr, replica, _ptr(s)))
+
+    def set_mcs_counter(self, t: int) -> None:
+        """Global MCS counter of the next MCS (keys its random numbers)."""
+        self._check(load_library().vegas_ising_set_mcs_counter(self.ptr, int(t)))
 
     def stats(self) -> dict:
         s = vegas_stats_t()

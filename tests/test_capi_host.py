@@ -199,6 +199,8 @@ def test_null_safety(lib):
     assert isinstance(lib.vegas_last_error(None), bytes)
     assert lib.vegas_stats(None, None) == vb.EINVAL
     assert lib.vegas_run(None, None, None, 1, 1) == vb.EINVAL
+    assert lib.vegas_set_mcs_counter(None, 5) == vb.EINVAL
+    assert lib.vegas_ising_set_mcs_counter(None, 5) == vb.EINVAL
     out = C.c_void_p()
     assert lib.vegas_create(None, 0, None, C.byref(out)) == vb.EINVAL and not out.value
 
