@@ -264,10 +264,80 @@ def host_description() -> dict:
             "build": "gcc -O2 -ffp-contract=off (oracle)"}
 
 
+def workload_oracle_sample(w, budget: int = 10_000_000):
+    """Oracle (CPU FP64, as it stands, one thread) on a bounded sample of a secondary workload:
+    the first samples in order, each over the first temperature/field steps of its schedule
+    (or the first MCS of its first step, when one step is already larger) that keep its
+    attempts within `budget`, until `budget` attempts are done. Returns (attempts, seconds,
+    description)."""
+    import oracle
+
+    R = w.replicas
+    done, secs, parts = 0, 0.0, []
+    for p, smp in enumerate(w.samples):
+        per_step = smp.n_sites * R * w.mcs
+        if per_step <= budget:
+            steps, mcs = min(w.n_steps, budget // per_step), w.mcs
+        else:
+            steps, mcs = 1, max(1, budget // (smp.n_sites * R))
+        rows = slice(p * R, (p + 1) * R)
+        t0 = time.perf_counter()
+        oracle.run(smp, w.T[rows, :steps], w.B[rows, :steps], mcs, seed=w.seed, inst_base=p * R)
+        secs += time.perf_counter() - t0
+        done += smp.n_sites * R * steps * mcs
+        parts.append((steps, mcs))
+        if done >= budget:
+            break
+    st = sorted({f"{a} x {b}" for a, b in parts})
+    desc = (f"{len(parts)} of the {len(w.samples)} samples ({R} replica(s) each), steps x MCS from the start "
+            f"of the schedule: {', '.join(st[:3])}{' ...' if len(st) > 3 else ''}; one thread: {done} attempts "
+            f"in {secs:.2f} s")
+    return done, secs, desc
+
+
+def workload_config(w, args, policy, attempts_per_step):
+    return {"workload": args.workload, "instances": w.n_inst, "sites": w.n_sites_total,
+            "steps_x_mcs": [w.n_steps, w.mcs], "attempts_per_step": attempts_per_step,
+            "l2": "working set inside L2" if w.n_sites_total * 16 < 100e6 else "larger than L2",
+            "policy": policy or "random", "type_stats": bool(args.type_stats), "snapshots": bool(args.snapshots)}
+
+
+def run_reference_workload(args):
+    """The oracle on a secondary workload: one bounded sample (workload_oracle_sample) per step."""
+    from lattices import workload
+    import oracle
+
+    oracle.build()
+    w = workload(args.workload, mcs=args.mcs if args.mcs != MCS else None)
+    policy = apply_policy(w.samples, args.policy)
+    for _ in range(args.warmup):
+        workload_oracle_sample(w)
+    attempts, secs, desc = 0, 0.0, ""
+    for _ in range(args.steps):
+        a, t, desc = workload_oracle_sample(w)
+        attempts += a
+        secs += t
+    value = attempts / secs
+    rank, world, _ = dist_env()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps, "higher_is_better": True,
+        "scaling": "strong" if len(w.samples) > 1 else "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(w, args, policy, w.attempts()),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc + " per step",
+                         "host": host_description()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload != "sg256x32":
+        return run_reference_workload(args)
     from lattices import sc_periodic
     import oracle
 
@@ -497,15 +567,15 @@ def run_workload(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": share["scaling"], "vs_baseline": None, "dtype": "f64" if w.precision == 64 else "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "instances": w.n_inst, "sites": w.n_sites_total,
-                       "steps_x_mcs": [w.n_steps, w.mcs], "attempts_per_step": share["job_attempts"],
-                       "l2": "working set inside L2" if w.n_sites_total * 16 < 100e6 else "larger than L2",
-                       "policy": policy or "random", "type_stats": bool(args.type_stats),
-                       "snapshots": bool(args.snapshots)},
+            "config": workload_config(w, args, policy, share["job_attempts"]),
             **shape,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
+        if not args.quick:
+            att, secs, desc = workload_oracle_sample(w)
+            line["cpu_baseline"] = {"value": att / secs, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                                    "host": host_description()}
         if world > 1:
             line["config"]["sharding"] = {
                 "by": "contiguous sample blocks balanced by attempts" if share["scaling"] == "strong"

@@ -164,6 +164,10 @@ def test_traffic_is_read_only_while_the_summary_matches_the_source(tmp_path):
 
 @pytest.mark.parametrize("name", ["np256", "sc8_fp64"])
 def test_secondary_workload_line(fake_device, capsys, name):
+    secondary_line(capsys, name)
+
+
+def secondary_line(capsys, name):
     from lattices import workload
 
     bench.run_workload(args(workload=name, steps=2, warmup=1))
@@ -176,7 +180,21 @@ def test_secondary_workload_line(fake_device, capsys, name):
     assert line["scaling"] == ("strong" if name == "np256" else "weak")
     assert line["dtype"] == ("f64" if name == "sc8_fp64" else "f32")
     assert line["gpu_launches"] == 3 * 2 * w.n_steps * w.mcs
+    c = line["cpu_baseline"]
+    assert c["kind"] == "oracle" and c["cores"] == 1 and c["value"] > 0 and c["unit"] == bench.UNIT
     if name == "np256":
         plain = FakeContext.made[1:]
         assert [m.inst_base for m in plain] == list(range(len(w.samples)))
         assert line["batched_over_plain"] > 0
+    return line
+
+
+def test_reference_arm_on_a_secondary_workload(fake_device, capsys):
+    """`--impl reference --workload NAME`: the oracle on the same config as the GPU line."""
+    ours = secondary_line(capsys, "sc8_fp64")
+    bench.run_reference(args(impl="reference", workload="sc8_fp64", steps=2, warmup=0))
+    ref = last_json(capsys)
+    assert ref["impl"] == "reference" and ref["value"] > 0 and ref["dtype"] == "f64"
+    assert ref["metric"] == ours["metric"] and ref["unit"] == ours["unit"]
+    assert ref["config"] == ours["config"] and ref["scaling"] == ours["scaling"]
+    assert ref["e2e"]["h2d_bytes_per_step"] == 0 and ref["cpu_baseline"]["value"] == ref["value"]
