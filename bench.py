@@ -295,6 +295,17 @@ def workload_oracle_sample(w, budget: int = 10_000_000):
     return done, secs, desc
 
 
+def workload_bytes_per_attempt(w) -> float:
+    """Algorithmic bytes per attempt of a workload: the spin read and written (float4 FP32 or
+    double4 FP64) plus the site's links (int32 neighbour + J as f32 or f64) shared by the
+    replicas that sweep them together; per-site parameters are left out."""
+    vec = 32 if w.precision == 64 else 16
+    link = 4 + (8 if w.precision == 64 else 4)
+    sites = sum(s.n_sites for s in w.samples)
+    edges = sum(s.n_edges for s in w.samples)
+    return 2.0 * vec + link * edges / (sites * w.replicas)
+
+
 def workload_config(w, args, policy, attempts_per_step):
     return {"workload": args.workload, "instances": w.n_inst, "sites": w.n_sites_total,
             "steps_x_mcs": [w.n_steps, w.mcs], "attempts_per_step": attempts_per_step,
@@ -572,6 +583,14 @@ def run_workload(args):
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
+        bpa = workload_bytes_per_attempt(w)
+        peak, peak_kind = peaks()
+        line["effective_roofline"] = {
+            "bytes_per_attempt": bpa, "achieved": bpa * value / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": bpa * value / 1e9 / peak, "peak_source": f"{peak_kind} HBM copy bandwidth",
+            "note": "algorithmic bytes x attempts/s; the working set stays in L2, so this is an effective "
+                    "figure that can exceed 1" if w.n_sites_total * 16 < 100e6 else
+                    "algorithmic bytes x attempts/s against the HBM peak"}
         if not args.quick:
             att, secs, desc = workload_oracle_sample(w)
             line["cpu_baseline"] = {"value": att / secs, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,

@@ -182,11 +182,28 @@ def secondary_line(capsys, name):
     assert line["gpu_launches"] == 3 * 2 * w.n_steps * w.mcs
     c = line["cpu_baseline"]
     assert c["kind"] == "oracle" and c["cores"] == 1 and c["value"] > 0 and c["unit"] == bench.UNIT
+    r = line["effective_roofline"]
+    assert r["achieved"] == pytest.approx(r["bytes_per_attempt"] * line["value"] / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     if name == "np256":
         plain = FakeContext.made[1:]
         assert [m.inst_base for m in plain] == list(range(len(w.samples)))
         assert line["batched_over_plain"] > 0
     return line
+
+
+def test_workload_bytes_per_attempt_follow_the_size_table():
+    """Spin read + write plus the links shared by the replicas: 32 + 48 B for a periodic sc
+    lattice swept alone in FP32, 64 + 72 B in FP64, 32 + 48/32 B for 32 replicas."""
+    from lattices import workload
+
+    assert bench.workload_bytes_per_attempt(workload("sc64_hyst", scale=0.125)) == pytest.approx(80.0)
+    assert bench.workload_bytes_per_attempt(workload("sc8_fp64")) == pytest.approx(136.0)
+    assert bench.workload_bytes_per_attempt(workload("sg256x32", scale=1 / 32)) == pytest.approx(33.5)
+    assert bench.BYTES_PER_ATTEMPT == pytest.approx(33.5)
+    w = workload("np256", scale=0.05)
+    z = sum(s.n_edges for s in w.samples) / sum(s.n_sites for s in w.samples)
+    assert 8 < z < 12 and bench.workload_bytes_per_attempt(w) == pytest.approx(32 + 8 * z)
 
 
 def test_reference_arm_on_a_secondary_workload(fake_device, capsys):
