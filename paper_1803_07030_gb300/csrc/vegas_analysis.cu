@@ -27,6 +27,13 @@ vegas_status ana_fail(vegas_status st, const std::string &m) {
     return st;
 }
 
+// A host exception caught at an entry point, as a status (called inside a catch block).
+vegas_status analysis_host_exception() {
+    std::string m;
+    const vegas_status st = status_of_current_exception(m);
+    return ana_fail(st, m);
+}
+
 // Sum of v over the block, in a fixed order; every thread gets the result.
 __device__ double block_sum(double v, double *sm) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
@@ -292,101 +299,109 @@ extern "C" const char *vegas_analysis_last_error(void) { return g_ana_err.c_str(
 extern "C" vegas_status vegas_thermal_averages(const double *series, int64_t n_series, int64_t len, int64_t cut,
                                                int32_t n_bins, const double *T, const double *n_sites, double *out,
                                                void *cuda_stream) {
-    if (!series || !T || !n_sites || !out) return ana_fail(VEGAS_EINVAL, "a required pointer is NULL");
-    if (n_series < 1 || len < 1 || cut < 0 || cut >= len) return ana_fail(VEGAS_EINVAL, "need n_series >= 1 and 0 <= cut < len");
-    if (n_bins < 2 || n_bins > 64) return ana_fail(VEGAS_EINVAL, "n_bins must be in [2, 64]");
-    if ((len - cut) / n_bins < 1) return ana_fail(VEGAS_EINVAL, "fewer records after the cut than bins");
-    if (n_series > INT32_MAX) return ana_fail(VEGAS_EINVAL, "too many series");
-    for (int64_t s = 0; s < n_series; ++s)
-        if (!(T[s] > 0.0) || !std::isfinite(T[s]) || !(n_sites[s] > 0.0))
-            return ana_fail(VEGAS_EINVAL, "T and n_sites must be finite and > 0");
-    vegas_status st = have_device();
-    if (st != VEGAS_OK) return st;
-    cudaStream_t stream = (cudaStream_t)cuda_stream;
-    DevBuf b;
-    double *d_h, *d_T, *d_N, *d_out;
-    const size_t hb = sizeof(double) * 4 * (size_t)n_series * (size_t)len;
-    ACK(b.alloc(&d_h, hb));
-    ACK(b.alloc(&d_T, sizeof(double) * n_series));
-    ACK(b.alloc(&d_N, sizeof(double) * n_series));
-    ACK(b.alloc(&d_out, sizeof(double) * VEGAS_AVG_FIELDS * n_series));
-    ACK(cudaMemcpyAsync(d_h, series, hb, cudaMemcpyHostToDevice, stream));
-    ACK(cudaMemcpyAsync(d_T, T, sizeof(double) * n_series, cudaMemcpyHostToDevice, stream));
-    ACK(cudaMemcpyAsync(d_N, n_sites, sizeof(double) * n_series, cudaMemcpyHostToDevice, stream));
-    thermal_kernel<<<(unsigned)n_series, kAnaThreads, 0, stream>>>(d_h, len, cut, n_bins, d_T, d_N, d_out);
-    ACK(cudaGetLastError());
-    ACK(cudaMemcpyAsync(out, d_out, sizeof(double) * VEGAS_AVG_FIELDS * n_series, cudaMemcpyDeviceToHost, stream));
-    ACK(cudaStreamSynchronize(stream));
-    return VEGAS_OK;
+    try {
+        if (!series || !T || !n_sites || !out) return ana_fail(VEGAS_EINVAL, "a required pointer is NULL");
+        if (n_series < 1 || len < 1 || cut < 0 || cut >= len) return ana_fail(VEGAS_EINVAL, "need n_series >= 1 and 0 <= cut < len");
+        if (n_bins < 2 || n_bins > 64) return ana_fail(VEGAS_EINVAL, "n_bins must be in [2, 64]");
+        if ((len - cut) / n_bins < 1) return ana_fail(VEGAS_EINVAL, "fewer records after the cut than bins");
+        if (n_series > INT32_MAX) return ana_fail(VEGAS_EINVAL, "too many series");
+        for (int64_t s = 0; s < n_series; ++s)
+            if (!(T[s] > 0.0) || !std::isfinite(T[s]) || !(n_sites[s] > 0.0))
+                return ana_fail(VEGAS_EINVAL, "T and n_sites must be finite and > 0");
+        vegas_status st = have_device();
+        if (st != VEGAS_OK) return st;
+        cudaStream_t stream = (cudaStream_t)cuda_stream;
+        DevBuf b;
+        double *d_h, *d_T, *d_N, *d_out;
+        const size_t hb = sizeof(double) * 4 * (size_t)n_series * (size_t)len;
+        ACK(b.alloc(&d_h, hb));
+        ACK(b.alloc(&d_T, sizeof(double) * n_series));
+        ACK(b.alloc(&d_N, sizeof(double) * n_series));
+        ACK(b.alloc(&d_out, sizeof(double) * VEGAS_AVG_FIELDS * n_series));
+        ACK(cudaMemcpyAsync(d_h, series, hb, cudaMemcpyHostToDevice, stream));
+        ACK(cudaMemcpyAsync(d_T, T, sizeof(double) * n_series, cudaMemcpyHostToDevice, stream));
+        ACK(cudaMemcpyAsync(d_N, n_sites, sizeof(double) * n_series, cudaMemcpyHostToDevice, stream));
+        thermal_kernel<<<(unsigned)n_series, kAnaThreads, 0, stream>>>(d_h, len, cut, n_bins, d_T, d_N, d_out);
+        ACK(cudaGetLastError());
+        ACK(cudaMemcpyAsync(out, d_out, sizeof(double) * VEGAS_AVG_FIELDS * n_series, cudaMemcpyDeviceToHost, stream));
+        ACK(cudaStreamSynchronize(stream));
+        return VEGAS_OK;
+    } catch (...) {
+        return analysis_host_exception();
+    }
 }
 
 extern "C" vegas_status vegas_reweight(const double *E, const double *O, int32_t K, int64_t n, int32_t n_obs,
                                        const double *betas_k, const double *betas_out, int32_t n_out,
                                        int32_t max_iter, double tol, double *out, double *g_out, int32_t *iters_out,
                                        void *cuda_stream) {
-    if (!E || !betas_k || (n_out > 0 && (!betas_out || !out)) || (n_obs > 0 && !O))
-        return ana_fail(VEGAS_EINVAL, "a required pointer is NULL");
-    if (K < 1 || n < 1 || n_obs < 0 || n_obs > kMaxObs || n_out < 0 || max_iter < 1 || !(tol > 0.0))
-        return ana_fail(VEGAS_EINVAL, "need K >= 1, n >= 1, 0 <= n_obs <= 8, n_out >= 0, max_iter >= 1, tol > 0");
-    const int64_t n_tot = (int64_t)K * n;
-    for (int32_t k = 0; k < K; ++k)
-        if (!std::isfinite(betas_k[k])) return ana_fail(VEGAS_EINVAL, "non-finite beta");
-    for (int64_t i = 0; i < n_tot; ++i)
-        if (!std::isfinite(E[i])) return ana_fail(VEGAS_EINVAL, "non-finite energy");
-    vegas_status st = have_device();
-    if (st != VEGAS_OK) return st;
-    cudaStream_t stream = (cudaStream_t)cuda_stream;
-    DevBuf b;
-    double *d_E, *d_O, *d_D, *d_bk, *d_bo, *d_g, *d_lse, *d_part, *d_obs;
-    const int parts = (int)std::min<int64_t>(256, (n_tot + kAnaThreads - 1) / kAnaThreads);
-    const int rows = std::max<int32_t>(K, n_out);
-    ACK(b.alloc(&d_E, sizeof(double) * n_tot));
-    ACK(b.alloc(&d_O, sizeof(double) * n_tot * std::max(n_obs, 1)));
-    ACK(b.alloc(&d_D, sizeof(double) * n_tot));
-    ACK(b.alloc(&d_bk, sizeof(double) * K));
-    ACK(b.alloc(&d_bo, sizeof(double) * std::max(n_out, 1)));
-    ACK(b.alloc(&d_g, sizeof(double) * K));
-    ACK(b.alloc(&d_lse, sizeof(double) * rows));
-    ACK(b.alloc(&d_part, sizeof(double) * (2 + kMaxObs) * (size_t)parts * rows));
-    ACK(b.alloc(&d_obs, sizeof(double) * (size_t)std::max(n_out, 1) * std::max(n_obs, 1)));
-    ACK(cudaMemcpyAsync(d_E, E, sizeof(double) * n_tot, cudaMemcpyHostToDevice, stream));
-    if (n_obs > 0) ACK(cudaMemcpyAsync(d_O, O, sizeof(double) * n_tot * n_obs, cudaMemcpyHostToDevice, stream));
-    ACK(cudaMemcpyAsync(d_bk, betas_k, sizeof(double) * K, cudaMemcpyHostToDevice, stream));
-    if (n_out > 0) ACK(cudaMemcpyAsync(d_bo, betas_out, sizeof(double) * n_out, cudaMemcpyHostToDevice, stream));
-    std::vector<double> g((size_t)K, 0.0), gn((size_t)K);
-    ACK(cudaMemcpyAsync(d_g, g.data(), sizeof(double) * K, cudaMemcpyHostToDevice, stream));
-    const double logn = std::log((double)n);
-    const int dgrid = (int)std::min<int64_t>((n_tot + 255) / 256, 4096);
-    int32_t it = 0;
-    for (it = 1; it <= max_iter; ++it) {
-        denom_kernel<<<dgrid, 256, 0, stream>>>(d_E, n_tot, d_bk, d_g, K, logn, d_D);
-        lse_kernel<<<dim3(parts, K), kAnaThreads, 0, stream>>>(d_E, d_D, d_O, 0, n_tot, d_bk, d_part);
-        combine_kernel<<<(K + 127) / 128, 128, 0, stream>>>(d_part, parts, K, 0, d_lse, nullptr);
-        ACK(cudaGetLastError());
-        ACK(cudaMemcpyAsync(gn.data(), d_lse, sizeof(double) * K, cudaMemcpyDeviceToHost, stream));
-        ACK(cudaStreamSynchronize(stream));
-        double diff = 0.0;
-        const double g0 = gn[0];
-        for (int32_t k = 0; k < K; ++k) {
-            gn[(size_t)k] -= g0;  // gauge: g_0 = 0
-            diff = std::max(diff, std::fabs(gn[(size_t)k] - g[(size_t)k]));
-        }
-        g = gn;
+    try {
+        if (!E || !betas_k || (n_out > 0 && (!betas_out || !out)) || (n_obs > 0 && !O))
+            return ana_fail(VEGAS_EINVAL, "a required pointer is NULL");
+        if (K < 1 || n < 1 || n_obs < 0 || n_obs > kMaxObs || n_out < 0 || max_iter < 1 || !(tol > 0.0))
+            return ana_fail(VEGAS_EINVAL, "need K >= 1, n >= 1, 0 <= n_obs <= 8, n_out >= 0, max_iter >= 1, tol > 0");
+        const int64_t n_tot = (int64_t)K * n;
+        for (int32_t k = 0; k < K; ++k)
+            if (!std::isfinite(betas_k[k])) return ana_fail(VEGAS_EINVAL, "non-finite beta");
+        for (int64_t i = 0; i < n_tot; ++i)
+            if (!std::isfinite(E[i])) return ana_fail(VEGAS_EINVAL, "non-finite energy");
+        vegas_status st = have_device();
+        if (st != VEGAS_OK) return st;
+        cudaStream_t stream = (cudaStream_t)cuda_stream;
+        DevBuf b;
+        double *d_E, *d_O, *d_D, *d_bk, *d_bo, *d_g, *d_lse, *d_part, *d_obs;
+        const int parts = (int)std::min<int64_t>(256, (n_tot + kAnaThreads - 1) / kAnaThreads);
+        const int rows = std::max<int32_t>(K, n_out);
+        ACK(b.alloc(&d_E, sizeof(double) * n_tot));
+        ACK(b.alloc(&d_O, sizeof(double) * n_tot * std::max(n_obs, 1)));
+        ACK(b.alloc(&d_D, sizeof(double) * n_tot));
+        ACK(b.alloc(&d_bk, sizeof(double) * K));
+        ACK(b.alloc(&d_bo, sizeof(double) * std::max(n_out, 1)));
+        ACK(b.alloc(&d_g, sizeof(double) * K));
+        ACK(b.alloc(&d_lse, sizeof(double) * rows));
+        ACK(b.alloc(&d_part, sizeof(double) * (2 + kMaxObs) * (size_t)parts * rows));
+        ACK(b.alloc(&d_obs, sizeof(double) * (size_t)std::max(n_out, 1) * std::max(n_obs, 1)));
+        ACK(cudaMemcpyAsync(d_E, E, sizeof(double) * n_tot, cudaMemcpyHostToDevice, stream));
+        if (n_obs > 0) ACK(cudaMemcpyAsync(d_O, O, sizeof(double) * n_tot * n_obs, cudaMemcpyHostToDevice, stream));
+        ACK(cudaMemcpyAsync(d_bk, betas_k, sizeof(double) * K, cudaMemcpyHostToDevice, stream));
+        if (n_out > 0) ACK(cudaMemcpyAsync(d_bo, betas_out, sizeof(double) * n_out, cudaMemcpyHostToDevice, stream));
+        std::vector<double> g((size_t)K, 0.0), gn((size_t)K);
         ACK(cudaMemcpyAsync(d_g, g.data(), sizeof(double) * K, cudaMemcpyHostToDevice, stream));
-        if (!std::isfinite(diff)) return ana_fail(VEGAS_EDEVICE, "reweighting iteration produced a non-finite value");
-        if (diff < tol) break;
+        const double logn = std::log((double)n);
+        const int dgrid = (int)std::min<int64_t>((n_tot + 255) / 256, 4096);
+        int32_t it = 0;
+        for (it = 1; it <= max_iter; ++it) {
+            denom_kernel<<<dgrid, 256, 0, stream>>>(d_E, n_tot, d_bk, d_g, K, logn, d_D);
+            lse_kernel<<<dim3(parts, K), kAnaThreads, 0, stream>>>(d_E, d_D, d_O, 0, n_tot, d_bk, d_part);
+            combine_kernel<<<(K + 127) / 128, 128, 0, stream>>>(d_part, parts, K, 0, d_lse, nullptr);
+            ACK(cudaGetLastError());
+            ACK(cudaMemcpyAsync(gn.data(), d_lse, sizeof(double) * K, cudaMemcpyDeviceToHost, stream));
+            ACK(cudaStreamSynchronize(stream));
+            double diff = 0.0;
+            const double g0 = gn[0];
+            for (int32_t k = 0; k < K; ++k) {
+                gn[(size_t)k] -= g0;  // gauge: g_0 = 0
+                diff = std::max(diff, std::fabs(gn[(size_t)k] - g[(size_t)k]));
+            }
+            g = gn;
+            ACK(cudaMemcpyAsync(d_g, g.data(), sizeof(double) * K, cudaMemcpyHostToDevice, stream));
+            if (!std::isfinite(diff)) return ana_fail(VEGAS_EDEVICE, "reweighting iteration produced a non-finite value");
+            if (diff < tol) break;
+        }
+        if (it > max_iter) it = max_iter;
+        if (g_out) std::memcpy(g_out, g.data(), sizeof(double) * K);
+        if (iters_out) *iters_out = it;
+        if (n_out > 0) {
+            denom_kernel<<<dgrid, 256, 0, stream>>>(d_E, n_tot, d_bk, d_g, K, logn, d_D);
+            lse_kernel<<<dim3(parts, n_out), kAnaThreads, 0, stream>>>(d_E, d_D, d_O, n_obs, n_tot, d_bo, d_part);
+            combine_kernel<<<(n_out + 127) / 128, 128, 0, stream>>>(d_part, parts, n_out, n_obs, d_lse, d_obs);
+            ACK(cudaGetLastError());
+            if (n_obs > 0)
+                ACK(cudaMemcpyAsync(out, d_obs, sizeof(double) * n_out * n_obs, cudaMemcpyDeviceToHost, stream));
+            ACK(cudaStreamSynchronize(stream));
+        }
+        return VEGAS_OK;
+    } catch (...) {
+        return analysis_host_exception();
     }
-    if (it > max_iter) it = max_iter;
-    if (g_out) std::memcpy(g_out, g.data(), sizeof(double) * K);
-    if (iters_out) *iters_out = it;
-    if (n_out > 0) {
-        denom_kernel<<<dgrid, 256, 0, stream>>>(d_E, n_tot, d_bk, d_g, K, logn, d_D);
-        lse_kernel<<<dim3(parts, n_out), kAnaThreads, 0, stream>>>(d_E, d_D, d_O, n_obs, n_tot, d_bo, d_part);
-        combine_kernel<<<(n_out + 127) / 128, 128, 0, stream>>>(d_part, parts, n_out, n_obs, d_lse, d_obs);
-        ACK(cudaGetLastError());
-        if (n_obs > 0)
-            ACK(cudaMemcpyAsync(out, d_obs, sizeof(double) * n_out * n_obs, cudaMemcpyDeviceToHost, stream));
-        ACK(cudaStreamSynchronize(stream));
-    }
-    return VEGAS_OK;
 }

@@ -146,6 +146,13 @@ vegas_status fail(vegas_ctx *c, vegas_status st, const std::string &msg) {
     return st;
 }
 
+// A host exception caught at an entry point, as a status (called inside a catch block).
+vegas_status host_exception(vegas_ctx *c) {
+    std::string m;
+    const vegas_status st = status_of_current_exception(m);
+    return fail(c, st, m);
+}
+
 #define CK(ctx, call)                                                                                     \
     do {                                                                                                  \
         cudaError_t e_ = (call);                                                                          \
@@ -447,8 +454,9 @@ extern "C" void vegas_default_options(vegas_options *o) {
     o->wave_lag = 0;
 }
 
-extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samples, const vegas_options *opt,
-                                     vegas_ctx **out) {
+// vegas_create without the exception guard; *made is the context under construction.
+static vegas_status create_context(const vegas_sample *samples, int32_t n_samples, const vegas_options *opt,
+                                   vegas_ctx **out, vegas_ctx **made) {
     if (!out) return fail(nullptr, VEGAS_EINVAL, "out is NULL");
     *out = nullptr;
     if (!samples || n_samples < 1) return fail(nullptr, VEGAS_EINVAL, "need at least one sample");
@@ -514,6 +522,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
 
     vegas_ctx *c = new (std::nothrow) vegas_ctx();
     if (!c) return fail(nullptr, VEGAS_ENOMEM, "host allocation failed");
+    *made = c;
     c->opt = o;
     c->precision = o.precision;
     c->R = o.replicas;
@@ -530,6 +539,7 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
         g_create_error = c->err;
         free_all(c);
         delete c;
+        *made = nullptr;
         return st;
     };
     int ndev = 0;
@@ -1146,500 +1156,548 @@ extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samp
     return VEGAS_OK;
 }
 
-extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B, int32_t n_steps, int32_t mcs) {
-    vegas_status st = check_usable(c);
-    if (st != VEGAS_OK) return st;
-    if (n_steps < 0 || mcs < 0) return fail(c, VEGAS_EINVAL, "n_steps and mcs_per_step must be >= 0");
-    if (n_steps == 0 || mcs == 0) return VEGAS_OK;
-    if (!T || !B) return fail(c, VEGAS_EINVAL, "T or B is NULL");
-    const int64_t NI = c->n_inst;
-    if ((int64_t)c->t + (int64_t)n_steps * mcs >= (int64_t)UINT32_MAX)
-        return fail(c, VEGAS_EINVAL, "global MCS counter would exceed 32 bits");
-    std::vector<double> sched((size_t)n_steps * NI * 2);
-    for (int64_t i = 0; i < NI; ++i)
-        for (int32_t s = 0; s < n_steps; ++s) {
-            const double Ti = T[i * n_steps + s], Bi = B[i * n_steps + s];
-            if (!(Ti > 0.0) || !std::isfinite(Ti)) return fail(c, VEGAS_EINVAL, "T must be finite and > 0");
-            if (!std::isfinite(Bi)) return fail(c, VEGAS_EINVAL, "B must be finite");
-            sched[((size_t)s * NI + i) * 2] = 1.0 / Ti;
-            sched[((size_t)s * NI + i) * 2 + 1] = Bi;
+extern "C" vegas_status vegas_create(const vegas_sample *samples, int32_t n_samples, const vegas_options *opt,
+                                     vegas_ctx **out) {
+    vegas_ctx *made = nullptr;
+    try {
+        return create_context(samples, n_samples, opt, out, &made);
+    } catch (...) {
+        const vegas_status st = host_exception(nullptr);
+        if (made) {
+            free_all(made);
+            delete made;
         }
-    if ((st = set_device(c)) != VEGAS_OK) return st;
-    const int64_t nrec = (int64_t)n_steps * mcs;
-    if (sched.size() > c->sched_cap) {
-        if (c->d_sched) {
-            cudaFree(c->d_sched);
-            c->device_bytes -= (int64_t)(c->sched_cap * sizeof(double));
-        }
-        c->sched_cap = 0;
-        CK(c, dalloc(c, &c->d_sched, sizeof(double) * sched.size()));
-        c->sched_cap = sched.size();
+        if (out) *out = nullptr;
+        return st;
     }
-    const size_t hneed = (size_t)nrec * NI * 4;
-    if (hneed > c->hist_cap) {
-        if (c->d_hist) {
-            cudaFree(c->d_hist);
-            c->device_bytes -= (int64_t)(c->hist_cap * sizeof(double));
-        }
-        c->hist_cap = 0;
-        CK(c, dalloc(c, &c->d_hist, sizeof(double) * hneed));
-        c->hist_cap = hneed;
-    }
-    const size_t aneed = (size_t)nrec * NI;
-    if (aneed > c->acc_hist_cap) {
-        if (c->d_acc_hist) {
-            cudaFree(c->d_acc_hist);
-            c->device_bytes -= (int64_t)(c->acc_hist_cap * sizeof(uint32_t));
-        }
-        c->acc_hist_cap = 0;
-        CK(c, dalloc(c, &c->d_acc_hist, sizeof(uint32_t) * aneed));
-        c->acc_hist_cap = aneed;
-    }
-    const size_t tneed = (size_t)nrec * NI * (size_t)c->n_types * 3;
-    if (tneed > c->type_hist_cap) {
-        if (c->d_type_hist) {
-            cudaFree(c->d_type_hist);
-            c->device_bytes -= (int64_t)(c->type_hist_cap * sizeof(double));
-        }
-        c->type_hist_cap = 0;
-        CK(c, dalloc(c, &c->d_type_hist, sizeof(double) * tneed));
-        c->type_hist_cap = tneed;
-    }
-    const int64_t vbytes = c->precision == 64 ? 32 : 16;
-    const size_t sneed = c->opt.snapshots ? (size_t)n_steps * (size_t)(c->n_sites * c->R * vbytes) : 0;
-    if (sneed > c->snap_cap) {
-        if (c->d_snap) {
-            cudaFree(c->d_snap);
-            c->device_bytes -= (int64_t)c->snap_cap;
-        }
-        c->snap_cap = 0;
-        CK(c, dalloc(c, &c->d_snap, sneed));
-        c->snap_cap = sneed;
-    }
-    CK(c, cudaMemcpyAsync(c->d_sched, sched.data(), sizeof(double) * sched.size(), cudaMemcpyHostToDevice, c->stream));
-    RunState rs{};
-    rs.t = c->t;
-    rs.rec = 0;
-    rs.ticket = 0;
-    rs.mcs = (uint32_t)mcs;
-    rs.sched = c->d_sched;
-    rs.hist = c->d_hist;
-    rs.acc = c->d_acc;
-    rs.acc_hist = c->d_acc_hist;
-    rs.sigma = c->d_sigma;
-    rs.type_hist = c->n_types > 0 ? c->d_type_hist : nullptr;
-    rs.rec_end = (uint32_t)nrec;
-    CK(c, cudaMemcpyAsync(c->d_run, &rs, sizeof rs, cudaMemcpyHostToDevice, c->stream));
+}
 
-    const bool use_graph = c->opt.graphs != 0 && !c->opt.timing;
-    if (use_graph && (st = build_graph(c)) != VEGAS_OK) return st;
-    std::vector<cudaEvent_t> ev;
-    if (c->opt.timing) {
-        ev.resize(2 * c->passes.size() * (size_t)mcs + 2);
-        for (auto &x : ev) CK(c, cudaEventCreate(&x));
-    }
-    cudaEvent_t e0, e1;
-    CK(c, cudaEventCreate(&e0));
-    CK(c, cudaEventCreate(&e1));
-    CK(c, cudaEventRecord(e0, c->stream));
-    double sweep_ms = 0.0;
-    // the kernels read the MCS counter, record index and schedule from the run state, which
-    // the reductions (per-class sweep) and the advance kernel (resident sweep) move forward
-    auto stream_mcs = [&](int32_t m0, int32_t n) -> vegas_status {
-        for (int32_t m = m0; m < m0 + n; ++m) {
-            if (use_graph) {
-                CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
-                c->graph_launches++;
-            } else if (c->opt.timing) {
-                std::vector<cudaEvent_t> sub(ev.begin() + (size_t)m * 2 * c->passes.size(),
-                                             ev.begin() + (size_t)(m + 1) * 2 * c->passes.size());
-                enqueue_mcs(c, c->stream, &sub);
-            } else {
-                enqueue_mcs(c, c->stream, nullptr);
+extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B, int32_t n_steps, int32_t mcs) {
+    try {
+        vegas_status st = check_usable(c);
+        if (st != VEGAS_OK) return st;
+        if (n_steps < 0 || mcs < 0) return fail(c, VEGAS_EINVAL, "n_steps and mcs_per_step must be >= 0");
+        if (n_steps == 0 || mcs == 0) return VEGAS_OK;
+        if (!T || !B) return fail(c, VEGAS_EINVAL, "T or B is NULL");
+        const int64_t NI = c->n_inst;
+        if ((int64_t)c->t + (int64_t)n_steps * mcs >= (int64_t)UINT32_MAX)
+            return fail(c, VEGAS_EINVAL, "global MCS counter would exceed 32 bits");
+        std::vector<double> sched((size_t)n_steps * NI * 2);
+        for (int64_t i = 0; i < NI; ++i)
+            for (int32_t s = 0; s < n_steps; ++s) {
+                const double Ti = T[i * n_steps + s], Bi = B[i * n_steps + s];
+                if (!(Ti > 0.0) || !std::isfinite(Ti)) return fail(c, VEGAS_EINVAL, "T must be finite and > 0");
+                if (!std::isfinite(Bi)) return fail(c, VEGAS_EINVAL, "B must be finite");
+                sched[((size_t)s * NI + i) * 2] = 1.0 / Ti;
+                sched[((size_t)s * NI + i) * 2 + 1] = Bi;
             }
-            c->kernel_launches += (int64_t)c->passes.size() + 1;
-            c->sweep_launches += (int64_t)c->passes.size();
+        if ((st = set_device(c)) != VEGAS_OK) return st;
+        const int64_t nrec = (int64_t)n_steps * mcs;
+        if (sched.size() > c->sched_cap) {
+            if (c->d_sched) {
+                cudaFree(c->d_sched);
+                c->device_bytes -= (int64_t)(c->sched_cap * sizeof(double));
+            }
+            c->sched_cap = 0;
+            CK(c, dalloc(c, &c->d_sched, sizeof(double) * sched.size()));
+            c->sched_cap = sched.size();
         }
-        return VEGAS_OK;
-    };
-    auto resident = [&](int32_t n) -> vegas_status {
-        if (n <= 0) return VEGAS_OK;
-        if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 2], c->stream));
-        enqueue_resident(c, c->stream, n);
-        if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 1], c->stream));
-        CK(c, cudaGetLastError());
-        c->kernel_launches += 2;
-        c->sweep_launches++;
-        return VEGAS_OK;
-    };
-    auto coop = [&](int32_t n) -> vegas_status {
-        if (n <= 0) return VEGAS_OK;
-        if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 2], c->stream));
-        enqueue_coop(c, c->stream, n);
-        if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 1], c->stream));
-        CK(c, cudaGetLastError());
-        c->kernel_launches += 2;
-        c->sweep_launches++;
-        return VEGAS_OK;
-    };
-    auto cluster = [&](int32_t n) -> vegas_status {
-        if (n <= 0) return VEGAS_OK;
-        if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 2], c->stream));
-        enqueue_cluster(c, c->stream, n);
-        if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 1], c->stream));
-        CK(c, cudaGetLastError());
-        c->kernel_launches += 2;
-        c->sweep_launches++;
-        return VEGAS_OK;
-    };
-    auto wave = [&](int32_t m0, int32_t n) -> vegas_status {
-        for (int32_t m = m0; m < m0 + n; ++m) {
-            if (c->opt.timing) CK(c, cudaEventRecord(ev[2 * (size_t)m], c->stream));
-            const int e = enqueue_wave(c, c->stream);
-            if (e != 0)
-                return fail(c, VEGAS_ECUDA, std::string("wavefront sweep launch: ") + cudaGetErrorString((cudaError_t)e));
-            if (c->opt.timing) CK(c, cudaEventRecord(ev[2 * (size_t)m + 1], c->stream));
+        const size_t hneed = (size_t)nrec * NI * 4;
+        if (hneed > c->hist_cap) {
+            if (c->d_hist) {
+                cudaFree(c->d_hist);
+                c->device_bytes -= (int64_t)(c->hist_cap * sizeof(double));
+            }
+            c->hist_cap = 0;
+            CK(c, dalloc(c, &c->d_hist, sizeof(double) * hneed));
+            c->hist_cap = hneed;
+        }
+        const size_t aneed = (size_t)nrec * NI;
+        if (aneed > c->acc_hist_cap) {
+            if (c->d_acc_hist) {
+                cudaFree(c->d_acc_hist);
+                c->device_bytes -= (int64_t)(c->acc_hist_cap * sizeof(uint32_t));
+            }
+            c->acc_hist_cap = 0;
+            CK(c, dalloc(c, &c->d_acc_hist, sizeof(uint32_t) * aneed));
+            c->acc_hist_cap = aneed;
+        }
+        const size_t tneed = (size_t)nrec * NI * (size_t)c->n_types * 3;
+        if (tneed > c->type_hist_cap) {
+            if (c->d_type_hist) {
+                cudaFree(c->d_type_hist);
+                c->device_bytes -= (int64_t)(c->type_hist_cap * sizeof(double));
+            }
+            c->type_hist_cap = 0;
+            CK(c, dalloc(c, &c->d_type_hist, sizeof(double) * tneed));
+            c->type_hist_cap = tneed;
+        }
+        const int64_t vbytes = c->precision == 64 ? 32 : 16;
+        const size_t sneed = c->opt.snapshots ? (size_t)n_steps * (size_t)(c->n_sites * c->R * vbytes) : 0;
+        if (sneed > c->snap_cap) {
+            if (c->d_snap) {
+                cudaFree(c->d_snap);
+                c->device_bytes -= (int64_t)c->snap_cap;
+            }
+            c->snap_cap = 0;
+            CK(c, dalloc(c, &c->d_snap, sneed));
+            c->snap_cap = sneed;
+        }
+        CK(c, cudaMemcpyAsync(c->d_sched, sched.data(), sizeof(double) * sched.size(), cudaMemcpyHostToDevice, c->stream));
+        RunState rs{};
+        rs.t = c->t;
+        rs.rec = 0;
+        rs.ticket = 0;
+        rs.mcs = (uint32_t)mcs;
+        rs.sched = c->d_sched;
+        rs.hist = c->d_hist;
+        rs.acc = c->d_acc;
+        rs.acc_hist = c->d_acc_hist;
+        rs.sigma = c->d_sigma;
+        rs.type_hist = c->n_types > 0 ? c->d_type_hist : nullptr;
+        rs.rec_end = (uint32_t)nrec;
+        CK(c, cudaMemcpyAsync(c->d_run, &rs, sizeof rs, cudaMemcpyHostToDevice, c->stream));
+
+        const bool use_graph = c->opt.graphs != 0 && !c->opt.timing;
+        if (use_graph && (st = build_graph(c)) != VEGAS_OK) return st;
+        std::vector<cudaEvent_t> ev;
+        if (c->opt.timing) {
+            ev.resize(2 * c->passes.size() * (size_t)mcs + 2);
+            for (auto &x : ev) CK(c, cudaEventCreate(&x));
+        }
+        cudaEvent_t e0, e1;
+        CK(c, cudaEventCreate(&e0));
+        CK(c, cudaEventCreate(&e1));
+        CK(c, cudaEventRecord(e0, c->stream));
+        double sweep_ms = 0.0;
+        // the kernels read the MCS counter, record index and schedule from the run state, which
+        // the reductions (per-class sweep) and the advance kernel (resident sweep) move forward
+        auto stream_mcs = [&](int32_t m0, int32_t n) -> vegas_status {
+            for (int32_t m = m0; m < m0 + n; ++m) {
+                if (use_graph) {
+                    CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
+                    c->graph_launches++;
+                } else if (c->opt.timing) {
+                    std::vector<cudaEvent_t> sub(ev.begin() + (size_t)m * 2 * c->passes.size(),
+                                                 ev.begin() + (size_t)(m + 1) * 2 * c->passes.size());
+                    enqueue_mcs(c, c->stream, &sub);
+                } else {
+                    enqueue_mcs(c, c->stream, nullptr);
+                }
+                c->kernel_launches += (int64_t)c->passes.size() + 1;
+                c->sweep_launches += (int64_t)c->passes.size();
+            }
+            return VEGAS_OK;
+        };
+        auto resident = [&](int32_t n) -> vegas_status {
+            if (n <= 0) return VEGAS_OK;
+            if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 2], c->stream));
+            enqueue_resident(c, c->stream, n);
+            if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 1], c->stream));
             CK(c, cudaGetLastError());
             c->kernel_launches += 2;
             c->sweep_launches++;
-        }
-        return VEGAS_OK;
-    };
-    auto run_variant = [&](int v, int32_t m0, int32_t n) -> vegas_status {
-        if (v == 4) return wave(m0, n);
-        if (v == 1) return resident(n);
-        if (v == 2) return coop(n);
-        if (v == 3) return cluster(n);
-        return stream_mcs(m0, n);
-    };
-    for (int32_t s = 0; s < n_steps; ++s) {
-        int32_t m0 = 0;
-        if (!c->tuned && mcs >= 2) {
-            // autotune: time a few MCS of each eligible sweep and block shape on the real chain
-            // (all give the same spins) and keep the fastest for this context. Shapes: threads
-            // per block of the resident sweep (so sites per thread), blocks per cluster of the
-            // cluster sweep.
-            struct Cand {
-                int v, a, b, split, group;  // sweep; threads (resident) or blocks per cluster,
-                                            // threads; cluster split; threads per small instance
-            };
-            std::vector<Cand> cand{{0, 0, 0, 0, 0}};
-            // instances of very different sizes (split and grouping candidates)
-            const bool uneven = c->res_items > 1 && 4 * (int64_t)c->min_instance_sites < c->max_instance_sites;
-            if (c->res_eligible) {
-                cand.push_back({1, 256, 0, 0, 0});
-                cand.push_back({1, 512, 0, 0, 0});
-                if (uneven) {  // small instances several to a block
-                    cand.push_back({1, 512, 0, 0, 128});
-                    cand.push_back({1, 512, 0, 0, 256});
-                }
+            return VEGAS_OK;
+        };
+        auto coop = [&](int32_t n) -> vegas_status {
+            if (n <= 0) return VEGAS_OK;
+            if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 2], c->stream));
+            enqueue_coop(c, c->stream, n);
+            if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 1], c->stream));
+            CK(c, cudaGetLastError());
+            c->kernel_launches += 2;
+            c->sweep_launches++;
+            return VEGAS_OK;
+        };
+        auto cluster = [&](int32_t n) -> vegas_status {
+            if (n <= 0) return VEGAS_OK;
+            if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 2], c->stream));
+            enqueue_cluster(c, c->stream, n);
+            if (c->opt.timing) CK(c, cudaEventRecord(ev[ev.size() - 1], c->stream));
+            CK(c, cudaGetLastError());
+            c->kernel_launches += 2;
+            c->sweep_launches++;
+            return VEGAS_OK;
+        };
+        auto wave = [&](int32_t m0, int32_t n) -> vegas_status {
+            for (int32_t m = m0; m < m0 + n; ++m) {
+                if (c->opt.timing) CK(c, cudaEventRecord(ev[2 * (size_t)m], c->stream));
+                const int e = enqueue_wave(c, c->stream);
+                if (e != 0)
+                    return fail(c, VEGAS_ECUDA, std::string("wavefront sweep launch: ") + cudaGetErrorString((cudaError_t)e));
+                if (c->opt.timing) CK(c, cudaEventRecord(ev[2 * (size_t)m + 1], c->stream));
+                CK(c, cudaGetLastError());
+                c->kernel_launches += 2;
+                c->sweep_launches++;
             }
-            if (c->coop_eligible) cand.push_back({2, 0, 0, 0, 0});
-            if (c->cluster_eligible) {
-                const int cs0 = c->cluster_cs, big = c->max_instance_sites;
-                cand.push_back({3, cs0, 256, 0, 0});
-                if (cs0 / 2 >= 2) cand.push_back({3, cs0 / 2, 256, 0, 0});
-                // batches of uneven instances: clusters for the largest, blocks (and groups of a
-                // block) for the rest
-                if (uneven)
-                    for (int sp : {big / 2, big / 4})
-                        if (sp > 0) {
-                            cand.push_back({3, 2, 512, sp, 128});
-                            cand.push_back({3, 4, 256, sp, 0});
-                        }
-            }
-            // longer probes when the step allows (less noise between close candidates), at most
-            // a quarter of the step
-            const int32_t probe = std::max(1, std::min(16, mcs / (4 * (int32_t)cand.size())));
-            if (probe * (int32_t)cand.size() <= mcs) {
-                float best = 0.f;
-                int best_v = c->variant;
-                Cand best_c = cand[0];
-                const int cs_rule = c->cluster_cs, ct_rule = c->cluster_threads, rt_rule = c->res_threads;
-                for (const Cand &vc : cand) {
-                    const int v = vc.v;
-                    // grouped instances: group_threads threads for up to 16 sites each per thread
-                    if (v == 1) set_resident_shape(c, vc.a, vc.group, vc.group * 16);
-                    if (v == 3) {
-                        if (!set_cluster_shape(c, vc.a, vc.b, vc.split)) continue;
-                        c->res.group_threads = vc.group < vc.b ? vc.group : 0;
-                        c->res.group_sites = c->res.group_threads * 16;
+            return VEGAS_OK;
+        };
+        auto run_variant = [&](int v, int32_t m0, int32_t n) -> vegas_status {
+            if (v == 4) return wave(m0, n);
+            if (v == 1) return resident(n);
+            if (v == 2) return coop(n);
+            if (v == 3) return cluster(n);
+            return stream_mcs(m0, n);
+        };
+        for (int32_t s = 0; s < n_steps; ++s) {
+            int32_t m0 = 0;
+            if (!c->tuned && mcs >= 2) {
+                // autotune: time a few MCS of each eligible sweep and block shape on the real chain
+                // (all give the same spins) and keep the fastest for this context. Shapes: threads
+                // per block of the resident sweep (so sites per thread), blocks per cluster of the
+                // cluster sweep.
+                struct Cand {
+                    int v, a, b, split, group;  // sweep; threads (resident) or blocks per cluster,
+                                                // threads; cluster split; threads per small instance
+                };
+                std::vector<Cand> cand{{0, 0, 0, 0, 0}};
+                // instances of very different sizes (split and grouping candidates)
+                const bool uneven = c->res_items > 1 && 4 * (int64_t)c->min_instance_sites < c->max_instance_sites;
+                if (c->res_eligible) {
+                    cand.push_back({1, 256, 0, 0, 0});
+                    cand.push_back({1, 512, 0, 0, 0});
+                    if (uneven) {  // small instances several to a block
+                        cand.push_back({1, 512, 0, 0, 128});
+                        cand.push_back({1, 512, 0, 0, 256});
                     }
-                    cudaEvent_t x0, x1;
-                    CK(c, cudaEventCreate(&x0));
-                    CK(c, cudaEventCreate(&x1));
-                    CK(c, cudaEventRecord(x0, c->stream));
-                    if ((st = run_variant(v, m0, probe)) != VEGAS_OK) return st;
-                    CK(c, cudaEventRecord(x1, c->stream));
-                    CK(c, cudaStreamSynchronize(c->stream));
-                    float ms = 0.f;
-                    CK(c, cudaEventElapsedTime(&ms, x0, x1));
-                    cudaEventDestroy(x0);
-                    cudaEventDestroy(x1);
-                    if (c->tune_ms[v] == 0.0 || ms / probe < c->tune_ms[v]) c->tune_ms[v] = ms / probe;
-                    sweep_ms += ms;
-                    if (v == cand[0].v || ms < best) {
-                        best = ms;
-                        best_v = v;
-                        best_c = vc;
-                    }
-                    m0 += probe;
-                    uint32_t e4 = 0;
-                    CK(c, cudaMemcpy(&e4, c->d_err, sizeof e4, cudaMemcpyDeviceToHost));
-                    if (e4) break;  // report the device error below
                 }
-                c->variant = best_v;
-                if (best_v == 1)
-                    set_resident_shape(c, best_c.a, best_c.group, best_c.group * 16);
-                else
-                    set_resident_shape(c, rt_rule);
+                if (c->coop_eligible) cand.push_back({2, 0, 0, 0, 0});
                 if (c->cluster_eligible) {
-                    if (best_v == 3) {
-                        set_cluster_shape(c, best_c.a, best_c.b, best_c.split);
-                        c->res.group_threads = best_c.group < best_c.b ? best_c.group : 0;
-                        c->res.group_sites = c->res.group_threads * 16;
-                    } else {
-                        set_cluster_shape(c, cs_rule, ct_rule);
+                    const int cs0 = c->cluster_cs, big = c->max_instance_sites;
+                    cand.push_back({3, cs0, 256, 0, 0});
+                    if (cs0 / 2 >= 2) cand.push_back({3, cs0 / 2, 256, 0, 0});
+                    // batches of uneven instances: clusters for the largest, blocks (and groups of a
+                    // block) for the rest
+                    if (uneven)
+                        for (int sp : {big / 2, big / 4})
+                            if (sp > 0) {
+                                cand.push_back({3, 2, 512, sp, 128});
+                                cand.push_back({3, 4, 256, sp, 0});
+                            }
+                }
+                // longer probes when the step allows (less noise between close candidates), at most
+                // a quarter of the step
+                const int32_t probe = std::max(1, std::min(16, mcs / (4 * (int32_t)cand.size())));
+                if (probe * (int32_t)cand.size() <= mcs) {
+                    float best = 0.f;
+                    int best_v = c->variant;
+                    Cand best_c = cand[0];
+                    const int cs_rule = c->cluster_cs, ct_rule = c->cluster_threads, rt_rule = c->res_threads;
+                    for (const Cand &vc : cand) {
+                        const int v = vc.v;
+                        // grouped instances: group_threads threads for up to 16 sites each per thread
+                        if (v == 1) set_resident_shape(c, vc.a, vc.group, vc.group * 16);
+                        if (v == 3) {
+                            if (!set_cluster_shape(c, vc.a, vc.b, vc.split)) continue;
+                            c->res.group_threads = vc.group < vc.b ? vc.group : 0;
+                            c->res.group_sites = c->res.group_threads * 16;
+                        }
+                        cudaEvent_t x0, x1;
+                        CK(c, cudaEventCreate(&x0));
+                        CK(c, cudaEventCreate(&x1));
+                        CK(c, cudaEventRecord(x0, c->stream));
+                        if ((st = run_variant(v, m0, probe)) != VEGAS_OK) return st;
+                        CK(c, cudaEventRecord(x1, c->stream));
+                        CK(c, cudaStreamSynchronize(c->stream));
+                        float ms = 0.f;
+                        CK(c, cudaEventElapsedTime(&ms, x0, x1));
+                        cudaEventDestroy(x0);
+                        cudaEventDestroy(x1);
+                        if (c->tune_ms[v] == 0.0 || ms / probe < c->tune_ms[v]) c->tune_ms[v] = ms / probe;
+                        sweep_ms += ms;
+                        if (v == cand[0].v || ms < best) {
+                            best = ms;
+                            best_v = v;
+                            best_c = vc;
+                        }
+                        m0 += probe;
+                        uint32_t e4 = 0;
+                        CK(c, cudaMemcpy(&e4, c->d_err, sizeof e4, cudaMemcpyDeviceToHost));
+                        if (e4) break;  // report the device error below
+                    }
+                    c->variant = best_v;
+                    if (best_v == 1)
+                        set_resident_shape(c, best_c.a, best_c.group, best_c.group * 16);
+                    else
+                        set_resident_shape(c, rt_rule);
+                    if (c->cluster_eligible) {
+                        if (best_v == 3) {
+                            set_cluster_shape(c, best_c.a, best_c.b, best_c.split);
+                            c->res.group_threads = best_c.group < best_c.b ? best_c.group : 0;
+                            c->res.group_sites = c->res.group_threads * 16;
+                        } else {
+                            set_cluster_shape(c, cs_rule, ct_rule);
+                        }
                     }
                 }
+                c->tuned = true;
             }
-            c->tuned = true;
-        }
 
-        if (m0 == 0 && c->tuned && use_graph && c->opt.graphs == 1 && step_graph_nodes(c, mcs) > 0) {
-            // every remaining step in one launch of the run graph
-            cudaGraphExec_t ge;
-            if (run_graph(c, mcs, &ge)) {
+            if (m0 == 0 && c->tuned && use_graph && c->opt.graphs == 1 && step_graph_nodes(c, mcs) > 0) {
+                // every remaining step in one launch of the run graph
+                cudaGraphExec_t ge;
+                if (run_graph(c, mcs, &ge)) {
+                    CK(c, cudaGraphLaunch(ge, c->stream));
+                    c->graph_launches++;
+                    const int64_t left = n_steps - s;
+                    // kernels per step: the sweep's (a persistent launch + advance; mcs x (wavefront +
+                    // reduction); or mcs x (passes + reduction)), the renormalisation, the snapshot,
+                    // the loop control
+                    const int64_t sweep_k = c->variant == 4 ? 2 * (int64_t)mcs
+                                            : (c->variant >= 1 ? 2 : (int64_t)mcs * ((int64_t)c->passes.size() + 1));
+                    c->kernel_launches += left * (sweep_k + 2 + (c->opt.snapshots ? 1 : 0));
+                    c->sweep_launches += c->variant == 4 ? left * (int64_t)mcs
+                                         : (c->variant >= 1 ? left : left * (int64_t)mcs * (int64_t)c->passes.size());
+                    break;
+                }
+            }
+            if (m0 == 0 && c->tuned && use_graph && c->variant < 2 && step_graph_nodes(c, mcs) > 0) {
+                // the whole step as one graph (the cooperative and cluster launches stay direct launches)
+                cudaGraphExec_t ge;
+                if ((st = step_graph(c, mcs, &ge)) != VEGAS_OK) return st;
                 CK(c, cudaGraphLaunch(ge, c->stream));
                 c->graph_launches++;
-                const int64_t left = n_steps - s;
-                // kernels per step: the sweep's (a persistent launch + advance; mcs x (wavefront +
-                // reduction); or mcs x (passes + reduction)), the renormalisation, the snapshot,
-                // the loop control
-                const int64_t sweep_k = c->variant == 4 ? 2 * (int64_t)mcs
-                                        : (c->variant >= 1 ? 2 : (int64_t)mcs * ((int64_t)c->passes.size() + 1));
-                c->kernel_launches += left * (sweep_k + 2 + (c->opt.snapshots ? 1 : 0));
-                c->sweep_launches += c->variant == 4 ? left * (int64_t)mcs
-                                     : (c->variant >= 1 ? left : left * (int64_t)mcs * (int64_t)c->passes.size());
-                break;
+                const int64_t nodes = step_graph_nodes(c, mcs);
+                c->kernel_launches += c->variant >= 1 ? 3 + (c->opt.snapshots ? 1 : 0) : nodes;
+                c->sweep_launches += c->variant >= 1 ? 1 : (int64_t)mcs * (int64_t)c->passes.size();
+                continue;
             }
-        }
-        if (m0 == 0 && c->tuned && use_graph && c->variant < 2 && step_graph_nodes(c, mcs) > 0) {
-            // the whole step as one graph (the cooperative and cluster launches stay direct launches)
-            cudaGraphExec_t ge;
-            if ((st = step_graph(c, mcs, &ge)) != VEGAS_OK) return st;
-            CK(c, cudaGraphLaunch(ge, c->stream));
-            c->graph_launches++;
-            const int64_t nodes = step_graph_nodes(c, mcs);
-            c->kernel_launches += c->variant >= 1 ? 3 + (c->opt.snapshots ? 1 : 0) : nodes;
-            c->sweep_launches += c->variant >= 1 ? 1 : (int64_t)mcs * (int64_t)c->passes.size();
-            continue;
-        }
-        if ((st = run_variant(c->variant, m0, mcs - m0)) != VEGAS_OK) return st;
-        enqueue_renorm(c, c->stream);
-        c->kernel_launches += c->opt.snapshots ? 2 : 1;
-        if (c->opt.timing) {  // read this step's sweep timings before the events are reused
-            CK(c, cudaStreamSynchronize(c->stream));
-            if (c->variant == 4) {
-                for (int32_t m = m0; m < mcs; ++m) {
-                    float ms = 0.f;
-                    CK(c, cudaEventElapsedTime(&ms, ev[2 * (size_t)m], ev[2 * (size_t)m + 1]));
-                    sweep_ms += ms;
-                }
-            } else if (c->variant >= 1) {
-                float ms = 0.f;
-                CK(c, cudaEventElapsedTime(&ms, ev[ev.size() - 2], ev[ev.size() - 1]));
-                sweep_ms += ms;
-            } else {
-                for (size_t k = (size_t)m0 * 2 * c->passes.size(); k + 1 < ev.size() - 2; k += 2) {
-                    float ms = 0.f;
-                    CK(c, cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
-                    sweep_ms += ms;
-                }
-            }
-        }
-    }
-    CK(c, cudaEventRecord(e1, c->stream));
-    CK(c, cudaGetLastError());
-    CK(c, cudaStreamSynchronize(c->stream));
-    float run_ms = 0.f;
-    CK(c, cudaEventElapsedTime(&run_ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    for (auto &x : ev) cudaEventDestroy(x);
-    c->last_run_ms = run_ms;
-    c->sweep_ms += sweep_ms;
-    uint32_t derr4[4] = {0, 0, 0, 0};
-    CK(c, cudaMemcpy(derr4, c->d_err, sizeof derr4, cudaMemcpyDeviceToHost));
-    const uint32_t derr = derr4[0];
-    // history: device [rec][inst][4] -> host per instance, appended
-    std::vector<double> h(hneed);
-    CK(c, cudaMemcpy(h.data(), c->d_hist, sizeof(double) * hneed, cudaMemcpyDeviceToHost));
-    for (int64_t i = 0; i < NI; ++i) {
-        auto &v = c->hist[(size_t)i];
-        const size_t old = v.size();
-        v.resize(old + (size_t)nrec * 4);
-        for (int64_t r = 0; r < nrec; ++r)
-            std::memcpy(&v[old + (size_t)r * 4], &h[((size_t)r * NI + i) * 4], 4 * sizeof(double));
-    }
-    std::vector<uint32_t> ha(aneed);
-    CK(c, cudaMemcpy(ha.data(), c->d_acc_hist, sizeof(uint32_t) * aneed, cudaMemcpyDeviceToHost));
-    for (int64_t i = 0; i < NI; ++i) {
-        auto &v = c->acc_hist[(size_t)i];
-        const size_t old = v.size();
-        v.resize(old + (size_t)nrec);
-        for (int64_t r = 0; r < nrec; ++r) v[old + (size_t)r] = ha[(size_t)r * NI + i];
-    }
-    if (tneed > 0) {  // [rec][inst][type][3] -> per instance, appended
-        std::vector<double> ht(tneed);
-        CK(c, cudaMemcpy(ht.data(), c->d_type_hist, sizeof(double) * tneed, cudaMemcpyDeviceToHost));
-        const size_t per = (size_t)c->n_types * 3;
-        for (int64_t i = 0; i < NI; ++i) {
-            auto &v = c->type_hist[(size_t)i];
-            const size_t old = v.size();
-            v.resize(old + (size_t)nrec * per);
-            for (int64_t r = 0; r < nrec; ++r)
-                std::memcpy(&v[old + (size_t)r * per], &ht[((size_t)r * NI + i) * per], per * sizeof(double));
-        }
-    }
-    if (sneed > 0) {  // [step][site][replica] in the device layout -> per instance, caller order
-        std::vector<unsigned char> hs(sneed);
-        CK(c, cudaMemcpy(hs.data(), c->d_snap, sneed, cudaMemcpyDeviceToHost));
-        const size_t step_bytes = (size_t)(c->n_sites * c->R * vbytes);
-        for (int32_t sm = 0; sm < c->n_samples; ++sm) {
-            const SampleInfo &si = c->samples[(size_t)sm];
-            for (int32_t r = 0; r < c->R; ++r) {
-                auto &v = c->snaps[(size_t)(sm * c->R + r)];
-                const size_t old = v.size();
-                v.resize(old + (size_t)n_steps * (size_t)si.n * 3);
-                for (int32_t st = 0; st < n_steps; ++st)
-                    for (int32_t g = 0; g < si.n; ++g) {
-                        const unsigned char *p =
-                            hs.data() + (size_t)st * step_bytes + ((size_t)(si.site_off + g) * c->R + r) * vbytes;
-                        double *o3 = &v[old + ((size_t)st * si.n + (size_t)si.orig[(size_t)g]) * 3];
-                        if (c->precision == 64) {
-                            std::memcpy(o3, p, 3 * sizeof(double));
-                        } else {
-                            float f[3];
-                            std::memcpy(f, p, sizeof f);
-                            for (int q = 0; q < 3; ++q) o3[q] = f[q];
-                        }
+            if ((st = run_variant(c->variant, m0, mcs - m0)) != VEGAS_OK) return st;
+            enqueue_renorm(c, c->stream);
+            c->kernel_launches += c->opt.snapshots ? 2 : 1;
+            if (c->opt.timing) {  // read this step's sweep timings before the events are reused
+                CK(c, cudaStreamSynchronize(c->stream));
+                if (c->variant == 4) {
+                    for (int32_t m = m0; m < mcs; ++m) {
+                        float ms = 0.f;
+                        CK(c, cudaEventElapsedTime(&ms, ev[2 * (size_t)m], ev[2 * (size_t)m + 1]));
+                        sweep_ms += ms;
                     }
+                } else if (c->variant >= 1) {
+                    float ms = 0.f;
+                    CK(c, cudaEventElapsedTime(&ms, ev[ev.size() - 2], ev[ev.size() - 1]));
+                    sweep_ms += ms;
+                } else {
+                    for (size_t k = (size_t)m0 * 2 * c->passes.size(); k + 1 < ev.size() - 2; k += 2) {
+                        float ms = 0.f;
+                        CK(c, cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+                        sweep_ms += ms;
+                    }
+                }
             }
         }
-        c->snapshot_steps += n_steps;
+        CK(c, cudaEventRecord(e1, c->stream));
+        CK(c, cudaGetLastError());
+        CK(c, cudaStreamSynchronize(c->stream));
+        float run_ms = 0.f;
+        CK(c, cudaEventElapsedTime(&run_ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        for (auto &x : ev) cudaEventDestroy(x);
+        c->last_run_ms = run_ms;
+        c->sweep_ms += sweep_ms;
+        uint32_t derr4[4] = {0, 0, 0, 0};
+        CK(c, cudaMemcpy(derr4, c->d_err, sizeof derr4, cudaMemcpyDeviceToHost));
+        const uint32_t derr = derr4[0];
+        // history: device [rec][inst][4] -> host per instance, appended
+        std::vector<double> h(hneed);
+        CK(c, cudaMemcpy(h.data(), c->d_hist, sizeof(double) * hneed, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < NI; ++i) {
+            auto &v = c->hist[(size_t)i];
+            const size_t old = v.size();
+            v.resize(old + (size_t)nrec * 4);
+            for (int64_t r = 0; r < nrec; ++r)
+                std::memcpy(&v[old + (size_t)r * 4], &h[((size_t)r * NI + i) * 4], 4 * sizeof(double));
+        }
+        std::vector<uint32_t> ha(aneed);
+        CK(c, cudaMemcpy(ha.data(), c->d_acc_hist, sizeof(uint32_t) * aneed, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < NI; ++i) {
+            auto &v = c->acc_hist[(size_t)i];
+            const size_t old = v.size();
+            v.resize(old + (size_t)nrec);
+            for (int64_t r = 0; r < nrec; ++r) v[old + (size_t)r] = ha[(size_t)r * NI + i];
+        }
+        if (tneed > 0) {  // [rec][inst][type][3] -> per instance, appended
+            std::vector<double> ht(tneed);
+            CK(c, cudaMemcpy(ht.data(), c->d_type_hist, sizeof(double) * tneed, cudaMemcpyDeviceToHost));
+            const size_t per = (size_t)c->n_types * 3;
+            for (int64_t i = 0; i < NI; ++i) {
+                auto &v = c->type_hist[(size_t)i];
+                const size_t old = v.size();
+                v.resize(old + (size_t)nrec * per);
+                for (int64_t r = 0; r < nrec; ++r)
+                    std::memcpy(&v[old + (size_t)r * per], &ht[((size_t)r * NI + i) * per], per * sizeof(double));
+            }
+        }
+        if (sneed > 0) {  // [step][site][replica] in the device layout -> per instance, caller order
+            std::vector<unsigned char> hs(sneed);
+            CK(c, cudaMemcpy(hs.data(), c->d_snap, sneed, cudaMemcpyDeviceToHost));
+            const size_t step_bytes = (size_t)(c->n_sites * c->R * vbytes);
+            for (int32_t sm = 0; sm < c->n_samples; ++sm) {
+                const SampleInfo &si = c->samples[(size_t)sm];
+                for (int32_t r = 0; r < c->R; ++r) {
+                    auto &v = c->snaps[(size_t)(sm * c->R + r)];
+                    const size_t old = v.size();
+                    v.resize(old + (size_t)n_steps * (size_t)si.n * 3);
+                    for (int32_t st = 0; st < n_steps; ++st)
+                        for (int32_t g = 0; g < si.n; ++g) {
+                            const unsigned char *p =
+                                hs.data() + (size_t)st * step_bytes + ((size_t)(si.site_off + g) * c->R + r) * vbytes;
+                            double *o3 = &v[old + ((size_t)st * si.n + (size_t)si.orig[(size_t)g]) * 3];
+                            if (c->precision == 64) {
+                                std::memcpy(o3, p, 3 * sizeof(double));
+                            } else {
+                                float f[3];
+                                std::memcpy(f, p, sizeof f);
+                                for (int q = 0; q < 3; ++q) o3[q] = f[q];
+                            }
+                        }
+                }
+            }
+            c->snapshot_steps += n_steps;
+        }
+        c->records += nrec;
+        c->t += (uint32_t)nrec;
+        c->device_error |= derr;
+        if (derr & kErrTimeout)
+            return fail(c, VEGAS_ETIMEOUT,
+                        c->variant == 4 ? "a warp of the wavefront sweep waited longer than timeout_ns for the class-0 "
+                                          "blocks that a class-1 block links to"
+                                        : "a grid barrier of the cooperative sweep waited longer than timeout_ns");
+        if (derr) {
+            char msg[200];
+            std::snprintf(msg, sizeof msg,
+                          "device error flags 0x%x (1: NaN energy change, 2: sphere sampler cap, 4: index check; "
+                          "check code %u, value %u)",
+                          derr, derr4[1], derr4[2]);
+            return fail(c, VEGAS_EDEVICE, msg);
+        }
+        return VEGAS_OK;
+    } catch (...) {
+        return host_exception(c);
     }
-    c->records += nrec;
-    c->t += (uint32_t)nrec;
-    c->device_error |= derr;
-    if (derr & kErrTimeout)
-        return fail(c, VEGAS_ETIMEOUT,
-                    c->variant == 4 ? "a warp of the wavefront sweep waited longer than timeout_ns for the class-0 "
-                                      "blocks that a class-1 block links to"
-                                    : "a grid barrier of the cooperative sweep waited longer than timeout_ns");
-    if (derr) {
-        char msg[200];
-        std::snprintf(msg, sizeof msg,
-                      "device error flags 0x%x (1: NaN energy change, 2: sphere sampler cap, 4: index check; "
-                      "check code %u, value %u)",
-                      derr, derr4[1], derr4[2]);
-        return fail(c, VEGAS_EDEVICE, msg);
-    }
-    return VEGAS_OK;
 }
 
 extern "C" vegas_status vegas_history(const vegas_ctx *cc, double *out, size_t capacity, size_t *n_written) {
-    vegas_ctx *c = const_cast<vegas_ctx *>(cc);
-    vegas_status st = check_usable(c);
-    if (st != VEGAS_OK) return st;
-    const size_t need = (size_t)c->n_inst * (size_t)c->records * 4;
-    if (n_written) *n_written = need;
-    if (!out) return VEGAS_OK;
-    if (capacity < need) return fail(c, VEGAS_EINVAL, "history buffer too small");
-    for (int i = 0; i < c->n_inst; ++i)
-        std::memcpy(out + (size_t)i * c->records * 4, c->hist[(size_t)i].data(), sizeof(double) * c->records * 4);
-    return VEGAS_OK;
+    try {
+        vegas_ctx *c = const_cast<vegas_ctx *>(cc);
+        vegas_status st = check_usable(c);
+        if (st != VEGAS_OK) return st;
+        const size_t need = (size_t)c->n_inst * (size_t)c->records * 4;
+        if (n_written) *n_written = need;
+        if (!out) return VEGAS_OK;
+        if (capacity < need) return fail(c, VEGAS_EINVAL, "history buffer too small");
+        for (int i = 0; i < c->n_inst; ++i)
+            std::memcpy(out + (size_t)i * c->records * 4, c->hist[(size_t)i].data(), sizeof(double) * c->records * 4);
+        return VEGAS_OK;
+    } catch (...) {
+        return host_exception(const_cast<vegas_ctx *>(cc));
+    }
 }
 
 extern "C" vegas_status vegas_accept_history(const vegas_ctx *cc, uint32_t *out, size_t capacity, size_t *n_written) {
-    vegas_ctx *c = const_cast<vegas_ctx *>(cc);
-    vegas_status st = check_usable(c);
-    if (st != VEGAS_OK) return st;
-    const size_t need = (size_t)c->n_inst * (size_t)c->records;
-    if (n_written) *n_written = need;
-    if (!out) return VEGAS_OK;
-    if (capacity < need) return fail(c, VEGAS_EINVAL, "acceptance buffer too small");
-    for (int i = 0; i < c->n_inst; ++i)
-        std::memcpy(out + (size_t)i * c->records, c->acc_hist[(size_t)i].data(), sizeof(uint32_t) * c->records);
-    return VEGAS_OK;
+    try {
+        vegas_ctx *c = const_cast<vegas_ctx *>(cc);
+        vegas_status st = check_usable(c);
+        if (st != VEGAS_OK) return st;
+        const size_t need = (size_t)c->n_inst * (size_t)c->records;
+        if (n_written) *n_written = need;
+        if (!out) return VEGAS_OK;
+        if (capacity < need) return fail(c, VEGAS_EINVAL, "acceptance buffer too small");
+        for (int i = 0; i < c->n_inst; ++i)
+            std::memcpy(out + (size_t)i * c->records, c->acc_hist[(size_t)i].data(), sizeof(uint32_t) * c->records);
+        return VEGAS_OK;
+    } catch (...) {
+        return host_exception(const_cast<vegas_ctx *>(cc));
+    }
 }
 
 extern "C" vegas_status vegas_type_history(const vegas_ctx *cc, double *out, size_t capacity, size_t *n_written) {
-    vegas_ctx *c = const_cast<vegas_ctx *>(cc);
-    vegas_status st = check_usable(c);
-    if (st != VEGAS_OK) return st;
-    if (c->n_types == 0) return fail(c, VEGAS_EINVAL, "per-type statistics need the option type_stats");
-    const size_t per = (size_t)c->records * (size_t)c->n_types * 3;
-    const size_t need = (size_t)c->n_inst * per;
-    if (n_written) *n_written = need;
-    if (!out) return VEGAS_OK;
-    if (capacity < need) return fail(c, VEGAS_EINVAL, "type history buffer too small");
-    for (int i = 0; i < c->n_inst; ++i)
-        std::memcpy(out + (size_t)i * per, c->type_hist[(size_t)i].data(), sizeof(double) * per);
-    return VEGAS_OK;
+    try {
+        vegas_ctx *c = const_cast<vegas_ctx *>(cc);
+        vegas_status st = check_usable(c);
+        if (st != VEGAS_OK) return st;
+        if (c->n_types == 0) return fail(c, VEGAS_EINVAL, "per-type statistics need the option type_stats");
+        const size_t per = (size_t)c->records * (size_t)c->n_types * 3;
+        const size_t need = (size_t)c->n_inst * per;
+        if (n_written) *n_written = need;
+        if (!out) return VEGAS_OK;
+        if (capacity < need) return fail(c, VEGAS_EINVAL, "type history buffer too small");
+        for (int i = 0; i < c->n_inst; ++i)
+            std::memcpy(out + (size_t)i * per, c->type_hist[(size_t)i].data(), sizeof(double) * per);
+        return VEGAS_OK;
+    } catch (...) {
+        return host_exception(const_cast<vegas_ctx *>(cc));
+    }
 }
 
 extern "C" vegas_status vegas_get_snapshot(const vegas_ctx *cc, int32_t inst, int64_t step, double *out) {
-    vegas_ctx *c = const_cast<vegas_ctx *>(cc);
-    vegas_status st = check_usable(c);
-    if (st != VEGAS_OK) return st;
-    if (!c->opt.snapshots) return fail(c, VEGAS_EINVAL, "snapshots need the option snapshots");
-    if (inst < 0 || inst >= c->n_inst) return fail(c, VEGAS_EINVAL, "instance out of range");
-    if (step < 0 || step >= c->snapshot_steps) return fail(c, VEGAS_EINVAL, "no snapshot for this step");
-    if (!out) return fail(c, VEGAS_EINVAL, "out is NULL");
-    const size_t n3 = (size_t)c->samples[(size_t)(inst / c->R)].n * 3;
-    std::memcpy(out, c->snaps[(size_t)inst].data() + (size_t)step * n3, sizeof(double) * n3);
-    return VEGAS_OK;
+    try {
+        vegas_ctx *c = const_cast<vegas_ctx *>(cc);
+        vegas_status st = check_usable(c);
+        if (st != VEGAS_OK) return st;
+        if (!c->opt.snapshots) return fail(c, VEGAS_EINVAL, "snapshots need the option snapshots");
+        if (inst < 0 || inst >= c->n_inst) return fail(c, VEGAS_EINVAL, "instance out of range");
+        if (step < 0 || step >= c->snapshot_steps) return fail(c, VEGAS_EINVAL, "no snapshot for this step");
+        if (!out) return fail(c, VEGAS_EINVAL, "out is NULL");
+        const size_t n3 = (size_t)c->samples[(size_t)(inst / c->R)].n * 3;
+        std::memcpy(out, c->snaps[(size_t)inst].data() + (size_t)step * n3, sizeof(double) * n3);
+        return VEGAS_OK;
+    } catch (...) {
+        return host_exception(const_cast<vegas_ctx *>(cc));
+    }
 }
 
 extern "C" vegas_status vegas_adaptive_width(const vegas_ctx *cc, double *out) {
-    vegas_ctx *c = const_cast<vegas_ctx *>(cc);
-    vegas_status st = check_usable(c);
-    if (st != VEGAS_OK) return st;
-    if (!out) return fail(c, VEGAS_EINVAL, "out is NULL");
-    if ((st = set_device(c)) != VEGAS_OK) return st;
-    CK(c, cudaMemcpy(out, c->d_sigma, sizeof(double) * (size_t)c->n_inst, cudaMemcpyDeviceToHost));
-    return VEGAS_OK;
+    try {
+        vegas_ctx *c = const_cast<vegas_ctx *>(cc);
+        vegas_status st = check_usable(c);
+        if (st != VEGAS_OK) return st;
+        if (!out) return fail(c, VEGAS_EINVAL, "out is NULL");
+        if ((st = set_device(c)) != VEGAS_OK) return st;
+        CK(c, cudaMemcpy(out, c->d_sigma, sizeof(double) * (size_t)c->n_inst, cudaMemcpyDeviceToHost));
+        return VEGAS_OK;
+    } catch (...) {
+        return host_exception(const_cast<vegas_ctx *>(cc));
+    }
 }
 
 extern "C" vegas_status vegas_set_adaptive_width(vegas_ctx *c, const double *in) {
-    vegas_status st = check_usable(c);
-    if (st != VEGAS_OK) return st;
-    if (!in) return fail(c, VEGAS_EINVAL, "in is NULL");
-    std::vector<double> h((size_t)c->n_inst, 0.0);
-    for (int32_t i = 0; i < c->n_inst; ++i) {
-        if (!c->samples[(size_t)(i / c->R)].has_adaptive) continue;
-        if (!(in[i] > 0.0) || !std::isfinite(in[i])) return fail(c, VEGAS_EINVAL, "width must be finite and > 0");
-        h[(size_t)i] = in[i];
+    try {
+        vegas_status st = check_usable(c);
+        if (st != VEGAS_OK) return st;
+        if (!in) return fail(c, VEGAS_EINVAL, "in is NULL");
+        std::vector<double> h((size_t)c->n_inst, 0.0);
+        for (int32_t i = 0; i < c->n_inst; ++i) {
+            if (!c->samples[(size_t)(i / c->R)].has_adaptive) continue;
+            if (!(in[i] > 0.0) || !std::isfinite(in[i])) return fail(c, VEGAS_EINVAL, "width must be finite and > 0");
+            h[(size_t)i] = in[i];
+        }
+        if ((st = set_device(c)) != VEGAS_OK) return st;
+        CK(c, cudaMemcpy(c->d_sigma, h.data(), sizeof(double) * (size_t)c->n_inst, cudaMemcpyHostToDevice));
+        return VEGAS_OK;
+    } catch (...) {
+        return host_exception(c);
     }
-    if ((st = set_device(c)) != VEGAS_OK) return st;
-    CK(c, cudaMemcpy(c->d_sigma, h.data(), sizeof(double) * (size_t)c->n_inst, cudaMemcpyHostToDevice));
-    return VEGAS_OK;
 }
 
 extern "C" vegas_status vegas_set_mcs_counter(vegas_ctx *c, uint32_t t) {
-    vegas_status st = check_usable(c);
-    if (st != VEGAS_OK) return st;
-    if (t == UINT32_MAX) return fail(c, VEGAS_EINVAL, "MCS counter must be below 2^32 - 1");
-    if (c->d_done) {
-        // the wavefront sweep's completion words hold t + 1 of past MCS; cleared, none can
-        // match an MCS of the new count before its class-0 block has finished
-        if ((st = set_device(c)) != VEGAS_OK) return st;
-        CK(c, cudaMemsetAsync(c->d_done, 0, sizeof(uint32_t) * (size_t)c->wave.nb0, c->stream));
-        CK(c, cudaStreamSynchronize(c->stream));
+    try {
+        vegas_status st = check_usable(c);
+        if (st != VEGAS_OK) return st;
+        if (t == UINT32_MAX) return fail(c, VEGAS_EINVAL, "MCS counter must be below 2^32 - 1");
+        if (c->d_done) {
+            // the wavefront sweep's completion words hold t + 1 of past MCS; cleared, none can
+            // match an MCS of the new count before its class-0 block has finished
+            if ((st = set_device(c)) != VEGAS_OK) return st;
+            CK(c, cudaMemsetAsync(c->d_done, 0, sizeof(uint32_t) * (size_t)c->wave.nb0, c->stream));
+            CK(c, cudaStreamSynchronize(c->stream));
+        }
+        c->t = t;
+        return VEGAS_OK;
+    } catch (...) {
+        return host_exception(c);
     }
-    c->t = t;
-    return VEGAS_OK;
 }
 
 namespace {
@@ -1689,55 +1747,71 @@ vegas_status spins_io(vegas_ctx *c, int32_t inst, double *out, const double *in)
 }  // namespace
 
 extern "C" vegas_status vegas_get_spins(const vegas_ctx *c, int32_t inst, double *out) {
-    if (!out) return fail(const_cast<vegas_ctx *>(c), VEGAS_EINVAL, "out is NULL");
-    return spins_io(const_cast<vegas_ctx *>(c), inst, out, nullptr);
+    try {
+        if (!out) return fail(const_cast<vegas_ctx *>(c), VEGAS_EINVAL, "out is NULL");
+        return spins_io(const_cast<vegas_ctx *>(c), inst, out, nullptr);
+    } catch (...) {
+        return host_exception(const_cast<vegas_ctx *>(c));
+    }
 }
 
 extern "C" vegas_status vegas_set_spins(vegas_ctx *c, int32_t inst, const double *in) {
-    if (!in) return fail(c, VEGAS_EINVAL, "in is NULL");
-    return spins_io(c, inst, nullptr, in);
+    try {
+        if (!in) return fail(c, VEGAS_EINVAL, "in is NULL");
+        return spins_io(c, inst, nullptr, in);
+    } catch (...) {
+        return host_exception(c);
+    }
 }
 
 extern "C" vegas_status vegas_accept_log(const vegas_ctx *cc, uint8_t *out, size_t capacity, size_t *n_written) {
-    vegas_ctx *c = const_cast<vegas_ctx *>(cc);
-    vegas_status st = check_usable(c);
-    if (st != VEGAS_OK) return st;
-    if (n_written) *n_written = (size_t)c->alog_bytes;
-    if (!out || c->alog_bytes == 0) return VEGAS_OK;
-    if (capacity < (size_t)c->alog_bytes) return fail(c, VEGAS_EINVAL, "accept log buffer too small");
-    if ((st = set_device(c)) != VEGAS_OK) return st;
-    CK(c, cudaMemcpy(out, c->d_alog, (size_t)c->alog_bytes, cudaMemcpyDeviceToHost));
-    return VEGAS_OK;
+    try {
+        vegas_ctx *c = const_cast<vegas_ctx *>(cc);
+        vegas_status st = check_usable(c);
+        if (st != VEGAS_OK) return st;
+        if (n_written) *n_written = (size_t)c->alog_bytes;
+        if (!out || c->alog_bytes == 0) return VEGAS_OK;
+        if (capacity < (size_t)c->alog_bytes) return fail(c, VEGAS_EINVAL, "accept log buffer too small");
+        if ((st = set_device(c)) != VEGAS_OK) return st;
+        CK(c, cudaMemcpy(out, c->d_alog, (size_t)c->alog_bytes, cudaMemcpyDeviceToHost));
+        return VEGAS_OK;
+    } catch (...) {
+        return host_exception(const_cast<vegas_ctx *>(cc));
+    }
 }
 
 extern "C" vegas_status vegas_stats(const vegas_ctx *c, vegas_stats_t *o) {
-    if (!c || !o) return VEGAS_EINVAL;
-    std::memset(o, 0, sizeof *o);
-    o->n_samples = c->n_samples;
-    o->n_instances = c->n_inst;
-    o->replicas = c->R;
-    o->precision = c->precision;
-    o->max_colours = c->max_colours;
-    o->variant = c->variant;
-    o->n_sites = c->n_sites;
-    o->n_edges = c->n_edges;
-    o->records = c->records;
-    o->mcs_done = c->t;
-    o->device_error = c->device_error;
-    o->kernel_launches = c->kernel_launches;
-    o->sweep_launches = c->sweep_launches;
-    o->sweep_ms = c->sweep_ms;
-    o->last_run_ms = c->last_run_ms;
-    o->device_bytes = c->device_bytes;
-    o->n_types = c->n_types;
-    o->snapshot_steps = c->snapshot_steps;
-    o->block_threads = c->variant == 1 ? c->res_threads : (c->variant == 3 ? c->cluster_threads : kThreads);
-    o->cluster_blocks = c->variant == 3 ? c->cluster_cs : 0;
-    o->split_sites = c->variant == 3 ? c->res.split_sites : 0;
-    o->group_threads = (c->variant == 1 || c->variant == 3) ? c->res.group_threads : 0;
-    o->group_sites = (c->variant == 1 || c->variant == 3) ? c->res.group_sites : 0;
-    o->graph_launches = c->graph_launches;
-    return VEGAS_OK;
+    try {
+        if (!c || !o) return VEGAS_EINVAL;
+        std::memset(o, 0, sizeof *o);
+        o->n_samples = c->n_samples;
+        o->n_instances = c->n_inst;
+        o->replicas = c->R;
+        o->precision = c->precision;
+        o->max_colours = c->max_colours;
+        o->variant = c->variant;
+        o->n_sites = c->n_sites;
+        o->n_edges = c->n_edges;
+        o->records = c->records;
+        o->mcs_done = c->t;
+        o->device_error = c->device_error;
+        o->kernel_launches = c->kernel_launches;
+        o->sweep_launches = c->sweep_launches;
+        o->sweep_ms = c->sweep_ms;
+        o->last_run_ms = c->last_run_ms;
+        o->device_bytes = c->device_bytes;
+        o->n_types = c->n_types;
+        o->snapshot_steps = c->snapshot_steps;
+        o->block_threads = c->variant == 1 ? c->res_threads : (c->variant == 3 ? c->cluster_threads : kThreads);
+        o->cluster_blocks = c->variant == 3 ? c->cluster_cs : 0;
+        o->split_sites = c->variant == 3 ? c->res.split_sites : 0;
+        o->group_threads = (c->variant == 1 || c->variant == 3) ? c->res.group_threads : 0;
+        o->group_sites = (c->variant == 1 || c->variant == 3) ? c->res.group_sites : 0;
+        o->graph_launches = c->graph_launches;
+        return VEGAS_OK;
+    } catch (...) {
+        return host_exception(const_cast<vegas_ctx *>(c));
+    }
 }
 
 extern "C" const char *vegas_last_error(const vegas_ctx *c) {

@@ -3,6 +3,9 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <exception>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -11,6 +14,27 @@
 #include "../../include/vegas.h"
 
 namespace vegas {
+
+// Status and message of the exception being handled (call it inside a catch block only): the
+// entry points turn host exceptions, such as a failed allocation, into a status instead of
+// letting them cross the C boundary.
+inline vegas_status status_of_current_exception(std::string &msg) {
+    try {
+        throw;
+    } catch (const std::bad_alloc &) {
+        msg = "host allocation failed";
+        return VEGAS_ENOMEM;
+    } catch (const std::length_error &) {
+        msg = "host allocation failed (size out of range)";
+        return VEGAS_ENOMEM;
+    } catch (const std::exception &e) {
+        msg = std::string("host error: ") + e.what();
+        return VEGAS_EINVAL;
+    } catch (...) {
+        msg = "host error";
+        return VEGAS_EINVAL;
+    }
+}
 
 constexpr int kMaxColours = 64;
 constexpr int kMaxTypes = 64;   // site types tracked by the per-type statistics

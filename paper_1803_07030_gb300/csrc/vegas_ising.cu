@@ -254,6 +254,13 @@ vegas_status ifail(vegas_ising *c, vegas_status st, const std::string &m) {
     return st;
 }
 
+// A host exception caught at an entry point, as a status (called inside a catch block).
+vegas_status ising_host_exception(vegas_ising *c) {
+    std::string m;
+    const vegas_status st = status_of_current_exception(m);
+    return ifail(c, st, m);
+}
+
 #define ICK(ctx, call)                                                                                 \
     do {                                                                                               \
         cudaError_t e_ = (call);                                                                       \
@@ -302,7 +309,8 @@ extern "C" void vegas_ising_default_options(vegas_ising_options *o) {
     o->timing = 0;
 }
 
-extern "C" vegas_status vegas_ising_create(const vegas_ising_options *opt, vegas_ising **out) {
+// vegas_ising_create without the exception guard; *made is the context under construction.
+static vegas_status ising_create(const vegas_ising_options *opt, vegas_ising **out, vegas_ising **made) {
     if (!out) return ifail(nullptr, VEGAS_EINVAL, "out is NULL");
     *out = nullptr;
     vegas_ising_options o;
@@ -320,6 +328,7 @@ extern "C" vegas_status vegas_ising_create(const vegas_ising_options *opt, vegas
         return ifail(nullptr, VEGAS_EINVAL, "init_up and timing must be 0 or 1");
     vegas_ising *c = new (std::nothrow) vegas_ising();
     if (!c) return ifail(nullptr, VEGAS_ENOMEM, "host allocation failed");
+    *made = c;
     c->opt = o;
     c->n = n;
     c->rows = o.dims == 3 ? (int64_t)o.L * o.L : o.L;
@@ -329,6 +338,7 @@ extern "C" vegas_status vegas_ising_create(const vegas_ising_options *opt, vegas
         g_ising_create_error = c->err;
         ising_free(c);
         delete c;
+        *made = nullptr;
         return st;
     };
     int ndev = 0;
@@ -380,132 +390,155 @@ extern "C" vegas_status vegas_ising_create(const vegas_ising_options *opt, vegas
     return VEGAS_OK;
 }
 
+extern "C" vegas_status vegas_ising_create(const vegas_ising_options *opt, vegas_ising **out) {
+    vegas_ising *made = nullptr;
+    try {
+        return ising_create(opt, out, &made);
+    } catch (...) {
+        const vegas_status st = ising_host_exception(nullptr);
+        if (made) {
+            ising_free(made);
+            delete made;
+        }
+        if (out) *out = nullptr;
+        return st;
+    }
+}
+
 extern "C" vegas_status vegas_ising_run(vegas_ising *c, const double *T, const double *h, int32_t n_steps,
                                         int32_t mcs) {
-    vegas_status st = ising_usable(c);
-    if (st != VEGAS_OK) return st;
-    if (n_steps < 0 || mcs < 0) return ifail(c, VEGAS_EINVAL, "n_steps and mcs_per_step must be >= 0");
-    if (n_steps == 0 || mcs == 0) return VEGAS_OK;
-    if (!T || !h) return ifail(c, VEGAS_EINVAL, "T or h is NULL");
-    if ((int64_t)c->t + (int64_t)n_steps * mcs >= (int64_t)UINT32_MAX)
-        return ifail(c, VEGAS_EINVAL, "global MCS counter would exceed 32 bits");
-    const int R = c->opt.replicas, Z = c->Z;
-    std::vector<IsingThr> thr((size_t)n_steps * R);
-    std::vector<double> hv((size_t)n_steps * R);
-    for (int r = 0; r < R; ++r)
-        for (int s = 0; s < n_steps; ++s) {
-            const double Tv = T[(int64_t)r * n_steps + s], hh = h[(int64_t)r * n_steps + s];
-            if (!(Tv > 0.0) || !std::isfinite(Tv)) return ifail(c, VEGAS_EINVAL, "T must be finite and > 0");
-            if (!std::isfinite(hh)) return ifail(c, VEGAS_EINVAL, "h must be finite");
-            const double beta = 1.0 / Tv;
-            IsingThr &e = thr[(size_t)s * R + r];
-            std::memset(&e, 0, sizeof e);
-            for (int sb = 0; sb < 2; ++sb)
-                for (int al = 0; al <= Z; ++al) {
-                    const double si = sb ? 1.0 : -1.0;
-                    const double sum = sb ? (double)(2 * al - Z) : (double)(Z - 2 * al);
-                    const double dE = 2.0 * si * (c->opt.J * sum + hh);
-                    const int cls = sb * (Z + 1) + al;
-                    if (dE <= 0.0) {
-                        e.always |= 1u << cls;
-                        continue;
+    try {
+        vegas_status st = ising_usable(c);
+        if (st != VEGAS_OK) return st;
+        if (n_steps < 0 || mcs < 0) return ifail(c, VEGAS_EINVAL, "n_steps and mcs_per_step must be >= 0");
+        if (n_steps == 0 || mcs == 0) return VEGAS_OK;
+        if (!T || !h) return ifail(c, VEGAS_EINVAL, "T or h is NULL");
+        if ((int64_t)c->t + (int64_t)n_steps * mcs >= (int64_t)UINT32_MAX)
+            return ifail(c, VEGAS_EINVAL, "global MCS counter would exceed 32 bits");
+        const int R = c->opt.replicas, Z = c->Z;
+        std::vector<IsingThr> thr((size_t)n_steps * R);
+        std::vector<double> hv((size_t)n_steps * R);
+        for (int r = 0; r < R; ++r)
+            for (int s = 0; s < n_steps; ++s) {
+                const double Tv = T[(int64_t)r * n_steps + s], hh = h[(int64_t)r * n_steps + s];
+                if (!(Tv > 0.0) || !std::isfinite(Tv)) return ifail(c, VEGAS_EINVAL, "T must be finite and > 0");
+                if (!std::isfinite(hh)) return ifail(c, VEGAS_EINVAL, "h must be finite");
+                const double beta = 1.0 / Tv;
+                IsingThr &e = thr[(size_t)s * R + r];
+                std::memset(&e, 0, sizeof e);
+                for (int sb = 0; sb < 2; ++sb)
+                    for (int al = 0; al <= Z; ++al) {
+                        const double si = sb ? 1.0 : -1.0;
+                        const double sum = sb ? (double)(2 * al - Z) : (double)(Z - 2 * al);
+                        const double dE = 2.0 * si * (c->opt.J * sum + hh);
+                        const int cls = sb * (Z + 1) + al;
+                        if (dE <= 0.0) {
+                            e.always |= 1u << cls;
+                            continue;
+                        }
+                        // accept iff w < x = exp(-beta dE) 2^32 (w integer): iff w < ceil(x)
+                        const double x = std::ceil(std::exp(-(beta * dE)) * 4294967296.0);
+                        if (x >= 4294967296.0)
+                            e.always |= 1u << cls;
+                        else
+                            e.thr[cls] = (uint32_t)x;
                     }
-                    // accept iff w < x = exp(-beta dE) 2^32 (w integer): iff w < ceil(x)
-                    const double x = std::ceil(std::exp(-(beta * dE)) * 4294967296.0);
-                    if (x >= 4294967296.0)
-                        e.always |= 1u << cls;
-                    else
-                        e.thr[cls] = (uint32_t)x;
-                }
-            hv[(size_t)s * R + r] = hh;
+                hv[(size_t)s * R + r] = hh;
+            }
+        ICK(c, cudaSetDevice(c->device));
+        const int64_t nrec = (int64_t)n_steps * mcs;
+        if (thr.size() > c->thr_cap) {
+            if (c->d_thr) cudaFree(c->d_thr);
+            if (c->d_h) cudaFree(c->d_h);
+            c->d_thr = nullptr;
+            c->d_h = nullptr;
+            c->thr_cap = 0;
+            ICK(c, cudaMalloc(&c->d_thr, sizeof(IsingThr) * thr.size()));
+            ICK(c, cudaMalloc(&c->d_h, sizeof(double) * thr.size()));
+            c->thr_cap = thr.size();
         }
-    ICK(c, cudaSetDevice(c->device));
-    const int64_t nrec = (int64_t)n_steps * mcs;
-    if (thr.size() > c->thr_cap) {
-        if (c->d_thr) cudaFree(c->d_thr);
-        if (c->d_h) cudaFree(c->d_h);
-        c->d_thr = nullptr;
-        c->d_h = nullptr;
-        c->thr_cap = 0;
-        ICK(c, cudaMalloc(&c->d_thr, sizeof(IsingThr) * thr.size()));
-        ICK(c, cudaMalloc(&c->d_h, sizeof(double) * thr.size()));
-        c->thr_cap = thr.size();
-    }
-    const size_t hneed = (size_t)nrec * R * 2;
-    if (hneed > c->hist_cap) {
-        if (c->d_hist) cudaFree(c->d_hist);
-        c->d_hist = nullptr;
-        c->hist_cap = 0;
-        ICK(c, cudaMalloc(&c->d_hist, sizeof(double) * hneed));
-        c->hist_cap = hneed;
-    }
-    ICK(c, cudaMemcpyAsync(c->d_thr, thr.data(), sizeof(IsingThr) * thr.size(), cudaMemcpyHostToDevice, c->stream));
-    ICK(c, cudaMemcpyAsync(c->d_h, hv.data(), sizeof(double) * hv.size(), cudaMemcpyHostToDevice, c->stream));
-    IsingRun rs{c->t, 0u, (uint32_t)mcs, 0u, c->d_thr, c->d_h, c->d_hist, c->d_acc};
-    ICK(c, cudaMemcpyAsync(c->d_run, &rs, sizeof rs, cudaMemcpyHostToDevice, c->stream));
-    std::vector<cudaEvent_t> ev;
-    if (c->opt.timing) {
-        ev.resize((size_t)nrec * 4);
-        for (auto &x : ev) ICK(c, cudaEventCreate(&x));
-    }
-    cudaEvent_t e0, e1;
-    ICK(c, cudaEventCreate(&e0));
-    ICK(c, cudaEventCreate(&e1));
-    ICK(c, cudaEventRecord(e0, c->stream));
-    const int rthreads = std::min(std::max(32, (R + 31) / 32 * 32), 512);
-    for (int64_t m = 0; m < nrec; ++m) {
-        for (int colour = 0; colour < 2; ++colour) {
-            if (c->opt.timing) ICK(c, cudaEventRecord(ev[(size_t)m * 4 + 2 * colour], c->stream));
-            launch_ising_pass(c, colour, c->stream);
-            if (c->opt.timing) ICK(c, cudaEventRecord(ev[(size_t)m * 4 + 2 * colour + 1], c->stream));
+        const size_t hneed = (size_t)nrec * R * 2;
+        if (hneed > c->hist_cap) {
+            if (c->d_hist) cudaFree(c->d_hist);
+            c->d_hist = nullptr;
+            c->hist_cap = 0;
+            ICK(c, cudaMalloc(&c->d_hist, sizeof(double) * hneed));
+            c->hist_cap = hneed;
         }
-        ising_reduce_kernel<<<1, rthreads, 0, c->stream>>>(c->d_run, R, c->n, Z, c->opt.J);
-    }
-    ICK(c, cudaGetLastError());
-    ICK(c, cudaEventRecord(e1, c->stream));
-    ICK(c, cudaStreamSynchronize(c->stream));
-    float ms = 0.f;
-    ICK(c, cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    double sw = 0.0;
-    for (size_t k = 0; k + 1 < ev.size(); k += 2) {
-        float x = 0.f;
-        ICK(c, cudaEventElapsedTime(&x, ev[k], ev[k + 1]));
-        sw += x;
-    }
-    for (auto &x : ev) cudaEventDestroy(x);
-    c->last_run_ms = ms;
-    c->sweep_ms += sw;
-    c->kernel_launches += nrec * 3;
-    c->sweep_launches += nrec * 2;
-    std::vector<double> hh(hneed);
-    ICK(c, cudaMemcpy(hh.data(), c->d_hist, sizeof(double) * hneed, cudaMemcpyDeviceToHost));
-    for (int r = 0; r < R; ++r) {
-        auto &v = c->hist[(size_t)r];
-        const size_t old = v.size();
-        v.resize(old + (size_t)nrec * 2);
-        for (int64_t k = 0; k < nrec; ++k) {
-            v[old + (size_t)k * 2] = hh[((size_t)k * R + r) * 2];
-            v[old + (size_t)k * 2 + 1] = hh[((size_t)k * R + r) * 2 + 1];
+        ICK(c, cudaMemcpyAsync(c->d_thr, thr.data(), sizeof(IsingThr) * thr.size(), cudaMemcpyHostToDevice, c->stream));
+        ICK(c, cudaMemcpyAsync(c->d_h, hv.data(), sizeof(double) * hv.size(), cudaMemcpyHostToDevice, c->stream));
+        IsingRun rs{c->t, 0u, (uint32_t)mcs, 0u, c->d_thr, c->d_h, c->d_hist, c->d_acc};
+        ICK(c, cudaMemcpyAsync(c->d_run, &rs, sizeof rs, cudaMemcpyHostToDevice, c->stream));
+        std::vector<cudaEvent_t> ev;
+        if (c->opt.timing) {
+            ev.resize((size_t)nrec * 4);
+            for (auto &x : ev) ICK(c, cudaEventCreate(&x));
         }
+        cudaEvent_t e0, e1;
+        ICK(c, cudaEventCreate(&e0));
+        ICK(c, cudaEventCreate(&e1));
+        ICK(c, cudaEventRecord(e0, c->stream));
+        const int rthreads = std::min(std::max(32, (R + 31) / 32 * 32), 512);
+        for (int64_t m = 0; m < nrec; ++m) {
+            for (int colour = 0; colour < 2; ++colour) {
+                if (c->opt.timing) ICK(c, cudaEventRecord(ev[(size_t)m * 4 + 2 * colour], c->stream));
+                launch_ising_pass(c, colour, c->stream);
+                if (c->opt.timing) ICK(c, cudaEventRecord(ev[(size_t)m * 4 + 2 * colour + 1], c->stream));
+            }
+            ising_reduce_kernel<<<1, rthreads, 0, c->stream>>>(c->d_run, R, c->n, Z, c->opt.J);
+        }
+        ICK(c, cudaGetLastError());
+        ICK(c, cudaEventRecord(e1, c->stream));
+        ICK(c, cudaStreamSynchronize(c->stream));
+        float ms = 0.f;
+        ICK(c, cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        double sw = 0.0;
+        for (size_t k = 0; k + 1 < ev.size(); k += 2) {
+            float x = 0.f;
+            ICK(c, cudaEventElapsedTime(&x, ev[k], ev[k + 1]));
+            sw += x;
+        }
+        for (auto &x : ev) cudaEventDestroy(x);
+        c->last_run_ms = ms;
+        c->sweep_ms += sw;
+        c->kernel_launches += nrec * 3;
+        c->sweep_launches += nrec * 2;
+        std::vector<double> hh(hneed);
+        ICK(c, cudaMemcpy(hh.data(), c->d_hist, sizeof(double) * hneed, cudaMemcpyDeviceToHost));
+        for (int r = 0; r < R; ++r) {
+            auto &v = c->hist[(size_t)r];
+            const size_t old = v.size();
+            v.resize(old + (size_t)nrec * 2);
+            for (int64_t k = 0; k < nrec; ++k) {
+                v[old + (size_t)k * 2] = hh[((size_t)k * R + r) * 2];
+                v[old + (size_t)k * 2 + 1] = hh[((size_t)k * R + r) * 2 + 1];
+            }
+        }
+        c->records += nrec;
+        c->t += (uint32_t)nrec;
+        return VEGAS_OK;
+    } catch (...) {
+        return ising_host_exception(c);
     }
-    c->records += nrec;
-    c->t += (uint32_t)nrec;
-    return VEGAS_OK;
 }
 
 extern "C" vegas_status vegas_ising_history(const vegas_ising *cc, double *out, size_t capacity, size_t *n_written) {
-    vegas_ising *c = const_cast<vegas_ising *>(cc);
-    vegas_status st = ising_usable(c);
-    if (st != VEGAS_OK) return st;
-    const size_t need = (size_t)c->opt.replicas * (size_t)c->records * 2;
-    if (n_written) *n_written = need;
-    if (!out) return VEGAS_OK;
-    if (capacity < need) return ifail(c, VEGAS_EINVAL, "history buffer too small");
-    for (int r = 0; r < c->opt.replicas; ++r)
-        std::memcpy(out + (size_t)r * c->records * 2, c->hist[(size_t)r].data(), sizeof(double) * c->records * 2);
-    return VEGAS_OK;
+    try {
+        vegas_ising *c = const_cast<vegas_ising *>(cc);
+        vegas_status st = ising_usable(c);
+        if (st != VEGAS_OK) return st;
+        const size_t need = (size_t)c->opt.replicas * (size_t)c->records * 2;
+        if (n_written) *n_written = need;
+        if (!out) return VEGAS_OK;
+        if (capacity < need) return ifail(c, VEGAS_EINVAL, "history buffer too small");
+        for (int r = 0; r < c->opt.replicas; ++r)
+            std::memcpy(out + (size_t)r * c->records * 2, c->hist[(size_t)r].data(), sizeof(double) * c->records * 2);
+        return VEGAS_OK;
+    } catch (...) {
+        return ising_host_exception(const_cast<vegas_ising *>(cc));
+    }
 }
 
 namespace vegas {
@@ -550,40 +583,56 @@ vegas_status ising_spins_io(vegas_ising *c, int32_t replica, int8_t *out, const 
 }  // namespace vegas
 
 extern "C" vegas_status vegas_ising_get_spins(const vegas_ising *c, int32_t replica, int8_t *out) {
-    if (!out) return ifail(const_cast<vegas_ising *>(c), VEGAS_EINVAL, "out is NULL");
-    return ising_spins_io(const_cast<vegas_ising *>(c), replica, out, nullptr);
+    try {
+        if (!out) return ifail(const_cast<vegas_ising *>(c), VEGAS_EINVAL, "out is NULL");
+        return ising_spins_io(const_cast<vegas_ising *>(c), replica, out, nullptr);
+    } catch (...) {
+        return ising_host_exception(const_cast<vegas_ising *>(c));
+    }
 }
 
 extern "C" vegas_status vegas_ising_set_spins(vegas_ising *c, int32_t replica, const int8_t *in) {
-    if (!in) return ifail(c, VEGAS_EINVAL, "in is NULL");
-    return ising_spins_io(c, replica, nullptr, in);
+    try {
+        if (!in) return ifail(c, VEGAS_EINVAL, "in is NULL");
+        return ising_spins_io(c, replica, nullptr, in);
+    } catch (...) {
+        return ising_host_exception(c);
+    }
 }
 
 extern "C" vegas_status vegas_ising_set_mcs_counter(vegas_ising *c, uint32_t t) {
-    vegas_status st = ising_usable(c);
-    if (st != VEGAS_OK) return st;
-    if (t == UINT32_MAX) return ifail(c, VEGAS_EINVAL, "MCS counter must be below 2^32 - 1");
-    c->t = t;
-    return VEGAS_OK;
+    try {
+        vegas_status st = ising_usable(c);
+        if (st != VEGAS_OK) return st;
+        if (t == UINT32_MAX) return ifail(c, VEGAS_EINVAL, "MCS counter must be below 2^32 - 1");
+        c->t = t;
+        return VEGAS_OK;
+    } catch (...) {
+        return ising_host_exception(c);
+    }
 }
 
 extern "C" vegas_status vegas_ising_stats(const vegas_ising *c, vegas_stats_t *o) {
-    if (!c || !o) return VEGAS_EINVAL;
-    std::memset(o, 0, sizeof *o);
-    o->n_samples = 1;
-    o->n_instances = c->opt.replicas;
-    o->replicas = c->opt.replicas;
-    o->max_colours = 2;
-    o->n_sites = c->n;
-    o->n_edges = c->n * c->Z;
-    o->records = c->records;
-    o->mcs_done = c->t;
-    o->kernel_launches = c->kernel_launches;
-    o->sweep_launches = c->sweep_launches;
-    o->sweep_ms = c->sweep_ms;
-    o->last_run_ms = c->last_run_ms;
-    o->device_bytes = c->device_bytes;
-    return VEGAS_OK;
+    try {
+        if (!c || !o) return VEGAS_EINVAL;
+        std::memset(o, 0, sizeof *o);
+        o->n_samples = 1;
+        o->n_instances = c->opt.replicas;
+        o->replicas = c->opt.replicas;
+        o->max_colours = 2;
+        o->n_sites = c->n;
+        o->n_edges = c->n * c->Z;
+        o->records = c->records;
+        o->mcs_done = c->t;
+        o->kernel_launches = c->kernel_launches;
+        o->sweep_launches = c->sweep_launches;
+        o->sweep_ms = c->sweep_ms;
+        o->last_run_ms = c->last_run_ms;
+        o->device_bytes = c->device_bytes;
+        return VEGAS_OK;
+    } catch (...) {
+        return ising_host_exception(const_cast<vegas_ising *>(c));
+    }
 }
 
 extern "C" const char *vegas_ising_last_error(const vegas_ising *c) {

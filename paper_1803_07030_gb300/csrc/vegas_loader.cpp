@@ -64,30 +64,34 @@ std::vector<uint64_t> morton_keys(const double *pos, int32_t n) {
 }  // namespace vegas
 
 extern "C" int32_t vegas_greedy_colour(int32_t n, const int64_t *row_ptr, const int32_t *col, int32_t *color) {
-    if (n < 0 || (n > 0 && (!row_ptr || !color))) return -1;
-    if (n > 0 && row_ptr[0] != 0) return -1;
-    for (int32_t i = 0; i < n; ++i)
-        if (row_ptr[i + 1] < row_ptr[i]) return -1;
-    if (n > 0 && row_ptr[n] > 0 && !col) return -1;
-    std::vector<int32_t> seen;  // seen[c] == i  <=>  colour c is used by a coloured neighbour of i
-    int32_t nc = 0;
-    for (int32_t i = 0; i < n; ++i) color[i] = -1;
-    for (int32_t i = 0; i < n; ++i) {
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            const int32_t j = col[e];
-            if (j < 0 || j >= n) return -1;
-            const int32_t cj = color[j];
-            if (cj >= 0) {
-                if ((size_t)cj >= seen.size()) seen.resize((size_t)cj + 1, -1);
-                seen[(size_t)cj] = i;
+    try {
+        if (n < 0 || (n > 0 && (!row_ptr || !color))) return -1;
+        if (n > 0 && row_ptr[0] != 0) return -1;
+        for (int32_t i = 0; i < n; ++i)
+            if (row_ptr[i + 1] < row_ptr[i]) return -1;
+        if (n > 0 && row_ptr[n] > 0 && !col) return -1;
+        std::vector<int32_t> seen;  // seen[c] == i  <=>  colour c is used by a coloured neighbour of i
+        int32_t nc = 0;
+        for (int32_t i = 0; i < n; ++i) color[i] = -1;
+        for (int32_t i = 0; i < n; ++i) {
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                const int32_t j = col[e];
+                if (j < 0 || j >= n) return -1;
+                const int32_t cj = color[j];
+                if (cj >= 0) {
+                    if ((size_t)cj >= seen.size()) seen.resize((size_t)cj + 1, -1);
+                    seen[(size_t)cj] = i;
+                }
             }
+            int32_t c = 0;
+            while ((size_t)c < seen.size() && seen[(size_t)c] == i) ++c;
+            color[i] = c;
+            nc = std::max(nc, c + 1);
         }
-        int32_t c = 0;
-        while ((size_t)c < seen.size() && seen[(size_t)c] == i) ++c;
-        color[i] = c;
-        nc = std::max(nc, c + 1);
+        return nc;
+    } catch (...) {
+        return -1;  // a host exception never crosses the C boundary
     }
-    return nc;
 }
 
 namespace vegas {

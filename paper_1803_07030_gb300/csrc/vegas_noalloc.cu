@@ -87,6 +87,13 @@ vegas_status fail(vegas_status st, const std::string &m) {
     return st;
 }
 
+// A host exception caught at the entry point, as a status (called inside a catch block).
+vegas_status noalloc_host_exception() {
+    std::string m;
+    const vegas_status st = status_of_current_exception(m);
+    return fail(st, m);
+}
+
 }  // namespace
 
 extern "C" const char *vegas_noalloc_last_error(void) { return g_err.c_str(); }
@@ -96,120 +103,124 @@ extern "C" vegas_status vegas_sweep_noalloc(void *spins, const void *links, cons
                                             int32_t n_colours, int32_t replicas, const double *beta,
                                             const double *field, const double *site_params, uint64_t seed,
                                             int32_t inst0, uint32_t t, double *out, void *stream) {
-    if (!spins || !links || !row_ptr || !site_id || !colour_start || !beta || !field || !out)
-        return fail(VEGAS_EINVAL, "a required pointer is NULL");
-    if (n_sites < 1) return fail(VEGAS_EINVAL, "n_sites must be >= 1");
-    if (replicas < 1 || replicas > kNoAllocMaxReplicas || (replicas & (replicas - 1)))
-        return fail(VEGAS_EINVAL, "replicas must be a power of two no larger than 32 (the static scratch holds the "
-                                  "partial sums of at most 32 replicas)");
-    if (n_colours < 1 || n_colours > kMaxColours) return fail(VEGAS_EINVAL, "n_colours must be in [1, 64]");
-    if (colour_start[0] != 0 || colour_start[n_colours] != n_sites)
-        return fail(VEGAS_EINVAL, "colour_start must run from 0 to n_sites");
-    for (int c = 0; c < n_colours; ++c)
-        if (colour_start[c + 1] < colour_start[c]) return fail(VEGAS_EINVAL, "colour_start must not decrease");
-    for (int r = 0; r < replicas; ++r)
-        if (!(beta[r] > 0.0) || !std::isfinite(beta[r]) || !std::isfinite(field[r]))
-            return fail(VEGAS_EINVAL, "beta must be finite and > 0, field finite");
+    try {
+        if (!spins || !links || !row_ptr || !site_id || !colour_start || !beta || !field || !out)
+            return fail(VEGAS_EINVAL, "a required pointer is NULL");
+        if (n_sites < 1) return fail(VEGAS_EINVAL, "n_sites must be >= 1");
+        if (replicas < 1 || replicas > kNoAllocMaxReplicas || (replicas & (replicas - 1)))
+            return fail(VEGAS_EINVAL, "replicas must be a power of two no larger than 32 (the static scratch holds the "
+                                      "partial sums of at most 32 replicas)");
+        if (n_colours < 1 || n_colours > kMaxColours) return fail(VEGAS_EINVAL, "n_colours must be in [1, 64]");
+        if (colour_start[0] != 0 || colour_start[n_colours] != n_sites)
+            return fail(VEGAS_EINVAL, "colour_start must run from 0 to n_sites");
+        for (int c = 0; c < n_colours; ++c)
+            if (colour_start[c + 1] < colour_start[c]) return fail(VEGAS_EINVAL, "colour_start must not decrease");
+        for (int r = 0; r < replicas; ++r)
+            if (!(beta[r] > 0.0) || !std::isfinite(beta[r]) || !std::isfinite(field[r]))
+                return fail(VEGAS_EINVAL, "beta must be finite and > 0, field finite");
 
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(VEGAS_EINVAL, "device ordinal too large");
-    void *base = nullptr;
-    {
-        // first call on this device: resolve the device address of the static scratch
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
-            e = cudaGetSymbolAddress(&g_addr[dev], g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                g_addr[dev] = nullptr;
-                return fail(VEGAS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+        if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(VEGAS_EINVAL, "device ordinal too large");
+        void *base = nullptr;
+        {
+            // first call on this device: resolve the device address of the static scratch
+            std::lock_guard<std::mutex> lk(g_mu);
+            if (!g_addr[dev]) {
+                e = cudaGetSymbolAddress(&g_addr[dev], g_noalloc_scratch);
+                if (e != cudaSuccess) {
+                    g_addr[dev] = nullptr;
+                    return fail(VEGAS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+                }
             }
+            base = g_addr[dev];
         }
-        base = g_addr[dev];
-    }
-    NoAllocHeader *hdr = (NoAllocHeader *)base;
-    double *partial = (double *)((unsigned char *)base + kHeaderBytes);
+        NoAllocHeader *hdr = (NoAllocHeader *)base;
+        double *partial = (double *)((unsigned char *)base + kHeaderBytes);
 
-    int sm = 0;
-    e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
-    int log2R = 0;
-    while ((1 << log2R) < replicas) ++log2R;
+        int sm = 0;
+        e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+        int log2R = 0;
+        while ((1 << log2R) < replicas) ++log2R;
 
-    // uniform site parameters: (nx, ny, nz, s, ex, ey, ez, k, kc); default +z field axis, s = 1
-    double p[9] = {0.0, 0.0, 1.0, 1.0, 0.0, 0.0, 1.0, 0.0, 0.0};
-    if (site_params) std::memcpy(p, site_params, sizeof p);
-    for (double v : p)
-        if (!std::isfinite(v)) return fail(VEGAS_EINVAL, "non-finite site parameter");
-    if (!(p[3] > 0.0)) return fail(VEGAS_EINVAL, "spin norm must be > 0");
+        // uniform site parameters: (nx, ny, nz, s, ex, ey, ez, k, kc); default +z field axis, s = 1
+        double p[9] = {0.0, 0.0, 1.0, 1.0, 0.0, 0.0, 1.0, 0.0, 0.0};
+        if (site_params) std::memcpy(p, site_params, sizeof p);
+        for (double v : p)
+            if (!std::isfinite(v)) return fail(VEGAS_EINVAL, "non-finite site parameter");
+        if (!(p[3] > 0.0)) return fail(VEGAS_EINVAL, "spin norm must be > 0");
 
-    // one direct-kernel launch per colour class; their blocks share the scratch's slots
-    PassArgs a;
-    std::memset(&a, 0, sizeof a);
-    a.spins = spins;
-    a.edges = links;
-    a.row_ptr = row_ptr;
-    a.orig = site_id;
-    a.run = &hdr->run;
-    a.err = hdr->err;
-    a.seed = seed;
-    a.site_off = 0;
-    a.log2R = log2R;
-    a.inst0 = inst0;
-    a.inst_local0 = 0;
-    a.n_inst = replicas;
-    a.n_sample_sites = n_sites;
-    a.deg = 0;
-    a.depth = 0;
-    a.lower_mode = 2;
-    a.params_mode = (p[7] != 0.0 || p[8] != 0.0) ? 1 : 0;
-    a.u32 = SiteParams32{(float)p[0], (float)p[1], (float)p[2], (float)p[3], (float)p[4],
-                         (float)p[5], (float)p[6], (float)p[7], (float)p[8]};
-    a.u64 = SiteParams64{p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8]};
-    const int per_class = std::max(1, kNoAllocMaxBlocks / n_colours);
-    const int occ = sm * pass_blocks_per_sm(32, a);
-    int grids[kMaxColours];
-    int total = 0;
-    for (int c = 0; c < n_colours; ++c) {
-        const int64_t work = (int64_t)(colour_start[c + 1] - colour_start[c]) << log2R;
-        const int64_t need = (work + kThreads - 1) / kThreads;
-        grids[c] = (int)std::max<int64_t>(1, std::min<int64_t>({need, (int64_t)per_class, (int64_t)occ}));
-        total += grids[c];
-    }
-    if (total > kNoAllocMaxBlocks) return fail(VEGAS_EINVAL, "too many colour classes for the static scratch");
+        // one direct-kernel launch per colour class; their blocks share the scratch's slots
+        PassArgs a;
+        std::memset(&a, 0, sizeof a);
+        a.spins = spins;
+        a.edges = links;
+        a.row_ptr = row_ptr;
+        a.orig = site_id;
+        a.run = &hdr->run;
+        a.err = hdr->err;
+        a.seed = seed;
+        a.site_off = 0;
+        a.log2R = log2R;
+        a.inst0 = inst0;
+        a.inst_local0 = 0;
+        a.n_inst = replicas;
+        a.n_sample_sites = n_sites;
+        a.deg = 0;
+        a.depth = 0;
+        a.lower_mode = 2;
+        a.params_mode = (p[7] != 0.0 || p[8] != 0.0) ? 1 : 0;
+        a.u32 = SiteParams32{(float)p[0], (float)p[1], (float)p[2], (float)p[3], (float)p[4],
+                             (float)p[5], (float)p[6], (float)p[7], (float)p[8]};
+        a.u64 = SiteParams64{p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8]};
+        const int per_class = std::max(1, kNoAllocMaxBlocks / n_colours);
+        const int occ = sm * pass_blocks_per_sm(32, a);
+        int grids[kMaxColours];
+        int total = 0;
+        for (int c = 0; c < n_colours; ++c) {
+            const int64_t work = (int64_t)(colour_start[c + 1] - colour_start[c]) << log2R;
+            const int64_t need = (work + kThreads - 1) / kThreads;
+            grids[c] = (int)std::max<int64_t>(1, std::min<int64_t>({need, (int64_t)per_class, (int64_t)occ}));
+            total += grids[c];
+        }
+        if (total > kNoAllocMaxBlocks) return fail(VEGAS_EINVAL, "too many colour classes for the static scratch");
 
-    SetupArgs sa;
-    std::memset(&sa, 0, sizeof sa);
-    sa.h = hdr;
-    sa.out = out;
-    sa.t = t;
-    sa.R = replicas;
-    sa.blocks = total;
-    for (int r = 0; r < replicas; ++r) {
-        sa.beta[r] = beta[r];
-        sa.B[r] = field[r];
+        SetupArgs sa;
+        std::memset(&sa, 0, sizeof sa);
+        sa.h = hdr;
+        sa.out = out;
+        sa.t = t;
+        sa.R = replicas;
+        sa.blocks = total;
+        for (int r = 0; r < replicas; ++r) {
+            sa.beta[r] = beta[r];
+            sa.B[r] = field[r];
+        }
+        cudaStream_t st = (cudaStream_t)stream;
+        noalloc_setup<<<1, 32, 0, st>>>(sa);
+        int slot = 0;
+        for (int c = 0; c < n_colours; ++c) {  // an empty class runs one block that writes zeros
+            a.g_begin = colour_start[c];
+            a.g_end = colour_start[c + 1];
+            a.lower_end = colour_start[c];
+            a.partial = partial + (int64_t)slot * replicas * 4;
+            launch_pass32(a, grids[c], st);
+            slot += grids[c];
+        }
+        ReduceArgs ra{partial, hdr->slot_base, hdr->slot_count, &hdr->run, nullptr, replicas, replicas, 1, 0, nullptr, 0};
+        launch_reduce(ra, st);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("sweep: ") + cudaGetErrorString(e));
+        uint32_t err = 0;
+        e = cudaMemcpy(&err, hdr->err, sizeof err, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("error word: ") + cudaGetErrorString(e));
+        if (err) return fail(VEGAS_EDEVICE, "device error flags " + std::to_string(err) + " (1: NaN energy change)");
+        return VEGAS_OK;
+    } catch (...) {
+        return noalloc_host_exception();
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    noalloc_setup<<<1, 32, 0, st>>>(sa);
-    int slot = 0;
-    for (int c = 0; c < n_colours; ++c) {  // an empty class runs one block that writes zeros
-        a.g_begin = colour_start[c];
-        a.g_end = colour_start[c + 1];
-        a.lower_end = colour_start[c];
-        a.partial = partial + (int64_t)slot * replicas * 4;
-        launch_pass32(a, grids[c], st);
-        slot += grids[c];
-    }
-    ReduceArgs ra{partial, hdr->slot_base, hdr->slot_count, &hdr->run, nullptr, replicas, replicas, 1, 0, nullptr, 0};
-    launch_reduce(ra, st);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("sweep: ") + cudaGetErrorString(e));
-    uint32_t err = 0;
-    e = cudaMemcpy(&err, hdr->err, sizeof err, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("error word: ") + cudaGetErrorString(e));
-    if (err) return fail(VEGAS_EDEVICE, "device error flags " + std::to_string(err) + " (1: NaN energy change)");
-    return VEGAS_OK;
 }

@@ -10,6 +10,8 @@ call then stops at the device query). The exported greedy colouring gets the sam
 """
 
 import ctypes as C
+import subprocess
+import sys
 import zlib
 
 import numpy as np
@@ -17,6 +19,7 @@ import pytest
 
 import paper_1803_07030_gb300 as vg
 from paper_1803_07030_gb300 import vegas as vb
+from conftest import ROOT
 from lattices import fcc_sphere, random_graph, sc_periodic, triangles
 
 MAKERS = [lambda: sc_periodic(4, k_uni=0.1), lambda: random_graph(40, 0.12, 5), lambda: fcc_sphere(3.0),
@@ -197,3 +200,29 @@ def test_greedy_colour_refuses_bad_csr(lib):
     assert call(-1, rp, col, out) == -1
     assert lib.vegas_greedy_colour(s.n_sites, vb._ptr(rp), None, vb._ptr(out)) == -1
     assert call(0, np.zeros(1, np.int64), col, out) == 0
+
+
+CHILD = """
+import ctypes as C, resource, sys
+sys.path.insert(0, {root!r})
+resource.setrlimit(resource.RLIMIT_AS, (2 << 30, 2 << 30))
+from paper_1803_07030_gb300 import vegas as vb
+from lattices import sc_periodic
+lib = vb.load_library()
+keep = vb._SampleArrays(sc_periodic(4))
+arr = (vb.vegas_sample * 1)(keep.c)
+out = C.c_void_p(1)
+st = lib.vegas_create(arr, 2 ** 31 - 1, None, C.byref(out))
+print(st, out.value is None, lib.vegas_last_error(None).decode())
+"""
+
+
+def test_failed_host_allocation_is_a_status_not_an_abort(lib):
+    """A host allocation that fails inside an entry point (here the per-sample table of
+    2^31 - 1 samples, in a process limited to 2 GB of address space) comes back as
+    VEGAS_ENOMEM with *out = NULL instead of an exception through the C boundary."""
+    r = subprocess.run([sys.executable, "-c", CHILD.format(root=ROOT)], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    st, null_out, msg = r.stdout.split(maxsplit=2)
+    assert int(st) == vb.ENOMEM and null_out == "True" and "allocation" in msg
