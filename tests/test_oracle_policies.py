@@ -15,7 +15,9 @@
                    cubic quadratures, dimer bond-angle histogram (chi^2)
   adaptive         the acceptance rate settles at 1/2; the width follows the control law
                    from the recorded acceptance counts and stays frozen after the first
-                   fifth of the step; the frozen part samples the Langevin law
+                   fifth of the step; the frozen part samples the Langevin law; in the
+                   ordered phase its energy decorrelates several times faster than under
+                   uniform trials (the efficiency the paper reports for it, Sec. IV.C)
   table            an all-random table gives the caller bit-identical chains; per-type
                    policies apply per site type
 """
@@ -29,7 +31,8 @@ from scipy import integrate, special, stats
 from conftest import binned
 
 import oracle
-from lattices import chain_open, core_shell_particle, dimers, free_spins
+from lattices import chain_open, core_shell_particle, dimers, free_spins, sc_periodic
+from oracle.analysis import tau_int
 
 from test_oracle_pins import langevin, sphere_grid
 
@@ -250,6 +253,24 @@ def test_adaptive_acceptance_and_control_law():
     # random policy at the same temperature: acceptance far below 1/2
     r0 = oracle.run(free_spins(n), [[T]], [[B]], 20, seed=21, spins=up)
     assert r0["accepted"][0].mean() / n < 0.25
+
+
+def test_adaptive_policy_shortens_the_energy_autocorrelation():
+    """6^3 ferromagnet at T = 0.3 (ordered; T_c is about 1.44), four replicas started aligned:
+    uniform trials are accepted about 5% of the time and the energy's integrated
+    autocorrelation time is tens of MCS; the adaptive width holds the acceptance near 1/2 and
+    the time falls by more than half (Sec. IV.C: the adaptive policy is the efficient one)."""
+    R, mcs, cut = 4, 4000, 800
+    up = np.tile([0.0, 0.0, 1.0], (R, 216, 1))
+    out = {}
+    for name, pol, par in (("random", oracle.RANDOM, 0.0), ("adaptive", oracle.ADAPTIVE, 0.5)):
+        s = sc_periodic(6).with_policy([pol], [par])
+        r = oracle.run(s, np.full((R, 1), 0.3), np.zeros((R, 1)), mcs, seed=31, spins=up, n_threads=R)
+        taus = [tau_int(e) for e in r["history"][:, cut:, 0]]
+        out[name] = (float(np.mean(taus)), r["accepted"][:, cut:].mean() / s.n_sites)
+    (tau_r, acc_r), (tau_a, acc_a) = out["random"], out["adaptive"]
+    assert acc_r < 0.1 and abs(acc_a - 0.5) < 0.05, out
+    assert tau_a < 0.5 * tau_r, out
 
 
 def test_adaptive_width_frozen_then_continued():
