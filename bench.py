@@ -126,11 +126,16 @@ def slowest_rank_ms(ms: float, world: int, device=None) -> float:
 
 
 def peaks():
+    """Measured HBM copy bandwidth (GB/s) of this GPU model if the file has it, else the
+    fallback figure."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
+    try:
         with open(p) as f:
-            d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+            v = float(json.load(f).get("hbm_gbs", 0.0))
+        if v > 0.0:
+            return v, "measured"
+    except (OSError, ValueError, TypeError, AttributeError):
+        pass
     return 6800.0, "fallback"
 
 

@@ -215,3 +215,14 @@ def test_reference_arm_on_a_secondary_workload(fake_device, capsys):
     assert ref["metric"] == ours["metric"] and ref["unit"] == ours["unit"]
     assert ref["config"] == ours["config"] and ref["scaling"] == ours["scaling"]
     assert ref["e2e"]["h2d_bytes_per_step"] == 0 and ref["cpu_baseline"]["value"] == ref["value"]
+
+
+def test_peak_falls_back_without_a_usable_measurement(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"bf16_tflops": 1900}')
+    assert bench.peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text("not json")
+    assert bench.peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6788.6}')
+    assert bench.peaks() == (6788.6, "measured")
