@@ -188,7 +188,11 @@ class ClockSampler:
     def __exit__(self, *exc):
         if self.proc:
             self.proc.terminate()
-            self.proc.wait(timeout=10)
+            try:
+                self.proc.wait(timeout=10)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()  # the sampler this object started, by its own handle
+                self.proc.wait()
             self.f.close()
         return False
 
