@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import shutil
 import statistics
 import subprocess
 import sys
@@ -176,13 +177,20 @@ class ClockSampler:
         self.path = os.path.join("/tmp", f"vegas_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
+        self.f = None
+        self.proc = None
+        if shutil.which("nvidia-smi") is None:  # no sampler: the line says the clocks are unknown
+            return self
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
+        except OSError:  # no nvidia-smi (or no temporary file): the line says the clocks are unknown
             self.proc = None
+            if self.f:
+                self.f.close()
+                os.remove(self.path)
         return self
 
     def __exit__(self, *exc):
