@@ -12,6 +12,13 @@ With N > 1 (launched by torchrun) every rank sweeps its own 32 replicas (instanc
 ranks divided by the slowest rank's time. `--impl reference` times the CPU FP64 oracle on
 this host's cores on a bounded sample of the same workload (one MCS of one replica per
 core per step).
+
+Other lines: `--workload NAME` times one run of a secondary workload's schedule (the 8^3 FP64
+ferromagnet, the 64^3 hysteresis loop, the core/shell particle, the 256 nanoparticles; under
+torchrun the nanoparticles are split over the ranks), with `--impl reference` the oracle on a
+bounded sample of it; `--policy`, `--variant`, `--type-stats`, `--snapshots` select the path;
+`--analysis` and `--ising` time the history analysis and the Ising model; `--quick` times the
+sweep alone (profiling runs).
 """
 
 from __future__ import annotations
