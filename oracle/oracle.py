@@ -178,6 +178,8 @@ class _Bound:
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:
+    """One Philox4x32-10 block (Salmon et al., SC'11) of a 4-word counter and 2-word key: the
+    generator every random number of the chain comes from."""
     c = np.ascontiguousarray(ctr, dtype=np.uint32)
     k = np.ascontiguousarray(key, dtype=np.uint32)
     o = np.zeros(4, dtype=np.uint32)
@@ -186,17 +188,21 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 
 def sphere(seed: int, c0: int, c1: int, c2: int, purpose: int):
-    """Returns (unit vector, candidates used)."""
+    """Marsaglia (1972) point on the unit sphere from Philox candidates (purpose | k): the trial
+    of the random policy (Sec. III.B). Returns (unit vector, candidates used)."""
     o = np.zeros(3)
     k = _load().vo_sphere(seed, c0, c1, c2, purpose, _ptr(o))
     return o, k
 
 
 def uniform(seed: int, c0: int, c1: int, c2: int, c3: int) -> float:
+    """53-bit uniform in [0, 1) from one Philox block: the acceptance draw of Eq. 4."""
     return _load().vo_uniform(seed, c0, c1, c2, c3)
 
 
 def greedy_colour(sample):
+    """Greedy colouring in site order (smallest colour no coloured neighbour has): the colour
+    classes of the sweep. Returns (colours, number of colours)."""
     n = sample.n_sites
     rp = np.ascontiguousarray(sample.row_ptr, dtype=np.int64)
     cl = np.ascontiguousarray(sample.col, dtype=np.int32)
@@ -206,12 +212,14 @@ def greedy_colour(sample):
 
 
 def energy(sample, S, B: float) -> float:
+    """Total energy of Eq. 1-3 (each bond once) of spins S [n, 3] in field B."""
     b = _Bound(sample)
     S = np.ascontiguousarray(S, dtype=np.float64).reshape(sample.n_sites, 3)
     return _load().vo_energy(b.ref, _ptr(S), float(B))
 
 
 def magnetisation(S) -> np.ndarray:
+    """M = sum_i S_i, the magnetization of the history (Sec. II)."""
     S = np.ascontiguousarray(S, dtype=np.float64).reshape(-1, 3)
     o = np.zeros(3)
     _load().vo_magnetisation(S.shape[0], _ptr(S), _ptr(o))
@@ -219,6 +227,7 @@ def magnetisation(S) -> np.ndarray:
 
 
 def delta_e(sample, S, i: int, trial, B: float) -> float:
+    """Energy change (Eq. 1-3) of replacing S_i by `trial`, in the oracle's fixed order."""
     b = _Bound(sample)
     S = np.ascontiguousarray(S, dtype=np.float64).reshape(sample.n_sites, 3)
     t = np.ascontiguousarray(trial, dtype=np.float64)
@@ -226,6 +235,7 @@ def delta_e(sample, S, i: int, trial, B: float) -> float:
 
 
 def renormalise(sample, S) -> np.ndarray:
+    """S_i <- s_i S_i / |S_i| (once per temperature/field step); qIsing sites keep their length."""
     b = _Bound(sample)
     S = np.array(S, dtype=np.float64).reshape(sample.n_sites, 3)
     _load().vo_renormalise(b.ref, _ptr(S))
@@ -233,6 +243,7 @@ def renormalise(sample, S) -> np.ndarray:
 
 
 def init_spins(sample, seed: int, inst: int) -> np.ndarray:
+    """Initial state of one instance: s_i times a Philox sphere point per site (Sec. III.B)."""
     b = _Bound(sample)
     S = np.zeros((sample.n_sites, 3))
     err = _load().vo_init_spins(b.ref, seed, inst, _ptr(S))
@@ -247,6 +258,7 @@ def log(x: float) -> float:
 
 
 def cap_height(theta: float) -> float:
+    """h = 1 - cos(theta) of the small-step policy's cap (Sec. II)."""
     return _load().vo_cap_height(float(theta))
 
 
