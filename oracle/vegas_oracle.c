@@ -153,6 +153,7 @@ int vo_sphere(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t pur
     return -1;
 }
 
+/* Uniform in [0, 1) from one Philox block (the acceptance draw of Eq. 4). */
 double vo_uniform(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
     uint32_t w[4];
     philox(seed, c0, c1, c2, c3, w);
@@ -200,6 +201,7 @@ static int normal_pair(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uin
     return 0;
 }
 
+/* u = v / |v|. */
 static void unit_of(const double v[3], double u[3]) {
     const double q = sqrt((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
     u[0] = v[0] / q;
@@ -285,8 +287,10 @@ int32_t vo_greedy_colour(int32_t n, const int64_t *row_ptr, const int32_t *col, 
 
 /* ---------------------------------------------------------------- energy */
 
+/* Spin norm s_i of the material file (Sec. III.C); 1 when not given. */
 static double norm_of(const vo_sample *s, int32_t i) { return s->spin_norm ? s->spin_norm[i] : 1.0; }
 
+/* Per-site axis (field axis n_i or anisotropy axis e_i); +z when not given. */
 static void axis_of(const double *a, int32_t i, double v[3]) {
     if (a) {
         v[0] = a[3 * (int64_t)i];
@@ -299,6 +303,7 @@ static void axis_of(const double *a, int32_t i, double v[3]) {
     }
 }
 
+/* Cubic anisotropy form of Eq. 3: x^2 y^2 + y^2 z^2 + x^2 z^2 of the spin's components. */
 static double cubic_form(const double v[3]) {
     const double xx = v[0] * v[0], yy = v[1] * v[1], zz = v[2] * v[2];
     return (xx * yy + yy * zz) + xx * zz;
@@ -322,12 +327,14 @@ static double site_energy(const vo_sample *s, const double *S, int32_t i, double
     return -0.5 * ex - B * zee - k * (pe * pe) - kc * cubic_form(Si);
 }
 
+/* Total energy (Eq. 1-3): the sum of the site energies, so every bond counts once. */
 double vo_energy(const vo_sample *s, const double *S, double B) {
     double E = 0.0;
     for (int32_t i = 0; i < s->n; ++i) E += site_energy(s, S, i, B);
     return E;
 }
 
+/* M = sum_i S_i, the magnetization recorded after every MCS (Sec. II). */
 void vo_magnetisation(int32_t n, const double *S, double M[3]) {
     M[0] = M[1] = M[2] = 0.0;
     for (int32_t i = 0; i < n; ++i) {
