@@ -624,6 +624,19 @@ class IsingContext:
         """Global MCS counter of the next MCS (keys its random numbers)."""
         self._check(load_library().vegas_ising_set_mcs_counter(self.ptr, int(t)))
 
+    def checkpoint(self) -> dict:
+        """Every replica's spins and the MCS counter: what a new context with the same options
+        needs to continue the chains bit for bit."""
+        return {"spins": [self.spins(r) for r in range(self.replicas)], "mcs": self.stats()["mcs_done"]}
+
+    def restore(self, state: dict) -> None:
+        """Load a checkpoint() of a context with the same options."""
+        if len(state["spins"]) != self.replicas:
+            raise ValueError("checkpoint has a different number of replicas")
+        for r, x in enumerate(state["spins"]):
+            self.set_spins(r, x)
+        self.set_mcs_counter(state["mcs"])
+
     def stats(self) -> dict:
         s = vegas_stats_t()
         self._check(load_library().vegas_ising_stats(self.ptr, C.byref(s)))
