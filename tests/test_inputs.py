@@ -70,3 +70,48 @@ def test_workload_shapes(name, n_inst, n_sites, steps, mcs, precision):
         B = w.B[0]
         assert B[0] == pytest.approx(2.0) and B[80] == pytest.approx(-2.0) and B[-1] == pytest.approx(2.0)
         assert np.allclose(np.abs(np.diff(B)), 0.05)
+
+
+def test_core_shell_recipe():
+    """Types by distance from the centre, exchange by the endpoint types, radial uniaxial
+    anisotropy on the surface sites (fewer than 12 links) only."""
+    s = core_shell_particle(seed=4, radius=6.0, core_radius=4.0)
+    centre_dist = np.linalg.norm(s.positions - s.positions.mean(axis=0), axis=1)
+    t = np.asarray(s.type)
+    assert set(np.unique(t).tolist()) == {0, 1}
+    assert centre_dist[t == 0].max() < centre_dist[t == 1].max()
+    src = _sources(s)
+    pair = {(0, 0): 1.0, (1, 1): 0.5, (0, 1): -0.3, (1, 0): -0.3}
+    assert all(J == pair[(int(t[i]), int(t[j]))] for i, j, J in zip(src, s.col, s.J))
+    _assert_symmetric(s)
+    deg = np.diff(s.row_ptr)
+    surf = deg < 12
+    assert surf.any() and (~surf).any() and deg.max() == 12
+    assert np.all(np.asarray(s.k_uni)[surf] == 0.5) and np.all(np.asarray(s.k_uni)[~surf] == 0.0)
+    e = np.asarray(s.e_uni)[surf]
+    assert np.allclose(np.linalg.norm(e, axis=1), 1.0)
+    r = s.positions[surf] - s.positions.mean(axis=0)
+    assert np.mean(np.sum(e * r, axis=1) / np.linalg.norm(r, axis=1)) > 0.95  # about radial
+
+
+def test_nanoparticle_batch_recipe():
+    """One site per unit volume (cube side 4^(1/3)): a radius-r particle holds about
+    (4/3) pi r^3 sites; radii between 3 and 15; temperatures 0.05 + (p mod 64) 2.95/63."""
+    w = workload("np256", mcs=1)
+    sizes = np.array([s.n_sites for s in w.samples])
+    radii = np.array([float(s.name.split("_r")[1]) for s in w.samples])
+    assert radii.min() >= 3.0 and radii.max() <= 15.0
+    ratio = sizes / (4.0 / 3.0 * np.pi * radii ** 3)
+    assert np.all(np.abs(ratio - 1.0) < 0.25) and abs(np.median(ratio) - 1.0) < 0.05
+    p = np.arange(256)
+    assert np.allclose(w.T[:, 0], 0.05 + (p % 64) * 2.95 / 63.0) and np.all(w.B == 0.0)
+
+
+def test_spin_glass_bonds_are_bimodal_and_shared():
+    """The +-J glass: J = +-1 per undirected bond, about half each, one realisation for every
+    replica (the workload has one sample)."""
+    w = workload("sg256x32", scale=1 / 16)
+    assert len(w.samples) == 1 and w.replicas == 32
+    J = np.asarray(w.samples[0].J)
+    assert set(np.unique(J).tolist()) == {-1.0, 1.0} and abs(np.mean(J)) < 0.05
+    _assert_symmetric(w.samples[0])
