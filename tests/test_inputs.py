@@ -115,3 +115,5 @@ def test_spin_glass_bonds_are_bimodal_and_shared():
     J = np.asarray(w.samples[0].J)
     assert set(np.unique(J).tolist()) == {-1.0, 1.0} and abs(np.mean(J)) < 0.05
     _assert_symmetric(w.samples[0])
+    k = np.arange(32)
+    assert np.allclose(w.T[:, 0], 0.1 * 20.0 ** (k / 31.0)) and np.all(w.B == 0.0)  # 0.1 -> 2.0, geometric
