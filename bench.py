@@ -371,6 +371,10 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    if args.analysis or args.ising:
+        print(json.dumps({"impl": "reference", "unavailable": "the analysis and Ising lines time the oracle "
+                          "themselves (their cpu_baseline); there is no separate reference arm for them"}), flush=True)
+        return 0
     if args.workload != "sg256x32":
         return run_reference_workload(args)
     from lattices import sc_periodic

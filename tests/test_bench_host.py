@@ -226,3 +226,10 @@ def test_peak_falls_back_without_a_usable_measurement(tmp_path, monkeypatch):
     assert bench.peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6788.6}')
     assert bench.peaks() == (6788.6, "measured")
+
+
+def test_reference_arm_is_not_silently_the_headline_for_other_lines(capsys):
+    for kw in ({"analysis": True}, {"ising": True}):
+        bench.run_reference(args(impl="reference", **kw))
+        line = last_json(capsys)
+        assert line["impl"] == "reference" and "unavailable" in line and "value" not in line
