@@ -245,6 +245,33 @@ def cpu_baseline_run(sample, n_threads, mcs=1):
     return n_threads * sample.n_sites * mcs / dt, dt
 
 
+PRECISION_BOUND = 1e-3  # |d(E/N)| the FP32 path must stay below (per result)
+
+
+def precision_statement(ctx, samples, replicas, B_last, instances) -> dict:
+    """The deterministic precision figure of a result, taken in the oracle leg after the timed
+    region: for a few instances, the last history record's E/N (FP32 spins, FP64 sums) against
+    the oracle's FP64 energy (Eq. 1-3) of the same instance's final spins (read with
+    vegas_get_spins). The spins are read after the step's FP64 renormalisation, which moves
+    each spin by at most a few FP32 ulps, so the figure also bounds what the renormalisation
+    changes. B_last: the field of the last step, per instance."""
+    import oracle
+
+    H = ctx.history()
+    worst, rows = 0.0, []
+    for i in instances:
+        smp = samples[i // replicas]
+        S = ctx.spins(i)
+        e_ref = oracle.energy(smp, S, float(B_last[i]))
+        d = abs(float(H[i, -1, 0]) - e_ref) / smp.n_sites
+        worst = max(worst, d)
+        rows.append({"instance": int(i), "sites": int(smp.n_sites), "e_per_site": e_ref / smp.n_sites,
+                     "d_e_per_site": d})
+    return {"d_e_per_site": worst, "bound": PRECISION_BOUND, "ok": bool(worst < PRECISION_BOUND),
+            "method": "last history record's E/N against the oracle's FP64 energy of the same final spins",
+            "checked": rows}
+
+
 POLICY_CODES = {"random": 0, "flip": 1, "small": 2, "gauss": 3, "hn": 4, "adaptive": 5}
 POLICY_DEFAULT_PARAM = {"random": 0.0, "flip": 0.0, "small": 0.5, "gauss": 0.4, "hn": 0.5, "adaptive": 1.0}
 
@@ -489,6 +516,10 @@ def run_ours(args):
     h2d = T.size * 2 * 8 + 40
     d2h = REPLICAS * mcs * 4 * 8 + 4
 
+    # the oracle leg (rank 0, after every timed region of this context): precision statement
+    precision = precision_statement(ctx, [s], REPLICAS, B[:, -1], (0, REPLICAS // 2, REPLICAS - 1)) \
+        if rank == 0 else None
+
     # plain single-instance path on the same lattice: one replica per context, R = 1
     ctx.close()
     torch.cuda.synchronize()
@@ -515,8 +546,14 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_desc(mcs),
+            "precision": precision,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "frac_basis": "sweep kernel: algorithmic bytes of one launch / its mean CUDA-event time",
+                         "headline_achieved": BYTES_PER_ATTEMPT * value / world / 1e9,
+                         "headline_frac": BYTES_PER_ATTEMPT * value / world / 1e9 / peak,
+                         "headline_basis": "whole step: algorithmic bytes per attempt x attempts/s per GPU "
+                                           "(every launch of the step, reductions and renormalisation included)",
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback 6.8 TB/s",
                          "kernel": kname, "bytes_per_attempt": BYTES_PER_ATTEMPT,
@@ -593,6 +630,14 @@ def run_workload(args):
         barrier()
     ms = slowest_rank_ms(a.elapsed_time(b), world, device="cuda")
     st1 = ctx.stats() if ctx is not None else None
+    precision = None
+    if rank == 0 and ctx is not None and not args.quick:
+        # the oracle leg, after the timed region: the first instance, the largest sample's
+        # first replica and the last instance
+        R = w.replicas
+        big = int(np.argmax([smp.n_sites for smp in share["samples"]]))
+        insts = sorted({0, big * R, len(share["samples"]) * R - 1})
+        precision = precision_statement(ctx, share["samples"], R, np.asarray(share["B"])[:, -1], insts)
     mine = float(st1["kernel_launches"] - st0["kernel_launches"]) if ctx is not None else 0.0
     launches = sum_over_ranks(mine, world, device="cuda")
     value = share["job_attempts"] * args.steps / (ms / 1000.0)
@@ -608,6 +653,7 @@ def run_workload(args):
             "data": "synthetic",
             "config": workload_config(w, args, policy, share["job_attempts"]),
             **shape,
+            "precision": precision,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }

@@ -444,26 +444,37 @@ int32_t vegas_greedy_colour(int32_t n_sites, const int64_t *row_ptr, const int32
  * [colour_start[c], colour_start[c+1]); no link joins two sites of one class.
  *   spins     device, [n_sites][replicas] x (x, y, z, unused) float32, 16-byte aligned;
  *             updated in place
- *   links     device, [n_edges] x (neighbour index as int32, J as float32 bits), every
- *             link present in both directions with equal J
- *   row_ptr   device, [n_sites + 1] int64 link offsets
- *   site_id   device, [n_sites] int32 ids used as Philox keys (the caller's numbering)
+ *   links     device, 8-byte aligned, [n_edges] x (neighbour index as int32, J as float32
+ *             bits), every link present in both directions with equal J; every neighbour
+ *             index in [0, n_sites)
+ *   row_ptr   device, 8-byte aligned, [n_sites + 1] int64 link offsets: row_ptr[0] == 0,
+ *             non-decreasing, row_ptr[n_sites] == n_edges (the links array's length)
+ *   site_id   device, 4-byte aligned, [n_sites] int32 ids used as Philox keys (the caller's
+ *             numbering)
  *   colour_start  host, [n_colours + 1], from 0 to n_sites, n_colours <= 64
  *   replicas  1, 2, 4, ..., 32 (larger values are rejected: the scratch holds 32)
  *   beta, field   host, [replicas]: 1/T > 0 and B of each replica
  *   site_params   host, 9 doubles (nx, ny, nz, s, ex, ey, ez, k, kc) shared by all
  *             sites, or NULL (field axis +z, s = 1, no anisotropy)
  *   seed, inst0, t  Philox key, instance id of replica 0, global MCS index
- *   out       device, [replicas][4] doubles: (E, Mx, My, Mz) after the MCS
+ *   out       device, 8-byte aligned, [replicas][4] doubles: (E, Mx, My, Mz) after the MCS
  *   stream    cudaStream_t or NULL (legacy default stream)
+ * The device arrays are not validated (the library cannot read them without copies):
+ * neighbour indices outside [0, n_sites) or row offsets past the links array are undefined
+ * behaviour. A debug build of the library (build(debug=True)) checks every row and
+ * neighbour index in the kernel and reports a bad one as VEGAS_EDEVICE (flag 4) instead of
+ * reading through it.
  * Computes what vegas_run computes for one MCS of an FP32 context with these replicas
  * (same random numbers for the same seed, ids, instances and t); no renormalisation.
- * Blocking: returns after the sweep finished on the stream. The first call on a device
- * looks up the device address of the static scratch (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture. Every call uses the
- * same scratch and rewrites it; calls whose GPU work overlaps (other threads, other
- * streams) race on it. Errors: VEGAS_EINVAL for bad sizes or pointers (message from
- * vegas_noalloc_last_error), VEGAS_ECUDA, VEGAS_EDEVICE (NaN energy change).
+ * Set-up: the first call on a device (and the first after that device's context has been
+ * replaced, e.g. by cudaDeviceReset) looks up the device address of the static scratch
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture begins. Blocking: every call waits for the sweep to finish on `stream` and reads
+ * the error word back with a blocking copy before it returns. Every call uses the same
+ * scratch and rewrites it; calls whose GPU work overlaps (other threads, other streams)
+ * race on it. Errors: VEGAS_EINVAL for bad sizes, NULL or misaligned pointers (message from
+ * vegas_noalloc_last_error), VEGAS_ECUDA, VEGAS_EDEVICE (1: NaN energy change; 4: a bad
+ * index seen by a debug build).
  */
 vegas_status vegas_sweep_noalloc(void *spins, const void *links, const int64_t *row_ptr, const int32_t *site_id,
                                  int32_t n_sites, const int32_t *colour_start, int32_t n_colours, int32_t replicas,

@@ -2,6 +2,7 @@
 // the schedule driver (one CUDA graph per MCS, replayed), history and spin I/O.
 // See include/vegas.h for the contract of every entry point.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -18,6 +19,15 @@ using namespace vegas;
 namespace {
 
 thread_local std::string g_create_error;
+
+// An NVTX range for the lifetime of the object (tracing: a profiler shows every vegas_run
+// and every temperature/field step it enqueues; without a profiler attached NVTX does nothing).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct SampleInfo {
     int32_t n = 0, n_colours = 0, uniform_degree = 0;
@@ -1192,6 +1202,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                 sched[((size_t)s * NI + i) * 2 + 1] = Bi;
             }
         if ((st = set_device(c)) != VEGAS_OK) return st;
+        NvtxRange run_range("vegas_run");
         const int64_t nrec = (int64_t)n_steps * mcs;
         if (sched.size() > c->sched_cap) {
             if (c->d_sched) {
@@ -1340,6 +1351,11 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             return stream_mcs(m0, n);
         };
         for (int32_t s = 0; s < n_steps; ++s) {
+            // one range per step; when the rest of the schedule goes out as one run graph, this
+            // step's range covers that launch
+            char step_name[48];
+            std::snprintf(step_name, sizeof step_name, "vegas_run step %d/%d", (int)s + 1, (int)n_steps);
+            NvtxRange step_range(step_name);
             int32_t m0 = 0;
             if (!c->tuned && mcs >= 2) {
                 // autotune: time a few MCS of each eligible sweep and block shape on the real chain

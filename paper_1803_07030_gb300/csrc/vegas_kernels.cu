@@ -365,6 +365,40 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
     return ok;
 }
 
+#ifdef VEGAS_DEBUG_CHECKS
+// Debug builds: the row of site g and every neighbour index in it, and the caller id, are
+// checked before the attempt reads through them; a bad one sets kErrIndex, records a code
+// and the value, and the attempt is skipped. n_edges_total == 0 means the link count is not
+// known (the allocation-free entry point): rows are then checked for order only.
+__device__ bool direct_row_ok(const PassArgs &a, int g, uint32_t orig) {
+    uint32_t code = 0;
+    int64_t val = 0;
+    const int64_t e0 = a.row_ptr[g], e1 = a.row_ptr[g + 1];
+    if (orig >= (uint32_t)a.n_sample_sites) {
+        code = 31;
+        val = orig;
+    } else if (e0 < 0 || e1 < e0 || (a.n_edges_total > 0 && e1 > a.n_edges_total)) {
+        code = 32;
+        val = g;
+    } else {
+        const int2 *E = (const int2 *)a.edges;
+        for (int64_t e = e0; e < e1; ++e) {
+            const int j = E[e].x;
+            if (j < 0 || j >= a.n_sites_total) {
+                code = 33;
+                val = j;
+                break;
+            }
+        }
+    }
+    if (code == 0) return true;
+    atomicOr(a.err, kErrIndex);
+    atomicCAS(a.err + 1, 0u, code);
+    a.err[2] = (uint32_t)val;
+    return false;
+}
+#endif
+
 // ------------------------------------------------------------------ FP32 colour pass (direct)
 // Any row length: reads row_ptr and gathers neighbours with plain loads.
 // PM: params_mode (0 uniform without anisotropy, 1 uniform, 2 per site).
@@ -391,6 +425,9 @@ __global__ void __launch_bounds__(kThreads, 2) pass32_kernel(const PassArgs a) {
     for (int64_t w = w0; w < n_work; w += stride) {
         const int g = a.g_begin + (int)(w >> a.log2R);
         const uint32_t orig = (uint32_t)__ldg(a.orig + g);
+#ifdef VEGAS_DEBUG_CHECKS
+        if (!direct_row_ok(a, g, orig)) continue;
+#endif
         bool nan_seen = false;
         float4 Sq;
         const bool ok = direct_attempt<PM, LM, POL>(S, E, a.row_ptr, g, r, R, a.lower_end, orig, site_params32(a, PM, g),

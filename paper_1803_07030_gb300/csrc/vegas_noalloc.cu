@@ -9,6 +9,7 @@
 // spins, links and caller ids as device pointers and keeps the only scratch it needs (the
 // per-block partial sums of energy and magnetization, the run state and the error word)
 // in one statically allocated device array of this file.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -78,9 +79,46 @@ __global__ void noalloc_setup(const SetupArgs s) {
     }
 }
 
+// Device address of the scratch, looked up once per CUDA context. The address belongs to the
+// context that loaded this module, not to the device ordinal: after the device's primary
+// context is reset (cudaDeviceReset) the module is loaded again and the array may sit
+// elsewhere, so the cache is keyed by the context's process-unique id (cuCtxGetId).
+struct ScratchSlot {
+    unsigned long long ctx_id;  // 0: not looked up yet
+    void *addr;
+};
 std::mutex g_mu;
-void *g_addr[kNoAllocMaxDevices] = {};
+ScratchSlot g_slot[kNoAllocMaxDevices] = {};
 thread_local std::string g_err;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// The unique id of the calling thread's current context, or 0 when there is none yet or the
+// driver does not offer the query (the scratch address is then looked up on every call).
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 vegas_status fail(vegas_status st, const std::string &m) {
     g_err = m;
@@ -106,6 +144,12 @@ extern "C" vegas_status vegas_sweep_noalloc(void *spins, const void *links, cons
     try {
         if (!spins || !links || !row_ptr || !site_id || !colour_start || !beta || !field || !out)
             return fail(VEGAS_EINVAL, "a required pointer is NULL");
+        // the kernels load spins as float4, links, row offsets and sums as 8-byte words: a
+        // misaligned device pointer would fault the GPU, so it is refused here
+        if ((uintptr_t)spins % 16 != 0) return fail(VEGAS_EINVAL, "spins must be 16-byte aligned");
+        if ((uintptr_t)links % 8 != 0 || (uintptr_t)row_ptr % 8 != 0 || (uintptr_t)out % 8 != 0)
+            return fail(VEGAS_EINVAL, "links, row_ptr and out must be 8-byte aligned");
+        if ((uintptr_t)site_id % 4 != 0) return fail(VEGAS_EINVAL, "site_id must be 4-byte aligned");
         if (n_sites < 1) return fail(VEGAS_EINVAL, "n_sites must be >= 1");
         if (replicas < 1 || replicas > kNoAllocMaxReplicas || (replicas & (replicas - 1)))
             return fail(VEGAS_EINVAL, "replicas must be a power of two no larger than 32 (the static scratch holds the "
@@ -125,16 +169,22 @@ extern "C" vegas_status vegas_sweep_noalloc(void *spins, const void *links, cons
         if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(VEGAS_EINVAL, "device ordinal too large");
         void *base = nullptr;
         {
-            // first call on this device: resolve the device address of the static scratch
+            // set-up, once per device and CUDA context, with the device current: the device
+            // address of the static scratch (in host code its name is only a host-side handle)
             std::lock_guard<std::mutex> lk(g_mu);
-            if (!g_addr[dev]) {
-                e = cudaGetSymbolAddress(&g_addr[dev], g_noalloc_scratch);
+            ScratchSlot &sl = g_slot[dev];
+            unsigned long long id = current_context_id();
+            if (id == 0 || sl.ctx_id != id) {
+                void *addr = nullptr;
+                e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
                 if (e != cudaSuccess) {
-                    g_addr[dev] = nullptr;
+                    sl = ScratchSlot{0, nullptr};
                     return fail(VEGAS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
                 }
+                if (id == 0) id = current_context_id();  // the lookup made the primary context current
+                sl = ScratchSlot{id, addr};
             }
-            base = g_addr[dev];
+            base = sl.addr;
         }
         NoAllocHeader *hdr = (NoAllocHeader *)base;
         double *partial = (double *)((unsigned char *)base + kHeaderBytes);
@@ -168,6 +218,8 @@ extern "C" vegas_status vegas_sweep_noalloc(void *spins, const void *links, cons
         a.inst_local0 = 0;
         a.n_inst = replicas;
         a.n_sample_sites = n_sites;
+        a.n_sites_total = n_sites;  // debug builds check neighbour indices against it
+        a.n_edges_total = 0;        // unknown here: debug builds check rows for order only
         a.deg = 0;
         a.depth = 0;
         a.lower_mode = 2;
@@ -218,7 +270,9 @@ extern "C" vegas_status vegas_sweep_noalloc(void *spins, const void *links, cons
         uint32_t err = 0;
         e = cudaMemcpy(&err, hdr->err, sizeof err, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return fail(VEGAS_ECUDA, std::string("error word: ") + cudaGetErrorString(e));
-        if (err) return fail(VEGAS_EDEVICE, "device error flags " + std::to_string(err) + " (1: NaN energy change)");
+        if (err)
+            return fail(VEGAS_EDEVICE, "device error flags " + std::to_string(err) +
+                                           " (1: NaN energy change, 4: bad row or neighbour index seen by a debug build)");
         return VEGAS_OK;
     } catch (...) {
         return noalloc_host_exception();

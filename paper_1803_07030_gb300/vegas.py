@@ -351,6 +351,14 @@ def vegas_sweep_noalloc(spins_ptr: int, links_ptr: int, row_ptr_ptr: int, site_i
     b = _arr(beta, np.float64)
     f = _arr(field, np.float64)
     sp = _arr(site_params, np.float64)
+    # the C side reads replicas entries of beta and field, 9 site parameters and
+    # n_colours + 1 colour starts from these host arrays
+    if cs is None or cs.ndim != 1 or cs.size < 2:
+        raise ValueError("colour_start needs n_colours + 1 >= 2 entries")
+    if b is None or f is None or b.size < replicas or f.size < replicas:
+        raise ValueError("beta and field need one entry per replica")
+    if sp is not None and sp.size != 9:
+        raise ValueError("site_params holds 9 values (nx, ny, nz, s, ex, ey, ez, k, kc)")
     lib = load_library()
     st = lib.vegas_sweep_noalloc(spins_ptr, links_ptr, row_ptr_ptr, site_id_ptr, n_sites, _ptr(cs), len(cs) - 1,
                                  replicas, _ptr(b), _ptr(f), _ptr(sp), seed, inst0, t, out_ptr, stream)
@@ -495,7 +503,13 @@ class Context:
         return vegas_get_spins(self.ptr, inst, self.n_sites[inst // self.replicas])
 
     def set_spins(self, inst: int, spins) -> None:
-        vegas_set_spins(self.ptr, inst, spins)
+        if not 0 <= inst < self.n_instances:
+            raise ValueError(f"instance {inst} outside [0, {self.n_instances})")
+        a = _arr(spins, np.float64)
+        n = self.n_sites[inst // self.replicas]
+        if a.shape != (n, 3):  # the library reads n_sites x 3 doubles
+            raise ValueError(f"spins of instance {inst} must have shape ({n}, 3), not {a.shape}")
+        vegas_set_spins(self.ptr, inst, a)
 
     def set_mcs_counter(self, t: int) -> None:
         """Global MCS counter of the next MCS (keys its random numbers)."""

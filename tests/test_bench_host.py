@@ -67,6 +67,11 @@ class FakeContext:
     def history(self):
         return np.zeros((self.n_inst, self.hist_rows, 4))
 
+    def spins(self, inst):
+        """Every spin along +z (the history says E = 0, so the precision figure is |E_up| / N)."""
+        n = self.samples[inst // self.R].n_sites
+        return np.tile([0.0, 0.0, 1.0], (n, 1))
+
     def stats(self):
         return {"kernel_launches": self.launches, "sweep_launches": self.sweeps, "sweep_ms": self.sweep_ms,
                 "variant": 0, "block_threads": 256, "cluster_blocks": 0, "split_sites": 0, "group_threads": 0,
@@ -131,6 +136,18 @@ def test_headline_line_fields_and_arithmetic(fake_device, capsys, monkeypatch):
     assert r["achieved"] == pytest.approx(bench.BYTES_PER_ATTEMPT * r["attempts_per_launch"] / (SWEEP_MS / 1e3) / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["traffic"] is None  # the committed counters describe the 256^3 lattice only
+    # the whole-step fraction: bytes per attempt x attempts/s of the line
+    assert r["headline_achieved"] == pytest.approx(bench.BYTES_PER_ATTEMPT * line["value"] / 1e9)
+    assert r["headline_frac"] == pytest.approx(r["headline_achieved"] / r["peak"])
+    # precision: the history's E/N (the fake's is 0) against the oracle's energy of the spins
+    import oracle
+    from lattices import sc_periodic
+
+    p = line["precision"]
+    up = np.tile([0.0, 0.0, 1.0], (n, 1))
+    e_up = abs(oracle.energy(sc_periodic(side, bimodal_seed=bench.SEED), up, 0.0)) / n
+    assert p["bound"] == 1e-3 and [c["instance"] for c in p["checked"]] == [0, 16, 31]
+    assert p["d_e_per_site"] == pytest.approx(e_up) and p["ok"] == (e_up < 1e-3)
     c = line["cpu_baseline"]
     assert c["kind"] == "oracle" and c["cores"] >= 1 and c["value"] > 0 and "host" in c
     e = line["e2e"]
@@ -182,6 +199,13 @@ def secondary_line(capsys, name):
     assert line["gpu_launches"] == 3 * 2 * w.n_steps * w.mcs
     c = line["cpu_baseline"]
     assert c["kind"] == "oracle" and c["cores"] == 1 and c["value"] > 0 and c["unit"] == bench.UNIT
+    p = line["precision"]
+    assert p["bound"] == 1e-3 and p["checked"] and p["checked"][0]["instance"] == 0
+    import oracle
+
+    smp0 = w.samples[0]
+    e_up = abs(oracle.energy(smp0, np.tile([0.0, 0.0, 1.0], (smp0.n_sites, 1)), float(w.B[0, -1]))) / smp0.n_sites
+    assert p["checked"][0]["d_e_per_site"] == pytest.approx(e_up)
     r = line["effective_roofline"]
     assert r["achieved"] == pytest.approx(r["bytes_per_attempt"] * line["value"] / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])

@@ -258,3 +258,36 @@ def test_ising_options_rejected_before_the_device(lib):
         with pytest.raises(vb.VegasError) as e:
             vb.IsingContext(**kw)
         assert e.value.status == vb.EINVAL, kw
+
+
+def test_noalloc_refuses_misaligned_pointers_before_the_device(lib):
+    """Misaligned device pointers would fault the GPU in the kernels' vector loads, so the
+    allocation-free entry point refuses them on the host: these calls never reach CUDA
+    (the pointer values are never dereferenced)."""
+    import ctypes as C
+
+    cs = np.array([0, 4, 8], dtype=np.int32)
+    beta = np.ones(2)
+    field = np.zeros(2)
+    good = dict(spins=0x10000, links=0x20000, row_ptr=0x30000, site_id=0x40000, out=0x50000)
+    for name, bad in (("spins", 0x10008), ("links", 0x20004), ("row_ptr", 0x30004), ("out", 0x50004),
+                      ("site_id", 0x40002)):
+        p = dict(good, **{name: bad})
+        st = lib.vegas_sweep_noalloc(p["spins"], p["links"], p["row_ptr"], p["site_id"], 8, cs.ctypes.data, 2, 2,
+                                     beta.ctypes.data, field.ctypes.data, None, 1, 0, 0, p["out"], None)
+        assert st == vb.EINVAL, name
+        assert "aligned" in lib.vegas_noalloc_last_error().decode(), name
+    assert C.sizeof(C.c_void_p) == 8
+
+
+def test_noalloc_binding_checks_host_array_lengths(lib):
+    args = (0x10000, 0x20000, 0x30000, 0x40000, 8)
+    with pytest.raises(ValueError):
+        vg.vegas_sweep_noalloc(*args, [0, 4, 8], 4, np.ones(2), np.zeros(4), out_ptr=0x50000)
+    with pytest.raises(ValueError):
+        vg.vegas_sweep_noalloc(*args, [0, 4, 8], 2, np.ones(2), np.zeros(1), out_ptr=0x50000)
+    with pytest.raises(ValueError):
+        vg.vegas_sweep_noalloc(*args, [0, 4, 8], 2, np.ones(2), np.zeros(2), site_params=np.zeros(8),
+                               out_ptr=0x50000)
+    with pytest.raises(ValueError):
+        vg.vegas_sweep_noalloc(*args, [8], 2, np.ones(2), np.zeros(2), out_ptr=0x50000)

@@ -72,3 +72,44 @@ def test_debug_build_checks_pass_and_spins_match(debug_lib, name, kw):
     assert st["variant"] == kw["variant"]
     for i, (a, b) in enumerate(zip(ref, got)):
         assert np.array_equal(a, b), (name, i)
+
+
+def _noalloc_call(torch, lay, s, R, T, B, library):
+    saved = vb._lib
+    try:
+        vb._lib = vb.load_library(library) if library else saved
+        out = torch.zeros((R, 4), dtype=torch.float64, device="cuda")
+        vg.vegas_sweep_noalloc(lay["spins"].data_ptr(), lay["links"].data_ptr(), lay["row_ptr"].data_ptr(),
+                               lay["site_id"].data_ptr(), s.n_sites, lay["colour_start"], R, 1.0 / T, B, seed=7,
+                               inst0=0, t=0, out_ptr=out.data_ptr(), stream=torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        return out.cpu().numpy(), lay["spins"].cpu().numpy()
+    finally:
+        vb._lib = saved
+
+
+def test_debug_build_checks_the_allocation_free_sweep(debug_lib):
+    """The allocation-free entry point cannot validate device arrays on the host; its debug
+    build checks every row and neighbour index in the kernel. Valid data: no flag, and the
+    same sums and spins as the normal build. A neighbour index past the sites: the kernel
+    skips that attempt and the call reports VEGAS_EDEVICE with the index flag (the bad index
+    is never used to address memory)."""
+    import torch
+    from conftest import noalloc_device_layout
+
+    s = sc_periodic((6, 4, 5), bimodal_seed=2)
+    R = 4
+    T = np.array([0.4, 0.9, 1.5, 2.2])
+    B = np.array([0.0, 0.1, 0.2, 0.3])
+    up = [np.tile([0.0, 0.0, 1.0], (s.n_sites, 1))] * R
+    ref = _noalloc_call(torch, noalloc_device_layout(torch, s, up), s, R, T, B, None)
+    got = _noalloc_call(torch, noalloc_device_layout(torch, s, up), s, R, T, B, debug_lib)
+    assert np.array_equal(ref[1], got[1])
+    assert np.allclose(ref[0], got[0], rtol=0, atol=1e-9 * s.n_sites)
+    lay = noalloc_device_layout(torch, s, up)
+    bad = lay["links_host"].copy()
+    bad[5, 0] = s.n_sites + 3  # one link points past the last site
+    lay["links"] = torch.from_numpy(bad).to("cuda")
+    with pytest.raises(vb.VegasError) as e:
+        _noalloc_call(torch, lay, s, R, T, B, debug_lib)
+    assert e.value.status == vb.EDEVICE and "4" in str(e.value)

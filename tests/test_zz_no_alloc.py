@@ -12,6 +12,8 @@ This file is collected last on purpose.
 import numpy as np
 import pytest
 
+from conftest import noalloc_device_layout
+
 import paper_1803_07030_gb300 as vg
 from paper_1803_07030_gb300 import vegas as vb
 from lattices import sc_periodic
@@ -28,36 +30,6 @@ def torch():
     return t
 
 
-def device_layout(torch, s, spins_by_replica):
-    """Colour-major renumbering (greedy colouring, caller ids ascending inside a class),
-    links as (neighbour, J float32 bits), spins as [site][replica][4] float32."""
-    n = s.n_sites
-    colour, nc = vg.vegas_greedy_colour(s.row_ptr, s.col)
-    order = np.lexsort((np.arange(n), colour))  # new index -> caller id
-    inv = np.empty(n, dtype=np.int64)
-    inv[order] = np.arange(n)
-    cstart = np.concatenate([[0], np.cumsum(np.bincount(colour, minlength=nc))]).astype(np.int32)
-    deg = np.diff(s.row_ptr)[order]
-    row_ptr = np.concatenate([[0], np.cumsum(deg)]).astype(np.int64)
-    first = np.repeat(s.row_ptr[order] - row_ptr[:-1], deg) + np.arange(row_ptr[-1])
-    links = np.empty((row_ptr[-1], 2), dtype=np.int32)
-    links[:, 0] = inv[s.col[first]]
-    links[:, 1] = s.J[first].astype(np.float32).view(np.int32)
-    R = len(spins_by_replica)
-    spins = np.zeros((n, R, 4), dtype=np.float32)
-    for r, S in enumerate(spins_by_replica):
-        spins[:, r, :3] = S[order]
-    dev = "cuda"
-    return {
-        "spins": torch.from_numpy(spins).to(dev),
-        "links": torch.from_numpy(links).to(dev),
-        "row_ptr": torch.from_numpy(row_ptr).to(dev),
-        "site_id": torch.from_numpy(order.astype(np.int32)).to(dev),
-        "colour_start": cstart,
-        "order": order,
-    }
-
-
 def test_no_alloc_sweep_matches_context_two_calls(torch):
     s = sc_periodic(12, bimodal_seed=3)
     R, seed, inst0 = 4, 5, 8
@@ -68,7 +40,7 @@ def test_no_alloc_sweep_matches_context_two_calls(torch):
         c.run(T[:, None], B[:, None], 2)  # one step of two MCS: records 0 and 1
         H = c.history()
         final = [c.spins(r) for r in range(R)]
-    lay = device_layout(torch, s, start)
+    lay = noalloc_device_layout(torch, s, start)
     out = torch.zeros((R, 4), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     got = []
@@ -91,7 +63,7 @@ def test_no_alloc_sweep_matches_context_two_calls(torch):
 
 def test_no_alloc_rejects_sizes_beyond_its_scratch(torch):
     s = sc_periodic(4)
-    lay = device_layout(torch, s, [np.tile([0, 0, 1.0], (s.n_sites, 1))])
+    lay = noalloc_device_layout(torch, s, [np.tile([0, 0, 1.0], (s.n_sites, 1))])
     out = torch.zeros((64, 4), dtype=torch.float64, device="cuda")
     with pytest.raises(vb.VegasError) as e:
         vg.vegas_sweep_noalloc(lay["spins"].data_ptr(), lay["links"].data_ptr(), lay["row_ptr"].data_ptr(),
