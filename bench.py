@@ -133,6 +133,12 @@ def slowest_rank_ms(ms: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def sweep_kernel_names(bits: int) -> list:
+    from paper_1803_07030_gb300.vegas import sweep_kernel_names as names
+
+    return names(bits)
+
+
 def peaks():
     """Measured HBM copy bandwidth (GB/s) of this GPU model if the file has it, else the
     fallback figure."""
@@ -568,6 +574,7 @@ def run_ours(args):
             "batched_over_plain": value / world / plain_value,
             "gpu_launches": launches,
             "variant": st1["variant"],
+            "sweep_kernels": sweep_kernel_names(st1.get("sweep_kernels", 0)),
             "create_s": create_s,
             "clocks": clk.summary(),
         }
@@ -653,6 +660,7 @@ def run_workload(args):
             "data": "synthetic",
             "config": workload_config(w, args, policy, share["job_attempts"]),
             **shape,
+            "sweep_kernels": sweep_kernel_names(st1.get("sweep_kernels", 0)) if st1 else [],
             "precision": precision,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),

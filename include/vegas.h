@@ -225,8 +225,20 @@ typedef struct {
     int32_t group_threads;      /* resident or cluster sweep in use: threads per small instance
                                    swept several to a block (0 = one instance per block) */
     int32_t group_sites;        /* the largest instance swept that way */
-    int32_t pad2_;
+    uint32_t sweep_kernels;     /* the kernels of the sweep in use (the variant of the last run),
+                                   one VEGAS_KERNEL_* bit each */
 } vegas_stats_t;
+
+/* Bits of vegas_stats_t.sweep_kernels: which sweep kernels a run launches. */
+#define VEGAS_KERNEL_PASS64 0x1u               /* FP64 colour pass */
+#define VEGAS_KERNEL_PASS32_DIRECT 0x2u        /* FP32 colour pass, plain loads, any rows */
+#define VEGAS_KERNEL_PASS32_STAGED 0x4u        /* FP32 colour pass, staged rows of six links */
+#define VEGAS_KERNEL_PASS32_R32 0x8u           /* FP32 colour pass, 32 replicas per site */
+#define VEGAS_KERNEL_PASS32_R32_POLICY 0x10u   /* the same with an update-policy table */
+#define VEGAS_KERNEL_RESIDENT32 0x20u          /* resident (persistent) sweep */
+#define VEGAS_KERNEL_COOP32 0x40u              /* cooperative sweep */
+#define VEGAS_KERNEL_CLUSTER32 0x80u           /* cluster sweep */
+#define VEGAS_KERNEL_WAVE32 0x100u             /* wavefront sweep */
 
 /* Fills *opt with the defaults listed above. */
 void vegas_default_options(vegas_options *opt);

@@ -1824,6 +1824,19 @@ extern "C" vegas_status vegas_stats(const vegas_ctx *c, vegas_stats_t *o) {
         o->group_threads = (c->variant == 1 || c->variant == 3) ? c->res.group_threads : 0;
         o->group_sites = (c->variant == 1 || c->variant == 3) ? c->res.group_sites : 0;
         o->graph_launches = c->graph_launches;
+        uint32_t kinds = 0;
+        if (c->variant == 1)
+            kinds = VEGAS_KERNEL_RESIDENT32;
+        else if (c->variant == 2)
+            kinds = VEGAS_KERNEL_COOP32;
+        else if (c->variant == 3)
+            kinds = VEGAS_KERNEL_CLUSTER32;
+        else if (c->variant == 4)
+            kinds = VEGAS_KERNEL_WAVE32;
+        else
+            for (const PassLaunch &p : c->passes)
+                kinds |= c->precision == 64 ? VEGAS_KERNEL_PASS64 : pass32_kind(p.args);
+        o->sweep_kernels = kinds;
         return VEGAS_OK;
     } catch (...) {
         return host_exception(const_cast<vegas_ctx *>(c));

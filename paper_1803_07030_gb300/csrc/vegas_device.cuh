@@ -116,9 +116,12 @@ __device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, f
         dE = fmaf(-p.k, __fmul_rn(__fsub_rn(pn, po), __fadd_rn(pn, po)), dE);
         dE = fmaf(-p.kc, __fsub_rn(cub32(px, py, pz), cub32(Si.x, Si.y, Si.z)), dE);
     }
-    // Metropolis acceptance (Eq. 4); NaN rejects
-    const float u = __fsub_rn(__uint_as_float(0x3F800000u | (wacc >> 9)), 1.0f);  // k 2^-23 in [0, 1)
-    acc = (dE <= 0.f) || (u < __expf(__fmul_rn(-beta, dE)));
+    // Metropolis acceptance (Eq. 4) with the uniform u = wacc 2^-32 (all 32 random bits):
+    // u < p  <=>  wacc < p 2^32, so the test is wacc < floor(p 2^32) (p 2^32 is exact in FP32,
+    // the conversion truncates) and P(accept) = floor(p 2^32) 2^-32 lies in (p - 2^-32, p].
+    // p >= 1 accepts outright (floor(2^32) does not fit 32 bits). NaN rejects.
+    const float pacc = __expf(__fmul_rn(-beta, dE));
+    acc = (dE <= 0.f) || (pacc >= 1.0f) || (wacc < __float2uint_rz(__fmul_rn(pacc, 0x1p32f)));
     nan_seen = (dE != dE);
     if (nan_seen) acc = false;
     const float qx = acc ? px : Si.x, qy = acc ? py : Si.y, qz = acc ? pz : Si.z;

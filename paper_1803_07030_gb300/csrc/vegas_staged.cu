@@ -359,4 +359,10 @@ PassFn select_pass32(const PassArgs &a) {
 
 int pass32_smem(const PassArgs &a) { return use_staged(a) ? staged_smem(a) : 0; }
 
+uint32_t pass32_kind(const PassArgs &a) {
+    if (!use_staged(a)) return VEGAS_KERNEL_PASS32_DIRECT;
+    if (use_r32(a)) return a.pol32 ? VEGAS_KERNEL_PASS32_R32_POLICY : VEGAS_KERNEL_PASS32_R32;
+    return VEGAS_KERNEL_PASS32_STAGED;
+}
+
 }  // namespace vegas

@@ -42,6 +42,16 @@ class vegas_sample(C.Structure):
         ("type_param", P),
     ]
 
+# bits of vegas_stats_t.sweep_kernels (VEGAS_KERNEL_*)
+KERNEL_BITS = {"pass64": 0x1, "pass32_direct": 0x2, "pass32_staged": 0x4, "pass32_r32": 0x8,
+               "pass32_r32_policy": 0x10, "resident32": 0x20, "coop32": 0x40, "cluster32": 0x80, "wave32": 0x100}
+
+
+def sweep_kernel_names(bits: int) -> list:
+    """Names of the sweep kernels in a vegas_stats_t.sweep_kernels mask."""
+    return [k for k, v in KERNEL_BITS.items() if bits & v]
+
+
 # update policies (vegas_policy)
 (POLICY_RANDOM, POLICY_SPIN_FLIP, POLICY_SMALL_STEP, POLICY_GAUSSIAN, POLICY_HINZKE_NOWAK, POLICY_ADAPTIVE,
  POLICY_QISING) = range(7)
@@ -101,7 +111,7 @@ class vegas_stats_t(C.Structure):
         ("split_sites", C.c_int32),
         ("group_threads", C.c_int32),
         ("group_sites", C.c_int32),
-        ("pad2_", C.c_int32),
+        ("sweep_kernels", C.c_uint32),
     ]
 
 

@@ -65,3 +65,86 @@ def noalloc_device_layout(torch, s, spins_by_replica):
         "order": order,
         "links_host": links,
     }
+
+
+# ----------------------------------------------------------------------------- statistics
+# Observables and the match criterion of the statistical parity tests (thermal averages,
+# Sec. IV.A; Landau & Binder's binning and jackknife): per chain, drop the first fifth of a
+# step's records, split the rest into 20 bins; e = <E>/N and m = <|M|>/N with the standard
+# error of the bin means, C_v = N var(e) / T^2 and chi = N var(m) / T with 20-bin jackknife
+# errors. Independent chains (replicas at the same T and B) are averaged; the error of the
+# average is the larger of the combined within-chain error and the spread between chains
+# (the latter also holds for chains that are still relaxing, which binning would miss).
+
+OBSERVABLES = ("e", "m", "cv", "chi")
+
+
+def _jackknife_var(x, pref, n_bins=20):
+    k = (len(x) // n_bins) * n_bins
+    bins = x[len(x) - k:].reshape(n_bins, -1)
+    jk = np.array([pref * np.var(np.delete(bins, j, axis=0).reshape(-1)) for j in range(n_bins)])
+    return pref * np.var(x), float(np.sqrt((n_bins - 1.0) / n_bins * np.sum((jk - jk.mean()) ** 2)))
+
+
+def chain_observables(H, N, T, cut=0.2, n_bins=20):
+    """H: [chains, records, 4] history records (E, Mx, My, Mz totals) of one temperature/field
+    step of independent chains at temperature T; N sites. Returns {name: (value, error)}."""
+    H = np.asarray(H, dtype=np.float64)
+    if H.ndim == 2:
+        H = H[None]
+    c0 = int(H.shape[1] * cut)
+    e = H[:, c0:, 0] / N
+    m = np.linalg.norm(H[:, c0:, 1:], axis=2) / N
+    out = {}
+    n = H.shape[0]
+    for name, x in (("e", e), ("m", m)):
+        vals, errs = [], []
+        for xi in x:
+            k = (len(xi) // n_bins) * n_bins
+            b = xi[len(xi) - k:].reshape(n_bins, -1).mean(axis=1)
+            vals.append(b.mean())
+            errs.append(b.std(ddof=1) / np.sqrt(n_bins))
+        out[name] = (vals, errs)
+    for name, x, pref in (("cv", e, N / T ** 2), ("chi", m, N / T)):
+        vals, errs = zip(*(_jackknife_var(xi, pref, n_bins) for xi in x))
+        out[name] = (list(vals), list(errs))
+    res = {}
+    for name, (vals, errs) in out.items():
+        v = float(np.mean(vals))
+        within = float(np.sqrt(np.sum(np.square(errs))) / n)
+        between = float(np.std(vals, ddof=1) / np.sqrt(n)) if n > 1 else 0.0
+        res[name] = (v, max(within, between))
+    return res
+
+
+def failing_observables(a, b, keys=OBSERVABLES, sigmas=3.0, floor=0.0):
+    """Keys whose values differ by more than `sigmas` combined standard errors (plus an
+    absolute floor for observables that vanish on both sides)."""
+    bad = []
+    for k in keys:
+        (x, sx), (y, sy) = a[k], b[k]
+        if not abs(x - y) <= sigmas * np.hypot(sx, sy) + floor:
+            bad.append(k)
+    return bad
+
+
+def assert_statistically_equal(run, keys=OBSERVABLES, label="", sigmas=3.0, floor=0.0):
+    """The match criterion with fresh seeds: run(attempt) returns a list of (gpu, oracle)
+    observable dicts (one per comparison point) from independent seeds that depend on
+    `attempt`. A point fails only if the same observable fails again with fresh seeds
+    (attempt 1), so a true 3-sigma excursion (0.27% per comparison) is not a failure."""
+    first = run(0)
+    bad = {i: failing_observables(g, o, keys, sigmas, floor) for i, (g, o) in enumerate(first)}
+    bad = {i: k for i, k in bad.items() if k}
+    for i, ks in bad.items():
+        g, o = first[i]
+        print(f"{label} point {i}: {ks} outside {sigmas} sigma with the first seeds: "
+              + ", ".join(f"{k} {g[k][0]:.6g}+-{g[k][1]:.2g} vs {o[k][0]:.6g}+-{o[k][1]:.2g}" for k in ks))
+    if not bad:
+        return first
+    second = run(1)
+    for i, ks in bad.items():
+        g, o = second[i]
+        again = failing_observables(g, o, ks, sigmas, floor)
+        assert not again, (label, i, {k: (g[k], o[k]) for k in again})
+    return second
