@@ -192,6 +192,13 @@ typedef struct {
                                blocks after the last class-0 block it links to, so that its
                                dependencies have usually finished when a warp reaches it;
                                0 = the number of warps of the launch. Default 0. */
+    int32_t wave_slab;      /* wavefront sweep with positions: sites are stored slab by slab
+                               along x, each slab plane by plane (z, then y, then x), so the
+                               planes in flight stay a few MB at any cross-section; > 0 the slab
+                               width in position units, 0 automatic (slabs of about 16384 sites
+                               per plane; whole planes when they are no larger), -1 whole planes.
+                               Default 0. */
+    int32_t pad_;
 } vegas_options;
 
 typedef struct {

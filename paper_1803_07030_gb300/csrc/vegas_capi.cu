@@ -462,6 +462,7 @@ extern "C" void vegas_default_options(vegas_options *o) {
     o->group_threads = 0;
     o->group_sites = 0;
     o->wave_lag = 0;
+    o->wave_slab = 0;
 }
 
 // vegas_create without the exception guard; *made is the context under construction.
@@ -482,6 +483,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         return fail(nullptr, VEGAS_EINVAL,
                     "the wavefront sweep (variant 4) is FP32 with one sample, 32 replicas and no per-type statistics");
     if (o.wave_lag < 0) return fail(nullptr, VEGAS_EINVAL, "wave_lag must be >= 0");
+    if (o.wave_slab < -1) return fail(nullptr, VEGAS_EINVAL, "wave_slab must be >= -1");
     if (o.cluster_split < 0) return fail(nullptr, VEGAS_EINVAL, "cluster_split must be >= 0");
     if (o.group_threads != 0 && o.group_threads != 64 && o.group_threads != 128 && o.group_threads != 256)
         return fail(nullptr, VEGAS_EINVAL, "group_threads must be 0, 64, 128 or 256");
@@ -511,7 +513,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
     int64_t n_sites = 0, n_edges = 0;
     for (int32_t s = 0; s < n_samples; ++s) {
         std::string e;
-        if (!load_sample(samples[s], L[(size_t)s], e, o.type_stats != 0, o.variant == 4))
+        if (!load_sample(samples[s], L[(size_t)s], e, o.type_stats != 0, o.variant == 4, (double)o.wave_slab))
             return fail(nullptr, VEGAS_EINVAL, "sample " + std::to_string(s) + ": " + e);
         n_sites += L[(size_t)s].n;
         n_edges += L[(size_t)s].n_edges + (L[(size_t)s].n_edges & 1);  // keep every sample 16-byte aligned

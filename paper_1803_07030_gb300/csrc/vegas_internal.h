@@ -81,6 +81,7 @@ struct LoadedSample {
     std::vector<int32_t> type;       // per site (new numbering); all 0 without a type array
     int32_t n_types = 1;             // 1 + the largest type
     bool uniform_params = false;     // every site has the same (s, n, k, e, kc)
+    double slab_width = 0.0;         // wavefront order: slab width along x (0: whole planes)
     bool has_anisotropy = false;     // some k or kc is non-zero
     // update policy per site (new numbering): code and parameter (cap height 1 - cos theta
     // for small step and Hinzke-Nowak, width for Gaussian and adaptive); empty when every
@@ -98,8 +99,11 @@ struct LoadedSample {
 // colour class, sites are ordered by type first (then Morton order or caller id). plane_order:
 // inside each class, positions are ordered by z, then y, then x (instead of the Morton curve),
 // so that every neighbour of a site lies within about one plane of it in memory order.
+// wave_slab (with plane_order): the sites are first cut into slabs along x, and ordered slab
+// by slab, each slab plane by plane (z, y, x): > 0 the slab width in position units, 0 an
+// automatic width (slabs of about 16384 sites per plane), < 0 no slabs.
 bool load_sample(const vegas_sample &s, LoadedSample &out, std::string &err, bool type_major = false,
-                 bool plane_order = false);
+                 bool plane_order = false, double wave_slab = -1.0);
 
 // ------------------------------------------------------------------ device-side layouts
 

@@ -96,7 +96,32 @@ extern "C" int32_t vegas_greedy_colour(int32_t n, const int64_t *row_ptr, const 
 
 namespace vegas {
 
-bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err, bool type_major, bool plane_order) {
+namespace {
+
+// Slab width along x of the wavefront order: the planes (distinct z) of a sample with many
+// sites per plane are cut into slabs of about 16384 sites per plane, so that the window of
+// planes a wavefront keeps in flight stays a few MB whatever the lattice's cross-section.
+// Returns 0 for no slabs.
+double auto_slab_width(const double *P, int32_t n) {
+    std::vector<double> z((size_t)n);
+    double xmin = P[0], xmax = P[0];
+    for (int32_t i = 0; i < n; ++i) {
+        z[(size_t)i] = P[3 * (size_t)i + 2];
+        xmin = std::min(xmin, P[3 * (size_t)i]);
+        xmax = std::max(xmax, P[3 * (size_t)i]);
+    }
+    std::sort(z.begin(), z.end());
+    const int64_t planes = std::unique(z.begin(), z.end()) - z.begin();
+    const int64_t per_plane = (n + planes - 1) / planes;
+    const int64_t n_slabs = (per_plane + 16383) / 16384;
+    if (n_slabs <= 1 || !(xmax > xmin)) return 0.0;
+    return (xmax - xmin) / (double)n_slabs * (1.0 + 1e-9);
+}
+
+}  // namespace
+
+bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err, bool type_major, bool plane_order,
+                 double wave_slab) {
     const int32_t n = s.n_sites;
     if (n < 1) { err = "n_sites must be >= 1"; return false; }
     if (!s.row_ptr) { err = "row_ptr is NULL"; return false; }
@@ -201,11 +226,19 @@ bool load_sample(const vegas_sample &s, LoadedSample &L, std::string &err, bool 
     L.orig.resize((size_t)n);
     L.inv.resize((size_t)n);
     for (int32_t i = 0; i < n; ++i) L.orig[(size_t)fill[(size_t)colour[(size_t)i]]++] = i;
-    if (s.positions && plane_order) {  // memory order inside each class: z, then y, then x
+    if (s.positions && plane_order) {  // memory order inside each class: slab, then z, y, x
         const double *P = s.positions;
+        const double width = wave_slab > 0.0 ? wave_slab : (wave_slab == 0.0 ? auto_slab_width(P, n) : 0.0);
+        double xmin = P[0];
+        for (int32_t i = 1; i < n; ++i) xmin = std::min(xmin, P[3 * (size_t)i]);
+        std::vector<int64_t> slab((size_t)n, 0);
+        if (width > 0.0)
+            for (int32_t i = 0; i < n; ++i) slab[(size_t)i] = (int64_t)std::floor((P[3 * (size_t)i] - xmin) / width);
+        L.slab_width = width;
         for (int32_t c = 0; c < nc; ++c)
             std::stable_sort(L.orig.begin() + L.cstart[(size_t)c], L.orig.begin() + L.cstart[(size_t)c + 1],
                              [&](int32_t x, int32_t y) {
+                                 if (slab[(size_t)x] != slab[(size_t)y]) return slab[(size_t)x] < slab[(size_t)y];
                                  for (int q = 2; q >= 0; --q)
                                      if (P[3 * (size_t)x + q] != P[3 * (size_t)y + q])
                                          return P[3 * (size_t)x + q] < P[3 * (size_t)y + q];

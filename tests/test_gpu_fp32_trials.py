@@ -9,6 +9,7 @@ larger mistake hides there:
 - free spins at B = 0: every energy change is 0, so every trial is accepted and the spins
   are the trials; their z and azimuth are uniform (Kolmogorov-Smirnov on 10^6 trials), the
   moments <S_a> = 0 and <S_a S_b> = delta_ab / 3 hold, and |S| = 1 to FP32 rounding;
+- the end-of-step renormalisation rounds like the FP64 formula s S/|S|;
 - spin-1/2 free spins (the qIsing policy) in a field: the trial is always the other value,
   so the stationary law is set by the acceptance probability exp(-beta dE) alone,
   <S_z> = tanh(beta B / 2) / 2, checked to about 1e-4.
@@ -74,3 +75,41 @@ def test_acceptance_probability_sets_the_two_state_law(beta_B):
     exact = 0.5 * np.tanh(beta_B / 2.0)
     assert abs(got - exact) < 4.0 * se + 2e-6, (got, se, exact)
     assert se < 2e-4
+
+
+@pytest.mark.parametrize("norm", [1.0, 2.0])
+def test_fp32_renormalisation_rounds_like_the_fp64_formula(norm):
+    """The end-of-step renormalisation of FP32 spins (S <- s S/|S| with |S|^2 in FP64) against
+    the FP64 formula evaluated on the host and rounded to FP32, for spins whose norm is off by
+    1e-7 (what Metropolis steps leave), 1e-4, 2^-11 (the series' range), 0.5 and 3 (the
+    direct formula), with spin norms s = 1 and 2. A ferromagnet held at T = 1e-6 rejects every
+    move, so only the renormalisation changes the spins (the accept log confirms it)."""
+    from lattices import sc_periodic
+
+    s = sc_periodic(8)
+    n = s.n_sites
+    s.spin_norm = np.full(n, norm)
+    rng = np.random.default_rng(5)
+    cases = [1e-7, -1e-4, 2.0 ** -11, -0.5, 2.0]  # |S| / s - 1 up to these (sign included)
+    R = len(cases) + 1
+    starts = []
+    for k in range(R):
+        d = np.tile([0.0, 0.0, 1.0], (n, 1)) + rng.normal(0.0, 1e-4, size=(n, 3))
+        d *= norm / np.linalg.norm(d, axis=1)[:, None]
+        if k < len(cases):
+            d *= 1.0 + cases[k] * rng.uniform(0.0, 1.0, size=(n, 1))
+        starts.append(d)
+    with vg.Context([s], precision=32, replicas=R, seed=79, accept_log_mcs=1, stream=None) as c:
+        for k in range(R):
+            c.set_spins(k, starts[k])
+        got0 = [c.spins(k) for k in range(R)]  # the FP32 values the kernels hold
+        c.run(np.full((R, 1), 1e-6), np.full((R, 1), 0.5), 1)
+        assert not c.accept_log().any()
+        got = [c.spins(k) for k in range(R)]
+    for k in range(R):
+        v = got0[k].astype(np.float32).astype(np.float64)
+        f = norm / np.sqrt((v * v).sum(axis=1))
+        want = (v * f[:, None]).astype(np.float32)
+        exact = np.mean(got[k].astype(np.float32) == want)
+        ulps = np.abs(got[k].astype(np.float32).view(np.int32) - want.view(np.int32))
+        assert exact > 0.9999 and ulps.max() <= 1, (k, exact, ulps.max())
