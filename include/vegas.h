@@ -246,6 +246,8 @@ typedef struct {
 #define VEGAS_KERNEL_COOP32 0x40u              /* cooperative sweep */
 #define VEGAS_KERNEL_CLUSTER32 0x80u           /* cluster sweep */
 #define VEGAS_KERNEL_WAVE32 0x100u             /* wavefront sweep */
+#define VEGAS_KERNEL_PASS32_R32_ONE_POLICY 0x200u /* 32 replicas per site, compiled for the one
+                                                     update policy of every site of the class */
 
 /* Fills *opt with the defaults listed above. */
 void vegas_default_options(vegas_options *opt);

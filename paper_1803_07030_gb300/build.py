@@ -16,8 +16,8 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libvegas.so")
 LIB_DEBUG = os.path.join(OUT_DIR, "libvegas_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["vegas_kernels.cu", "vegas_staged.cu", "vegas_wave.cu", "vegas_analysis.cu", "vegas_ising.cu", "vegas_capi.cu", "vegas_noalloc.cu", "vegas_loader.cpp"]
-HEADERS = ["vegas_internal.h", "vegas_device.cuh", "vegas_staged.cuh", os.path.join("..", "..", "include", "vegas.h")]
+SOURCES = ["vegas_kernels.cu", "vegas_staged.cu", "vegas_policy32.cu", "vegas_wave.cu", "vegas_analysis.cu", "vegas_ising.cu", "vegas_capi.cu", "vegas_noalloc.cu", "vegas_loader.cpp"]
+HEADERS = ["vegas_internal.h", "vegas_device.cuh", "vegas_staged.cuh", "vegas_r32.cuh", os.path.join("..", "..", "include", "vegas.h")]
 
 
 def _nvcc() -> str:
@@ -50,8 +50,10 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
         obj = os.path.join(OUT_DIR, src + f".{os.getpid()}{'.dbg' if debug else ''}.o")
         path = os.path.join(CSRC, src)
         if src.endswith(".cu"):
-            cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "1444",
-                   "-c", path, "-o", obj]
+            # -ftz=true: FP32 subnormals flush to zero (spins, fields and energy changes are O(1);
+            # the special-function instructions then need no subnormal fix-ups); FP64 is unaffected
+            cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-ftz=true", "-Xcompiler", "-fPIC", "-diag-suppress",
+                   "1444", "-c", path, "-o", obj]
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
             if debug:

@@ -810,6 +810,13 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
             a.pk = si.uniform_params ? nullptr : c->d_pk;
             a.pol = si.has_policy ? c->d_pol : nullptr;
             a.pol32 = si.has_policy ? c->d_pol32 : nullptr;
+            a.pol_fixed = -1;
+            if (a.pol32 && nc > 0) {  // one policy over the whole pass: a specialised kernel
+                const int32_t g0 = si.site_off + sb, code = h_pol32[(size_t)g0].code;
+                bool same = true;
+                for (int32_t g = g0 + 1; g < si.site_off + se && same; ++g) same = h_pol32[(size_t)g].code == code;
+                if (same) a.pol_fixed = code;
+            }
             a.run = c->d_run;
             a.err = c->d_err;
             a.alog = c->d_alog;

@@ -152,9 +152,12 @@ __device__ __forceinline__ float3 unit32(float x, float y, float z) {
 
 constexpr int kPolCapSphere = 6;  // internal: the random third of Hinzke-Nowak, as a cap of height 2
 
+// PC >= 0: every site of the pass has policy PC (the kernel is specialised: the other
+// policies' code is not compiled in); -1: the policy of each site from its table entry.
+template <int PC = -1>
 __device__ __forceinline__ float3 policy_trial32(const PolicySite32 ps, float sigma, const float4 Si, float sn,
                                                  uint4 rw) {
-    int code = ps.code;
+    int code = PC >= 0 ? PC : ps.code;
     if (code == kPolQIsing) {  // another of the 2 s + 1 values along z, uniformly
         const int n2 = (int)(2.0f * sn);
         const int idx = (int)(Si.z + sn + 0.5f);

@@ -189,6 +189,8 @@ struct PassArgs {
     int32_t depth;             // staged FP32 kernel: cp.async pipeline depth (2..4); 0 = direct kernel
     uint32_t *ticket;          // R = 32 staged kernel: next block of 8 sites of this pass (zeroed
                                // by the MCS's reduction); unused by the other kernels
+    int32_t pol_fixed;         // FP32 with a policy table: the one policy of every site of the
+                               // pass, or -1 (mixed, or no table)
     SiteParams32 u32;
     SiteParams64 u64;
 };

@@ -1,0 +1,149 @@
+// The replica-batched FP32 colour pass (R = 32, rows of six links): shared by the translation
+// unit of the staged kernels (no policy table, or a table read per site) and the one of the
+// kernels specialised to a single update policy.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "vegas_device.cuh"
+#include "vegas_internal.h"
+#include "vegas_staged.cuh"
+
+namespace vegas {
+namespace {
+
+// Replica-batched sweep (R = 32): one warp = one site x 32 replicas, depth-2 pipeline. A
+// warp takes blocks of eight consecutive sites from the pass's ticket counter, so the blocks
+// in flight stay about one per warp and consecutive in memory order however unevenly the
+// warps progress: the neighbour rows they share are still in L2 when the last of them reads
+// them. The eight groups of a block are unrolled, so every ring slot and offset is a
+// constant: group j of a block computes from row slot j & 1 and its link slot; the next
+// ticket is drawn at j = 0 and its block's links copied at j = 4; rows of group j + 2 (the
+// next block's first two at j = 6, 7) are copied at the end of group j.
+// POL = 1 adds the sites' update policies (8 bytes each, staged with the caller ids); POL =
+// 2 + c does the same for a pass whose sites all have policy c, with the trial of that policy
+// alone compiled in (each site's parameter still comes from its entry).
+template <int PM, int LM, int POL>
+__global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
+    constexpr int DEG = 6, D = 2, BS = 8, R = 32;
+    constexpr int ROWS = D * (DEG + 1) * 32 * 16;
+    constexpr int LINK_BYTES = BS * DEG * 8;
+    constexpr int POL_OFF = LINK_BYTES + BS * 4;
+    constexpr int SLOT = POL_OFF + (POL ? BS * 8 : 0);
+    constexpr int WARP_BYTES = ROWS + 2 * SLOT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const RunState *rs_ = a.run;
+    const uint32_t t = rs_->t;
+    const uint32_t step_idx = rs_->rec / rs_->mcs;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = lane;
+    unsigned char *wbase = smem + warp * WARP_BYTES;
+    float4 *rows = (float4 *)wbase;
+    unsigned char *lslots = wbase + ROWS;
+    float4 *S = (float4 *)a.spins;
+    const float4 *Sr = S + r;
+    const int2 *E = (const int2 *)a.edges;
+    const uint32_t inst = (uint32_t)(a.inst0 + r);
+    const double *sc = rs_->sched + ((int64_t)step_idx * a.n_inst + a.inst_local0 + r) * 2;
+    const float beta = (float)sc[0], B = (float)sc[1];
+    const float sigma = (POL && rs_->sigma) ? (float)rs_->sigma[a.inst_local0 + r] : 0.f;
+    const int g_end = a.g_end;
+    uint32_t rk0[10], rk1[10];
+    {
+        uint32_t x = (uint32_t)a.seed, y = (uint32_t)(a.seed >> 32);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            rk0[q] = x;
+            rk1[q] = y;
+            x += 0x9E3779B9u;
+            y += 0xBB67AE85u;
+        }
+    }
+    auto issue_links = [&](int sb, int slot) {
+        if (sb >= g_end) return;
+        const int ns = min(BS, g_end - sb);
+        unsigned char *dst = lslots + slot * SLOT;
+        const unsigned char *src = (const unsigned char *)(E + a.edge_base + (int64_t)(sb - a.site_off) * DEG);
+        VEGAS_CHECK(sb >= a.g_begin && sb + ns <= a.n_sites_total, 11, sb);
+        VEGAS_CHECK(a.edge_base + (int64_t)(sb - a.site_off + ns) * DEG <= a.n_edges_total, 12, sb);
+        VEGAS_CHECK(((uintptr_t)src & 15) == 0, 13, sb);
+        if (lane < ns * (DEG / 2)) cp16(dst + 16 * lane, src + 16 * lane);
+        if (lane < ns) cp4(dst + LINK_BYTES + 4 * lane, a.orig + sb + lane);
+        if (POL && lane < ns) cp8(dst + POL_OFF + 8 * lane, a.pol32 + sb + lane);
+    };
+    auto issue_rows = [&](int g, int lslot, int j, int rslot) {
+        if (g >= g_end) return;
+        const int4 *lk = (const int4 *)(lslots + lslot * SLOT) + j * (DEG / 2);
+        float4 *dst = rows + rslot * (DEG + 1) * 32 + lane;
+        VEGAS_CHECK(g < a.n_sites_total, 14, g);
+#pragma unroll
+        for (int q = 0; q < DEG / 2; ++q) {
+            const int4 l = lk[q];
+            VEGAS_CHECK(l.x >= 0 && l.x < a.n_sites_total && l.z >= 0 && l.z < a.n_sites_total, 15, l.x);
+            cp16(dst + (2 * q) * 32, Sr + (int64_t)l.x * R);
+            cp16(dst + (2 * q + 1) * 32, Sr + (int64_t)l.z * R);
+        }
+        cp16(dst + DEG * 32, Sr + (int64_t)g * R);
+    };
+
+    const uint32_t n_blocks = (uint32_t)(g_end - a.g_begin + BS - 1) / BS;  // a ticket past them ends the warp
+    uint32_t tk = 0;
+    if (lane == 0) tk = atomicAdd(a.ticket, 1u);
+    int sb = a.g_begin + (int)min(__shfl_sync(0xFFFFFFFFu, tk, 0), n_blocks) * BS;
+    issue_links(sb, 0);
+    cp_commit();
+    cp_wait<0>();
+    __syncwarp();
+    issue_rows(sb, 0, 0, 0);
+    cp_commit();
+    issue_rows(sb + 1, 0, 1, 1);
+    cp_commit();
+    Acc32 acc;
+    bool nan_seen = false;
+    const bool log_accepts = a.alog && t < a.alog_mcs;
+    int ls = 0;
+    while (sb < g_end) {
+        int sb2 = g_end;  // the next block (drawn at j = 0, known from j = 4)
+#pragma unroll
+        for (int j = 0; j < BS; ++j) {
+            cp_wait<D - 1>();
+            __syncwarp();
+            const int g = sb + j;
+            if (g < g_end) {
+                const unsigned char *slot = lslots + ls * SLOT;
+                const uint32_t orig = ((const uint32_t *)(slot + LINK_BYTES))[j];
+                staged_attempt<DEG, PM, LM, POL>(a, (const int4 *)slot + j * (DEG / 2),
+                                                 rows + (j & 1) * (DEG + 1) * 32 + lane, orig, g, r, R, t, inst, rk0, rk1,
+                                                 beta, B, S, acc, nan_seen, log_accepts,
+                                                 (const PolicySite32 *)(slot + POL_OFF) + j, sigma);
+            }
+            __syncwarp();
+            if (j == 0 && lane == 0) tk = atomicAdd(a.ticket, 1u);
+            if (j == 4) {
+                sb2 = a.g_begin + (int)min(__shfl_sync(0xFFFFFFFFu, tk, 0), n_blocks) * BS;
+                issue_links(sb2, ls ^ 1);
+            }
+            if (j + 2 < BS)
+                issue_rows(sb + j + 2, ls, j + 2, j & 1);
+            else
+                issue_rows(sb2 + j + 2 - BS, ls ^ 1, j + 2 - BS, j & 1);
+            cp_commit();
+        }
+        sb = sb2;
+        ls ^= 1;
+    }
+    cp_wait<0>();
+    if (nan_seen) atomicOr(a.err, kErrNaN);
+    acc.flush();
+    block_partials(acc.d, acc.nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs_, a.inst_local0));
+}
+
+}  // namespace
+
+// The R = 32 kernels specialised to one update policy (code 1 .. 6), built in their own
+// translation unit.
+PassFn select_r32_fixed(int pm, int lm, int code);
+
+}  // namespace vegas

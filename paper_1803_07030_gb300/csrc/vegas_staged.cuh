@@ -46,7 +46,8 @@ __device__ __forceinline__ uint4 trial_block32(uint32_t orig, uint32_t t, uint32
 
 // One staged attempt with its random block c already drawn: links lk (int4 pairs), rows
 // row[j*32] (neighbour j) and row[DEG*32] (own) in shared memory; with POL, the site's
-// update policy *ps too. LM 3 takes the lower sums as all (lower_all) or none at run time.
+// update policy *ps too (POL 1: the policy from the entry; POL 2 + c: every site has policy
+// c). LM 3 takes the lower sums as all (lower_all) or none at run time.
 template <int DEG, int PM, int LM, int POL = 0>
 __device__ __forceinline__ void staged_attempt_rw(const PassArgs &a, const int4 *lk, const float4 *row, uint32_t orig,
                                                   int g, int r, int R, uint32_t t, uint4 c, float beta, float B,
@@ -71,7 +72,7 @@ __device__ __forceinline__ void staged_attempt_rw(const PassArgs &a, const int4 
     bool ok, bad;
     float e_i;
     const float3 P =
-        POL ? policy_trial32(*ps, sigma, Si, p.sn, c) : trial_random32(c, p.sn);
+        POL ? policy_trial32<(POL >= 2 ? POL - 2 : -1)>(*ps, sigma, Si, p.sn, c) : trial_random32(c, p.sn);
     attempt32<PM, LM == 3 ? 1 : LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, P, c.z, Sn, ok, e_i, bad);
     nan_seen |= bad;
     if (ok) S[(int64_t)g * R + r] = Sn;

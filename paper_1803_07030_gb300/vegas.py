@@ -44,7 +44,8 @@ class vegas_sample(C.Structure):
 
 # bits of vegas_stats_t.sweep_kernels (VEGAS_KERNEL_*)
 KERNEL_BITS = {"pass64": 0x1, "pass32_direct": 0x2, "pass32_staged": 0x4, "pass32_r32": 0x8,
-               "pass32_r32_policy": 0x10, "resident32": 0x20, "coop32": 0x40, "cluster32": 0x80, "wave32": 0x100}
+               "pass32_r32_policy": 0x10, "resident32": 0x20, "coop32": 0x40, "cluster32": 0x80, "wave32": 0x100,
+               "pass32_r32_one_policy": 0x200}
 
 
 def sweep_kernel_names(bits: int) -> list:

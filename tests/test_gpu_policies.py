@@ -355,3 +355,52 @@ def test_qising_needs_half_integer_norms():
     with pytest.raises(vg.VegasError) as e:
         ctx([s])
     assert "qIsing" in str(e.value)
+
+
+SPECIALISED = [(oracle.SPIN_FLIP, 0.0), (oracle.SMALL_STEP, 0.6), (oracle.GAUSSIAN, 0.4), (oracle.HINZKE_NOWAK, 0.5),
+               (oracle.ADAPTIVE, 0.8), (oracle.QISING, 0.0)]
+
+
+@pytest.mark.parametrize("policy,param", SPECIALISED, ids=[str(p) for p, _ in SPECIALISED])
+def test_single_policy_kernel_equals_table_kernels(policy, param):
+    """A sample whose sites all have one policy runs the R = 32 kernel compiled for that policy
+    alone; its spins, accepted counts and adaptive widths equal the table-driven direct
+    kernel's bit for bit. Two site types with the same policy but different parameters keep
+    the per-site parameter in play."""
+    s = sc_periodic(12, k_uni=0.3)
+    s.type = (np.arange(s.n_sites) % 3 == 0).astype(np.int32)
+    if policy == oracle.QISING:
+        s.spin_norm = np.where(s.type == 0, 0.5, 1.0)
+    s.with_policy([policy, policy], [param, 1.5 * param if param else 0.0])
+    T = np.linspace(0.3, 2.5, 32)[:, None]
+    B = np.full_like(T, 0.15)
+    with ctx([s], replicas=32, seed=36, variant=0) as a, \
+            ctx([s], replicas=32, seed=36, variant=0, pipeline_depth=1) as b:
+        a.run(T, B, 10)
+        b.run(T, B, 10)
+        assert vg.vegas.sweep_kernel_names(a.stats()["sweep_kernels"]) == ["pass32_r32_one_policy"]
+        assert vg.vegas.sweep_kernel_names(b.stats()["sweep_kernels"]) == ["pass32_direct"]
+        assert np.array_equal(a.accept_history(), b.accept_history())
+        assert np.array_equal(a.adaptive_width(), b.adaptive_width())
+        for i in (0, 13, 31):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+
+
+def test_policy_kernel_per_colour_class():
+    """Each colour class gets its own kernel: a class whose sites all move at random runs the
+    kernel without a table, a class of one other policy the specialised kernel; the spins
+    equal the direct kernel's."""
+    s = sc_periodic(10)
+    colour, _ = vg.vegas_greedy_colour(s.row_ptr, s.col)
+    s.type = colour.astype(np.int32)  # type = class: class 0 random, class 1 Gaussian
+    s.with_policy([oracle.RANDOM, oracle.GAUSSIAN], [0.0, 0.3])
+    T = np.linspace(0.5, 2.0, 32)[:, None]
+    B = np.zeros_like(T)
+    with ctx([s], replicas=32, seed=37, variant=0) as a, \
+            ctx([s], replicas=32, seed=37, variant=0, pipeline_depth=1) as b:
+        a.run(T, B, 8)
+        b.run(T, B, 8)
+        assert sorted(vg.vegas.sweep_kernel_names(a.stats()["sweep_kernels"])) == \
+            ["pass32_r32", "pass32_r32_one_policy"]
+        for i in (0, 31):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
