@@ -198,7 +198,11 @@ typedef struct {
                                width in position units, 0 automatic (slabs of about 16384 sites
                                per plane; whole planes when they are no larger), -1 whole planes.
                                Default 0. */
-    int32_t pad_;
+    int32_t resident_smem;  /* resident sweep (variant 1): 1 keeps each instance's spins in
+                               shared memory for all MCS of a step (12 bytes per site; instances of
+                               at most 17066 sites; 512 or 1024 threads per block), -1 never, 0 the
+                               automatic choice times it beside the other shapes (with variant 1
+                               fixed: global memory). Default 0. */
 } vegas_options;
 
 typedef struct {
@@ -248,6 +252,7 @@ typedef struct {
 #define VEGAS_KERNEL_WAVE32 0x100u             /* wavefront sweep */
 #define VEGAS_KERNEL_PASS32_R32_ONE_POLICY 0x200u /* 32 replicas per site, compiled for the one
                                                      update policy of every site of the class */
+#define VEGAS_KERNEL_RESIDENT32_SMEM 0x400u    /* resident sweep, spins in shared memory */
 
 /* Fills *opt with the defaults listed above. */
 void vegas_default_options(vegas_options *opt);

@@ -97,6 +97,7 @@ struct vegas_ctx {
     uint32_t *d_queue = nullptr;
     ResidentArgs res{};
     int res_threads = 256, res_grid = 1;
+    bool res_smem_eligible = false;  // every instance's spins fit the shared-memory form
     int res_items = 0;          // instances of the resident and cluster sweeps
     bool res_policy = false;    // some sample has a policy table (kernel choice for the shapes)
     bool res_eligible = false, tuned = false;
@@ -212,14 +213,37 @@ int ilog2(int v) {
 // Block shape of the resident sweep: threads per block, as many blocks as fit (at most one
 // per instance), and the grouping of small instances (group_threads threads per instance of
 // at most group_sites sites, several per block; 0 = one instance per block).
-void set_resident_shape(vegas_ctx *c, int threads, int group_threads = 0, int group_sites = 0) {
-    c->res_threads = threads;
-    c->res_grid = (int)std::min<int64_t>((int64_t)c->res_items,
-                                         (int64_t)c->sm_count * resident_blocks_per_sm(threads, c->res_policy));
+// smem: each instance's spins in shared memory for the whole launch (512 or 1024 threads; a
+// group's region is then at most kResSmemBytes / (12 x groups) sites). Returns false, leaving
+// the spins in global memory, when that form does not fit the device.
+constexpr int64_t kResSmemBytes = 200 * 1024;  // spins in shared memory: 12 bytes per site
+
+bool set_resident_shape(vegas_ctx *c, int threads, int group_threads = 0, int group_sites = 0, bool smem = false) {
     const bool grouped = group_threads > 0 && group_threads < threads && threads % group_threads == 0 &&
                          threads / group_threads <= 15;
     c->res.group_threads = grouped ? group_threads : 0;
     c->res.group_sites = grouped ? group_sites : 0;
+    c->res.smem_sites = 0;
+    if (smem && c->res_smem_eligible) {
+        const int64_t ng = grouped ? threads / group_threads : 1;
+        if (grouped) c->res.group_sites = (int)std::min<int64_t>(group_sites, kResSmemBytes / (12 * ng));
+        c->res.smem_sites = c->max_instance_sites;
+        const size_t bytes = resident_smem_bytes(c->res, threads);
+        const int bps = resident_blocks_per_sm(threads, c->res_policy, bytes);
+        cudaGetLastError();
+        if (bps > 0) {
+            c->res_threads = threads;
+            c->res_grid = (int)std::min<int64_t>((int64_t)c->res_items, (int64_t)c->sm_count * bps);
+            return true;
+        }
+        c->res.smem_sites = 0;
+        c->res.group_sites = grouped ? group_sites : 0;
+        threads = std::min(threads, 512);
+    }
+    c->res_threads = threads;
+    c->res_grid = (int)std::min<int64_t>((int64_t)c->res_items,
+                                         (int64_t)c->sm_count * resident_blocks_per_sm(threads, c->res_policy));
+    return !smem;
 }
 
 // Shape of the cluster sweep: cs blocks of `threads` per cluster, as many clusters as fit,
@@ -463,6 +487,7 @@ extern "C" void vegas_default_options(vegas_options *o) {
     o->group_sites = 0;
     o->wave_lag = 0;
     o->wave_slab = 0;
+    o->resident_smem = 0;
 }
 
 // vegas_create without the exception guard; *made is the context under construction.
@@ -484,6 +509,9 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
                     "the wavefront sweep (variant 4) is FP32 with one sample, 32 replicas and no per-type statistics");
     if (o.wave_lag < 0) return fail(nullptr, VEGAS_EINVAL, "wave_lag must be >= 0");
     if (o.wave_slab < -1) return fail(nullptr, VEGAS_EINVAL, "wave_slab must be >= -1");
+    if (o.resident_smem < -1 || o.resident_smem > 1) return fail(nullptr, VEGAS_EINVAL, "resident_smem must be -1, 0 or 1");
+    if (o.resident_smem == 1 && o.variant != 1 && o.variant != -1)
+        return fail(nullptr, VEGAS_EINVAL, "resident_smem = 1 needs the resident sweep (variant 1 or automatic)");
     if (o.cluster_split < 0) return fail(nullptr, VEGAS_EINVAL, "cluster_split must be >= 0");
     if (o.group_threads != 0 && o.group_threads != 64 && o.group_threads != 128 && o.group_threads != 256)
         return fail(nullptr, VEGAS_EINVAL, "group_threads must be 0, 64, 128 or 256");
@@ -948,7 +976,16 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         c->res_policy = any_policy;
         ResidentArgs &ra = c->res;
         std::memset(&ra, 0, sizeof ra);
-        set_resident_shape(c, c->max_instance_sites >= 4096 ? 512 : 256, o.group_threads, o.group_sites);
+        c->res_smem_eligible = o.resident_smem >= 0 && 12 * (int64_t)c->max_instance_sites <= kResSmemBytes;
+        if (o.resident_smem == 1 && !c->res_smem_eligible) {
+            c->err = "resident_smem = 1: the largest instance does not fit in shared memory (12 bytes per site, at "
+                     "most " + std::to_string(kResSmemBytes / 12) + " sites)";
+            return bail(VEGAS_EINVAL);
+        }
+        if (o.resident_smem == 1)
+            set_resident_shape(c, 1024, o.group_threads, o.group_sites, true);
+        else
+            set_resident_shape(c, c->max_instance_sites >= 4096 ? 512 : 256, o.group_threads, o.group_sites);
         ra.spins = c->d_spins;
         ra.edges = c->d_edges;
         ra.row_ptr = c->d_rowptr;
@@ -1374,16 +1411,25 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                 struct Cand {
                     int v, a, b, split, group;  // sweep; threads (resident) or blocks per cluster,
                                                 // threads; cluster split; threads per small instance
+                    int sm = 0;                 // resident: spins in shared memory
                 };
                 std::vector<Cand> cand{{0, 0, 0, 0, 0}};
                 // instances of very different sizes (split and grouping candidates)
                 const bool uneven = c->res_items > 1 && 4 * (int64_t)c->min_instance_sites < c->max_instance_sites;
-                if (c->res_eligible) {
+                if (c->res_eligible && c->opt.resident_smem != 1) {
                     cand.push_back({1, 256, 0, 0, 0});
                     cand.push_back({1, 512, 0, 0, 0});
                     if (uneven) {  // small instances several to a block
                         cand.push_back({1, 512, 0, 0, 128});
                         cand.push_back({1, 512, 0, 0, 256});
+                    }
+                }
+                if (c->res_eligible && c->res_smem_eligible) {  // spins in shared memory
+                    cand.push_back({1, 1024, 0, 0, 0, 1});
+                    cand.push_back({1, 512, 0, 0, 0, 1});
+                    if (uneven) {
+                        cand.push_back({1, 1024, 0, 0, 128, 1});
+                        cand.push_back({1, 1024, 0, 0, 256, 1});
                     }
                 }
                 if (c->coop_eligible) cand.push_back({2, 0, 0, 0, 0});
@@ -1411,7 +1457,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     for (const Cand &vc : cand) {
                         const int v = vc.v;
                         // grouped instances: group_threads threads for up to 16 sites each per thread
-                        if (v == 1) set_resident_shape(c, vc.a, vc.group, vc.group * 16);
+                        if (v == 1 && !set_resident_shape(c, vc.a, vc.group, vc.group * 16, vc.sm != 0)) continue;
                         if (v == 3) {
                             if (!set_cluster_shape(c, vc.a, vc.b, vc.split)) continue;
                             c->res.group_threads = vc.group < vc.b ? vc.group : 0;
@@ -1442,7 +1488,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     }
                     c->variant = best_v;
                     if (best_v == 1)
-                        set_resident_shape(c, best_c.a, best_c.group, best_c.group * 16);
+                        set_resident_shape(c, best_c.a, best_c.group, best_c.group * 16, best_c.sm != 0);
                     else
                         set_resident_shape(c, rt_rule);
                     if (c->cluster_eligible) {
@@ -1835,7 +1881,7 @@ extern "C" vegas_status vegas_stats(const vegas_ctx *c, vegas_stats_t *o) {
         o->graph_launches = c->graph_launches;
         uint32_t kinds = 0;
         if (c->variant == 1)
-            kinds = VEGAS_KERNEL_RESIDENT32;
+            kinds = c->res.smem_sites > 0 ? VEGAS_KERNEL_RESIDENT32_SMEM : VEGAS_KERNEL_RESIDENT32;
         else if (c->variant == 2)
             kinds = VEGAS_KERNEL_COOP32;
         else if (c->variant == 3)

@@ -183,16 +183,18 @@ __device__ __forceinline__ float3 policy_trial32(const PolicySite32 ps, float si
         const float sh = __fmul_rn(u23(rw.x), h);
         const float z = __fsub_rn(1.0f, sh);
         const float r = sqrtf(fmaxf(__fmul_rn(sh, __fsub_rn(2.0f, sh)), 0.0f));
-        float3 e1;
-        const float ax = fabsf(u.x), ay = fabsf(u.y), az = fabsf(u.z);
-        if (ax <= ay && ax <= az)
-            e1 = unit32(0.f, -u.z, u.y);
-        else if (ay <= az)
-            e1 = unit32(u.z, 0.f, -u.x);
-        else
-            e1 = unit32(-u.y, u.x, 0.f);
-        const float3 e2 = make_float3(fmaf(u.y, e1.z, -__fmul_rn(u.z, e1.y)), fmaf(u.z, e1.x, -__fmul_rn(u.x, e1.z)),
-                                      fmaf(u.x, e1.y, -__fmul_rn(u.y, e1.x)));
+        // orthonormal frame (e1, e2, u) without branches (Duff, Burgess, Christensen, Hery,
+        // Kensler, Liani, Villemin, "Building an orthonormal basis, revisited", JCGT 6(1),
+        // 2017): with s = sign(u_z) and a = -1 / (s + u_z), e1 = (1 + s a u_x^2, s a u_x u_y,
+        // -s u_x), e2 = (a u_x u_y, s + a u_y^2, -u_y); |s + u_z| >= 1, so nothing diverges
+        // between the lanes of a warp. The azimuth is uniform, so the frame's orientation
+        // about u does not change the law of the trial.
+        const float sgn = copysignf(1.0f, u.z);
+        const float am = __fdividef(-1.0f, __fadd_rn(sgn, u.z));
+        const float b = __fmul_rn(__fmul_rn(u.x, u.y), am);
+        const float3 e1 = make_float3(fmaf(__fmul_rn(sgn, __fmul_rn(u.x, u.x)), am, 1.0f), __fmul_rn(sgn, b),
+                                      -__fmul_rn(sgn, u.x));
+        const float3 e2 = make_float3(b, fmaf(__fmul_rn(u.y, u.y), am, sgn), -u.y);
         const float x = __fmul_rn(r, cphi), y = __fmul_rn(r, sphi);
         return make_float3(__fmul_rn(sn, fmaf(x, e1.x, fmaf(y, e2.x, __fmul_rn(z, u.x)))),
                            __fmul_rn(sn, fmaf(x, e1.y, fmaf(y, e2.y, __fmul_rn(z, u.y)))),
@@ -200,7 +202,7 @@ __device__ __forceinline__ float3 policy_trial32(const PolicySite32 ps, float si
     }
     // Gaussian (fixed width) or adaptive (the instance's width): direction of u + sigma g
     const float sg = code == kPolAdaptive ? sigma : ps.par;
-    const float rad = sqrtf(-2.0f * logf(__fsub_rn(1.0f, u23(rw.x))));  // 1 - u in (0, 1]
+    const float rad = sqrtf(__fmul_rn(-2.0f, __logf(__fsub_rn(1.0f, u23(rw.x)))));  // 1 - u in (0, 1]
     // (2k + 1) 2^-23 - 1 lies strictly inside (-1, 1); sqrt 2 erfinv of it is standard normal
     const float g2 = __fmul_rn(1.41421356237310f, erfinvf(fmaf(u23(rw.w), 2.0f, -1.0f + 0x1p-23f)));
     const float3 v = unit32(fmaf(sg, __fmul_rn(rad, cphi), u.x), fmaf(sg, __fmul_rn(rad, sphi), u.y), fmaf(sg, g2, u.z));

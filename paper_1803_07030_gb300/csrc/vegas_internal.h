@@ -273,6 +273,9 @@ struct ResidentArgs {
                                // one block each (0: every instance by a whole cluster)
     int32_t group_threads;     // > 0: a block sweeps instances of at most group_sites sites
     int32_t group_sites;       // NT / group_threads at a time, group_threads threads each
+    int32_t smem_sites;        // resident sweep: > 0 keeps each instance's spins in shared memory
+                               // for the whole launch (room for this many sites per block, or
+                               // group_sites per group); 0 reads and writes them in global memory
 };
 
 // Grid barrier of the cooperative sweep (zeroed before every launch).
@@ -354,7 +357,10 @@ void launch_snapshot(const void *spins, void *snap, int64_t n16, const RunState 
 // Cooperative launch (all blocks co-resident); returns the CUDA error of the launch.
 int launch_coop(const CoopArgs &a, int grid, void *stream);
 int coop_blocks_per_sm(bool pol);
-int resident_blocks_per_sm(int threads, bool pol);
+// Blocks of the resident sweep per SM (smem_bytes > 0: the shared-memory form, whose limit
+// is raised here; 0 when it does not fit).
+int resident_blocks_per_sm(int threads, bool pol, size_t smem_bytes = 0);
+size_t resident_smem_bytes(const ResidentArgs &a, int threads);
 // Cluster sweep: n_clusters clusters of cs blocks of `threads` (256 or 512); returns the CUDA
 // error of the launch.
 int launch_cluster(const ResidentArgs &a, int n_clusters, int cs, int threads, void *stream);

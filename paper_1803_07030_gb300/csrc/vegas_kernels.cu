@@ -399,6 +399,57 @@ __device__ bool direct_row_ok(const PassArgs &a, int g, uint32_t orig) {
 }
 #endif
 
+// The same attempt with the instance's spins in shared memory (resident sweep with spins kept
+// on chip for the whole step): sp holds x, y, z of the instance's sites in three arrays of
+// cap floats, site g at g - g0. Neighbour values, the field's row order and every rounding
+// are those of direct_attempt, so the results are bit for bit the same.
+template <int POL>
+__device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const int2 *E, const int64_t *row_ptr, int g,
+                                             int lower_end, uint32_t orig, const Site32 &p, float beta, float B,
+                                             uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1, Acc32 &acc,
+                                             bool &nan_seen, const PolicySite32 *pol, float sigma, float4 &Sq) {
+    const int i = g - g0;
+    const float4 Si = make_float4(sp[i], sp[cap + i], sp[2 * cap + i], 0.f);
+    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+    const int64_t e0 = __ldg(row_ptr + g), e1 = __ldg(row_ptr + g + 1);
+    const int deg = (int)(e1 - e0);
+    if (deg <= kDirectRow) {
+        int2 ed[kDirectRow];
+#pragma unroll
+        for (int k = 0; k < kDirectRow; ++k)
+            if (k < deg) ed[k] = __ldg(E + e0 + k);
+#pragma unroll
+        for (int k = 0; k < kDirectRow; ++k)
+            if (k < deg) {
+                const int j = ed[k].x - g0;
+                link32(make_float4(sp[j], sp[cap + j], sp[2 * cap + j], 0.f), __int_as_float(ed[k].y),
+                       ed[k].x < lower_end, hx, hy, hz, lx, ly, lz);
+            }
+    } else {
+        for (int64_t e = e0; e < e1; ++e) {
+            const int2 ed = __ldg(E + e);
+            const int j = ed.x - g0;
+            link32(make_float4(sp[j], sp[cap + j], sp[2 * cap + j], 0.f), __int_as_float(ed.y), ed.x < lower_end, hx,
+                   hy, hz, lx, ly, lz);
+        }
+    }
+    const uint4 rw = philox10(make_uint4(orig, t, inst, kPurposeTrial32), k0, k1);
+    const float3 P = POL ? policy_trial32(pol[g], sigma, Si, p.sn, rw) : trial_random32(rw, p.sn);
+    float4 Sn;
+    bool ok, bad;
+    float e_i;
+    attempt32<2, 2>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, P, rw.z, Sn, ok, e_i, bad);
+    nan_seen |= bad;
+    if (ok) {
+        sp[i] = Sn.x;
+        sp[cap + i] = Sn.y;
+        sp[2 * cap + i] = Sn.z;
+    }
+    acc.add(e_i, Sn, ok);
+    Sq = Sn;
+    return ok;
+}
+
 // ------------------------------------------------------------------ FP32 colour pass (direct)
 // Any row length: reads row_ptr and gathers neighbours with plain loads.
 // PM: params_mode (0 uniform without anisotropy, 1 uniform, 2 per site).
@@ -469,10 +520,13 @@ __device__ __forceinline__ void group_sync(int bar, int nthreads) {
 }
 
 
-template <int NT, int POL>
+// SM = 1: the instance's spins are copied into shared memory (sp, three arrays of cap floats)
+// before the first MCS, every attempt reads and writes them there, and they are copied back
+// after the last MCS of the launch; only the links and parameters come from L2 and HBM.
+template <int NT, int POL, int SM = 0>
 __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, const ResidentInst &I, double (*s_red)[4], uint32_t *s_acc,
                                      double (*s_tm)[kResidentMaxTypes][3], bool &nan_seen, int gtid, int gthreads,
-                                     int gbar) {
+                                     int gbar, float *sp = nullptr, int cap = 0) {
     float4 *S = (float4 *)a.spins;
     const int2 *E = (const int2 *)a.edges;
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
@@ -486,6 +540,16 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
     const double *sc = rs->sched + ((int64_t)step * a.n_inst + I.inst_local) * 2;
     const float beta = (float)sc[0], B = (float)sc[1];
     const uint32_t inst = (uint32_t)I.inst_id;
+    if (SM) {  // the instance's spins into shared memory
+        for (int g = I.g_begin + gtid; g < I.g_end; g += gthreads) {
+            const float4 v = S[(int64_t)g * R + I.r];
+            const int i = g - I.g_begin;
+            sp[i] = v.x;
+            sp[cap + i] = v.y;
+            sp[2 * cap + i] = v.z;
+        }
+        group_sync(gbar, gthreads);
+    }
     for (int m = 0; m < a.mcs; ++m) {
         const uint32_t t = t0 + (uint32_t)m;
         const bool log_accepts = a.alog && t < a.alog_mcs;
@@ -501,8 +565,11 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
                 // add signed zeros only, so spins and decisions equal the specialised paths'
                 const Site32 p = resident_params(a, I, g);
                 float4 Sq;
-                const bool ok = direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, I.r, R, sg.z, orig, p, beta, B, t,
-                                                          inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq);
+                const bool ok =
+                    SM ? smem_attempt<POL>(sp, cap, I.g_begin, E, a.row_ptr, g, sg.z, orig, p, beta, B, t, inst, k0, k1,
+                                           acc, nan_seen, a.pol, sigma, Sq)
+                       : direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, I.r, R, sg.z, orig, p, beta, B, t, inst, k0, k1,
+                                                   acc, nan_seen, a.pol, sigma, Sq);
                 tm[0] = __fadd_rn(tm[0], Sq.x);
                 tm[1] = __fadd_rn(tm[1], Sq.y);
                 tm[2] = __fadd_rn(tm[2], Sq.z);
@@ -568,15 +635,23 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
         }
         group_sync(gbar, gthreads);
     }
+    if (SM)  // the last MCS ended at a barrier: its spins go back to global memory
+        for (int g = I.g_begin + gtid; g < I.g_end; g += gthreads) {
+            const int i = g - I.g_begin;
+            S[(int64_t)g * R + I.r] = make_float4(sp[i], sp[cap + i], sp[2 * cap + i], 0.f);
+        }
 }
 
 // Draws instances from the queue and sweeps them until it is empty (first >= 0: start with
 // that one). An instance of at most group_sites sites comes with NT / group_threads - 1 more
 // (the queue is largest first, so they are no larger), and the block sweeps them at once,
 // a group of group_threads threads each; larger instances take the whole block.
-template <int NT, int POL>
+// SM = 1: spins in shared memory, dyn: the block's dynamic shared memory (a group gi of ng
+// takes region gi of a.group_sites sites, a whole-block instance all a.smem_sites).
+template <int NT, int POL, int SM = 0>
 __device__ __forceinline__ void resident_loop(const ResidentArgs &a, int first, double (*s_red)[4], uint32_t *s_acc,
-                                              double (*s_tm)[kResidentMaxTypes][3], int *s_items, bool &nan_seen) {
+                                              double (*s_tm)[kResidentMaxTypes][3], int *s_items, bool &nan_seen,
+                                              float *dyn = nullptr) {
     const int GT = a.group_threads;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -599,8 +674,9 @@ __device__ __forceinline__ void resident_loop(const ResidentArgs &a, int first, 
         const int gt = NT / ng, gi = (int)threadIdx.x / gt, item = s_items[gi];
         if (item < a.n_items) {
             const ResidentInst I = a.insts[item];
-            resident_sweep_block<NT, POL>(a, I, s_red, s_acc, s_tm, nan_seen, (int)threadIdx.x - gi * gt, gt,
-                                          ng == 1 ? 0 : 1 + gi);
+            const int cap = ng == 1 ? a.smem_sites : a.group_sites;
+            resident_sweep_block<NT, POL, SM>(a, I, s_red, s_acc, s_tm, nan_seen, (int)threadIdx.x - gi * gt, gt,
+                                              ng == 1 ? 0 : 1 + gi, SM ? dyn + (size_t)gi * 3 * cap : nullptr, cap);
         }
         __syncthreads();  // every group is done before the items are drawn again
     }
@@ -614,14 +690,15 @@ __device__ __noinline__ void resident_loop_call(const ResidentArgs &a, int first
     resident_loop<NT, POL>(a, first, s_red, s_acc, s_tm, s_items, nan_seen);
 }
 
-template <int NT, int POL>
+template <int NT, int POL, int SM = 0>
 __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
     __shared__ int s_items[NT / 32 + 1];  // the instances drawn (one per group) and their count
     __shared__ double s_red[NT / 32][4];
     __shared__ uint32_t s_acc[NT / 32];
     __shared__ double s_tm[NT / 32][kResidentMaxTypes][3];  // per warp and type, segment order
+    extern __shared__ float res_dyn[];                       // SM: the instances' spins
     bool nan_seen = false;
-    resident_loop<NT, POL>(a, -1, s_red, s_acc, s_tm, s_items, nan_seen);
+    resident_loop<NT, POL, SM>(a, -1, s_red, s_acc, s_tm, s_items, nan_seen, res_dyn);
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }
 
@@ -1212,14 +1289,35 @@ int coop_blocks_per_sm(bool pol) {
 
 using ResFn = void (*)(ResidentArgs);
 
-ResFn select_resident(int threads, bool pol) {
+// Spins in global memory: 256 or 512 threads; in shared memory (smem = 1): 512 or 1024.
+ResFn select_resident(int threads, bool pol, bool smem) {
+    if (smem) {
+        if (threads >= 1024) return pol ? resident32_kernel<1024, 1, 1> : resident32_kernel<1024, 0, 1>;
+        return pol ? resident32_kernel<512, 1, 1> : resident32_kernel<512, 0, 1>;
+    }
     if (threads >= 512) return pol ? resident32_kernel<512, 1> : resident32_kernel<512, 0>;
     return pol ? resident32_kernel<256, 1> : resident32_kernel<256, 0>;
 }
 
+int resident_threads(int threads, bool smem) {
+    if (smem) return threads >= 1024 ? 1024 : 512;
+    return threads >= 512 ? 512 : 256;
+}
+
+// Dynamic shared memory of the resident sweep: three floats per site of the largest region
+// (a whole-block instance, or all groups' regions together).
+size_t resident_smem_bytes(const ResidentArgs &a, int threads) {
+    if (a.smem_sites <= 0) return 0;
+    const int nt = resident_threads(threads, true);
+    const int ng = a.group_threads > 0 && a.group_threads < nt ? nt / a.group_threads : 1;
+    const int64_t sites = std::max<int64_t>(a.smem_sites, ng > 1 ? (int64_t)ng * a.group_sites : 0);
+    return (size_t)sites * 3 * sizeof(float);
+}
+
 void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream) {
-    const int nt = threads >= 512 ? 512 : 256;
-    select_resident(nt, a.pol != nullptr)<<<grid, nt, 0, (cudaStream_t)stream>>>(a);
+    const bool smem = a.smem_sites > 0;
+    const int nt = resident_threads(threads, smem);
+    select_resident(nt, a.pol != nullptr, smem)<<<grid, nt, resident_smem_bytes(a, threads), (cudaStream_t)stream>>>(a);
 }
 
 using ClusterFn = void (*)(ResidentArgs);
@@ -1262,11 +1360,15 @@ int cluster_capacity(int cs, int threads, bool pol) {
     return n;
 }
 
-int resident_blocks_per_sm(int threads, bool pol) {
+int resident_blocks_per_sm(int threads, bool pol, size_t smem_bytes) {
     int nb = 0;
-    const int nt = threads >= 512 ? 512 : 256;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_resident(nt, pol), nt, 0);
-    return nb > 0 ? nb : 1;
+    const bool smem = smem_bytes > 0;
+    const int nt = resident_threads(threads, smem);
+    const ResFn k = select_resident(nt, pol, smem);
+    if (smem && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess)
+        return 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, nt, smem_bytes);
+    return nb > 0 ? nb : (smem ? 0 : 1);
 }
 
 int pass_blocks_per_sm(int precision, const PassArgs &a) {

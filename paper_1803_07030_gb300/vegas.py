@@ -45,7 +45,7 @@ class vegas_sample(C.Structure):
 # bits of vegas_stats_t.sweep_kernels (VEGAS_KERNEL_*)
 KERNEL_BITS = {"pass64": 0x1, "pass32_direct": 0x2, "pass32_staged": 0x4, "pass32_r32": 0x8,
                "pass32_r32_policy": 0x10, "resident32": 0x20, "coop32": 0x40, "cluster32": 0x80, "wave32": 0x100,
-               "pass32_r32_one_policy": 0x200}
+               "pass32_r32_one_policy": 0x200, "resident32_smem": 0x400}
 
 
 def sweep_kernel_names(bits: int) -> list:
@@ -83,7 +83,7 @@ class vegas_options(C.Structure):
         ("cluster_split", C.c_int32),
         ("wave_lag", C.c_int32),
         ("wave_slab", C.c_int32),
-        ("pad_", C.c_int32),
+        ("resident_smem", C.c_int32),
     ]
 
 
@@ -449,7 +449,8 @@ class Context:
     variant (-1 automatic, 0 per class, 1 resident, 2 cooperative, 3 cluster, 4 wavefront),
     graphs (1 a run as one graph, 2 a graph per step, 0 none), the cluster and grouping shapes
     (cluster_blocks, cluster_threads, cluster_split, group_threads, group_sites; 0 =
-    automatic or off), wave_lag, wave_slab, and the testing options max_blocks, pipeline_depth,
+    automatic or off), wave_lag, wave_slab, resident_smem (1: the resident sweep keeps spins in
+    shared memory), and the testing options max_blocks, pipeline_depth,
     timeout_ns, fault_inject. library: load another build (the debug build) for this and
     later contexts.
     """
@@ -460,7 +461,7 @@ class Context:
                  pipeline_depth: int = 0, timeout_ns: int = 0, fault_inject: int = 0,
                  type_stats: bool = False, snapshots: bool = False, cluster_blocks: int = 0,
                  cluster_threads: int = 0, cluster_split: int = 0, group_threads: int = 0, group_sites: int = 0,
-                 wave_lag: int = 0, wave_slab: int = 0, library: Optional[str] = None):
+                 wave_lag: int = 0, wave_slab: int = 0, resident_smem: int = 0, library: Optional[str] = None):
         self.samples = list(samples)
         self.n_sites = [int(np.asarray(s.row_ptr).shape[0] - 1) for s in self.samples]
         if library is not None:
@@ -489,6 +490,7 @@ class Context:
         o.group_sites = group_sites
         o.wave_lag = wave_lag
         o.wave_slab = wave_slab
+        o.resident_smem = resident_smem
         o.cuda_stream = _current_stream() if stream == "torch" else stream
         self.replicas = replicas
         self.ptr = None

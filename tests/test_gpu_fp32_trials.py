@@ -91,7 +91,7 @@ def test_fp32_renormalisation_rounds_like_the_fp64_formula(norm):
     s.spin_norm = np.full(n, norm)
     rng = np.random.default_rng(5)
     cases = [1e-7, -1e-4, 2.0 ** -11, -0.5, 2.0]  # |S| / s - 1 up to these (sign included)
-    R = len(cases) + 1
+    R = 8  # the five cases, then unperturbed spins
     starts = []
     for k in range(R):
         d = np.tile([0.0, 0.0, 1.0], (n, 1)) + rng.normal(0.0, 1e-4, size=(n, 3))

@@ -235,6 +235,59 @@ def test_resident_sweep_equals_per_class_sweep(R):
         assert np.array_equal(a.accept_log(), b.accept_log())
 
 
+@pytest.mark.parametrize("R", [1, 4])
+def test_resident_sweep_with_spins_in_shared_memory(R):
+    """The resident sweep with each instance's spins in shared memory for the whole step equals
+    the per-class sweep bit for bit (spins, accept log) across runs and steps."""
+    samples = _uneven_batch()
+    n = len(samples) * R
+    T = np.stack([np.linspace(0.3, 2.5, 3) * (1 + 0.05 * i) for i in range(n)])
+    B = np.stack([np.array([0.4, -0.2, 0.1]) * (1 + 0.1 * i) for i in range(n)])
+    with ctx(samples, replicas=R, seed=13, variant=0, accept_log_mcs=3) as a, \
+            ctx(samples, replicas=R, seed=13, variant=1, resident_smem=1, accept_log_mcs=3) as b:
+        a.run(T, B, 7)
+        b.run(T[:, :1], B[:, :1], 7)
+        b.run(T[:, 1:], B[:, 1:], 7)
+        st = b.stats()
+        assert vb.sweep_kernel_names(st["sweep_kernels"]) == ["resident32_smem"] and st["block_threads"] == 1024
+        for i in range(n):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+        for i in range(n):
+            assert_fp32_history_close(a.history()[i], b.history()[i], samples[i // R].n_sites)
+        assert np.array_equal(a.accept_log(), b.accept_log())
+
+
+def test_resident_shared_memory_groups_policies_and_types():
+    """Small instances several to a block, each group with its own region of shared memory,
+    with update policies (adaptive width included) and per-type statistics."""
+    ps = nanoparticle_batch(9, seed=14, r_max=8.0)
+    for p in ps:
+        p.type = (np.arange(p.n_sites) % 2).astype(np.int32)
+        p.with_policy([oracle.ADAPTIVE, oracle.HINZKE_NOWAK], [0.8, 0.4])
+    T = np.linspace(0.4, 2.0, 2 * len(ps))[:, None] * np.array([[1.0, 0.8]])
+    B = np.full_like(T, 0.1)
+    with ctx(ps, replicas=2, seed=30, variant=1, resident_smem=1, group_threads=128, group_sites=600,
+             type_stats=True) as a, ctx(ps, replicas=2, seed=30, variant=0, type_stats=True) as b:
+        a.run(T, B, 6)
+        b.run(T, B, 6)
+        st = a.stats()
+        assert vb.sweep_kernel_names(st["sweep_kernels"]) == ["resident32_smem"]
+        assert st["group_threads"] == 128 and 0 < st["group_sites"] <= 600
+        for i in range(2 * len(ps)):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+        n = max(p.n_sites for p in ps)
+        assert np.all(np.abs(a.history() - b.history()) <= 1e-6 * n)
+        assert np.all(np.abs(a.type_history() - b.type_history()) <= 1e-6 * n)
+        assert np.array_equal(a.accept_history(), b.accept_history())
+        assert np.array_equal(a.adaptive_width(), b.adaptive_width())
+
+
+def test_resident_shared_memory_refuses_instances_that_do_not_fit():
+    with pytest.raises(vb.VegasError) as e:
+        ctx([sc_periodic(30)], variant=1, resident_smem=1)  # 27,000 sites x 12 bytes
+    assert e.value.status == vb.EINVAL and "shared memory" in str(e.value)
+
+
 def test_resident_split_runs_and_autotune():
     samples = _uneven_batch()
     T = np.linspace(0.5, 2.0, len(samples))[:, None] * np.ones((1, 2))
