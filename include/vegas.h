@@ -198,11 +198,14 @@ typedef struct {
                                width in position units, 0 automatic (slabs of about 16384 sites
                                per plane; whole planes when they are no larger), -1 whole planes.
                                Default 0. */
-    int32_t resident_smem;  /* resident sweep (variant 1): 1 keeps each instance's spins in
-                               shared memory for all MCS of a step (12 bytes per site; instances of
-                               at most 17066 sites; 512 or 1024 threads per block), -1 never, 0 the
-                               automatic choice times it beside the other shapes (with variant 1
-                               fixed: global memory). Default 0. */
+    int32_t resident_smem;  /* resident and cluster sweeps (variants 1, 3): 1 keeps the spins
+                               in shared memory for all MCS of a step (12 bytes per site; instances
+                               of at most 17066 sites): the resident sweep holds each instance in its
+                               block (512 or 1024 threads), the cluster sweep a copy of it in every
+                               block of the cluster, an accepted spin written to every copy through
+                               distributed shared memory; -1 never; 0 the automatic choice times it
+                               beside the other shapes (with variant 1 or 3 fixed: global memory).
+                               Default 0. */
 } vegas_options;
 
 typedef struct {
@@ -253,6 +256,8 @@ typedef struct {
 #define VEGAS_KERNEL_PASS32_R32_ONE_POLICY 0x200u /* 32 replicas per site, compiled for the one
                                                      update policy of every site of the class */
 #define VEGAS_KERNEL_RESIDENT32_SMEM 0x400u    /* resident sweep, spins in shared memory */
+#define VEGAS_KERNEL_CLUSTER32_SMEM 0x800u     /* cluster sweep, spins copied in every block's
+                                                  shared memory */
 
 /* Fills *opt with the defaults listed above. */
 void vegas_default_options(vegas_options *opt);

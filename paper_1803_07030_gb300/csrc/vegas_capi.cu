@@ -98,6 +98,8 @@ struct vegas_ctx {
     ResidentArgs res{};
     int res_threads = 256, res_grid = 1;
     bool res_smem_eligible = false;  // every instance's spins fit the shared-memory form
+    bool res_smem = false;           // the resident sweep keeps spins in shared memory
+    bool cluster_smem = false;       // the cluster sweep keeps copies of the spins in shared memory
     int res_items = 0;          // instances of the resident and cluster sweeps
     bool res_policy = false;    // some sample has a policy table (kernel choice for the shapes)
     bool res_eligible = false, tuned = false;
@@ -223,21 +225,20 @@ bool set_resident_shape(vegas_ctx *c, int threads, int group_threads = 0, int gr
                          threads / group_threads <= 15;
     c->res.group_threads = grouped ? group_threads : 0;
     c->res.group_sites = grouped ? group_sites : 0;
-    c->res.smem_sites = 0;
+    c->res_smem = false;
     if (smem && c->res_smem_eligible) {
-        const int64_t ng = grouped ? threads / group_threads : 1;
-        if (grouped) c->res.group_sites = (int)std::min<int64_t>(group_sites, kResSmemBytes / (12 * ng));
-        c->res.smem_sites = c->max_instance_sites;
-        const size_t bytes = resident_smem_bytes(c->res, threads);
-        const int bps = resident_blocks_per_sm(threads, c->res_policy, bytes);
+        ResidentArgs a = c->res;
+        if (grouped) a.group_sites = (int)std::min<int64_t>(group_sites, kResSmemBytes / (12 * (threads / group_threads)));
+        a.smem_sites = c->max_instance_sites;
+        const int bps = resident_blocks_per_sm(threads, c->res_policy, resident_smem_bytes(a, threads));
         cudaGetLastError();
         if (bps > 0) {
+            c->res.group_sites = a.group_sites;
+            c->res_smem = true;
             c->res_threads = threads;
             c->res_grid = (int)std::min<int64_t>((int64_t)c->res_items, (int64_t)c->sm_count * bps);
             return true;
         }
-        c->res.smem_sites = 0;
-        c->res.group_sites = grouped ? group_sites : 0;
         threads = std::min(threads, 512);
     }
     c->res_threads = threads;
@@ -247,16 +248,31 @@ bool set_resident_shape(vegas_ctx *c, int threads, int group_threads = 0, int gr
 }
 
 // Shape of the cluster sweep: cs blocks of `threads` per cluster, as many clusters as fit,
-// and instances of at most `split` sites swept by one block each (0: all by clusters);
+// instances of at most `split` sites swept by one block each (0: all by clusters), those of at
+// most group_sites sites several to a block in groups of group_threads threads (-1: the
+// grouping already set), and with smem every block's copy of the spins in shared memory;
 // false (shape unchanged) if no such cluster fits.
-bool set_cluster_shape(vegas_ctx *c, int cs, int threads, int split = 0) {
-    const int cap = cluster_capacity(cs, threads, c->res_policy);
+bool set_cluster_shape(vegas_ctx *c, int cs, int threads, int split = 0, int group_threads = -1, int group_sites = 0,
+                       bool smem = false) {
+    if (smem && !c->res_smem_eligible) return false;
+    ResidentArgs a = c->res;
+    if (group_threads >= 0) {
+        a.group_threads = group_threads > 0 && group_threads < threads ? group_threads : 0;
+        a.group_sites = a.group_threads > 0 ? group_sites : 0;
+    }
+    if (smem && a.group_threads > 0)
+        a.group_sites = (int)std::min<int64_t>(a.group_sites, kResSmemBytes / (12 * (threads / a.group_threads)));
+    a.smem_sites = smem ? c->max_instance_sites : 0;
+    const int cap = cluster_capacity(cs, threads, c->res_policy, cluster_smem_bytes(a, threads));
     cudaGetLastError();
     if (cap <= 0) return false;
     c->cluster_cs = cs;
     c->cluster_threads = threads;
     c->cluster_n = (int)std::min<int64_t>((int64_t)c->res_items, cap);
+    c->cluster_smem = smem;
     c->res.split_sites = split;
+    c->res.group_threads = a.group_threads;
+    c->res.group_sites = a.group_sites;
     return true;
 }
 
@@ -283,6 +299,7 @@ void enqueue_resident(vegas_ctx *c, cudaStream_t st, int32_t n) {
     cudaMemsetAsync(c->d_queue, 0, sizeof(uint32_t), st);
     ResidentArgs a = c->res;
     a.mcs = n;
+    a.smem_sites = c->res_smem ? c->max_instance_sites : 0;
     launch_resident(a, c->res_grid, c->res_threads, st);
     launch_advance(c->d_run, n, st);
 }
@@ -301,6 +318,7 @@ void enqueue_cluster(vegas_ctx *c, cudaStream_t st, int32_t n) {
     cudaMemsetAsync(c->d_queue, 0, sizeof(uint32_t), st);
     ResidentArgs a = c->res;
     a.mcs = n;
+    a.smem_sites = c->cluster_smem ? c->max_instance_sites : 0;
     launch_cluster(a, c->cluster_n, c->cluster_cs, c->cluster_threads, st);
     launch_advance(c->d_run, n, st);
 }
@@ -510,8 +528,8 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
     if (o.wave_lag < 0) return fail(nullptr, VEGAS_EINVAL, "wave_lag must be >= 0");
     if (o.wave_slab < -1) return fail(nullptr, VEGAS_EINVAL, "wave_slab must be >= -1");
     if (o.resident_smem < -1 || o.resident_smem > 1) return fail(nullptr, VEGAS_EINVAL, "resident_smem must be -1, 0 or 1");
-    if (o.resident_smem == 1 && o.variant != 1 && o.variant != -1)
-        return fail(nullptr, VEGAS_EINVAL, "resident_smem = 1 needs the resident sweep (variant 1 or automatic)");
+    if (o.resident_smem == 1 && o.variant != 1 && o.variant != 3 && o.variant != -1)
+        return fail(nullptr, VEGAS_EINVAL, "resident_smem = 1 needs the resident or cluster sweep (variant 1, 3 or automatic)");
     if (o.cluster_split < 0) return fail(nullptr, VEGAS_EINVAL, "cluster_split must be >= 0");
     if (o.group_threads != 0 && o.group_threads != 64 && o.group_threads != 128 && o.group_threads != 256)
         return fail(nullptr, VEGAS_EINVAL, "group_threads must be 0, 64, 128 or 256");
@@ -1025,7 +1043,8 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
             }
             c->cluster_threads = nt;
             if (cap > 0) {
-                c->cluster_eligible = set_cluster_shape(c, cs, nt, o.cluster_split);
+                c->cluster_eligible = set_cluster_shape(c, cs, nt, o.cluster_split, -1, 0,
+                                                        o.variant == 3 && o.resident_smem == 1);
             }
             cudaGetLastError();  // an unsupported cluster shape only makes the sweep ineligible
         }
@@ -1445,6 +1464,14 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                                 cand.push_back({3, 2, 512, sp, 128});
                                 cand.push_back({3, 4, 256, sp, 0});
                             }
+                    if (c->res_smem_eligible) {  // every block's copy of the spins in shared memory
+                        cand.push_back({3, 2, 512, uneven ? big / 2 : 0, 0, 1});
+                        cand.push_back({3, 4, 512, uneven ? big / 4 : 0, 0, 1});
+                        if (uneven) {
+                            cand.push_back({3, 2, 512, big / 2, 128, 1});
+                            cand.push_back({3, 4, 512, big / 4, 128, 1});
+                        }
+                    }
                 }
                 // longer probes when the step allows (less noise between close candidates), at most
                 // a quarter of the step
@@ -1458,11 +1485,8 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                         const int v = vc.v;
                         // grouped instances: group_threads threads for up to 16 sites each per thread
                         if (v == 1 && !set_resident_shape(c, vc.a, vc.group, vc.group * 16, vc.sm != 0)) continue;
-                        if (v == 3) {
-                            if (!set_cluster_shape(c, vc.a, vc.b, vc.split)) continue;
-                            c->res.group_threads = vc.group < vc.b ? vc.group : 0;
-                            c->res.group_sites = c->res.group_threads * 16;
-                        }
+                        if (v == 3 && !set_cluster_shape(c, vc.a, vc.b, vc.split, vc.group, vc.group * 16, vc.sm != 0))
+                            continue;
                         cudaEvent_t x0, x1;
                         CK(c, cudaEventCreate(&x0));
                         CK(c, cudaEventCreate(&x1));
@@ -1487,19 +1511,16 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                         if (e4) break;  // report the device error below
                     }
                     c->variant = best_v;
+                    // the shape of the sweep kept goes last: the two persistent sweeps share the
+                    // grouping of small instances
+                    if (c->cluster_eligible && best_v != 3) set_cluster_shape(c, cs_rule, ct_rule, 0, 0, 0);
                     if (best_v == 1)
                         set_resident_shape(c, best_c.a, best_c.group, best_c.group * 16, best_c.sm != 0);
                     else
                         set_resident_shape(c, rt_rule);
-                    if (c->cluster_eligible) {
-                        if (best_v == 3) {
-                            set_cluster_shape(c, best_c.a, best_c.b, best_c.split);
-                            c->res.group_threads = best_c.group < best_c.b ? best_c.group : 0;
-                            c->res.group_sites = c->res.group_threads * 16;
-                        } else {
-                            set_cluster_shape(c, cs_rule, ct_rule);
-                        }
-                    }
+                    if (best_v == 3)
+                        set_cluster_shape(c, best_c.a, best_c.b, best_c.split, best_c.group, best_c.group * 16,
+                                          best_c.sm != 0);
                 }
                 c->tuned = true;
             }
@@ -1881,11 +1902,11 @@ extern "C" vegas_status vegas_stats(const vegas_ctx *c, vegas_stats_t *o) {
         o->graph_launches = c->graph_launches;
         uint32_t kinds = 0;
         if (c->variant == 1)
-            kinds = c->res.smem_sites > 0 ? VEGAS_KERNEL_RESIDENT32_SMEM : VEGAS_KERNEL_RESIDENT32;
+            kinds = c->res_smem ? VEGAS_KERNEL_RESIDENT32_SMEM : VEGAS_KERNEL_RESIDENT32;
         else if (c->variant == 2)
             kinds = VEGAS_KERNEL_COOP32;
         else if (c->variant == 3)
-            kinds = VEGAS_KERNEL_CLUSTER32;
+            kinds = c->cluster_smem ? VEGAS_KERNEL_CLUSTER32_SMEM : VEGAS_KERNEL_CLUSTER32;
         else if (c->variant == 4)
             kinds = VEGAS_KERNEL_WAVE32;
         else

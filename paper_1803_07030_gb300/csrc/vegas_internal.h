@@ -365,7 +365,10 @@ size_t resident_smem_bytes(const ResidentArgs &a, int threads);
 // error of the launch.
 int launch_cluster(const ResidentArgs &a, int n_clusters, int cs, int threads, void *stream);
 // Clusters of cs blocks of `threads` that fit on the device at once (0 when none or on error).
-int cluster_capacity(int cs, int threads, bool pol);
+// Clusters of cs blocks that fit at once (smem_bytes > 0: the form with spins in shared
+// memory, whose limit is raised here); 0 when none fits.
+int cluster_capacity(int cs, int threads, bool pol, size_t smem_bytes = 0);
+size_t cluster_smem_bytes(const ResidentArgs &a, int threads);
 
 // Wavefront sweep: launch of `grid` blocks of kThreads; returns the CUDA error of the launch.
 // wave_blocks_per_sm is the occupancy of its kernel for a parameter mode.

@@ -684,10 +684,11 @@ __device__ __forceinline__ void resident_loop(const ResidentArgs &a, int first, 
 
 // The same as a separate function, for the cluster sweep's second phase: its registers are
 // then allocated apart from the cluster phase's.
-template <int NT, int POL>
+template <int NT, int POL, int SM = 0>
 __device__ __noinline__ void resident_loop_call(const ResidentArgs &a, int first, double (*s_red)[4], uint32_t *s_acc,
-                                                double (*s_tm)[kResidentMaxTypes][3], int *s_items, bool &nan_seen) {
-    resident_loop<NT, POL>(a, first, s_red, s_acc, s_tm, s_items, nan_seen);
+                                                double (*s_tm)[kResidentMaxTypes][3], int *s_items, bool &nan_seen,
+                                                float *dyn = nullptr) {
+    resident_loop<NT, POL, SM>(a, first, s_red, s_acc, s_tm, s_items, nan_seen, dyn);
 }
 
 template <int NT, int POL, int SM = 0>
@@ -712,7 +713,13 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
 // queued largest first: from the first one with at most split_sites sites on, the blocks of
 // a cluster leave the loop together and sweep instances alone, as the resident sweep does
 // (rank 0 keeps the one just drawn), so small instances do not hold a whole cluster.
-template <int NT, int POL>
+// SM = 1: every block of the cluster keeps a full copy of the instance's spins in its shared
+// memory; an attempt reads its own copy, and an accepted spin is written to every block's
+// copy (distributed shared memory). No block reads a site of the class being swept, and the
+// cluster barrier at the end of the class orders those writes before the next class reads
+// them, so every copy holds the same values at every barrier. The blocks then sweep small
+// instances alone, each in its own shared memory as the resident sweep does.
+template <int NT, int POL, int SM = 0>
 __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentArgs a) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -732,6 +739,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
     const int n_types = a.n_types;
     RunState *rs = a.run;
     bool nan_seen = false;
+    extern __shared__ float cl_dyn[];  // SM: this block's copy of the instance's spins
+    const int cap = a.smem_sites;
     int alone = -2;  // >= -1: the blocks sweep alone from now on (-1: draw the next instance)
     for (;;) {
         if (rank == 0 && threadIdx.x == 0) s_item = (int)atomicAdd(a.queue, 1u);
@@ -750,6 +759,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
         const double *sc = rs->sched + ((int64_t)step * a.n_inst + I.inst_local) * 2;
         const float beta = (float)sc[0], B = (float)sc[1];
         const uint32_t inst = (uint32_t)I.inst_id;
+        if (SM) {  // every block: the whole instance into its own shared memory
+            for (int g = I.g_begin + (int)threadIdx.x; g < I.g_end; g += NT) {
+                const float4 v = S[(int64_t)g * R + I.r];
+                const int i = g - I.g_begin;
+                cl_dyn[i] = v.x;
+                cl_dyn[cap + i] = v.y;
+                cl_dyn[2 * cap + i] = v.z;
+            }
+            cl.sync();  // no block writes into a copy that is still being loaded
+        }
         for (int m = 0; m < a.mcs; ++m) {
             const uint32_t t = t0 + (uint32_t)m;
             const bool log_accepts = a.alog && t < a.alog_mcs;
@@ -762,8 +781,23 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
                     const uint32_t orig = (uint32_t)__ldg(a.orig + g);
                     const Site32 p = resident_params(a, I, g);
                     float4 Sq;
-                    const bool ok = direct_attempt<2, 2, POL, 1>(S, E, a.row_ptr, g, I.r, R, sg.z, orig, p, beta, B, t,
-                                                                 inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq);
+                    bool ok;
+                    if (SM) {
+                        ok = smem_attempt<POL>(cl_dyn, cap, I.g_begin, E, a.row_ptr, g, sg.z, orig, p, beta, B, t,
+                                               inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq);
+                        if (ok) {  // the new spin into the other blocks' copies
+                            const int i = g - I.g_begin;
+                            for (int b = 1; b < CS; ++b) {
+                                float *o = cl.map_shared_rank(cl_dyn, (rank + b) % CS);
+                                o[i] = Sq.x;
+                                o[cap + i] = Sq.y;
+                                o[2 * cap + i] = Sq.z;
+                            }
+                        }
+                    } else {
+                        ok = direct_attempt<2, 2, POL, 1>(S, E, a.row_ptr, g, I.r, R, sg.z, orig, p, beta, B, t, inst,
+                                                          k0, k1, acc, nan_seen, a.pol, sigma, Sq);
+                    }
                     tm[0] = __fadd_rn(tm[0], Sq.x);
                     tm[1] = __fadd_rn(tm[1], Sq.y);
                     tm[2] = __fadd_rn(tm[2], Sq.z);
@@ -845,11 +879,19 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
             }
             cl.sync();  // the width and the totals' buffers are ready for the next MCS
         }
+        if (SM)  // each block's own sites back to global memory (the copies agree after the last barrier)
+            for (int q = 0; q < I.n_segs; ++q) {
+                const int4 sg = a.segs[I.seg_off + q];
+                for (int g = sg.x + rank * NT + (int)threadIdx.x; g < sg.y; g += CS * NT) {
+                    const int i = g - I.g_begin;
+                    S[(int64_t)g * R + I.r] = make_float4(cl_dyn[i], cl_dyn[cap + i], cl_dyn[2 * cap + i], 0.f);
+                }
+            }
     }
-    // small instances: no shared memory of another block is read from here on
+    // small instances: no shared memory of another block is read or written from here on
     if (alone >= -1) {
         __shared__ int s_items[NT / 32 + 1];
-        resident_loop_call<NT, POL>(a, alone, s_red, s_acc, s_tm, s_items, nan_seen);
+        resident_loop_call<NT, POL, SM>(a, alone, s_red, s_acc, s_tm, s_items, nan_seen, cl_dyn);
     }
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }
@@ -1322,15 +1364,30 @@ void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream)
 
 using ClusterFn = void (*)(ResidentArgs);
 
-ClusterFn select_cluster(int threads, bool pol) {
+ClusterFn select_cluster(int threads, bool pol, bool smem) {
+    if (smem) {
+        if (threads >= 512) return pol ? cluster32_kernel<512, 1, 1> : cluster32_kernel<512, 0, 1>;
+        return pol ? cluster32_kernel<256, 1, 1> : cluster32_kernel<256, 0, 1>;
+    }
     if (threads >= 512) return pol ? cluster32_kernel<512, 1> : cluster32_kernel<512, 0>;
     return pol ? cluster32_kernel<256, 1> : cluster32_kernel<256, 0>;
+}
+
+// Dynamic shared memory of the cluster sweep with spins in shared memory: a copy of the
+// largest instance per block, or the groups' regions of its single-block phase.
+size_t cluster_smem_bytes(const ResidentArgs &a, int threads) {
+    if (a.smem_sites <= 0) return 0;
+    const int nt = threads >= 512 ? 512 : 256;
+    const int ng = a.group_threads > 0 && a.group_threads < nt ? nt / a.group_threads : 1;
+    const int64_t sites = std::max<int64_t>(a.smem_sites, ng > 1 ? (int64_t)ng * a.group_sites : 0);
+    return (size_t)sites * 3 * sizeof(float);
 }
 
 int launch_cluster(const ResidentArgs &a, int n_clusters, int cs, int threads, void *stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_clusters * cs);
     cfg.blockDim = dim3(threads >= 512 ? 512 : 256);
+    cfg.dynamicSmemBytes = cluster_smem_bytes(a, threads);
     cfg.stream = (cudaStream_t)stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1339,15 +1396,19 @@ int launch_cluster(const ResidentArgs &a, int n_clusters, int cs, int threads, v
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return (int)cudaLaunchKernelEx(&cfg, select_cluster(threads, a.pol != nullptr), a);
+    return (int)cudaLaunchKernelEx(&cfg, select_cluster(threads, a.pol != nullptr, a.smem_sites > 0), a);
 }
 
-int cluster_capacity(int cs, int threads, bool pol) {
-    ClusterFn k = select_cluster(threads, pol);
+int cluster_capacity(int cs, int threads, bool pol, size_t smem_bytes) {
+    ClusterFn k = select_cluster(threads, pol, smem_bytes > 0);
     if (cs > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+    if (smem_bytes > 0 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess)
+        return 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs);
     cfg.blockDim = dim3(threads >= 512 ? 512 : 256);
+    cfg.dynamicSmemBytes = smem_bytes;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cs;

@@ -518,6 +518,52 @@ def test_cluster_sweep_batch_with_policies_and_types():
             assert np.all(np.abs(a.type_history()[i] - b.type_history()[i]) <= 1e-6 * n)
 
 
+@pytest.mark.parametrize("cs,threads,split,group", [(2, 512, 0, 0), (4, 512, 700, 0), (2, 256, 700, 128)])
+def test_cluster_sweep_with_spin_copies_in_shared_memory(cs, threads, split, group):
+    """The cluster sweep with a copy of the instance's spins in every block's shared memory
+    (accepted spins written to all copies through distributed shared memory), with and
+    without small instances swept alone or in groups, equals the per-class sweep bit for
+    bit over two steps and two runs."""
+    ps = nanoparticle_batch(7, seed=15, r_max=9.0)
+    T = np.linspace(0.4, 2.4, 2 * len(ps))[:, None] * np.array([[1.0, 0.7]])
+    B = np.full_like(T, 0.15)
+    kw = dict(cluster_blocks=cs, cluster_threads=threads, cluster_split=split, group_threads=group, group_sites=600)
+    with ctx(ps, replicas=2, seed=33, variant=3, resident_smem=1, accept_log_mcs=3, **kw) as a, \
+            ctx(ps, replicas=2, seed=33, variant=0, accept_log_mcs=3) as b:
+        a.run(T[:, :1], B[:, :1], 5)
+        a.run(T[:, 1:], B[:, 1:], 5)
+        b.run(T, B, 5)
+        st = a.stats()
+        assert vb.sweep_kernel_names(st["sweep_kernels"]) == ["cluster32_smem"]
+        assert st["cluster_blocks"] == cs and st["split_sites"] == split
+        for i in range(2 * len(ps)):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+        n = max(p.n_sites for p in ps)
+        assert np.all(np.abs(a.history() - b.history()) <= 1e-6 * n)
+        assert np.array_equal(a.accept_log(), b.accept_log())
+
+
+def test_cluster_shared_memory_with_policies_and_types():
+    ps = nanoparticle_batch(6, seed=16, r_max=9.0)
+    for p in ps:
+        p.type = (np.arange(p.n_sites) % 2).astype(np.int32)
+        p.with_policy([oracle.ADAPTIVE, oracle.HINZKE_NOWAK], [0.8, 0.4])
+    T = np.linspace(0.4, 2.0, 12)[:, None]
+    B = np.full_like(T, 0.2)
+    with ctx(ps, replicas=2, seed=26, variant=0, type_stats=True) as a, \
+            ctx(ps, replicas=2, seed=26, variant=3, resident_smem=1, cluster_blocks=2, cluster_threads=512,
+                cluster_split=1500, type_stats=True) as b:
+        a.run(T, B, 10)
+        b.run(T, B, 10)
+        assert vb.sweep_kernel_names(b.stats()["sweep_kernels"]) == ["cluster32_smem"]
+        assert np.array_equal(a.accept_history(), b.accept_history())
+        assert np.array_equal(a.adaptive_width(), b.adaptive_width())
+        for i in range(12):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+            n = ps[i // 2].n_sites
+            assert np.all(np.abs(a.type_history()[i] - b.type_history()[i]) <= 1e-6 * n)
+
+
 def test_cluster_rejected_for_fp64():
     with pytest.raises(vb.VegasError) as e:
         ctx([sc_periodic(4)], precision=64, variant=3)
