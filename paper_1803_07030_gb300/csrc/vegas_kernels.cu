@@ -1115,11 +1115,11 @@ __global__ void renorm64_kernel(const RenormArgs a) {
 
 // FP32 spins: |S|^2 in FP64 (the squares of floats are exact in FP64, so n2 carries an error
 // of at most 2^-52), then the rescaling. GB300 runs few FP64 operations per SM and clock, so
-// the common case (s = 1 and |S|^2 within 2^-10 of 1, which every spin drawn or kept by a
+// the common case (s = 1 and |S|^2 within 2^-16 of 1, which every spin drawn or kept by a
 // Metropolis step is: |u| ~ 1e-7) avoids the FP64 square root and division: with u = n2 - 1
 // (exact), 1/sqrt(1 + u) - 1 = -u/2 + 3u^2/8 - (5/16) u^3 + ..., and S' = S + S d with d the
 // first two terms in FP32, one FMA per component. d is off by at most (5/16)|u|^3 + 2^-24 |u|,
-// so S + S d is within 4e-10 |S| of S s/|S| at |u| = 2^-10 and within 1e-14 |S| at the usual
+// so S + S d is within 5e-13 |S| of S s/|S| at |u| = 2^-16 and within 1e-14 |S| at the usual
 // |u| ~ 1e-7: it rounds to the same float as the FP64 product unless that product lies that
 // close to a rounding boundary (half a float ulp is 3e-8 |S|). Other spins take the FP64
 // formula s / sqrt(n2).
@@ -1132,7 +1132,7 @@ __global__ void renorm32_kernel(const RenormArgs a) {
         const double n2 = fma(x, x, fma(y, y, z * z));
         const double s = a.norm[w >> a.log2R];
         const double u = n2 - 1.0;
-        if (s == 1.0 && fabs(u) < 0x1p-10) {
+        if (s == 1.0 && fabs(u) < 0x1p-16) {
             const float uf = (float)u;
             const float d = __fmul_rn(uf, fmaf(0.375f, uf, -0.5f));
             S[w] = make_float4(fmaf(v.x, d, v.x), fmaf(v.y, d, v.y), fmaf(v.z, d, v.z), 0.f);
