@@ -201,7 +201,7 @@ typedef struct {
     int32_t resident_smem;  /* resident and cluster sweeps (variants 1, 3): 1 keeps the spins
                                in shared memory for all MCS of a step (12 bytes per site; instances
                                of at most 17066 sites): the resident sweep holds each instance in its
-                               block (512 or 1024 threads), the cluster sweep a copy of it in every
+                               block (512 threads), the cluster sweep a copy of it in every
                                block of the cluster, an accepted spin written to every copy through
                                distributed shared memory; -1 never; 0 the automatic choice times it
                                beside the other shapes (with variant 1 or 3 fixed: global memory).

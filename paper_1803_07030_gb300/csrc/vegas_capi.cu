@@ -1001,7 +1001,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
             return bail(VEGAS_EINVAL);
         }
         if (o.resident_smem == 1)
-            set_resident_shape(c, 1024, o.group_threads, o.group_sites, true);
+            set_resident_shape(c, 512, o.group_threads, o.group_sites, true);
         else
             set_resident_shape(c, c->max_instance_sites >= 4096 ? 512 : 256, o.group_threads, o.group_sites);
         ra.spins = c->d_spins;
@@ -1444,11 +1444,10 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     }
                 }
                 if (c->res_eligible && c->res_smem_eligible) {  // spins in shared memory
-                    cand.push_back({1, 1024, 0, 0, 0, 1});
                     cand.push_back({1, 512, 0, 0, 0, 1});
                     if (uneven) {
-                        cand.push_back({1, 1024, 0, 0, 128, 1});
-                        cand.push_back({1, 1024, 0, 0, 256, 1});
+                        cand.push_back({1, 512, 0, 0, 128, 1});
+                        cand.push_back({1, 512, 0, 0, 256, 1});
                     }
                 }
                 if (c->coop_eligible) cand.push_back({2, 0, 0, 0, 0});

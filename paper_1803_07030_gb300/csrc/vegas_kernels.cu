@@ -403,16 +403,16 @@ __device__ bool direct_row_ok(const PassArgs &a, int g, uint32_t orig) {
 // on chip for the whole step): sp holds x, y, z of the instance's sites in three arrays of
 // cap floats, site g at g - g0. Neighbour values, the field's row order and every rounding
 // are those of direct_attempt, so the results are bit for bit the same.
+// The row (first link e0, deg links) comes from the caller, which loads it ahead.
 template <int POL>
-__device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const int2 *E, const int64_t *row_ptr, int g,
+__device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const int2 *E, int64_t e0, int deg, int g,
                                              int lower_end, uint32_t orig, const Site32 &p, float beta, float B,
                                              uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1, Acc32 &acc,
                                              bool &nan_seen, const PolicySite32 *pol, float sigma, float4 &Sq) {
     const int i = g - g0;
     const float4 Si = make_float4(sp[i], sp[cap + i], sp[2 * cap + i], 0.f);
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-    const int64_t e0 = __ldg(row_ptr + g), e1 = __ldg(row_ptr + g + 1);
-    const int deg = (int)(e1 - e0);
+    const int64_t e1 = e0 + deg;
     if (deg <= kDirectRow) {
         int2 ed[kDirectRow];
 #pragma unroll
@@ -448,6 +448,49 @@ __device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const i
     acc.add(e_i, Sn, ok);
     Sq = Sn;
     return ok;
+}
+
+// Links of a row (at most kDirectRow, so at most two 128-byte lines) into L1 ahead of use.
+__device__ __forceinline__ void prefetch_row_l1(const int2 *E, int64_t e0, int deg) {
+    if (deg <= 0) return;
+    const char *p0 = (const char *)(E + e0), *p1 = (const char *)(E + e0 + deg) - 1;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p0));
+    if (((uintptr_t)p0 >> 7) != ((uintptr_t)p1 >> 7)) asm volatile("prefetch.global.L1 [%0];" ::"l"(p1));
+}
+
+// The sites of one colour segment that a thread sweeps with the spins in shared memory: g,
+// g + stride, ... below end. Each row is read two sites ahead and its links prefetched into
+// L1 one site ahead, so the L2 latency of the link gathers overlaps the previous attempts.
+// visit(g, e0, deg) runs the attempt of site g with its row.
+template <typename F>
+__device__ __forceinline__ void smem_segment(const int64_t *row_ptr, const int2 *E, int g, int end, int stride,
+                                             F &&visit) {
+    int64_t c0 = 0, n0 = 0;
+    int cdeg = 0, ndeg = 0;
+    if (g < end) {
+        c0 = __ldg(row_ptr + g);
+        cdeg = (int)(__ldg(row_ptr + g + 1) - c0);
+    }
+    if (g + stride < end) {
+        n0 = __ldg(row_ptr + g + stride);
+        ndeg = (int)(__ldg(row_ptr + g + stride + 1) - n0);
+        prefetch_row_l1(E, n0, ndeg);
+    }
+    for (; g < end; g += stride) {
+        const int gm = g + 2 * stride;
+        int64_t m0 = 0;
+        int mdeg = 0;
+        if (gm < end) {
+            m0 = __ldg(row_ptr + gm);
+            mdeg = (int)(__ldg(row_ptr + gm + 1) - m0);
+        }
+        visit(g, c0, cdeg);
+        if (gm < end) prefetch_row_l1(E, m0, mdeg);
+        c0 = n0;
+        cdeg = ndeg;
+        n0 = m0;
+        ndeg = mdeg;
+    }
 }
 
 // ------------------------------------------------------------------ FP32 colour pass (direct)
@@ -559,14 +602,15 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
         for (int q = 0; q < I.n_segs; ++q) {
             const int4 sg = a.segs[I.seg_off + q];  // {begin, end, class begin, type | last << 16}
             float tm[3] = {0.f, 0.f, 0.f};
-            for (int g = sg.x + gtid; g < sg.y; g += gthreads) {
+            // the attempt of site g: one code path for every parameter mode (with k = kc = 0 the
+            // anisotropy terms add signed zeros only, so spins and decisions equal the specialised
+            // paths'); SM: row given, spins in shared memory
+            auto visit = [&](int g, int64_t e0, int deg) {
                 const uint32_t orig = (uint32_t)__ldg(a.orig + g);
-                // one code path for every parameter mode: with k = kc = 0 the anisotropy terms
-                // add signed zeros only, so spins and decisions equal the specialised paths'
                 const Site32 p = resident_params(a, I, g);
                 float4 Sq;
                 const bool ok =
-                    SM ? smem_attempt<POL>(sp, cap, I.g_begin, E, a.row_ptr, g, sg.z, orig, p, beta, B, t, inst, k0, k1,
+                    SM ? smem_attempt<POL>(sp, cap, I.g_begin, E, e0, deg, g, sg.z, orig, p, beta, B, t, inst, k0, k1,
                                            acc, nan_seen, a.pol, sigma, Sq)
                        : direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, I.r, R, sg.z, orig, p, beta, B, t, inst, k0, k1,
                                                    acc, nan_seen, a.pol, sigma, Sq);
@@ -576,7 +620,11 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
                 if (log_accepts)
                     a.alog[(int64_t)t * a.alog_stride + I.alog_base + (int64_t)I.r * I.n_sample_sites + orig] =
                         ok ? 1 : 0;
-            }
+            };
+            if (SM)
+                smem_segment(a.row_ptr, E, sg.x + gtid, sg.y, gthreads, visit);
+            else
+                for (int g = sg.x + gtid; g < sg.y; g += gthreads) visit(g, 0, 0);
             if (n_types > 0) {  // this segment's magnetization into its type (fixed order)
                 double d[3] = {(double)tm[0], (double)tm[1], (double)tm[2]};
                 for (int off = 16; off > 0; off >>= 1) {
@@ -777,13 +825,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
             for (int q = 0; q < I.n_segs; ++q) {
                 const int4 sg = a.segs[I.seg_off + q];  // {begin, end, class begin, type | last << 16}
                 float tm[3] = {0.f, 0.f, 0.f};
-                for (int g = sg.x + rank * NT + (int)threadIdx.x; g < sg.y; g += CS * NT) {
+                auto visit = [&](int g, int64_t e0, int deg) {
                     const uint32_t orig = (uint32_t)__ldg(a.orig + g);
                     const Site32 p = resident_params(a, I, g);
                     float4 Sq;
                     bool ok;
                     if (SM) {
-                        ok = smem_attempt<POL>(cl_dyn, cap, I.g_begin, E, a.row_ptr, g, sg.z, orig, p, beta, B, t,
+                        ok = smem_attempt<POL>(cl_dyn, cap, I.g_begin, E, e0, deg, g, sg.z, orig, p, beta, B, t,
                                                inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq);
                         if (ok) {  // the new spin into the other blocks' copies
                             const int i = g - I.g_begin;
@@ -804,7 +852,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
                     if (log_accepts)
                         a.alog[(int64_t)t * a.alog_stride + I.alog_base + (int64_t)I.r * I.n_sample_sites + orig] =
                             ok ? 1 : 0;
-                }
+                };
+                if (SM)
+                    smem_segment(a.row_ptr, E, sg.x + rank * NT + (int)threadIdx.x, sg.y, CS * NT, visit);
+                else
+                    for (int g = sg.x + rank * NT + (int)threadIdx.x; g < sg.y; g += CS * NT) visit(g, 0, 0);
                 if (n_types > 0) {
                     double d[3] = {(double)tm[0], (double)tm[1], (double)tm[2]};
                     for (int off = 16; off > 0; off >>= 1) {
@@ -1331,18 +1383,16 @@ int coop_blocks_per_sm(bool pol) {
 
 using ResFn = void (*)(ResidentArgs);
 
-// Spins in global memory: 256 or 512 threads; in shared memory (smem = 1): 512 or 1024.
+// Spins in global memory: 256 or 512 threads; in shared memory (smem = 1): 512 (1024 threads
+// would leave 64 registers per thread and spill).
 ResFn select_resident(int threads, bool pol, bool smem) {
-    if (smem) {
-        if (threads >= 1024) return pol ? resident32_kernel<1024, 1, 1> : resident32_kernel<1024, 0, 1>;
-        return pol ? resident32_kernel<512, 1, 1> : resident32_kernel<512, 0, 1>;
-    }
+    if (smem) return pol ? resident32_kernel<512, 1, 1> : resident32_kernel<512, 0, 1>;
     if (threads >= 512) return pol ? resident32_kernel<512, 1> : resident32_kernel<512, 0>;
     return pol ? resident32_kernel<256, 1> : resident32_kernel<256, 0>;
 }
 
 int resident_threads(int threads, bool smem) {
-    if (smem) return threads >= 1024 ? 1024 : 512;
+    if (smem) return 512;
     return threads >= 512 ? 512 : 256;
 }
 

@@ -249,7 +249,7 @@ def test_resident_sweep_with_spins_in_shared_memory(R):
         b.run(T[:, :1], B[:, :1], 7)
         b.run(T[:, 1:], B[:, 1:], 7)
         st = b.stats()
-        assert vb.sweep_kernel_names(st["sweep_kernels"]) == ["resident32_smem"] and st["block_threads"] == 1024
+        assert vb.sweep_kernel_names(st["sweep_kernels"]) == ["resident32_smem"] and st["block_threads"] == 512
         for i in range(n):
             assert np.array_equal(a.spins(i), b.spins(i)), i
         for i in range(n):
