@@ -65,6 +65,7 @@ struct vegas_ctx {
     std::vector<PassLaunch> passes;
     // device buffers
     void *d_spins = nullptr, *d_edges = nullptr, *d_p0 = nullptr, *d_p1 = nullptr, *d_pk = nullptr;
+    int2 *d_ell = nullptr;  // links as fixed rows of kEllRow (spins-in-shared-memory sweeps)
     int64_t *d_rowptr = nullptr, *d_slot_base = nullptr;
     uint32_t *d_pass_tickets = nullptr;  // [passes] block counters of the R = 32 staged kernel
     int32_t n_groups = 1;      // type groups of the partial slots (n_types with type_stats)
@@ -189,7 +190,7 @@ void free_all(vegas_ctx *c) {
     for (cudaGraph_t g : c->run_graph_defs) cudaGraphDestroy(g);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
-    void *bufs[] = {c->d_spins, c->d_edges, c->d_p0, c->d_p1, c->d_pk, c->d_rowptr, c->d_slot_base, c->d_orig,
+    void *bufs[] = {c->d_spins, c->d_edges, c->d_ell, c->d_p0, c->d_p1, c->d_pk, c->d_rowptr, c->d_slot_base, c->d_orig,
                     c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog,
                     c->d_insts, c->d_cstart, c->d_queue, c->d_bar, c->d_coop_partial, c->d_acc, c->d_acc_hist,
                     c->d_pol, c->d_pol32, c->d_qis, c->d_sigma, c->d_adapt_n, c->d_type_hist, c->d_snap, c->d_segs,
@@ -994,7 +995,20 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         c->res_policy = any_policy;
         ResidentArgs &ra = c->res;
         std::memset(&ra, 0, sizeof ra);
-        c->res_smem_eligible = o.resident_smem >= 0 && 12 * (int64_t)c->max_instance_sites <= kResSmemBytes;
+        // spins in shared memory: every instance fits at 12 bytes per site and every row in a
+        // fixed row of kEllRow links (the form reads links without row offsets)
+        int64_t max_deg = 0;
+        for (int64_t g = 0; g < n_sites; ++g) max_deg = std::max(max_deg, h_rowptr[(size_t)g + 1] - h_rowptr[(size_t)g]);
+        c->res_smem_eligible = o.resident_smem >= 0 && 12 * (int64_t)c->max_instance_sites <= kResSmemBytes &&
+                               max_deg <= kEllRow;
+        if (c->res_smem_eligible) {
+            std::vector<int2> h_ell((size_t)n_sites * kEllRow, make_int2(-1, 0));
+            for (int64_t g = 0; g < n_sites; ++g)
+                for (int64_t e = h_rowptr[(size_t)g]; e < h_rowptr[(size_t)g + 1]; ++e)
+                    h_ell[(size_t)g * kEllRow + (size_t)(e - h_rowptr[(size_t)g])] = h_e32[(size_t)e];
+            DALLOC(c->d_ell, sizeof(int2) * h_ell.size());
+            H2D(c->d_ell, h_ell.data(), sizeof(int2) * h_ell.size());
+        }
         if (o.resident_smem == 1 && !c->res_smem_eligible) {
             c->err = "resident_smem = 1: the largest instance does not fit in shared memory (12 bytes per site, at "
                      "most " + std::to_string(kResSmemBytes / 12) + " sites)";
@@ -1006,6 +1020,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
             set_resident_shape(c, c->max_instance_sites >= 4096 ? 512 : 256, o.group_threads, o.group_sites);
         ra.spins = c->d_spins;
         ra.edges = c->d_edges;
+        ra.ell = (const int4 *)c->d_ell;
         ra.row_ptr = c->d_rowptr;
         ra.orig = c->d_orig;
         ra.p0 = c->d_p0;

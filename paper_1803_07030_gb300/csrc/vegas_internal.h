@@ -246,6 +246,8 @@ struct ResidentInst {
     SiteParams32 u;
 };
 
+constexpr int kEllRow = 12;  // links per fixed row of the spins-in-shared-memory sweeps
+
 // Persistent sweep: every block takes instances from a queue (largest first) and runs all
 // MCS of one temperature/field step on each, colour class after colour class.
 struct ResidentArgs {
@@ -273,6 +275,9 @@ struct ResidentArgs {
                                // one block each (0: every instance by a whole cluster)
     int32_t group_threads;     // > 0: a block sweeps instances of at most group_sites sites
     int32_t group_sites;       // NT / group_threads at a time, group_threads threads each
+    const int4 *ell;           // spins in shared memory: every site's links as a fixed row of
+                               // 12 (neighbour, J float bits) pairs in row order, padded with
+                               // neighbour -1 ([global site][6] int4)
     int32_t smem_sites;        // resident sweep: > 0 keeps each instance's spins in shared memory
                                // for the whole launch (room for this many sites per block, or
                                // group_sites per group); 0 reads and writes them in global memory

@@ -401,36 +401,32 @@ __device__ bool direct_row_ok(const PassArgs &a, int g, uint32_t orig) {
 
 // The same attempt with the instance's spins in shared memory (resident sweep with spins kept
 // on chip for the whole step): sp holds x, y, z of the instance's sites in three arrays of
-// cap floats, site g at g - g0. Neighbour values, the field's row order and every rounding
-// are those of direct_attempt, so the results are bit for bit the same.
-// The row (first link e0, deg links) comes from the caller, which loads it ahead.
+// cap floats, site g at g - g0. The site's links come as a fixed row of kEllRow (neighbour,
+// J) pairs in row order, padded with neighbour -1 (erow, 16-byte aligned), so no row offset is
+// read before them. Neighbour values, the field's row order and every rounding are those of
+// direct_attempt, so the results are bit for bit the same.
 template <int POL>
-__device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const int2 *E, int64_t e0, int deg, int g,
-                                             int lower_end, uint32_t orig, const Site32 &p, float beta, float B,
-                                             uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1, Acc32 &acc,
-                                             bool &nan_seen, const PolicySite32 *pol, float sigma, float4 &Sq) {
+__device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const int4 *erow, int g, int lower_end,
+                                             uint32_t orig, const Site32 &p, float beta, float B, uint32_t t,
+                                             uint32_t inst, uint32_t k0, uint32_t k1, Acc32 &acc, bool &nan_seen,
+                                             const PolicySite32 *pol, float sigma, float4 &Sq) {
     const int i = g - g0;
     const float4 Si = make_float4(sp[i], sp[cap + i], sp[2 * cap + i], 0.f);
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-    const int64_t e1 = e0 + deg;
-    if (deg <= kDirectRow) {
-        int2 ed[kDirectRow];
+    int4 q[kEllRow / 2];
 #pragma unroll
-        for (int k = 0; k < kDirectRow; ++k)
-            if (k < deg) ed[k] = __ldg(E + e0 + k);
+    for (int k = 0; k < kEllRow / 2; ++k) q[k] = __ldg(erow + k);
 #pragma unroll
-        for (int k = 0; k < kDirectRow; ++k)
-            if (k < deg) {
-                const int j = ed[k].x - g0;
-                link32(make_float4(sp[j], sp[cap + j], sp[2 * cap + j], 0.f), __int_as_float(ed[k].y),
-                       ed[k].x < lower_end, hx, hy, hz, lx, ly, lz);
-            }
-    } else {
-        for (int64_t e = e0; e < e1; ++e) {
-            const int2 ed = __ldg(E + e);
-            const int j = ed.x - g0;
-            link32(make_float4(sp[j], sp[cap + j], sp[2 * cap + j], 0.f), __int_as_float(ed.y), ed.x < lower_end, hx,
-                   hy, hz, lx, ly, lz);
+    for (int k = 0; k < kEllRow / 2; ++k) {
+        if (q[k].x >= 0) {
+            const int j = q[k].x - g0;
+            link32(make_float4(sp[j], sp[cap + j], sp[2 * cap + j], 0.f), __int_as_float(q[k].y), q[k].x < lower_end,
+                   hx, hy, hz, lx, ly, lz);
+        }
+        if (q[k].z >= 0) {
+            const int j = q[k].z - g0;
+            link32(make_float4(sp[j], sp[cap + j], sp[2 * cap + j], 0.f), __int_as_float(q[k].w), q[k].z < lower_end,
+                   hx, hy, hz, lx, ly, lz);
         }
     }
     const uint4 rw = philox10(make_uint4(orig, t, inst, kPurposeTrial32), k0, k1);
@@ -450,46 +446,29 @@ __device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const i
     return ok;
 }
 
-// Links of a row (at most kDirectRow, so at most two 128-byte lines) into L1 ahead of use.
-__device__ __forceinline__ void prefetch_row_l1(const int2 *E, int64_t e0, int deg) {
-    if (deg <= 0) return;
-    const char *p0 = (const char *)(E + e0), *p1 = (const char *)(E + e0 + deg) - 1;
+// One fixed row of links (96 bytes: at most two 128-byte lines) and the caller id of a site
+// into L1 ahead of use.
+__device__ __forceinline__ void prefetch_site_l1(const int4 *ell, const int32_t *orig, int g) {
+    const char *p0 = (const char *)(ell + (size_t)g * (kEllRow / 2));
+    const char *p1 = p0 + kEllRow * sizeof(int2) - 1;
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p0));
     if (((uintptr_t)p0 >> 7) != ((uintptr_t)p1 >> 7)) asm volatile("prefetch.global.L1 [%0];" ::"l"(p1));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(orig + g));
 }
 
 // The sites of one colour segment that a thread sweeps with the spins in shared memory: g,
-// g + stride, ... below end. Each row is read two sites ahead and its links prefetched into
-// L1 one site ahead, so the L2 latency of the link gathers overlaps the previous attempts.
-// visit(g, e0, deg) runs the attempt of site g with its row.
+// g + stride, ... below end; the next site's links are prefetched into L1 while the current
+// one is computed, and after the last one the thread's first site of the next segment
+// (next_g, if below next_end), whose class comes after the barrier.
 template <typename F>
-__device__ __forceinline__ void smem_segment(const int64_t *row_ptr, const int2 *E, int g, int end, int stride,
-                                             F &&visit) {
-    int64_t c0 = 0, n0 = 0;
-    int cdeg = 0, ndeg = 0;
-    if (g < end) {
-        c0 = __ldg(row_ptr + g);
-        cdeg = (int)(__ldg(row_ptr + g + 1) - c0);
-    }
-    if (g + stride < end) {
-        n0 = __ldg(row_ptr + g + stride);
-        ndeg = (int)(__ldg(row_ptr + g + stride + 1) - n0);
-        prefetch_row_l1(E, n0, ndeg);
-    }
+__device__ __forceinline__ void smem_segment(const int4 *ell, const int32_t *orig, int g, int end, int stride,
+                                             int next_g, int next_end, F &&visit) {
     for (; g < end; g += stride) {
-        const int gm = g + 2 * stride;
-        int64_t m0 = 0;
-        int mdeg = 0;
-        if (gm < end) {
-            m0 = __ldg(row_ptr + gm);
-            mdeg = (int)(__ldg(row_ptr + gm + 1) - m0);
-        }
-        visit(g, c0, cdeg);
-        if (gm < end) prefetch_row_l1(E, m0, mdeg);
-        c0 = n0;
-        cdeg = ndeg;
-        n0 = m0;
-        ndeg = mdeg;
+        if (g + stride < end)
+            prefetch_site_l1(ell, orig, g + stride);
+        else if (next_g < next_end)
+            prefetch_site_l1(ell, orig, next_g);
+        visit(g);
     }
 }
 
@@ -605,13 +584,13 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
             // the attempt of site g: one code path for every parameter mode (with k = kc = 0 the
             // anisotropy terms add signed zeros only, so spins and decisions equal the specialised
             // paths'); SM: row given, spins in shared memory
-            auto visit = [&](int g, int64_t e0, int deg) {
+            auto visit = [&](int g) {
                 const uint32_t orig = (uint32_t)__ldg(a.orig + g);
                 const Site32 p = resident_params(a, I, g);
                 float4 Sq;
                 const bool ok =
-                    SM ? smem_attempt<POL>(sp, cap, I.g_begin, E, e0, deg, g, sg.z, orig, p, beta, B, t, inst, k0, k1,
-                                           acc, nan_seen, a.pol, sigma, Sq)
+                    SM ? smem_attempt<POL>(sp, cap, I.g_begin, a.ell + (size_t)g * (kEllRow / 2), g, sg.z, orig, p,
+                                           beta, B, t, inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq)
                        : direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, I.r, R, sg.z, orig, p, beta, B, t, inst, k0, k1,
                                                    acc, nan_seen, a.pol, sigma, Sq);
                 tm[0] = __fadd_rn(tm[0], Sq.x);
@@ -621,10 +600,12 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
                     a.alog[(int64_t)t * a.alog_stride + I.alog_base + (int64_t)I.r * I.n_sample_sites + orig] =
                         ok ? 1 : 0;
             };
-            if (SM)
-                smem_segment(a.row_ptr, E, sg.x + gtid, sg.y, gthreads, visit);
-            else
-                for (int g = sg.x + gtid; g < sg.y; g += gthreads) visit(g, 0, 0);
+            if (SM) {
+                const int4 nx = q + 1 < I.n_segs ? a.segs[I.seg_off + q + 1] : make_int4(0, 0, 0, 0);
+                smem_segment(a.ell, a.orig, sg.x + gtid, sg.y, gthreads, nx.x + gtid, nx.y, visit);
+            } else {
+                for (int g = sg.x + gtid; g < sg.y; g += gthreads) visit(g);
+            }
             if (n_types > 0) {  // this segment's magnetization into its type (fixed order)
                 double d[3] = {(double)tm[0], (double)tm[1], (double)tm[2]};
                 for (int off = 16; off > 0; off >>= 1) {
@@ -825,14 +806,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
             for (int q = 0; q < I.n_segs; ++q) {
                 const int4 sg = a.segs[I.seg_off + q];  // {begin, end, class begin, type | last << 16}
                 float tm[3] = {0.f, 0.f, 0.f};
-                auto visit = [&](int g, int64_t e0, int deg) {
+                auto visit = [&](int g) {
                     const uint32_t orig = (uint32_t)__ldg(a.orig + g);
                     const Site32 p = resident_params(a, I, g);
                     float4 Sq;
                     bool ok;
                     if (SM) {
-                        ok = smem_attempt<POL>(cl_dyn, cap, I.g_begin, E, e0, deg, g, sg.z, orig, p, beta, B, t,
-                                               inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq);
+                        ok = smem_attempt<POL>(cl_dyn, cap, I.g_begin, a.ell + (size_t)g * (kEllRow / 2), g, sg.z,
+                                               orig, p, beta, B, t, inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq);
                         if (ok) {  // the new spin into the other blocks' copies
                             const int i = g - I.g_begin;
                             for (int b = 1; b < CS; ++b) {
@@ -853,10 +834,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
                         a.alog[(int64_t)t * a.alog_stride + I.alog_base + (int64_t)I.r * I.n_sample_sites + orig] =
                             ok ? 1 : 0;
                 };
-                if (SM)
-                    smem_segment(a.row_ptr, E, sg.x + rank * NT + (int)threadIdx.x, sg.y, CS * NT, visit);
-                else
-                    for (int g = sg.x + rank * NT + (int)threadIdx.x; g < sg.y; g += CS * NT) visit(g, 0, 0);
+                const int off = rank * NT + (int)threadIdx.x;
+                if (SM) {
+                    const int4 nx = q + 1 < I.n_segs ? a.segs[I.seg_off + q + 1] : make_int4(0, 0, 0, 0);
+                    smem_segment(a.ell, a.orig, sg.x + off, sg.y, CS * NT, nx.x + off, nx.y, visit);
+                } else {
+                    for (int g = sg.x + off; g < sg.y; g += CS * NT) visit(g);
+                }
                 if (n_types > 0) {
                     double d[3] = {(double)tm[0], (double)tm[1], (double)tm[2]};
                     for (int off = 16; off > 0; off >>= 1) {
