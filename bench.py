@@ -615,7 +615,8 @@ def run_workload(args):
     if share["samples"]:
         ctx = vg.Context(share["samples"], precision=w.precision, replicas=w.replicas, seed=w.seed,
                          inst_base=share["inst_base"], device=dev, stream=int(stream.cuda_stream),
-                         variant=args.variant, type_stats=args.type_stats, snapshots=args.snapshots)
+                         variant=args.variant, type_stats=args.type_stats, snapshots=args.snapshots,
+                         resident_smem=args.resident_smem)
 
     def barrier():
         if world > 1:
@@ -853,6 +854,9 @@ def main():
                     help="sweep variant: -1 automatic (timed on the first run), 0 per colour class, 1 resident, 3 cluster, "
                          "2 cooperative, 4 wavefront (both classes per launch); profiling commands fix it because ncu "
                          "distorts the automatic timing")
+    ap.add_argument("--resident-smem", type=int, default=0, choices=[-1, 0, 1],
+                    help="secondary workloads: 1 keeps spins in shared memory in the resident or cluster sweep, "
+                         "-1 never, 0 automatic (profiling commands fix it with --variant)")
     ap.add_argument("--analysis", action="store_true", help="time the history analysis instead of the sweep")
     ap.add_argument("--ising", action="store_true", help="time the multi-spin-coded Ising workload")
     ap.add_argument("--type-stats", action="store_true", help="secondary workloads: record per-type magnetization")
