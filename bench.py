@@ -616,7 +616,7 @@ def run_workload(args):
         ctx = vg.Context(share["samples"], precision=w.precision, replicas=w.replicas, seed=w.seed,
                          inst_base=share["inst_base"], device=dev, stream=int(stream.cuda_stream),
                          variant=args.variant, type_stats=args.type_stats, snapshots=args.snapshots,
-                         resident_smem=args.resident_smem)
+                         resident_smem=args.resident_smem, graphs=args.graphs)
 
     def barrier():
         if world > 1:
@@ -857,6 +857,9 @@ def main():
     ap.add_argument("--resident-smem", type=int, default=0, choices=[-1, 0, 1],
                     help="secondary workloads: 1 keeps spins in shared memory in the resident or cluster sweep, "
                          "-1 never, 0 automatic (profiling commands fix it with --variant)")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1, 2],
+                    help="secondary workloads: 1 a run as one CUDA graph, 2 a graph per step, 0 direct launches "
+                         "(profilers see the kernels of graphs without conditional nodes only)")
     ap.add_argument("--analysis", action="store_true", help="time the history analysis instead of the sweep")
     ap.add_argument("--ising", action="store_true", help="time the multi-spin-coded Ising workload")
     ap.add_argument("--type-stats", action="store_true", help="secondary workloads: record per-type magnetization")
