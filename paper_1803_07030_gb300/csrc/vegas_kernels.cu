@@ -547,8 +547,8 @@ __device__ __forceinline__ void group_sync(int bar, int nthreads) {
 // after the last MCS of the launch; only the links and parameters come from L2 and HBM.
 template <int NT, int POL, int SM = 0>
 __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, const ResidentInst &I, double (*s_red)[4], uint32_t *s_acc,
-                                     double (*s_tm)[kResidentMaxTypes][3], bool &nan_seen, int gtid, int gthreads,
-                                     int gbar, float *sp = nullptr, int cap = 0) {
+                                     double (*s_tm)[kResidentMaxTypes][3], double (*s_part)[4], bool &nan_seen,
+                                     int gtid, int gthreads, int gbar, float *sp = nullptr, int cap = 0) {
     float4 *S = (float4 *)a.spins;
     const int2 *E = (const int2 *)a.edges;
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
@@ -620,28 +620,33 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
             }
             if (sg.w >> 16) group_sync(gbar, gthreads);  // the last segment of a colour class
         }
+        // the MCS's totals in FP64 with few FP64 operations (GB300 runs two per SM and clock):
+        // every thread leaves its four sums in shared memory, then warp q of the group adds
+        // quantity q over the group's threads (each lane a fixed stride, then a butterfly),
+        // so the order, and the result, is fixed
         acc.flush();
-        double v[4] = {acc.d[0], acc.d[1], acc.d[2], acc.d[3]};
         uint32_t na = acc.nacc;
-        for (int off = 16; off > 0; off >>= 1) {
+        for (int off = 16; off > 0; off >>= 1) na += __shfl_xor_sync(0xFFFFFFFFu, na, off);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
-            na += __shfl_xor_sync(0xFFFFFFFFu, na, off);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) s_red[warp][q] = v[q];
-            s_acc[warp] = na;
+        for (int q = 0; q < 4; ++q) s_part[threadIdx.x][q] = acc.d[q];
+        if (lane == 0) s_acc[warp] = na;
+        group_sync(gbar, gthreads);
+        {
+            const int gw = gtid >> 5, nw = gthreads >> 5, t0 = (int)threadIdx.x - gtid;
+            for (int q = gw; q < 4; q += nw) {
+                double x = 0.0;
+                for (int k = lane; k < gthreads; k += 32) x += s_part[t0 + k][q];
+                for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, off);
+                if (lane == 0) s_red[gw0][q] = x;
+            }
         }
         group_sync(gbar, gthreads);
         if (gtid == 0) {
-            double sum[4] = {0.0, 0.0, 0.0, 0.0};
+            double sum[4];
             uint32_t nsum = 0;
-            for (int w = gw0; w < gw0 + (gthreads >> 5); ++w) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) sum[q] += s_red[w][q];
-                nsum += s_acc[w];
-            }
+            for (int q = 0; q < 4; ++q) sum[q] = s_red[gw0][q];
+            for (int w = gw0; w < gw0 + (gthreads >> 5); ++w) nsum += s_acc[w];
             const int64_t rec = (int64_t)rec0 + m;
             double *h = rs->hist + (rec * a.n_inst + I.inst_local) * 4;
 #pragma unroll
@@ -679,8 +684,8 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
 // takes region gi of a.group_sites sites, a whole-block instance all a.smem_sites).
 template <int NT, int POL, int SM = 0>
 __device__ __forceinline__ void resident_loop(const ResidentArgs &a, int first, double (*s_red)[4], uint32_t *s_acc,
-                                              double (*s_tm)[kResidentMaxTypes][3], int *s_items, bool &nan_seen,
-                                              float *dyn = nullptr) {
+                                              double (*s_tm)[kResidentMaxTypes][3], double (*s_part)[4], int *s_items,
+                                              bool &nan_seen, float *dyn = nullptr) {
     const int GT = a.group_threads;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -704,8 +709,8 @@ __device__ __forceinline__ void resident_loop(const ResidentArgs &a, int first, 
         if (item < a.n_items) {
             const ResidentInst I = a.insts[item];
             const int cap = ng == 1 ? a.smem_sites : a.group_sites;
-            resident_sweep_block<NT, POL, SM>(a, I, s_red, s_acc, s_tm, nan_seen, (int)threadIdx.x - gi * gt, gt,
-                                              ng == 1 ? 0 : 1 + gi, SM ? dyn + (size_t)gi * 3 * cap : nullptr, cap);
+            resident_sweep_block<NT, POL, SM>(a, I, s_red, s_acc, s_tm, s_part, nan_seen, (int)threadIdx.x - gi * gt,
+                                              gt, ng == 1 ? 0 : 1 + gi, SM ? dyn + (size_t)gi * 3 * cap : nullptr, cap);
         }
         __syncthreads();  // every group is done before the items are drawn again
     }
@@ -715,9 +720,9 @@ __device__ __forceinline__ void resident_loop(const ResidentArgs &a, int first, 
 // then allocated apart from the cluster phase's.
 template <int NT, int POL, int SM = 0>
 __device__ __noinline__ void resident_loop_call(const ResidentArgs &a, int first, double (*s_red)[4], uint32_t *s_acc,
-                                                double (*s_tm)[kResidentMaxTypes][3], int *s_items, bool &nan_seen,
-                                                float *dyn = nullptr) {
-    resident_loop<NT, POL, SM>(a, first, s_red, s_acc, s_tm, s_items, nan_seen, dyn);
+                                                double (*s_tm)[kResidentMaxTypes][3], double (*s_part)[4],
+                                                int *s_items, bool &nan_seen, float *dyn = nullptr) {
+    resident_loop<NT, POL, SM>(a, first, s_red, s_acc, s_tm, s_part, s_items, nan_seen, dyn);
 }
 
 template <int NT, int POL, int SM = 0>
@@ -726,9 +731,10 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
     __shared__ double s_red[NT / 32][4];
     __shared__ uint32_t s_acc[NT / 32];
     __shared__ double s_tm[NT / 32][kResidentMaxTypes][3];  // per warp and type, segment order
+    __shared__ double s_part[NT][4];                         // every thread's MCS totals
     extern __shared__ float res_dyn[];                       // SM: the instances' spins
     bool nan_seen = false;
-    resident_loop<NT, POL, SM>(a, -1, s_red, s_acc, s_tm, s_items, nan_seen, res_dyn);
+    resident_loop<NT, POL, SM>(a, -1, s_red, s_acc, s_tm, s_part, s_items, nan_seen, res_dyn);
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }
 
@@ -927,7 +933,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
     // small instances: no shared memory of another block is read or written from here on
     if (alone >= -1) {
         __shared__ int s_items[NT / 32 + 1];
-        resident_loop_call<NT, POL, SM>(a, alone, s_red, s_acc, s_tm, s_items, nan_seen, cl_dyn);
+        __shared__ double s_part[NT][4];
+        resident_loop_call<NT, POL, SM>(a, alone, s_red, s_acc, s_tm, s_part, s_items, nan_seen, cl_dyn);
     }
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }
