@@ -94,21 +94,29 @@ __device__ __forceinline__ float3 trial_random32(uint4 rw, float sn) {
     __sincosf(phi, &sphi, &cphi);
     const float rho2 = fmaf(-z, z, 1.0f);
     const float rho = __fmul_rn(rho2, rsqrtf(rho2));
-    return make_float3(__fmul_rn(sn, __fmul_rn(rho, cphi)), __fmul_rn(sn, __fmul_rn(rho, sphi)), __fmul_rn(sn, z));
+    // x and y in packed pairs (each lane of a pair rounds as the scalar operation does)
+    const float2 xy = __fmul2_rn(make_float2(sn, sn), __fmul2_rn(make_float2(rho, rho), make_float2(cphi, sphi)));
+    return make_float3(xy.x, xy.y, __fmul_rn(sn, z));
 }
 
 // One Metropolis attempt in FP32 on the trial P, written with explicit roundings (fmaf
 // where a fused multiply-add is meant, __fmul_rn / __fadd_rn elsewhere) so that every
 // kernel that calls it computes bit-identical results for the same inputs, whatever the
 // surrounding code. h is the exchange field sum_j J_ij S_j (row order), l its part over
-// lower colours; wacc is the random word of the acceptance uniform.
+// lower colours (x and y of each as a packed pair: the packed FP32 instructions of sm_100+
+// round each lane as the scalar operation does, so the results are the same bits); wacc is
+// the random word of the acceptance uniform.
 template <int PM, int LM>
-__device__ __forceinline__ void attempt32(const float4 Si, float hx, float hy, float hz, float lx, float ly, float lz,
+__device__ __forceinline__ void attempt32(const float4 Si, float2 hxy, float hz, float2 lxy, float lz,
                                           const Site32 &p, float beta, float B, const float3 P, uint32_t wacc,
                                           float4 &Sn, bool &acc, float &e_i, bool &nan_seen) {
-    const float Hx = fmaf(B, p.nx, hx), Hy = fmaf(B, p.ny, hy), Hz = fmaf(B, p.nz, hz);
+    const float2 Hxy = __ffma2_rn(make_float2(B, B), make_float2(p.nx, p.ny), hxy);
+    const float Hz = fmaf(B, p.nz, hz);
+    const float Hx = Hxy.x, Hy = Hxy.y, lx = lxy.x, ly = lxy.y;
     const float px = P.x, py = P.y, pz = P.z;
-    const float dx = __fsub_rn(px, Si.x), dy = __fsub_rn(py, Si.y), dz = __fsub_rn(pz, Si.z);
+    // P - S as P + (-S): the same rounding
+    const float2 dxy = __fadd2_rn(make_float2(px, py), make_float2(-Si.x, -Si.y));
+    const float dx = dxy.x, dy = dxy.y, dz = __fsub_rn(pz, Si.z);
     float dE = -fmaf(dx, Hx, fmaf(dy, Hy, __fmul_rn(dz, Hz)));
     if (PM != 0) {
         const float pn = fmaf(px, p.ex, fmaf(py, p.ey, __fmul_rn(pz, p.ez)));
@@ -214,36 +222,37 @@ __device__ __forceinline__ float3 policy_trial32(const PolicySite32 ps, float si
 // Also counts the accepted attempts.
 struct Acc32 {
     double d[4] = {0.0, 0.0, 0.0, 0.0};
-    float f[4] = {0.f, 0.f, 0.f, 0.f};
+    float2 fem = make_float2(0.f, 0.f);  // E and Mz
+    float2 fxy = make_float2(0.f, 0.f);  // Mx and My
     int n = 0;
     uint32_t nacc = 0;
     __device__ __forceinline__ void add(float e, float4 q, bool ok) {
         nacc += ok ? 1u : 0u;
-        f[0] = __fadd_rn(f[0], e);
-        f[1] = __fadd_rn(f[1], q.x);
-        f[2] = __fadd_rn(f[2], q.y);
-        f[3] = __fadd_rn(f[3], q.z);
+        fem = __fadd2_rn(fem, make_float2(e, q.z));
+        fxy = __fadd2_rn(fxy, make_float2(q.x, q.y));
         if (++n == 64) flush();
     }
 
     __device__ __forceinline__ void flush() {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            d[q] += (double)f[q];
-            f[q] = 0.f;
-        }
+        d[0] += (double)fem.x;
+        d[1] += (double)fxy.x;
+        d[2] += (double)fxy.y;
+        d[3] += (double)fem.y;
+        fem = make_float2(0.f, 0.f);
+        fxy = make_float2(0.f, 0.f);
         n = 0;
     }
 };
 
-__device__ __forceinline__ void link32(const float4 Sj, float J, bool lower, float &hx, float &hy, float &hz,
-                                       float &lx, float &ly, float &lz) {
-    hx = fmaf(J, Sj.x, hx);
-    hy = fmaf(J, Sj.y, hy);
+// One link's share of the field: x and y as a packed pair (one instruction, the same two
+// roundings), z alone; with `lower`, also of the part over lower colours.
+__device__ __forceinline__ void link32(const float4 Sj, float J, bool lower, float2 &hxy, float &hz, float2 &lxy,
+                                       float &lz) {
+    const float2 jj = make_float2(J, J), sxy = make_float2(Sj.x, Sj.y);
+    hxy = __ffma2_rn(jj, sxy, hxy);
     hz = fmaf(J, Sj.z, hz);
     if (lower) {
-        lx = fmaf(J, Sj.x, lx);
-        ly = fmaf(J, Sj.y, ly);
+        lxy = __ffma2_rn(jj, sxy, lxy);
         lz = fmaf(J, Sj.z, lz);
     }
 }

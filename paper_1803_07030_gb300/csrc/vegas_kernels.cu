@@ -313,7 +313,8 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
                                                bool &nan_seen, const PolicySite32 *pol, float sigma, float4 &Sq) {
     const int64_t si = (int64_t)g * R + r;
     const float4 Si = S[si];
-    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+    float2 hxy = make_float2(0.f, 0.f), lxy = make_float2(0.f, 0.f);
+    float hz = 0.f, lz = 0.f;
     const int64_t e0 = __ldg(row_ptr + g), e1 = __ldg(row_ptr + g + 1);
     const int deg = (int)(e1 - e0);
     if (deg <= kDirectRow) {
@@ -336,20 +337,17 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (k0 + k < deg)
-                    link32(Sj[k], __int_as_float(ed[k0 + k].y), LM == 2 && ed[k0 + k].x < lower_end, hx, hy, hz, lx, ly,
-                           lz);
+                    link32(Sj[k], __int_as_float(ed[k0 + k].y), LM == 2 && ed[k0 + k].x < lower_end, hxy, hz, lxy, lz);
         }
     } else {
         for (int64_t e = e0; e < e1; ++e) {
             const int2 ed = __ldg(E + e);
             const float4 *q = S + (int64_t)ed.x * R + r;
-            link32(CG ? __ldcg(q) : __ldg(q), __int_as_float(ed.y), LM == 2 && ed.x < lower_end, hx, hy, hz,
-                   lx, ly, lz);
+            link32(CG ? __ldcg(q) : __ldg(q), __int_as_float(ed.y), LM == 2 && ed.x < lower_end, hxy, hz, lxy, lz);
         }
     }
     if (LM == 1) {
-        lx = hx;
-        ly = hy;
+        lxy = hxy;
         lz = hz;
     }
     const uint4 rw = philox10(make_uint4(orig, t, inst, kPurposeTrial32), k0, k1);
@@ -357,7 +355,7 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
     float4 Sn;
     bool ok, bad;
     float e_i;
-    attempt32<PM, LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, P, rw.z, Sn, ok, e_i, bad);
+    attempt32<PM, LM>(Si, hxy, hz, lxy, lz, p, beta, B, P, rw.z, Sn, ok, e_i, bad);
     nan_seen |= bad;
     if (ok) S[si] = Sn;
     acc.add(e_i, Sn, ok);
@@ -412,7 +410,8 @@ __device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const i
                                              const PolicySite32 *pol, float sigma, float4 &Sq) {
     const int i = g - g0;
     const float4 Si = make_float4(sp[i], sp[cap + i], sp[2 * cap + i], 0.f);
-    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+    float2 hxy = make_float2(0.f, 0.f), lxy = make_float2(0.f, 0.f);
+    float hz = 0.f, lz = 0.f;
     int4 q[kEllRow / 2];
 #pragma unroll
     for (int k = 0; k < kEllRow / 2; ++k) q[k] = __ldg(erow + k);
@@ -421,12 +420,12 @@ __device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const i
         if (q[k].x >= 0) {
             const int j = q[k].x - g0;
             link32(make_float4(sp[j], sp[cap + j], sp[2 * cap + j], 0.f), __int_as_float(q[k].y), q[k].x < lower_end,
-                   hx, hy, hz, lx, ly, lz);
+                   hxy, hz, lxy, lz);
         }
         if (q[k].z >= 0) {
             const int j = q[k].z - g0;
             link32(make_float4(sp[j], sp[cap + j], sp[2 * cap + j], 0.f), __int_as_float(q[k].w), q[k].z < lower_end,
-                   hx, hy, hz, lx, ly, lz);
+                   hxy, hz, lxy, lz);
         }
     }
     const uint4 rw = philox10(make_uint4(orig, t, inst, kPurposeTrial32), k0, k1);
@@ -434,7 +433,7 @@ __device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const i
     float4 Sn;
     bool ok, bad;
     float e_i;
-    attempt32<2, 2>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, P, rw.z, Sn, ok, e_i, bad);
+    attempt32<2, 2>(Si, hxy, hz, lxy, lz, p, beta, B, P, rw.z, Sn, ok, e_i, bad);
     nan_seen |= bad;
     if (ok) {
         sp[i] = Sn.x;

@@ -55,16 +55,16 @@ __device__ __forceinline__ void staged_attempt_rw(const PassArgs &a, const int4 
                                                   const PolicySite32 *ps = nullptr, float sigma = 0.f,
                                                   bool lower_all = true) {
     const Site32 p = site_params32(a, PM, g);
-    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+    float2 hxy = make_float2(0.f, 0.f), lxy = make_float2(0.f, 0.f);
+    float hz = 0.f, lz = 0.f;
 #pragma unroll
     for (int j = 0; j < DEG / 2; ++j) {
         const int4 q = lk[j];
-        link32(row[(2 * j) * 32], __int_as_float(q.y), LM == 2 && q.x < a.lower_end, hx, hy, hz, lx, ly, lz);
-        link32(row[(2 * j + 1) * 32], __int_as_float(q.w), LM == 2 && q.z < a.lower_end, hx, hy, hz, lx, ly, lz);
+        link32(row[(2 * j) * 32], __int_as_float(q.y), LM == 2 && q.x < a.lower_end, hxy, hz, lxy, lz);
+        link32(row[(2 * j + 1) * 32], __int_as_float(q.w), LM == 2 && q.z < a.lower_end, hxy, hz, lxy, lz);
     }
     if (LM == 1 || (LM == 3 && lower_all)) {
-        lx = hx;
-        ly = hy;
+        lxy = hxy;
         lz = hz;
     }
     const float4 Si = row[DEG * 32];
@@ -73,7 +73,7 @@ __device__ __forceinline__ void staged_attempt_rw(const PassArgs &a, const int4 
     float e_i;
     const float3 P =
         POL ? policy_trial32<(POL >= 2 ? POL - 2 : -1)>(*ps, sigma, Si, p.sn, c) : trial_random32(c, p.sn);
-    attempt32<PM, LM == 3 ? 1 : LM>(Si, hx, hy, hz, lx, ly, lz, p, beta, B, P, c.z, Sn, ok, e_i, bad);
+    attempt32<PM, LM == 3 ? 1 : LM>(Si, hxy, hz, lxy, lz, p, beta, B, P, c.z, Sn, ok, e_i, bad);
     nan_seen |= bad;
     if (ok) S[(int64_t)g * R + r] = Sn;
     if (log_accepts)
