@@ -106,7 +106,7 @@ def fake_device(monkeypatch):
 
 
 def args(**kw):
-    a = dict(gpus=1, steps=3, warmup=2, mcs=bench.MCS, impl="ours", side=bench.L_SIDE, workload="sg256x32",
+    a = dict(gpus=1, steps=3, warmup=2, mcs=bench.MCS, impl="ours", side=bench.L_SIDE, depth=0, workload="sg256x32",
              policy="", variant=-1, analysis=False, ising=False, type_stats=False, snapshots=False, quick=False,
              resident_smem=0, graphs=1)
     a.update(kw)
