@@ -41,7 +41,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Metropolis spin-update attempts/s on 1 GB300; batched vs plain; % HBM roofline"
 UNIT = "attempts/s"
 L_SIDE, REPLICAS, MCS, SEED = 256, 32, 200, 1
-L_DEPTH = 256  # z extent of the lattice (profiling cases may be flatter)
+L_DEPTH = 0  # z extent of the lattice, 0: the side (profiling cases may be flatter)
 # algorithmic bytes per attempt: 16 B read + 16 B write of the FP32 spin (float4), plus one
 # row of six (int32 col, f32 J) links = 48 B shared by the 32 replicas that sweep it together
 BYTES_PER_ATTEMPT = 16 + 16 + 48.0 / REPLICAS
@@ -65,7 +65,7 @@ def workload_desc(mcs):
     return {
         "workload": f"sg{L_SIDE}x32: 32 temperature replicas (T 0.1->2.0 geometric) of a {L_SIDE}^3 periodic sc +-J "
                     f"spin glass, random moves, {mcs} MCS per step, FP32 spins / FP64 history",
-        "sites_per_replica": L_SIDE * L_SIDE * L_DEPTH,
+        "sites_per_replica": L_SIDE * L_SIDE * (L_DEPTH or L_SIDE),
         "replicas_per_gpu": REPLICAS,
         "mcs_per_step": mcs,
         "l2": "inputs larger than L2 (8.6 GB of spins + 0.8 GB of links per GPU)",
@@ -457,7 +457,7 @@ def run_ours(args):
 
     vg.build()
     mcs = args.mcs
-    s = sc_periodic(L_SIDE if L_DEPTH == L_SIDE else (L_SIDE, L_SIDE, L_DEPTH), bimodal_seed=SEED)
+    s = sc_periodic(L_SIDE if L_DEPTH in (0, L_SIDE) else (L_SIDE, L_SIDE, L_DEPTH), bimodal_seed=SEED)
     policy = apply_policy([s], args.policy)
     T = temperatures()[:, None]
     B = np.zeros_like(T)
@@ -497,7 +497,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     achieved = BYTES_PER_ATTEMPT * attempts_per_launch / (sweep_ms / 1000.0) / 1e9
     # the committed counters are those of the 256^3 workload; another side has none
-    traffic = profiled_traffic(ksummary, ksources) if L_SIDE == 256 and L_DEPTH == 256 else None
+    traffic = profiled_traffic(ksummary, ksources) if L_SIDE == 256 and L_DEPTH in (0, 256) else None
 
     if args.quick or policy:
         if rank == 0:
@@ -870,7 +870,7 @@ def main():
                     help="time the sweep only (no e2e, plain-path or CPU-baseline legs); for profiling runs")
     args = ap.parse_args()
     L_SIDE = args.side
-    L_DEPTH = args.depth if args.depth > 0 else args.side
+    L_DEPTH = args.depth
     if args.impl == "reference":
         return run_reference(args)
     if args.analysis:
