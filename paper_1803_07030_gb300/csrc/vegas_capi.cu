@@ -119,6 +119,7 @@ struct vegas_ctx {
     WaveArgs wave{};
     int wave_grid = 1;
     int32_t *d_tasks = nullptr;
+    int32_t *d_deps = nullptr;  // wavefront sweep: distinct class-0 blocks of each class-1 block
     uint32_t *d_done = nullptr, *d_ticket = nullptr;
     double *d_wave_partial = nullptr;
     int64_t *d_wave_slot_base = nullptr;
@@ -194,7 +195,7 @@ void free_all(vegas_ctx *c) {
                     c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog,
                     c->d_insts, c->d_cstart, c->d_queue, c->d_bar, c->d_coop_partial, c->d_acc, c->d_acc_hist,
                     c->d_pol, c->d_pol32, c->d_qis, c->d_sigma, c->d_adapt_n, c->d_type_hist, c->d_snap, c->d_segs,
-                    c->d_tasks, c->d_done, c->d_ticket, c->d_pass_tickets, c->d_wave_partial, c->d_wave_slot_base, c->d_wave_slot_count};
+                    c->d_tasks, c->d_deps, c->d_done, c->d_ticket, c->d_pass_tickets, c->d_wave_partial, c->d_wave_slot_base, c->d_wave_slot_count};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -1104,13 +1105,27 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         if (o.max_blocks > 0) c->wave_grid = std::min(c->wave_grid, o.max_blocks);
         const int64_t W = (int64_t)c->wave_grid * (kThreads / 32);
         const int32_t n0 = si.cstart[1], n1 = si.cstart[2] - si.cstart[1];
-        const int32_t nb0 = (n0 + 7) / 8, nb1 = (n1 + 7) / 8;
-        // last class-0 block that class-1 block q links to
-        std::vector<int32_t> D((size_t)nb1, 0);
-        for (int32_t g = si.cstart[1]; g < si.cstart[2]; ++g) {
-            int32_t &d = D[(size_t)((g - si.cstart[1]) / 8)];
-            for (int64_t e = l.row_ptr[(size_t)g]; e < l.row_ptr[(size_t)g + 1]; ++e)
-                d = std::max(d, l.col[(size_t)e] / 8);
+        constexpr int BS = kWaveBlockSites;
+        const int32_t nb0 = (n0 + BS - 1) / BS, nb1 = (n1 + BS - 1) / BS;
+        // the class-0 blocks that class-1 block q links to (distinct, ascending; D: the last)
+        std::vector<int32_t> D((size_t)nb1, 0), deps((size_t)nb1 * kWaveDeps, -1);
+        for (int32_t q = 0; q < nb1; ++q) {
+            int32_t *dq = &deps[(size_t)q * kWaveDeps];
+            int nd = 0;
+            const int32_t g0 = si.cstart[1] + q * BS, g1 = std::min(g0 + BS, si.cstart[2]);
+            for (int32_t g = g0; g < g1; ++g)
+                for (int64_t e = l.row_ptr[(size_t)g]; e < l.row_ptr[(size_t)g + 1]; ++e) {
+                    const int32_t b = l.col[(size_t)e] / BS;
+                    if (std::find(dq, dq + nd, b) != dq + nd) continue;
+                    if (nd == kWaveDeps) {
+                        c->err = "the wavefront sweep needs every block of 16 class-1 sites to link to at most 32 "
+                                 "blocks of class-0 sites";
+                        return bail(VEGAS_EINVAL);
+                    }
+                    dq[nd++] = b;
+                }
+            std::sort(dq, dq + nd);
+            D[(size_t)q] = nd > 0 ? dq[nd - 1] : 0;
         }
         // class-0 blocks in memory order; each class-1 block after class-0 block
         // min(D + lag, nb0 - 1), so every dependency comes earlier in the list
@@ -1137,12 +1152,14 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
                 return bail(VEGAS_EINVAL);
             }
         DALLOC(c->d_tasks, sizeof(int32_t) * tasks.size());
+        DALLOC(c->d_deps, sizeof(int32_t) * std::max<size_t>(deps.size(), 1));
         DALLOC(c->d_done, sizeof(uint32_t) * (size_t)nb0);
         DALLOC(c->d_ticket, sizeof(uint32_t));
         DALLOC(c->d_wave_partial, sizeof(double) * 4 * (size_t)c->wave_grid * R);
         DALLOC(c->d_wave_slot_base, sizeof(int64_t));
         DALLOC(c->d_wave_slot_count, sizeof(int32_t));
         H2D(c->d_tasks, tasks.data(), sizeof(int32_t) * tasks.size());
+        if (!deps.empty()) H2D(c->d_deps, deps.data(), sizeof(int32_t) * deps.size());
         const int64_t zero = 0;
         const int32_t gcount = c->wave_grid;
         H2D(c->d_wave_slot_base, &zero, sizeof zero);
@@ -1160,6 +1177,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         wa.pass = p0;
         wa.pass.partial = c->d_wave_partial;
         wa.tasks = c->d_tasks;
+        wa.deps = c->d_deps;
         wa.ticket = c->d_ticket;
         wa.done = c->d_done;
         wa.n_tasks = (int32_t)tasks.size();

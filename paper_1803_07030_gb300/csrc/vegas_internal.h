@@ -311,9 +311,14 @@ struct CoopArgs {
 // MCS (done[b] == t + 1, published with release semantics). Every class-1 block comes after
 // all of its class-0 dependencies in tasks[], and the holder of a ticket is a running warp,
 // which makes the waits finite; each wait is still bounded by timeout_ns.
+constexpr int kWaveBlockSites = 16;  // sites per task of the wavefront sweep
+constexpr int kWaveDeps = 32;        // class-0 blocks a class-1 block may link to
+
 struct WaveArgs {
     PassArgs pass;             // class 0: links, parameters, spins, run state; partial = [block][32][4]
     const int32_t *tasks;      // [n_tasks]: b < nb0 is block b of class 0, else block b - nb0 of class 1
+    const int32_t *deps;       // [nb1][kWaveDeps]: the distinct class-0 blocks each class-1 block
+                               // links to, padded with -1
     uint32_t *ticket;          // next task of the launch (zeroed before every launch)
     uint32_t *done;            // [nb0] MCS counter + 1 of the MCS in which class-0 block b last finished
     int32_t n_tasks, nb0;

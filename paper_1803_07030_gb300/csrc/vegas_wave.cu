@@ -2,15 +2,16 @@
 // both colour classes of an MCS (Sec. II, Eq. 4), so the rows that the class-0 half of the
 // sweep reads are still in L2 when the class-1 half needs them.
 //
-// Each class is cut into blocks of 8 consecutive sites. The host lists the blocks in sweep
+// Each class is cut into blocks of 16 consecutive sites. The host lists the blocks in sweep
 // order: class-0 blocks in memory order, and each class-1 block some distance after the
-// last class-0 block that holds one of its neighbours. Every warp draws the index of its
-// next task from a ticket counter (so the tasks in flight are always about one per warp,
-// consecutive in the list: a narrow window that L2 holds), and runs it as eight groups of
-// one site x 32 replicas with the depth-2 cp.async pipeline of the batched per-class
-// kernel. A class-0
+// last class-0 block that holds one of its neighbours, and gives every class-1 block the row
+// of distinct class-0 blocks it links to. Every warp draws the index of its next task from a
+// ticket counter (so the tasks in flight are always about one per warp, consecutive in the
+// list: a narrow window that L2 holds), and runs it as sixteen groups of one site x 32
+// replicas with the depth-2 cp.async pipeline of the batched per-class kernel. A class-0
 // block publishes done[b] = t + 1 when its spins are stored; a class-1 block reads its
-// neighbours' rows only after every class-0 block it links to has published. Since class-1
+// neighbours' rows only after every class-0 block of its row has published (one acquire
+// load per lane). Since class-1
 // sites link only to class-0 sites, this gives every attempt the same neighbour values as
 // the per-class sweep (class 0 from the previous MCS, class 1 after class 0 of this MCS),
 // and the same Philox counters, so the spins are bit for bit those of that sweep.
@@ -49,11 +50,11 @@ __device__ __forceinline__ uint64_t wave_ns() {
     return t;
 }
 
-constexpr int kWaveBS = 8;                                  // sites per block
+constexpr int kWaveBS = kWaveBlockSites;                    // sites per block (task)
 constexpr int kWaveRows = 2 * 7 * 32 * 16;                  // two groups of 7 rows of 32 replicas
-constexpr int kWaveLinkBytes = kWaveBS * 6 * 8;             // 48 links (col, J)
+constexpr int kWaveLinkBytes = kWaveBS * 6 * 8;             // 96 links (col, J)
 constexpr int kWaveSlot = kWaveLinkBytes + kWaveBS * 4;     // links + caller ids
-constexpr int kWaveWarpBytes = kWaveRows + 2 * kWaveSlot;   // 8000
+constexpr int kWaveWarpBytes = kWaveRows + 2 * kWaveSlot;   // 8832
 constexpr int kWaveSmem = (kThreads / 32) * kWaveWarpBytes;
 
 template <int PM>
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(kThreads, 3) wave32_r32(const WaveArgs w) {
         VEGAS_CHECK(ns >= 1 && ns <= BS && sb >= a.g_begin && se <= w.c1_end, 21, sb);
         VEGAS_CHECK(a.edge_base + (int64_t)(se - a.site_off) * DEG <= a.n_edges_total, 22, sb);
         VEGAS_CHECK(((uintptr_t)src & 15) == 0, 23, sb);
-        if (lane < ns * (DEG / 2)) cp16(dst + 16 * lane, src + 16 * lane);
+        for (int k = lane; k < ns * (DEG / 2); k += 32) cp16(dst + 16 * k, src + 16 * k);
         if (lane < ns) cp4(dst + kWaveLinkBytes + 4 * lane, a.orig + sb + lane);
     };
     auto issue_rows = [&](int g, int se, int lslot, int j, int rslot) {
@@ -120,26 +121,28 @@ __global__ void __launch_bounds__(kThreads, 3) wave32_r32(const WaveArgs w) {
         }
         cp16(dst + DEG * 32, Sr + (int64_t)g * R);
     };
-    // every class-0 block linked from the class-1 block staged in link slot ls has finished
-    // this MCS (warp-uniform)
-    auto deps_ready = [&](int ls, int ns) -> bool {
-        const int2 *lk = (const int2 *)(lslots + ls * kWaveSlot);
-        bool ok = true;
-        for (int k = lane; k < ns * DEG; k += 32) {
-            const int c = lk[k].x;
-            bool in = c >= a.g_begin && c < a.g_end;  // a class-1 site links only to class 0
-            if (in) ok &= ld_acquire(w.done + (c - a.g_begin) / BS) == tag;
-            else atomicOr(a.err, kErrIndex);
+    // every class-0 block that class-1 block b links to (its row of distinct blocks, one per
+    // lane) has finished this MCS (warp-uniform)
+    auto deps_ready = [&](int b) -> bool {
+        static_assert(kWaveDeps == 32, "one dependency per lane");
+        const int d = __ldg(w.deps + (size_t)(b - w.nb0) * kWaveDeps + lane);
+#ifdef VEGAS_DEBUG_CHECKS
+        if (d >= w.nb0) {
+            atomicOr(a.err, kErrIndex);
+            atomicCAS(a.err + 1, 0u, 26u);
+            a.err[2] = (uint32_t)d;
         }
+#endif
+        const bool ok = d < 0 || d >= w.nb0 || ld_acquire(w.done + d) == tag;
         return __all_sync(0xFFFFFFFFu, ok);
     };
     // bounded wait for deps_ready; false when this warp or another one gave up
-    auto wait_deps = [&](int ls, int ns) -> bool {
-        if (deps_ready(ls, ns)) return true;
+    auto wait_deps = [&](int b) -> bool {
+        if (deps_ready(b)) return true;
         const uint64_t t0 = __shfl_sync(0xFFFFFFFFu, wave_ns(), 0);
         for (;;) {
             __nanosleep(128);
-            if (deps_ready(ls, ns)) return true;
+            if (deps_ready(b)) return true;
             int give_up = 0;
             if (lane == 0) {
                 if (ld_volatile(a.err) & kErrTimeout) {
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 3) wave32_r32(const WaveArgs w) {
     while (m < w.n_tasks) {
         const bool c1 = b >= w.nb0;
         if (!pre) {
-            if (c1 && !wait_deps(ls, se - sb)) break;
+            if (c1 && !wait_deps(b)) break;
             __syncwarp();  // orders the lanes' acquire loads before every lane's row copies
             issue_rows(sb, se, ls, 0, 0);
             cp_commit();
@@ -210,9 +213,9 @@ __global__ void __launch_bounds__(kThreads, 3) wave32_r32(const WaveArgs w) {
                 block_range(b2, sb2, se2);
                 issue_links(sb2, se2, ls ^ 1);
             }
-            // rows of the next block's first two groups go out at j = 6, 7, after the
+            // rows of the next block's first two groups go out at j = BS - 2, BS - 1, after the
             // __syncwarp that follows the wait at the top of those groups
-            if (j == 5 && has2) ready2 = b2 < w.nb0 || deps_ready(ls ^ 1, se2 - sb2);
+            if (j == BS - 3 && has2) ready2 = b2 < w.nb0 || deps_ready(b2);
             if (j + 2 < BS)
                 issue_rows(sb + j + 2, se, ls, j + 2, j & 1);
             else if (ready2)
