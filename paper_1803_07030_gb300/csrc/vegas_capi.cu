@@ -1118,8 +1118,9 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
                     const int32_t b = l.col[(size_t)e] / BS;
                     if (std::find(dq, dq + nd, b) != dq + nd) continue;
                     if (nd == kWaveDeps) {
-                        c->err = "the wavefront sweep needs every block of 16 class-1 sites to link to at most 32 "
-                                 "blocks of class-0 sites";
+                        c->err = "the wavefront sweep needs every block of " + std::to_string(BS) +
+                                 " class-1 sites to link to at most " + std::to_string(kWaveDeps) +
+                                 " blocks of class-0 sites";
                         return bail(VEGAS_EINVAL);
                     }
                     dq[nd++] = b;

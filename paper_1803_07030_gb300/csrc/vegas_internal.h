@@ -311,7 +311,7 @@ struct CoopArgs {
 // MCS (done[b] == t + 1, published with release semantics). Every class-1 block comes after
 // all of its class-0 dependencies in tasks[], and the holder of a ticket is a running warp,
 // which makes the waits finite; each wait is still bounded by timeout_ns.
-constexpr int kWaveBlockSites = 16;  // sites per task of the wavefront sweep
+constexpr int kWaveBlockSites = 8;   // sites per task of the wavefront sweep
 constexpr int kWaveDeps = 32;        // class-0 blocks a class-1 block may link to
 
 struct WaveArgs {

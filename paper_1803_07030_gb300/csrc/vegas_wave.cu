@@ -2,12 +2,12 @@
 // both colour classes of an MCS (Sec. II, Eq. 4), so the rows that the class-0 half of the
 // sweep reads are still in L2 when the class-1 half needs them.
 //
-// Each class is cut into blocks of 16 consecutive sites. The host lists the blocks in sweep
+// Each class is cut into blocks of 8 consecutive sites. The host lists the blocks in sweep
 // order: class-0 blocks in memory order, and each class-1 block some distance after the
 // last class-0 block that holds one of its neighbours, and gives every class-1 block the row
 // of distinct class-0 blocks it links to. Every warp draws the index of its next task from a
 // ticket counter (so the tasks in flight are always about one per warp, consecutive in the
-// list: a narrow window that L2 holds), and runs it as sixteen groups of one site x 32
+// list: a narrow window that L2 holds), and runs it as eight groups of one site x 32
 // replicas with the depth-2 cp.async pipeline of the batched per-class kernel. A class-0
 // block publishes done[b] = t + 1 when its spins are stored; a class-1 block reads its
 // neighbours' rows only after every class-0 block of its row has published (one acquire
@@ -52,9 +52,9 @@ __device__ __forceinline__ uint64_t wave_ns() {
 
 constexpr int kWaveBS = kWaveBlockSites;                    // sites per block (task)
 constexpr int kWaveRows = 2 * 7 * 32 * 16;                  // two groups of 7 rows of 32 replicas
-constexpr int kWaveLinkBytes = kWaveBS * 6 * 8;             // 96 links (col, J)
+constexpr int kWaveLinkBytes = kWaveBS * 6 * 8;             // the block's links (col, J)
 constexpr int kWaveSlot = kWaveLinkBytes + kWaveBS * 4;     // links + caller ids
-constexpr int kWaveWarpBytes = kWaveRows + 2 * kWaveSlot;   // 8832
+constexpr int kWaveWarpBytes = kWaveRows + 2 * kWaveSlot;
 constexpr int kWaveSmem = (kThreads / 32) * kWaveWarpBytes;
 
 template <int PM>
