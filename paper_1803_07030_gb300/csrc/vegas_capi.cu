@@ -946,6 +946,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
     // ---- resident sweep: one entry per instance, largest first
     if (!p64) {
         std::vector<ResidentInst> insts;
+        int32_t any_aniso = 0;  // some instance with anisotropy or per-site parameters
         std::vector<int32_t> h_cs;  // class starts (cooperative sweep)
         std::vector<int4> h_segs;   // sweep segments (resident sweep)
         int64_t alog_off = 0;
@@ -973,6 +974,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
                 I.inst_local = s * R + r;
                 I.r = r;
                 I.params_mode = si.uniform_params ? (si.has_anisotropy ? 1 : 0) : 2;
+                if (I.params_mode != 0) any_aniso = 1;
                 I.n_sample_sites = si.n;
                 I.adaptive = si.has_adaptive ? 1 : 0;
                 I.alog_base = alog_off;
@@ -996,6 +998,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         c->res_policy = any_policy;
         ResidentArgs &ra = c->res;
         std::memset(&ra, 0, sizeof ra);
+        ra.any_aniso = any_aniso;
         // spins in shared memory: every instance fits at 12 bytes per site and every row in a
         // fixed row of kEllRow links (the form reads links without row offsets)
         int64_t max_deg = 0;

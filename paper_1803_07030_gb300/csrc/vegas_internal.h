@@ -278,6 +278,7 @@ struct ResidentArgs {
     const int4 *ell;           // spins in shared memory: every site's links as a fixed row of
                                // 12 (neighbour, J float bits) pairs in row order, padded with
                                // neighbour -1 ([global site][6] int4)
+    int32_t any_aniso;         // 0: no instance has anisotropy or per-site parameters
     int32_t smem_sites;        // resident sweep: > 0 keeps each instance's spins in shared memory
                                // for the whole launch (room for this many sites per block, or
                                // group_sites per group); 0 reads and writes them in global memory

@@ -403,7 +403,9 @@ __device__ bool direct_row_ok(const PassArgs &a, int g, uint32_t orig) {
 // J) pairs in row order, padded with neighbour -1 (erow, 16-byte aligned), so no row offset is
 // read before them. Neighbour values, the field's row order and every rounding are those of
 // direct_attempt, so the results are bit for bit the same.
-template <int POL>
+// AN = 0: no instance has anisotropy or per-site parameters, so the anisotropy terms (zeros
+// there) are left out; the spins and decisions are those of the general form.
+template <int POL, int AN = 1>
 __device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const int4 *erow, int g, int lower_end,
                                              uint32_t orig, const Site32 &p, float beta, float B, uint32_t t,
                                              uint32_t inst, uint32_t k0, uint32_t k1, Acc32 &acc, bool &nan_seen,
@@ -433,7 +435,7 @@ __device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const i
     float4 Sn;
     bool ok, bad;
     float e_i;
-    attempt32<2, 2>(Si, hxy, hz, lxy, lz, p, beta, B, P, rw.z, Sn, ok, e_i, bad);
+    attempt32<AN ? 2 : 0, 2>(Si, hxy, hz, lxy, lz, p, beta, B, P, rw.z, Sn, ok, e_i, bad);
     nan_seen |= bad;
     if (ok) {
         sp[i] = Sn.x;
@@ -544,7 +546,7 @@ __device__ __forceinline__ void group_sync(int bar, int nthreads) {
 // SM = 1: the instance's spins are copied into shared memory (sp, three arrays of cap floats)
 // before the first MCS, every attempt reads and writes them there, and they are copied back
 // after the last MCS of the launch; only the links and parameters come from L2 and HBM.
-template <int NT, int POL, int SM = 0>
+template <int NT, int POL, int SM = 0, int AN = 1>
 __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, const ResidentInst &I, double (*s_red)[4], uint32_t *s_acc,
                                      double (*s_tm)[kResidentMaxTypes][3], double (*s_part)[4], bool &nan_seen,
                                      int gtid, int gthreads, int gbar, float *sp = nullptr, int cap = 0) {
@@ -588,8 +590,8 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
                 const Site32 p = resident_params(a, I, g);
                 float4 Sq;
                 const bool ok =
-                    SM ? smem_attempt<POL>(sp, cap, I.g_begin, a.ell + (size_t)g * (kEllRow / 2), g, sg.z, orig, p,
-                                           beta, B, t, inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq)
+                    SM ? smem_attempt<POL, AN>(sp, cap, I.g_begin, a.ell + (size_t)g * (kEllRow / 2), g, sg.z, orig,
+                                               p, beta, B, t, inst, k0, k1, acc, nan_seen, a.pol, sigma, Sq)
                        : direct_attempt<2, 2, POL>(S, E, a.row_ptr, g, I.r, R, sg.z, orig, p, beta, B, t, inst, k0, k1,
                                                    acc, nan_seen, a.pol, sigma, Sq);
                 tm[0] = __fadd_rn(tm[0], Sq.x);
@@ -681,7 +683,7 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
 // a group of group_threads threads each; larger instances take the whole block.
 // SM = 1: spins in shared memory, dyn: the block's dynamic shared memory (a group gi of ng
 // takes region gi of a.group_sites sites, a whole-block instance all a.smem_sites).
-template <int NT, int POL, int SM = 0>
+template <int NT, int POL, int SM = 0, int AN = 1>
 __device__ __forceinline__ void resident_loop(const ResidentArgs &a, int first, double (*s_red)[4], uint32_t *s_acc,
                                               double (*s_tm)[kResidentMaxTypes][3], double (*s_part)[4], int *s_items,
                                               bool &nan_seen, float *dyn = nullptr) {
@@ -708,7 +710,7 @@ __device__ __forceinline__ void resident_loop(const ResidentArgs &a, int first, 
         if (item < a.n_items) {
             const ResidentInst I = a.insts[item];
             const int cap = ng == 1 ? a.smem_sites : a.group_sites;
-            resident_sweep_block<NT, POL, SM>(a, I, s_red, s_acc, s_tm, s_part, nan_seen, (int)threadIdx.x - gi * gt,
+            resident_sweep_block<NT, POL, SM, AN>(a, I, s_red, s_acc, s_tm, s_part, nan_seen, (int)threadIdx.x - gi * gt,
                                               gt, ng == 1 ? 0 : 1 + gi, SM ? dyn + (size_t)gi * 3 * cap : nullptr, cap);
         }
         __syncthreads();  // every group is done before the items are drawn again
@@ -724,7 +726,7 @@ __device__ __noinline__ void resident_loop_call(const ResidentArgs &a, int first
     resident_loop<NT, POL, SM>(a, first, s_red, s_acc, s_tm, s_part, s_items, nan_seen, dyn);
 }
 
-template <int NT, int POL, int SM = 0>
+template <int NT, int POL, int SM = 0, int AN = 1>
 __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
     __shared__ int s_items[NT / 32 + 1];  // the instances drawn (one per group) and their count
     __shared__ double s_red[NT / 32][4];
@@ -733,7 +735,7 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
     __shared__ double s_part[NT][4];                         // every thread's MCS totals
     extern __shared__ float res_dyn[];                       // SM: the instances' spins
     bool nan_seen = false;
-    resident_loop<NT, POL, SM>(a, -1, s_red, s_acc, s_tm, s_part, s_items, nan_seen, res_dyn);
+    resident_loop<NT, POL, SM, AN>(a, -1, s_red, s_acc, s_tm, s_part, s_items, nan_seen, res_dyn);
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }
 
@@ -1375,7 +1377,8 @@ using ResFn = void (*)(ResidentArgs);
 
 // Spins in global memory: 256 or 512 threads; in shared memory (smem = 1): 512 (1024 threads
 // would leave 64 registers per thread and spill).
-ResFn select_resident(int threads, bool pol, bool smem) {
+ResFn select_resident(int threads, bool pol, bool smem, bool aniso = true) {
+    if (smem && !aniso) return pol ? resident32_kernel<512, 1, 1, 0> : resident32_kernel<512, 0, 1, 0>;
     if (smem) return pol ? resident32_kernel<512, 1, 1> : resident32_kernel<512, 0, 1>;
     if (threads >= 512) return pol ? resident32_kernel<512, 1> : resident32_kernel<512, 0>;
     return pol ? resident32_kernel<256, 1> : resident32_kernel<256, 0>;
@@ -1399,7 +1402,8 @@ size_t resident_smem_bytes(const ResidentArgs &a, int threads) {
 void launch_resident(const ResidentArgs &a, int grid, int threads, void *stream) {
     const bool smem = a.smem_sites > 0;
     const int nt = resident_threads(threads, smem);
-    select_resident(nt, a.pol != nullptr, smem)<<<grid, nt, resident_smem_bytes(a, threads), (cudaStream_t)stream>>>(a);
+    select_resident(nt, a.pol != nullptr, smem, a.any_aniso != 0)<<<grid, nt, resident_smem_bytes(a, threads),
+                                                                     (cudaStream_t)stream>>>(a);
 }
 
 using ClusterFn = void (*)(ResidentArgs);
@@ -1467,6 +1471,10 @@ int resident_blocks_per_sm(int threads, bool pol, size_t smem_bytes) {
     const int nt = resident_threads(threads, smem);
     const ResFn k = select_resident(nt, pol, smem);
     if (smem && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess)
+        return 0;
+    // the form without anisotropy terms takes the same shared memory
+    if (smem && cudaFuncSetAttribute(select_resident(nt, pol, smem, false), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_bytes) != cudaSuccess)
         return 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, nt, smem_bytes);
     return nb > 0 ? nb : (smem ? 0 : 1);

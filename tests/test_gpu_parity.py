@@ -235,11 +235,12 @@ def test_resident_sweep_equals_per_class_sweep(R):
         assert np.array_equal(a.accept_log(), b.accept_log())
 
 
-@pytest.mark.parametrize("R", [1, 4])
-def test_resident_sweep_with_spins_in_shared_memory(R):
+@pytest.mark.parametrize("R,aniso", [(1, True), (4, True), (2, False)])
+def test_resident_sweep_with_spins_in_shared_memory(R, aniso):
     """The resident sweep with each instance's spins in shared memory for the whole step equals
-    the per-class sweep bit for bit (spins, accept log) across runs and steps."""
-    samples = _uneven_batch()
+    the per-class sweep bit for bit (spins, accept log) across runs and steps; with and without
+    an instance with anisotropy (without, the kernel leaves the anisotropy terms out)."""
+    samples = _uneven_batch() if aniso else nanoparticle_batch(8, seed=12, r_max=7.0)
     n = len(samples) * R
     T = np.stack([np.linspace(0.3, 2.5, 3) * (1 + 0.05 * i) for i in range(n)])
     B = np.stack([np.array([0.4, -0.2, 0.1]) * (1 + 0.1 * i) for i in range(n)])
