@@ -51,7 +51,7 @@ CSRC = os.path.join(ROOT, "paper_1803_07030_gb300", "csrc")
 # classes one launch covers
 SWEEP_KERNELS = {
     "per_class": ("pass32_r32", os.path.join(ROOT, "profiles", "pass32_r32_sg256x32.txt"),
-                  [os.path.join(CSRC, f) for f in ("vegas_staged.cu", "vegas_staged.cuh", "vegas_device.cuh")], 1),
+                  [os.path.join(CSRC, f) for f in ("vegas_r32.cuh", "vegas_staged.cuh", "vegas_device.cuh")], 1),
     "wave": ("wave32_r32", os.path.join(ROOT, "profiles", "wave32_r32_sg256x32.txt"),
              [os.path.join(CSRC, f) for f in ("vegas_wave.cu", "vegas_staged.cuh", "vegas_device.cuh")], 2),
 }
