@@ -154,7 +154,9 @@ def test_policy_table_without_params_rejected(lib):
                                  {"variant": 2, "type_stats": 1}, {"graphs": 3}, {"graphs": -1},
                                  {"cluster_blocks": 1}, {"cluster_blocks": 17}, {"cluster_threads": 300},
                                  {"cluster_split": -1}, {"group_threads": 100}, {"group_sites": -1},
-                                 {"wave_lag": -1}, {"variant": 5}])
+                                 {"wave_lag": -1}, {"variant": 5}, {"wave_slab": -2}, {"resident_smem": 2},
+                                 {"resident_smem": -2}, {"resident_smem": 1, "variant": 0},
+                                 {"resident_smem": 1, "variant": 2}])
 def test_invalid_options_rejected(lib, opt):
     st, msg = _create_status([sc_periodic(4)], **opt)
     assert st == vb.EINVAL, (opt, msg)

@@ -5,7 +5,7 @@ class-0 blocks it links to have finished. Every attempt then sees the neighbour 
 the per-class sweep and draws the same Philox counters, so the spins and the accept/reject
 decisions must agree bit for bit; the history sums agree up to the order of the FP32 block
 sums. The cases cover the three parameter modes, class sizes that are not multiples of the
-8-site block, grids from one block (many tasks per warp, long dependency waits) to the whole
+8-site block, slab orders with periodic boundaries across slabs, grids from one block (many tasks per warp, long dependency waits) to the whole
 device (about one task per warp), a tight and a default queueing lag, samples with and
 without positions, and the bounded wait that reports a lost dependency instead of hanging.
 """
@@ -81,6 +81,19 @@ def test_wave_matches_per_class_sweep(shape, mode, max_blocks, lag):
         a.run(T, B, 7)
         b.run(T, B, 7)
         assert b.stats()["variant"] == 4
+        assert_same_chain(a, b, s.n_sites)
+
+
+@pytest.mark.parametrize("shape,slab", [((24, 20, 16), 6), ((16, 12, 10), 4), ((16, 16, 16), -1)])
+def test_wave_slab_orders_match_per_class_sweep(shape, slab):
+    """Sites stored slab by slab along x (wave_slab in position units; -1 whole planes): the
+    boundary columns of a slab, whose class-1 sites wait for the next slab's class-0 blocks,
+    and the periodic wrap in every direction keep the per-class sweep's chain."""
+    s = lattice(shape, 0)
+    T, B = schedule(2)
+    with ctx([s], seed=47, variant=0) as a, ctx([s], seed=47, variant=4, wave_slab=slab) as b:
+        a.run(T, B, 5)
+        b.run(T, B, 5)
         assert_same_chain(a, b, s.n_sites)
 
 
