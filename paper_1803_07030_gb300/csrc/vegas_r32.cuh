@@ -88,25 +88,6 @@ __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
         cp16(dst + DEG * 32, Sr + (int64_t)g * R);
     };
 
-    // the next block's rows into L2 ahead of their copies: its own rows once it is drawn (one
-    // 128-byte line per lane), its neighbour rows once its links have landed
-    auto prefetch_own = [&](int sb) {
-        const int s = lane >> 2;
-        if (sb + s < g_end) {
-            const char *p = (const char *)(S + (int64_t)(sb + s) * R) + (lane & 3) * 128;
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-        }
-    };
-    auto prefetch_neighbours = [&](int sb, int lslot) {
-        const int ns = min(BS, g_end - sb);
-        const int2 *lk = (const int2 *)(lslots + lslot * SLOT);
-        for (int k = lane; k < ns * DEG; k += 32) {
-            const char *p = (const char *)(S + (int64_t)lk[k].x * R);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + q * 128));
-        }
-    };
-
     const uint32_t n_blocks = (uint32_t)(g_end - a.g_begin + BS - 1) / BS;  // a ticket past them ends the warp
     uint32_t tk = 0;
     if (lane == 0) tk = atomicAdd(a.ticket, 1u);
@@ -143,10 +124,7 @@ __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
             if (j == 4) {
                 sb2 = a.g_begin + (int)min(__shfl_sync(0xFFFFFFFFu, tk, 0), n_blocks) * BS;
                 issue_links(sb2, ls ^ 1);
-                prefetch_own(sb2);
             }
-            // the wait at the top of j = 6 covered the links copied at j = 4
-            if (j == 6 && sb2 < g_end) prefetch_neighbours(sb2, ls ^ 1);
             if (j + 2 < BS)
                 issue_rows(sb + j + 2, ls, j + 2, j & 1);
             else
