@@ -901,6 +901,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
                 const int64_t per_sm = (work + c->sm_count - 1) / c->sm_count;
                 pl.threads = (int)std::min<int64_t>(kThreads, std::max<int64_t>(32, (per_sm + 31) / 32 * 32));
             }
+            if (c->precision != 64) pl.threads = pass32_threads(a);  // the R = 32 kernel runs 7-warp blocks
             const int64_t need = (work + pl.threads - 1) / pl.threads;
             int64_t cap = (int64_t)c->sm_count * pass_blocks_per_sm(c->precision, a);
             if (o.max_blocks > 0) cap = std::min<int64_t>(cap, o.max_blocks);

@@ -335,6 +335,7 @@ using PassFn = void (*)(PassArgs);
 // dynamic shared memory; the direct kernel for a parameter mode, lower mode and policy flag.
 PassFn select_pass32(const PassArgs &a);
 int pass32_smem(const PassArgs &a);
+int pass32_threads(const PassArgs &a);  // threads per block of that kernel
 // The kernel select_pass32 picks, as a VEGAS_KERNEL_* bit of include/vegas.h.
 uint32_t pass32_kind(const PassArgs &a);
 PassFn select_direct(int pm, int lm, bool pol);

@@ -1280,7 +1280,7 @@ PassFn select_direct(int pm, int lm, bool pol) {
 }
 
 void launch_pass32(const PassArgs &a, int grid, void *stream) {
-    select_pass32(a)<<<grid, kThreads, pass32_smem(a), (cudaStream_t)stream>>>(a);
+    select_pass32(a)<<<grid, pass32_threads(a), pass32_smem(a), (cudaStream_t)stream>>>(a);
 }
 
 void launch_pass64(const PassArgs &a, int grid, int threads, void *stream) {
@@ -1487,7 +1487,7 @@ int pass_blocks_per_sm(int precision, const PassArgs &a) {
     else {
         const int sm = pass32_smem(a);
         if (sm > 0) cudaFuncSetAttribute(select_pass32(a), cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_pass32(a), kThreads, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_pass32(a), pass32_threads(a), sm);
     }
     return nb > 0 ? nb : 1;
 }

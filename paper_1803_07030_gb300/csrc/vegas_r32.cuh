@@ -25,14 +25,56 @@ namespace {
 // POL = 1 adds the sites' update policies (8 bytes each, staged with the caller ids); POL =
 // 2 + c does the same for a pass whose sites all have policy c, with the trial of that policy
 // alone compiled in (each site's parameter still comes from its entry).
+// Without a policy table the kernel runs in blocks of 7 warps, four blocks per SM (72
+// registers, 56 KB of shared memory each: 28 warps per SM); with one, in blocks of 8 warps,
+// three per SM. The block's partial sums are formed in each warp's own shared-memory area
+// once its sweep is done, so the block needs no other shared memory.
+template <int POL>
+struct R32Shape {
+    static constexpr int DEG = 6, D = 2, BS = 8;
+    static constexpr int WARPS = POL ? 8 : 7, MIN_BLOCKS = POL ? 3 : 4;
+    static constexpr int ROWS = D * (DEG + 1) * 32 * 16;
+    static constexpr int LINK_BYTES = BS * DEG * 8;
+    static constexpr int POL_OFF = LINK_BYTES + BS * 4;
+    static constexpr int SLOT = POL_OFF + (POL ? BS * 8 : 0);
+    static constexpr int WARP_BYTES = ROWS + 2 * SLOT;
+};
+
+// Fixed-order block sums of (E, Mx, My, Mz) per replica and the accepted counts, through the
+// warps' own areas of the dynamic shared memory (the same order as block_partials: a butterfly
+// inside the warp, then the warps in order).
+__device__ __forceinline__ void block_partials_r32(double v[4], uint32_t nacc, unsigned char *smem, int warp_bytes,
+                                                   double *out, uint32_t *acc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *mine = (double *)(smem + (size_t)warp * warp_bytes);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) mine[lane * 4 + q] = v[q];
+    ((uint32_t *)(mine + 32 * 4))[lane] = nacc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double a4[4] = {0.0, 0.0, 0.0, 0.0};
+        uint32_t na = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const double *o = (const double *)(smem + (size_t)w * warp_bytes);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a4[q] += o[threadIdx.x * 4 + q];
+            na += ((const uint32_t *)(o + 32 * 4))[threadIdx.x];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[threadIdx.x * 4 + q] = a4[q];
+        if (acc && na) atomicAdd(acc + threadIdx.x, na);
+    }
+}
+
 template <int PM, int LM, int POL>
-__global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
-    constexpr int DEG = 6, D = 2, BS = 8, R = 32;
-    constexpr int ROWS = D * (DEG + 1) * 32 * 16;
-    constexpr int LINK_BYTES = BS * DEG * 8;
-    constexpr int POL_OFF = LINK_BYTES + BS * 4;
-    constexpr int SLOT = POL_OFF + (POL ? BS * 8 : 0);
-    constexpr int WARP_BYTES = ROWS + 2 * SLOT;
+__global__ void __launch_bounds__(R32Shape<POL>::WARPS * 32, R32Shape<POL>::MIN_BLOCKS) pass32_r32(const PassArgs a) {
+    using Sh = R32Shape<POL>;
+    constexpr int DEG = Sh::DEG, D = Sh::D, BS = Sh::BS, R = 32;
+    constexpr int ROWS = Sh::ROWS;
+    constexpr int LINK_BYTES = Sh::LINK_BYTES;
+    constexpr int POL_OFF = Sh::POL_OFF;
+    constexpr int SLOT = Sh::SLOT;
+    constexpr int WARP_BYTES = Sh::WARP_BYTES;
     extern __shared__ __align__(16) unsigned char smem[];
     const RunState *rs_ = a.run;
     const uint32_t t = rs_->t;
@@ -137,7 +179,9 @@ __global__ void __launch_bounds__(kThreads, 3) pass32_r32(const PassArgs a) {
     cp_wait<0>();
     if (nan_seen) atomicOr(a.err, kErrNaN);
     acc.flush();
-    block_partials(acc.d, acc.nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs_, a.inst_local0));
+    __syncwarp();  // every lane's copies have landed and been read: the warp's area is free
+    block_partials_r32(acc.d, acc.nacc, smem, WARP_BYTES, a.partial + (int64_t)blockIdx.x * R * 4,
+                       acc_counters(rs_, a.inst_local0));
 }
 
 }  // namespace

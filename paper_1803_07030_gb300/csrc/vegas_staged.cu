@@ -229,7 +229,7 @@ bool use_staged(const PassArgs &a) { return staged_shape(a) && (!a.pol32 || use_
 int staged_smem(const PassArgs &a) {
     if (use_r32(a)) {
         const bool table = a.pol32 && a.pol_fixed != kPolRandom;  // policy entries staged with the links
-        return (kThreads / 32) * (2 * 7 * 32 * 16 + 2 * (8 * 6 * 8 + 8 * 4 + (table ? 8 * 8 : 0)));
+        return table ? R32Shape<1>::WARPS * R32Shape<1>::WARP_BYTES : R32Shape<0>::WARPS * R32Shape<0>::WARP_BYTES;
     }
     return (kThreads / 32) * staged_geom(6, a.depth, a.log2R).warp_bytes;
 }
@@ -246,6 +246,12 @@ PassFn select_pass32(const PassArgs &a) {
 }
 
 int pass32_smem(const PassArgs &a) { return use_staged(a) ? staged_smem(a) : 0; }
+
+int pass32_threads(const PassArgs &a) {
+    if (!use_r32(a)) return kThreads;
+    const bool table = a.pol32 && a.pol_fixed != kPolRandom;
+    return 32 * (table ? R32Shape<1>::WARPS : R32Shape<0>::WARPS);
+}
 
 uint32_t pass32_kind(const PassArgs &a) {
     if (!use_staged(a)) return VEGAS_KERNEL_PASS32_DIRECT;
