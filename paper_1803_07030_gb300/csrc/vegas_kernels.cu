@@ -1157,8 +1157,7 @@ __global__ void renorm64_kernel(const RenormArgs a) {
     }
 }
 
-// FP32 spins: |S|^2 in FP64 (the squares of floats are exact in FP64, so n2 carries an error
-// of at most 2^-52), then the rescaling. GB300 runs few FP64 operations per SM and clock, so
+// FP32 spins: |S|^2 - 1 in FP64 (the squares of floats are exact in FP64), then the rescaling. GB300 runs few FP64 operations per SM and clock, so
 // the common case (s = 1 and |S|^2 within 2^-16 of 1, which every spin drawn or kept by a
 // Metropolis step is: |u| ~ 1e-7) avoids the FP64 square root and division: with u = n2 - 1
 // (exact), 1/sqrt(1 + u) - 1 = -u/2 + 3u^2/8 - (5/16) u^3 + ..., and S' = S + S d with d the
@@ -1173,15 +1172,17 @@ __global__ void renorm32_kernel(const RenormArgs a) {
         if (a.qis && a.qis[w >> a.log2R]) continue;  // discrete values keep their length
         const float4 v = S[w];
         const double x = v.x, y = v.y, z = v.z;
-        const double n2 = fma(x, x, fma(y, y, z * z));
+        // u = |S|^2 - 1 in three FP64 FMAs (z^2 - 1 is exact, then two roundings of 2^-53
+        // relative each), and s = 1 tested on its bits: few FP64 operations, as GB300 runs two
+        // per SM and clock
+        const double u = fma(x, x, fma(y, y, fma(z, z, -1.0)));
         const double s = a.norm[w >> a.log2R];
-        const double u = n2 - 1.0;
-        if (s == 1.0 && fabs(u) < 0x1p-16) {
-            const float uf = (float)u;
+        const float uf = (float)u;
+        if (__double_as_longlong(s) == 0x3FF0000000000000LL && fabsf(uf) < 0x1p-16f) {
             const float d = __fmul_rn(uf, fmaf(0.375f, uf, -0.5f));
             S[w] = make_float4(fmaf(v.x, d, v.x), fmaf(v.y, d, v.y), fmaf(v.z, d, v.z), 0.f);
         } else {
-            const double f = s / sqrt(n2);
+            const double f = s / sqrt(u + 1.0);
             S[w] = make_float4((float)(x * f), (float)(y * f), (float)(z * f), 0.f);
         }
     }
