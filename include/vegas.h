@@ -206,6 +206,12 @@ typedef struct {
                                distributed shared memory; -1 never; 0 the automatic choice times it
                                beside the other shapes (with variant 1 or 3 fixed: global memory).
                                Default 0. */
+    int32_t renorm_fold;    /* FP32, one sample of two colour classes swept by the kernel of 32
+                               replicas per site (per-class sweep): 0 renormalises the spins to
+                               their norms s_i inside the step's last class-1 pass instead of in
+                               a pass of their own (the same arithmetic at the same point of the
+                               step, so the same bits); -1 always in a pass of their own.
+                               Default 0. */
 } vegas_options;
 
 typedef struct {
@@ -258,6 +264,8 @@ typedef struct {
 #define VEGAS_KERNEL_RESIDENT32_SMEM 0x400u    /* resident sweep, spins in shared memory */
 #define VEGAS_KERNEL_CLUSTER32_SMEM 0x800u     /* cluster sweep, spins copied in every block's
                                                   shared memory */
+#define VEGAS_KERNEL_PASS32_R32_RENORM 0x1000u /* 32 replicas per site, the step's last class-1
+                                                  pass renormalising every spin (renorm_fold) */
 
 /* Fills *opt with the defaults listed above. */
 void vegas_default_options(vegas_options *opt);

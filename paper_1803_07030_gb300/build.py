@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libvegas.so")
 LIB_DEBUG = os.path.join(OUT_DIR, "libvegas_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["vegas_kernels.cu", "vegas_staged.cu", "vegas_policy32.cu", "vegas_wave.cu", "vegas_analysis.cu", "vegas_ising.cu", "vegas_capi.cu", "vegas_noalloc.cu", "vegas_loader.cpp"]
+SOURCES = ["vegas_kernels.cu", "vegas_staged.cu", "vegas_policy32.cu", "vegas_r32_renorm.cu", "vegas_wave.cu", "vegas_analysis.cu", "vegas_ising.cu", "vegas_capi.cu", "vegas_noalloc.cu", "vegas_loader.cpp"]
 HEADERS = ["vegas_internal.h", "vegas_device.cuh", "vegas_staged.cuh", "vegas_r32.cuh", os.path.join("..", "..", "include", "vegas.h")]
 
 

@@ -120,6 +120,12 @@ struct vegas_ctx {
     int wave_grid = 1;
     int32_t *d_tasks = nullptr;
     int32_t *d_deps = nullptr;  // wavefront sweep: distinct class-0 blocks of each class-1 block
+    // renormalisation folded into the step's last class-1 pass (per-class sweep, R = 32)
+    bool fold_ok = false;
+    PassArgs fold_args{};       // the class-1 pass's arguments with the fold's fields
+    int32_t fold_nb0 = 0;       // class-0 blocks
+    int32_t *d_fold_deps = nullptr, *d_fold_deg = nullptr;
+    uint32_t *d_fold_cnt = nullptr;
     uint32_t *d_done = nullptr, *d_ticket = nullptr;
     double *d_wave_partial = nullptr;
     int64_t *d_wave_slot_base = nullptr;
@@ -195,7 +201,8 @@ void free_all(vegas_ctx *c) {
                     c->d_slot_count, c->d_norm, c->d_partial, c->d_sched, c->d_hist, c->d_run, c->d_err, c->d_alog,
                     c->d_insts, c->d_cstart, c->d_queue, c->d_bar, c->d_coop_partial, c->d_acc, c->d_acc_hist,
                     c->d_pol, c->d_pol32, c->d_qis, c->d_sigma, c->d_adapt_n, c->d_type_hist, c->d_snap, c->d_segs,
-                    c->d_tasks, c->d_deps, c->d_done, c->d_ticket, c->d_pass_tickets, c->d_wave_partial, c->d_wave_slot_base, c->d_wave_slot_count};
+                    c->d_tasks, c->d_deps, c->d_done, c->d_ticket, c->d_pass_tickets, c->d_wave_partial, c->d_wave_slot_base, c->d_wave_slot_count,
+                    c->d_fold_deps, c->d_fold_deg, c->d_fold_cnt};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -278,15 +285,25 @@ bool set_cluster_shape(vegas_ctx *c, int cs, int threads, int split = 0, int gro
     return true;
 }
 
-// Launch one MCS: every colour class of every sample, then the reduction.
-void enqueue_mcs(vegas_ctx *c, cudaStream_t st, std::vector<cudaEvent_t> *ev) {
+// The step's last class-1 pass renormalises the spins (per-class sweep of a sample that
+// allows it; option renorm_fold).
+bool fold_active(const vegas_ctx *c) { return c->fold_ok && c->variant == 0; }
+
+// Launch one MCS: every colour class of every sample, then the reduction. last: the step's
+// last MCS, whose class-1 pass then renormalises every spin when fold_active.
+void enqueue_mcs(vegas_ctx *c, cudaStream_t st, std::vector<cudaEvent_t> *ev, bool last = false) {
+    const bool fold = last && fold_active(c);
+    if (fold) cudaMemsetAsync(c->d_fold_cnt, 0, sizeof(uint32_t) * (size_t)c->fold_nb0, st);
     int k = 0;
     for (const PassLaunch &p : c->passes) {
         if (ev) cudaEventRecord((*ev)[2 * k], st);
-        if (c->precision == 64)
+        if (c->precision == 64) {
             launch_pass64(p.args, p.grid, p.threads, st);
-        else
+        } else if (fold && k == 1) {
+            launch_pass32(c->fold_args, p.grid, st);
+        } else {
             launch_pass32(p.args, p.grid, st);
+        }
         if (ev) cudaEventRecord((*ev)[2 * k + 1], st);
         ++k;
     }
@@ -336,13 +353,14 @@ int enqueue_wave(vegas_ctx *c, cudaStream_t st) {
     return e;
 }
 
-// Renormalisation at the end of a step, then (option snapshots) the copy of the final state.
-void enqueue_renorm(vegas_ctx *c, cudaStream_t st) {
+// Renormalisation at the end of a step (unless the step's last pass did it: folded), then
+// (option snapshots) the copy of the final state.
+void enqueue_renorm(vegas_ctx *c, cudaStream_t st, bool folded = false) {
     RenormArgs ra{c->d_spins, c->d_norm, c->n_sites * c->R, c->log2R, c->d_qis};
     const int grid = (int)std::min<int64_t>((ra.n_work + 255) / 256, (int64_t)c->sm_count * 8);
     if (c->precision == 64)
         launch_renorm64(ra, grid, st);
-    else
+    else if (!folded)
         launch_renorm32(ra, grid, st);
     if (c->opt.snapshots) {
         const int64_t n16 = c->n_sites * c->R * (c->precision == 64 ? 2 : 1);
@@ -379,9 +397,9 @@ vegas_status step_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
     } else if (c->variant == 2) {
         enqueue_coop(c, c->cap_stream, mcs);
     } else {
-        for (int32_t m = 0; m < mcs; ++m) enqueue_mcs(c, c->cap_stream, nullptr);
+        for (int32_t m = 0; m < mcs; ++m) enqueue_mcs(c, c->cap_stream, nullptr, m == mcs - 1);
     }
-    enqueue_renorm(c, c->cap_stream);
+    enqueue_renorm(c, c->cap_stream, fold_active(c));
     CK(c, cudaStreamEndCapture(c->cap_stream, &g));
     cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
@@ -409,10 +427,9 @@ bool run_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
     cudaGraphExec_t ge = nullptr;
     bool capturing = false;
     auto give_up = [&]() {
-        if (capturing) {
-            cudaGraph_t junk = nullptr;
-            cudaStreamEndCapture(c->cap_stream, &junk);
-            if (junk) cudaGraphDestroy(junk);
+        if (capturing) {  // the graph it returns is the conditional node's body, owned by g
+            cudaGraph_t body_out = nullptr;
+            cudaStreamEndCapture(c->cap_stream, &body_out);
         }
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
@@ -442,9 +459,9 @@ bool run_graph(vegas_ctx *c, int32_t mcs, cudaGraphExec_t *out) {
     } else if (c->variant == 4) {
         for (int32_t m = 0; m < mcs; ++m) enqueue_wave(c, c->cap_stream);
     } else {
-        for (int32_t m = 0; m < mcs; ++m) enqueue_mcs(c, c->cap_stream, nullptr);
+        for (int32_t m = 0; m < mcs; ++m) enqueue_mcs(c, c->cap_stream, nullptr, m == mcs - 1);
     }
-    enqueue_renorm(c, c->cap_stream);
+    enqueue_renorm(c, c->cap_stream, fold_active(c));
     launch_run_ctrl(c->d_run, (unsigned long long)loop, c->cap_stream);
     cudaGraph_t captured = nullptr;
     capturing = false;
@@ -479,6 +496,31 @@ vegas_status set_device(vegas_ctx *c) {
     return VEGAS_OK;
 }
 
+// The distinct class-0 blocks (bs sites each, counted from the sample's first site) that each
+// block of bs class-1 sites links to: ascending, -1 padded, width per block; last[q] is the
+// largest of block q's (0 when it has none). False when a block links to more than width.
+bool class1_block_deps(const SampleInfo &si, const LoadedSample &l, int bs, int width, std::vector<int32_t> &deps,
+                       std::vector<int32_t> &last) {
+    const int32_t n1 = si.cstart[2] - si.cstart[1], nb1 = (n1 + bs - 1) / bs;
+    deps.assign((size_t)nb1 * width, -1);
+    last.assign((size_t)nb1, 0);
+    for (int32_t q = 0; q < nb1; ++q) {
+        int32_t *dq = &deps[(size_t)q * width];
+        int nd = 0;
+        const int32_t g0 = si.cstart[1] + q * bs, g1 = std::min(g0 + bs, si.cstart[2]);
+        for (int32_t g = g0; g < g1; ++g)
+            for (int64_t e = l.row_ptr[(size_t)g]; e < l.row_ptr[(size_t)g + 1]; ++e) {
+                const int32_t b = l.col[(size_t)e] / bs;
+                if (std::find(dq, dq + nd, b) != dq + nd) continue;
+                if (nd == width) return false;
+                dq[nd++] = b;
+            }
+        std::sort(dq, dq + nd);
+        last[(size_t)q] = nd > 0 ? dq[nd - 1] : 0;
+    }
+    return true;
+}
+
 }  // namespace
 
 extern "C" void vegas_default_options(vegas_options *o) {
@@ -508,6 +550,7 @@ extern "C" void vegas_default_options(vegas_options *o) {
     o->wave_lag = 0;
     o->wave_slab = 0;
     o->resident_smem = 0;
+    o->renorm_fold = 0;
 }
 
 // vegas_create without the exception guard; *made is the context under construction.
@@ -530,6 +573,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
     if (o.wave_lag < 0) return fail(nullptr, VEGAS_EINVAL, "wave_lag must be >= 0");
     if (o.wave_slab < -1) return fail(nullptr, VEGAS_EINVAL, "wave_slab must be >= -1");
     if (o.resident_smem < -1 || o.resident_smem > 1) return fail(nullptr, VEGAS_EINVAL, "resident_smem must be -1, 0 or 1");
+    if (o.renorm_fold < -1 || o.renorm_fold > 0) return fail(nullptr, VEGAS_EINVAL, "renorm_fold must be -1 or 0");
     if (o.resident_smem == 1 && o.variant != 1 && o.variant != 3 && o.variant != -1)
         return fail(nullptr, VEGAS_EINVAL, "resident_smem = 1 needs the resident or cluster sweep (variant 1, 3 or automatic)");
     if (o.cluster_split < 0) return fail(nullptr, VEGAS_EINVAL, "cluster_split must be >= 0");
@@ -1095,6 +1139,54 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         ca.skip_block = o.fault_inject == 1 ? 0 : -1;
         c->coop_eligible = true;
     }
+    // ---- renormalisation folded into the step's last class-1 pass: one sample of two colour
+    // classes swept by the R = 32 kernel without a policy table (every class-1 link to class 0),
+    // no discrete-valued sites, every class-0 block read by some class-1 block
+    if (c->precision == 32 && o.renorm_fold == 0 && n_samples == 1 && c->R == 32 && c->passes.size() == 2 &&
+        !c->d_qis && c->samples[0].n_colours == 2) {
+        const SampleInfo &si = c->samples[0];
+        const PassArgs &p0 = c->passes[0].args, &p1 = c->passes[1].args;
+        const bool whole = p0.g_begin == si.site_off && p0.g_end == si.site_off + si.cstart[1] &&
+                           p1.g_begin == si.site_off + si.cstart[1] && p1.g_end == si.site_off + si.cstart[2];
+        std::vector<int32_t> deps, last;
+        if (whole && p1.lower_mode == 1 && pass32_kind(p0) == VEGAS_KERNEL_PASS32_R32 &&
+            pass32_kind(p1) == VEGAS_KERNEL_PASS32_R32 &&
+            class1_block_deps(si, L[0], kFoldBlockSites, kFoldDeps, deps, last)) {
+            const int32_t nb0 = (si.cstart[1] + kFoldBlockSites - 1) / kFoldBlockSites;
+            std::vector<int32_t> deg((size_t)nb0, 0);
+            for (int32_t d : deps)
+                if (d >= 0) deg[(size_t)d]++;
+            if (nb0 > 0 && std::find(deg.begin(), deg.end(), 0) == deg.end()) {
+                DALLOC(c->d_fold_deps, sizeof(int32_t) * deps.size());
+                DALLOC(c->d_fold_deg, sizeof(int32_t) * deg.size());
+                DALLOC(c->d_fold_cnt, sizeof(uint32_t) * deg.size());
+                H2D(c->d_fold_deps, deps.data(), sizeof(int32_t) * deps.size());
+                H2D(c->d_fold_deg, deg.data(), sizeof(int32_t) * deg.size());
+                if (cudaMemsetAsync(c->d_fold_cnt, 0, sizeof(uint32_t) * deg.size(), c->stream) != cudaSuccess ||
+                    cudaStreamSynchronize(c->stream) != cudaSuccess) {  // the host vectors go out of scope
+                    c->err = "upload of the class-1 block reads failed";
+                    return bail(VEGAS_ECUDA);
+                }
+                PassArgs &fa = c->fold_args;
+                fa = p1;
+                fa.fold_deps = c->d_fold_deps;
+                fa.fold_deg = c->d_fold_deg;
+                fa.fold_cnt = c->d_fold_cnt;
+                fa.fold_norm = c->d_norm;
+                fa.fold_c0_begin = p0.g_begin;
+                fa.fold_c0_end = p0.g_end;
+                // sets the kernel's shared-memory limit; the same block shape as the plain pass
+                const bool same_shape = pass_blocks_per_sm(32, fa) == pass_blocks_per_sm(32, p1) &&
+                                        pass32_threads(fa) == pass32_threads(p1) && pass32_smem(fa) == pass32_smem(p1);
+                if (cudaGetLastError() != cudaSuccess || !same_shape) {
+                    c->err = "the renormalising class-1 pass does not fit beside the plain one";
+                    return bail(VEGAS_ECUDA);
+                }
+                c->fold_nb0 = nb0;
+                c->fold_ok = true;
+            }
+        }
+    }
     // ---- wavefront sweep: task order and completion flags
     if (o.variant == 4) {
         const SampleInfo &si = c->samples[0];
@@ -1112,25 +1204,11 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         constexpr int BS = kWaveBlockSites;
         const int32_t nb0 = (n0 + BS - 1) / BS, nb1 = (n1 + BS - 1) / BS;
         // the class-0 blocks that class-1 block q links to (distinct, ascending; D: the last)
-        std::vector<int32_t> D((size_t)nb1, 0), deps((size_t)nb1 * kWaveDeps, -1);
-        for (int32_t q = 0; q < nb1; ++q) {
-            int32_t *dq = &deps[(size_t)q * kWaveDeps];
-            int nd = 0;
-            const int32_t g0 = si.cstart[1] + q * BS, g1 = std::min(g0 + BS, si.cstart[2]);
-            for (int32_t g = g0; g < g1; ++g)
-                for (int64_t e = l.row_ptr[(size_t)g]; e < l.row_ptr[(size_t)g + 1]; ++e) {
-                    const int32_t b = l.col[(size_t)e] / BS;
-                    if (std::find(dq, dq + nd, b) != dq + nd) continue;
-                    if (nd == kWaveDeps) {
-                        c->err = "the wavefront sweep needs every block of " + std::to_string(BS) +
-                                 " class-1 sites to link to at most " + std::to_string(kWaveDeps) +
-                                 " blocks of class-0 sites";
-                        return bail(VEGAS_EINVAL);
-                    }
-                    dq[nd++] = b;
-                }
-            std::sort(dq, dq + nd);
-            D[(size_t)q] = nd > 0 ? dq[nd - 1] : 0;
+        std::vector<int32_t> D, deps;
+        if (!class1_block_deps(si, l, BS, kWaveDeps, deps, D)) {
+            c->err = "the wavefront sweep needs every block of " + std::to_string(BS) +
+                     " class-1 sites to link to at most " + std::to_string(kWaveDeps) + " blocks of class-0 sites";
+            return bail(VEGAS_EINVAL);
         }
         // class-0 blocks in memory order; each class-1 block after class-0 block
         // min(D + lag, nb0 - 1), so every dependency comes earlier in the list
@@ -1384,19 +1462,22 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
         CK(c, cudaEventCreate(&e1));
         CK(c, cudaEventRecord(e0, c->stream));
         double sweep_ms = 0.0;
+        bool folded = false;  // this step's last class-1 pass renormalised the spins
         // the kernels read the MCS counter, record index and schedule from the run state, which
         // the reductions (per-class sweep) and the advance kernel (resident sweep) move forward
         auto stream_mcs = [&](int32_t m0, int32_t n) -> vegas_status {
             for (int32_t m = m0; m < m0 + n; ++m) {
-                if (use_graph) {
+                const bool last = m == mcs - 1;
+                folded = folded || (last && fold_active(c));
+                if (use_graph && !(last && fold_active(c))) {
                     CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
                     c->graph_launches++;
                 } else if (c->opt.timing) {
                     std::vector<cudaEvent_t> sub(ev.begin() + (size_t)m * 2 * c->passes.size(),
                                                  ev.begin() + (size_t)(m + 1) * 2 * c->passes.size());
-                    enqueue_mcs(c, c->stream, &sub);
+                    enqueue_mcs(c, c->stream, &sub, last);
                 } else {
-                    enqueue_mcs(c, c->stream, nullptr);
+                    enqueue_mcs(c, c->stream, nullptr, last);
                 }
                 c->kernel_launches += (int64_t)c->passes.size() + 1;
                 c->sweep_launches += (int64_t)c->passes.size();
@@ -1460,6 +1541,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
             std::snprintf(step_name, sizeof step_name, "vegas_run step %d/%d", (int)s + 1, (int)n_steps);
             NvtxRange step_range(step_name);
             int32_t m0 = 0;
+            folded = false;
             if (!c->tuned && mcs >= 2) {
                 // autotune: time a few MCS of each eligible sweep and block shape on the real chain
                 // (all give the same spins) and keep the fastest for this context. Shapes: threads
@@ -1574,7 +1656,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     // the loop control
                     const int64_t sweep_k = c->variant == 4 ? 2 * (int64_t)mcs
                                             : (c->variant >= 1 ? 2 : (int64_t)mcs * ((int64_t)c->passes.size() + 1));
-                    c->kernel_launches += left * (sweep_k + 2 + (c->opt.snapshots ? 1 : 0));
+                    c->kernel_launches += left * (sweep_k + (fold_active(c) ? 1 : 2) + (c->opt.snapshots ? 1 : 0));
                     c->sweep_launches += c->variant == 4 ? left * (int64_t)mcs
                                          : (c->variant >= 1 ? left : left * (int64_t)mcs * (int64_t)c->passes.size());
                     break;
@@ -1587,13 +1669,13 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                 CK(c, cudaGraphLaunch(ge, c->stream));
                 c->graph_launches++;
                 const int64_t nodes = step_graph_nodes(c, mcs);
-                c->kernel_launches += c->variant >= 1 ? 3 + (c->opt.snapshots ? 1 : 0) : nodes;
+                c->kernel_launches += c->variant >= 1 ? 3 + (c->opt.snapshots ? 1 : 0) : nodes - (fold_active(c) ? 1 : 0);
                 c->sweep_launches += c->variant >= 1 ? 1 : (int64_t)mcs * (int64_t)c->passes.size();
                 continue;
             }
             if ((st = run_variant(c->variant, m0, mcs - m0)) != VEGAS_OK) return st;
-            enqueue_renorm(c, c->stream);
-            c->kernel_launches += c->opt.snapshots ? 2 : 1;
+            enqueue_renorm(c, c->stream, folded);
+            c->kernel_launches += (folded ? 0 : 1) + (c->opt.snapshots ? 1 : 0);
             if (c->opt.timing) {  // read this step's sweep timings before the events are reused
                 CK(c, cudaStreamSynchronize(c->stream));
                 if (c->variant == 4) {
@@ -1949,6 +2031,7 @@ extern "C" vegas_status vegas_stats(const vegas_ctx *c, vegas_stats_t *o) {
         else
             for (const PassLaunch &p : c->passes)
                 kinds |= c->precision == 64 ? VEGAS_KERNEL_PASS64 : pass32_kind(p.args);
+        if (fold_active(c)) kinds |= VEGAS_KERNEL_PASS32_R32_RENORM;
         o->sweep_kernels = kinds;
         return VEGAS_OK;
     } catch (...) {

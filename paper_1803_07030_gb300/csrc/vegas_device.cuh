@@ -266,5 +266,45 @@ __device__ __forceinline__ Site32 site_params32(const PassArgs &a, int PMv, int 
     return p;
 }
 
+// ------------------------------------------------------------------ FP32 renormalisation
+// u = |S|^2 - 1 of a float spin with no FP64 operation (GB300 runs two of those per SM and
+// clock): each square split into its rounded value and its exact rounding error (Dekker's
+// product, the error from one FMA), the rounded squares summed with Knuth's TwoSum (both
+// parts exact), 1 taken off exactly (Sterbenz: the sum lies in [1/2, 2] whenever |u| <= 1/2)
+// and the five error terms added in. The tail's own roundings stay below 2^-44, so for |u|
+// <= 1/2 the result is u + delta, |delta| < 2^-44, rounded once to a float; further out it
+// is only a rough value. The _rn intrinsics keep the products out of the sums.
+__device__ __forceinline__ float norm2_minus1_f32(float x, float y, float z) {
+    const float px = __fmul_rn(x, x), py = __fmul_rn(y, y), pz = __fmul_rn(z, z);
+    const float ex = fmaf(x, x, -px), ey = fmaf(y, y, -py), ez = fmaf(z, z, -pz);
+    const float s1 = __fadd_rn(px, py), b1 = __fsub_rn(s1, px);
+    const float t1 = __fadd_rn(__fsub_rn(px, __fsub_rn(s1, b1)), __fsub_rn(py, b1));
+    const float s2 = __fadd_rn(s1, pz), b2 = __fsub_rn(s2, s1);
+    const float t2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, b2)), __fsub_rn(pz, b2));
+    const float tail = __fadd_rn(__fadd_rn(t1, t2), __fadd_rn(__fadd_rn(ex, ey), ez));
+    return __fadd_rn(__fsub_rn(s2, 1.0f), tail);
+}
+
+// The FP64 formula s / sqrt(1 + u), u from three FP64 FMAs; not inlined, so that the rare
+// call costs the callers' common path no registers.
+__device__ __noinline__ float4 renorm_spin32_fp64(const float4 v, double s) {
+    const double x = v.x, y = v.y, z = v.z;
+    const double f = s / sqrt(fma(x, x, fma(y, y, fma(z, z, -1.0))) + 1.0);
+    return make_float4((float)(x * f), (float)(y * f), (float)(z * f), 0.f);
+}
+
+// S <- s S / |S| for one float spin. For s = 1 (tested on its bits) and |u| < 2^-16, u = |S|^2
+// - 1 (every spin a Metropolis step leaves has |u| ~ 1e-7): S + S d with d = -u/2 + 3u^2/8,
+// the first terms of (1 + u)^(-1/2) - 1, in one FMA per component and no FP64 operation;
+// otherwise the FP64 formula.
+__device__ __forceinline__ float4 renorm_spin32(const float4 v, double s) {
+    const float uf = norm2_minus1_f32(v.x, v.y, v.z);
+    if (__double_as_longlong(s) == 0x3FF0000000000000LL && fabsf(uf) < 0x1p-16f) {
+        const float d = __fmul_rn(uf, fmaf(0.375f, uf, -0.5f));
+        return make_float4(fmaf(v.x, d, v.x), fmaf(v.y, d, v.y), fmaf(v.z, d, v.z), 0.f);
+    }
+    return renorm_spin32_fp64(v, s);
+}
+
 }  // namespace
 }  // namespace vegas

@@ -191,6 +191,15 @@ struct PassArgs {
                                // by the MCS's reduction); unused by the other kernels
     int32_t pol_fixed;         // FP32 with a policy table: the one policy of every site of the
                                // pass, or -1 (mixed, or no table)
+    // The step's last class-1 pass of a two-class sample (R = 32 kernel) with the
+    // renormalisation folded in, else NULL: class-1 spins are stored renormalised, and each
+    // class-0 block of kFoldBlockSites sites is renormalised by the warp whose class-1 block is
+    // the last of its readers to finish.
+    const int32_t *fold_deps;  // [class-1 block][kFoldDeps] distinct class-0 blocks read, -1 padded
+    const int32_t *fold_deg;   // [class-0 block] class-1 blocks that read it
+    uint32_t *fold_cnt;        // [class-0 block] of those finished (zeroed before the pass)
+    const double *fold_norm;   // [global site] s_i
+    int32_t fold_c0_begin, fold_c0_end;  // global sites of class 0
     SiteParams32 u32;
     SiteParams64 u64;
 };
@@ -314,6 +323,8 @@ struct CoopArgs {
 // which makes the waits finite; each wait is still bounded by timeout_ns.
 constexpr int kWaveBlockSites = 8;   // sites per task of the wavefront sweep
 constexpr int kWaveDeps = 32;        // class-0 blocks a class-1 block may link to
+constexpr int kFoldBlockSites = 8;   // the R = 32 kernel's blocks of sites
+constexpr int kFoldDeps = 32;        // class-0 blocks a class-1 block may read (one per lane)
 
 struct WaveArgs {
     PassArgs pass;             // class 0: links, parameters, spins, run state; partial = [block][32][4]

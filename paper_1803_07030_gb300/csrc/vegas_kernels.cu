@@ -1100,6 +1100,9 @@ __global__ void __launch_bounds__(256) reduce_kernel(const ReduceArgs a) {
             const int64_t base = a.slot_base[s * a.n_groups + k];
             const int32_t cnt = a.slot_count[s * a.n_groups + k];
             double u[4] = {0.0, 0.0, 0.0, 0.0};
+            // unrolled so that several slots' loads are in flight at once; the sums still run
+            // in slot order
+#pragma unroll 8
             for (int32_t j = lane; j < cnt; j += 32) {
                 const double *p = a.partial + ((base + j) * a.R + r) * 4;
 #pragma unroll
@@ -1157,34 +1160,20 @@ __global__ void renorm64_kernel(const RenormArgs a) {
     }
 }
 
-// FP32 spins: |S|^2 - 1 in FP64 (the squares of floats are exact in FP64), then the rescaling. GB300 runs few FP64 operations per SM and clock, so
-// the common case (s = 1 and |S|^2 within 2^-16 of 1, which every spin drawn or kept by a
-// Metropolis step is: |u| ~ 1e-7) avoids the FP64 square root and division: with u = n2 - 1
-// (exact), 1/sqrt(1 + u) - 1 = -u/2 + 3u^2/8 - (5/16) u^3 + ..., and S' = S + S d with d the
-// first two terms in FP32, one FMA per component. d is off by at most (5/16)|u|^3 + 2^-24 |u|,
-// so S + S d is within 5e-13 |S| of S s/|S| at |u| = 2^-16 and within 1e-14 |S| at the usual
-// |u| ~ 1e-7: it rounds to the same float as the FP64 product unless that product lies that
-// close to a rounding boundary (half a float ulp is 3e-8 |S|). Other spins take the FP64
-// formula s / sqrt(n2).
+// FP32 spins (renorm_spin32): in the common case (s = 1 and |S|^2 within 2^-16 of 1, which
+// every spin drawn or kept by a Metropolis step is: |u| ~ 1e-7) no FP64 operation at all.
+// u = |S|^2 - 1 comes from FP32 products and sums with their exact errors, within 2^-44 of
+// the exact value; 1/sqrt(1 + u) - 1 = -u/2 + 3u^2/8 - (5/16) u^3 + ..., and S' = S + S d with
+// d the first two terms in FP32, one FMA per component. d is off by at most (5/16)|u|^3 +
+// 2^-24 |u| + 2^-45, so S + S d is within 5e-13 |S| of S s/|S| at |u| = 2^-16 and within
+// 5e-14 |S| at the usual |u| ~ 1e-7: it rounds to the same float as the exact product unless
+// that product lies that close to a rounding boundary (half a float ulp is 3e-8 |S|). Other
+// spins take the FP64 formula s / sqrt(|S|^2).
 __global__ void renorm32_kernel(const RenormArgs a) {
     float4 *S = (float4 *)a.spins;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < a.n_work; w += (int64_t)gridDim.x * blockDim.x) {
         if (a.qis && a.qis[w >> a.log2R]) continue;  // discrete values keep their length
-        const float4 v = S[w];
-        const double x = v.x, y = v.y, z = v.z;
-        // u = |S|^2 - 1 in three FP64 FMAs (z^2 - 1 is exact, then two roundings of 2^-53
-        // relative each), and s = 1 tested on its bits: few FP64 operations, as GB300 runs two
-        // per SM and clock
-        const double u = fma(x, x, fma(y, y, fma(z, z, -1.0)));
-        const double s = a.norm[w >> a.log2R];
-        const float uf = (float)u;
-        if (__double_as_longlong(s) == 0x3FF0000000000000LL && fabsf(uf) < 0x1p-16f) {
-            const float d = __fmul_rn(uf, fmaf(0.375f, uf, -0.5f));
-            S[w] = make_float4(fmaf(v.x, d, v.x), fmaf(v.y, d, v.y), fmaf(v.z, d, v.z), 0.f);
-        } else {
-            const double f = s / sqrt(u + 1.0);
-            S[w] = make_float4((float)(x * f), (float)(y * f), (float)(z * f), 0.f);
-        }
+        S[w] = renorm_spin32(S[w], a.norm[w >> a.log2R]);
     }
 }
 

@@ -66,8 +66,38 @@ __device__ __forceinline__ void block_partials_r32(double v[4], uint32_t nacc, u
     }
 }
 
-template <int PM, int LM, int POL>
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Renormalise class-0 block b (its sites x 32 replicas, lane = replica), four rows in flight.
+__device__ __forceinline__ void renorm_block32(const PassArgs &a, float4 *S, int b, int lane) {
+    const int g0 = a.fold_c0_begin + b * kFoldBlockSites;
+    const int n = min(kFoldBlockSites, a.fold_c0_end - g0);
+#pragma unroll
+    for (int h = 0; h < kFoldBlockSites; h += 4) {
+        float4 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (h + k < n) v[k] = __ldcg(S + (int64_t)(g0 + h + k) * 32 + lane);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (h + k < n) S[(int64_t)(g0 + h + k) * 32 + lane] = renorm_spin32(v[k], __ldg(a.fold_norm + g0 + h + k));
+    }
+}
+
+// RN = 1 (the step's last class-1 pass of a two-class sample, POL = 0): every attempt stores
+// its spin renormalised, and once a block's eight groups are done the warp counts the block
+// finished for each class-0 block it read (one per lane, an acquire-release add after the
+// block's copies have landed); the warp whose add completes a class-0 block's count of readers
+// renormalises that block. No class-1 block reads it afterwards in this pass and nothing else
+// reads spins before the pass ends, so every spin is renormalised after its last use of the
+// step: the same values as a renormalisation pass after the sweep.
+template <int PM, int LM, int POL, int RN = 0>
 __global__ void __launch_bounds__(R32Shape<POL>::WARPS * 32, R32Shape<POL>::MIN_BLOCKS) pass32_r32(const PassArgs a) {
+    static_assert(RN == 0 || POL == 0, "the folded renormalisation runs without a policy table");
     using Sh = R32Shape<POL>;
     constexpr int DEG = Sh::DEG, D = Sh::D, BS = Sh::BS, R = 32;
     constexpr int ROWS = Sh::ROWS;
@@ -75,6 +105,7 @@ __global__ void __launch_bounds__(R32Shape<POL>::WARPS * 32, R32Shape<POL>::MIN_
     constexpr int POL_OFF = Sh::POL_OFF;
     constexpr int SLOT = Sh::SLOT;
     constexpr int WARP_BYTES = Sh::WARP_BYTES;
+    static_assert(BS == kFoldBlockSites && kFoldDeps == 32, "the host's blocks of class sites; one per lane");
     extern __shared__ __align__(16) unsigned char smem[];
     const RunState *rs_ = a.run;
     const uint32_t t = rs_->t;
@@ -156,7 +187,7 @@ __global__ void __launch_bounds__(R32Shape<POL>::WARPS * 32, R32Shape<POL>::MIN_
             if (g < g_end) {
                 const unsigned char *slot = lslots + ls * SLOT;
                 const uint32_t orig = ((const uint32_t *)(slot + LINK_BYTES))[j];
-                staged_attempt<DEG, PM, LM, POL>(a, (const int4 *)slot + j * (DEG / 2),
+                staged_attempt<DEG, PM, LM, POL, RN != 0>(a, (const int4 *)slot + j * (DEG / 2),
                                                  rows + (j & 1) * (DEG + 1) * 32 + lane, orig, g, r, R, t, inst, rk0, rk1,
                                                  beta, B, S, acc, nan_seen, log_accepts,
                                                  (const PolicySite32 *)(slot + POL_OFF) + j, sigma);
@@ -172,6 +203,13 @@ __global__ void __launch_bounds__(R32Shape<POL>::WARPS * 32, R32Shape<POL>::MIN_
             else
                 issue_rows(sb2 + j + 2 - BS, ls ^ 1, j + 2 - BS, j & 1);
             cp_commit();
+        }
+        if (RN) {
+            const int dep = a.fold_deps[(int64_t)((sb - a.g_begin) / BS) * kFoldDeps + lane];
+            __syncwarp();  // every lane's copies of this block have landed and been read
+            const bool last = dep >= 0 && atom_add_acq_rel(a.fold_cnt + dep, 1u) + 1u == (uint32_t)__ldg(a.fold_deg + dep);
+            for (uint32_t m = __ballot_sync(0xFFFFFFFFu, last); m; m &= m - 1)
+                renorm_block32(a, S, __shfl_sync(0xFFFFFFFFu, dep, __ffs(m) - 1), lane);
         }
         sb = sb2;
         ls ^= 1;
@@ -189,5 +227,8 @@ __global__ void __launch_bounds__(R32Shape<POL>::WARPS * 32, R32Shape<POL>::MIN_
 // The R = 32 kernels specialised to one update policy (code 1 .. 6), built in their own
 // translation unit.
 PassFn select_r32_fixed(int pm, int lm, int code);
+// The R = 32 kernel of the step's last class-1 pass with the renormalisation folded in
+// (lower mode 1: every link of class 1 goes to class 0), in the same unit.
+PassFn select_r32_renorm(int pm);
 
 }  // namespace vegas

@@ -216,6 +216,7 @@ PassFn select_r32_table(int pm, int lm, bool pol) {
 // R = 32 kernel of a pass: with a policy table, specialised to the one policy of the class
 // when it has one (random: the kernel without a table, which draws the same trial).
 PassFn select_r32(const PassArgs &a) {
+    if (a.fold_deps) return select_r32_renorm(a.params_mode);
     if (a.pol32 && a.pol_fixed == kPolRandom) return select_r32_table(a.params_mode, a.lower_mode, false);
     if (a.pol32 && a.pol_fixed > kPolRandom) return select_r32_fixed(a.params_mode, a.lower_mode, a.pol_fixed);
     return select_r32_table(a.params_mode, a.lower_mode, a.pol32 != nullptr);
@@ -256,6 +257,7 @@ int pass32_threads(const PassArgs &a) {
 uint32_t pass32_kind(const PassArgs &a) {
     if (!use_staged(a)) return VEGAS_KERNEL_PASS32_DIRECT;
     if (use_r32(a)) {
+        if (a.fold_deps) return VEGAS_KERNEL_PASS32_R32_RENORM;
         if (!a.pol32 || a.pol_fixed == kPolRandom) return VEGAS_KERNEL_PASS32_R32;
         return a.pol_fixed > kPolRandom ? VEGAS_KERNEL_PASS32_R32_ONE_POLICY : VEGAS_KERNEL_PASS32_R32_POLICY;
     }

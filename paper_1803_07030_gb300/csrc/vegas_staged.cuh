@@ -47,8 +47,9 @@ __device__ __forceinline__ uint4 trial_block32(uint32_t orig, uint32_t t, uint32
 // One staged attempt with its random block c already drawn: links lk (int4 pairs), rows
 // row[j*32] (neighbour j) and row[DEG*32] (own) in shared memory; with POL, the site's
 // update policy *ps too (POL 1: the policy from the entry; POL 2 + c: every site has policy
-// c). LM 3 takes the lower sums as all (lower_all) or none at run time.
-template <int DEG, int PM, int LM, int POL = 0>
+// c). LM 3 takes the lower sums as all (lower_all) or none at run time. RN stores the spin
+// after the attempt renormalised, accepted or not (the step's last pass over the site).
+template <int DEG, int PM, int LM, int POL = 0, bool RN = false>
 __device__ __forceinline__ void staged_attempt_rw(const PassArgs &a, const int4 *lk, const float4 *row, uint32_t orig,
                                                   int g, int r, int R, uint32_t t, uint4 c, float beta, float B,
                                                   float4 *S, Acc32 &acc, bool &nan_seen, bool log_accepts,
@@ -75,21 +76,24 @@ __device__ __forceinline__ void staged_attempt_rw(const PassArgs &a, const int4 
         POL ? policy_trial32<(POL >= 2 ? POL - 2 : -1)>(*ps, sigma, Si, p.sn, c) : trial_random32(c, p.sn);
     attempt32<PM, LM == 3 ? 1 : LM>(Si, hxy, hz, lxy, lz, p, beta, B, P, c.z, Sn, ok, e_i, bad);
     nan_seen |= bad;
-    if (ok) S[(int64_t)g * R + r] = Sn;
+    if (RN)
+        S[(int64_t)g * R + r] = renorm_spin32(Sn, __ldg(a.fold_norm + g));
+    else if (ok)
+        S[(int64_t)g * R + r] = Sn;
     if (log_accepts)
         a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
     acc.add(e_i, Sn, ok);
 }
 
 // The same, drawing the random block first.
-template <int DEG, int PM, int LM, int POL = 0>
+template <int DEG, int PM, int LM, int POL = 0, bool RN = false>
 __device__ __forceinline__ void staged_attempt(const PassArgs &a, const int4 *lk, const float4 *row, uint32_t orig,
                                                int g, int r, int R, uint32_t t, uint32_t inst, const uint32_t *rk0,
                                                const uint32_t *rk1, float beta, float B, float4 *S, Acc32 &acc,
                                                bool &nan_seen, bool log_accepts, const PolicySite32 *ps = nullptr,
                                                float sigma = 0.f) {
-    staged_attempt_rw<DEG, PM, LM, POL>(a, lk, row, orig, g, r, R, t, trial_block32(orig, t, inst, rk0, rk1), beta, B,
-                                        S, acc, nan_seen, log_accepts, ps, sigma);
+    staged_attempt_rw<DEG, PM, LM, POL, RN>(a, lk, row, orig, g, r, R, t, trial_block32(orig, t, inst, rk0, rk1), beta,
+                                            B, S, acc, nan_seen, log_accepts, ps, sigma);
 }
 
 }  // namespace

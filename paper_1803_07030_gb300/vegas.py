@@ -45,7 +45,8 @@ class vegas_sample(C.Structure):
 # bits of vegas_stats_t.sweep_kernels (VEGAS_KERNEL_*)
 KERNEL_BITS = {"pass64": 0x1, "pass32_direct": 0x2, "pass32_staged": 0x4, "pass32_r32": 0x8,
                "pass32_r32_policy": 0x10, "resident32": 0x20, "coop32": 0x40, "cluster32": 0x80, "wave32": 0x100,
-               "pass32_r32_one_policy": 0x200, "resident32_smem": 0x400, "cluster32_smem": 0x800}
+               "pass32_r32_one_policy": 0x200, "resident32_smem": 0x400, "cluster32_smem": 0x800,
+               "pass32_r32_renorm": 0x1000}
 
 
 def sweep_kernel_names(bits: int) -> list:
@@ -84,6 +85,7 @@ class vegas_options(C.Structure):
         ("wave_lag", C.c_int32),
         ("wave_slab", C.c_int32),
         ("resident_smem", C.c_int32),
+        ("renorm_fold", C.c_int32),
     ]
 
 
@@ -450,7 +452,8 @@ class Context:
     graphs (1 a run as one graph, 2 a graph per step, 0 none), the cluster and grouping shapes
     (cluster_blocks, cluster_threads, cluster_split, group_threads, group_sites; 0 =
     automatic or off), wave_lag, wave_slab, resident_smem (1: the resident sweep keeps spins in
-    shared memory), and the testing options max_blocks, pipeline_depth,
+    shared memory), renorm_fold (-1: the renormalisation always in a pass of its own), and the
+    testing options max_blocks, pipeline_depth,
     timeout_ns, fault_inject. library: load another build (the debug build) for this and
     later contexts.
     """
@@ -461,7 +464,8 @@ class Context:
                  pipeline_depth: int = 0, timeout_ns: int = 0, fault_inject: int = 0,
                  type_stats: bool = False, snapshots: bool = False, cluster_blocks: int = 0,
                  cluster_threads: int = 0, cluster_split: int = 0, group_threads: int = 0, group_sites: int = 0,
-                 wave_lag: int = 0, wave_slab: int = 0, resident_smem: int = 0, library: Optional[str] = None):
+                 wave_lag: int = 0, wave_slab: int = 0, resident_smem: int = 0, renorm_fold: int = 0,
+                 library: Optional[str] = None):
         self.samples = list(samples)
         self.n_sites = [int(np.asarray(s.row_ptr).shape[0] - 1) for s in self.samples]
         if library is not None:
@@ -491,6 +495,7 @@ class Context:
         o.wave_lag = wave_lag
         o.wave_slab = wave_slab
         o.resident_smem = resident_smem
+        o.renorm_fold = renorm_fold
         o.cuda_stream = _current_stream() if stream == "torch" else stream
         self.replicas = replicas
         self.ptr = None

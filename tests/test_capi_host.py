@@ -156,7 +156,7 @@ def test_policy_table_without_params_rejected(lib):
                                  {"cluster_split": -1}, {"group_threads": 100}, {"group_sites": -1},
                                  {"wave_lag": -1}, {"variant": 5}, {"wave_slab": -2}, {"resident_smem": 2},
                                  {"resident_smem": -2}, {"resident_smem": 1, "variant": 0},
-                                 {"resident_smem": 1, "variant": 2}])
+                                 {"resident_smem": 1, "variant": 2}, {"renorm_fold": 1}, {"renorm_fold": -2}])
 def test_invalid_options_rejected(lib, opt):
     st, msg = _create_status([sc_periodic(4)], **opt)
     assert st == vb.EINVAL, (opt, msg)

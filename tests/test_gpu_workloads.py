@@ -102,7 +102,8 @@ def test_headline_kernel_statistics_pm_j_glass_r32():
         with ctx([s], precision=32, replicas=R, seed=101 + 2 * attempt, variant=0) as c:
             c.run(T, B, mcs)
             st = c.stats()
-            assert vb.sweep_kernel_names(st["sweep_kernels"]) == ["pass32_r32"], st["sweep_kernels"]
+            # the headline kernel, its step's last class-1 pass with the renormalisation folded in
+            assert vb.sweep_kernel_names(st["sweep_kernels"]) == ["pass32_r32", "pass32_r32_renorm"], st["sweep_kernels"]
             H = c.history()
         ref = oracle.run(s, T, B, mcs, seed=102 + 2 * attempt, n_threads=oracle_threads())["history"]
         pts = []
@@ -170,7 +171,7 @@ def test_hysteresis_reversal_ensemble():
     def run(attempt):
         with ctx([s], replicas=R, seed=21 + 2 * attempt, variant=0) as c:
             c.run(T, B, mcs)
-            assert vb.sweep_kernel_names(c.stats()["sweep_kernels"]) == ["pass32_r32"]
+            assert vb.sweep_kernel_names(c.stats()["sweep_kernels"]) == ["pass32_r32", "pass32_r32_renorm"]
             H = c.history()
         ref = oracle.run(s, T, B, mcs, seed=22 + 2 * attempt, n_threads=oracle_threads())["history"]
         return trajectories(H), trajectories(ref)
