@@ -1082,59 +1082,66 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
 }
 
 // ------------------------------------------------------------------ per-MCS reduction
-// One warp per instance sums its sample's block partials over every colour class in a
-// fixed order and appends the record; the last block to finish advances the MCS
+// One block per instance sums its sample's block partials over every colour class in a fixed
+// order (thread k takes slots k, k + 256, ... in turn, then a butterfly inside each warp and
+// the warps in order) and appends the record; the last block to finish advances the MCS
 // counter and the record index (no waiting: a ticket counter, not a barrier). Block 0 also
 // zeroes the passes' block counters: every pass of this MCS has finished.
 __global__ void __launch_bounds__(256) reduce_kernel(const ReduceArgs a) {
+    __shared__ double red[8][4];
     RunState *rs = a.run;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int il = blockIdx.x * 8 + warp;
+    const int il = blockIdx.x;
     const uint32_t rec = rs->rec;
     if (blockIdx.x == 0 && a.tickets)
         for (int k = threadIdx.x; k < a.n_tickets; k += blockDim.x) a.tickets[k] = 0u;
-    if (il < a.n_inst) {
-        const int s = il / a.R, r = il % a.R;
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int k = 0; k < a.n_groups; ++k) {  // type groups in order, then their total
-            const int64_t base = a.slot_base[s * a.n_groups + k];
-            const int32_t cnt = a.slot_count[s * a.n_groups + k];
-            double u[4] = {0.0, 0.0, 0.0, 0.0};
-            // unrolled so that several slots' loads are in flight at once; the sums still run
-            // in slot order
-#pragma unroll 8
-            for (int32_t j = lane; j < cnt; j += 32) {
-                const double *p = a.partial + ((base + j) * a.R + r) * 4;
+    const int s = il / a.R, r = il % a.R;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < a.n_groups; ++k) {  // type groups in order, then their total
+        const int64_t base = a.slot_base[s * a.n_groups + k];
+        const int32_t cnt = a.slot_count[s * a.n_groups + k];
+        double u[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
+            const double4_32a p = *(const double4_32a *)(a.partial + ((base + j) * a.R + r) * 4);
+            u[0] += p.x;
+            u[1] += p.y;
+            u[2] += p.z;
+            u[3] += p.w;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) u[q] += p[q];
-            }
-            for (int off = 16; off > 0; off >>= 1) {
+            for (int q = 0; q < 4; ++q) u[q] += __shfl_xor_sync(0xFFFFFFFFu, u[q], off);
+        }
+        if (lane == 0)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) u[q] += __shfl_xor_sync(0xFFFFFFFFu, u[q], off);
-            }
+            for (int q = 0; q < 4; ++q) red[warp][q] = u[q];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t4[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] += u[q];
-            if (lane == 0 && a.n_types > 0 && rs->type_hist) {
+                for (int q = 0; q < 4; ++q) t4[q] += red[w][q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] += t4[q];
+            if (a.n_types > 0 && rs->type_hist) {
                 double *th = rs->type_hist + (((int64_t)rec * a.n_inst + il) * a.n_types + k) * 3;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) th[c] = u[c + 1];
+                for (int c = 0; c < 3; ++c) th[c] = t4[c + 1];
             }
         }
-        if (lane == 0) {
-            double *h = rs->hist + ((int64_t)rec * a.n_inst + il) * 4;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) h[q] = v[q];
-            if (rs->acc) {  // accepted attempts of this MCS; the adaptive width follows them
-                const uint32_t n = rs->acc[il];
-                rs->acc[il] = 0;
-                if (rs->acc_hist) rs->acc_hist[(int64_t)rec * a.n_inst + il] = n;
-                if (a.adapt_n && a.adapt_n[il] > 0 && rs->sigma && rec % rs->mcs < rs->mcs / 5)
-                    rs->sigma[il] = adapt_width(rs->sigma[il], n, a.adapt_n[il]);
-            }
-        }
+        __syncthreads();  // red is reused by the next group
     }
-    __syncthreads();
     if (threadIdx.x == 0) {
+        double *h = rs->hist + ((int64_t)rec * a.n_inst + il) * 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h[q] = v[q];
+        if (rs->acc) {  // accepted attempts of this MCS; the adaptive width follows them
+            const uint32_t n = rs->acc[il];
+            rs->acc[il] = 0;
+            if (rs->acc_hist) rs->acc_hist[(int64_t)rec * a.n_inst + il] = n;
+            if (a.adapt_n && a.adapt_n[il] > 0 && rs->sigma && rec % rs->mcs < rs->mcs / 5)
+                rs->sigma[il] = adapt_width(rs->sigma[il], n, a.adapt_n[il]);
+        }
         __threadfence();
         const uint32_t done = atomicAdd(&rs->ticket, 1u);
         if (done == gridDim.x - 1) {
@@ -1278,8 +1285,7 @@ void launch_pass64(const PassArgs &a, int grid, int threads, void *stream) {
 }
 
 void launch_reduce(const ReduceArgs &a, void *stream) {
-    const int grid = (a.n_inst + 7) / 8;
-    reduce_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    reduce_kernel<<<a.n_inst, 256, 0, (cudaStream_t)stream>>>(a);
 }
 
 void launch_renorm32(const RenormArgs &a, int grid, void *stream) {
