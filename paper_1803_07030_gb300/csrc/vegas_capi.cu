@@ -50,6 +50,15 @@ struct PassLaunch {
     int64_t slot = 0;          // first block slot
 };
 
+// One sweep launch of an MCS of the per-class sweep: a single pass, or the direct FP32 passes
+// of one colour class of several samples (or type groups) merged into one launch.
+struct LaunchGroup {
+    std::vector<int> passes;     // indices into the context's passes
+    int grid = 0;                // merged: the passes' blocks together
+    PassArgs *d_args = nullptr;  // merged: the passes' arguments
+    int32_t *d_first = nullptr;  // merged: first block of each pass, and the total
+};
+
 }  // namespace
 
 struct vegas_ctx {
@@ -120,6 +129,7 @@ struct vegas_ctx {
     int wave_grid = 1;
     int32_t *d_tasks = nullptr;
     int32_t *d_deps = nullptr;  // wavefront sweep: distinct class-0 blocks of each class-1 block
+    std::vector<LaunchGroup> launches;  // the per-class sweep's launches of one MCS, in class order
     // renormalisation folded into the step's last class-1 pass (per-class sweep, R = 32)
     bool fold_ok = false;
     PassArgs fold_args{};       // the class-1 pass's arguments with the fold's fields
@@ -205,6 +215,10 @@ void free_all(vegas_ctx *c) {
                     c->d_fold_deps, c->d_fold_deg, c->d_fold_cnt};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (LaunchGroup &lg : c->launches) {
+        if (lg.d_args) cudaFree(lg.d_args);
+        if (lg.d_first) cudaFree(lg.d_first);
+    }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
@@ -295,11 +309,14 @@ void enqueue_mcs(vegas_ctx *c, cudaStream_t st, std::vector<cudaEvent_t> *ev, bo
     const bool fold = last && fold_active(c);
     if (fold) cudaMemsetAsync(c->d_fold_cnt, 0, sizeof(uint32_t) * (size_t)c->fold_nb0, st);
     int k = 0;
-    for (const PassLaunch &p : c->passes) {
+    for (const LaunchGroup &lg : c->launches) {
+        const PassLaunch &p = c->passes[(size_t)lg.passes[0]];
         if (ev) cudaEventRecord((*ev)[2 * k], st);
-        if (c->precision == 64) {
+        if (lg.d_args) {
+            launch_pass32_multi(p.args, lg.d_args, lg.d_first, (int32_t)lg.passes.size(), lg.grid, st);
+        } else if (c->precision == 64) {
             launch_pass64(p.args, p.grid, p.threads, st);
-        } else if (fold && k == 1) {
+        } else if (fold && lg.passes[0] == 1) {
             launch_pass32(c->fold_args, p.grid, st);
         } else {
             launch_pass32(p.args, p.grid, st);
@@ -375,7 +392,7 @@ constexpr int64_t kMaxStepGraphNodes = 20000;
 // -1 when such a graph would be too large.
 int64_t step_graph_nodes(const vegas_ctx *c, int32_t mcs) {
     const int64_t sweep = c->variant == 4 ? 3 * (int64_t)mcs
-                                         : (c->variant >= 1 ? 3 : (int64_t)mcs * ((int64_t)c->passes.size() + 1));
+                                         : (c->variant >= 1 ? 3 : (int64_t)mcs * ((int64_t)c->launches.size() + 1));
     const int64_t n = sweep + 1 + (c->opt.snapshots ? 1 : 0);
     return n <= kMaxStepGraphNodes ? n : -1;
 }
@@ -980,6 +997,58 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         return bail(VEGAS_ECUDA);
     }
     for (size_t k = 0; k < c->passes.size(); ++k) c->passes[k].args.ticket = c->d_pass_tickets + k;
+    // the sweep's launches of one MCS, class by class: the direct FP32 passes of a class that
+    // share a kernel go out as one launch, every other pass alone
+    {
+        int32_t n_col = 0;
+        for (const PassLaunch &pl : c->passes) n_col = std::max(n_col, pl.col + 1);
+        for (int32_t col = 0; col < n_col; ++col) {
+            std::vector<LaunchGroup> merged;  // by kernel: params mode, lower mode, policy table
+            std::vector<int> keys;
+            for (size_t k = 0; k < c->passes.size(); ++k) {
+                const PassLaunch &pl = c->passes[k];
+                if (pl.col != col) continue;
+                const PassArgs &a = pl.args;
+                if (c->precision == 64 || !pass32_direct(a)) {
+                    LaunchGroup lg;
+                    lg.passes.push_back((int)k);
+                    c->launches.push_back(lg);
+                    continue;
+                }
+                const int key = (a.params_mode * 3 + a.lower_mode) * 2 + (a.pol32 ? 1 : 0);
+                size_t q = 0;
+                while (q < keys.size() && keys[q] != key) ++q;
+                if (q == keys.size()) {
+                    keys.push_back(key);
+                    merged.emplace_back();
+                }
+                merged[q].passes.push_back((int)k);
+            }
+            for (LaunchGroup &lg : merged) {
+                if (lg.passes.size() > 1) {
+                    std::vector<PassArgs> args;
+                    std::vector<int32_t> first(1, 0);
+                    for (int k : lg.passes) {
+                        args.push_back(c->passes[(size_t)k].args);
+                        first.push_back(first.back() + c->passes[(size_t)k].grid);
+                    }
+                    lg.grid = first.back();
+                    c->launches.push_back(lg);  // owns the buffers from here (freed with the context)
+                    LaunchGroup &own = c->launches.back();
+                    DALLOC(own.d_args, sizeof(PassArgs) * args.size());
+                    DALLOC(own.d_first, sizeof(int32_t) * first.size());
+                    H2D(own.d_args, args.data(), sizeof(PassArgs) * args.size());
+                    H2D(own.d_first, first.data(), sizeof(int32_t) * first.size());
+                    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {  // the host vectors go out of scope
+                        c->err = "upload of the merged passes failed";
+                        return bail(VEGAS_ECUDA);
+                    }
+                } else {
+                    c->launches.push_back(lg);
+                }
+            }
+        }
+    }
     DALLOC(c->d_slot_base, sizeof(int64_t) * h_sb.size());
     DALLOC(c->d_slot_count, sizeof(int32_t) * h_sc.size());
     H2D(c->d_slot_base, h_sb.data(), sizeof(int64_t) * h_sb.size());
@@ -1454,7 +1523,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
         if (use_graph && (st = build_graph(c)) != VEGAS_OK) return st;
         std::vector<cudaEvent_t> ev;
         if (c->opt.timing) {
-            ev.resize(2 * c->passes.size() * (size_t)mcs + 2);
+            ev.resize(2 * c->launches.size() * (size_t)mcs + 2);
             for (auto &x : ev) CK(c, cudaEventCreate(&x));
         }
         cudaEvent_t e0, e1;
@@ -1473,14 +1542,14 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
                     c->graph_launches++;
                 } else if (c->opt.timing) {
-                    std::vector<cudaEvent_t> sub(ev.begin() + (size_t)m * 2 * c->passes.size(),
-                                                 ev.begin() + (size_t)(m + 1) * 2 * c->passes.size());
+                    std::vector<cudaEvent_t> sub(ev.begin() + (size_t)m * 2 * c->launches.size(),
+                                                 ev.begin() + (size_t)(m + 1) * 2 * c->launches.size());
                     enqueue_mcs(c, c->stream, &sub, last);
                 } else {
                     enqueue_mcs(c, c->stream, nullptr, last);
                 }
-                c->kernel_launches += (int64_t)c->passes.size() + 1;
-                c->sweep_launches += (int64_t)c->passes.size();
+                c->kernel_launches += (int64_t)c->launches.size() + 1;
+                c->sweep_launches += (int64_t)c->launches.size();
             }
             return VEGAS_OK;
         };
@@ -1655,10 +1724,10 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     // reduction); or mcs x (passes + reduction)), the renormalisation, the snapshot,
                     // the loop control
                     const int64_t sweep_k = c->variant == 4 ? 2 * (int64_t)mcs
-                                            : (c->variant >= 1 ? 2 : (int64_t)mcs * ((int64_t)c->passes.size() + 1));
+                                            : (c->variant >= 1 ? 2 : (int64_t)mcs * ((int64_t)c->launches.size() + 1));
                     c->kernel_launches += left * (sweep_k + (fold_active(c) ? 1 : 2) + (c->opt.snapshots ? 1 : 0));
                     c->sweep_launches += c->variant == 4 ? left * (int64_t)mcs
-                                         : (c->variant >= 1 ? left : left * (int64_t)mcs * (int64_t)c->passes.size());
+                                         : (c->variant >= 1 ? left : left * (int64_t)mcs * (int64_t)c->launches.size());
                     break;
                 }
             }
@@ -1670,7 +1739,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                 c->graph_launches++;
                 const int64_t nodes = step_graph_nodes(c, mcs);
                 c->kernel_launches += c->variant >= 1 ? 3 + (c->opt.snapshots ? 1 : 0) : nodes - (fold_active(c) ? 1 : 0);
-                c->sweep_launches += c->variant >= 1 ? 1 : (int64_t)mcs * (int64_t)c->passes.size();
+                c->sweep_launches += c->variant >= 1 ? 1 : (int64_t)mcs * (int64_t)c->launches.size();
                 continue;
             }
             if ((st = run_variant(c->variant, m0, mcs - m0)) != VEGAS_OK) return st;
@@ -1689,7 +1758,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     CK(c, cudaEventElapsedTime(&ms, ev[ev.size() - 2], ev[ev.size() - 1]));
                     sweep_ms += ms;
                 } else {
-                    for (size_t k = (size_t)m0 * 2 * c->passes.size(); k + 1 < ev.size() - 2; k += 2) {
+                    for (size_t k = (size_t)m0 * 2 * c->launches.size(); k + 1 < ev.size() - 2; k += 2) {
                         float ms = 0.f;
                         CK(c, cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
                         sweep_ms += ms;

@@ -348,6 +348,11 @@ PassFn select_pass32(const PassArgs &a);
 int pass32_smem(const PassArgs &a);
 int pass32_threads(const PassArgs &a);  // threads per block of that kernel
 // The kernel select_pass32 picks, as a VEGAS_KERNEL_* bit of include/vegas.h.
+// The direct FP32 passes of one colour class of several samples (same kernel, key's template
+// fields) in one launch; passes[p] runs blocks first[p] .. first[p + 1] - 1 of the grid.
+void launch_pass32_multi(const PassArgs &key, const PassArgs *passes, const int32_t *first, int32_t n, int grid,
+                         void *stream);
+bool pass32_direct(const PassArgs &a);  // the pass runs the direct (plain-load) kernel
 uint32_t pass32_kind(const PassArgs &a);
 PassFn select_direct(int pm, int lm, bool pol);
 

@@ -477,8 +477,10 @@ __device__ __forceinline__ void smem_segment(const int4 *ell, const int32_t *ori
 // Any row length: reads row_ptr and gathers neighbours with plain loads.
 // PM: params_mode (0 uniform without anisotropy, 1 uniform, 2 per site).
 // LM: lower_mode (0 no lower links, 1 all links lower, 2 test each link).
+// block / grid: the block's index in the pass and the pass's block count (blockIdx.x and
+// gridDim.x in the pass's own launch).
 template <int PM, int LM, int POL>
-__global__ void __launch_bounds__(kThreads, 2) pass32_kernel(const PassArgs a) {
+__device__ __forceinline__ void pass32_body(const PassArgs &a, int block, int grid) {
     const RunState *rs = a.run;
     const uint32_t t = rs->t;
     const uint32_t step = rs->rec / rs->mcs;
@@ -487,8 +489,8 @@ __global__ void __launch_bounds__(kThreads, 2) pass32_kernel(const PassArgs a) {
     float4 *S = (float4 *)a.spins;
     const int2 *E = (const int2 *)a.edges;
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t w0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)grid * blockDim.x;
+    const int64_t w0 = (int64_t)block * blockDim.x + threadIdx.x;
     // a thread always serves the same replica (the stride is a multiple of 32 >= R)
     const int r = (int)(w0 & (R - 1));
     const uint32_t inst = (uint32_t)(a.inst0 + r);
@@ -511,7 +513,42 @@ __global__ void __launch_bounds__(kThreads, 2) pass32_kernel(const PassArgs a) {
             a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
     }
     acc.flush();
-    block_partials(acc.d, acc.nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs, a.inst_local0));
+    block_partials(acc.d, acc.nacc, R, a.partial + (int64_t)block * R * 4, acc_counters(rs, a.inst_local0));
+}
+
+template <int PM, int LM, int POL>
+__global__ void __launch_bounds__(kThreads, 2) pass32_kernel(const PassArgs a) {
+    pass32_body<PM, LM, POL>(a, blockIdx.x, gridDim.x);
+}
+
+// Several passes of one colour class with the same kernel (the samples of a batch) in one
+// launch: block b runs block b - first[p] of pass p, first[p] <= b < first[p + 1], with that
+// pass's arguments (copied to shared memory) and block count, so every block does what it does
+// in the pass's own launch and writes the same partial sums.
+template <int PM, int LM, int POL>
+__global__ void __launch_bounds__(kThreads, 2) pass32_multi_kernel(const PassArgs *passes, const int32_t *first,
+                                                                   int32_t n) {
+    static_assert(sizeof(PassArgs) % 8 == 0, "copied as 8-byte words");
+    __shared__ PassArgs s_a;
+    __shared__ int s_p;
+    if (threadIdx.x == 0) {  // the last pass whose first block is <= blockIdx.x
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(first + mid) <= (int32_t)blockIdx.x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        s_p = lo;
+    }
+    __syncthreads();
+    const int p = s_p;
+    const uint64_t *src = (const uint64_t *)(passes + p);
+    for (int i = threadIdx.x; i < (int)(sizeof(PassArgs) / 8); i += blockDim.x) ((uint64_t *)&s_a)[i] = __ldg(src + i);
+    __syncthreads();
+    const int f = __ldg(first + p);
+    pass32_body<PM, LM, POL>(s_a, (int)blockIdx.x - f, __ldg(first + p + 1) - f);
 }
 
 // ------------------------------------------------------------------ resident (persistent) sweep
@@ -1274,6 +1311,26 @@ PassFn select_direct(int pm, int lm, bool pol) {
         },
     };
     return tab[pol ? 1 : 0][pm][lm];
+}
+
+using MultiFn = void (*)(const PassArgs *, const int32_t *, int32_t);
+
+void launch_pass32_multi(const PassArgs &key, const PassArgs *passes, const int32_t *first, int32_t n, int grid,
+                         void *stream) {
+    static const MultiFn tab[2][3][3] = {
+        {
+            {pass32_multi_kernel<0, 0, 0>, pass32_multi_kernel<0, 1, 0>, pass32_multi_kernel<0, 2, 0>},
+            {pass32_multi_kernel<1, 0, 0>, pass32_multi_kernel<1, 1, 0>, pass32_multi_kernel<1, 2, 0>},
+            {pass32_multi_kernel<2, 0, 0>, pass32_multi_kernel<2, 1, 0>, pass32_multi_kernel<2, 2, 0>},
+        },
+        {
+            {pass32_multi_kernel<0, 0, 1>, pass32_multi_kernel<0, 1, 1>, pass32_multi_kernel<0, 2, 1>},
+            {pass32_multi_kernel<1, 0, 1>, pass32_multi_kernel<1, 1, 1>, pass32_multi_kernel<1, 2, 1>},
+            {pass32_multi_kernel<2, 0, 1>, pass32_multi_kernel<2, 1, 1>, pass32_multi_kernel<2, 2, 1>},
+        },
+    };
+    tab[key.pol32 ? 1 : 0][key.params_mode][key.lower_mode]<<<grid, kThreads, 0, (cudaStream_t)stream>>>(passes, first,
+                                                                                                            n);
 }
 
 void launch_pass32(const PassArgs &a, int grid, void *stream) {

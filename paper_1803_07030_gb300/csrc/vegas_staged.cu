@@ -248,6 +248,8 @@ PassFn select_pass32(const PassArgs &a) {
 
 int pass32_smem(const PassArgs &a) { return use_staged(a) ? staged_smem(a) : 0; }
 
+bool pass32_direct(const PassArgs &a) { return !use_staged(a); }
+
 int pass32_threads(const PassArgs &a) {
     if (!use_r32(a)) return kThreads;
     const bool table = a.pol32 && a.pol_fixed != kPolRandom;

@@ -393,6 +393,30 @@ def test_persistent_run_is_one_graph_launch(variant):
         assert np.array_equal(a.history(), b.history())
 
 
+@pytest.mark.parametrize("timing", [False, True])
+def test_per_class_sweep_merges_the_samples_passes(timing):
+    """The per-class sweep sends the direct passes of one colour class of every sample of a
+    batch out as one launch (each block runs the block it runs in its pass's own launch): far
+    fewer launches than passes, and the spins of the resident sweep bit for bit, with one
+    graph per run and with direct launches timed by events."""
+    ps = nanoparticle_batch(10, seed=15, r_max=6.0)
+    T = np.linspace(0.4, 2.0, len(ps))[:, None] * np.array([[1.0, 0.8]])
+    B = np.full_like(T, 0.2)
+    mcs = 6
+    with ctx(ps, seed=31, variant=0, timing=timing, accept_log_mcs=2) as a, \
+            ctx(ps, seed=31, variant=1, accept_log_mcs=2) as b:
+        a.run(T, B, mcs)
+        b.run(T, B, mcs)
+        st = a.stats()
+        assert st["variant"] == 0
+        # two steps of four colour classes, at most three kernels (lower-link modes) per class
+        assert st["sweep_launches"] <= 2 * mcs * 4 * 3 < 2 * mcs * 4 * len(ps)
+        for i in range(len(ps)):
+            assert np.array_equal(a.spins(i), b.spins(i)), i
+        assert np.array_equal(a.accept_log(), b.accept_log())
+        assert_fp32_history_close(a.history(), b.history(), max(p.n_sites for p in ps))
+
+
 def test_autotuner_picks_a_sweep_and_block_shape():
     """The first run times every eligible sweep and block shape (threads per block of the
     resident sweep, blocks per cluster of the cluster sweep) on the real chain; whatever it
