@@ -79,7 +79,8 @@ def test_acceptance_probability_sets_the_two_state_law(beta_B):
 
 @pytest.mark.parametrize("norm", [1.0, 2.0])
 def test_fp32_renormalisation_rounds_like_the_fp64_formula(norm):
-    """The end-of-step renormalisation of FP32 spins (S <- s S/|S| with |S|^2 in FP64) against
+    """The end-of-step renormalisation of FP32 spins (S <- s S/|S|, |S|^2 - 1 from FP32 products
+    and sums with their exact errors, the FP64 formula off the series' range) against
     the FP64 formula evaluated on the host and rounded to FP32, for spins whose norm is off by
     up to 1e-7 (what Metropolis steps leave) and 1e-5 (the series' range), 2^-11, 0.5 and 2
     (the direct formula), with spin norms s = 1 and 2. A ferromagnet held at T = 1e-6 rejects every
