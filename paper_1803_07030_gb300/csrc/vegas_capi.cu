@@ -122,6 +122,7 @@ struct vegas_ctx {
     bool coop_eligible = false;
     CoopArgs coop{};
     int coop_grid = 1;
+    int coop_grid_max = 1;  // every block the GPU holds at once, capped by the widest class and max_blocks
     GridBarrier *d_bar = nullptr;
     double *d_coop_partial = nullptr;
     // wavefront sweep: both classes of an MCS in one launch
@@ -302,6 +303,11 @@ bool set_cluster_shape(vegas_ctx *c, int cs, int threads, int split = 0, int gro
 // The step's last class-1 pass renormalises the spins (per-class sweep of a sample that
 // allows it; option renorm_fold).
 bool fold_active(const vegas_ctx *c) { return c->fold_ok && c->variant == 0; }
+
+// The cooperative sweep's grid: bps blocks per SM, within coop_grid_max. Every grid barrier
+// takes one arrival per block, so more blocks than the sample needs cost time: on the 64^3
+// lattice 2 blocks per SM ran 12.5 G attempts/s, 1 ran 12.1 and 3 ran 10.6.
+void set_coop_shape(vegas_ctx *c, int bps) { c->coop_grid = std::max(1, std::min(c->coop_grid_max, c->sm_count * bps)); }
 
 // Launch one MCS: every colour class of every sample, then the reduction. last: the step's
 // last MCS, whose class-1 pass then renormalises every spin when fold_active.
@@ -1184,18 +1190,20 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
     }
     // ---- cooperative sweep: one sample, every block on every class
     if (!p64 && n_samples == 1 && !c->passes.empty() && !c->any_adaptive && !o.type_stats) {
-        c->coop_grid = c->sm_count * coop_blocks_per_sm(any_policy);
-        if (o.max_blocks > 0) c->coop_grid = std::min(c->coop_grid, o.max_blocks);
+        c->coop_grid_max = c->sm_count * coop_blocks_per_sm(any_policy, c->passes[0].args.deg);
+        if (o.max_blocks > 0) c->coop_grid_max = std::min(c->coop_grid_max, o.max_blocks);
         {  // no more blocks than one thread per site and replica of the largest class: a small
            // sample's grid barriers then wait on the blocks that have work only
             const SampleInfo &si = c->samples[0];
             int64_t widest = 0;
             for (int32_t q = 0; q < si.n_colours; ++q)
                 widest = std::max<int64_t>(widest, (int64_t)(si.cstart[(size_t)q + 1] - si.cstart[(size_t)q]) * R);
-            c->coop_grid = (int)std::max<int64_t>(1, std::min<int64_t>(c->coop_grid, (widest + kCoopThreads - 1) / kCoopThreads));
+            c->coop_grid_max =
+                (int)std::max<int64_t>(1, std::min<int64_t>(c->coop_grid_max, (widest + kCoopThreads - 1) / kCoopThreads));
         }
+        set_coop_shape(c, 2);
         DALLOC(c->d_bar, sizeof(GridBarrier));
-        DALLOC(c->d_coop_partial, sizeof(double) * 4 * 2 * (size_t)c->coop_grid * R);  // two MCS in turn
+        DALLOC(c->d_coop_partial, sizeof(double) * 4 * 2 * (size_t)c->coop_grid_max * R);  // two MCS in turn
         CoopArgs &ca = c->coop;
         std::memset(&ca, 0, sizeof ca);
         ca.pass = c->passes[0].args;
@@ -1639,7 +1647,9 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                         cand.push_back({1, 512, 0, 0, 256, 1});
                     }
                 }
-                if (c->coop_eligible) cand.push_back({2, 0, 0, 0, 0});
+                if (c->coop_eligible)  // blocks per SM
+                    for (int bps = 1; bps <= 3 && c->sm_count * (bps - 1) < c->coop_grid_max; ++bps)
+                        cand.push_back({2, bps, 0, 0, 0});
                 if (c->cluster_eligible) {
                     const int cs0 = c->cluster_cs, big = c->max_instance_sites;
                     cand.push_back({3, cs0, 256, 0, 0});
@@ -1673,6 +1683,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                         const int v = vc.v;
                         // grouped instances: group_threads threads for up to 16 sites each per thread
                         if (v == 1 && !set_resident_shape(c, vc.a, vc.group, vc.group * 16, vc.sm != 0)) continue;
+                        if (v == 2) set_coop_shape(c, vc.a);
                         if (v == 3 && !set_cluster_shape(c, vc.a, vc.b, vc.split, vc.group, vc.group * 16, vc.sm != 0))
                             continue;
                         cudaEvent_t x0, x1;
@@ -1702,6 +1713,7 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                     // the shape of the sweep kept goes last: the two persistent sweeps share the
                     // grouping of small instances
                     if (c->cluster_eligible && best_v != 3) set_cluster_shape(c, cs_rule, ct_rule, 0, 0, 0);
+                    set_coop_shape(c, best_v == 2 ? best_c.a : 2);
                     if (best_v == 1)
                         set_resident_shape(c, best_c.a, best_c.group, best_c.group * 16, best_c.sm != 0);
                     else

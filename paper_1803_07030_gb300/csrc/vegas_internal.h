@@ -294,11 +294,14 @@ struct ResidentArgs {
 };
 
 // Grid barrier of the cooperative sweep (zeroed before every launch).
+// Grid barrier: the arrival counter and the generation word the waiting blocks poll sit on
+// separate 128-byte lines, so the polling loads do not queue with the arrivals' atomics.
 struct GridBarrier {
     uint32_t count;  // blocks arrived at the current barrier
+    uint32_t pad0_[31];
     uint32_t gen;    // completed barriers
     uint32_t abort;  // set when a wait timed out: every block leaves
-    uint32_t pad_;
+    uint32_t pad1_[30];
 };
 
 // Cooperative sweep of one sample (R replicas): all blocks sweep each colour class together
@@ -384,7 +387,7 @@ void launch_snapshot(const void *spins, void *snap, int64_t n16, const RunState 
 
 // Cooperative launch (all blocks co-resident); returns the CUDA error of the launch.
 int launch_coop(const CoopArgs &a, int grid, void *stream);
-int coop_blocks_per_sm(bool pol);
+int coop_blocks_per_sm(bool pol, int deg);  // deg: the sample's uniform row length, or 0
 // Blocks of the resident sweep per SM (smem_bytes > 0: the shared-memory form, whose limit
 // is raised here; 0 when it does not fit).
 int resident_blocks_per_sm(int threads, bool pol, size_t smem_bytes = 0);

@@ -306,18 +306,34 @@ constexpr int kDirectRow = 12;  // rows up to this length gather all neighbours 
 // POL = 1: the sample has an update-policy table (pol[g], the instance's width sigma).
 // CG = 1: neighbour spins are read with ld.global.cg (L2 only) because other blocks of the same
 // launch write them (cooperative and cluster sweeps); otherwise through the read-only path.
-template <int PM, int LM, int POL, int CG = 0>
+// UD > 0: every row has UD links and site g's start at ud_e0 (a sample of uniform degree), so
+// row_ptr is not read and all UD neighbour rows are in flight together.
+template <int PM, int LM, int POL, int CG = 0, int UD = 0>
 __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const int64_t *row_ptr, int g, int r, int R,
                                                int lower_end, uint32_t orig, const Site32 &p, float beta, float B,
                                                uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1, Acc32 &acc,
-                                               bool &nan_seen, const PolicySite32 *pol, float sigma, float4 &Sq) {
+                                               bool &nan_seen, const PolicySite32 *pol, float sigma, float4 &Sq,
+                                               int64_t ud_e0 = 0) {
     const int64_t si = (int64_t)g * R + r;
     const float4 Si = S[si];
     float2 hxy = make_float2(0.f, 0.f), lxy = make_float2(0.f, 0.f);
     float hz = 0.f, lz = 0.f;
-    const int64_t e0 = __ldg(row_ptr + g), e1 = __ldg(row_ptr + g + 1);
-    const int deg = (int)(e1 - e0);
-    if (deg <= kDirectRow) {
+    const int64_t e0 = UD > 0 ? ud_e0 : __ldg(row_ptr + g);
+    const int deg = UD > 0 ? UD : (int)(__ldg(row_ptr + g + 1) - e0);
+    if (UD > 0) {
+        int2 ed[UD > 0 ? UD : 1];
+        float4 Sj[UD > 0 ? UD : 1];
+#pragma unroll
+        for (int k = 0; k < UD; ++k) ed[k] = __ldg(E + e0 + k);
+#pragma unroll
+        for (int k = 0; k < UD; ++k) {
+            const float4 *q = S + (int64_t)ed[k].x * R + r;
+            Sj[k] = CG ? __ldcg(q) : __ldg(q);
+        }
+#pragma unroll
+        for (int k = 0; k < UD; ++k)
+            link32(Sj[k], __int_as_float(ed[k].y), LM == 2 && ed[k].x < lower_end, hxy, hz, lxy, lz);
+    } else if (deg <= kDirectRow) {
         // all links first, then the neighbour rows with every load in flight together; the
         // field still sums in row order
         int2 ed[kDirectRow];
@@ -340,7 +356,7 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
                     link32(Sj[k], __int_as_float(ed[k0 + k].y), LM == 2 && ed[k0 + k].x < lower_end, hxy, hz, lxy, lz);
         }
     } else {
-        for (int64_t e = e0; e < e1; ++e) {
+        for (int64_t e = e0; e < e0 + deg; ++e) {
             const int2 ed = __ldg(E + e);
             const float4 *q = S + (int64_t)ed.x * R + r;
             link32(CG ? __ldcg(q) : __ldg(q), __int_as_float(ed.y), LM == 2 && ed.x < lower_end, hxy, hz, lxy, lz);
@@ -1028,7 +1044,8 @@ __device__ bool grid_barrier(GridBarrier *b, uint32_t nblocks, int64_t timeout_n
     return s_ok != 0;
 }
 
-template <int NT, int POL>
+// UD > 0: a sample whose every row has UD links (direct_attempt's uniform-degree path).
+template <int NT, int POL, int UD = 0>
 __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
     const PassArgs &a = ca.pass;
     RunState *rs = a.run;
@@ -1094,8 +1111,9 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
                 if (a.params_mode == 2) p = site_params32(a, 2, g);
                 // one code path for every parameter mode (zero constants add signed zeros)
                 float4 Sq;
-                const bool ok = direct_attempt<2, 2, POL, 1>(S, E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t, inst, k0,
-                                                          k1, acc, nan_seen, a.pol32, 0.f, Sq);
+                const bool ok = direct_attempt<2, 2, POL, 1, UD>(S, E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t, inst,
+                                                              k0, k1, acc, nan_seen, a.pol32, 0.f, Sq,
+                                                              a.edge_base + (int64_t)(g - a.site_off) * UD);
                 if (log_accepts)
                     a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
             }
@@ -1402,6 +1420,14 @@ void launch_snapshot(const void *spins, void *snap, int64_t n16, const RunState 
 }
 
 
+using CoopFn = void (*)(CoopArgs);
+
+// rows of six links (the simple cubic lattices) take the uniform-degree form
+CoopFn select_coop(bool pol, int deg) {
+    if (deg == 6) return pol ? coop32_kernel<kCoopThreads, 1, 6> : coop32_kernel<kCoopThreads, 0, 6>;
+    return pol ? coop32_kernel<kCoopThreads, 1> : coop32_kernel<kCoopThreads, 0>;
+}
+
 int launch_coop(const CoopArgs &a, int grid, void *stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -1413,16 +1439,12 @@ int launch_coop(const CoopArgs &a, int grid, void *stream) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (a.pass.pol32) return (int)cudaLaunchKernelEx(&cfg, coop32_kernel<kCoopThreads, 1>, a);
-    return (int)cudaLaunchKernelEx(&cfg, coop32_kernel<kCoopThreads, 0>, a);
+    return (int)cudaLaunchKernelEx(&cfg, select_coop(a.pass.pol32 != nullptr, a.pass.deg), a);
 }
 
-int coop_blocks_per_sm(bool pol) {
+int coop_blocks_per_sm(bool pol, int deg) {
     int nb = 0;
-    if (pol)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop32_kernel<kCoopThreads, 1>, kCoopThreads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop32_kernel<kCoopThreads, 0>, kCoopThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_coop(pol, deg), kCoopThreads, 0);
     return nb > 0 ? nb : 1;
 }
 
