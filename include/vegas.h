@@ -133,8 +133,8 @@ typedef struct {
                                (vegas_stats reports the choice); 0 one launch per colour
                                class, 1 resident: one persistent launch per step, a block per
                                instance (FP32), 2 cooperative: one launch per step, all blocks
-                               sweep one sample class by class (FP32, one sample, no adaptive
-                               policy), 3 cluster: one persistent launch per step, a thread-
+                               sweep one sample class by class (FP32 or FP64, one sample, no
+                               adaptive policy), 3 cluster: one persistent launch per step, a thread-
                                block cluster of 2 .. 16 blocks per instance, the blocks meeting at
                                the hardware cluster barrier between colour classes (FP32),
                                4 wavefront: one launch per MCS runs both colour classes,
@@ -256,7 +256,7 @@ typedef struct {
 #define VEGAS_KERNEL_PASS32_R32 0x8u           /* FP32 colour pass, 32 replicas per site */
 #define VEGAS_KERNEL_PASS32_R32_POLICY 0x10u   /* the same with an update-policy table */
 #define VEGAS_KERNEL_RESIDENT32 0x20u          /* resident (persistent) sweep */
-#define VEGAS_KERNEL_COOP32 0x40u              /* cooperative sweep */
+#define VEGAS_KERNEL_COOP32 0x40u              /* cooperative sweep, FP32 */
 #define VEGAS_KERNEL_CLUSTER32 0x80u           /* cluster sweep */
 #define VEGAS_KERNEL_WAVE32 0x100u             /* wavefront sweep */
 #define VEGAS_KERNEL_PASS32_R32_ONE_POLICY 0x200u /* 32 replicas per site, compiled for the one
@@ -266,6 +266,7 @@ typedef struct {
                                                   shared memory */
 #define VEGAS_KERNEL_PASS32_R32_RENORM 0x1000u /* 32 replicas per site, the step's last class-1
                                                   pass renormalising every spin (renorm_fold) */
+#define VEGAS_KERNEL_COOP64 0x2000u            /* cooperative sweep, FP64 */
 
 /* Fills *opt with the defaults listed above. */
 void vegas_default_options(vegas_options *opt);

@@ -615,8 +615,8 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         return fail(nullptr, VEGAS_EINVAL, "type_stats and snapshots must be 0 or 1");
     if (o.variant == 2 && o.type_stats)
         return fail(nullptr, VEGAS_EINVAL, "the cooperative sweep (variant 2) does not record per-type statistics");
-    if (o.variant == 2 && (o.precision != 32 || n_samples != 1))
-        return fail(nullptr, VEGAS_EINVAL, "the cooperative sweep (variant 2) is FP32 with one sample");
+    if (o.variant == 2 && n_samples != 1)
+        return fail(nullptr, VEGAS_EINVAL, "the cooperative sweep (variant 2) runs one sample");
     if (o.pipeline_depth < 0 || o.pipeline_depth > 3) return fail(nullptr, VEGAS_EINVAL, "pipeline_depth must be 0..3");
     if (o.variant == 1 && o.precision != 32)
         return fail(nullptr, VEGAS_EINVAL, "the resident sweep (variant 1) is FP32 only");
@@ -1189,17 +1189,30 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         }
     }
     // ---- cooperative sweep: one sample, every block on every class
-    if (!p64 && n_samples == 1 && !c->passes.empty() && !c->any_adaptive && !o.type_stats) {
-        c->coop_grid_max = c->sm_count * coop_blocks_per_sm(any_policy, c->passes[0].args.deg);
+    if (n_samples == 1 && !c->passes.empty() && !c->any_adaptive && !o.type_stats) {
+        const int nt = kCoopThreads;
+        c->coop_grid_max = c->sm_count * coop_blocks_per_sm(any_policy, c->passes[0].args.deg, p64);
         if (o.max_blocks > 0) c->coop_grid_max = std::min(c->coop_grid_max, o.max_blocks);
+        const SampleInfo &si = c->samples[0];
         {  // no more blocks than one thread per site and replica of the largest class: a small
            // sample's grid barriers then wait on the blocks that have work only
-            const SampleInfo &si = c->samples[0];
             int64_t widest = 0;
             for (int32_t q = 0; q < si.n_colours; ++q)
                 widest = std::max<int64_t>(widest, (int64_t)(si.cstart[(size_t)q + 1] - si.cstart[(size_t)q]) * R);
+            // FP64: down to one site and replica group per block (a block's FP64 work is what bounds it)
+            const int64_t per_block = p64 ? R : nt;
             c->coop_grid_max =
-                (int)std::max<int64_t>(1, std::min<int64_t>(c->coop_grid_max, (widest + kCoopThreads - 1) / kCoopThreads));
+                (int)std::max<int64_t>(1, std::min<int64_t>(c->coop_grid_max, (widest + per_block - 1) / per_block));
+        }
+        if (p64) {  // the class starts (FP32 contexts built them with the resident sweep's tables)
+            std::vector<int32_t> h_cs;
+            for (int32_t q = 0; q <= si.n_colours; ++q) h_cs.push_back(si.site_off + si.cstart[(size_t)q]);
+            DALLOC(c->d_cstart, sizeof(int32_t) * h_cs.size());
+            H2D(c->d_cstart, h_cs.data(), sizeof(int32_t) * h_cs.size());
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess) {  // h_cs goes out of scope
+                c->err = "upload of the class starts failed";
+                return bail(VEGAS_ECUDA);
+            }
         }
         set_coop_shape(c, 2);
         DALLOC(c->d_bar, sizeof(GridBarrier));
@@ -1214,6 +1227,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         ca.partial = c->d_coop_partial;
         ca.timeout_ns = o.timeout_ns > 0 ? o.timeout_ns : 2000000000LL;
         ca.skip_block = o.fault_inject == 1 ? 0 : -1;
+        ca.fp64 = p64 ? 1 : 0;
         c->coop_eligible = true;
     }
     // ---- renormalisation folded into the step's last class-1 pass: one sample of two colour
@@ -1374,7 +1388,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         c->tuned = true;
     } else {
         // automatic: timed on the first run; until then, the shape suggests one
-        c->variant = (c->n_inst >= 2 && c->max_instance_sites <= 16384) ? 1 : 0;
+        c->variant = (c->res_eligible && c->n_inst >= 2 && c->max_instance_sites <= 16384) ? 1 : 0;
     }
 
     // ---- initial state
@@ -2104,7 +2118,7 @@ extern "C" vegas_status vegas_stats(const vegas_ctx *c, vegas_stats_t *o) {
         if (c->variant == 1)
             kinds = c->res_smem ? VEGAS_KERNEL_RESIDENT32_SMEM : VEGAS_KERNEL_RESIDENT32;
         else if (c->variant == 2)
-            kinds = VEGAS_KERNEL_COOP32;
+            kinds = c->precision == 64 ? VEGAS_KERNEL_COOP64 : VEGAS_KERNEL_COOP32;
         else if (c->variant == 3)
             kinds = c->cluster_smem ? VEGAS_KERNEL_CLUSTER32_SMEM : VEGAS_KERNEL_CLUSTER32;
         else if (c->variant == 4)

@@ -40,6 +40,7 @@ constexpr int kMaxColours = 64;
 constexpr int kMaxTypes = 64;   // site types tracked by the per-type statistics
 constexpr int kThreads = 256;  // threads per block of the sweep kernels
 constexpr int kCoopThreads = 256;  // threads per block of the cooperative sweep
+constexpr int kCoop64Threads = 32; // the same in FP64: small blocks spread a class over many SMs
 
 // Random-number purposes (fourth Philox counter word; low 16 bits hold a candidate index).
 constexpr uint32_t kPurposeTrial64 = 0x00000u;   // FP64 sphere candidates
@@ -315,6 +316,7 @@ struct CoopArgs {
     double *partial;           // [2][block][R][4]: the partials of two MCS in turn
     int64_t timeout_ns;        // longest wait at one barrier
     int32_t skip_block;        // fault injection: this block never arrives (-1: none)
+    int32_t fp64;              // 1: FP64 spins (coop64_kernel)
 };
 
 // Wavefront sweep of one two-colour sample with R = 32 replicas: both colour classes of an
@@ -387,7 +389,7 @@ void launch_snapshot(const void *spins, void *snap, int64_t n16, const RunState 
 
 // Cooperative launch (all blocks co-resident); returns the CUDA error of the launch.
 int launch_coop(const CoopArgs &a, int grid, void *stream);
-int coop_blocks_per_sm(bool pol, int deg);  // deg: the sample's uniform row length, or 0
+int coop_blocks_per_sm(bool pol, int deg, bool fp64);  // deg: the sample's uniform row length, or 0
 // Blocks of the resident sweep per SM (smem_bytes > 0: the shared-memory form, whose limit
 // is raised here; 0 when it does not fit).
 int resident_blocks_per_sm(int threads, bool pol, size_t smem_bytes = 0);

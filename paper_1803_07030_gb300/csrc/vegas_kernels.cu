@@ -186,12 +186,120 @@ __device__ __forceinline__ double adapt_width(double sigma, uint32_t accepted, i
 }
 
 // ------------------------------------------------------------------ FP64 colour pass
+// A spin through L2 only (ld.global.cg): other blocks of the same launch write spins.
+__device__ __forceinline__ double4_32a ldcg_spin64(const double4_32a *p) {
+    const double2 lo = __ldcg((const double2 *)p), hi = __ldcg((const double2 *)p + 1);
+    return make_double4_32a(lo.x, lo.y, hi.x, hi.y);
+}
+
+// One FP64 attempt at site g, replica r (Eq. 1-4, the oracle's order of operations) at MCS t
+// of step `step`, adding the site's share of E and M to acc4 and the decision to nacc. Links to
+// sites below lower_end count as lower colours when lower_mode is 2 (1: every link). CG = 1
+// reads the neighbour spins through L2 only (the cooperative sweep, whose other blocks write
+// them within the launch).
+template <int CG = 0>
+__device__ __forceinline__ void site64(const PassArgs &a, int g, int r, int R, uint32_t t, uint32_t step,
+                                       int lower_mode, int lower_end, double4_32a *S, const Edge64 *E, uint32_t k0,
+                                       uint32_t k1, double acc4[4], uint32_t &nacc) {
+    const RunState *rs = a.run;
+    const double *sched = rs->sched;
+    const uint32_t inst = (uint32_t)(a.inst0 + r);
+    const double *sc = sched + ((int64_t)step * a.n_inst + a.inst_local0 + r) * 2;
+    const double beta = sc[0], B = sc[1];
+    const uint32_t orig = (uint32_t)a.orig[g];
+    double nx, ny, nz, sn, ex, ey, ez, k, kc;
+    if (a.params_mode == 2) {
+        const double4_32a p0 = ((const double4_32a *)a.p0)[g], p1 = ((const double4_32a *)a.p1)[g];
+        nx = p0.x; ny = p0.y; nz = p0.z; sn = p0.w;
+        ex = p1.x; ey = p1.y; ez = p1.z; k = p1.w;
+        kc = ((const double *)a.pk)[g];
+    } else {
+        nx = a.u64.nx; ny = a.u64.ny; nz = a.u64.nz; sn = a.u64.s;
+        ex = a.u64.ex; ey = a.u64.ey; ez = a.u64.ez; k = a.u64.k; kc = a.u64.kc;
+    }
+    const int64_t si = (int64_t)g * R + r;
+    const double4_32a Si = S[si];
+    // local field in the caller's row order, plus the links to lower colours
+    double hx = 0.0, hy = 0.0, hz = 0.0, lx = 0.0, ly = 0.0, lz = 0.0;
+    for (int64_t e = a.row_ptr[g]; e < a.row_ptr[g + 1]; ++e) {
+        const Edge64 ed = E[e];
+        const double4_32a Sj = CG ? ldcg_spin64(S + (int64_t)ed.col * R + r) : S[(int64_t)ed.col * R + r];
+        hx = da(hx, dm(ed.J, Sj.x));
+        hy = da(hy, dm(ed.J, Sj.y));
+        hz = da(hz, dm(ed.J, Sj.z));
+        if (lower_mode == 1 || (lower_mode == 2 && ed.col < lower_end)) {
+            lx = da(lx, dm(ed.J, Sj.x));
+            ly = da(ly, dm(ed.J, Sj.y));
+            lz = da(lz, dm(ed.J, Sj.z));
+        }
+    }
+    hx = da(hx, dm(B, nx));
+    hy = da(hy, dm(B, ny));
+    hz = da(hz, dm(B, nz));
+    // trial: uniform on the sphere of radius s_i, or the site's update policy
+    double px, py, pz;
+    if (a.pol && a.pol[g].code == kPolQIsing) {  // another of the 2 s + 1 values along z
+        const int n2 = (int)dm(2.0, sn);
+        const int idx = (int)da(da(Si.z, sn), 0.5);
+        const uint4 w = philox10(make_uint4(orig, t, inst, kPurposeTrial64), k0, k1);
+        int k = (int)dm(u53(w.x, w.y), (double)n2);
+        if (k >= n2) k = n2 - 1;
+        if (k >= idx) k += 1;
+        px = 0.0;
+        py = 0.0;
+        pz = ds((double)k, sn);
+    } else {
+        const double3 u = a.pol ? policy_trial64(a.pol[g], rs->sigma ? rs->sigma[a.inst_local0 + r] : 0.0, Si, sn,
+                                                 orig, t, inst, k0, k1, a.err)
+                                : sphere64(orig, t, inst, kPurposeTrial64, k0, k1, a.err);
+        px = dm(sn, u.x);
+        py = dm(sn, u.y);
+        pz = dm(sn, u.z);
+    }
+    // energy change (Eq. 1-3) in a fixed order
+    const double dx = ds(px, Si.x), dy = ds(py, Si.y), dz = ds(pz, Si.z);
+    const double dEex = -da(da(dm(dx, hx), dm(dy, hy)), dm(dz, hz));
+    double dE = dEex;
+    if (a.params_mode != 0) {
+        const double pn = da(da(dm(px, ex), dm(py, ey)), dm(pz, ez));
+        const double po = da(da(dm(Si.x, ex), dm(Si.y, ey)), dm(Si.z, ez));
+        const double dEan = -dm(k, ds(dm(pn, pn), dm(po, po)));
+        const double dEcub = -dm(kc, ds(cub64(px, py, pz), cub64(Si.x, Si.y, Si.z)));
+        dE = da(da(dEex, dEan), dEcub);
+    }
+    // Metropolis acceptance (Eq. 4), k_B = 1
+    bool acc;
+    if (dE <= 0.0) {
+        acc = true;
+    } else {
+        const uint4 wa = philox10(make_uint4(orig, t, inst, kPurposeAccept64), k0, k1);
+        acc = u53(wa.x, wa.y) < exp(-dm(beta, dE));
+    }
+    if (isnan(dE)) {
+        atomicOr(a.err, kErrNaN);
+        acc = false;
+    }
+    if (acc) S[si] = make_double4_32a(px, py, pz, 0.0);
+    if (a.alog && t < a.alog_mcs)
+        a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = acc ? 1 : 0;
+    // this site's share of E and M after the MCS
+    const double qx = acc ? px : Si.x, qy = acc ? py : Si.y, qz = acc ? pz : Si.z;
+    double e_i = -(qx * lx + qy * ly + qz * lz) - B * (qx * nx + qy * ny + qz * nz);
+    if (a.params_mode != 0) {
+        const double pe = qx * ex + qy * ey + qz * ez;
+        e_i -= k * pe * pe + kc * cub64(qx, qy, qz);
+    }
+    acc4[0] += e_i;
+    acc4[1] += qx;
+    acc4[2] += qy;
+    acc4[3] += qz;
+    nacc += acc ? 1u : 0u;
+}
 
 __global__ void __launch_bounds__(kThreads) pass64_kernel(const PassArgs a) {
     const RunState *rs = a.run;
     const uint32_t t = rs->t;
     const uint32_t step = rs->rec / rs->mcs;
-    const double *sched = rs->sched;
     const int R = 1 << a.log2R;
     const int64_t n_work = (int64_t)(a.g_end - a.g_begin) << a.log2R;
     double4_32a *S = (double4_32a *)a.spins;
@@ -200,101 +308,9 @@ __global__ void __launch_bounds__(kThreads) pass64_kernel(const PassArgs a) {
     double acc4[4] = {0.0, 0.0, 0.0, 0.0};
     uint32_t nacc = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += stride) {
-        const int g = a.g_begin + (int)(w >> a.log2R);
-        const int r = (int)(w & (R - 1));
-        const uint32_t inst = (uint32_t)(a.inst0 + r);
-        const double *sc = sched + ((int64_t)step * a.n_inst + a.inst_local0 + r) * 2;
-        const double beta = sc[0], B = sc[1];
-        const uint32_t orig = (uint32_t)a.orig[g];
-        double nx, ny, nz, sn, ex, ey, ez, k, kc;
-        if (a.params_mode == 2) {
-            const double4_32a p0 = ((const double4_32a *)a.p0)[g], p1 = ((const double4_32a *)a.p1)[g];
-            nx = p0.x; ny = p0.y; nz = p0.z; sn = p0.w;
-            ex = p1.x; ey = p1.y; ez = p1.z; k = p1.w;
-            kc = ((const double *)a.pk)[g];
-        } else {
-            nx = a.u64.nx; ny = a.u64.ny; nz = a.u64.nz; sn = a.u64.s;
-            ex = a.u64.ex; ey = a.u64.ey; ez = a.u64.ez; k = a.u64.k; kc = a.u64.kc;
-        }
-        const int64_t si = (int64_t)g * R + r;
-        const double4_32a Si = S[si];
-        // local field in the caller's row order, plus the links to lower colours
-        double hx = 0.0, hy = 0.0, hz = 0.0, lx = 0.0, ly = 0.0, lz = 0.0;
-        for (int64_t e = a.row_ptr[g]; e < a.row_ptr[g + 1]; ++e) {
-            const Edge64 ed = E[e];
-            const double4_32a Sj = S[(int64_t)ed.col * R + r];
-            hx = da(hx, dm(ed.J, Sj.x));
-            hy = da(hy, dm(ed.J, Sj.y));
-            hz = da(hz, dm(ed.J, Sj.z));
-            if (a.lower_mode == 1 || (a.lower_mode == 2 && ed.col < a.lower_end)) {
-                lx = da(lx, dm(ed.J, Sj.x));
-                ly = da(ly, dm(ed.J, Sj.y));
-                lz = da(lz, dm(ed.J, Sj.z));
-            }
-        }
-        hx = da(hx, dm(B, nx));
-        hy = da(hy, dm(B, ny));
-        hz = da(hz, dm(B, nz));
-        // trial: uniform on the sphere of radius s_i, or the site's update policy
-        double px, py, pz;
-        if (a.pol && a.pol[g].code == kPolQIsing) {  // another of the 2 s + 1 values along z
-            const int n2 = (int)dm(2.0, sn);
-            const int idx = (int)da(da(Si.z, sn), 0.5);
-            const uint4 w = philox10(make_uint4(orig, t, inst, kPurposeTrial64), k0, k1);
-            int k = (int)dm(u53(w.x, w.y), (double)n2);
-            if (k >= n2) k = n2 - 1;
-            if (k >= idx) k += 1;
-            px = 0.0;
-            py = 0.0;
-            pz = ds((double)k, sn);
-        } else {
-            const double3 u = a.pol ? policy_trial64(a.pol[g], rs->sigma ? rs->sigma[a.inst_local0 + r] : 0.0, Si, sn,
-                                                     orig, t, inst, k0, k1, a.err)
-                                    : sphere64(orig, t, inst, kPurposeTrial64, k0, k1, a.err);
-            px = dm(sn, u.x);
-            py = dm(sn, u.y);
-            pz = dm(sn, u.z);
-        }
-        // energy change (Eq. 1-3) in a fixed order
-        const double dx = ds(px, Si.x), dy = ds(py, Si.y), dz = ds(pz, Si.z);
-        const double dEex = -da(da(dm(dx, hx), dm(dy, hy)), dm(dz, hz));
-        double dE = dEex;
-        if (a.params_mode != 0) {
-            const double pn = da(da(dm(px, ex), dm(py, ey)), dm(pz, ez));
-            const double po = da(da(dm(Si.x, ex), dm(Si.y, ey)), dm(Si.z, ez));
-            const double dEan = -dm(k, ds(dm(pn, pn), dm(po, po)));
-            const double dEcub = -dm(kc, ds(cub64(px, py, pz), cub64(Si.x, Si.y, Si.z)));
-            dE = da(da(dEex, dEan), dEcub);
-        }
-        // Metropolis acceptance (Eq. 4), k_B = 1
-        bool acc;
-        if (dE <= 0.0) {
-            acc = true;
-        } else {
-            const uint4 wa = philox10(make_uint4(orig, t, inst, kPurposeAccept64), k0, k1);
-            acc = u53(wa.x, wa.y) < exp(-dm(beta, dE));
-        }
-        if (isnan(dE)) {
-            atomicOr(a.err, kErrNaN);
-            acc = false;
-        }
-        if (acc) S[si] = make_double4_32a(px, py, pz, 0.0);
-        if (a.alog && t < a.alog_mcs)
-            a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = acc ? 1 : 0;
-        // this site's share of E and M after the MCS
-        const double qx = acc ? px : Si.x, qy = acc ? py : Si.y, qz = acc ? pz : Si.z;
-        double e_i = -(qx * lx + qy * ly + qz * lz) - B * (qx * nx + qy * ny + qz * nz);
-        if (a.params_mode != 0) {
-            const double pe = qx * ex + qy * ey + qz * ez;
-            e_i -= k * pe * pe + kc * cub64(qx, qy, qz);
-        }
-        acc4[0] += e_i;
-        acc4[1] += qx;
-        acc4[2] += qy;
-        acc4[3] += qz;
-        nacc += acc ? 1u : 0u;
-    }
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += stride)
+        site64(a, a.g_begin + (int)(w >> a.log2R), (int)(w & (R - 1)), R, t, step, a.lower_mode, a.lower_end, S, E, k0,
+               k1, acc4, nacc);
     block_partials(acc4, nacc, R, a.partial + (int64_t)blockIdx.x * R * 4, acc_counters(rs, a.inst_local0));
 }
 
@@ -1136,6 +1152,81 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
     if (nan_seen) atomicOr(a.err, kErrNaN);
 }
 
+// The cooperative sweep in FP64 (the attempt of pass64_kernel, so the oracle's spins bit for
+// bit): blocks of NT threads, every block on every class, the same bounded grid barrier and
+// deferred record as coop32_kernel. GB300 runs about two FP64 operations per SM and clock, so
+// the host spreads a class over many SMs with small blocks (about one thread per site of the
+// widest class) instead of filling a few.
+template <int NT>
+__global__ void __launch_bounds__(NT) coop64_kernel(const CoopArgs ca) {
+    const PassArgs &a = ca.pass;
+    RunState *rs = a.run;
+    const uint32_t t0 = rs->t, rec0 = rs->rec;
+    const uint32_t step = rec0 / rs->mcs;
+    const int R = 1 << a.log2R;
+    double4_32a *S = (double4_32a *)a.spins;
+    const Edge64 *E = (const Edge64 *)a.edges;
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    // lane l serves replica l mod R (as block_partials needs); site v of a class goes to block
+    // v mod grid, so a class's sites spread over every block (over as many SMs' FP64 units as
+    // the grid has blocks) before any block takes two
+    const int r = (int)threadIdx.x & (R - 1);
+    const int64_t v0 = (int64_t)(threadIdx.x >> a.log2R) * gridDim.x + blockIdx.x;
+    const int64_t vstride = (int64_t)gridDim.x * (NT >> a.log2R);
+    const bool skip = (int)blockIdx.x == ca.skip_block;
+    // block 0 adds the block partials of MCS mm (buffer mm & 1) into the history: one warp per
+    // replica, lanes striding over the blocks, a fixed tree
+    auto record = [&](int mm) {
+        if (blockIdx.x != 0) return;
+        const double *part = ca.partial + (int64_t)(mm & 1) * gridDim.x * R * 4;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int rr = warp; rr < R; rr += NT / 32) {
+            double v[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int b = lane; b < (int)gridDim.x; b += 32) {
+                const double *p = part + ((int64_t)b * R + rr) * 4;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] += __ldcg(p + q);
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] += __shfl_xor_sync(0xFFFFFFFFu, v[q], off);
+            }
+            if (lane == 0) {
+                double *h = rs->hist + ((int64_t)(rec0 + mm) * a.n_inst + a.inst_local0 + rr) * 4;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) h[q] = v[q];
+                if (rs->acc) {
+                    const uint32_t n = atomicExch(rs->acc + a.inst_local0 + rr, 0u);
+                    if (rs->acc_hist) rs->acc_hist[(int64_t)(rec0 + mm) * a.n_inst + a.inst_local0 + rr] = n;
+                }
+            }
+        }
+    };
+    const bool deferred = ca.n_colours >= 2;
+    for (int m = 0; m < ca.mcs; ++m) {
+        const uint32_t t = t0 + (uint32_t)m;
+        double acc4[4] = {0.0, 0.0, 0.0, 0.0};
+        uint32_t nacc = 0;
+        for (int c = 0; c < ca.n_colours; ++c) {
+            const int cb = ca.cstart[c], ce = ca.cstart[c + 1];
+            for (int64_t v = v0; v < ce - cb; v += vstride)
+                site64<1>(a, cb + (int)v, r, R, t, step, 2, cb, S, E, k0, k1, acc4, nacc);
+            if (!grid_barrier(ca.bar, gridDim.x, ca.timeout_ns, a.err, skip)) return;
+            if (deferred && c == 0 && m > 0) record(m - 1);
+        }
+        block_partials(acc4, nacc, R, ca.partial + ((int64_t)(m & 1) * gridDim.x + blockIdx.x) * R * 4,
+                       acc_counters(rs, a.inst_local0));
+        if (!deferred) {
+            if (!grid_barrier(ca.bar, gridDim.x, ca.timeout_ns, a.err, skip)) return;
+            record(m);
+        }
+    }
+    if (deferred && ca.mcs > 0) {
+        if (!grid_barrier(ca.bar, gridDim.x, ca.timeout_ns, a.err, skip)) return;
+        record(ca.mcs - 1);
+    }
+}
+
 // ------------------------------------------------------------------ per-MCS reduction
 // One block per instance sums its sample's block partials over every colour class in a fixed
 // order (thread k takes slots k, k + 256, ... in turn, then a butterfly inside each warp and
@@ -1439,12 +1530,19 @@ int launch_coop(const CoopArgs &a, int grid, void *stream) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (a.fp64) {
+        cfg.blockDim = dim3(kCoop64Threads);
+        return (int)cudaLaunchKernelEx(&cfg, coop64_kernel<kCoop64Threads>, a);
+    }
     return (int)cudaLaunchKernelEx(&cfg, select_coop(a.pass.pol32 != nullptr, a.pass.deg), a);
 }
 
-int coop_blocks_per_sm(bool pol, int deg) {
+int coop_blocks_per_sm(bool pol, int deg, bool fp64) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_coop(pol, deg), kCoopThreads, 0);
+    if (fp64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop64_kernel<kCoop64Threads>, kCoop64Threads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_coop(pol, deg), kCoopThreads, 0);
     return nb > 0 ? nb : 1;
 }
 

@@ -46,7 +46,7 @@ class vegas_sample(C.Structure):
 KERNEL_BITS = {"pass64": 0x1, "pass32_direct": 0x2, "pass32_staged": 0x4, "pass32_r32": 0x8,
                "pass32_r32_policy": 0x10, "resident32": 0x20, "coop32": 0x40, "cluster32": 0x80, "wave32": 0x100,
                "pass32_r32_one_policy": 0x200, "resident32_smem": 0x400, "cluster32_smem": 0x800,
-               "pass32_r32_renorm": 0x1000}
+               "pass32_r32_renorm": 0x1000, "coop64": 0x2000}
 
 
 def sweep_kernel_names(bits: int) -> list:

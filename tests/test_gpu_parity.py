@@ -327,12 +327,41 @@ def test_cooperative_sweep_equals_per_class_sweep(make, R):
         assert np.array_equal(a.accept_history(), b.accept_history())  # recorded one MCS late, in order
 
 
-def test_cooperative_barrier_timeout_is_reported_not_hung():
+@pytest.mark.parametrize("case", ["sc8", "core_shell_policies"])
+def test_fp64_cooperative_sweep_bitwise(case):
+    """The FP64 cooperative sweep (one launch per step, all blocks on every colour class with
+    grid barriers between them) against the oracle: spins, accept log and accepted counts bit
+    for bit, history within 1e-12; on the 8^3 ferromagnet and on a core/shell particle of
+    uneven rows with a table of (non-adaptive) update policies, two replicas."""
+    if case == "sc8":
+        s, R = sc_periodic(8), 1
+    else:
+        s = core_shell_particle(seed=2, radius=4.0, core_radius=2.5).with_policy(
+            [oracle.HINZKE_NOWAK, oracle.GAUSSIAN], [0.5, 0.3])
+        R = 2
+    T = np.stack([[3.0 - 0.5 * r, 1.0, 0.3] for r in range(R)])
+    B = np.stack([[0.0, 0.2 * r, -0.1] for r in range(R)])
+    mcs = 8
+    with ctx([s], precision=64, replicas=R, seed=21, variant=2, accept_log_mcs=3 * mcs) as c:
+        c.run(T, B, mcs)
+        assert vb.sweep_kernel_names(c.stats()["sweep_kernels"]) == ["coop64"]
+        ref = oracle.run(s, T, B, mcs, seed=21, log_mcs=3 * mcs, n_threads=R)
+        assert ref["err"] == 0
+        alog = c.accept_log().reshape(3 * mcs, R, -1)
+        for r in range(R):
+            assert first_divergence(c.spins(r), ref["spins"][r]) is None, r
+            assert np.array_equal(alog[:, r], ref["accept_log"][r]), r
+            assert np.array_equal(c.accept_history()[r], ref["accepted"][r]), r
+            assert_history_close(c.history()[r], ref["history"][r], s.n_sites)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_cooperative_barrier_timeout_is_reported_not_hung(precision):
     """One block leaves before its first grid barrier (host-requested fault injection): the
     other blocks give up after timeout_ns, the run fails with ETIMEOUT, and the context
     refuses further work. No trap, no hang."""
     s = sc_periodic(12)
-    with ctx([s], seed=1, variant=2, timeout_ns=50_000_000, fault_inject=1) as c:
+    with ctx([s], precision=precision, seed=1, variant=2, timeout_ns=50_000_000, fault_inject=1) as c:
         with pytest.raises(vb.VegasError) as e:
             c.run([[1.0]], [[0.0]], 3)
         assert e.value.status == vb.ETIMEOUT
