@@ -1191,7 +1191,32 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
     // ---- cooperative sweep: one sample, every block on every class
     if (n_samples == 1 && !c->passes.empty() && !c->any_adaptive && !o.type_stats) {
         const int nt = kCoopThreads;
-        c->coop_grid_max = c->sm_count * coop_blocks_per_sm(any_policy, c->passes[0].args.deg, p64);
+        // FP32 rows of at most kEllRow links other than the sc lattices' six: fixed padded rows
+        // (the resident sweep's, or built here), read without row offsets
+        const int deg0 = c->passes[0].args.deg;
+        bool use_ell = false;
+        if (!p64 && deg0 != 6) {
+            int64_t max_deg = 0;
+            for (int64_t g = 0; g < n_sites; ++g)
+                max_deg = std::max(max_deg, h_rowptr[(size_t)g + 1] - h_rowptr[(size_t)g]);
+            if (max_deg <= kEllRow) {
+                if (!c->d_ell) {
+                    std::vector<int2> h_ell((size_t)n_sites * kEllRow, make_int2(-1, 0));
+                    for (int64_t g = 0; g < n_sites; ++g)
+                        for (int64_t e = h_rowptr[(size_t)g]; e < h_rowptr[(size_t)g + 1]; ++e)
+                            h_ell[(size_t)g * kEllRow + (size_t)(e - h_rowptr[(size_t)g])] = h_e32[(size_t)e];
+                    DALLOC(c->d_ell, sizeof(int2) * h_ell.size());
+                    H2D(c->d_ell, h_ell.data(), sizeof(int2) * h_ell.size());
+                    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {  // h_ell goes out of scope
+                        c->err = "upload of the fixed link rows failed";
+                        return bail(VEGAS_ECUDA);
+                    }
+                }
+                use_ell = true;
+            }
+        }
+        const int form = p64 ? 0 : (deg0 == 6 ? 6 : (use_ell ? kEllRow : 0));
+        c->coop_grid_max = c->sm_count * coop_blocks_per_sm(any_policy, form, p64);
         if (o.max_blocks > 0) c->coop_grid_max = std::min(c->coop_grid_max, o.max_blocks);
         const SampleInfo &si = c->samples[0];
         {  // no more blocks than one thread per site and replica of the largest class: a small
@@ -1228,6 +1253,7 @@ static vegas_status create_context(const vegas_sample *samples, int32_t n_sample
         ca.timeout_ns = o.timeout_ns > 0 ? o.timeout_ns : 2000000000LL;
         ca.skip_block = o.fault_inject == 1 ? 0 : -1;
         ca.fp64 = p64 ? 1 : 0;
+        ca.ell = use_ell ? c->d_ell : nullptr;
         c->coop_eligible = true;
     }
     // ---- renormalisation folded into the step's last class-1 pass: one sample of two colour

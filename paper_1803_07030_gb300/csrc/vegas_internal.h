@@ -317,6 +317,7 @@ struct CoopArgs {
     int64_t timeout_ns;        // longest wait at one barrier
     int32_t skip_block;        // fault injection: this block never arrives (-1: none)
     int32_t fp64;              // 1: FP64 spins (coop64_kernel)
+    const int2 *ell;           // FP32 rows of at most kEllRow links as fixed padded rows, or NULL
 };
 
 // Wavefront sweep of one two-colour sample with R = 32 replicas: both colour classes of an
@@ -389,7 +390,7 @@ void launch_snapshot(const void *spins, void *snap, int64_t n16, const RunState 
 
 // Cooperative launch (all blocks co-resident); returns the CUDA error of the launch.
 int launch_coop(const CoopArgs &a, int grid, void *stream);
-int coop_blocks_per_sm(bool pol, int deg, bool fp64);  // deg: the sample's uniform row length, or 0
+int coop_blocks_per_sm(bool pol, int form, bool fp64);  // form: 6 (rows of six links), kEllRow (padded rows) or 0
 // Blocks of the resident sweep per SM (smem_bytes > 0: the shared-memory form, whose limit
 // is raised here; 0 when it does not fit).
 int resident_blocks_per_sm(int threads, bool pol, size_t smem_bytes = 0);

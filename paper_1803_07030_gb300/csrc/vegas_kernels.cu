@@ -323,7 +323,8 @@ constexpr int kDirectRow = 12;  // rows up to this length gather all neighbours 
 // CG = 1: neighbour spins are read with ld.global.cg (L2 only) because other blocks of the same
 // launch write them (cooperative and cluster sweeps); otherwise through the read-only path.
 // UD > 0: every row has UD links and site g's start at ud_e0 (a sample of uniform degree), so
-// row_ptr is not read and all UD neighbour rows are in flight together.
+// row_ptr is not read and all UD neighbour rows are in flight together. UD = kEllRow: E holds
+// fixed rows of kEllRow links in row order, padded with col = -1 entries, which are skipped.
 template <int PM, int LM, int POL, int CG = 0, int UD = 0>
 __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const int64_t *row_ptr, int g, int r, int R,
                                                int lower_end, uint32_t orig, const Site32 &p, float beta, float B,
@@ -337,18 +338,21 @@ __device__ __forceinline__ bool direct_attempt(float4 *S, const int2 *E, const i
     const int64_t e0 = UD > 0 ? ud_e0 : __ldg(row_ptr + g);
     const int deg = UD > 0 ? UD : (int)(__ldg(row_ptr + g + 1) - e0);
     if (UD > 0) {
+        constexpr bool PAD = UD == kEllRow;
         int2 ed[UD > 0 ? UD : 1];
         float4 Sj[UD > 0 ? UD : 1];
 #pragma unroll
         for (int k = 0; k < UD; ++k) ed[k] = __ldg(E + e0 + k);
 #pragma unroll
-        for (int k = 0; k < UD; ++k) {
-            const float4 *q = S + (int64_t)ed[k].x * R + r;
-            Sj[k] = CG ? __ldcg(q) : __ldg(q);
-        }
+        for (int k = 0; k < UD; ++k)
+            if (!PAD || ed[k].x >= 0) {
+                const float4 *q = S + (int64_t)ed[k].x * R + r;
+                Sj[k] = CG ? __ldcg(q) : __ldg(q);
+            }
 #pragma unroll
         for (int k = 0; k < UD; ++k)
-            link32(Sj[k], __int_as_float(ed[k].y), LM == 2 && ed[k].x < lower_end, hxy, hz, lxy, lz);
+            if (!PAD || ed[k].x >= 0)
+                link32(Sj[k], __int_as_float(ed[k].y), LM == 2 && ed[k].x < lower_end, hxy, hz, lxy, lz);
     } else if (deg <= kDirectRow) {
         // all links first, then the neighbour rows with every load in flight together; the
         // field still sums in row order
@@ -1060,7 +1064,8 @@ __device__ bool grid_barrier(GridBarrier *b, uint32_t nblocks, int64_t timeout_n
     return s_ok != 0;
 }
 
-// UD > 0: a sample whose every row has UD links (direct_attempt's uniform-degree path).
+// UD > 0: a sample whose every row has UD links (direct_attempt's uniform-degree path); UD =
+// kEllRow: rows of at most kEllRow links read as fixed, padded rows (ca.ell).
 template <int NT, int POL, int UD = 0>
 __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
     const PassArgs &a = ca.pass;
@@ -1127,9 +1132,10 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
                 if (a.params_mode == 2) p = site_params32(a, 2, g);
                 // one code path for every parameter mode (zero constants add signed zeros)
                 float4 Sq;
-                const bool ok = direct_attempt<2, 2, POL, 1, UD>(S, E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t, inst,
-                                                              k0, k1, acc, nan_seen, a.pol32, 0.f, Sq,
-                                                              a.edge_base + (int64_t)(g - a.site_off) * UD);
+                const bool ok = direct_attempt<2, 2, POL, 1, UD>(
+                    S, UD == kEllRow ? ca.ell : E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t, inst, k0, k1, acc,
+                    nan_seen, a.pol32, 0.f, Sq,
+                    UD == kEllRow ? (int64_t)g * kEllRow : a.edge_base + (int64_t)(g - a.site_off) * UD);
                 if (log_accepts)
                     a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
             }
@@ -1513,9 +1519,11 @@ void launch_snapshot(const void *spins, void *snap, int64_t n16, const RunState 
 
 using CoopFn = void (*)(CoopArgs);
 
-// rows of six links (the simple cubic lattices) take the uniform-degree form
-CoopFn select_coop(bool pol, int deg) {
-    if (deg == 6) return pol ? coop32_kernel<kCoopThreads, 1, 6> : coop32_kernel<kCoopThreads, 0, 6>;
+// rows of six links (the simple cubic lattices) take the uniform-degree form, other rows of at
+// most kEllRow links the padded fixed rows when the host built them (form = kEllRow)
+CoopFn select_coop(bool pol, int form) {
+    if (form == 6) return pol ? coop32_kernel<kCoopThreads, 1, 6> : coop32_kernel<kCoopThreads, 0, 6>;
+    if (form == kEllRow) return pol ? coop32_kernel<kCoopThreads, 1, kEllRow> : coop32_kernel<kCoopThreads, 0, kEllRow>;
     return pol ? coop32_kernel<kCoopThreads, 1> : coop32_kernel<kCoopThreads, 0>;
 }
 
@@ -1534,15 +1542,16 @@ int launch_coop(const CoopArgs &a, int grid, void *stream) {
         cfg.blockDim = dim3(kCoop64Threads);
         return (int)cudaLaunchKernelEx(&cfg, coop64_kernel<kCoop64Threads>, a);
     }
-    return (int)cudaLaunchKernelEx(&cfg, select_coop(a.pass.pol32 != nullptr, a.pass.deg), a);
+    return (int)cudaLaunchKernelEx(&cfg, select_coop(a.pass.pol32 != nullptr, a.pass.deg == 6 ? 6 : (a.ell ? kEllRow : 0)),
+                                   a);
 }
 
-int coop_blocks_per_sm(bool pol, int deg, bool fp64) {
+int coop_blocks_per_sm(bool pol, int form, bool fp64) {
     int nb = 0;
     if (fp64)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop64_kernel<kCoop64Threads>, kCoop64Threads, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_coop(pol, deg), kCoopThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_coop(pol, form), kCoopThreads, 0);
     return nb > 0 ? nb : 1;
 }
 

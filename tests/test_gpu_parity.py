@@ -310,8 +310,11 @@ def test_resident_split_runs_and_autotune():
 # bounded grid barrier. Same arithmetic and random numbers: spins equal the per-class sweep.
 
 @pytest.mark.parametrize("make,R", [(lambda: sc_periodic(16, k_uni=0.05), 1), (lambda: sc_periodic(12, bimodal_seed=2), 4),
-                                    (lambda: core_shell_particle(seed=3, radius=5.0, core_radius=3.5), 2)])
+                                    (lambda: core_shell_particle(seed=3, radius=5.0, core_radius=3.5), 2),
+                                    (lambda: fcc_sphere(4.5).with_policy([oracle.GAUSSIAN], [0.4]), 2)])
 def test_cooperative_sweep_equals_per_class_sweep(make, R):
+    """Rows of six links take the uniform-degree form, rows of at most twelve the padded
+    fixed rows (with and without a policy table): the per-class sweep's spins bit for bit."""
     s = make()
     T = np.stack([np.array([2.0, 0.9, 0.5]) * (1 + 0.1 * i) for i in range(R)])
     B = np.stack([np.array([0.5, -0.5, 1.0]) for _ in range(R)])
