@@ -1064,6 +1064,104 @@ __device__ bool grid_barrier(GridBarrier *b, uint32_t nblocks, int64_t timeout_n
     return s_ok != 0;
 }
 
+// The grid barrier in two halves, so that a block can do work between arriving and waiting
+// that no other block's writes affect. Arrival: every thread of the block is done, thread 0
+// notes the generation and adds the block to the count (the last block advances the
+// generation). Wait: thread 0 waits, bounded as in grid_barrier, until the generation moves.
+struct BarrierTicket {
+    uint32_t gen;
+    bool released;
+};
+__device__ __forceinline__ BarrierTicket grid_arrive(GridBarrier *b, uint32_t nblocks, bool skip) {
+    BarrierTicket tk{0u, false};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile GridBarrier *vb = b;
+        tk.gen = vb->gen;
+        __threadfence();
+        if (!skip && atomicAdd(&b->count, 1u) == nblocks - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+            tk.released = true;
+        }
+    }
+    return tk;  // meaningful in thread 0 only
+}
+__device__ bool grid_wait(GridBarrier *b, BarrierTicket tk, int64_t timeout_ns, uint32_t *err, bool skip) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = skip ? 0 : 1;  // fault injection: the block left without arriving
+        volatile GridBarrier *vb = b;
+        if (ok && !tk.released) {
+            const uint64_t t0 = global_ns();
+            while (vb->gen == tk.gen) {
+                if (vb->abort) {
+                    ok = 0;
+                    break;
+                }
+                if ((int64_t)(global_ns() - t0) > timeout_ns) {
+                    atomicOr(err, kErrTimeout);
+                    atomicExch(&b->abort, 1u);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (vb->abort) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// One attempt on a row of six links split in two: prep6 takes everything that no other
+// block writes during a class (caller id, parameters, the site's own spin, which only its own
+// thread writes, the links, the Philox block and the trial), finish6 the neighbour spins
+// (through L2), the field in row order and the decision. Together they compute what
+// direct_attempt<2, 2, POL, 1, 6> computes, operation for operation.
+struct Prep6 {
+    uint32_t orig, wacc;
+    Site32 p;
+    float4 Si;
+    int2 ed[6];
+    float3 P;
+};
+template <int POL>
+__device__ __forceinline__ void prep6(const PassArgs &a, int g, int r, int R, uint32_t t, uint32_t inst, uint32_t k0,
+                                      uint32_t k1, const float4 *S, const int2 *E, Prep6 &q) {
+    q.orig = (uint32_t)__ldg(a.orig + g);
+    q.p = Site32{a.u32.nx, a.u32.ny, a.u32.nz, a.u32.s, a.u32.ex, a.u32.ey, a.u32.ez, a.u32.k, a.u32.kc};
+    if (a.params_mode == 2) q.p = site_params32(a, 2, g);
+    q.Si = S[(int64_t)g * R + r];
+    const int64_t e0 = a.edge_base + (int64_t)(g - a.site_off) * 6;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q.ed[k] = __ldg(E + e0 + k);
+    const uint4 rw = philox10(make_uint4(q.orig, t, inst, kPurposeTrial32), k0, k1);
+    q.P = POL ? policy_trial32(a.pol32[g], 0.f, q.Si, q.p.sn, rw) : trial_random32(rw, q.p.sn);
+    q.wacc = rw.z;
+}
+__device__ __forceinline__ bool finish6(const Prep6 &q, int g, int r, int R, int lower_end, float beta, float B,
+                                        float4 *S, Acc32 &acc, bool &nan_seen, float4 &Sq) {
+    float2 hxy = make_float2(0.f, 0.f), lxy = make_float2(0.f, 0.f);
+    float hz = 0.f, lz = 0.f;
+    float4 Sj[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Sj[k] = __ldcg(S + (int64_t)q.ed[k].x * R + r);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) link32(Sj[k], __int_as_float(q.ed[k].y), q.ed[k].x < lower_end, hxy, hz, lxy, lz);
+    float4 Sn;
+    bool ok, bad;
+    float e_i;
+    attempt32<2, 2>(q.Si, hxy, hz, lxy, lz, q.p, beta, B, q.P, q.wacc, Sn, ok, e_i, bad);
+    nan_seen |= bad;
+    if (ok) S[(int64_t)g * R + r] = Sn;
+    acc.add(e_i, Sn, ok);
+    Sq = Sn;
+    return ok;
+}
+
 // UD > 0: a sample whose every row has UD links (direct_attempt's uniform-degree path); UD =
 // kEllRow: rows of at most kEllRow links read as fixed, padded rows (ca.ell).
 template <int NT, int POL, int UD = 0>
@@ -1118,6 +1216,71 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
     // none adds the counts of MCS m + 1 before the next barrier, which block 0 reaches only
     // after recording. That saves one grid barrier per MCS.
     const bool deferred = ca.n_colours >= 2;
+    if (UD == 6 && deferred) {
+        // Split-phase barriers: after arriving at the end of a class, a block prepares its
+        // first attempt of the next class (prep6) and only then waits. The MCS's partial sums
+        // go out after its last wait, so every block adds the MCS's accepted counts only
+        // after block 0 has recorded the previous MCS (which it does after the next class-0
+        // wait, and before arriving at the class-1 barrier the other blocks then wait on).
+        Acc32 acc;
+        BarrierTicket tk{0u, false};
+        bool pending = false;  // an arrival not yet waited for
+        for (int m = 0; m < ca.mcs; ++m) {
+            const uint32_t t = t0 + (uint32_t)m;
+            const bool log_accepts = a.alog && t < a.alog_mcs;
+            for (int c = 0; c < ca.n_colours; ++c) {
+                const int cb = ca.cstart[c], ce = ca.cstart[c + 1];
+                const int64_t n_work = (int64_t)(ce - cb) << a.log2R;
+                const bool has = w0 < n_work;
+                Prep6 q;
+                if (has) prep6<POL>(a, cb + (int)(w0 >> a.log2R), r, R, t, inst, k0, k1, S, E, q);
+                if (pending) {
+                    if (!grid_wait(ca.bar, tk, ca.timeout_ns, a.err, skip)) return;
+                    pending = false;
+                    if (c == 0) {  // MCS m - 1 is over everywhere: its partial sums
+                        acc.flush();
+                        block_partials(acc.d, acc.nacc, R,
+                                       ca.partial + ((int64_t)((m - 1) & 1) * gridDim.x + blockIdx.x) * R * 4,
+                                       acc_counters(rs, a.inst_local0));
+                        acc = Acc32();
+                    }
+                    if (c == 1 && m > 0) record(m - 1);
+                }
+                if (has) {
+                    const int g = cb + (int)(w0 >> a.log2R);
+                    float4 Sq;
+                    const bool ok = finish6(q, g, r, R, cb, beta, B, S, acc, nan_seen, Sq);
+                    if (log_accepts)
+                        a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + q.orig] =
+                            ok ? 1 : 0;
+                }
+                for (int64_t w = w0 + stride; w < n_work; w += stride) {
+                    const int g = cb + (int)(w >> a.log2R);
+                    const uint32_t orig = (uint32_t)__ldg(a.orig + g);
+                    Site32 p{a.u32.nx, a.u32.ny, a.u32.nz, a.u32.s, a.u32.ex, a.u32.ey, a.u32.ez, a.u32.k, a.u32.kc};
+                    if (a.params_mode == 2) p = site_params32(a, 2, g);
+                    float4 Sq;
+                    const bool ok = direct_attempt<2, 2, POL, 1, 6>(S, E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t,
+                                                                     inst, k0, k1, acc, nan_seen, a.pol32, 0.f, Sq,
+                                                                     a.edge_base + (int64_t)(g - a.site_off) * 6);
+                    if (log_accepts)
+                        a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
+                }
+                tk = grid_arrive(ca.bar, gridDim.x, skip);
+                pending = true;
+            }
+        }
+        if (pending) {
+            if (!grid_wait(ca.bar, tk, ca.timeout_ns, a.err, skip)) return;
+            acc.flush();
+            block_partials(acc.d, acc.nacc, R, ca.partial + ((int64_t)((ca.mcs - 1) & 1) * gridDim.x + blockIdx.x) * R * 4,
+                           acc_counters(rs, a.inst_local0));
+            if (!grid_barrier(ca.bar, gridDim.x, ca.timeout_ns, a.err, skip)) return;
+            record(ca.mcs - 1);
+        }
+        if (nan_seen) atomicOr(a.err, kErrNaN);
+        return;
+    }
     for (int m = 0; m < ca.mcs; ++m) {
         const uint32_t t = t0 + (uint32_t)m;
         const bool log_accepts = a.alog && t < a.alog_mcs;
