@@ -1116,41 +1116,48 @@ __device__ bool grid_wait(GridBarrier *b, BarrierTicket tk, int64_t timeout_ns, 
     return s_ok != 0;
 }
 
-// One attempt on a row of six links split in two: prep6 takes everything that no other
-// block writes during a class (caller id, parameters, the site's own spin, which only its own
-// thread writes, the links, the Philox block and the trial), finish6 the neighbour spins
+// One attempt on a fixed row of UD links (6: rows of six links; kEllRow: padded rows, col = -1
+// entries skipped) split in two: prep_attempt takes everything that no other block writes
+// during a class (caller id, parameters, the site's own spin, which only its own thread
+// writes, the links, the Philox block and the trial), finish_attempt the neighbour spins
 // (through L2), the field in row order and the decision. Together they compute what
-// direct_attempt<2, 2, POL, 1, 6> computes, operation for operation.
-struct Prep6 {
+// direct_attempt<2, 2, POL, 1, UD> computes, operation for operation.
+template <int UD>
+struct PrepU {
     uint32_t orig, wacc;
     Site32 p;
     float4 Si;
-    int2 ed[6];
+    int2 ed[UD > 0 ? UD : 1];
     float3 P;
 };
-template <int POL>
-__device__ __forceinline__ void prep6(const PassArgs &a, int g, int r, int R, uint32_t t, uint32_t inst, uint32_t k0,
-                                      uint32_t k1, const float4 *S, const int2 *E, Prep6 &q) {
+template <int UD, int POL>
+__device__ __forceinline__ void prep_attempt(const PassArgs &a, const int2 *E, int64_t e0, int g, int r, int R,
+                                             uint32_t t, uint32_t inst, uint32_t k0, uint32_t k1, const float4 *S,
+                                             PrepU<UD> &q) {
     q.orig = (uint32_t)__ldg(a.orig + g);
     q.p = Site32{a.u32.nx, a.u32.ny, a.u32.nz, a.u32.s, a.u32.ex, a.u32.ey, a.u32.ez, a.u32.k, a.u32.kc};
     if (a.params_mode == 2) q.p = site_params32(a, 2, g);
     q.Si = S[(int64_t)g * R + r];
-    const int64_t e0 = a.edge_base + (int64_t)(g - a.site_off) * 6;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) q.ed[k] = __ldg(E + e0 + k);
+    for (int k = 0; k < UD; ++k) q.ed[k] = __ldg(E + e0 + k);
     const uint4 rw = philox10(make_uint4(q.orig, t, inst, kPurposeTrial32), k0, k1);
     q.P = POL ? policy_trial32(a.pol32[g], 0.f, q.Si, q.p.sn, rw) : trial_random32(rw, q.p.sn);
     q.wacc = rw.z;
 }
-__device__ __forceinline__ bool finish6(const Prep6 &q, int g, int r, int R, int lower_end, float beta, float B,
-                                        float4 *S, Acc32 &acc, bool &nan_seen, float4 &Sq) {
+template <int UD>
+__device__ __forceinline__ bool finish_attempt(const PrepU<UD> &q, int g, int r, int R, int lower_end, float beta,
+                                               float B, float4 *S, Acc32 &acc, bool &nan_seen, float4 &Sq) {
+    constexpr bool PAD = UD == kEllRow;
     float2 hxy = make_float2(0.f, 0.f), lxy = make_float2(0.f, 0.f);
     float hz = 0.f, lz = 0.f;
-    float4 Sj[6];
+    float4 Sj[UD > 0 ? UD : 1];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) Sj[k] = __ldcg(S + (int64_t)q.ed[k].x * R + r);
+    for (int k = 0; k < UD; ++k)
+        if (!PAD || q.ed[k].x >= 0) Sj[k] = __ldcg(S + (int64_t)q.ed[k].x * R + r);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) link32(Sj[k], __int_as_float(q.ed[k].y), q.ed[k].x < lower_end, hxy, hz, lxy, lz);
+    for (int k = 0; k < UD; ++k)
+        if (!PAD || q.ed[k].x >= 0)
+            link32(Sj[k], __int_as_float(q.ed[k].y), q.ed[k].x < lower_end, hxy, hz, lxy, lz);
     float4 Sn;
     bool ok, bad;
     float e_i;
@@ -1216,9 +1223,9 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
     // none adds the counts of MCS m + 1 before the next barrier, which block 0 reaches only
     // after recording. That saves one grid barrier per MCS.
     const bool deferred = ca.n_colours >= 2;
-    if (UD == 6 && deferred) {
+    if (UD > 0 && deferred) {
         // Split-phase barriers: after arriving at the end of a class, a block prepares its
-        // first attempt of the next class (prep6) and only then waits. The MCS's partial sums
+        // first attempt of the next class (prep_attempt) and only then waits. The MCS's partial sums
         // go out after its last wait, so every block adds the MCS's accepted counts only
         // after block 0 has recorded the previous MCS (which it does after the next class-0
         // wait, and before arriving at the class-1 barrier the other blocks then wait on).
@@ -1232,8 +1239,13 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
                 const int cb = ca.cstart[c], ce = ca.cstart[c + 1];
                 const int64_t n_work = (int64_t)(ce - cb) << a.log2R;
                 const bool has = w0 < n_work;
-                Prep6 q;
-                if (has) prep6<POL>(a, cb + (int)(w0 >> a.log2R), r, R, t, inst, k0, k1, S, E, q);
+                PrepU<UD> q;
+                if (has) {
+                    const int g = cb + (int)(w0 >> a.log2R);
+                    prep_attempt<UD, POL>(a, UD == kEllRow ? ca.ell : E,
+                                          UD == kEllRow ? (int64_t)g * kEllRow : a.edge_base + (int64_t)(g - a.site_off) * UD,
+                                          g, r, R, t, inst, k0, k1, S, q);
+                }
                 if (pending) {
                     if (!grid_wait(ca.bar, tk, ca.timeout_ns, a.err, skip)) return;
                     pending = false;
@@ -1249,7 +1261,7 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
                 if (has) {
                     const int g = cb + (int)(w0 >> a.log2R);
                     float4 Sq;
-                    const bool ok = finish6(q, g, r, R, cb, beta, B, S, acc, nan_seen, Sq);
+                    const bool ok = finish_attempt<UD>(q, g, r, R, cb, beta, B, S, acc, nan_seen, Sq);
                     if (log_accepts)
                         a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + q.orig] =
                             ok ? 1 : 0;
@@ -1260,9 +1272,10 @@ __global__ void __launch_bounds__(NT) coop32_kernel(const CoopArgs ca) {
                     Site32 p{a.u32.nx, a.u32.ny, a.u32.nz, a.u32.s, a.u32.ex, a.u32.ey, a.u32.ez, a.u32.k, a.u32.kc};
                     if (a.params_mode == 2) p = site_params32(a, 2, g);
                     float4 Sq;
-                    const bool ok = direct_attempt<2, 2, POL, 1, 6>(S, E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t,
-                                                                     inst, k0, k1, acc, nan_seen, a.pol32, 0.f, Sq,
-                                                                     a.edge_base + (int64_t)(g - a.site_off) * 6);
+                    const bool ok = direct_attempt<2, 2, POL, 1, UD>(
+                        S, UD == kEllRow ? ca.ell : E, a.row_ptr, g, r, R, cb, orig, p, beta, B, t, inst, k0, k1, acc,
+                        nan_seen, a.pol32, 0.f, Sq,
+                        UD == kEllRow ? (int64_t)g * kEllRow : a.edge_base + (int64_t)(g - a.site_off) * UD);
                     if (log_accepts)
                         a.alog[(int64_t)t * a.alog_stride + a.alog_base + (int64_t)r * a.n_sample_sites + orig] = ok ? 1 : 0;
                 }
