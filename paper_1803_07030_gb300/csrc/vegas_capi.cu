@@ -252,7 +252,8 @@ bool set_resident_shape(vegas_ctx *c, int threads, int group_threads = 0, int gr
     c->res_smem = false;
     if (smem && c->res_smem_eligible) {
         ResidentArgs a = c->res;
-        if (grouped) a.group_sites = (int)std::min<int64_t>(group_sites, kResSmemBytes / (12 * (threads / group_threads)));
+        if (grouped)  // an even cap: the groups' regions then keep the budget with even starts
+            a.group_sites = (int)std::min<int64_t>(group_sites, (kResSmemBytes / (12 * (threads / group_threads))) & ~1);
         a.smem_sites = c->max_instance_sites;
         const int bps = resident_blocks_per_sm(threads, c->res_policy, resident_smem_bytes(a, threads));
         cudaGetLastError();
@@ -285,7 +286,7 @@ bool set_cluster_shape(vegas_ctx *c, int cs, int threads, int split = 0, int gro
         a.group_sites = a.group_threads > 0 ? group_sites : 0;
     }
     if (smem && a.group_threads > 0)
-        a.group_sites = (int)std::min<int64_t>(a.group_sites, kResSmemBytes / (12 * (threads / a.group_threads)));
+        a.group_sites = (int)std::min<int64_t>(a.group_sites, (kResSmemBytes / (12 * (threads / a.group_threads))) & ~1);
     a.smem_sites = smem ? c->max_instance_sites : 0;
     const int cap = cluster_capacity(cs, threads, c->res_policy, cluster_smem_bytes(a, threads));
     cudaGetLastError();

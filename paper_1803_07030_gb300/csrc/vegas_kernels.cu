@@ -433,9 +433,22 @@ __device__ bool direct_row_ok(const PassArgs &a, int g, uint32_t orig) {
 }
 #endif
 
+// Spins in shared memory (the resident and cluster sweeps): a region of 3 cap floats holds x and
+// y of site i as one 8-byte pair at pair index i and z at float 2 cap + i, so a neighbour takes
+// two loads; regions start at multiples of 3 cap floats with cap even, so the pairs are 8-byte
+// aligned.
+__device__ __forceinline__ float4 sm_spin(const float *sp, int cap, int i) {
+    const float2 xy = ((const float2 *)sp)[i];
+    return make_float4(xy.x, xy.y, sp[2 * cap + i], 0.f);
+}
+__device__ __forceinline__ void sm_set(float *sp, int cap, int i, float x, float y, float z) {
+    ((float2 *)sp)[i] = make_float2(x, y);
+    sp[2 * cap + i] = z;
+}
+
 // The same attempt with the instance's spins in shared memory (resident sweep with spins kept
-// on chip for the whole step): sp holds x, y, z of the instance's sites in three arrays of
-// cap floats, site g at g - g0. The site's links come as a fixed row of kEllRow (neighbour,
+// on chip for the whole step): sp holds the instance's sites in the layout of sm_spin, site g
+// at g - g0. The site's links come as a fixed row of kEllRow (neighbour,
 // J) pairs in row order, padded with neighbour -1 (erow, 16-byte aligned), so no row offset is
 // read before them. Neighbour values, the field's row order and every rounding are those of
 // direct_attempt, so the results are bit for bit the same.
@@ -447,7 +460,7 @@ __device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const i
                                              uint32_t inst, uint32_t k0, uint32_t k1, Acc32 &acc, bool &nan_seen,
                                              const PolicySite32 *pol, float sigma, float4 &Sq) {
     const int i = g - g0;
-    const float4 Si = make_float4(sp[i], sp[cap + i], sp[2 * cap + i], 0.f);
+    const float4 Si = sm_spin(sp, cap, i);
     float2 hxy = make_float2(0.f, 0.f), lxy = make_float2(0.f, 0.f);
     float hz = 0.f, lz = 0.f;
     int4 q[kEllRow / 2];
@@ -457,12 +470,12 @@ __device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const i
     for (int k = 0; k < kEllRow / 2; ++k) {
         if (q[k].x >= 0) {
             const int j = q[k].x - g0;
-            link32(make_float4(sp[j], sp[cap + j], sp[2 * cap + j], 0.f), __int_as_float(q[k].y), q[k].x < lower_end,
+            link32(sm_spin(sp, cap, j), __int_as_float(q[k].y), q[k].x < lower_end,
                    hxy, hz, lxy, lz);
         }
         if (q[k].z >= 0) {
             const int j = q[k].z - g0;
-            link32(make_float4(sp[j], sp[cap + j], sp[2 * cap + j], 0.f), __int_as_float(q[k].w), q[k].z < lower_end,
+            link32(sm_spin(sp, cap, j), __int_as_float(q[k].w), q[k].z < lower_end,
                    hxy, hz, lxy, lz);
         }
     }
@@ -473,11 +486,7 @@ __device__ __forceinline__ bool smem_attempt(float *sp, int cap, int g0, const i
     float e_i;
     attempt32<AN ? 2 : 0, 2>(Si, hxy, hz, lxy, lz, p, beta, B, P, rw.z, Sn, ok, e_i, bad);
     nan_seen |= bad;
-    if (ok) {
-        sp[i] = Sn.x;
-        sp[cap + i] = Sn.y;
-        sp[2 * cap + i] = Sn.z;
-    }
+    if (ok) sm_set(sp, cap, i, Sn.x, Sn.y, Sn.z);
     acc.add(e_i, Sn, ok);
     Sq = Sn;
     return ok;
@@ -639,10 +648,7 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
     if (SM) {  // the instance's spins into shared memory
         for (int g = I.g_begin + gtid; g < I.g_end; g += gthreads) {
             const float4 v = S[(int64_t)g * R + I.r];
-            const int i = g - I.g_begin;
-            sp[i] = v.x;
-            sp[cap + i] = v.y;
-            sp[2 * cap + i] = v.z;
+            sm_set(sp, cap, g - I.g_begin, v.x, v.y, v.z);
         }
         group_sync(gbar, gthreads);
     }
@@ -746,7 +752,7 @@ __device__ __forceinline__ void resident_sweep_block(const ResidentArgs &a, cons
     if (SM)  // the last MCS ended at a barrier: its spins go back to global memory
         for (int g = I.g_begin + gtid; g < I.g_end; g += gthreads) {
             const int i = g - I.g_begin;
-            S[(int64_t)g * R + I.r] = make_float4(sp[i], sp[cap + i], sp[2 * cap + i], 0.f);
+            S[(int64_t)g * R + I.r] = sm_spin(sp, cap, i);
         }
 }
 
@@ -784,7 +790,8 @@ __device__ __forceinline__ void resident_loop(const ResidentArgs &a, int first, 
             const ResidentInst I = a.insts[item];
             const int cap = ng == 1 ? a.smem_sites : a.group_sites;
             resident_sweep_block<NT, POL, SM, AN>(a, I, s_red, s_acc, s_tm, s_part, nan_seen, (int)threadIdx.x - gi * gt,
-                                              gt, ng == 1 ? 0 : 1 + gi, SM ? dyn + (size_t)gi * 3 * cap : nullptr, cap);
+                                              gt, ng == 1 ? 0 : 1 + gi,
+                                              SM ? dyn + (size_t)gi * 3 * (size_t)((cap + 1) & ~1) : nullptr, cap);
         }
         __syncthreads();  // every group is done before the items are drawn again
     }
@@ -806,7 +813,7 @@ __global__ void __launch_bounds__(NT) resident32_kernel(const ResidentArgs a) {
     __shared__ uint32_t s_acc[NT / 32];
     __shared__ double s_tm[NT / 32][kResidentMaxTypes][3];  // per warp and type, segment order
     __shared__ double s_part[NT][4];                         // every thread's MCS totals
-    extern __shared__ float res_dyn[];                       // SM: the instances' spins
+    extern __shared__ __align__(16) float res_dyn[];         // SM: the instances' spins
     bool nan_seen = false;
     resident_loop<NT, POL, SM, AN>(a, -1, s_red, s_acc, s_tm, s_part, s_items, nan_seen, res_dyn);
     if (nan_seen) atomicOr(a.err, kErrNaN);
@@ -848,7 +855,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
     const int n_types = a.n_types;
     RunState *rs = a.run;
     bool nan_seen = false;
-    extern __shared__ float cl_dyn[];  // SM: this block's copy of the instance's spins
+    extern __shared__ __align__(16) float cl_dyn[];  // SM: this block's copy of the instance's spins
     const int cap = a.smem_sites;
     int alone = -2;  // >= -1: the blocks sweep alone from now on (-1: draw the next instance)
     for (;;) {
@@ -871,10 +878,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
         if (SM) {  // every block: the whole instance into its own shared memory
             for (int g = I.g_begin + (int)threadIdx.x; g < I.g_end; g += NT) {
                 const float4 v = S[(int64_t)g * R + I.r];
-                const int i = g - I.g_begin;
-                cl_dyn[i] = v.x;
-                cl_dyn[cap + i] = v.y;
-                cl_dyn[2 * cap + i] = v.z;
+                sm_set(cl_dyn, cap, g - I.g_begin, v.x, v.y, v.z);
             }
             cl.sync();  // no block writes into a copy that is still being loaded
         }
@@ -897,10 +901,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
                         if (ok) {  // the new spin into the other blocks' copies
                             const int i = g - I.g_begin;
                             for (int b = 1; b < CS; ++b) {
-                                float *o = cl.map_shared_rank(cl_dyn, (rank + b) % CS);
-                                o[i] = Sq.x;
-                                o[cap + i] = Sq.y;
-                                o[2 * cap + i] = Sq.z;
+                                sm_set(cl.map_shared_rank(cl_dyn, (rank + b) % CS), cap, i, Sq.x, Sq.y, Sq.z);
                             }
                         }
                     } else {
@@ -1000,7 +1001,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
                 const int4 sg = a.segs[I.seg_off + q];
                 for (int g = sg.x + rank * NT + (int)threadIdx.x; g < sg.y; g += CS * NT) {
                     const int i = g - I.g_begin;
-                    S[(int64_t)g * R + I.r] = make_float4(cl_dyn[i], cl_dyn[cap + i], cl_dyn[2 * cap + i], 0.f);
+                    S[(int64_t)g * R + I.r] = sm_spin(cl_dyn, cap, i);
                 }
             }
     }
@@ -1753,7 +1754,8 @@ size_t resident_smem_bytes(const ResidentArgs &a, int threads) {
     if (a.smem_sites <= 0) return 0;
     const int nt = resident_threads(threads, true);
     const int ng = a.group_threads > 0 && a.group_threads < nt ? nt / a.group_threads : 1;
-    const int64_t sites = std::max<int64_t>(a.smem_sites, ng > 1 ? (int64_t)ng * a.group_sites : 0);
+    // groups' regions start at even site counts (sm_spin's pairs stay 8-byte aligned)
+    const int64_t sites = std::max<int64_t>(a.smem_sites, ng > 1 ? (int64_t)ng * ((a.group_sites + 1) & ~1) : 0);
     return (size_t)sites * 3 * sizeof(float);
 }
 
@@ -1781,7 +1783,8 @@ size_t cluster_smem_bytes(const ResidentArgs &a, int threads) {
     if (a.smem_sites <= 0) return 0;
     const int nt = threads >= 512 ? 512 : 256;
     const int ng = a.group_threads > 0 && a.group_threads < nt ? nt / a.group_threads : 1;
-    const int64_t sites = std::max<int64_t>(a.smem_sites, ng > 1 ? (int64_t)ng * a.group_sites : 0);
+    // groups' regions start at even site counts (sm_spin's pairs stay 8-byte aligned)
+    const int64_t sites = std::max<int64_t>(a.smem_sites, ng > 1 ? (int64_t)ng * ((a.group_sites + 1) & ~1) : 0);
     return (size_t)sites * 3 * sizeof(float);
 }
 
