@@ -1709,6 +1709,9 @@ extern "C" vegas_status vegas_run(vegas_ctx *c, const double *T, const double *B
                         if (uneven) {
                             cand.push_back({3, 2, 512, big / 2, 128, 1});
                             cand.push_back({3, 4, 512, big / 4, 128, 1});
+                            // clusters for the largest only: they set the launch's length
+                            cand.push_back({3, 2, 512, big * 3 / 4, 256, 1});
+                            cand.push_back({3, 2, 512, big * 7 / 8, 256, 1});
                         }
                     }
                 }

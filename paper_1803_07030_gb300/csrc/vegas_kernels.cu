@@ -797,10 +797,10 @@ __device__ __forceinline__ void resident_loop(const ResidentArgs &a, int first, 
     }
 }
 
-// The same as a separate function, for the cluster sweep's second phase: its registers are
-// then allocated apart from the cluster phase's.
+// The same, for the cluster sweep's second phase (inlined: a call kept its registers apart from
+// the cluster phase's but made the phase slower than the resident kernel).
 template <int NT, int POL, int SM = 0>
-__device__ __noinline__ void resident_loop_call(const ResidentArgs &a, int first, double (*s_red)[4], uint32_t *s_acc,
+__device__ __forceinline__ void resident_loop_call(const ResidentArgs &a, int first, double (*s_red)[4], uint32_t *s_acc,
                                                 double (*s_tm)[kResidentMaxTypes][3], double (*s_part)[4],
                                                 int *s_items, bool &nan_seen, float *dyn = nullptr) {
     resident_loop<NT, POL, SM>(a, first, s_red, s_acc, s_tm, s_part, s_items, nan_seen, dyn);
@@ -960,7 +960,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) cluster32_kernel(const ResidentA
                 }
                 for (int q = 0; q < 4; ++q) s_blk[q] = sum[q];
                 s_blk[4] = (double)nsum;
-                for (int k = 0; k < kResidentMaxTypes; ++k)
+                // per-type magnetization only with per-type statistics (a serial chain on one
+                // thread while the cluster waits)
+                for (int k = 0; k < n_types && k < kResidentMaxTypes; ++k)
                     for (int c = 0; c < 3; ++c) {
                         double x = 0.0;
                         for (int w = 0; w < NT / 32; ++w) {
