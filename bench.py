@@ -617,7 +617,10 @@ def run_workload(args):
         ctx = vg.Context(share["samples"], precision=w.precision, replicas=w.replicas, seed=w.seed,
                          inst_base=share["inst_base"], device=dev, stream=int(stream.cuda_stream),
                          variant=args.variant, type_stats=args.type_stats, snapshots=args.snapshots,
-                         resident_smem=args.resident_smem, graphs=args.graphs)
+                         resident_smem=args.resident_smem, graphs=args.graphs,
+                         cluster_blocks=args.cluster_blocks, cluster_threads=args.cluster_threads,
+                         cluster_split=args.cluster_split, group_threads=args.group_threads,
+                         group_sites=16 * args.group_threads)
 
     def barrier():
         if world > 1:
@@ -859,6 +862,15 @@ def main():
     ap.add_argument("--resident-smem", type=int, default=0, choices=[-1, 0, 1],
                     help="secondary workloads: 1 keeps spins in shared memory in the resident or cluster sweep, "
                          "-1 never, 0 automatic (profiling commands fix it with --variant)")
+    ap.add_argument("--cluster-blocks", type=int, default=0,
+                    help="secondary workloads with --variant 3: blocks per cluster (0 automatic); with the next "
+                         "three, the shape the automatic choice keeps, for profiling commands")
+    ap.add_argument("--cluster-threads", type=int, default=0, help="threads per block of the cluster sweep (0 automatic)")
+    ap.add_argument("--cluster-split", type=int, default=0,
+                    help="cluster sweep: instances of at most this many sites swept by one block each (0: all by clusters)")
+    ap.add_argument("--group-threads", type=int, default=0,
+                    help="resident or cluster sweep: threads per small instance swept several to a block "
+                         "(up to 16 sites per thread; 0 off)")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1, 2],
                     help="secondary workloads: 1 a run as one CUDA graph, 2 a graph per step, 0 direct launches "
                          "(profilers see the kernels of graphs without conditional nodes only)")

@@ -43,7 +43,8 @@ class FakeContext:
     made = []
 
     def __init__(self, samples, precision=32, replicas=1, seed=1, inst_base=0, device=-1, stream=None,
-                 timing=False, variant=-1, type_stats=False, snapshots=False, resident_smem=0, graphs=1):
+                 timing=False, variant=-1, type_stats=False, snapshots=False, resident_smem=0, graphs=1,
+                 cluster_blocks=0, cluster_threads=0, cluster_split=0, group_threads=0, group_sites=0):
         self.samples, self.R, self.inst_base, self.precision = list(samples), replicas, inst_base, precision
         self.launches = self.sweeps = 0
         self.sweep_ms = 0.0
@@ -108,7 +109,7 @@ def fake_device(monkeypatch):
 def args(**kw):
     a = dict(gpus=1, steps=3, warmup=2, mcs=bench.MCS, impl="ours", side=bench.L_SIDE, depth=0, workload="sg256x32",
              policy="", variant=-1, analysis=False, ising=False, type_stats=False, snapshots=False, quick=False,
-             resident_smem=0, graphs=1)
+             resident_smem=0, graphs=1, cluster_blocks=0, cluster_threads=0, cluster_split=0, group_threads=0)
     a.update(kw)
     return types.SimpleNamespace(**a)
 
